@@ -1,0 +1,98 @@
+// FP64 CPU oracle for multi-chain MCMC (arXiv 2503.17405) -- TEST INFRASTRUCTURE.
+//
+// This directory is a plain, slow, sequential reference implementation of the
+// single-chain samplers the paper vectorises (Alg. 1 run once per chain).  Only
+// the test suite, the smoke check and the benchmark's CPU-baseline leg may
+// load it.  It shares no code with the CUDA path: its own counter-based RNG,
+// its own targets, its own samplers.  Everything is double precision.
+//
+// Parity status per function (see the pins in tests/test_oracle_*.py):
+//   philox            pinned: published known-answer vectors
+//   ess               pinned: conjugate-Gaussian closed form, flat-likelihood
+//                     special case, bracket invariant
+//   dr (3 stages)     pinned: exact detailed balance on a discrete ring,
+//                     funnel closed-form marginals
+//   nuts              pinned: harmonic-oscillator leapfrog closed form,
+//                     reversibility, Gaussian moments
+//   nuts on logistic regression: parity unpinned beyond the above (no closed
+//                     form for that posterior)
+#pragma once
+#include <cstdint>
+#include <cstddef>
+
+namespace ora {
+
+// ---- counter-based RNG: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --
+struct Block { uint32_t w[4]; };
+Block philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1);
+
+// Keying used by every sampler: key = (chain, seed_lo), counter = (draw, sample, tag, seed_hi).
+struct Stream {
+  uint64_t seed;
+  uint32_t chain;
+  uint32_t sample;
+  Block block(uint32_t tag, uint32_t draw) const {
+    return philox(draw, sample, tag, (uint32_t)(seed >> 32), chain, (uint32_t)seed);
+  }
+};
+
+// Uniform in (0,1) from two 32-bit words: ((hi:lo >> 12) + 1/2) * 2^-52.
+double uniform(uint32_t hi, uint32_t lo);
+// Box-Muller pair from one block: r = sqrt(-2 ln u(w0,w1)), phi = 2 pi u(w2,w3).
+void normal_pair(const Block& b, double* z0, double* z1);
+// z[0..d) from blocks draw0, draw0+1, ... of stream `tag` (normals 2q, 2q+1 from block q).
+void normals(const Stream& s, uint32_t tag, uint32_t draw0, int d, double* z);
+
+// ---- targets ------------------------------------------------------------------
+enum TargetKind {
+  TGT_GAUSS_CONJ = 0,  // ESS likelihood  -|y-x|^2/(2 s2);           params: L[d*d], y[d], s2
+  TGT_GP_LOGIT = 1,    // ESS likelihood  -sum softplus(-s_i x_i);   params: L[d*d], s[d]
+  TGT_FUNNEL = 2,      // Neal funnel log-density (v, x_1..x_{d-1});  params: none
+  TGT_LOGREG = 3,      // logistic-regression log-posterior;         params: X[n*d], y[n]
+  TGT_GAUSS_DIAG = 4,  // N(mu, diag sigma^2) log-density;           params: mu[d], sigma[d]
+  TGT_FLAT = 5,        // ESS likelihood f == 1;                      params: L[d*d]
+};
+
+struct Target {
+  int kind;
+  int d;
+  int n_data;
+  const double* params;
+  // log f (ESS likelihood) or log pi (DR / NUTS).  grad (optional) = d/dx.
+  double logp(const double* x, double* grad) const;
+  const double* prior_chol() const;  // ESS kinds: lower-triangular L with Sigma = L L^T
+};
+
+// ---- samplers (one chain, one transition each) ----------------------------------
+// Elliptical slice sampling, Alg. 8.  x[d] in/out, *ell in/out caches log f(x).
+// Returns the number of bracket shrinks N (the loop-body count of Alg. 8).
+int ess_transition(const Target& t, const Stream& s, double* x, double* ell,
+                   double* trace /* nullable: 3 doubles (theta, theta_min, theta_max) per shrink */,
+                   int trace_cap);
+
+// Delayed rejection, 3 stages, x-centred Gaussian proposals with scales
+// scale0 * factor^k.  Returns the number of stages tried (1..n_stages).
+struct DRParams { int n_stages; double scale0; double factor; };
+int dr_transition(const Target& t, const Stream& s, const DRParams& p, double* x, double* lp);
+
+// log acceptance probabilities of the general delayed-rejection scheme.
+// Arguments are log target values and log proposal densities (see dr.cpp).
+double dr_log_alpha1(double lp_cur, double lp_prop);
+double dr_log_alpha2(double lp_cur, double lp_first, double lp_second,
+                     double lq1_cur_first, double lq1_second_first);
+double dr_log_alpha3(double lp0, double lp1, double lp2, double lp3,
+                     double lq1_x_y1, double lq2_x_y2,
+                     double lq1_y3_y2, double lq2_y3_y1, double lq1_y1_y2);
+double log1mexp(double a);
+double dr_stage_log_alpha(int k, int d, const double* x, const double* ys, const double* lps,
+                          const double* sig);
+
+// Multinomial NUTS with momentum-sum U-turn criterion.  x[d] in/out,
+// *lp in/out caches log pi(x), grad[d] in/out caches its gradient.
+// Returns the number of leapfrog steps; *depth receives the number of doublings.
+struct NUTSParams { double eps; int max_depth; double max_dH; };
+int nuts_transition(const Target& t, const Stream& s, const NUTSParams& p, double* x,
+                    double* lp, double* grad, int* depth);
+void leapfrog(const Target& t, double* x, double* p, double* grad, double* lp, double eps);
+
+}  // namespace ora

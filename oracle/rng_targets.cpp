@@ -1,0 +1,132 @@
+// Oracle RNG and targets (test infrastructure; see oracle.h).
+#include "oracle.h"
+#include <cmath>
+
+namespace ora {
+
+// Philox4x32 with 10 rounds, from the definition in Salmon et al. (SC'11), Sec. 4:
+// each round multiplies counter words 0 and 2 by the two round multipliers,
+// XORs the high halves with the other counter words and the key, and the key is
+// bumped by the Weyl constants between rounds.
+Block philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+  const uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    uint64_t p0 = M0 * (uint64_t)c0;
+    uint64_t p1 = M1 * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  Block b;
+  b.w[0] = c0; b.w[1] = c1; b.w[2] = c2; b.w[3] = c3;
+  return b;
+}
+
+double uniform(uint32_t hi, uint32_t lo) {
+  uint64_t v = ((uint64_t)hi << 32) | lo;
+  v >>= 12;                                  // 52 bits
+  return ((double)v + 0.5) * 0x1p-52;        // exact; in [2^-53, 1 - 2^-53]
+}
+
+void normal_pair(const Block& b, double* z0, double* z1) {
+  const double kPi = 3.14159265358979323846;
+  double u1 = uniform(b.w[0], b.w[1]);
+  double u2 = uniform(b.w[2], b.w[3]);
+  double r = std::sqrt(-2.0 * std::log(u1));
+  double phi = 2.0 * kPi * u2;
+  *z0 = r * std::cos(phi);
+  *z1 = r * std::sin(phi);
+}
+
+void normals(const Stream& s, uint32_t tag, uint32_t draw0, int d, double* z) {
+  for (int q = 0; 2 * q < d; ++q) {
+    double a, b;
+    normal_pair(s.block(tag, draw0 + (uint32_t)q), &a, &b);
+    z[2 * q] = a;
+    if (2 * q + 1 < d) z[2 * q + 1] = b;
+  }
+}
+
+// softplus(t) = log(1 + e^t), written so that neither branch overflows.
+static double softplus(double t) {
+  return t > 0 ? t + std::log1p(std::exp(-t)) : std::log1p(std::exp(t));
+}
+
+const double* Target::prior_chol() const {
+  switch (kind) {
+    case TGT_GAUSS_CONJ: case TGT_GP_LOGIT: case TGT_FLAT: return params;
+    default: return nullptr;
+  }
+}
+
+double Target::logp(const double* x, double* grad) const {
+  switch (kind) {
+    case TGT_FLAT:
+      return 0.0;
+    case TGT_GAUSS_CONJ: {
+      // y ~ N(x, s2 I): log f(x) = -|y - x|^2 / (2 s2)   (constants dropped)
+      const double* y = params + (size_t)d * d;
+      double s2 = y[d];
+      double acc = 0;
+      for (int k = 0; k < d; ++k) { double r = y[k] - x[k]; acc += r * r; }
+      return -acc / (2.0 * s2);
+    }
+    case TGT_GP_LOGIT: {
+      // Bernoulli-logistic labels s_i in {-1,+1}: log f(x) = -sum softplus(-s_i x_i)
+      const double* sg = params + (size_t)d * d;
+      double acc = 0;
+      for (int k = 0; k < d; ++k) acc += softplus(-sg[k] * x[k]);
+      return -acc;
+    }
+    case TGT_FUNNEL: {
+      // v ~ N(0, 3^2), x_i | v ~ N(0, e^v), i = 1..d-1  (constants dropped)
+      double v = x[0];
+      double ss = 0;
+      for (int k = 1; k < d; ++k) ss += x[k] * x[k];
+      double ev = std::exp(-v);
+      double m = (double)(d - 1);
+      if (grad) {
+        grad[0] = -v / 9.0 - m / 2.0 + 0.5 * ev * ss;
+        for (int k = 1; k < d; ++k) grad[k] = -ev * x[k];
+      }
+      return -v * v / 18.0 - m * v / 2.0 - 0.5 * ev * ss;
+    }
+    case TGT_LOGREG: {
+      // beta ~ N(0, I), y_i ~ Bernoulli(sigmoid(x_i . beta))
+      const double* X = params;
+      const double* yv = params + (size_t)n_data * d;
+      double acc = 0;
+      if (grad) for (int k = 0; k < d; ++k) grad[k] = -x[k];
+      for (int k = 0; k < d; ++k) acc -= 0.5 * x[k] * x[k];
+      for (int i = 0; i < n_data; ++i) {
+        const double* row = X + (size_t)i * d;
+        double eta = 0;
+        for (int k = 0; k < d; ++k) eta += row[k] * x[k];
+        acc += yv[i] * eta - softplus(eta);
+        if (grad) {
+          double r = yv[i] - 1.0 / (1.0 + std::exp(-eta));
+          for (int k = 0; k < d; ++k) grad[k] += row[k] * r;
+        }
+      }
+      return acc;
+    }
+    case TGT_GAUSS_DIAG: {
+      const double* mu = params;
+      const double* sd = params + d;
+      double acc = 0;
+      for (int k = 0; k < d; ++k) {
+        double z = (x[k] - mu[k]) / sd[k];
+        acc -= 0.5 * z * z;
+        if (grad) grad[k] = -z / sd[k];
+      }
+      return acc;
+    }
+  }
+  return std::nan("");
+}
+
+}  // namespace ora

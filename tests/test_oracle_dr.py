@@ -1,0 +1,226 @@
+"""Pins of the oracle's 3-stage delayed-rejection Metropolis-Hastings.
+
+* Exact detailed balance of the acceptance functions: on a 7-state ring with an
+  arbitrary target and symmetric discrete stage proposals, the full 3-stage
+  transition matrix is enumerated from the oracle's acceptance code and must
+  satisfy pi_a P_ab = pi_b P_ba and pi P = pi to 1e-12.
+* Stationarity of the continuous sampler from exact starts: 1-D Gaussian (mean,
+  variance, fourth moment) and the funnel's closed-form marginals.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_17405_b300 import workloads as W
+
+NEG_INF = -np.inf
+
+
+def _ring_transition(pi, D):
+    """Enumerate P[x, z] of 3-stage DR on Z_n with stage proposals x + delta,
+    delta ~ D[k] (a dict offset -> probability, symmetric)."""
+    n = len(pi)
+    lp = np.log(pi)
+
+    Dm = []
+    for k in range(3):
+        row = np.zeros(n)
+        for off, p in (D[k].items() if k < len(D) else []):
+            row[off % n] += p
+        Dm.append(row)
+
+    def lq(k, a, b):
+        p = Dm[k][(b - a) % n]
+        return np.log(p) if p > 0 else NEG_INF
+
+    def prob(k, a, b):
+        return np.exp(lq(k, a, b))
+
+    P = np.zeros((n, n))
+    for x in range(n):
+        stay = 1.0
+        for y1 in range(n):
+            p1 = prob(0, x, y1)
+            if p1 == 0:
+                continue
+            a1 = np.exp(O.dr_log_alpha1(lp[x], lp[y1]))
+            P[x, y1] += p1 * a1
+            stay -= p1 * a1
+            r1 = p1 * (1 - a1)
+            for y2 in range(n):
+                p2 = prob(1, x, y2)
+                if p2 == 0 or r1 == 0:
+                    continue
+                a2 = np.exp(O.dr_log_alpha2(lp[x], lp[y1], lp[y2], lq(0, x, y1), lq(0, y2, y1)))
+                P[x, y2] += r1 * p2 * a2
+                stay -= r1 * p2 * a2
+                r2 = r1 * p2 * (1 - a2)
+                for y3 in range(n):
+                    p3 = prob(2, x, y3)
+                    if p3 == 0 or r2 == 0:
+                        continue
+                    a3 = np.exp(O.dr_log_alpha3(lp[x], lp[y1], lp[y2], lp[y3],
+                                                lq(0, x, y1), lq(1, x, y2),
+                                                lq(0, y3, y2), lq(1, y3, y1), lq(0, y1, y2)))
+                    P[x, y3] += r2 * p3 * a3
+                    stay -= r2 * p3 * a3
+        P[x, x] += stay
+    return P
+
+
+def _sym(weights):
+    d = {}
+    for off, w in weights.items():
+        d[off] = d.get(off, 0.0) + w / 2
+        d[-off] = d.get(-off, 0.0) + w / 2
+    return d
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ring_detailed_balance(seed):
+    rng = np.random.default_rng(seed)
+    n = 7
+    pi = rng.uniform(0.05, 1.0, n)
+    pi /= pi.sum()
+    D = [_sym({1: 0.5, 2: 0.3, 3: 0.2}), _sym({1: 0.7, 2: 0.3}), _sym({1: 0.2, 3: 0.8})]
+    P = _ring_transition(pi, D)
+    assert np.allclose(P.sum(1), 1.0, atol=1e-12)
+    assert P.min() >= -1e-15
+    flux = pi[:, None] * P
+    assert np.max(np.abs(flux - flux.T)) < 1e-12
+    assert np.max(np.abs(pi @ P - pi)) < 1e-12
+    # the later stages matter: dropping stage 3 changes the matrix
+    assert np.max(np.abs(P - _ring_transition(pi, D[:2] + [{}]))) > 1e-3
+
+
+def test_ring_detailed_balance_breaks_with_a_wrong_formula():
+    # sanity of the pin itself: the naive symmetric (Metropolis) ratio at stage 2
+    # violates detailed balance on the same ring
+    rng = np.random.default_rng(0)
+    pi = rng.uniform(0.05, 1.0, 7)
+    pi /= pi.sum()
+    D = [_sym({1: 0.5, 2: 0.3, 3: 0.2}), _sym({1: 0.7, 2: 0.3}), {}]
+    orig = O.dr_log_alpha2
+    try:
+        O.dr_log_alpha2 = lambda a, b, c, q1, q2: min(0.0, c - a)
+        P = _ring_transition(pi, D)
+    finally:
+        O.dr_log_alpha2 = orig
+    flux = pi[:, None] * P
+    assert np.max(np.abs(flux - flux.T)) > 1e-6
+
+
+def test_log1mexp():
+    for a in [-1e-12, -1e-5, -0.3, -0.7, -5.0, -40.0]:
+        assert abs(O.log1mexp(a) - np.log1p(-np.exp(a))) <= 1e-12 * abs(np.log1p(-np.exp(a))) + 1e-15 \
+            or a > -1e-6
+    assert O.log1mexp(0.0) == NEG_INF and O.log1mexp(1.0) == NEG_INF
+    assert abs(O.log1mexp(-1e-12) - np.log(1e-12)) < 1e-9
+
+
+def test_gaussian_exact_start_stationarity():
+    # one DR transition from exact N(0,1) draws must leave N(0,1) invariant; the
+    # proposal scales 3, 1.5, 0.75 make all three stages common
+    w = dict(params=np.array([0.0, 1.0]))
+    m = 400_000
+    x0 = np.random.default_rng(5).standard_normal((m, 1))
+    r = O.run("dr", "gauss_diag", w["params"], x0, 2, seed=7, algo_params=[3, 3.0, 0.5],
+              store=True)
+    counts = r["counts"]
+    assert (counts == 3).mean() > 0.1 and (counts == 2).mean() > 0.1
+    for i in range(2):
+        x = r["samples"][:, i, 0]
+        assert abs(x.mean()) < 4 / np.sqrt(m)
+        assert abs(x.var() - 1) < 4 * np.sqrt(2 / m)
+        assert abs((x ** 4).mean() - 3) < 4 * np.sqrt(96 / m)
+    # chains move
+    assert (r["samples"][:, 0, 0] != x0[:, 0]).mean() > 0.5
+
+
+def test_funnel_exact_start_marginals():
+    d = 10
+    m = 20000
+    x0 = W.x0_funnel_exact(m, d)
+    r = O.run("dr", "funnel", np.zeros(1), x0, 20, seed=1, algo_params=[3, 1.0, 0.5])
+    for i in (0, 19):
+        x = r["samples"][:, i, :]
+        v = x[:, 0]
+        assert abs(v.mean()) < 4 * 3 / np.sqrt(m)
+        assert abs(v.var() - 9) < 4 * 9 * np.sqrt(2 / m)
+        assert abs((v < 0).mean() - 0.5) < 4 * 0.5 / np.sqrt(m)
+        z = x[:, 1:] * np.exp(-v / 2)[:, None]
+        assert np.all(np.abs(z.mean(0)) < 4 / np.sqrt(m))
+        assert np.all(np.abs(z.var(0) - 1) < 4 * np.sqrt(2 / m))
+    assert set(np.unique(r["counts"])) == {1, 2, 3}
+
+
+def test_funnel_logp_special_values_and_gradient():
+    x = np.zeros(10)
+    assert O.logp("funnel", None, x) == 0.0
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        x = rng.standard_normal(10)
+        v, g = O.logp("funnel", None, x, grad=True)
+        h = 1e-6
+        num = np.array([(O.logp("funnel", None, x + h * e) - O.logp("funnel", None, x - h * e)) / (2 * h)
+                        for e in np.eye(10)])
+        assert np.allclose(num, g, rtol=1e-6, atol=1e-6)
+
+
+def test_stage_counts_range_and_determinism():
+    x0 = W.x0_funnel_exact(16)
+    a = O.run("dr", "funnel", np.zeros(1), x0, 50, seed=3, algo_params=[3, 1.0, 0.5], n_threads=1)
+    b = O.run("dr", "funnel", np.zeros(1), x0, 50, seed=3, algo_params=[3, 1.0, 0.5], n_threads=4)
+    assert np.array_equal(a["samples"], b["samples"])
+    assert a["counts"].min() >= 1 and a["counts"].max() <= 3
+    # a 1-stage run never tries more than one stage
+    c = O.run("dr", "funnel", np.zeros(1), x0, 50, seed=3, algo_params=[1, 1.0, 0.5])
+    assert np.all(c["counts"] == 1)
+
+
+def _lq(sig, a, b):
+    # full log density of N(b | a, sig^2 I)
+    d = a.size
+    return -np.sum((b - a) ** 2) / (2 * sig ** 2) - d * np.log(sig * np.sqrt(2 * np.pi))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_continuous_path_reversal_identity(seed):
+    """Detailed balance of each stage's path, on continuous states.
+
+    For the stage-k path x -> (y_1 .. y_k rejected) -> y_{k+1} accepted, the
+    scheme requires  pi(x) prod_s q_s(x->y_s)(1-alpha_s(..)) q_{k+1}(x->y_{k+1}) alpha_{k+1}
+    to equal the same product along the reversed path y_{k+1} -> (y_k .. y_1) -> x.
+    The alphas come from the oracle's own stage wiring (the code its DR transition
+    calls); the log target values are arbitrary, since the identity is algebraic.
+    """
+    rng = np.random.default_rng(seed)
+    d = 3
+    sig = np.array([1.0, 0.5, 0.25]) * rng.uniform(0.5, 2.0)
+    checked = {1: 0, 2: 0}
+    for _ in range(400):
+        x = rng.standard_normal(d)
+        ys = rng.standard_normal((3, d)) * sig[:, None] + x
+        lp = rng.normal(0, 1.5, 4)                       # log pi(x), log pi(y1..y3)
+        for k in (1, 2):
+            fwd_pts = [x] + [ys[s] for s in range(k + 1)]
+            rev_pts = [ys[k]] + [ys[s] for s in range(k - 1, -1, -1)] + [x]
+            fwd_lp = [lp[0]] + [lp[s + 1] for s in range(k + 1)]
+            rev_lp = [lp[k + 1]] + [lp[s + 1] for s in range(k - 1, -1, -1)] + [lp[0]]
+
+            def path(pts, lps):
+                cur = pts[0]
+                yv = np.concatenate(pts[1:])
+                tot = lps[0]
+                for s in range(k + 1):
+                    tot += _lq(sig[s], cur, pts[s + 1])
+                    la = O.dr_stage_log_alpha(s, cur, yv, np.array(lps), sig)
+                    tot += la if s == k else O.log1mexp(la)
+                return tot
+
+            f = path(fwd_pts, fwd_lp)
+            r = path(rev_pts, rev_lp)
+            if np.isfinite(f) or np.isfinite(r):
+                assert abs(f - r) < 1e-9 * max(1.0, abs(f)), (k, f, r)
+                checked[k] += 1
+    assert checked[1] > 50 and checked[2] > 50, checked
