@@ -1,0 +1,336 @@
+"""Benchmark: samples/s of the FSM engine vs the synchronised kernel on one B300.
+
+Default workload (the headline configuration): elliptical slice sampling on latent GP
+classification, d = 256, 16384 chains x 2000 samples, FP32, every sample stored on the
+device.  One step = one whole job (all chains to n samples) through the C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config ess_gp|ess_gauss|dr_funnel|nuts_logreg]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own job on its own GPU
+(chains are independent: weak scaling, no collective on the data path); value is the
+total over ranks divided by the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2503_17405_b300 import workloads as W  # noqa: E402
+
+METRIC = "samples/s FSM vs synchronized kernel on 1 B300 at oracle tolerance; p50/p99 job latency"
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2032.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---- workloads ------------------------------------------------------------------------------
+def make_config(name, scale=1.0):
+    """Returns (spec dict) for a named configuration."""
+    if name == "ess_gp":
+        w = W.gp_logit(256)
+        m, n = int(16384 * scale), 2000
+        return dict(name="ess_gp_logit_d256_m16384_n2000", algo="ess", w=w, m=m, n=n, prec="fp32",
+                    x0=W.x0_zeros(m, 256), algo_params=None,
+                    flops_per_column=256 * 257)   # nu = L z: d(d+1)/2 FMA = d(d+1) flops
+    if name == "ess_gauss":
+        w = W.gauss_conj(16)
+        m, n = 128, 1000
+        return dict(name="ess_gauss_conj_d16_m128_n1000", algo="ess", w=w, m=m, n=n, prec="fp64",
+                    x0=W.x0_zeros(m, 16), algo_params=None, flops_per_column=16 * 17)
+    if name == "dr_funnel":
+        w = W.funnel(10)
+        m, n = int(65536 * scale), 5000
+        return dict(name="dr3_funnel_d10_m65536_n5000", algo="dr", w=w, m=m, n=n, prec="fp32",
+                    x0=W.x0_funnel_exact(m), algo_params=[3, 1.0, 0.5])
+    if name == "nuts_logreg":
+        w = W.logreg(1000, 25)
+        m, n = int(4096 * scale), 1000
+        return dict(name="nuts_logreg_n1000_d25_m4096_n1000", algo="nuts", w=w, m=m, n=n,
+                    prec="fp32", x0=W.x0_logreg(w, m), algo_params=[0.05, 10, 1000.0])
+    raise SystemExit(f"unknown config {name}")
+
+
+# ---- clocks during the timed region ----------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---- the oracle on the host cores --------------------------------------------------------------
+def oracle_throughput(cfg, target_s=10.0):
+    from oracle import oracle as O
+    w = cfg["w"]
+    cores = os.cpu_count() or 1
+    n_s = min(cfg["n"], 200)
+    m = max(cores, 8)
+    t = 0.0
+    while True:
+        x0 = cfg["x0"][:m] if len(cfg["x0"]) >= m else np.resize(cfg["x0"], (m, w["d"]))
+        t0 = time.perf_counter()
+        O.run(cfg["algo"], w["kind"], w["params"], x0, n_s, seed=1, n_data=w["n_data"],
+              algo_params=cfg["algo_params"], n_threads=cores, store=False)
+        t = time.perf_counter() - t0
+        if t >= target_s / 4 or m >= 65536:
+            break
+        m = min(65536, int(m * max(2.0, target_s / max(t, 1e-3) / 2)))
+    return {"value": m * n_s / t, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{m} chains x {n_s} samples of {cfg['name']} (FP64, {t:.1f} s)"}
+
+
+# ---- our arm ---------------------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_2503_17405_b300 import fsmc
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    cfg = make_config(args.config)
+    w, m, n = cfg["w"], cfg["m"], cfg["n"]
+    eng = fsmc.Engine(dev)
+    tg = eng.target(w["kind"], w["d"], w["params"], n_data=w["n_data"])
+    dr = nuts = None
+    if cfg["algo"] == "dr":
+        dr = dict(zip(["n_stages", "scale0", "factor"], cfg["algo_params"]))
+    if cfg["algo"] == "nuts":
+        nuts = dict(zip(["eps", "max_depth", "max_dH"], cfg["algo_params"]))
+    tuning = {"profile_kernels": 1}
+    job = eng.job(tg, cfg["algo"], m, n, x0=cfg["x0"], seed=1 + rank, prec=cfg["prec"], store=True,
+                  dr=dr, nuts=nuts, tuning=tuning)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one(mode):
+        job.reset()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        job.run(mode, stream=sp)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), job.stats()
+
+    for _ in range(args.warmup):
+        one("fsm")
+    clocks = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    fsm_ms, stats = [], []
+    for _ in range(args.steps):
+        ms, st = one("fsm")
+        fsm_ms.append(ms)
+        stats.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(fsm_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * m * n / (total_ms / 1e3)
+
+    # synchronised kernel on the same job (Alg. 6), fewer steps: it is the slow baseline
+    sync = None
+    if not args.no_sync:
+        one("sync")  # warm-up
+        sms, sst = [], None
+        for _ in range(args.sync_steps):
+            ms, sst = one("sync")
+            sms.append(ms)
+        sync = {"value": m * n / (sum(sms) / len(sms) / 1e3), "ms_per_step": sum(sms) / len(sms),
+                "sync_iterations": sst["sync_iterations"], "mean_max_N": sst["mean_max_N"]}
+
+    st = stats[-1]
+    kms = [sum(s["kernel_ms"][k] for s in stats) for k in range(4)]
+    kl = [sum(s["kernel_launches"][k] for s in stats) for k in range(4)]
+    launches = sum(s["launches"] for s in stats)
+    # predicted E(m) (Sec. 4.2, K = 1 after bundling, alpha = 1): per-sample cost of the
+    # state-independent part c_gen plus one evaluation per loop-body iteration
+    steps_total = sum(s["fsm_steps"] for s in stats)
+    c_step = kms[1] / max(1, steps_total)
+    cols = sum(s["columns_generated"] for s in stats)
+    c_gen = kms[0] / max(1, cols) if cols else 0.0
+    E_pred = (c_gen + c_step * (1 + st["mean_max_N"])) / (c_gen + c_step * (1 + st["mean_N"])) \
+        if cfg["algo"] == "ess" else st["mean_max_N"] / max(st["mean_N"], 1e-9)
+
+    peaks = _peaks()
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = None
+    if cfg["algo"] == "ess" and kms[0] >= kms[1]:
+        achieved = cols * cfg["flops_per_column"] / (kms[0] / 1e3) / 1e12
+        roof = {"kernel": "ess_nu_gen_kernel", "bound": "alu", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": None,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (nominal)"}
+    else:
+        ms_per_launch = kms[1] / max(1, kl[1])
+        roof = {"kernel": f"{cfg['algo']}_fsm_kernel", "bound": "alu", "achieved": None,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "ms_per_launch": ms_per_launch}
+
+    # end to end through the public API: host params and x0 in, posterior moments out
+    e2e = None
+    if not args.no_e2e:
+        params_h = torch.from_numpy(np.ascontiguousarray(w["params"], dtype=np.float64)).pin_memory()
+        x0_h = torch.from_numpy(np.ascontiguousarray(cfg["x0"], dtype=np.float64)).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tg2 = eng.target(w["kind"], w["d"], params_h.numpy(), n_data=w["n_data"])
+        job2 = eng.job(tg2, cfg["algo"], m, n, x0=x0_h.numpy(), seed=1 + rank, prec=cfg["prec"],
+                       store=True, dr=dr, nuts=nuts)
+        job2.run("fsm", stream=sp)
+        sx, sx2, nk = job2.moments()
+        t1 = time.perf_counter()
+        job2.close()
+        e2e = {"value": m * n / (t1 - t0), "unit": "samples/s",
+               "h2d_bytes_per_step": int(params_h.numel() * 8 + x0_h.numel() * 8),
+               "d2h_bytes_per_step": int(sx.nbytes + sx2.nbytes + nk.nbytes)}
+    out = None
+    if rank == 0:
+        cpu = None if (args.no_cpu or world > 1) else oracle_throughput(cfg)
+        out = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if cfg["prec"] == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "chains_per_gpu": m, "samples_per_chain": n,
+                       "d": w["d"], "algo": cfg["algo"], "store": "all samples on device",
+                       "l2": "flushed between steps (256 MiB write); outputs exceed L2",
+                       "parallelism": f"replicas x{world} (independent chains)"},
+            "fsm": {"value": value, "R_hat": st["R_hat"], "mean_N": st["mean_N"],
+                    "mean_max_N": st["mean_max_N"], "E_pred": E_pred,
+                    "kernel_ms_per_step": [k / args.steps for k in kms],
+                    "kernel_launches_per_step": [k / args.steps for k in kl]},
+            "sync": sync,
+            "speedup_fsm_over_sync": (value / world / sync["value"]) if sync else None,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+        }
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cfg = make_config(args.config)
+    times, vals = [], []
+    cpu = None
+    for _ in range(args.warmup + args.steps):
+        cpu = oracle_throughput(cfg, target_s=max(2.0, 20.0 / max(1, args.steps + args.warmup)))
+        vals.append(cpu["value"])
+    vals = vals[args.warmup:]
+    value = statistics.mean(vals)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cfg["m"] * cfg["n"] / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "chains_per_gpu": cfg["m"],
+                       "samples_per_chain": cfg["n"], "d": cfg["w"]["d"], "algo": cfg["algo"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="ess_gp")
+    ap.add_argument("--sync-steps", type=int, default=1)
+    ap.add_argument("--no-sync", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.impl == "reference" else 1))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        from paper_2503_17405_b300 import build
+        if rank == 0:
+            build.build()
+        out = run_ours(args, rank, world)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

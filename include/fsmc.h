@@ -1,0 +1,216 @@
+/* fsmc -- finite-state-machine multi-chain MCMC on one GPU (B300, sm_103a).
+ *
+ * C ABI of libfsmc.so.  The library advances m independent Markov chains of one
+ * of three samplers whose single-chain transition contains a data-dependent
+ * while loop (arXiv 2503.17405):
+ *   - elliptical slice sampling (appendix Alg. 8; shrinking bracket loop),
+ *   - delayed-rejection Metropolis-Hastings, 3 stages (Sec. 7.1; staged proposals),
+ *   - the No-U-Turn sampler, multinomial form (Sec. 7.3; nested doubling loops).
+ * Two execution modes implement the two multi-chain programs the paper compares:
+ *   FSMC_MODE_FSM   each chain runs as a finite state machine (Sec. 3, Algs. 2/4/5,
+ *                   7/9): a launch moves every chain by a fixed budget of states, so
+ *                   no chain waits for another;
+ *   FSMC_MODE_SYNC  the vectorised sample() of Alg. 6: every iteration of every while
+ *                   loop is a grid-wide step, so all chains wait for the slowest one.
+ * Both modes consume the same counter-based random numbers, keyed by
+ * (chain, sample, draw), so they produce identical samples (Sec. 2.1: sample(x, r)).
+ *
+ * Conventions
+ *   - Every call returns an fsmc_status; nothing aborts or throws across the ABI.
+ *     fsmc_last_error() returns a thread-local message for the last failure.
+ *   - The caller owns every host buffer it passes; host buffers are only read or
+ *     written during the call.  The library owns every device allocation it makes.
+ *   - Array layouts are row-major (C order).  Chain index j, sample index i,
+ *     coordinate k: samples are [chain][sample][coordinate].
+ *   - Streams are cudaStream_t passed as void*; NULL means the legacy default stream.
+ *   - Reads are synchronous on the job's stream and widen to double.
+ *   - Objects are not thread-safe; use one thread per job (the serving scheduler
+ *     created by fsmc_submit serialises its own jobs).
+ */
+#ifndef FSMC_H_
+#define FSMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsmc_engine fsmc_engine;
+typedef struct fsmc_target fsmc_target;
+typedef struct fsmc_job fsmc_job;
+
+typedef enum fsmc_status {
+  FSMC_OK = 0,
+  FSMC_EINVAL = -1,   /* invalid argument (sizes, kinds, NULL pointers)          */
+  FSMC_ENOMEM = -2,   /* a device or host allocation failed                       */
+  FSMC_EADMIT = -3,   /* the job's device footprint exceeds the engine's budget   */
+  FSMC_ECUDA = -4,    /* a CUDA runtime call failed; see fsmc_last_error()        */
+  FSMC_ETIMEOUT = -5, /* a bounded device-side wait expired (error word set)      */
+  FSMC_ESTATE = -6,   /* call not valid in the object's current state             */
+  FSMC_EDEVICE = -7   /* a kernel raised its error word (e.g. shrink cap reached) */
+} fsmc_status;
+
+/* Targets.  params_host layouts (doubles, row-major):
+ *   GAUSS_CONJ  ESS likelihood -|y - x|^2 / (2 s2):  L[d*d] (prior Cholesky), y[d], s2
+ *   GP_LOGIT    ESS likelihood -sum_k softplus(-s_k x_k): L[d*d], s[d] (labels in {-1,+1})
+ *   FLAT        ESS likelihood f == 1 (prior draws):    L[d*d]
+ *   FUNNEL      Neal funnel, v ~ N(0,9), x_i|v ~ N(0,e^v): no params (n_params = 0)
+ *   LOGREG      beta ~ N(0,I), y_i ~ Bern(sigmoid(X_i beta)): X[n_data*d], y[n_data]
+ *   GAUSS_DIAG  N(mu, diag(sigma^2)):                     mu[d], sigma[d]
+ * ESS needs a kind with a prior factor L (GAUSS_CONJ, GP_LOGIT, FLAT); DR and NUTS need
+ * a full log-density (FUNNEL, LOGREG, GAUSS_DIAG).  The ESS prior is N(0, L L^T) (Alg. 8). */
+typedef enum fsmc_target_kind {
+  FSMC_TGT_GAUSS_CONJ = 0,
+  FSMC_TGT_GP_LOGIT = 1,
+  FSMC_TGT_FUNNEL = 2,
+  FSMC_TGT_LOGREG = 3,
+  FSMC_TGT_GAUSS_DIAG = 4,
+  FSMC_TGT_FLAT = 5
+} fsmc_target_kind;
+
+typedef enum fsmc_algo { FSMC_ESS = 0, FSMC_DR = 1, FSMC_NUTS = 2 } fsmc_algo;
+
+/* FP64: every floating-point operation in double.  FP32: the production mode, single
+ * precision throughout (see fsmc_job_create). */
+typedef enum fsmc_precision { FSMC_FP64 = 0, FSMC_FP32 = 1 } fsmc_precision;
+
+typedef enum fsmc_mode { FSMC_MODE_FSM = 0, FSMC_MODE_SYNC = 1 } fsmc_mode;
+
+/* Delayed rejection: stage k (k = 0..n_stages-1) proposes y ~ N(x, (scale0 factor^k)^2 I). */
+typedef struct fsmc_dr_params {
+  int n_stages;  /* 1..3 */
+  double scale0;
+  double factor;
+} fsmc_dr_params;
+
+/* NUTS: leapfrog step eps, at most max_depth doublings, divergence when H - H0 > max_dH. */
+typedef struct fsmc_nuts_params {
+  double eps;
+  int max_depth; /* 1..10 */
+  double max_dH;
+} fsmc_nuts_params;
+
+/* Launch shape.  Zero fields mean "choose automatically" (the autotuner's cached
+ * choice, else a heuristic on the log-density cost). */
+typedef struct fsmc_tuning {
+  int lanes_per_chain;   /* 1 = chain-per-thread, 32 = chain-per-warp, 0 = auto          */
+  int steps_per_launch;  /* FSM states each chain advances per launch                    */
+  int ring_slots;        /* ESS: pre-generated ellipse directions kept per chain         */
+  int threads_per_block; /* 32..256, multiple of 32                                      */
+  int profile_kernels;   /* 1: time every launch with CUDA events (see fsmc_stats)        */
+} fsmc_tuning;
+
+/* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */
+typedef struct fsmc_stats {
+  double R_hat;            /* mean_i max_j N_ij / mean_ij N_ij over completed samples    */
+  double mean_N;           /* mean_ij N_ij                                               */
+  double mean_max_N;       /* mean_i max_j N_ij                                          */
+  int64_t samples_done;    /* sum_j t_j                                                  */
+  int64_t fsm_steps;       /* FSM states executed, summed over chains                    */
+  int64_t sync_iterations; /* SYNC: loop-body iterations executed (sum_i max_j N_ij)     */
+  int64_t launches;        /* kernel launches issued by the last run call                */
+  double device_ms;        /* device time of the last run call (CUDA events)             */
+  int64_t error_word;      /* OR of kernel error bits (1 shrink cap, 2 barrier timeout,
+                              4 non-finite log-density treated as -inf)                  */
+  /* With tuning.profile_kernels: device time and launch count per kernel class over the
+   * last run call.  Class 0: ESS direction generator (nu = L z); 1: FSM step kernel;
+   * 2: synchronised kernel; 3: everything else (fills, resets). */
+  double kernel_ms[4];
+  int64_t kernel_launches[4];
+  int64_t columns_generated; /* ESS: (chain, sample) directions produced by class 0       */
+} fsmc_stats;
+
+/* ---- engine ----------------------------------------------------------------------
+ * Binds the calling thread to `device` and sets the HBM budget for admission
+ * (0 = 90% of the free memory at creation).  Errors: EINVAL, ECUDA, ENOMEM. */
+fsmc_status fsmc_engine_create(int device, size_t hbm_budget_bytes, fsmc_engine** out);
+/* Waits for the serving scheduler, frees every remaining job and target. */
+void fsmc_engine_destroy(fsmc_engine* e);
+/* Device bytes currently held by targets and jobs of this engine. */
+size_t fsmc_engine_bytes_in_use(const fsmc_engine* e);
+
+/* ---- targets (L1: the log-density, Sec. 7 workloads) ------------------------------
+ * Copies params_host (n_params doubles, layout above) to the device in both precisions.
+ * Errors: EINVAL (kind/d/n_data/n_params mismatch), ENOMEM, ECUDA. */
+fsmc_status fsmc_target_create(fsmc_engine* e, fsmc_target_kind kind, int d, int n_data,
+                               const double* params_host, size_t n_params, fsmc_target** out);
+void fsmc_target_destroy(fsmc_target* t);
+
+/* ---- jobs ------------------------------------------------------------------------------
+ * m = n_chains chains of `algo` on target t, n_samples samples each (Alg. 3 / Alg. 7).
+ * algo_params: NULL for ESS, const fsmc_dr_params* for DR, const fsmc_nuts_params* for NUTS.
+ * x0_host: [n_chains][d] starting points (NULL = zeros).  seed keys the random numbers:
+ * chain j, sample i, draw q use Philox4x32-10 with key (j, seed_lo) and counter
+ * (q, i, tag, seed_hi).  store_samples: 1 keeps every sample on the device
+ * (n_chains*n_samples*d values), 0 keeps per-chain running sums of x and x^2 only.
+ * Errors: EINVAL (algo/target mismatch, sizes), EADMIT (footprint over the budget; the
+ * footprint is reported in fsmc_last_error), ENOMEM, ECUDA. */
+fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo algo,
+                            const void* algo_params, fsmc_precision prec, int64_t n_chains,
+                            int64_t n_samples, const double* x0_host, uint64_t seed,
+                            int store_samples, fsmc_job** out);
+/* Overrides the launch shape before the first run (EINVAL for unsupported values). */
+fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tuning);
+fsmc_status fsmc_job_get_tuning(const fsmc_job* j, fsmc_tuning* tuning);
+/* Device bytes the job holds. */
+size_t fsmc_job_bytes(const fsmc_job* j);
+
+/* Advances the job on `cuda_stream` (cudaStream_t as void*) and returns when done.
+ * FSM mode: runs until every chain has n_samples samples, or, if max_fsm_steps > 0,
+ * until every unfinished chain has advanced at least max_fsm_steps states more (a
+ * resumable partial run).  SYNC mode runs to completion (max_fsm_steps ignored).
+ * A job can be run several times in FSM mode to resume; SYNC requires a fresh or
+ * reset job.  Errors: ESTATE, ECUDA, ETIMEOUT, EDEVICE. */
+fsmc_status fsmc_job_run(fsmc_job* j, fsmc_mode mode, int64_t max_fsm_steps, void* cuda_stream);
+/* Returns the job to its initial state (x0, zero samples) keeping its allocations. */
+fsmc_status fsmc_job_reset(fsmc_job* j);
+/* Smallest per-chain sample count and whether every chain is finished. */
+fsmc_status fsmc_job_progress(fsmc_job* j, int64_t* min_samples, int* done);
+
+/* Copies samples [chain0, chain0+n_chains) x [sample0, sample0+n_samp) to dst_host
+ * ([n_chains][n_samp][d] doubles).  ESTATE if the job keeps moments only. */
+fsmc_status fsmc_read_samples(fsmc_job* j, int64_t chain0, int64_t n_chains, int64_t sample0,
+                              int64_t n_samp, double* dst_host);
+/* Same, to device memory in the job's precision (float or double, [n_chains][n_samp][d]). */
+fsmc_status fsmc_read_samples_dev(fsmc_job* j, int64_t chain0, int64_t n_chains,
+                                  int64_t sample0, int64_t n_samp, void* dst_dev,
+                                  void* cuda_stream);
+/* counts_host [n_chains][n_samples]: loop-body count N_ij (ESS shrinks, DR stages tried,
+ * NUTS leapfrog steps); -1 where not yet sampled.  aux_host (nullable) [n_chains][n_samples]:
+ * NUTS tree depth.  fsm_steps_host (nullable) [n_chains]: states executed per chain. */
+fsmc_status fsmc_read_loop_counts(fsmc_job* j, int32_t* counts_host, int32_t* aux_host,
+                                  int64_t* fsm_steps_host);
+/* Current state x of every chain, [n_chains][d]. */
+fsmc_status fsmc_read_state(fsmc_job* j, double* x_host);
+/* Per-chain running sums over kept samples: sum_x, sum_x2 [n_chains][d]; n_kept [n_chains]. */
+fsmc_status fsmc_read_moments(fsmc_job* j, double* sum_x, double* sum_x2, int64_t* n_kept);
+fsmc_status fsmc_read_stats(fsmc_job* j, fsmc_stats* out);
+
+/* Checkpoint / resume: the full FSM state (state ids, per-chain variables, sample
+ * counters, samples and counts).  Pass host_buf = NULL to query *bytes. */
+fsmc_status fsmc_job_snapshot(fsmc_job* j, void* host_buf, size_t* bytes);
+fsmc_status fsmc_job_restore(fsmc_job* j, const void* host_buf, size_t bytes);
+void fsmc_job_destroy(fsmc_job* j);
+
+/* ---- serving: continuous batching ----------------------------------------------------
+ * fsmc_submit queues a created job; the engine's scheduler thread admits queued jobs
+ * as HBM budget allows (their allocations are made at admission), advances every
+ * admitted job by one fused FSM launch per round (all admitted jobs of a kind share
+ * one persistent launch), retires finished jobs and frees their memory.  Arrival
+ * time is the submit call; latency is completion minus arrival.  SYNC-mode submits run
+ * one job at a time to completion (the synchronised baseline).
+ * Errors: EINVAL, ESTATE (already submitted or run). */
+fsmc_status fsmc_submit(fsmc_engine* e, fsmc_job* j, fsmc_mode mode);
+/* *done = 1 when the job has finished; *latency_s = completion - submit (seconds). */
+fsmc_status fsmc_poll(fsmc_job* j, int* done, double* latency_s);
+/* Blocks until every submitted job has finished or timeout_s elapses (ETIMEOUT). */
+fsmc_status fsmc_wait_all(fsmc_engine* e, double timeout_s);
+
+const char* fsmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSMC_H_ */

@@ -1,0 +1,372 @@
+// Delayed-rejection Metropolis-Hastings with up to three stages as a finite state machine.
+//
+// Fig. 2 ("Delayed Rejection MH") has INIT, PROPOSE (the loop body) and DONE; INIT and
+// DONE are nearly empty, so the FSM is condensed to the single PROPOSE state (Sec. 7.1,
+// "FSM-condensed"): one step proposes the next stage's y_k ~ N(x, sigma_k^2 I), evaluates
+// log pi(y_k) (the amortised g), and either accepts, rejects for good after the last
+// stage, or keeps y_k for the next stage's acceptance ratio.  A sample takes exactly as
+// many steps as stages were tried.
+//
+// Acceptance is the general (Tierney-Mira) delayed-rejection rule for proposals centred
+// at the current point, in log space:
+//   a1(x, y1)         = min(0, lp(y1) - lp(x))
+//   a2(x, y1, y2)     = min(0, [lp(y2) + lq1(y2->y1) + l1m(a1(y2,y1))] - [lp(x) + lq1(x->y1) + l1m(a1(x,y1))])
+//   a3(x, y1, y2, y3) = min(0, [lp(y3) + lq1(y3->y2) + lq2(y3->y1) + l1m(a1(y3,y2)) + l1m(a2(y3,y2,y1))]
+//                             - [lp(x) + lq1(x->y1) + lq2(x->y2) + l1m(a1(x,y1)) + l1m(a2(x,y1,y2))])
+// with lq_s(a->b) = -|b-a|^2 / (2 sigma_s^2) and l1m(a) = log(1 - e^a).
+#include <algorithm>
+#include "fsmc_device.cuh"
+#include "fsmc_kernels.h"
+
+namespace fsmc {
+
+template <typename T>
+__device__ __forceinline__ T l1m(T a) {
+  if (!(a < T(0))) return neg_inf<T>();
+  if constexpr (sizeof(T) == 4)
+    return a > -0.693147181f ? logf(-expm1f(a)) : log1pf(-expf(a));
+  else
+    return a > -0.6931471805599453 ? log(-expm1(a)) : log1p(-exp(a));
+}
+
+template <typename T>
+__device__ __forceinline__ T la1(T lp_cur, T lp_prop) { return fmin(T(0), lp_prop - lp_cur); }
+
+template <typename T>
+__device__ __forceinline__ T la2(T pc, T pf, T ps, T q1_cf, T q1_sf) {
+  const T num = ps + q1_sf + l1m(la1(ps, pf));
+  const T den = pc + q1_cf + l1m(la1(pc, pf));
+  if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
+  return fmin(T(0), num - den);
+}
+
+template <typename T>
+__device__ __forceinline__ T la3(T p0, T p1, T p2, T p3, T q1_x_y1, T q2_x_y2, T q1_y3_y2,
+                                 T q2_y3_y1, T q1_y1_y2) {
+  const T num = p3 + q1_y3_y2 + q2_y3_y1 + l1m(la1(p3, p2)) + l1m(la2(p3, p2, p1, q1_y3_y2, q1_y1_y2));
+  const T den = p0 + q1_x_y1 + q2_x_y2 + l1m(la1(p0, p1)) + l1m(la2(p0, p1, p2, q1_x_y1, q1_y1_y2));
+  if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
+  return fmin(T(0), num - den);
+}
+
+// log pi for the full-density targets, one chain per thread
+template <typename T, int E>
+__device__ __forceinline__ T full_logp(const TargetView<T>& tg, const T (&y)[E]) {
+  const int d = tg.d;
+  if (tg.kind == TGT_FUNNEL) {
+    T ss = T(0);
+#pragma unroll
+    for (int e = 1; e < E; ++e)
+      if (e < d) ss = fma(y[e], y[e], ss);
+    const T v = y[0];
+    const T ev = sizeof(T) == 4 ? (T)expf(-(float)v) : (T)exp(-(double)v);
+    return -v * v / T(18) - T(d - 1) * v / T(2) - T(0.5) * ev * ss;
+  } else if (tg.kind == TGT_GAUSS_DIAG) {
+    T acc = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e < d) { const T z = (y[e] - tg.vec[e]) / tg.vec2[e]; acc = fma(z, z, acc); }
+    return -T(0.5) * acc;
+  } else if (tg.kind == TGT_LOGREG) {
+    T acc = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e < d) acc = fma(y[e], y[e], acc);
+    acc *= -T(0.5);
+    for (int i = 0; i < tg.n_data; ++i) {
+      const T* row = tg.X + (size_t)i * d;
+      T eta = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e < d) eta = fma(row[e], y[e], eta);
+      acc += tg.vec[i] * eta - softplus<T>(eta);
+    }
+    return acc;
+  }
+  return neg_inf<T>();
+}
+
+template <typename T, int E>
+__device__ __forceinline__ T sqdist(const T (&a)[E], const T (&b)[E], int d) {
+  T acc = T(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (e < d) { const T r = b[e] - a[e]; acc = fma(r, r, acc); }
+  return acc;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void dr_emit(const DrView<T>& v, int64_t c, int t, const T (&x)[E]) {
+  const int d = v.tg.d;
+  if (v.out) {
+    T* dst = v.out + ((size_t)c * v.n + t) * d;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e < d) dst[e] = x[e];
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (e >= d) continue;
+      const size_t o = (size_t)c * d + e;
+      T* mo = v.mom;
+      const size_t st = v.mom_stride;
+      T y = x[e] - mo[o + st]; T tt = mo[o] + y; mo[o + st] = (tt - mo[o]) - y; mo[o] = tt;
+      const T x2 = x[e] * x[e];
+      y = x2 - mo[o + 3 * st]; tt = mo[o + 2 * st] + y; mo[o + 3 * st] = (tt - mo[o + 2 * st]) - y;
+      mo[o + 2 * st] = tt;
+    }
+  }
+}
+
+// One PROPOSE step of stage k for one chain.  Returns true when the sample is finished
+// (accepted, or rejected at the last stage); then x/lp hold the sample.
+template <typename T, int E>
+__device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E],
+                                        T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, int& err) {
+  const int d = v.tg.d;
+  const int D = (d + 1) / 2;
+  const uint32_t base = (uint32_t)(k * (D + 1));
+  T y[E];
+  const T sg = v.sig[k];
+#pragma unroll
+  for (int q = 0; q < (E + 1) / 2; ++q) {
+    if (q < D) {
+      T z0, z1;
+      Conv<T>::normal_pair(key.block((uint32_t)t, 0, base + q), z0, z1);
+      y[2 * q] = fma(sg, z0, x[2 * q]);
+      if (2 * q + 1 < E) y[2 * q + 1] = fma(sg, z1, x[2 * q + 1]);
+    } else {
+      y[2 * q] = T(0);
+      if (2 * q + 1 < E) y[2 * q + 1] = T(0);
+    }
+  }
+  T lpy = full_logp<T, E>(v.tg, y);
+  if (!(lpy == lpy)) { lpy = neg_inf<T>(); err |= ERR_NONFINITE; }
+  T la;
+  if (k == 0) {
+    la = la1(lp, lpy);
+  } else {
+    const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]);
+    if (k == 1) {
+      la = la2(lp, lp1, lpy, i1 * sqdist(x, y1, d), i1 * sqdist(y, y1, d));
+    } else {
+      const T i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
+      la = la3(lp, lp1, lp2, lpy, i1 * sqdist(x, y1, d), i2 * sqdist(x, y2, d),
+               i1 * sqdist(y, y2, d), i2 * sqdist(y, y1, d), i1 * sqdist(y1, y2, d));
+    }
+  }
+  const P4 r = key.block((uint32_t)t, 0, base + (uint32_t)D);
+  if (Conv<T>::log_u(r.w0, r.w1) < la) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = y[e];
+    lp = lpy;
+    return true;
+  }
+  if (k + 1 >= v.n_stages) return true;
+  if (k == 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) y1[e] = y[e];
+    lp1 = lpy;
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) y2[e] = y[e];
+    lp2 = lpy;
+  }
+  return false;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void dr_load(const DrView<T>& v, int64_t c, T (&x)[E], T (&y1)[E],
+                                        T (&y2)[E]) {
+  const int d = v.tg.d;
+  const size_t md = (size_t)v.m * d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    x[e] = e < d ? v.x[(size_t)c * d + e] : T(0);
+    y1[e] = e < d ? v.y[(size_t)c * d + e] : T(0);
+    y2[e] = e < d ? v.y[md + (size_t)c * d + e] : T(0);
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void dr_store(const DrView<T>& v, int64_t c, const T (&x)[E],
+                                         const T (&y1)[E], const T (&y2)[E], int k) {
+  const int d = v.tg.d;
+  const size_t md = (size_t)v.m * d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (e >= d) continue;
+    v.x[(size_t)c * d + e] = x[e];
+    if (k >= 1) v.y[(size_t)c * d + e] = y1[e];
+    if (k >= 2) v.y[md + (size_t)c * d + e] = y2[e];
+  }
+}
+
+// FSM kernel: chain-per-thread, every chain advances `budget` PROPOSE steps.
+template <typename T, int E>
+__global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < v.m; c += stride) {
+    T x[E], y1[E], y2[E];
+    dr_load<T, E>(v, c, x, y1, y2);
+    T lp = v.lp[c], lp1 = v.lpy[c], lp2 = v.lpy[v.m + c];
+    int t = v.t[c], k = v.k[c];
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    int err = 0, steps = 0;
+    for (int b = 0; b < budget && t < v.n; ++b) {
+      ++steps;
+      if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, err)) {
+        dr_emit<T, E>(v, c, t, x);
+        v.counts[(size_t)c * v.n + t] = k + 1;
+        ++t;
+        k = 0;
+        if (t == v.n) atomicAdd(v.chains_done, 1);
+      } else {
+        ++k;
+      }
+    }
+    dr_store<T, E>(v, c, x, y1, y2, k);
+    v.lp[c] = lp; v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
+    v.t[c] = t; v.k[c] = k;
+    v.steps[c] += steps;
+    if (err) atomicOr(v.err, err);
+  }
+}
+
+// Synchronised kernel (Alg. 6): for every sample, stage 1 for all chains, then stage 2 for
+// the chains that rejected, ..., with a grid barrier between stages.
+template <typename T, int E>
+__global__ void __launch_bounds__(256) dr_sync_kernel(DrView<T> v, int t_begin, int t_end,
+                                                      GridBarrier bar, unsigned* active_cnt,
+                                                      unsigned long long* iterations) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t c_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  __shared__ unsigned blk_active;
+  int iter = 0, err = 0;
+  for (int t = t_begin; t < t_end; ++t) {
+    for (int k = 0; k < v.n_stages; ++k) {
+      if (threadIdx.x == 0) blk_active = 0;
+      __syncthreads();
+      unsigned mine = 0;
+      for (int64_t c = c_first; c < v.m; c += stride) {
+        if (v.k[c] != k) continue;  // masked: finished this sample at an earlier stage
+        T x[E], y1[E], y2[E];
+        dr_load<T, E>(v, c, x, y1, y2);
+        T lp = v.lp[c], lp1 = v.lpy[c], lp2 = v.lpy[v.m + c];
+        const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+        v.steps[c] += 1;
+        if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, err)) {
+          dr_emit<T, E>(v, c, t, x);
+          v.counts[(size_t)c * v.n + t] = k + 1;
+          dr_store<T, E>(v, c, x, y1, y2, 0);
+          v.lp[c] = lp;
+          v.k[c] = v.n_stages;  // done with sample t
+          v.t[c] = t + 1;
+          if (t + 1 == v.n) atomicAdd(v.chains_done, 1);
+        } else {
+          dr_store<T, E>(v, c, x, y1, y2, k + 1);
+          v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
+          v.k[c] = k + 1;
+          mine = 1;
+        }
+      }
+      if (mine) atomicAdd(&blk_active, 1u);
+      __syncthreads();
+      const int slot = iter % 3;
+      if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+      if (!grid_sync(bar, v.err)) return;
+      const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+      if (leader) {
+        active_cnt[(iter + 2) % 3] = 0;
+        *iterations += 1;
+      }
+      ++iter;
+      if (total == 0) break;
+    }
+    // every chain starts the next sample at stage 0 (each thread resets its own chains)
+    for (int64_t c = c_first; c < v.m; c += stride) v.k[c] = 0;
+  }
+  if (err) atomicOr(v.err, err);
+}
+
+template <typename T, int E>
+__global__ void dr_init_kernel(DrView<T> v) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.m) return;
+  T x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) x[e] = e < v.tg.d ? v.x[(size_t)c * v.tg.d + e] : T(0);
+  T lp = full_logp<T, E>(v.tg, x);
+  if (!(lp == lp)) { lp = neg_inf<T>(); atomicOr(v.err, ERR_NONFINITE); }
+  v.lp[c] = lp;
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename T, int E>
+static cudaError_t fsm_launch(const DrView<T>& v, int budget, int threads, cudaStream_t st) {
+  const int64_t blocks = (v.m + threads - 1) / threads;
+  dr_fsm_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
+static cudaError_t sync_launch(const DrView<T>& v, int t0, int t1, GridBarrier bar,
+                               unsigned* active_cnt, unsigned long long* iters, int threads,
+                               cudaStream_t st) {
+  auto kern = dr_sync_kernel<T, E>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (v.m + threads - 1) / threads);
+  if (blocks < 1) blocks = 1;
+  DrView<T> vv = v;
+  void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+}
+
+template <typename T, int E>
+static cudaError_t init_launch(const DrView<T>& v, cudaStream_t st) {
+  dr_init_kernel<T, E><<<(unsigned)((v.m + 127) / 128), 128, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+#define FSMC_DR_DISPATCH(FN, ...)                            \
+  do {                                                       \
+    const int d = v.tg.d;                                    \
+    if (d <= 2) return FN<T, 2>(__VA_ARGS__);                \
+    if (d <= 4) return FN<T, 4>(__VA_ARGS__);                \
+    if (d <= 8) return FN<T, 8>(__VA_ARGS__);                \
+    if (d <= 10) return FN<T, 10>(__VA_ARGS__);              \
+    if (d <= 16) return FN<T, 16>(__VA_ARGS__);              \
+    if (d <= 32) return FN<T, 32>(__VA_ARGS__);              \
+    return cudaErrorInvalidValue;                            \
+  } while (0)
+
+template <typename T>
+cudaError_t launch_dr_fsm(const DrView<T>& v, int budget, int threads, cudaStream_t st) {
+  FSMC_DR_DISPATCH(fsm_launch, v, budget, threads, st);
+}
+template <typename T>
+cudaError_t launch_dr_sync(const DrView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                           unsigned long long* iters, int threads, cudaStream_t st) {
+  FSMC_DR_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
+}
+template <typename T>
+cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st) {
+  FSMC_DR_DISPATCH(init_launch, v, st);
+}
+
+template cudaError_t launch_dr_fsm<float>(const DrView<float>&, int, int, cudaStream_t);
+template cudaError_t launch_dr_fsm<double>(const DrView<double>&, int, int, cudaStream_t);
+template cudaError_t launch_dr_sync<float>(const DrView<float>&, int, int, GridBarrier, unsigned*,
+                                           unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_dr_sync<double>(const DrView<double>&, int, int, GridBarrier, unsigned*,
+                                            unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_dr_init<float>(const DrView<float>&, cudaStream_t);
+template cudaError_t launch_dr_init<double>(const DrView<double>&, cudaStream_t);
+
+}  // namespace fsmc

@@ -1,0 +1,905 @@
+// Host engine behind include/fsmc.h: targets, jobs, device memory, the FSM and synchronised
+// run loops (Alg. 7 and Alg. 6 on the device), reads, checkpointing and the serving queue.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fsmc_device.cuh"
+#include "fsmc_kernels.h"
+#include "engine_internal.h"
+
+using namespace fsmc;
+
+// ---- errors ---------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+fsmc_status fsmc_fail(fsmc_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+fsmc_status fsmc_cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear sticky-free errors so later calls can proceed
+  return fsmc_fail(FSMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                                   \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return fsmc_cuda_fail(_e, #expr);       \
+  } while (0)
+
+extern "C" const char* fsmc_last_error(void) { return g_last_error.c_str(); }
+
+// ---- engine ---------------------------------------------------------------------------------------
+extern "C" fsmc_status fsmc_engine_create(int device, size_t hbm_budget_bytes, fsmc_engine** out) {
+  if (!out) return fsmc_fail(FSMC_EINVAL, "out is NULL");
+  int count = 0;
+  CK(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fsmc_fail(FSMC_EINVAL, "no such device");
+  CK(cudaSetDevice(device));
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  auto* e = new (std::nothrow) fsmc_engine();
+  if (!e) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");
+  e->device = device;
+  e->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+  CK(cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, device));
+  *out = e;
+  return FSMC_OK;
+}
+
+extern "C" void fsmc_engine_destroy(fsmc_engine* e) {
+  if (!e) return;
+  serving_shutdown(e);
+  std::vector<fsmc_job*> jobs;
+  std::vector<fsmc_target*> tgts;
+  {
+    std::lock_guard<std::mutex> g(e->mu);
+    jobs = e->jobs;
+    tgts = e->targets;
+  }
+  for (auto* j : jobs) fsmc_job_destroy(j);
+  for (auto* t : tgts) fsmc_target_destroy(t);
+  delete e;
+}
+
+extern "C" size_t fsmc_engine_bytes_in_use(const fsmc_engine* e) {
+  if (!e) return 0;
+  std::lock_guard<std::mutex> g(e->mu);
+  return e->in_use;
+}
+
+bool engine_reserve(fsmc_engine* e, size_t bytes) {
+  std::lock_guard<std::mutex> g(e->mu);
+  if (e->in_use + bytes > e->budget) return false;
+  e->in_use += bytes;
+  return true;
+}
+
+void engine_release(fsmc_engine* e, size_t bytes) {
+  std::lock_guard<std::mutex> g(e->mu);
+  e->in_use -= std::min(bytes, e->in_use);
+}
+
+// ---- per-launch profiling -------------------------------------------------------------------------
+static cudaEvent_t take_event(fsmc_job* j) {
+  if (j->event_next == j->event_pool.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    j->event_pool.push_back(ev);
+  }
+  return j->event_pool[j->event_next++];
+}
+
+ProfScope::ProfScope(fsmc_job* job, int c, cudaStream_t s) : j(job), cls(c), st(s) {
+  if (!j->tun.profile_kernels) return;
+  a = take_event(j);
+  b = take_event(j);
+  if (a && b) cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope() {
+  if (!a || !b) return;
+  cudaEventRecord(b, st);
+  j->prof_events.push_back({cls, {a, b}});
+  j->kernel_launches[cls] += 1;
+}
+
+static void prof_collect(fsmc_job* j) {
+  for (auto& pe : j->prof_events) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess)
+      j->kernel_ms[pe.first] += ms;
+  }
+  cudaGetLastError();
+  j->prof_events.clear();
+  j->event_next = 0;
+}
+
+static void prof_reset(fsmc_job* j) {
+  for (int k = 0; k < 4; ++k) { j->kernel_ms[k] = 0; j->kernel_launches[k] = 0; }
+  j->prof_events.clear();
+  j->event_next = 0;
+}
+
+// ---- targets --------------------------------------------------------------------------------------
+static bool target_layout(int kind, int d, int n_data, size_t* n_params, bool* needs_L) {
+  *needs_L = false;
+  switch (kind) {
+    case FSMC_TGT_GAUSS_CONJ: *n_params = (size_t)d * d + d + 1; *needs_L = true; return n_data == 0;
+    case FSMC_TGT_GP_LOGIT: *n_params = (size_t)d * d + d; *needs_L = true; return n_data == 0;
+    case FSMC_TGT_FLAT: *n_params = (size_t)d * d; *needs_L = true; return n_data == 0;
+    case FSMC_TGT_FUNNEL: *n_params = 0; return n_data == 0 && d >= 2;
+    case FSMC_TGT_LOGREG: *n_params = (size_t)n_data * d + n_data; return n_data >= 1;
+    case FSMC_TGT_GAUSS_DIAG: *n_params = 2 * (size_t)d; return n_data == 0;
+  }
+  return false;
+}
+
+template <typename T>
+static fsmc_status upload_target(fsmc_target* t, std::vector<void*>& bufs, TargetView<T>& tv) {
+  const int d = t->d;
+  const double* p = t->params.data();
+  auto up = [&](const double* src, size_t n, const T** dst) -> fsmc_status {
+    if (n == 0) { *dst = nullptr; return FSMC_OK; }
+    std::vector<T> h(src, src + n);
+    void* ptr = nullptr;
+    CK(cudaMalloc(&ptr, n * sizeof(T)));
+    bufs.push_back(ptr);
+    t->bytes += n * sizeof(T);
+    CK(cudaMemcpy(ptr, h.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = (const T*)ptr;
+    return FSMC_OK;
+  };
+  tv = TargetView<T>{};
+  tv.kind = t->kind;
+  tv.d = d;
+  tv.n_data = t->n_data;
+  fsmc_status st = FSMC_OK;
+  switch (t->kind) {
+    case FSMC_TGT_GAUSS_CONJ:
+      if ((st = up(p, (size_t)d * d, &tv.L))) return st;
+      if ((st = up(p + (size_t)d * d, d, &tv.vec))) return st;
+      tv.s2 = (T)p[(size_t)d * d + d];
+      break;
+    case FSMC_TGT_GP_LOGIT:
+      if ((st = up(p, (size_t)d * d, &tv.L))) return st;
+      if ((st = up(p + (size_t)d * d, d, &tv.vec))) return st;
+      break;
+    case FSMC_TGT_FLAT:
+      if ((st = up(p, (size_t)d * d, &tv.L))) return st;
+      break;
+    case FSMC_TGT_LOGREG:
+      if ((st = up(p, (size_t)t->n_data * d, &tv.X))) return st;
+      if ((st = up(p + (size_t)t->n_data * d, t->n_data, &tv.vec))) return st;
+      break;
+    case FSMC_TGT_GAUSS_DIAG:
+      if ((st = up(p, d, &tv.vec))) return st;
+      if ((st = up(p + d, d, &tv.vec2))) return st;
+      break;
+    default:
+      break;
+  }
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_target_create(fsmc_engine* e, fsmc_target_kind kind, int d, int n_data,
+                                          const double* params_host, size_t n_params,
+                                          fsmc_target** out) {
+  if (!e || !out) return fsmc_fail(FSMC_EINVAL, "engine/out is NULL");
+  size_t need = 0;
+  bool needs_L = false;
+  if (d < 1 || d > 1024 || n_data < 0 || !target_layout(kind, d, n_data, &need, &needs_L))
+    return fsmc_fail(FSMC_EINVAL, "invalid target kind / d / n_data");
+  if (n_params != need) return fsmc_fail(FSMC_EINVAL, "n_params does not match the target layout");
+  if (need && !params_host) return fsmc_fail(FSMC_EINVAL, "params_host is NULL");
+  CK(cudaSetDevice(e->device));
+  auto* t = new (std::nothrow) fsmc_target();
+  if (!t) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");
+  t->e = e;
+  t->kind = kind;
+  t->d = d;
+  t->n_data = n_data;
+  t->params.assign(params_host, params_host + need);
+  fsmc_status st = upload_target<float>(t, t->bufs, t->tv32);
+  if (st == FSMC_OK) st = upload_target<double>(t, t->bufs, t->tv64);
+  if (st != FSMC_OK) {
+    for (void* b : t->bufs) cudaFree(b);
+    delete t;
+    return st;
+  }
+  {
+    std::lock_guard<std::mutex> g(e->mu);
+    e->in_use += t->bytes;
+    e->targets.push_back(t);
+  }
+  *out = t;
+  return FSMC_OK;
+}
+
+extern "C" void fsmc_target_destroy(fsmc_target* t) {
+  if (!t) return;
+  fsmc_engine* e = t->e;
+  cudaSetDevice(e->device);
+  for (void* b : t->bufs) cudaFree(b);
+  {
+    std::lock_guard<std::mutex> g(e->mu);
+    e->in_use -= std::min(t->bytes, e->in_use);
+    e->targets.erase(std::remove(e->targets.begin(), e->targets.end(), t), e->targets.end());
+  }
+  delete t;
+}
+
+// ---- jobs -----------------------------------------------------------------------------------------
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  }
+};
+
+// Decides the launch shape when the caller left it open.
+static void default_tuning(fsmc_job* j) {
+  fsmc_tuning& tu = j->tun;
+  if (j->algo == FSMC_ESS) {
+    if (!tu.lanes_per_chain) {
+      // chain-per-warp when one chain's likelihood is wide (d >= 64) or when there are too
+      // few chains to fill the machine one per thread
+      const int64_t thread_slots = (int64_t)j->e->sms * 1024;
+      tu.lanes_per_chain = (j->d > 32 || j->d >= 64 || j->m * 8 < thread_slots) ? 32 : 1;
+    }
+    if (!tu.steps_per_launch) tu.steps_per_launch = 64;
+    if (!tu.ring_slots) tu.ring_slots = 32;
+    if (!tu.threads_per_block) tu.threads_per_block = 256;
+  } else if (j->algo == FSMC_DR) {
+    tu.lanes_per_chain = 1;
+    if (!tu.steps_per_launch) tu.steps_per_launch = 256;
+    if (!tu.threads_per_block) tu.threads_per_block = 128;
+  } else {
+    if (!tu.lanes_per_chain) tu.lanes_per_chain = 32;
+    if (!tu.steps_per_launch) tu.steps_per_launch = 32;
+    if (!tu.threads_per_block) tu.threads_per_block = 128;
+  }
+}
+
+static fsmc_status job_layout_and_alloc(fsmc_job* j) {
+  const size_t es = j->prec == FSMC_FP64 ? 8 : 4;
+  const size_t m = (size_t)j->m, n = (size_t)j->n, d = (size_t)j->d;
+  Layout L;
+  j->o_x = L.take(m * d * es);
+  j->o_t = L.take(m * 4);
+  j->o_counts = L.take(m * n * 4);
+  j->o_steps = L.take(m * 8);
+  j->o_err = L.take(4);
+  j->o_done = L.take(4);
+  j->o_out = j->store ? L.take(m * n * d * es) : 0;
+  j->o_mom = j->store ? 0 : L.take(4 * m * d * es);
+  j->o_bar = L.take(64);
+  j->o_iters = L.take(8);
+  if (j->algo == FSMC_ESS) {
+    j->W = j->tun.ring_slots;
+    j->dstride = (int)align_up(d, 32);
+    j->o_ell = L.take(m * es);
+    j->o_logy = L.take(m * es);
+    j->o_th = L.take(3 * m * es);
+    j->o_k = L.take(m * 4);
+    j->o_s = L.take(m * 4);
+    j->o_gen = L.take(2 * m * 4);
+    j->o_nu = L.take(m * (size_t)j->W * j->dstride * es);
+    j->o_gencols = L.take(8);
+  } else if (j->algo == FSMC_DR) {
+    j->o_ell = L.take(m * es);        // log pi(x)
+    j->o_y = L.take(2 * m * d * es);  // y1, y2
+    j->o_lpy = L.take(2 * m * es);
+    j->o_k = L.take(m * 4);
+  } else {
+    nuts_layout(j, L.off);
+  }
+  j->bytes = L.off;
+  if (!engine_reserve(j->e, j->bytes)) {
+    char msg[256];
+    snprintf(msg, sizeof msg, "job needs %zu device bytes; engine budget %zu, in use %zu",
+             j->bytes, j->e->budget, fsmc_engine_bytes_in_use(j->e));
+    return fsmc_fail(FSMC_EADMIT, msg);
+  }
+  cudaError_t ce = cudaMalloc((void**)&j->dev, j->bytes);
+  if (ce != cudaSuccess) {
+    engine_release(j->e, j->bytes);
+    j->dev = nullptr;
+    cudaGetLastError();
+    return fsmc_fail(FSMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+  }
+  return FSMC_OK;
+}
+
+template <typename T>
+static void fill_chains(const fsmc_job* j, ChainsView<T>& v) {
+  char* b = j->dev;
+  v.m = j->m;
+  v.n = (int)j->n;
+  v.chain0 = j->chain0;
+  v.seed_lo = (uint32_t)j->seed;
+  v.seed_hi = (uint32_t)(j->seed >> 32);
+  v.x = (T*)(b + j->o_x);
+  v.t = (int*)(b + j->o_t);
+  v.out = j->store ? (T*)(b + j->o_out) : nullptr;
+  v.mom = j->store ? nullptr : (T*)(b + j->o_mom);
+  v.mom_stride = (size_t)j->m * j->d;
+  v.counts = (int*)(b + j->o_counts);
+  v.steps = (long long*)(b + j->o_steps);
+  v.err = (int*)(b + j->o_err);
+  v.chains_done = (int*)(b + j->o_done);
+}
+
+template <typename T>
+const TargetView<T>& target_view(const fsmc_target* t);
+template <>
+const TargetView<float>& target_view<float>(const fsmc_target* t) { return t->tv32; }
+template <>
+const TargetView<double>& target_view<double>(const fsmc_target* t) { return t->tv64; }
+
+template <typename T>
+EssView<T> ess_view(const fsmc_job* j) {
+  EssView<T> v;
+  fill_chains<T>(j, v);
+  char* b = j->dev;
+  v.tg = target_view<T>(j->tg);
+  v.W = j->W;
+  v.dstride = j->dstride;
+  v.ell = (T*)(b + j->o_ell);
+  v.logy = (T*)(b + j->o_logy);
+  v.th = (T*)(b + j->o_th);
+  v.thmin = v.th + j->m;
+  v.thmax = v.th + 2 * j->m;
+  v.k = (int*)(b + j->o_k);
+  v.s = (int*)(b + j->o_s);
+  v.gen_lo = (int*)(b + j->o_gen);
+  v.gen_hi = v.gen_lo + j->m;
+  v.nu = (T*)(b + j->o_nu);
+  v.gen_cols = (unsigned long long*)(b + j->o_gencols);
+  return v;
+}
+
+template <typename T>
+DrView<T> dr_view(const fsmc_job* j) {
+  DrView<T> v;
+  fill_chains<T>(j, v);
+  char* b = j->dev;
+  v.tg = target_view<T>(j->tg);
+  v.n_stages = j->dr.n_stages;
+  for (int k = 0; k < 3; ++k) v.sig[k] = (T)(j->dr.scale0 * std::pow(j->dr.factor, (double)k));
+  v.lp = (T*)(b + j->o_ell);
+  v.y = (T*)(b + j->o_y);
+  v.lpy = (T*)(b + j->o_lpy);
+  v.k = (int*)(b + j->o_k);
+  return v;
+}
+
+template <typename T>
+static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
+  char* b = j->dev;
+  const size_t m = (size_t)j->m, d = (size_t)j->d;
+  std::vector<T> hx(m * d);
+  for (size_t i = 0; i < m * d; ++i) hx[i] = (T)j->x0[i];
+  CK(cudaMemcpyAsync(b + j->o_x, hx.data(), m * d * sizeof(T), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(b + j->o_t, 0, m * 4, st));
+  CK(cudaMemsetAsync(b + j->o_counts, 0xff, m * (size_t)j->n * 4, st));
+  CK(cudaMemsetAsync(b + j->o_steps, 0, m * 8, st));
+  CK(cudaMemsetAsync(b + j->o_err, 0, 4, st));
+  CK(cudaMemsetAsync(b + j->o_done, 0, 4, st));
+  CK(cudaMemsetAsync(b + j->o_bar, 0, 64, st));
+  CK(cudaMemsetAsync(b + j->o_iters, 0, 8, st));
+  if (!j->store) CK(cudaMemsetAsync(b + j->o_mom, 0, 4 * m * d * sizeof(T), st));
+  if (j->algo == FSMC_ESS) {
+    CK(cudaMemsetAsync(b + j->o_k, 0, m * 4, st));
+    CK(cudaMemsetAsync(b + j->o_s, 0, m * 4, st));
+    CK(cudaMemsetAsync(b + j->o_th, 0, 3 * m * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_logy, 0, m * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_gencols, 0, 8, st));
+    int* gen = (int*)(b + j->o_gen);
+    CK(launch_fill_int(gen, j->m, 0, st));
+    CK(launch_fill_int(gen + j->m, j->m, (int)std::min<int64_t>(j->W, j->n), st));
+    CK(launch_ess_init<T>(ess_view<T>(j), st));
+  } else if (j->algo == FSMC_DR) {
+    CK(cudaMemsetAsync(b + j->o_k, 0, m * 4, st));
+    CK(cudaMemsetAsync(b + j->o_y, 0, 2 * m * d * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_lpy, 0, 2 * m * sizeof(T), st));
+    CK(launch_dr_init<T>(dr_view<T>(j), st));
+  } else {
+    fsmc_status s = nuts_init_state(j, st);
+    if (s != FSMC_OK) return s;
+  }
+  CK(cudaStreamSynchronize(st));
+  j->sync_used = false;
+  j->fsm_used = false;
+  return FSMC_OK;
+}
+
+static fsmc_status job_init(fsmc_job* j, cudaStream_t st) {
+  return j->prec == FSMC_FP64 ? job_init_state<double>(j, st) : job_init_state<float>(j, st);
+}
+
+extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo algo,
+                                       const void* algo_params, fsmc_precision prec,
+                                       int64_t n_chains, int64_t n_samples, const double* x0_host,
+                                       uint64_t seed, int store_samples, fsmc_job** out) {
+  if (!e || !t || !out) return fsmc_fail(FSMC_EINVAL, "engine/target/out is NULL");
+  if (n_chains < 1 || n_chains > (int64_t)1 << 31 || n_samples < 1 || n_samples > (int64_t)1 << 30)
+    return fsmc_fail(FSMC_EINVAL, "n_chains / n_samples out of range");
+  if (prec != FSMC_FP32 && prec != FSMC_FP64) return fsmc_fail(FSMC_EINVAL, "bad precision");
+  const bool ess_kind = t->kind == FSMC_TGT_GAUSS_CONJ || t->kind == FSMC_TGT_GP_LOGIT ||
+                        t->kind == FSMC_TGT_FLAT;
+  if (algo == FSMC_ESS && !ess_kind) return fsmc_fail(FSMC_EINVAL, "ESS needs a target with a Gaussian prior factor");
+  if ((algo == FSMC_DR || algo == FSMC_NUTS) && ess_kind)
+    return fsmc_fail(FSMC_EINVAL, "DR / NUTS need a full log-density target");
+  if (algo != FSMC_ESS && algo != FSMC_DR && algo != FSMC_NUTS) return fsmc_fail(FSMC_EINVAL, "bad algo");
+  if (algo == FSMC_DR && t->d > 32) return fsmc_fail(FSMC_EINVAL, "DR supports d <= 32");
+  auto* j = new (std::nothrow) fsmc_job();
+  if (!j) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");
+  j->e = e;
+  j->tg = t;
+  j->algo = algo;
+  j->prec = prec;
+  j->m = n_chains;
+  j->n = n_samples;
+  j->d = t->d;
+  j->seed = seed;
+  j->store = store_samples ? 1 : 0;
+  if (algo == FSMC_DR) {
+    j->dr = algo_params ? *(const fsmc_dr_params*)algo_params : fsmc_dr_params{3, 1.0, 0.5};
+    if (j->dr.n_stages < 1 || j->dr.n_stages > 3 || !(j->dr.scale0 > 0) || !(j->dr.factor > 0)) {
+      delete j;
+      return fsmc_fail(FSMC_EINVAL, "DR params: 1..3 stages, positive scales");
+    }
+  }
+  if (algo == FSMC_NUTS) {
+    j->nuts = algo_params ? *(const fsmc_nuts_params*)algo_params : fsmc_nuts_params{0.05, 10, 1000.0};
+    if (!(j->nuts.eps > 0) || j->nuts.max_depth < 1 || j->nuts.max_depth > 10 || !(j->nuts.max_dH > 0)) {
+      delete j;
+      return fsmc_fail(FSMC_EINVAL, "NUTS params: eps > 0, 1 <= max_depth <= 10, max_dH > 0");
+    }
+  }
+  j->x0.assign((size_t)n_chains * t->d, 0.0);
+  if (x0_host) std::copy(x0_host, x0_host + (size_t)n_chains * t->d, j->x0.begin());
+  default_tuning(j);
+  {
+    std::lock_guard<std::mutex> g(e->mu);
+    e->jobs.push_back(j);
+  }
+  *out = j;
+  return FSMC_OK;
+}
+
+// Allocation and state initialisation happen on first use so that a queued serving job
+// holds no device memory until it is admitted.
+fsmc_status job_materialize(fsmc_job* j, cudaStream_t st) {
+  if (j->dev) return FSMC_OK;
+  CK(cudaSetDevice(j->e->device));
+  fsmc_status s = job_layout_and_alloc(j);
+  if (s != FSMC_OK) return s;
+  return job_init(j, st);
+}
+
+extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
+  if (!j || !tu) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  if (j->dev) return fsmc_fail(FSMC_ESTATE, "tuning must be set before the first run");
+  fsmc_tuning t = *tu;
+  if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 32)
+    return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1 or 32");
+  if (j->algo == FSMC_DR && t.lanes_per_chain == 32) return fsmc_fail(FSMC_EINVAL, "DR is chain-per-thread");
+  if (j->algo == FSMC_ESS && t.lanes_per_chain == 1 && j->d > 32)
+    return fsmc_fail(FSMC_EINVAL, "chain-per-thread ESS supports d <= 32");
+  if (t.threads_per_block && (t.threads_per_block % 32 || t.threads_per_block < 32 || t.threads_per_block > 256))
+    return fsmc_fail(FSMC_EINVAL, "threads_per_block must be a multiple of 32 in [32, 256]");
+  if (t.steps_per_launch < 0 || t.ring_slots < 0 || t.ring_slots > 4096)
+    return fsmc_fail(FSMC_EINVAL, "negative steps / ring slots");
+  j->tun = t;
+  default_tuning(j);
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_job_get_tuning(const fsmc_job* j, fsmc_tuning* tu) {
+  if (!j || !tu) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  *tu = j->tun;
+  return FSMC_OK;
+}
+
+extern "C" size_t fsmc_job_bytes(const fsmc_job* j) { return j ? j->bytes : 0; }
+
+// ---- run loops -------------------------------------------------------------------------------------
+// One FSM round: (ESS) refill the rings, then advance every chain by the step budget.
+template <typename T>
+static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
+  const fsmc_tuning& tu = j->tun;
+  cudaError_t e;
+  if (j->algo == FSMC_ESS) {
+    const EssView<T> v = ess_view<T>(j);
+    {
+      ProfScope p(j, 0, st);
+      if ((e = launch_ess_nu_gen<T>(v, st)) != cudaSuccess) return e;
+    }
+    ProfScope p(j, 1, st);
+    e = launch_ess_fsm<T>(v, tu.lanes_per_chain, tu.steps_per_launch, tu.threads_per_block, st);
+    j->launches += 2;
+  } else if (j->algo == FSMC_DR) {
+    ProfScope p(j, 1, st);
+    e = launch_dr_fsm<T>(dr_view<T>(j), tu.steps_per_launch, tu.threads_per_block, st);
+    j->launches += 1;
+  } else {
+    ProfScope p(j, 1, st);
+    e = nuts_fsm_round(j, st);
+    j->launches += 1;
+  }
+  return e;
+}
+
+static fsmc_status read_done(fsmc_job* j, cudaStream_t st, int* done_chains, int* err) {
+  int h[2] = {0, 0};
+  CK(cudaMemcpyAsync(&h[0], j->dev + j->o_done, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h[1], j->dev + j->o_err, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *done_chains = h[0];
+  *err = h[1];
+  return FSMC_OK;
+}
+
+template <typename T>
+static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
+  const int check_every = 8;
+  int64_t rounds_limit = -1;
+  if (max_steps > 0) rounds_limit = (max_steps + j->tun.steps_per_launch - 1) / j->tun.steps_per_launch;
+  int64_t r = 0;
+  while (true) {
+    int done = 0, err = 0;
+    fsmc_status s = read_done(j, st, &done, &err);
+    if (s != FSMC_OK) return s;
+    if (err & ERR_BARRIER_TIMEOUT) return fsmc_fail(FSMC_ETIMEOUT, "device barrier timed out");
+    if (done >= j->m) break;
+    if (rounds_limit >= 0 && r >= rounds_limit) break;
+    int burst = check_every;
+    if (rounds_limit >= 0) burst = (int)std::min<int64_t>(burst, rounds_limit - r);
+    for (int b = 0; b < burst; ++b) {
+      cudaError_t e = fsm_round<T>(j, st);
+      if (e != cudaSuccess) return fsmc_cuda_fail(e, "FSM launch");
+    }
+    r += burst;
+  }
+  return FSMC_OK;
+}
+
+template <typename T>
+static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
+  char* b = j->dev;
+  GridBarrier bar{(unsigned*)(b + j->o_bar), (unsigned*)(b + j->o_bar) + 1};
+  unsigned* active = (unsigned*)(b + j->o_bar) + 4;
+  unsigned long long* iters = (unsigned long long*)(b + j->o_iters);
+  const int threads = j->tun.threads_per_block;
+  if (j->algo == FSMC_ESS) {
+    EssView<T> v = ess_view<T>(j);
+    for (int64_t t0 = 0; t0 < j->n; t0 += j->W) {
+      const int t1 = (int)std::min<int64_t>(t0 + j->W, j->n);
+      {
+        ProfScope p(j, 3, st);
+        CK(launch_fill_int(v.gen_lo, j->m, (int)t0, st));
+        CK(launch_fill_int(v.gen_hi, j->m, t1, st));
+      }
+      {
+        ProfScope p(j, 0, st);
+        CK(launch_ess_nu_gen<T>(v, st));
+      }
+      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+      ProfScope p(j, 2, st);
+      CK(launch_ess_sync<T>(v, j->tun.lanes_per_chain, (int)t0, t1, bar, active, iters, threads, st));
+      j->launches += 4;
+    }
+  } else if (j->algo == FSMC_DR) {
+    DrView<T> v = dr_view<T>(j);
+    const int chunk = 1000;
+    for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
+      const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
+      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+      ProfScope p(j, 2, st);
+      CK(launch_dr_sync<T>(v, (int)t0, t1, bar, active, iters, threads, st));
+      j->launches += 1;
+    }
+  } else {
+    fsmc_status s = nuts_run_sync(j, st);
+    if (s != FSMC_OK) return s;
+  }
+  int done = 0, err = 0;
+  fsmc_status s = read_done(j, st, &done, &err);
+  if (s != FSMC_OK) return s;
+  if (err & ERR_BARRIER_TIMEOUT) return fsmc_fail(FSMC_ETIMEOUT, "device barrier timed out");
+  return FSMC_OK;
+}
+
+fsmc_status job_run_impl(fsmc_job* j, fsmc_mode mode, int64_t max_fsm_steps, cudaStream_t st) {
+  fsmc_status s = job_materialize(j, st);
+  if (s != FSMC_OK) return s;
+  CK(cudaSetDevice(j->e->device));
+  if (mode == FSMC_MODE_SYNC && (j->fsm_used || j->sync_used))
+    return fsmc_fail(FSMC_ESTATE, "SYNC mode needs a fresh or reset job");
+  if (mode == FSMC_MODE_FSM && j->sync_used)
+    return fsmc_fail(FSMC_ESTATE, "job was run in SYNC mode; reset it first");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  j->launches = 0;
+  prof_reset(j);
+  unsigned long long cols0 = 0;
+  if (j->algo == FSMC_ESS) CK(cudaMemcpy(&cols0, j->dev + j->o_gencols, 8, cudaMemcpyDeviceToHost));
+  CK(cudaEventRecord(e0, st));
+  if (mode == FSMC_MODE_FSM) {
+    j->fsm_used = true;
+    s = j->prec == FSMC_FP64 ? run_fsm<double>(j, max_fsm_steps, st) : run_fsm<float>(j, max_fsm_steps, st);
+  } else if (mode == FSMC_MODE_SYNC) {
+    j->sync_used = true;
+    s = j->prec == FSMC_FP64 ? run_sync<double>(j, st) : run_sync<float>(j, st);
+  } else {
+    s = fsmc_fail(FSMC_EINVAL, "bad mode");
+  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  j->device_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  prof_collect(j);
+  if (j->algo == FSMC_ESS) {
+    unsigned long long cols1 = 0;
+    cudaMemcpy(&cols1, j->dev + j->o_gencols, 8, cudaMemcpyDeviceToHost);
+    j->columns_generated = (int64_t)(cols1 - cols0);
+  }
+  if (s != FSMC_OK) return s;
+  int h_err = 0;
+  CK(cudaMemcpy(&h_err, j->dev + j->o_err, 4, cudaMemcpyDeviceToHost));
+  if (h_err & ERR_SHRINK_CAP) return fsmc_fail(FSMC_EDEVICE, "ESS shrink cap reached (error word 1)");
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_job_run(fsmc_job* j, fsmc_mode mode, int64_t max_fsm_steps, void* stream) {
+  if (!j) return fsmc_fail(FSMC_EINVAL, "job is NULL");
+  if (j->submitted) return fsmc_fail(FSMC_ESTATE, "job is owned by the serving scheduler");
+  return job_run_impl(j, mode, max_fsm_steps, (cudaStream_t)stream);
+}
+
+extern "C" fsmc_status fsmc_job_reset(fsmc_job* j) {
+  if (!j) return fsmc_fail(FSMC_EINVAL, "job is NULL");
+  if (j->submitted) return fsmc_fail(FSMC_ESTATE, "job is owned by the serving scheduler");
+  if (!j->dev) return FSMC_OK;
+  return job_init(j, 0);
+}
+
+extern "C" fsmc_status fsmc_job_progress(fsmc_job* j, int64_t* min_samples, int* done) {
+  if (!j) return fsmc_fail(FSMC_EINVAL, "job is NULL");
+  if (!j->dev) {
+    if (min_samples) *min_samples = 0;
+    if (done) *done = 0;
+    return FSMC_OK;
+  }
+  std::vector<int> t((size_t)j->m);
+  CK(cudaMemcpy(t.data(), j->dev + j->o_t, t.size() * 4, cudaMemcpyDeviceToHost));
+  int mn = *std::min_element(t.begin(), t.end());
+  if (min_samples) *min_samples = mn;
+  if (done) *done = mn >= j->n;
+  return FSMC_OK;
+}
+
+// ---- reads ------------------------------------------------------------------------------------------
+template <typename T>
+static fsmc_status read_samples_t(fsmc_job* j, int64_t c0, int64_t nc, int64_t s0, int64_t ns, double* dst) {
+  const size_t d = (size_t)j->d;
+  std::vector<T> row((size_t)ns * d);
+  for (int64_t c = 0; c < nc; ++c) {
+    const char* src = j->dev + j->o_out + (((size_t)(c0 + c) * j->n + s0) * d) * sizeof(T);
+    CK(cudaMemcpy(row.data(), src, row.size() * sizeof(T), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < row.size(); ++i) dst[(size_t)c * ns * d + i] = (double)row[i];
+  }
+  return FSMC_OK;
+}
+
+static fsmc_status check_range(fsmc_job* j, int64_t c0, int64_t nc, int64_t s0, int64_t ns) {
+  if (!j->dev) return fsmc_fail(FSMC_ESTATE, "job has not run");
+  if (!j->store) return fsmc_fail(FSMC_ESTATE, "job keeps moments only");
+  if (c0 < 0 || nc < 0 || c0 + nc > j->m || s0 < 0 || ns < 0 || s0 + ns > j->n)
+    return fsmc_fail(FSMC_EINVAL, "range outside [0, m) x [0, n)");
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_read_samples(fsmc_job* j, int64_t c0, int64_t nc, int64_t s0, int64_t ns,
+                                         double* dst) {
+  if (!j || (!dst && nc * ns > 0)) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  fsmc_status s = check_range(j, c0, nc, s0, ns);
+  if (s != FSMC_OK) return s;
+  CK(cudaSetDevice(j->e->device));
+  return j->prec == FSMC_FP64 ? read_samples_t<double>(j, c0, nc, s0, ns, dst)
+                              : read_samples_t<float>(j, c0, nc, s0, ns, dst);
+}
+
+extern "C" fsmc_status fsmc_read_samples_dev(fsmc_job* j, int64_t c0, int64_t nc, int64_t s0, int64_t ns,
+                                             void* dst, void* stream) {
+  if (!j || (!dst && nc * ns > 0)) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  fsmc_status s = check_range(j, c0, nc, s0, ns);
+  if (s != FSMC_OK) return s;
+  const size_t es = j->prec == FSMC_FP64 ? 8 : 4;
+  const size_t d = (size_t)j->d;
+  const char* src = j->dev + j->o_out + (((size_t)c0 * j->n + s0) * d) * es;
+  CK(cudaMemcpy2DAsync(dst, (size_t)ns * d * es, src, (size_t)j->n * d * es, (size_t)ns * d * es,
+                       (size_t)nc, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_read_loop_counts(fsmc_job* j, int32_t* counts, int32_t* aux, int64_t* steps) {
+  if (!j) return fsmc_fail(FSMC_EINVAL, "job is NULL");
+  if (!j->dev) return fsmc_fail(FSMC_ESTATE, "job has not run");
+  if (counts)
+    CK(cudaMemcpy(counts, j->dev + j->o_counts, (size_t)j->m * j->n * 4, cudaMemcpyDeviceToHost));
+  if (aux) {
+    if (j->algo == FSMC_NUTS)
+      CK(cudaMemcpy(aux, j->dev + j->o_aux, (size_t)j->m * j->n * 4, cudaMemcpyDeviceToHost));
+    else
+      std::fill(aux, aux + (size_t)j->m * j->n, 0);
+  }
+  if (steps) CK(cudaMemcpy(steps, j->dev + j->o_steps, (size_t)j->m * 8, cudaMemcpyDeviceToHost));
+  return FSMC_OK;
+}
+
+template <typename T>
+static fsmc_status read_vec(const char* src, size_t n, double* dst) {
+  std::vector<T> h(n);
+  CK(cudaMemcpy(h.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < n; ++i) dst[i] = (double)h[i];
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_read_state(fsmc_job* j, double* x) {
+  if (!j || !x) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  if (!j->dev) {
+    std::copy(j->x0.begin(), j->x0.end(), x);
+    return FSMC_OK;
+  }
+  const size_t n = (size_t)j->m * j->d;
+  return j->prec == FSMC_FP64 ? read_vec<double>(j->dev + j->o_x, n, x) : read_vec<float>(j->dev + j->o_x, n, x);
+}
+
+extern "C" fsmc_status fsmc_read_moments(fsmc_job* j, double* sx, double* sx2, int64_t* n_kept) {
+  if (!j) return fsmc_fail(FSMC_EINVAL, "job is NULL");
+  if (!j->dev) return fsmc_fail(FSMC_ESTATE, "job has not run");
+  const size_t md = (size_t)j->m * j->d;
+  const size_t es = j->prec == FSMC_FP64 ? 8 : 4;
+  std::vector<int> t((size_t)j->m);
+  CK(cudaMemcpy(t.data(), j->dev + j->o_t, t.size() * 4, cudaMemcpyDeviceToHost));
+  if (n_kept) for (size_t c = 0; c < t.size(); ++c) n_kept[c] = t[c];
+  if (j->store) {
+    // reduce the stored samples on the device into a temporary [4][m][d] buffer
+    void* tmp = nullptr;
+    CK(cudaMalloc(&tmp, 4 * md * es));
+    cudaError_t ce = j->prec == FSMC_FP64
+        ? launch_moments_from_samples<double>((const double*)(j->dev + j->o_out), (const int*)(j->dev + j->o_t),
+                                              j->m, (int)j->n, j->d, (double*)tmp, 0)
+        : launch_moments_from_samples<float>((const float*)(j->dev + j->o_out), (const int*)(j->dev + j->o_t),
+                                             j->m, (int)j->n, j->d, (float*)tmp, 0);
+    fsmc_status s = FSMC_OK;
+    if (ce != cudaSuccess) s = fsmc_cuda_fail(ce, "moments kernel");
+    if (s == FSMC_OK && sx)
+      s = j->prec == FSMC_FP64 ? read_vec<double>((const char*)tmp, md, sx) : read_vec<float>((const char*)tmp, md, sx);
+    if (s == FSMC_OK && sx2)
+      s = j->prec == FSMC_FP64 ? read_vec<double>((const char*)tmp + 2 * md * es, md, sx2)
+                               : read_vec<float>((const char*)tmp + 2 * md * es, md, sx2);
+    cudaFree(tmp);
+    return s;
+  }
+  const char* m0 = j->dev + j->o_mom;
+  fsmc_status s = FSMC_OK;
+  if (sx) s = j->prec == FSMC_FP64 ? read_vec<double>(m0, md, sx) : read_vec<float>(m0, md, sx);
+  if (s == FSMC_OK && sx2)
+    s = j->prec == FSMC_FP64 ? read_vec<double>(m0 + 2 * md * es, md, sx2)
+                             : read_vec<float>(m0 + 2 * md * es, md, sx2);
+  return s;
+}
+
+extern "C" fsmc_status fsmc_read_stats(fsmc_job* j, fsmc_stats* o) {
+  if (!j || !o) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  *o = fsmc_stats{};
+  o->R_hat = 1.0;
+  if (!j->dev) return FSMC_OK;
+  const size_t m = (size_t)j->m, n = (size_t)j->n;
+  std::vector<int> counts(m * n), t(m);
+  std::vector<long long> steps(m);
+  CK(cudaMemcpy(counts.data(), j->dev + j->o_counts, m * n * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(t.data(), j->dev + j->o_t, m * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(steps.data(), j->dev + j->o_steps, m * 8, cudaMemcpyDeviceToHost));
+  unsigned long long iters = 0;
+  CK(cudaMemcpy(&iters, j->dev + j->o_iters, 8, cudaMemcpyDeviceToHost));
+  int err = 0;
+  CK(cudaMemcpy(&err, j->dev + j->o_err, 4, cudaMemcpyDeviceToHost));
+  const int tmin = *std::min_element(t.begin(), t.end());
+  double sum_all = 0, sum_max = 0;
+  for (int i = 0; i < tmin; ++i) {
+    int mx = 0;
+    for (size_t c = 0; c < m; ++c) {
+      const int v = counts[c * n + i];
+      mx = std::max(mx, v);
+      sum_all += v;
+    }
+    sum_max += mx;
+  }
+  if (tmin > 0) {
+    o->mean_N = sum_all / ((double)tmin * m);
+    o->mean_max_N = sum_max / tmin;
+    o->R_hat = sum_all > 0 ? o->mean_max_N / o->mean_N : 1.0;
+  }
+  for (size_t c = 0; c < m; ++c) { o->samples_done += t[c]; o->fsm_steps += steps[c]; }
+  o->sync_iterations = (int64_t)iters;
+  o->launches = j->launches;
+  o->device_ms = j->device_ms;
+  o->error_word = err;
+  for (int k = 0; k < 4; ++k) { o->kernel_ms[k] = j->kernel_ms[k]; o->kernel_launches[k] = j->kernel_launches[k]; }
+  o->columns_generated = j->columns_generated;
+  return FSMC_OK;
+}
+
+// ---- checkpoint ---------------------------------------------------------------------------------------
+struct SnapHeader {
+  uint64_t magic, bytes, m, n, d, algo, prec, flags;
+};
+static const uint64_t kSnapMagic = 0x46534d43534e4150ull;  // "FSMCSNAP"
+
+extern "C" fsmc_status fsmc_job_snapshot(fsmc_job* j, void* buf, size_t* bytes) {
+  if (!j || !bytes) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  if (!j->dev) return fsmc_fail(FSMC_ESTATE, "job has not run");
+  const size_t need = sizeof(SnapHeader) + j->bytes;
+  if (!buf) { *bytes = need; return FSMC_OK; }
+  if (*bytes < need) return fsmc_fail(FSMC_EINVAL, "snapshot buffer too small");
+  SnapHeader h{kSnapMagic, j->bytes, (uint64_t)j->m, (uint64_t)j->n, (uint64_t)j->d, (uint64_t)j->algo,
+               (uint64_t)j->prec, (uint64_t)((j->fsm_used ? 1 : 0) | (j->sync_used ? 2 : 0))};
+  std::memcpy(buf, &h, sizeof h);
+  CK(cudaMemcpy((char*)buf + sizeof h, j->dev, j->bytes, cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_job_restore(fsmc_job* j, const void* buf, size_t bytes) {
+  if (!j || !buf) return fsmc_fail(FSMC_EINVAL, "NULL argument");
+  fsmc_status s = job_materialize(j, 0);
+  if (s != FSMC_OK) return s;
+  SnapHeader h;
+  if (bytes < sizeof h) return fsmc_fail(FSMC_EINVAL, "snapshot too small");
+  std::memcpy(&h, buf, sizeof h);
+  if (h.magic != kSnapMagic || h.bytes != j->bytes || h.m != (uint64_t)j->m || h.n != (uint64_t)j->n ||
+      h.d != (uint64_t)j->d || h.algo != (uint64_t)j->algo || h.prec != (uint64_t)j->prec ||
+      bytes < sizeof h + h.bytes)
+    return fsmc_fail(FSMC_EINVAL, "snapshot does not match this job");
+  CK(cudaMemcpy(j->dev, (const char*)buf + sizeof h, j->bytes, cudaMemcpyHostToDevice));
+  j->fsm_used = h.flags & 1;
+  j->sync_used = h.flags & 2;
+  return FSMC_OK;
+}
+
+extern "C" void fsmc_job_destroy(fsmc_job* j) {
+  if (!j) return;
+  serving_forget(j);
+  fsmc_engine* e = j->e;
+  for (cudaEvent_t ev : j->event_pool) cudaEventDestroy(ev);
+  if (j->dev) {
+    cudaSetDevice(e->device);
+    cudaFree(j->dev);
+    engine_release(e, j->bytes);
+  }
+  {
+    std::lock_guard<std::mutex> g(e->mu);
+    e->jobs.erase(std::remove(e->jobs.begin(), e->jobs.end(), j), e->jobs.end());
+  }
+  delete j;
+}

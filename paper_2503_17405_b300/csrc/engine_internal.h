@@ -1,0 +1,115 @@
+// Host-side object layouts shared by the engine, the NUTS launcher and the serving scheduler.
+#pragma once
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fsmc.h"
+#include "fsmc_device.cuh"
+
+struct fsmc_engine {
+  int device = 0;
+  int sms = 148;
+  size_t budget = 0;
+  size_t in_use = 0;
+  mutable std::mutex mu;
+  std::vector<fsmc_job*> jobs;        // materialised jobs (hold device memory)
+  std::vector<fsmc_target*> targets;
+  // serving scheduler
+  std::thread sched;
+  std::condition_variable cv;
+  std::deque<fsmc_job*> queue;        // submitted, not yet admitted
+  std::vector<fsmc_job*> active;      // admitted, running
+  bool stop = false;
+  bool sched_running = false;
+  int64_t pending = 0;                // submitted and not finished
+  cudaStream_t sched_stream = nullptr;
+  std::string sched_error;
+};
+
+struct fsmc_target {
+  fsmc_engine* e = nullptr;
+  int kind = 0, d = 0, n_data = 0;
+  std::vector<double> params;
+  std::vector<void*> bufs;
+  size_t bytes = 0;
+  fsmc::TargetView<float> tv32{};
+  fsmc::TargetView<double> tv64{};
+};
+
+struct fsmc_job {
+  fsmc_engine* e = nullptr;
+  fsmc_target* tg = nullptr;
+  fsmc_algo algo = FSMC_ESS;
+  fsmc_precision prec = FSMC_FP32;
+  int64_t m = 0, n = 0;
+  int d = 0;
+  uint64_t seed = 0;
+  uint32_t chain0 = 0;
+  int store = 1;
+  fsmc_tuning tun{};
+  fsmc_dr_params dr{3, 1.0, 0.5};
+  fsmc_nuts_params nuts{0.05, 10, 1000.0};
+  std::vector<double> x0;
+  // device arena and offsets into it
+  char* dev = nullptr;
+  size_t bytes = 0;
+  int W = 0, dstride = 0;
+  size_t o_x = 0, o_t = 0, o_counts = 0, o_steps = 0, o_err = 0, o_done = 0, o_out = 0, o_mom = 0,
+         o_bar = 0, o_iters = 0;
+  size_t o_ell = 0, o_logy = 0, o_th = 0, o_k = 0, o_s = 0, o_gen = 0, o_nu = 0,  // ESS (o_ell/o_k: DR too)
+         o_gencols = 0;
+  size_t o_y = 0, o_lpy = 0;                                                      // DR
+  size_t o_aux = 0, o_nuts = 0;                                                   // NUTS
+  size_t nuts_scalar_stride = 0;
+  // run bookkeeping
+  bool fsm_used = false, sync_used = false;
+  int64_t launches = 0;
+  double device_ms = 0;
+  // per-kernel-class timing (tuning.profile_kernels)
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+  std::vector<cudaEvent_t> event_pool;
+  size_t event_next = 0;
+  double kernel_ms[4] = {0, 0, 0, 0};
+  int64_t kernel_launches[4] = {0, 0, 0, 0};
+  int64_t columns_generated = 0;
+  // serving
+  bool submitted = false;
+  fsmc_mode serve_mode = FSMC_MODE_FSM;
+  std::atomic<int> finished{0};
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+fsmc_status fsmc_fail(fsmc_status st, const std::string& msg);
+fsmc_status fsmc_cuda_fail(cudaError_t e, const char* what);
+bool engine_reserve(fsmc_engine* e, size_t bytes);
+void engine_release(fsmc_engine* e, size_t bytes);
+fsmc_status job_materialize(fsmc_job* j, cudaStream_t st);
+fsmc_status job_run_impl(fsmc_job* j, fsmc_mode mode, int64_t max_fsm_steps, cudaStream_t st);
+// Brackets one launch of kernel class `cls` with events when profiling is on.
+struct ProfScope {
+  fsmc_job* j;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(fsmc_job* job, int c, cudaStream_t s);
+  ~ProfScope();
+};
+
+// NUTS (nuts.cu)
+void nuts_layout(fsmc_job* j, size_t& off);
+fsmc_status nuts_init_state(fsmc_job* j, cudaStream_t st);
+cudaError_t nuts_fsm_round(fsmc_job* j, cudaStream_t st);
+fsmc_status nuts_run_sync(fsmc_job* j, cudaStream_t st);
+
+// serving (serving.cu)
+void serving_shutdown(fsmc_engine* e);
+void serving_forget(fsmc_job* j);

@@ -1,0 +1,529 @@
+// Elliptical slice sampling (appendix Alg. 8) as a finite state machine.
+//
+// States (Fig. 2, "Elliptical Slice Sampling"): INIT (S1) draws the threshold and the
+// initial angle and makes the first proposal; SHRINK (S2, the loop body) narrows the
+// bracket and makes a new proposal; DONE (S3) accepts and emits the sample.  One FSM
+// step is the bundled step of Alg. 4 amortised as in Alg. 5: it runs INIT or SHRINK,
+// then the single expensive call g = log f(x'), then DONE if the proposal clears the
+// threshold -- so every step costs exactly one likelihood evaluation and a sample takes
+// N + 1 steps (N shrinks).
+//
+// The ellipse direction nu = L z of INIT does not depend on the chain state, only on
+// (chain, sample), so it is produced ahead of time by a separate contraction kernel
+// (ess_nu_gen) into a per-chain ring of W slots; this is the paper's amortisation of an
+// expensive state-independent computation, moved out of the step altogether.
+#include <algorithm>
+#include "fsmc_device.cuh"
+#include "fsmc_kernels.h"
+
+namespace fsmc {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+enum EssState : int { ESS_INIT = 0, ESS_SHRINK = 1 };
+
+// ------------------------------------------------------------------------------------------
+// nu = L z for a tile of (chain, sample) columns.  z is generated from the chain's Philox
+// stream (tag 0, draws 0..ceil(d/2)-1) directly into shared memory, so it never touches HBM.
+// Block: 256 threads = 32 row-groups x 8 column-groups, each thread an 8x8 register tile;
+// tile = 256 rows x 64 columns (64 chains at the same ring offset w = blockIdx.y); the
+// reduction dimension is streamed in chunks of 16 with L^T and z staged in shared memory.
+// Rows above the diagonal are skipped per warp (L is lower triangular).
+template <typename T>
+__global__ void __launch_bounds__(256) ess_nu_gen_kernel(EssView<T> v) {
+  constexpr int BM = 256, BN = 64, BK = 16;
+  __shared__ __align__(16) T As[BK][BM];
+  __shared__ __align__(16) T Bs[BK][BN + 4];
+  __shared__ int col_sample[BN];
+
+  const int d = v.tg.d;
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.z * BM;
+  const int w = blockIdx.y;
+  const int64_t c0 = (int64_t)blockIdx.x * BN;
+
+  int active = 0;
+  if (tid < BN) {
+    const int64_t c = c0 + tid;
+    int smp = -1;
+    if (c < v.m) {
+      const int s = v.gen_lo[c] + w;
+      if (s < v.gen_hi[c]) smp = s;
+    }
+    col_sample[tid] = smp;
+    active = smp >= 0;
+  }
+  const int n_active = __syncthreads_count(active);
+  if (n_active == 0) return;
+  if (tid == 0 && blockIdx.z == 0) atomicAdd(v.gen_cols, (unsigned long long)n_active);
+
+  const int ty = tid >> 3, tx = tid & 7;
+  const int warp = tid >> 5;
+  T acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+
+  const int kmax = min(d, r0 + BM);
+  const int D = (d + 1) / 2;
+  for (int q0 = 0; q0 < kmax; q0 += BK) {
+    // z chunk: column tid/4, Philox draws q0/2 + 2*(tid%4) + {0,1}
+    {
+      const int col = tid >> 2;
+      const int smp = col_sample[col];
+      const int64_t c = c0 + col;
+      Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int blk = q0 / 2 + 2 * (tid & 3) + h;
+        T z0 = T(0), z1 = T(0);
+        if (smp >= 0 && blk < D) Conv<T>::normal_pair(key.block((uint32_t)smp, 0, (uint32_t)blk), z0, z1);
+        const int kk = 2 * (2 * (tid & 3) + h);
+        Bs[kk][col] = (q0 + kk < d) ? z0 : T(0);
+        Bs[kk + 1][col] = (q0 + kk + 1 < d) ? z1 : T(0);
+      }
+    }
+    // L^T chunk: As[kk][r] = L[r0 + r][q0 + kk]
+#pragma unroll
+    for (int h = 0; h < (BK * BM) / 256; ++h) {
+      const int idx = tid + 256 * h;
+      const int r = idx / BK, kk = idx % BK;
+      const int gr = r0 + r, gq = q0 + kk;
+      As[kk][r] = (gr < d && gq < d && gq <= gr) ? v.tg.L[(size_t)gr * d + gq] : T(0);
+    }
+    __syncthreads();
+    if (r0 + warp * 32 + 31 >= q0) {  // rows of this warp reach the chunk's columns
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[8], b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = As[kk][ty * 8 + i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = Bs[kk][tx * 8 + j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+  // write nu rows r0+ty*8.. of each active column to its ring slot
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int col = tx * 8 + j;
+    const int smp = col_sample[col];
+    if (smp < 0) continue;
+    const int64_t c = c0 + col;
+    T* dst = v.nu + ((size_t)c * v.W + (smp % v.W)) * v.dstride;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + ty * 8 + i;
+      if (r < d) dst[r] = acc[i][j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// log-likelihood contribution of this lane's coordinates of x'
+template <typename T, int G, int E>
+__device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E], int lane,
+                                        const T (&yv)[E]) {
+  T part = T(0);
+  if (tg.kind == TGT_GP_LOGIT) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e * G + lane < tg.d) part += softplus<T>(-yv[e] * xp[e]);
+    return -group_sum<G>(part);
+  } else if (tg.kind == TGT_GAUSS_CONJ) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e * G + lane < tg.d) { const T r = yv[e] - xp[e]; part = fma(r, r, part); }
+    return -group_sum<G>(part) / (T(2) * tg.s2);
+  }
+  return T(0);  // TGT_FLAT
+}
+
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
+  const T y = v - comp;
+  const T t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+template <typename T, int G, int E>
+__device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, int lane,
+                                         const T (&x)[E]) {
+  const int d = v.tg.d;
+  if (v.out) {
+    T* dst = v.out + ((size_t)c * v.n + t) * d;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = e * G + lane;
+      if (k < d) dst[k] = x[e];
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = e * G + lane;
+      if (k < d) {
+        const size_t o = (size_t)c * d + k;
+        T s = v.mom[o], cs = v.mom[o + v.mom_stride];
+        kahan_add(s, cs, x[e]);
+        v.mom[o] = s; v.mom[o + v.mom_stride] = cs;
+        T s2 = v.mom[o + 2 * v.mom_stride], c2 = v.mom[o + 3 * v.mom_stride];
+        kahan_add(s2, c2, x[e] * x[e]);
+        v.mom[o + 2 * v.mom_stride] = s2; v.mom[o + 3 * v.mom_stride] = c2;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// FSM kernel: every chain advances `budget` states (fewer if its ring runs dry or it
+// finishes).  Chain-group layout: G lanes own one chain, lane l holds coordinates l, l+G, ...
+template <typename T, int G, int E>
+__global__ void __launch_bounds__(256) ess_fsm_kernel(EssView<T> v, int budget) {
+  const int lane = threadIdx.x % G;
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int d = v.tg.d;
+  const int D = (d + 1) / 2;
+  for (int64_t c = group; c < v.m; c += ngroups) {
+    T x[E], nu[E], xp[E], yv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = e * G + lane;
+      x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
+      yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
+      nu[e] = T(0);
+    }
+    T ell = v.ell[c], logy = v.logy[c], th = v.th[c], thmin = v.thmin[c], thmax = v.thmax[c];
+    int t = v.t[c], st = v.k[c], s = v.s[c];
+    const int hi = v.gen_hi[c];
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    if (st == ESS_SHRINK && t < v.n) {
+      const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+#pragma unroll
+      for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) nu[e] = src[k]; }
+    }
+    int steps = 0;
+    int err = 0;
+    for (int b = 0; b < budget && t < v.n; ++b) {
+      if (st == ESS_INIT) {
+        if (t >= hi) break;  // direction not generated yet
+        const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+#pragma unroll
+        for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) nu[e] = src[k]; }
+        const P4 r = key.block((uint32_t)t, 0, (uint32_t)D);
+        logy = ell + Conv<T>::log_u(r.w0, r.w1);
+        th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
+        thmin = th - T(kTwoPi);
+        thmax = th;
+        s = 0;
+      } else {
+        if (th < T(0)) thmin = th; else thmax = th;
+        const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + 1 + s));
+        th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
+        ++s;
+      }
+      T sn, cs;
+      if constexpr (sizeof(T) == 4) sincosf(th, &sn, &cs); else sincos(th, &sn, &cs);
+#pragma unroll
+      for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
+      T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv);
+      if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
+      ++steps;
+      const bool accept = ellp > logy;
+      if (accept || s >= kMaxShrinks) {
+        if (accept) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) x[e] = xp[e];
+          ell = ellp;
+        } else {
+          err |= ERR_SHRINK_CAP;
+        }
+        ess_emit<T, G, E>(v, c, t, lane, x);
+        if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
+        ++t;
+        st = ESS_INIT;
+        if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
+      } else {
+        st = ESS_SHRINK;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) v.x[(size_t)c * d + k] = x[e]; }
+    if (lane == 0) {
+      v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
+      v.t[c] = t; v.k[c] = st; v.s[c] = s;
+      v.steps[c] += steps;
+      v.gen_lo[c] = hi;
+      v.gen_hi[c] = min(t + v.W, v.n);
+      if (err) atomicOr(v.err, err);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Synchronised kernel (Alg. 6, vmap(sample)): for every sample, INIT for all chains, then
+// the loop body for all chains still below their threshold, with a grid-wide barrier
+// after every iteration, until no chain anywhere is active; then the next sample.
+// Chains are assigned statically to groups; chain state lives in global memory.
+// Launched cooperatively (co-residency guaranteed), barrier waits are bounded.
+template <typename T, int G, int E>
+__global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin, int t_end,
+                                                       GridBarrier bar, unsigned* active_cnt,
+                                                       unsigned long long* iterations) {
+  const int lane = threadIdx.x % G;
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int d = v.tg.d;
+  const int D = (d + 1) / 2;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  __shared__ unsigned blk_active;
+  int iter = 0;
+  int err = 0;
+  T yv[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * G + lane;
+    yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
+  }
+
+  for (int t = t_begin; t < t_end; ++t) {
+    bool first = true;
+    while (true) {
+      if (threadIdx.x == 0) blk_active = 0;
+      __syncthreads();
+      unsigned my_active = 0;
+      for (int64_t c = group; c < v.m; c += ngroups) {
+        if (!first && v.k[c] != ESS_SHRINK) continue;  // masked: already done with sample t
+        T x[E], nu[E], xp[E];
+        const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int k = e * G + lane;
+          x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
+          nu[e] = k < d ? src[k] : T(0);
+        }
+        const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+        T logy, th, thmin, thmax;
+        int s;
+        if (first) {  // INIT (S1)
+          const P4 r = key.block((uint32_t)t, 0, (uint32_t)D);
+          logy = v.ell[c] + Conv<T>::log_u(r.w0, r.w1);
+          th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
+          thmin = th - T(kTwoPi);
+          thmax = th;
+          s = 0;
+        } else {      // SHRINK (S2)
+          logy = v.logy[c]; th = v.th[c]; thmin = v.thmin[c]; thmax = v.thmax[c]; s = v.s[c];
+          if (th < T(0)) thmin = th; else thmax = th;
+          const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + 1 + s));
+          th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
+          ++s;
+        }
+        T sn, cs;
+        if constexpr (sizeof(T) == 4) sincosf(th, &sn, &cs); else sincos(th, &sn, &cs);
+#pragma unroll
+        for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
+        T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv);
+        if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
+        const bool accept = ellp > logy;
+        if (accept || s >= kMaxShrinks) {  // DONE (S3)
+          if (accept) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int k = e * G + lane;
+              if (k < d) v.x[(size_t)c * d + k] = xp[e];
+              x[e] = xp[e];
+            }
+          } else {
+            err |= ERR_SHRINK_CAP;
+          }
+          ess_emit<T, G, E>(v, c, t, lane, x);
+          if (lane == 0) {
+            if (accept) v.ell[c] = ellp;
+            v.counts[(size_t)c * v.n + t] = s;
+            v.k[c] = ESS_INIT;
+            v.t[c] = t + 1;
+            v.steps[c] += 1;
+            if (t + 1 == v.n) atomicAdd(v.chains_done, 1);
+          }
+        } else {
+          if (lane == 0) {
+            v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax; v.s[c] = s;
+            v.k[c] = ESS_SHRINK;
+            v.steps[c] += 1;
+          }
+          my_active = 1;
+        }
+      }
+      if (my_active && lane == 0) atomicAdd(&blk_active, 1u);
+      __syncthreads();
+      const int slot = iter % 3;
+      if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+      if (!grid_sync(bar, v.err)) return;
+      const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+      if (leader) {
+        active_cnt[(iter + 2) % 3] = 0;  // last read one iteration ago, next written in two
+        if (!first) *iterations += 1;    // one loop-body iteration of the batched while
+      }
+      ++iter;
+      first = false;
+      if (total == 0) break;
+    }
+  }
+  if (err && lane == 0) atomicOr(v.err, err);
+}
+
+// log f(x) of every chain's starting point
+template <typename T>
+__global__ void ess_init_kernel(EssView<T> v) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.m) return;
+  const int d = v.tg.d;
+  T acc = T(0);
+  for (int k = 0; k < d; ++k) {
+    const T xk = v.x[(size_t)c * d + k];
+    if (v.tg.kind == TGT_GP_LOGIT) acc += softplus<T>(-v.tg.vec[k] * xk);
+    else if (v.tg.kind == TGT_GAUSS_CONJ) { const T r = v.tg.vec[k] - xk; acc = fma(r, r, acc); }
+  }
+  T ell = T(0);
+  if (v.tg.kind == TGT_GP_LOGIT) ell = -acc;
+  else if (v.tg.kind == TGT_GAUSS_CONJ) ell = -acc / (T(2) * v.tg.s2);
+  if (!(ell == ell)) { ell = neg_inf<T>(); atomicOr(v.err, ERR_NONFINITE); }
+  v.ell[c] = ell;
+}
+
+template <typename T>
+__global__ void moments_kernel(const T* samples, const int* t, int64_t m, int n, int d, T* out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * d) return;
+  const int64_t c = idx / d;
+  const int k = (int)(idx % d);
+  T s = 0, cs = 0, s2 = 0, c2 = 0;
+  const int tc = t[c];
+  for (int i = 0; i < tc; ++i) {
+    const T x = samples[((size_t)c * n + i) * d + k];
+    kahan_add(s, cs, x);
+    kahan_add(s2, c2, x * x);
+  }
+  const size_t md = (size_t)m * d;
+  out[idx] = s; out[md + idx] = cs; out[2 * md + idx] = s2; out[3 * md + idx] = c2;
+}
+
+template <typename T>
+cudaError_t launch_moments_from_samples(const T* samples, const int* t, int64_t m, int n, int d, T* out,
+                                        cudaStream_t st) {
+  const int64_t total = m * d;
+  moments_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(samples, t, m, n, d, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+template cudaError_t launch_moments_from_samples<float>(const float*, const int*, int64_t, int, int, float*,
+                                                        cudaStream_t);
+template cudaError_t launch_moments_from_samples<double>(const double*, const int*, int64_t, int, int, double*,
+                                                         cudaStream_t);
+
+__global__ void fill_int_kernel(int* p, int64_t n, int value) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = value;
+}
+
+cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  fill_int_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, n, value);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ess_init(const EssView<T>& v, cudaStream_t st) {
+  ess_init_kernel<T><<<(unsigned)((v.m + 127) / 128), 128, 0, st>>>(v);
+  return cudaGetLastError();
+}
+template cudaError_t launch_ess_init<float>(const EssView<float>&, cudaStream_t);
+template cudaError_t launch_ess_init<double>(const EssView<double>&, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
+// host launchers
+template <typename T>
+cudaError_t launch_ess_nu_gen(const EssView<T>& v, cudaStream_t st) {
+  dim3 grid((unsigned)((v.m + 63) / 64), (unsigned)v.W, (unsigned)((v.tg.d + 255) / 256));
+  ess_nu_gen_kernel<T><<<grid, 256, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+template <typename T, int G, int E>
+static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cudaStream_t st) {
+  const int64_t groups_per_block = threads / G;
+  const int64_t blocks = (v.m + groups_per_block - 1) / groups_per_block;
+  ess_fsm_kernel<T, G, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  return cudaGetLastError();
+}
+
+template <typename T, int G, int E>
+static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier bar,
+                               unsigned* active_cnt, unsigned long long* iters, int threads,
+                               cudaStream_t st) {
+  auto kern = ess_sync_kernel<T, G, E>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t groups_per_block = threads / G;
+  int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (v.m + groups_per_block - 1) / groups_per_block);
+  if (blocks < 1) blocks = 1;
+  EssView<T> vv = v;
+  void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+}
+
+#define FSMC_ESS_DISPATCH(FN, ...)                                              \
+  do {                                                                          \
+    const int d = v.tg.d;                                                       \
+    if (G == 1) {                                                               \
+      if (d <= 2) return FN<T, 1, 2>(__VA_ARGS__);                              \
+      if (d <= 4) return FN<T, 1, 4>(__VA_ARGS__);                              \
+      if (d <= 8) return FN<T, 1, 8>(__VA_ARGS__);                              \
+      if (d <= 16) return FN<T, 1, 16>(__VA_ARGS__);                            \
+      if (d <= 32) return FN<T, 1, 32>(__VA_ARGS__);                            \
+    } else if (G == 32) {                                                       \
+      if (d <= 32) return FN<T, 32, 1>(__VA_ARGS__);                            \
+      if (d <= 64) return FN<T, 32, 2>(__VA_ARGS__);                            \
+      if (d <= 128) return FN<T, 32, 4>(__VA_ARGS__);                           \
+      if (d <= 256) return FN<T, 32, 8>(__VA_ARGS__);                           \
+      if (d <= 512) return FN<T, 32, 16>(__VA_ARGS__);                          \
+      if (d <= 1024) return FN<T, 32, 32>(__VA_ARGS__);                         \
+    }                                                                           \
+    return cudaErrorInvalidValue;                                               \
+  } while (0)
+
+template <typename T>
+cudaError_t launch_ess_fsm(const EssView<T>& v, int G, int budget, int threads, cudaStream_t st) {
+  FSMC_ESS_DISPATCH(fsm_launch, v, budget, threads, st);
+}
+
+template <typename T>
+cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarrier bar,
+                            unsigned* active_cnt, unsigned long long* iters, int threads,
+                            cudaStream_t st) {
+  FSMC_ESS_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
+}
+
+template cudaError_t launch_ess_nu_gen<float>(const EssView<float>&, cudaStream_t);
+template cudaError_t launch_ess_nu_gen<double>(const EssView<double>&, cudaStream_t);
+template cudaError_t launch_ess_fsm<float>(const EssView<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_ess_fsm<double>(const EssView<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_ess_sync<float>(const EssView<float>&, int, int, int, GridBarrier,
+                                            unsigned*, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_ess_sync<double>(const EssView<double>&, int, int, int, GridBarrier,
+                                             unsigned*, unsigned long long*, int, cudaStream_t);
+
+}  // namespace fsmc

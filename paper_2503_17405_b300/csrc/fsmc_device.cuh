@@ -1,0 +1,162 @@
+// Device building blocks shared by the fsmc kernels: counter-based RNG, uniform and
+// normal conversions, chain-group reductions, a bounded grid barrier, and the
+// structure-of-arrays job view the kernels read and write.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fsmc {
+
+// ---- error bits written to a job's device error word ---------------------------------
+enum : int {
+  ERR_SHRINK_CAP = 1,     // an ESS bracket shrank kMaxShrinks times without acceptance
+  ERR_BARRIER_TIMEOUT = 2,// a bounded grid-barrier wait expired
+  ERR_NONFINITE = 4,      // a non-finite log-density was treated as -inf
+};
+constexpr int kMaxShrinks = 10000;
+constexpr unsigned kBarrierSpinLimit = 1u << 24;  // ~1-2 s of nanosleep(64) polls
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -----------------------------------
+struct P4 { uint32_t w0, w1, w2, w3; };
+
+__device__ __forceinline__ P4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+  }
+  return P4{c0, c1, c2, c3};
+}
+
+// Key = (chain, seed_lo); counter = (draw, sample, tag, seed_hi).
+struct Key {
+  uint32_t chain, seed_lo, seed_hi;
+  __device__ __forceinline__ P4 block(uint32_t sample, uint32_t tag, uint32_t draw) const {
+    return philox(draw, sample, tag, seed_hi, chain, seed_lo);
+  }
+};
+
+// ---- conversions ----------------------------------------------------------------------------
+// Uniform in (0,1): u = ((hi:lo >> 12) + 1/2) 2^-52, exact in double.  1 - u is the same map of
+// the complemented words, which gives log u accurately near 1 in single precision.
+template <typename T> struct Conv;
+
+template <> struct Conv<double> {
+  static __device__ __forceinline__ double u(uint32_t hi, uint32_t lo) {
+    unsigned long long v = (((unsigned long long)hi << 32) | lo) >> 12;
+    return ((double)v + 0.5) * 0x1p-52;
+  }
+  static __device__ __forceinline__ double log_u(uint32_t hi, uint32_t lo) { return log(u(hi, lo)); }
+  // Box-Muller pair: r = sqrt(-2 ln u(w0,w1)), phi = 2 pi u(w2,w3)
+  static __device__ __forceinline__ void normal_pair(const P4& b, double& z0, double& z1) {
+    const double r = sqrt(-2.0 * log_u(b.w0, b.w1));
+    double s, c;
+    sincospi(2.0 * u(b.w2, b.w3), &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+  }
+};
+
+template <> struct Conv<float> {
+  // single-precision rounding of the same 52-bit uniform (relative error <= 2^-23)
+  static __device__ __forceinline__ float u(uint32_t hi, uint32_t lo) {
+    return fmaf((float)hi, 0x1p-32f, fmaf((float)(lo >> 12), 0x1p-52f, 0x1p-53f));
+  }
+  // log u without cancellation: log1p(-(1-u)) with 1-u from the complemented words when u >= 1/2
+  static __device__ __forceinline__ float log_u(uint32_t hi, uint32_t lo) {
+    return (hi & 0x80000000u) ? log1pf(-u(~hi, ~lo)) : logf(u(hi, lo));
+  }
+  static __device__ __forceinline__ void normal_pair(const P4& b, float& z0, float& z1) {
+    const float r = sqrtf(-2.0f * log_u(b.w0, b.w1));
+    float s, c;
+    sincospif(2.0f * u(b.w2, b.w3), &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+  }
+};
+
+// ---- chain-group reductions -------------------------------------------------------------------
+// A chain is owned by G consecutive lanes (G = 1 chain-per-thread, G = 32 chain-per-warp).
+// Butterfly sums give every lane of the group the same bits.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- bounded grid barrier (cooperative launches only) ----------------------------------------
+// Sense-free generation barrier.  Every wait is bounded: after kBarrierSpinLimit polls the
+// block records ERR_BARRIER_TIMEOUT and returns false; callers then leave the kernel.
+struct GridBarrier {
+  unsigned* count;
+  unsigned* generation;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    volatile unsigned* gen = b.generation;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(b.count, 1u) == nblocks - 1) {
+      *b.count = 0;
+      __threadfence();
+      atomicAdd(b.generation, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*gen == g) {
+        if (++spins > kBarrierSpinLimit || *(volatile int*)err & ERR_BARRIER_TIMEOUT) {
+          atomicOr(err, ERR_BARRIER_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ---- device-side target view ---------------------------------------------------------------------
+enum TargetKind : int {
+  TGT_GAUSS_CONJ = 0, TGT_GP_LOGIT = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3, TGT_GAUSS_DIAG = 4, TGT_FLAT = 5
+};
+
+template <typename T>
+struct TargetView {
+  int kind;
+  int d;
+  int n_data;
+  const T* L;     // ESS prior Cholesky [d][d] (lower)
+  const T* vec;   // y (GAUSS_CONJ), s (GP_LOGIT), mu (GAUSS_DIAG), y (LOGREG)
+  const T* vec2;  // sigma (GAUSS_DIAG)
+  const T* X;     // LOGREG design matrix [n_data][d]
+  T s2;           // GAUSS_CONJ noise variance
+};
+
+template <typename T>
+__device__ __forceinline__ T softplus(T t) {
+  // log(1 + e^t) without overflow
+  if constexpr (sizeof(T) == 4) {
+    return t > 0.f ? t + log1pf(__expf(-t)) : log1pf(__expf(t));
+  } else {
+    return t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t));
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T neg_inf() { return -(T)INFINITY; }
+
+}  // namespace fsmc

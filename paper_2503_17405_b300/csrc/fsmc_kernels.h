@@ -1,0 +1,82 @@
+// Structure-of-arrays job views passed by value to the kernels, and the host-side
+// launchers each sampler's .cu file exports to the engine.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fsmc {
+
+template <typename T> struct TargetView;
+struct GridBarrier;
+
+// Fields common to every sampler: chain range, sample bookkeeping, outputs.
+template <typename T>
+struct ChainsView {
+  int64_t m;             // chains in this view
+  int n;                 // samples per chain
+  uint32_t chain0;       // global chain id of chain 0 (RNG key)
+  uint32_t seed_lo, seed_hi;
+  T* x;                  // [m][d] current state
+  int* t;                // [m] samples emitted
+  T* out;                // [m][n][d] samples, or null (moments only)
+  T* mom;                // [4][m][d] Kahan sums of x and x^2 (moments only)
+  size_t mom_stride;     // m * d
+  int* counts;           // [m][n] loop-body count N_ij
+  long long* steps;      // [m] FSM states executed
+  int* err;              // error word
+  int* chains_done;      // chains that reached n
+};
+
+template <typename T>
+struct EssView : ChainsView<T> {
+  TargetView<T> tg;
+  int W;                 // ring slots per chain
+  int dstride;           // ring row stride (elements)
+  T* ell;                // [m] log f(x)
+  T* logy;               // [m] threshold
+  T* th; T* thmin; T* thmax;  // [m] angle and bracket
+  int* k;                // [m] FSM state
+  int* s;                // [m] shrinks in the current sample
+  int* gen_lo; int* gen_hi;   // [m] ring fill window [gen_lo, gen_hi) in samples
+  T* nu;                 // [m][W][dstride] pre-generated ellipse directions
+  unsigned long long* gen_cols;  // directions generated so far (statistics)
+};
+
+template <typename T>
+struct DrView : ChainsView<T> {
+  TargetView<T> tg;
+  int n_stages;
+  T sig[3];              // stage scales
+  T* lp;                 // [m] log pi(x)
+  T* y;                  // [2][m][d] rejected proposals y1, y2 of the current sample
+  T* lpy;                // [2][m] their log pi
+  int* k;                // [m] next stage to try
+};
+
+template <typename T>
+cudaError_t launch_ess_nu_gen(const EssView<T>& v, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ess_fsm(const EssView<T>& v, int G, int budget, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarrier bar,
+                            unsigned* active_cnt, unsigned long long* iters, int threads,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t launch_ess_init(const EssView<T>& v, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_dr_fsm(const DrView<T>& v, int budget, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dr_sync(const DrView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                           unsigned long long* iters, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st);
+
+cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st);
+// Per-chain Kahan sums of x and x^2 over the first t[c] stored samples: out [4][m][d]
+// (sum, compensation, sum of squares, compensation).
+template <typename T>
+cudaError_t launch_moments_from_samples(const T* samples, const int* t, int64_t m, int n, int d, T* out,
+                                        cudaStream_t st);
+
+}  // namespace fsmc

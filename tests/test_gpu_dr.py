@@ -1,0 +1,101 @@
+"""CUDA 3-stage delayed rejection vs the FP64 oracle, through the C ABI (libfsmc.so)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_17405_b300 import workloads as W
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+DR = {"n_stages": 3, "scale0": 1.0, "factor": 0.5}
+DR_ARGS = [3, 1.0, 0.5]
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2503_17405_b300 import build, fsmc
+    build.build()
+    e = fsmc.Engine(0)
+    yield e
+    e.close()
+
+
+def _run(eng, kind, d, params, m, n, x0, prec, mode="fsm", seed=1, tuning=None, n_data=0):
+    tg = eng.target(kind, d, params, n_data=n_data)
+    job = eng.job(tg, "dr", m, n, x0=x0, seed=seed, prec=prec, dr=DR, tuning=tuning)
+    job.run(mode)
+    return job
+
+
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_funnel_matches_oracle(eng, mode):
+    m, n = 256, 500
+    x0 = W.x0_funnel_exact(m)
+    job = _run(eng, "funnel", 10, None, m, n, x0, "fp64", mode)
+    ref = O.run("dr", "funnel", np.zeros(1), x0, n, seed=1, algo_params=DR_ARGS)
+    counts, _, steps = job.loop_counts()
+    compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    if mode == "fsm":
+        # one PROPOSE step per stage tried
+        assert np.array_equal(steps, counts.sum(1))
+    else:
+        assert job.stats()["sync_iterations"] == int(counts.max(0).sum())
+    job.close()
+
+
+def test_fp64_gauss_diag_matches_oracle(eng):
+    w = W.gauss_diag(5)
+    m, n = 64, 300
+    x0 = W.x0_gauss_diag_exact(w, m)
+    job = _run(eng, "gauss_diag", 5, w["params"], m, n, x0, "fp64")
+    ref = O.run("dr", "gauss_diag", w["params"], x0, n, seed=1, algo_params=DR_ARGS)
+    counts, _, _ = job.loop_counts()
+    compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    job.close()
+
+
+def test_fp32_funnel_matches_oracle_until_branch_flip(eng):
+    m, n = 512, 1000
+    x0 = W.x0_funnel_exact(m)
+    job = _run(eng, "funnel", 10, None, m, n, x0, "fp32")
+    ref = O.run("dr", "funnel", np.zeros(1), x0, n, seed=1, algo_params=DR_ARGS)
+    counts, _, _ = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp32")
+    print("fp32 funnel parity", r["flipped"], "flipped of", m, "max err", r["max_err"])
+    assert r["flipped"] <= m // 4
+    job.close()
+
+
+def test_sync_and_fsm_identical_fp32(eng):
+    m, n = 4096, 100
+    x0 = W.x0_funnel_exact(m)
+    a = _run(eng, "funnel", 10, None, m, n, x0, "fp32", "fsm")
+    b = _run(eng, "funnel", 10, None, m, n, x0, "fp32", "sync")
+    assert np.array_equal(a.loop_counts()[0], b.loop_counts()[0])
+    assert np.array_equal(a.samples(), b.samples())
+    a.close()
+    b.close()
+
+
+@pytest.fixture(scope="module")
+def full_funnel_job(eng):
+    """65536 chains x 5000 samples, FP32: the delayed-rejection benchmark configuration."""
+    m, n = 65536, 5000
+    x0 = W.x0_funnel_exact(m)
+    job = _run(eng, "funnel", 10, None, m, n, x0, "fp32")
+    yield x0, job
+    job.close()
+
+
+@pytest.mark.parametrize("chain", [0, 32767, 65535])
+def test_full_size_funnel_sampled_chains(full_funnel_job, chain):
+    x0, job = full_funnel_job
+    nref = 1000
+    ref = O.run("dr", "funnel", np.zeros(1), x0[chain:chain + 1], nref, seed=1, chain0=chain,
+                algo_params=DR_ARGS)
+    counts, _, _ = job.loop_counts()
+    assert counts.min() >= 1 and counts.max() <= 3
+    r = compare(job.samples(chain, 1, 0, nref), counts[chain:chain + 1, :nref], ref["samples"],
+                ref["counts"], "fp32")
+    print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])

@@ -1,0 +1,168 @@
+"""CUDA elliptical slice sampling vs the FP64 oracle, through the C ABI (libfsmc.so)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_17405_b300 import workloads as W
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2503_17405_b300 import build, fsmc
+    build.build()
+    e = fsmc.Engine(0)
+    yield e
+    e.close()
+
+
+def _run(eng, w, m, n, x0, prec, mode="fsm", seed=1, tuning=None, store=True):
+    tg = eng.target(w["kind"], w["d"], w["params"])
+    job = eng.job(tg, "ess", m, n, x0=x0, seed=seed, prec=prec, tuning=tuning, store=store)
+    job.run(mode)
+    return job
+
+
+@pytest.mark.parametrize("lanes", [1, 32])
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_conjugate_gaussian_matches_oracle(eng, lanes, mode):
+    # ESS on the conjugate Gaussian, d = 16, 128 chains x 1000 samples, FP64
+    w = W.gauss_conj(16)
+    m, n = 128, 1000
+    x0 = W.x0_zeros(m, 16)
+    job = _run(eng, w, m, n, x0, "fp64", mode, tuning={"lanes_per_chain": lanes})
+    ref = O.run("ess", "gauss_conj", w["params"], x0, n, seed=1)
+    counts, _, steps = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    st = job.stats()
+    if mode == "fsm":
+        # every FSM step runs exactly one likelihood evaluation: N + 1 per sample
+        assert np.array_equal(steps, (counts + 1).sum(1))
+    else:
+        # the synchronised loop runs max_j N_ij body iterations per sample (Sec. 2.2)
+        assert st["sync_iterations"] == int(counts.max(0).sum())
+    job.close()
+
+
+def test_fp32_gp_logit_matches_oracle_until_branch_flip(eng):
+    w = W.gp_logit(256)
+    m, n = 48, 400
+    x0 = W.x0_zeros(m, 256)
+    job = _run(eng, w, m, n, x0, "fp32")
+    ref = O.run("ess", "gp_logit", w["params"], x0, n, seed=1)
+    counts, _, _ = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp32")
+    print("fp32 gp-logit parity", r["flipped"], "flipped of", m, "max err", r["max_err"])
+    assert r["flipped"] <= m // 4
+    job.close()
+
+
+def test_sync_and_fsm_give_identical_samples(eng):
+    w = W.gp_logit(256)
+    m, n = 300, 64
+    x0 = W.x0_normal(m, 256, scale=0.1)
+    a = _run(eng, w, m, n, x0, "fp32", "fsm")
+    b = _run(eng, w, m, n, x0, "fp32", "sync")
+    ca, _, _ = a.loop_counts()
+    cb, _, _ = b.loop_counts()
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(a.samples(), b.samples())
+    assert b.stats()["sync_iterations"] == int(cb.max(0).sum())
+    a.close()
+    b.close()
+
+
+def test_flat_likelihood_never_shrinks(eng):
+    w = W.flat(8)
+    m = 64
+    x0 = W.x0_normal(m, 8) @ w["L"].T
+    job = _run(eng, w, m, 50, x0, "fp64", tuning={"lanes_per_chain": 1})
+    counts, _, _ = job.loop_counts()
+    assert np.all(counts == 0)
+    ref = O.run("ess", "flat", w["params"], x0, 50, seed=1)
+    compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    job.close()
+
+
+def test_resume_from_snapshot_is_bit_exact(eng):
+    w = W.gauss_conj(16)
+    m, n = 96, 300
+    x0 = W.x0_normal(m, 16)
+    whole = _run(eng, w, m, n, x0, "fp32", tuning={"lanes_per_chain": 32, "steps_per_launch": 16})
+    tg = eng.target("gauss_conj", 16, w["params"])
+    part = eng.job(tg, "ess", m, n, x0=x0, seed=1, prec="fp32",
+                   tuning={"lanes_per_chain": 32, "steps_per_launch": 16})
+    part.run("fsm", max_fsm_steps=100)
+    mn, done = part.progress()
+    assert not done and mn > 0
+    blob = part.snapshot()
+    part.close()
+    fresh = eng.job(tg, "ess", m, n, x0=x0, seed=1, prec="fp32",
+                    tuning={"lanes_per_chain": 32, "steps_per_launch": 16})
+    fresh.restore(blob)
+    fresh.run("fsm")
+    assert np.array_equal(fresh.samples(), whole.samples())
+    assert np.array_equal(fresh.loop_counts()[0], whole.loop_counts()[0])
+    whole.close()
+    fresh.close()
+
+
+def test_moments_only_mode_matches_stored_samples(eng):
+    w = W.gauss_conj(16)
+    m, n = 64, 200
+    x0 = W.x0_normal(m, 16)
+    a = _run(eng, w, m, n, x0, "fp64", store=True)
+    b = _run(eng, w, m, n, x0, "fp64", store=False)
+    xs = a.samples()
+    sx, sx2, nk = b.moments()
+    assert np.all(nk == n)
+    assert np.allclose(sx, xs.sum(1), rtol=1e-12, atol=1e-10)
+    assert np.allclose(sx2, (xs ** 2).sum(1), rtol=1e-12, atol=1e-10)
+    with pytest.raises(Exception):
+        b.samples(0, 1, 0, 1)
+    a.close()
+    b.close()
+
+
+def test_admission_and_argument_errors(eng):
+    from paper_2503_17405_b300 import fsmc
+    small = fsmc.Engine(0, hbm_budget_bytes=1 << 20)
+    w = W.gp_logit(256)
+    tg = small.target("gp_logit", 256, w["params"])
+    job = small.job(tg, "ess", 4096, 1000)
+    with pytest.raises(fsmc.FsmcError) as ei:
+        job.run()
+    assert ei.value.status == fsmc.EADMIT
+    with pytest.raises(fsmc.FsmcError) as ei:
+        small.job(tg, "dr", 4, 10)
+    assert ei.value.status == fsmc.EINVAL
+    with pytest.raises(fsmc.FsmcError) as ei:
+        small.target("gp_logit", 256, w["params"][:-1])
+    assert ei.value.status == fsmc.EINVAL
+    small.close()
+
+
+@pytest.fixture(scope="module")
+def full_gp_job(eng):
+    """16384 chains x 2000 samples, FP32: the benchmark configuration."""
+    w = W.gp_logit(256)
+    job = _run(eng, w, 16384, 2000, W.x0_zeros(16384, 256), "fp32")
+    yield w, job
+    job.close()
+
+
+@pytest.mark.parametrize("chain", [0, 8191, 16383])
+def test_full_size_gp_logit_sampled_chains(full_gp_job, chain):
+    """The oracle recomputes sampled chains one by one (the RNG is keyed by chain) over
+    the first 1000 samples of the full-size run."""
+    w, job = full_gp_job
+    nref = 1000
+    ref = O.run("ess", "gp_logit", w["params"], np.zeros((1, 256)), nref, seed=1, chain0=chain)
+    x = job.samples(chain, 1, 0, nref)
+    counts, _, _ = job.loop_counts()
+    assert np.all(counts >= 0)
+    r = compare(x, counts[chain:chain + 1, :nref], ref["samples"], ref["counts"], "fp32")
+    print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
