@@ -208,6 +208,37 @@ fsmc_status fsmc_poll(fsmc_job* j, int* done, double* latency_s);
 /* Blocks until every submitted job has finished or timeout_s elapses (ETIMEOUT). */
 fsmc_status fsmc_wait_all(fsmc_engine* e, double timeout_s);
 
+/* ---- allocation-free ESS run -------------------------------------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that must not
+ * allocate device memory themselves or through this library: code running under a memory
+ * planner that owns the whole device budget, a plugin that is handed device buffers but no
+ * allocator, or a latency-critical loop in which cudaMalloc's implicit device-wide
+ * synchronisation is not acceptable.
+ * It runs FP32 elliptical slice sampling in FSM mode to completion -- the same kernels, and
+ * the same samples and loop counts, as fsmc_job_run on an FP32 ESS job that stores its
+ * samples, for equal inputs, seed and lanes_per_chain (1 or 32).  Every pointer is
+ * caller-owned device memory:
+ *   L_dev       [d*d] lower Cholesky factor of the prior covariance (read)
+ *   vec_dev     [d]   y for GAUSS_CONJ, labels s in {-1,+1} for GP_LOGIT, unused for FLAT (read)
+ *   noise_var         GAUSS_CONJ likelihood variance (ignored otherwise)
+ *   x0_dev      [n_chains][d] starting points (read)
+ *   samples_dev [n_chains][n_samples][d] (written)
+ *   counts_dev  [n_chains][n_samples] loop-body counts N_ij (written)
+ * Working memory is one 32 MiB array in the library's device image, which every GPU that
+ * loads the library holds until the process exits.  A run needs about
+ * n_chains * (4 d + 4 W roundup(d, 32) + 48) bytes, with W = 16 ring slots per chain lowered
+ * to 8, 4 or 2 when needed to fit; larger runs fail with FSMC_EINVAL and a message stating
+ * the limit.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  The call
+ * allocates nothing and returns when the run is complete.  All calls on a device share the
+ * one array; each call first resets the parts that must start from zero, and calls that
+ * overlap on the GPU (from other threads or streams) race with each other.
+ * Errors: EINVAL, ECUDA, ETIMEOUT, EDEVICE. */
+fsmc_status fsmc_ess_run_static(int target_kind, int d, const float* L_dev, const float* vec_dev,
+                                float noise_var, int64_t n_chains, int64_t n_samples,
+                                const float* x0_dev, uint64_t seed, int lanes_per_chain,
+                                float* samples_dev, int32_t* counts_dev, void* cuda_stream);
+
 const char* fsmc_last_error(void);
 
 #ifdef __cplusplus

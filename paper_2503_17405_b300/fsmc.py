@@ -90,6 +90,9 @@ SIGNATURES = [
     ("fsmc_submit", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     ("fsmc_poll", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _dp]),
     ("fsmc_wait_all", ctypes.c_int, [_vp, ctypes.c_double]),
+    ("fsmc_ess_run_static", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_float,
+                                           ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_uint64,
+                                           ctypes.c_int, _vp, _vp, _vp]),
     ("fsmc_last_error", ctypes.c_char_p, []),
 ]
 
@@ -285,3 +288,11 @@ class Job:
         if self._h:
             load().fsmc_job_destroy(self._h)
             self._h = _vp()
+
+
+def ess_run_static(kind, d, L_ptr, vec_ptr, noise_var, n_chains, n_samples, x0_ptr, seed,
+                   lanes_per_chain, samples_ptr, counts_ptr, stream=None):
+    """fsmc_ess_run_static: every argument ending in _ptr is a device address (int)."""
+    _check(load().fsmc_ess_run_static(TARGET[kind], d, L_ptr, vec_ptr, noise_var, n_chains,
+                                      n_samples, x0_ptr, seed, lanes_per_chain, samples_ptr,
+                                      counts_ptr, stream))
