@@ -104,9 +104,14 @@ def normals(seed, chain, sample, tag, draw0, d):
     return z
 
 
+def _params(params):
+    p = _f64(params if params is not None else np.zeros(1))
+    return p if p.size else np.zeros(1)
+
+
 def logp(kind, params, x, n_data=0, grad=False):
     x = _f64(x)
-    params = _f64(params if params is not None else np.zeros(1))
+    params = _params(params)
     g = np.zeros_like(x) if grad else None
     v = lib().ora_logp(TARGET[kind], x.size, n_data, _dp(params), _dp(x), _dp(g))
     return (v, g) if grad else v
@@ -115,7 +120,7 @@ def logp(kind, params, x, n_data=0, grad=False):
 def leapfrog(kind, params, x, p, eps, n_steps, n_data=0):
     x = _f64(x).copy()
     p = _f64(p).copy()
-    params = _f64(params if params is not None else np.zeros(1))
+    params = _params(params)
     lib().ora_leapfrog(TARGET[kind], x.size, n_data, _dp(params), _dp(x), _dp(p), eps, n_steps)
     return x, p
 
@@ -137,7 +142,7 @@ def run(algo, kind, params, x0, n_samples, seed, chain0=0, n_data=0, algo_params
     """
     x0 = _f64(x0)
     m, d = x0.shape
-    params = _f64(params if params is not None else np.zeros(1))
+    params = _params(params)
     ap = None if algo_params is None else _f64(algo_params)
     samples = np.zeros((m, n_samples, d)) if store else None
     counts = np.zeros((m, n_samples), dtype=np.int32)

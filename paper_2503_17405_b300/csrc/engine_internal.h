@@ -68,8 +68,7 @@ struct fsmc_job {
   size_t o_ell = 0, o_logy = 0, o_th = 0, o_k = 0, o_s = 0, o_gen = 0, o_nu = 0,  // ESS (o_ell/o_k: DR too)
          o_gencols = 0;
   size_t o_y = 0, o_lpy = 0;                                                      // DR
-  size_t o_aux = 0, o_nuts = 0;                                                   // NUTS
-  size_t nuts_scalar_stride = 0;
+  size_t o_aux = 0, o_nuts = 0, o_nuts_end = 0;                                   // NUTS
   // run bookkeeping
   bool fsm_used = false, sync_used = false;
   int64_t launches = 0;

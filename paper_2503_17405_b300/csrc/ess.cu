@@ -28,8 +28,9 @@ enum EssState : int { ESS_INIT = 0, ESS_SHRINK = 1 };
 // tile = 256 rows x 64 columns (64 chains at the same ring offset w = blockIdx.y); the
 // reduction dimension is streamed in chunks of 16 with L^T and z staged in shared memory.
 // Rows above the diagonal are skipped per warp (L is lower triangular).
+// One tile (bx = chain tile, by = ring offset, bz = row tile); called by all 256 threads.
 template <typename T>
-__global__ void __launch_bounds__(256) ess_nu_gen_kernel(EssView<T> v) {
+__device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx, int by, int bz) {
   constexpr int BM = 256, BN = 64, BK = 16;
   __shared__ __align__(16) T As[BK][BM];
   __shared__ __align__(16) T Bs[BK][BN + 4];
@@ -37,9 +38,9 @@ __global__ void __launch_bounds__(256) ess_nu_gen_kernel(EssView<T> v) {
 
   const int d = v.tg.d;
   const int tid = threadIdx.x;
-  const int r0 = blockIdx.z * BM;
-  const int w = blockIdx.y;
-  const int64_t c0 = (int64_t)blockIdx.x * BN;
+  const int r0 = bz * BM;
+  const int w = by;
+  const int64_t c0 = bx * BN;
 
   int active = 0;
   if (tid < BN) {
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(256) ess_nu_gen_kernel(EssView<T> v) {
   }
   const int n_active = __syncthreads_count(active);
   if (n_active == 0) return;
-  if (tid == 0 && blockIdx.z == 0) atomicAdd(v.gen_cols, (unsigned long long)n_active);
+  if (tid == 0 && bz == 0) atomicAdd(v.gen_cols, (unsigned long long)n_active);
 
   const int ty = tid >> 3, tx = tid & 7;
   const int warp = tid >> 5;
@@ -122,6 +123,12 @@ __global__ void __launch_bounds__(256) ess_nu_gen_kernel(EssView<T> v) {
       if (r < d) dst[r] = acc[i][j];
     }
   }
+  __syncthreads();  // the next tile reuses the shared staging
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ess_nu_gen_kernel(EssView<T> v) {
+  ess_nu_gen_tile<T>(v, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -184,13 +191,10 @@ __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, 
 // FSM kernel: every chain advances `budget` states (fewer if its ring runs dry or it
 // finishes).  Chain-group layout: G lanes own one chain, lane l holds coordinates l, l+G, ...
 template <typename T, int G, int E>
-__global__ void __launch_bounds__(256) ess_fsm_kernel(EssView<T> v, int budget) {
-  const int lane = threadIdx.x % G;
-  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+__device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c, int budget, int lane) {
   const int d = v.tg.d;
   const int D = (d + 1) / 2;
-  for (int64_t c = group; c < v.m; c += ngroups) {
+  {
     T x[E], nu[E], xp[E], yv[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -264,6 +268,52 @@ __global__ void __launch_bounds__(256) ess_fsm_kernel(EssView<T> v, int budget) 
       if (err) atomicOr(v.err, err);
     }
   }
+}
+
+template <typename T, int G, int E>
+__global__ void __launch_bounds__(256) ess_fsm_kernel(EssView<T> v, int budget) {
+  const int lane = threadIdx.x % G;
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E>(v, c, budget, lane);
+}
+
+// ---- fused launches over several jobs (serving) --------------------------------------------------
+// Job k owns the work items [off[k], off[k+1]) of the flattened range; a block or chain
+// group finds its job by binary search.
+__device__ __forceinline__ int find_job(const int64_t* off, int njobs, int64_t item) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ess_nu_gen_multi_kernel(const EssView<T>* views, const int64_t* off,
+                                                               int njobs) {
+  const int64_t item = blockIdx.x;
+  const int k = find_job(off, njobs, item);
+  const EssView<T> v = views[k];
+  const int64_t local = item - off[k];
+  const int64_t nbx = (v.m + 63) / 64;
+  const int64_t per_z = nbx * v.W;
+  const int bz = (int)(local / per_z);
+  const int by = (int)((local % per_z) / nbx);
+  const int64_t bx = local % nbx;
+  ess_nu_gen_tile<T>(v, bx, by, bz);
+}
+
+template <typename T, int G, int E>
+__global__ void __launch_bounds__(256) ess_fsm_multi_kernel(const EssView<T>* views, const int64_t* off,
+                                                            int njobs, int64_t total, int budget) {
+  const int lane = threadIdx.x % G;
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  if (item >= total) return;
+  const int k = find_job(off, njobs, item);
+  const EssView<T> v = views[k];
+  ess_advance_chain<T, G, E>(v, item - off[k], budget, lane);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -510,6 +560,37 @@ cudaError_t launch_ess_fsm(const EssView<T>& v, int G, int budget, int threads, 
   FSMC_ESS_DISPATCH(fsm_launch, v, budget, threads, st);
 }
 
+template <typename T, int G, int E>
+static cudaError_t fsm_multi_launch(const EssView<T>& v, const EssView<T>* views, const int64_t* off,
+                                    int njobs, int64_t total, int budget, int threads, cudaStream_t st) {
+  (void)v;
+  const int64_t groups_per_block = threads / G;
+  const int64_t blocks = (total + groups_per_block - 1) / groups_per_block;
+  ess_fsm_multi_kernel<T, G, E><<<(unsigned)blocks, threads, 0, st>>>(views, off, njobs, total, budget);
+  return cudaGetLastError();
+}
+
+// `v` is any job of the group (it selects G and E from its d); all jobs share them.
+template <typename T>
+cudaError_t launch_ess_fsm_multi(const EssView<T>& v, int G, const EssView<T>* views, const int64_t* off,
+                                 int njobs, int64_t total, int budget, int threads, cudaStream_t st) {
+  FSMC_ESS_DISPATCH(fsm_multi_launch, v, views, off, njobs, total, budget, threads, st);
+}
+
+template <typename T>
+cudaError_t launch_ess_nu_gen_multi(const EssView<T>* views, const int64_t* off, int njobs,
+                                    int64_t total_tiles, cudaStream_t st) {
+  if (total_tiles <= 0) return cudaSuccess;
+  ess_nu_gen_multi_kernel<T><<<(unsigned)total_tiles, 256, 0, st>>>(views, off, njobs);
+  return cudaGetLastError();
+}
+
+// shape of the group an ESS job belongs to: jobs with equal (lanes, E) share a fused launch
+int ess_group_E(int G, int d) {
+  if (G == 1) return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32;
+  return d <= 32 ? 1 : d <= 64 ? 2 : d <= 128 ? 4 : d <= 256 ? 8 : d <= 512 ? 16 : 32;
+}
+
 template <typename T>
 cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarrier bar,
                             unsigned* active_cnt, unsigned long long* iters, int threads,
@@ -517,6 +598,14 @@ cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarr
   FSMC_ESS_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
 }
 
+template cudaError_t launch_ess_fsm_multi<float>(const EssView<float>&, int, const EssView<float>*,
+                                                 const int64_t*, int, int64_t, int, int, cudaStream_t);
+template cudaError_t launch_ess_fsm_multi<double>(const EssView<double>&, int, const EssView<double>*,
+                                                  const int64_t*, int, int64_t, int, int, cudaStream_t);
+template cudaError_t launch_ess_nu_gen_multi<float>(const EssView<float>*, const int64_t*, int, int64_t,
+                                                    cudaStream_t);
+template cudaError_t launch_ess_nu_gen_multi<double>(const EssView<double>*, const int64_t*, int, int64_t,
+                                                     cudaStream_t);
 template cudaError_t launch_ess_nu_gen<float>(const EssView<float>&, cudaStream_t);
 template cudaError_t launch_ess_nu_gen<double>(const EssView<double>&, cudaStream_t);
 template cudaError_t launch_ess_fsm<float>(const EssView<float>&, int, int, int, cudaStream_t);

@@ -72,12 +72,16 @@ template <> struct Conv<float> {
   static __device__ __forceinline__ float log_u(uint32_t hi, uint32_t lo) {
     return (hi & 0x80000000u) ? log1pf(-u(~hi, ~lo)) : logf(u(hi, lo));
   }
+  // Box-Muller with the hardware approximations: the radius from __logf (absolute error
+  // ~4e-7 in log u) and the angle phi = 2 pi u written as psi + pi with psi in [-pi, pi),
+  // where __sincosf is accurate to ~5e-7 (cos phi = -cos psi, sin phi = -sin psi).
   static __device__ __forceinline__ void normal_pair(const P4& b, float& z0, float& z1) {
-    const float r = sqrtf(-2.0f * log_u(b.w0, b.w1));
+    const float r = sqrtf(fmaxf(-2.0f * __logf(u(b.w0, b.w1)), 0.f));
+    const float psi = fmaf(6.28318530717958647692f, u(b.w2, b.w3), -3.14159265358979323846f);
     float s, c;
-    sincospif(2.0f * u(b.w2, b.w3), &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(psi, &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
   }
 };
 
@@ -148,9 +152,10 @@ struct TargetView {
 
 template <typename T>
 __device__ __forceinline__ T softplus(T t) {
-  // log(1 + e^t) without overflow
+  // log(1 + e^t) without overflow.  Single precision uses the hardware exp2/log2
+  // approximations: the absolute error per term stays below ~2e-7.
   if constexpr (sizeof(T) == 4) {
-    return t > 0.f ? t + log1pf(__expf(-t)) : log1pf(__expf(t));
+    return fmaxf(t, 0.f) + __logf(1.f + __expf(-fabsf(t)));
   } else {
     return t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t));
   }

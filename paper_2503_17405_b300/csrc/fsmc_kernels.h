@@ -63,6 +63,15 @@ cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarr
                             cudaStream_t st);
 template <typename T>
 cudaError_t launch_ess_init(const EssView<T>& v, cudaStream_t st);
+// Fused launches over several ESS jobs: views[k] is job k's view in device memory and
+// off[k] .. off[k+1] its range of work items (direction tiles, or chains).
+template <typename T>
+cudaError_t launch_ess_nu_gen_multi(const EssView<T>* views, const int64_t* off, int njobs,
+                                    int64_t total_tiles, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ess_fsm_multi(const EssView<T>& any, int G, const EssView<T>* views, const int64_t* off,
+                                 int njobs, int64_t total, int budget, int threads, cudaStream_t st);
+int ess_group_E(int G, int d);
 
 template <typename T>
 cudaError_t launch_dr_fsm(const DrView<T>& v, int budget, int threads, cudaStream_t st);

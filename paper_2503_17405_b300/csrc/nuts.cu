@@ -1,14 +1,738 @@
-// NUTS as a finite state machine (filled in below the ESS / DR path).
+// The No-U-Turn sampler (multinomial form) as a finite state machine.
+//
+// States (Fig. 2, "HMC-NUTS"): INIT draws the momentum and opens the trajectory; DOUBLE
+// picks the direction of the next subtree; INTEGRATE (the inner loop body) takes one
+// leapfrog step, adds the new leaf to the subtree and merges completed blocks; CHECK (the
+// outer loop body's tail) accepts the finished subtree progressively and tests the whole
+// trajectory for a U-turn; DONE emits the sample.  One FSM step is Alg. 9's bundled step
+// inside an amortised step: the cheap states run inline until the next gradient is
+// needed, then exactly one gradient evaluation (one leapfrog) is made.  A sample costs as
+// many steps as it takes leapfrog steps.
+//
+// The subtree is built iteratively: after leaf L (0-based) of subtree j, every block of
+// 2^(l+1) leaves that L completes is merged with its left half, which waits in a per-level
+// slot; a block that U-turns, or a leaf that diverges, ends the transition.  The random
+// numbers are keyed exactly like the recursive definition (direction and progressive
+// acceptance of doubling j: tag 1, draw j; the merge at level l of block b of subtree j:
+// tag 2, draw (j << 16) | (b << 4) | l; momentum: tag 0).
+//
+// Layout: one chain per warp; lane l holds coordinates l, l + 32, ....
+#include <algorithm>
 #include "engine_internal.h"
+#include "fsmc_device.cuh"
 #include "fsmc_kernels.h"
 
-void nuts_layout(fsmc_job* j, size_t& off) { (void)j; (void)off; }
-fsmc_status nuts_init_state(fsmc_job* j, cudaStream_t st) {
-  (void)j; (void)st;
-  return fsmc_fail(FSMC_EINVAL, "NUTS kernels are not built in this library");
+namespace fsmc {
+
+enum NutsState : int { N_INIT = 0, N_DOUBLE = 1, N_INTEGRATE = 2, N_CHECK = 3, N_DONE = 4 };
+enum NutsVec : int { V_GX = 0, V_XL, V_PL, V_GL, V_XR, V_PR, V_GR, V_RHO, V_XP, V_GP, NV };
+enum NutsSc : int { S_LPX = 0, S_LPL, S_LPR, S_LPP, S_H0, S_LOGW, NSC };
+enum NutsInt : int { I_ST = 0, I_J, I_L, I_V, I_NLEAP, NI };
+constexpr int kLevels = 10;   // slots for levels 0..9
+constexpr int kWarpsMax = 8;  // warps per block (threads <= 256)
+constexpr int kWsm = 160;     // per-warp scratch: theta (<= 128) + 32 residuals
+
+template <typename T>
+struct NutsView : ChainsView<T> {
+  TargetView<T> tg;
+  T eps, max_dH;
+  int max_depth;
+  T* vec;   // [NV][m][d]
+  T* sc;    // [NSC][m]
+  int* iv;  // [NI][m]
+  T* stk;   // [m][kLevels][4][d]: p_first, rho, prop x, prop grad
+  T* stks;  // [m][kLevels][2]: prop log-density, log-weight
+  T* sub;   // [3][m][d]: completed subtree rho, prop x, prop grad (synchronised mode)
+  T* subs;  // [2][m]: its prop log-density and log-weight
+  int* aux; // [m][n] tree depth
+};
+
+template <typename T>
+__device__ __forceinline__ T t_exp(T a) { if constexpr (sizeof(T) == 4) return expf(a); else return exp(a); }
+template <typename T>
+__device__ __forceinline__ T t_log(T a) { if constexpr (sizeof(T) == 4) return logf(a); else return log(a); }
+
+template <typename T>
+__device__ __forceinline__ T logaddexp(T a, T b) {
+  if (a == neg_inf<T>()) return b;
+  if (b == neg_inf<T>()) return a;
+  const T m = a > b ? a : b;
+  return m + t_log(t_exp(a - m) + t_exp(b - m));
 }
-cudaError_t nuts_fsm_round(fsmc_job* j, cudaStream_t st) { (void)j; (void)st; return cudaErrorNotSupported; }
+
+template <typename T, int E>
+__device__ __forceinline__ T wdot(const T (&a)[E], const T (&b)[E]) {
+  T s = T(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) s = fma(a[e], b[e], s);  // padded coordinates hold 0
+  return group_sum<32>(s);
+}
+
+// log pi(x) and its gradient, one chain per warp.  wsm: this warp's shared scratch.
+template <typename T, int E>
+__device__ T logp_grad(const TargetView<T>& tg, const T (&x)[E], T (&g)[E], int lane, T* wsm) {
+  const int d = tg.d;
+  if (tg.kind == TGT_GAUSS_DIAG) {
+    T acc = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      if (k < d) {
+        const T z = (x[e] - tg.vec[k]) / tg.vec2[k];
+        acc = fma(z, z, acc);
+        g[e] = -z / tg.vec2[k];
+      } else {
+        g[e] = T(0);
+      }
+    }
+    return -T(0.5) * group_sum<32>(acc);
+  }
+  if (tg.kind == TGT_FUNNEL) {
+    const T v = __shfl_sync(0xffffffffu, x[0], 0);
+    T ss = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      if (k >= 1 && k < d) ss = fma(x[e], x[e], ss);
+    }
+    ss = group_sum<32>(ss);
+    const T ev = t_exp(-v);
+    const T m1 = T(d - 1);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      g[e] = (k >= 1 && k < d) ? -ev * x[e] : T(0);
+    }
+    if (lane == 0) g[0] = -v / T(9) - m1 / T(2) + T(0.5) * ev * ss;
+    return -v * v / T(18) - m1 * v / T(2) - T(0.5) * ev * ss;
+  }
+  // TGT_LOGREG: eta = X theta row by row (lanes over rows), then grad = X^T r (lanes over
+  // coordinates), 32 rows at a time through the warp's shared scratch.
+  const int n = tg.n_data;
+  T* th = wsm;
+  T* rs = wsm + 128;
+  T sq = T(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = lane + 32 * e;
+    if (k < d) { th[k] = x[e]; sq = fma(x[e], x[e], sq); }
+    g[e] = T(0);
+  }
+  __syncwarp();
+  T lpart = T(0);
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    T r = T(0);
+    if (i < n) {
+      const T* row = tg.X + (size_t)i * d;
+      T eta = T(0);
+      for (int k = 0; k < d; ++k) eta = fma(row[k], th[k], eta);
+      const T yi = tg.vec[i];
+      const T sig = T(1) / (T(1) + t_exp(-eta));
+      r = yi - sig;
+      lpart += yi * eta - softplus<T>(eta);
+    }
+    rs[lane] = r;
+    __syncwarp();
+    const int q_end = min(32, n - i0);
+    for (int q = 0; q < q_end; ++q) {
+      const T rq = rs[q];
+      const T* row = tg.X + (size_t)(i0 + q) * d;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = lane + 32 * e;
+        if (k < d) g[e] = fma(row[k], rq, g[e]);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = lane + 32 * e;
+    if (k < d) g[e] -= x[e];
+  }
+  return group_sum<32>(lpart) - T(0.5) * group_sum<32>(sq);
+}
+
+// ---- per-chain register state ---------------------------------------------------------------------
+template <typename T, int E>
+struct Chain {
+  T x[E], gx[E], xl[E], pl[E], gl[E], xr[E], pr[E], gr[E], rho[E], xp[E], gp[E];
+  T lpx, lpl, lpr, lpp, H0, logW;
+  int st, j, L, v, nleap, t;
+};
+
+template <typename T, int E>
+__device__ __forceinline__ void vload(const NutsView<T>& v, const T* base, int64_t c, int lane, T (&a)[E]) {
+  const int d = v.tg.d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = lane + 32 * e;
+    a[e] = k < d ? base[(size_t)c * d + k] : T(0);
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void vstore(const NutsView<T>& v, T* base, int64_t c, int lane, const T (&a)[E]) {
+  const int d = v.tg.d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = lane + 32 * e;
+    if (k < d) base[(size_t)c * d + k] = a[e];
+  }
+}
+
+template <typename T, int E>
+__device__ void chain_load(const NutsView<T>& v, int64_t c, int lane, Chain<T, E>& s) {
+  const size_t md = (size_t)v.m * v.tg.d;
+  vload<T, E>(v, v.x, c, lane, s.x);
+  vload<T, E>(v, v.vec + V_GX * md, c, lane, s.gx);
+  vload<T, E>(v, v.vec + V_XL * md, c, lane, s.xl);
+  vload<T, E>(v, v.vec + V_PL * md, c, lane, s.pl);
+  vload<T, E>(v, v.vec + V_GL * md, c, lane, s.gl);
+  vload<T, E>(v, v.vec + V_XR * md, c, lane, s.xr);
+  vload<T, E>(v, v.vec + V_PR * md, c, lane, s.pr);
+  vload<T, E>(v, v.vec + V_GR * md, c, lane, s.gr);
+  vload<T, E>(v, v.vec + V_RHO * md, c, lane, s.rho);
+  vload<T, E>(v, v.vec + V_XP * md, c, lane, s.xp);
+  vload<T, E>(v, v.vec + V_GP * md, c, lane, s.gp);
+  const int64_t m = v.m;
+  s.lpx = v.sc[S_LPX * m + c]; s.lpl = v.sc[S_LPL * m + c]; s.lpr = v.sc[S_LPR * m + c];
+  s.lpp = v.sc[S_LPP * m + c]; s.H0 = v.sc[S_H0 * m + c]; s.logW = v.sc[S_LOGW * m + c];
+  s.st = v.iv[I_ST * m + c]; s.j = v.iv[I_J * m + c]; s.L = v.iv[I_L * m + c];
+  s.v = v.iv[I_V * m + c]; s.nleap = v.iv[I_NLEAP * m + c];
+  s.t = v.t[c];
+}
+
+template <typename T, int E>
+__device__ void chain_store(const NutsView<T>& v, int64_t c, int lane, const Chain<T, E>& s) {
+  const size_t md = (size_t)v.m * v.tg.d;
+  vstore<T, E>(v, v.x, c, lane, s.x);
+  vstore<T, E>(v, v.vec + V_GX * md, c, lane, s.gx);
+  vstore<T, E>(v, v.vec + V_XL * md, c, lane, s.xl);
+  vstore<T, E>(v, v.vec + V_PL * md, c, lane, s.pl);
+  vstore<T, E>(v, v.vec + V_GL * md, c, lane, s.gl);
+  vstore<T, E>(v, v.vec + V_XR * md, c, lane, s.xr);
+  vstore<T, E>(v, v.vec + V_PR * md, c, lane, s.pr);
+  vstore<T, E>(v, v.vec + V_GR * md, c, lane, s.gr);
+  vstore<T, E>(v, v.vec + V_RHO * md, c, lane, s.rho);
+  vstore<T, E>(v, v.vec + V_XP * md, c, lane, s.xp);
+  vstore<T, E>(v, v.vec + V_GP * md, c, lane, s.gp);
+  if (lane == 0) {
+    const int64_t m = v.m;
+    v.sc[S_LPX * m + c] = s.lpx; v.sc[S_LPL * m + c] = s.lpl; v.sc[S_LPR * m + c] = s.lpr;
+    v.sc[S_LPP * m + c] = s.lpp; v.sc[S_H0 * m + c] = s.H0; v.sc[S_LOGW * m + c] = s.logW;
+    v.iv[I_ST * m + c] = s.st; v.iv[I_J * m + c] = s.j; v.iv[I_L * m + c] = s.L;
+    v.iv[I_V * m + c] = s.v; v.iv[I_NLEAP * m + c] = s.nleap;
+    v.t[c] = s.t;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T* stk_vec(const NutsView<T>& v, int64_t c, int lvl, int f) {
+  return v.stk + (((size_t)c * kLevels + lvl) * 4 + f) * v.tg.d;
+}
+
+// INIT (S1): momentum, H0, a one-point trajectory.
+template <typename T, int E>
+__device__ void nuts_init(const NutsView<T>& v, const Key& key, int lane, Chain<T, E>& s) {
+  const int d = v.tg.d;
+  T p[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = lane + 32 * e;
+    p[e] = T(0);
+    if (k < d) {
+      T z0, z1;
+      Conv<T>::normal_pair(key.block((uint32_t)s.t, 0, (uint32_t)(k >> 1)), z0, z1);
+      p[e] = (k & 1) ? z1 : z0;
+    }
+  }
+  s.H0 = -s.lpx + T(0.5) * wdot<T, E>(p, p);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    s.xl[e] = s.xr[e] = s.xp[e] = s.x[e];
+    s.gl[e] = s.gr[e] = s.gp[e] = s.gx[e];
+    s.pl[e] = s.pr[e] = s.rho[e] = p[e];
+  }
+  s.lpl = s.lpr = s.lpp = s.lpx;
+  s.logW = -s.H0;
+  s.j = 0;
+  s.nleap = 0;
+  s.st = N_DOUBLE;
+}
+
+// DOUBLE (S2): direction of subtree j.
+template <typename T, int E>
+__device__ __forceinline__ void nuts_double(const Key& key, Chain<T, E>& s) {
+  const P4 b = key.block((uint32_t)s.t, 1, (uint32_t)s.j);
+  s.v = (b.w0 & 0x80000000u) ? 1 : -1;  // u(w0, w1) < 1/2 exactly when the top bit is clear
+  s.L = 0;
+  s.st = N_INTEGRATE;
+}
+
+// Completed subtree summary handed from INTEGRATE to CHECK.
+template <typename T, int E>
+struct Sub {
+  T rho[E], xp[E], gp[E];
+  T lpp, logW;
+};
+
+// INTEGRATE (S3): one leapfrog from the edge on side v, then the merges this leaf completes.
+// Returns 0: keep integrating; 1: subtree complete (summary in `out`); 2: subtree invalid.
+template <typename T, int E>
+__device__ int nuts_integrate(const NutsView<T>& v, const Key& key, int64_t c, int lane, T* wsm,
+                              Chain<T, E>& s, Sub<T, E>& out) {
+  const int d = v.tg.d;
+  T xe[E], pe[E], ge[E];
+  const bool left = s.v < 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    xe[e] = left ? s.xl[e] : s.xr[e];
+    pe[e] = left ? s.pl[e] : s.pr[e];
+    ge[e] = left ? s.gl[e] : s.gr[e];
+  }
+  const T es = s.v < 0 ? -v.eps : v.eps;
+  const T half = T(0.5) * es;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    pe[e] += half * ge[e];
+    xe[e] += es * pe[e];
+  }
+  T lpe = logp_grad<T, E>(v.tg, xe, ge, lane, wsm);
+#pragma unroll
+  for (int e = 0; e < E; ++e) pe[e] += half * ge[e];
+  s.nleap += 1;
+  if (!(lpe == lpe)) { lpe = neg_inf<T>(); atomicOr(v.err, ERR_NONFINITE); }
+  // the new leaf becomes the trajectory's edge on side v
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (left) { s.xl[e] = xe[e]; s.pl[e] = pe[e]; s.gl[e] = ge[e]; }
+    else { s.xr[e] = xe[e]; s.pr[e] = pe[e]; s.gr[e] = ge[e]; }
+  }
+  if (left) s.lpl = lpe; else s.lpr = lpe;
+  const T H = -lpe + T(0.5) * wdot<T, E>(pe, pe);
+  bool valid = (H - s.H0 <= v.max_dH);
+  if (!valid) return 2;
+  // leaf summary
+  T cpf[E], crho[E], cxp[E], cgp[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) { cpf[e] = pe[e]; crho[e] = pe[e]; cxp[e] = xe[e]; cgp[e] = ge[e]; }
+  T clpp = lpe, clogW = -H;
+  int lvl = 0;
+  while (((s.L >> lvl) & 1) != 0) {
+    // merge with the waiting left half of level lvl
+    T spf[E], srho[E];
+    const T* sp = stk_vec(v, c, lvl, 0);
+    const T* sr = stk_vec(v, c, lvl, 1);
+    const T slpp = v.stks[((size_t)c * kLevels + lvl) * 2];
+    const T slogW = v.stks[((size_t)c * kLevels + lvl) * 2 + 1];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      spf[e] = k < d ? sp[k] : T(0);
+      srho[e] = k < d ? sr[k] : T(0);
+    }
+    const T nlogW = logaddexp(slogW, clogW);
+    const uint32_t blk = (uint32_t)(s.L >> (lvl + 1));
+    const uint32_t draw = ((uint32_t)s.j << 16) | (blk << 4) | (uint32_t)(lvl + 1);
+    const P4 b = key.block((uint32_t)s.t, 2, draw);
+    if (!(Conv<T>::log_u(b.w0, b.w1) < clogW - nlogW)) {  // keep the left half's proposal
+      const T* sx = stk_vec(v, c, lvl, 2);
+      const T* sg = stk_vec(v, c, lvl, 3);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = lane + 32 * e;
+        cxp[e] = k < d ? sx[k] : T(0);
+        cgp[e] = k < d ? sg[k] : T(0);
+      }
+      clpp = slpp;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) { crho[e] = srho[e] + crho[e]; cpf[e] = spf[e]; }
+    clogW = nlogW;
+    ++lvl;
+    valid = wdot<T, E>(crho, cpf) > T(0) && wdot<T, E>(crho, pe) > T(0);
+    if (!valid) return 2;
+  }
+  if (s.L == (1 << s.j) - 1) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) { out.rho[e] = crho[e]; out.xp[e] = cxp[e]; out.gp[e] = cgp[e]; }
+    out.lpp = clpp;
+    out.logW = clogW;
+    return 1;
+  }
+  // this block waits as the left half of level lvl
+  T* dp = stk_vec(v, c, lvl, 0);
+  T* dr = stk_vec(v, c, lvl, 1);
+  T* dx = stk_vec(v, c, lvl, 2);
+  T* dg = stk_vec(v, c, lvl, 3);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = lane + 32 * e;
+    if (k < d) { dp[k] = cpf[e]; dr[k] = crho[e]; dx[k] = cxp[e]; dg[k] = cgp[e]; }
+  }
+  if (lane == 0) {
+    v.stks[((size_t)c * kLevels + lvl) * 2] = clpp;
+    v.stks[((size_t)c * kLevels + lvl) * 2 + 1] = clogW;
+  }
+  __syncwarp();
+  s.L += 1;
+  return 0;
+}
+
+// CHECK (S4): progressive acceptance of the finished subtree and the trajectory U-turn test.
+// Returns true when the transition continues with another doubling.
+template <typename T, int E>
+__device__ bool nuts_check(const NutsView<T>& v, const Key& key, Chain<T, E>& s, const Sub<T, E>& sb) {
+  const P4 b = key.block((uint32_t)s.t, 1, (uint32_t)s.j);
+  if (Conv<T>::log_u(b.w2, b.w3) < sb.logW - s.logW) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) { s.xp[e] = sb.xp[e]; s.gp[e] = sb.gp[e]; }
+    s.lpp = sb.lpp;
+  }
+  s.logW = logaddexp(s.logW, sb.logW);
+#pragma unroll
+  for (int e = 0; e < E; ++e) s.rho[e] += sb.rho[e];
+  const bool turn = !(wdot<T, E>(s.rho, s.pl) > T(0) && wdot<T, E>(s.rho, s.pr) > T(0));
+  if (turn || s.j + 1 >= v.max_depth) return false;
+  s.j += 1;
+  s.st = N_DOUBLE;
+  return true;
+}
+
+// DONE (S5): the proposal becomes the sample.
+template <typename T, int E>
+__device__ void nuts_done(const NutsView<T>& v, int64_t c, int lane, Chain<T, E>& s) {
+  const int d = v.tg.d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) { s.x[e] = s.xp[e]; s.gx[e] = s.gp[e]; }
+  s.lpx = s.lpp;
+  if (v.out) {
+    T* dst = v.out + ((size_t)c * v.n + s.t) * d;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      if (k < d) dst[k] = s.x[e];
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      if (k >= d) continue;
+      const size_t o = (size_t)c * d + k;
+      const size_t st = v.mom_stride;
+      T* mo = v.mom;
+      T y = s.x[e] - mo[o + st]; T tt = mo[o] + y; mo[o + st] = (tt - mo[o]) - y; mo[o] = tt;
+      const T x2 = s.x[e] * s.x[e];
+      y = x2 - mo[o + 3 * st]; tt = mo[o + 2 * st] + y; mo[o + 3 * st] = (tt - mo[o + 2 * st]) - y;
+      mo[o + 2 * st] = tt;
+    }
+  }
+  if (lane == 0) {
+    v.counts[(size_t)c * v.n + s.t] = s.nleap;
+    v.aux[(size_t)c * v.n + s.t] = s.j + 1;
+  }
+  s.t += 1;
+  s.st = N_INIT;
+  if (s.t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
+}
+
+// ---- FSM kernel: each chain advances `budget` leapfrog steps ---------------------------------------
+template <typename T, int E>
+__global__ void __launch_bounds__(256) nuts_fsm_kernel(NutsView<T> v, int budget) {
+  __shared__ T wsm_all[kWarpsMax][kWsm];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  T* wsm = wsm_all[wib];
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < v.m; c += nwarps) {
+    Chain<T, E> s;
+    chain_load<T, E>(v, c, lane, s);
+    if (s.t >= v.n) continue;
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    long long steps = 0;
+    for (int b = 0; b < budget && s.t < v.n; ++b) {
+      if (s.st == N_INIT) nuts_init<T, E>(v, key, lane, s);
+      if (s.st == N_DOUBLE) nuts_double<T, E>(key, s);
+      Sub<T, E> sb;
+      const int r = nuts_integrate<T, E>(v, key, c, lane, wsm, s, sb);
+      ++steps;
+      if (r == 1 && nuts_check<T, E>(v, key, s, sb)) continue;
+      if (r != 0) nuts_done<T, E>(v, c, lane, s);
+    }
+    chain_store<T, E>(v, c, lane, s);
+    if (lane == 0) v.steps[c] += steps;
+  }
+}
+
+// ---- synchronised kernel (Alg. 6 with nested loops) --------------------------------------------------
+// Per sample: INIT and DOUBLE for all chains; then the inner loop -- one leapfrog for every
+// chain still building its subtree, grid barrier, until no chain is building -- then CHECK
+// for all chains whose subtree completed; repeat while any chain doubles again; then DONE.
+template <typename T, int E>
+__device__ void sub_store(const NutsView<T>& v, int64_t c, int lane, const Sub<T, E>& sb) {
+  const size_t md = (size_t)v.m * v.tg.d;
+  vstore<T, E>(v, v.sub, c, lane, sb.rho);
+  vstore<T, E>(v, v.sub + md, c, lane, sb.xp);
+  vstore<T, E>(v, v.sub + 2 * md, c, lane, sb.gp);
+  if (lane == 0) { v.subs[c] = sb.lpp; v.subs[v.m + c] = sb.logW; }
+}
+
+template <typename T, int E>
+__device__ void sub_load(const NutsView<T>& v, int64_t c, int lane, Sub<T, E>& sb) {
+  const size_t md = (size_t)v.m * v.tg.d;
+  vload<T, E>(v, v.sub, c, lane, sb.rho);
+  vload<T, E>(v, v.sub + md, c, lane, sb.xp);
+  vload<T, E>(v, v.sub + 2 * md, c, lane, sb.gp);
+  sb.lpp = v.subs[c];
+  sb.logW = v.subs[v.m + c];
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256) nuts_sync_kernel(NutsView<T> v, int t_begin, int t_end,
+                                                        GridBarrier bar, unsigned* active_cnt,
+                                                        unsigned long long* iterations) {
+  __shared__ T wsm_all[kWarpsMax][kWsm];
+  __shared__ unsigned blk_active;
+  const int lane = threadIdx.x & 31;
+  T* wsm = wsm_all[threadIdx.x >> 5];
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  int iter = 0;
+  // one grid-wide count of chains in state `want`; false on barrier timeout
+  auto count_state = [&](int want, unsigned& total) -> bool {
+    if (threadIdx.x == 0) blk_active = 0;
+    __syncthreads();
+    unsigned mine = 0;
+    for (int64_t c = warp0; c < v.m; c += nwarps)
+      if (v.iv[I_ST * v.m + c] == want) ++mine;
+    if (lane == 0 && mine) atomicAdd(&blk_active, mine);
+    __syncthreads();
+    const int slot = iter % 3;
+    if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+    if (!grid_sync(bar, v.err)) return false;
+    total = *(volatile unsigned*)&active_cnt[slot];
+    if (leader) active_cnt[(iter + 2) % 3] = 0;
+    ++iter;
+    return true;
+  };
+  for (int t = t_begin; t < t_end; ++t) {
+    for (int64_t c = warp0; c < v.m; c += nwarps) {
+      Chain<T, E> s;
+      chain_load<T, E>(v, c, lane, s);
+      const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+      nuts_init<T, E>(v, key, lane, s);
+      nuts_double<T, E>(key, s);
+      chain_store<T, E>(v, c, lane, s);
+    }
+    while (true) {  // outer loop: doublings
+      while (true) {  // inner loop: leapfrog steps of the current subtrees
+        for (int64_t c = warp0; c < v.m; c += nwarps) {
+          if (v.iv[I_ST * v.m + c] != N_INTEGRATE) continue;
+          Chain<T, E> s;
+          chain_load<T, E>(v, c, lane, s);
+          const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+          Sub<T, E> sb;
+          const int r = nuts_integrate<T, E>(v, key, c, lane, wsm, s, sb);
+          if (r == 1) { sub_store<T, E>(v, c, lane, sb); s.st = N_CHECK; }
+          if (r == 2) s.st = N_DONE;
+          chain_store<T, E>(v, c, lane, s);
+          if (lane == 0) v.steps[c] += 1;
+        }
+        unsigned building = 0;
+        if (!count_state(N_INTEGRATE, building)) return;
+        if (leader) *iterations += 1;
+        if (building == 0) break;
+      }
+      for (int64_t c = warp0; c < v.m; c += nwarps) {
+        if (v.iv[I_ST * v.m + c] != N_CHECK) continue;
+        Chain<T, E> s;
+        chain_load<T, E>(v, c, lane, s);
+        const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+        Sub<T, E> sb;
+        sub_load<T, E>(v, c, lane, sb);
+        if (nuts_check<T, E>(v, key, s, sb)) nuts_double<T, E>(key, s);
+        else s.st = N_DONE;
+        chain_store<T, E>(v, c, lane, s);
+      }
+      unsigned doubling = 0;
+      if (!count_state(N_INTEGRATE, doubling)) return;
+      if (doubling == 0) break;
+    }
+    for (int64_t c = warp0; c < v.m; c += nwarps) {
+      Chain<T, E> s;
+      chain_load<T, E>(v, c, lane, s);
+      nuts_done<T, E>(v, c, lane, s);
+      chain_store<T, E>(v, c, lane, s);
+    }
+  }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256) nuts_init_kernel(NutsView<T> v) {
+  __shared__ T wsm_all[kWarpsMax][kWsm];
+  const int lane = threadIdx.x & 31;
+  T* wsm = wsm_all[threadIdx.x >> 5];
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const size_t md = (size_t)v.m * v.tg.d;
+  for (int64_t c = warp; c < v.m; c += nwarps) {
+    T x[E], g[E];
+    vload<T, E>(v, v.x, c, lane, x);
+    T lp = logp_grad<T, E>(v.tg, x, g, lane, wsm);
+    if (!(lp == lp)) { lp = neg_inf<T>(); if (lane == 0) atomicOr(v.err, ERR_NONFINITE); }
+    vstore<T, E>(v, v.vec + V_GX * md, c, lane, g);
+    if (lane == 0) v.sc[S_LPX * v.m + c] = lp;
+  }
+}
+
+// ---- host side --------------------------------------------------------------------------------------------
+template <typename T>
+static NutsView<T> nuts_view(const fsmc_job* j) {
+  NutsView<T> v{};
+  char* b = j->dev;
+  v.m = j->m;
+  v.n = (int)j->n;
+  v.chain0 = j->chain0;
+  v.seed_lo = (uint32_t)j->seed;
+  v.seed_hi = (uint32_t)(j->seed >> 32);
+  v.x = (T*)(b + j->o_x);
+  v.t = (int*)(b + j->o_t);
+  v.out = j->store ? (T*)(b + j->o_out) : nullptr;
+  v.mom = j->store ? nullptr : (T*)(b + j->o_mom);
+  v.mom_stride = (size_t)j->m * j->d;
+  v.counts = (int*)(b + j->o_counts);
+  v.steps = (long long*)(b + j->o_steps);
+  v.err = (int*)(b + j->o_err);
+  v.chains_done = (int*)(b + j->o_done);
+  if constexpr (sizeof(T) == 8) v.tg = j->tg->tv64; else v.tg = j->tg->tv32;
+  v.eps = (T)j->nuts.eps;
+  v.max_dH = (T)j->nuts.max_dH;
+  v.max_depth = j->nuts.max_depth;
+  const size_t es = sizeof(T);
+  const size_t m = (size_t)j->m, d = (size_t)j->d;
+  size_t o = j->o_nuts;
+  auto take = [&](size_t bytes) { size_t r = o; o = (o + bytes + 255) / 256 * 256; return r; };
+  v.vec = (T*)(b + take(NV * m * d * es));
+  v.sc = (T*)(b + take(NSC * m * es));
+  v.iv = (int*)(b + take(NI * m * 4));
+  v.stk = (T*)(b + take(m * kLevels * 4 * d * es));
+  v.stks = (T*)(b + take(m * kLevels * 2 * es));
+  v.sub = (T*)(b + take(3 * m * d * es));
+  v.subs = (T*)(b + take(2 * m * es));
+  v.aux = (int*)(b + j->o_aux);
+  return v;
+}
+
+}  // namespace fsmc
+
+using namespace fsmc;
+
+void nuts_layout(fsmc_job* j, size_t& off) {
+  const size_t es = j->prec == FSMC_FP64 ? 8 : 4;
+  const size_t m = (size_t)j->m, d = (size_t)j->d;
+  auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) / 256 * 256; return r; };
+  j->o_aux = take(m * (size_t)j->n * 4);
+  j->o_nuts = off;
+  take(NV * m * d * es);
+  take(NSC * m * es);
+  take(NI * m * 4);
+  take(m * kLevels * 4 * d * es);
+  take(m * kLevels * 2 * es);
+  take(3 * m * d * es);
+  take(2 * m * es);
+  j->o_nuts_end = off;
+}
+
+#define FSMC_NUTS_DISPATCH(FN, ...)                   \
+  do {                                                \
+    const int d = j->d;                               \
+    if (d <= 32) return FN<T, 1>(__VA_ARGS__);        \
+    if (d <= 64) return FN<T, 2>(__VA_ARGS__);        \
+    if (d <= 128) return FN<T, 4>(__VA_ARGS__);       \
+    return cudaErrorInvalidValue;                     \
+  } while (0)
+
+template <typename T, int E>
+static cudaError_t nuts_init_launch(fsmc_job* j, cudaStream_t st) {
+  const NutsView<T> v = nuts_view<T>(j);
+  const int threads = 128;
+  const int64_t blocks = (j->m * 32 + threads - 1) / threads;
+  nuts_init_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
+static cudaError_t nuts_fsm_launch(fsmc_job* j, cudaStream_t st) {
+  const NutsView<T> v = nuts_view<T>(j);
+  const int threads = j->tun.threads_per_block;
+  const int64_t blocks = (j->m * 32 + threads - 1) / threads;
+  nuts_fsm_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, j->tun.steps_per_launch);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
+static cudaError_t nuts_sync_launch(fsmc_job* j, int t0, int t1, GridBarrier bar, unsigned* active,
+                                    unsigned long long* iters, cudaStream_t st) {
+  NutsView<T> v = nuts_view<T>(j);
+  auto kern = nuts_sync_kernel<T, E>;
+  const int threads = j->tun.threads_per_block;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = std::min<int64_t>((int64_t)per_sm * j->e->sms, (j->m * 32 + threads - 1) / threads);
+  if (blocks < 1) blocks = 1;
+  void* args[] = {(void*)&v, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active, (void*)&iters};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+}
+
+template <typename T>
+static cudaError_t nuts_init_t(fsmc_job* j, cudaStream_t st) { FSMC_NUTS_DISPATCH(nuts_init_launch, j, st); }
+template <typename T>
+static cudaError_t nuts_fsm_t(fsmc_job* j, cudaStream_t st) { FSMC_NUTS_DISPATCH(nuts_fsm_launch, j, st); }
+template <typename T>
+static cudaError_t nuts_sync_t(fsmc_job* j, int t0, int t1, GridBarrier bar, unsigned* active,
+                               unsigned long long* iters, cudaStream_t st) {
+  FSMC_NUTS_DISPATCH(nuts_sync_launch, j, t0, t1, bar, active, iters, st);
+}
+
+fsmc_status nuts_init_state(fsmc_job* j, cudaStream_t st) {
+  if (j->d > 128) return fsmc_fail(FSMC_EINVAL, "NUTS supports d <= 128");
+  char* b = j->dev;
+  const size_t es = j->prec == FSMC_FP64 ? 8 : 4;
+  const size_t m = (size_t)j->m, d = (size_t)j->d;
+  (void)es; (void)d;
+  // the NUTS state block starts zeroed (state INIT = 0)
+  cudaError_t e = cudaMemsetAsync(b + j->o_nuts, 0, j->o_nuts_end - j->o_nuts, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b + j->o_aux, 0, m * (size_t)j->n * 4, st);
+  if (e == cudaSuccess) e = j->prec == FSMC_FP64 ? nuts_init_t<double>(j, st) : nuts_init_t<float>(j, st);
+  if (e != cudaSuccess) return fsmc_cuda_fail(e, "NUTS init");
+  return FSMC_OK;
+}
+
+cudaError_t nuts_fsm_round(fsmc_job* j, cudaStream_t st) {
+  return j->prec == FSMC_FP64 ? nuts_fsm_t<double>(j, st) : nuts_fsm_t<float>(j, st);
+}
+
 fsmc_status nuts_run_sync(fsmc_job* j, cudaStream_t st) {
-  (void)j; (void)st;
-  return fsmc_fail(FSMC_EINVAL, "NUTS kernels are not built in this library");
+  char* b = j->dev;
+  GridBarrier bar{(unsigned*)(b + j->o_bar), (unsigned*)(b + j->o_bar) + 1};
+  unsigned* active = (unsigned*)(b + j->o_bar) + 4;
+  unsigned long long* iters = (unsigned long long*)(b + j->o_iters);
+  const int chunk = 100;
+  for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
+    const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
+    cudaError_t e = cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+      ProfScope p(j, 2, st);
+      e = j->prec == FSMC_FP64 ? nuts_sync_t<double>(j, (int)t0, t1, bar, active, iters, st)
+                               : nuts_sync_t<float>(j, (int)t0, t1, bar, active, iters, st);
+    }
+    if (e != cudaSuccess) return fsmc_cuda_fail(e, "NUTS synchronised launch");
+    j->launches += 1;
+  }
+  return FSMC_OK;
 }

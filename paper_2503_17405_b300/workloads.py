@@ -57,7 +57,7 @@ def gp_logit(d=256, seed=DATA_SEED, lengthscale=0.1, jitter=1e-6):
 
 
 def funnel(d=10):
-    return dict(kind="funnel", d=d, n_data=0, params=np.zeros(1))
+    return dict(kind="funnel", d=d, n_data=0, params=np.zeros(0))
 
 
 def logreg(n=1000, d=25, seed=DATA_SEED):
