@@ -44,8 +44,18 @@ def _peaks():
 
 
 # ---- workloads ------------------------------------------------------------------------------
-def make_config(name, scale=1.0):
-    """Returns (spec dict) for a named configuration."""
+def make_config(name, scale=1.0, samples=None):
+    """Returns (spec dict) for a named configuration (scale/samples shrink it for profiling)."""
+    cfg = _make_config(name, scale)
+    if samples:
+        cfg["n"] = samples
+        cfg["name"] += f"_n{samples}"
+    if scale != 1.0:
+        cfg["name"] += f"_scale{scale:g}"
+    return cfg
+
+
+def _make_config(name, scale):
     if name == "ess_gp":
         w = W.gp_logit(256)
         m, n = int(16384 * scale), 2000
@@ -149,7 +159,7 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
-    cfg = make_config(args.config)
+    cfg = make_config(args.config, args.scale, args.samples)
     w, m, n = cfg["w"], cfg["m"], cfg["n"]
     eng = fsmc.Engine(dev)
     tg = eng.target(w["kind"], w["d"], w["params"], n_data=w["n_data"])
@@ -288,7 +298,7 @@ def run_ours(args, rank, world):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    cfg = make_config(args.config)
+    cfg = make_config(args.config, args.scale, args.samples)
     times, vals = [], []
     cpu = None
     for _ in range(args.warmup + args.steps):
@@ -307,6 +317,79 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---- serving stream (C5) ------------------------------------------------------------------------------
+def run_serving(args):
+    """Poisson-arriving mixed jobs through fsmc_submit; FSM co-scheduled vs the synchronised
+    kernel one job at a time.  Latency = completion - submit, as the library records it."""
+    import torch
+    from paper_2503_17405_b300 import fsmc
+
+    torch.cuda.set_device(0)
+    base = W.serving_jobs(args.serve_jobs, rate_hz=1.0, scale=args.serve_scale)
+    cache = {}
+
+    def target(eng, j):
+        key = (j["kind"], j["d"], j["n_data"], j["data_seed"])
+        if key not in cache:
+            if j["kind"] == "ess_gp":
+                cache[key] = W.gp_logit(j["d"], seed=j["data_seed"])
+            else:
+                cache[key] = W.logreg(j["n_data"], j["d"], seed=j["data_seed"])
+        w = cache[key]
+        return w, eng.target(w["kind"], w["d"], w["params"], n_data=w["n_data"])
+
+    def one_pass(mode, rate_hz):
+        eng = fsmc.Engine(0)
+        jobs = [dict(j) for j in base]
+        t = 0.0
+        rng = np.random.default_rng(7)
+        for j in jobs:
+            if rate_hz:
+                t += rng.exponential(1.0 / rate_hz)
+            j["arrival"] = t
+        live, lat, samples = [], [], 0
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(jobs) or live:
+            now = time.perf_counter() - t0
+            while k < len(jobs) and jobs[k]["arrival"] <= now:
+                j = jobs[k]
+                w, tg = target(eng, j)
+                x0 = W.x0_zeros(j["chains"], j["d"]) if j["kind"] == "ess_gp" else W.x0_logreg(w, j["chains"])
+                job = eng.job(tg, "ess" if j["kind"] == "ess_gp" else "nuts", j["chains"], j["draws"],
+                              x0=x0, seed=1 + k, prec="fp32", store=False,
+                              nuts={"eps": 0.05, "max_depth": 10, "max_dH": 1000.0})
+                job.submit(mode)
+                live.append(job)
+                samples += j["chains"] * j["draws"]
+                k += 1
+            for job in list(live):
+                done, latency = job.poll()
+                if done:
+                    job.moments()
+                    lat.append(latency)
+                    job.close()
+                    live.remove(job)
+            time.sleep(0.0005)
+        makespan = time.perf_counter() - t0
+        eng.close()
+        return {"makespan_s": makespan, "samples_per_s": samples / makespan,
+                "p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)), "jobs": len(lat)}
+
+    cap = one_pass("fsm", 0.0)                 # all jobs at t = 0: capacity
+    rate = 0.8 * cap["jobs"] / cap["makespan_s"]
+    fsm = one_pass("fsm", rate)
+    sync = one_pass("sync", rate) if not args.no_sync else None
+    return {"metric": METRIC, "value": fsm["samples_per_s"], "unit": "samples/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving_{args.serve_jobs}_jobs_scale{args.serve_scale:g}",
+                       "arrivals": "Poisson", "offered_load": "0.8 x measured FSM capacity",
+                       "rate_jobs_per_s": rate},
+            "p50_latency_s": fsm["p50_latency_s"], "p99_latency_s": fsm["p99_latency_s"],
+            "fsm": fsm, "sync_one_at_a_time": sync, "capacity_pass": cap}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,7 +401,14 @@ def main():
     ap.add_argument("--no-sync", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0, help="chains x scale (profiling only)")
+    ap.add_argument("--samples", type=int, default=None, help="samples per chain (profiling only)")
+    ap.add_argument("--serve-jobs", type=int, default=40)
+    ap.add_argument("--serve-scale", type=float, default=0.25)
     args = ap.parse_args()
+    if args.config == "serving":
+        print(json.dumps(run_serving(args)))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.impl == "reference" else 1))
     if args.impl == "reference":

@@ -84,6 +84,7 @@ bool engine_reserve(fsmc_engine* e, size_t bytes) {
 void engine_release(fsmc_engine* e, size_t bytes) {
   std::lock_guard<std::mutex> g(e->mu);
   e->in_use -= std::min(bytes, e->in_use);
+  e->cv.notify_all();  // queued serving jobs may fit now
 }
 
 // ---- per-launch profiling -------------------------------------------------------------------------
@@ -552,11 +553,38 @@ static fsmc_status read_done(fsmc_job* j, cudaStream_t st, int* done_chains, int
   return FSMC_OK;
 }
 
+// Captures `rounds` FSM rounds on `st` into an executable graph (views are fixed for the
+// life of the job, so the graph stays valid across runs and resets).
+template <typename T>
+static fsmc_status capture_rounds(fsmc_job* j, int rounds, cudaStream_t st) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  const int64_t launches0 = j->launches;
+  for (int b = 0; b < rounds && e == cudaSuccess; ++b) e = fsm_round<T>(j, st);
+  j->launches = launches0;
+  cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fsmc_cuda_fail(e, "FSM launch (capture)"); }
+  if (e2 != cudaSuccess) return fsmc_cuda_fail(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&j->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { j->graph_exec = nullptr; return fsmc_cuda_fail(e, "cudaGraphInstantiate"); }
+  j->graph_rounds = rounds;
+  return FSMC_OK;
+}
+
 template <typename T>
 static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
   const int check_every = 8;
   int64_t rounds_limit = -1;
   if (max_steps > 0) rounds_limit = (max_steps + j->tun.steps_per_launch - 1) / j->tun.steps_per_launch;
+  // whole runs on a real stream replay a captured burst; profiled or partial runs launch directly
+  const bool graph = rounds_limit < 0 && !j->tun.profile_kernels && st != nullptr;
+  if (graph && !j->graph_exec) {
+    fsmc_status s = capture_rounds<T>(j, check_every, st);
+    if (s != FSMC_OK) return s;
+  }
+  const int per_round = j->algo == FSMC_ESS ? 2 : 1;
   int64_t r = 0;
   while (true) {
     int done = 0, err = 0;
@@ -567,9 +595,15 @@ static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
     if (rounds_limit >= 0 && r >= rounds_limit) break;
     int burst = check_every;
     if (rounds_limit >= 0) burst = (int)std::min<int64_t>(burst, rounds_limit - r);
-    for (int b = 0; b < burst; ++b) {
-      cudaError_t e = fsm_round<T>(j, st);
-      if (e != cudaSuccess) return fsmc_cuda_fail(e, "FSM launch");
+    if (graph) {
+      CK(cudaGraphLaunch(j->graph_exec, st));
+      j->launches += (int64_t)per_round * j->graph_rounds;
+      burst = j->graph_rounds;
+    } else {
+      for (int b = 0; b < burst; ++b) {
+        cudaError_t e = fsm_round<T>(j, st);
+        if (e != cudaSuccess) return fsmc_cuda_fail(e, "FSM launch");
+      }
     }
     r += burst;
   }
@@ -850,6 +884,60 @@ extern "C" fsmc_status fsmc_read_stats(fsmc_job* j, fsmc_stats* o) {
   return FSMC_OK;
 }
 
+// ---- fused multi-job rounds (serving) -------------------------------------------------------------------
+fsmc_status multibuf_ensure(MultiBuf& b, size_t bytes) {
+  if (b.cap >= bytes) return FSMC_OK;
+  multibuf_free(b);
+  size_t cap = 4096;
+  while (cap < bytes) cap *= 2;
+  CK(cudaMalloc(&b.d_buf, cap));
+  CK(cudaMallocHost(&b.h_stage, cap));
+  b.cap = cap;
+  return FSMC_OK;
+}
+
+void multibuf_free(MultiBuf& b) {
+  if (b.d_buf) cudaFree(b.d_buf);
+  if (b.h_stage) cudaFreeHost(b.h_stage);
+  b = MultiBuf{};
+}
+
+int ess_job_group(const fsmc_job* j) { return j->tun.lanes_per_chain * 64 + ess_group_E(j->tun.lanes_per_chain, j->d); }
+
+template <typename T>
+static cudaError_t ess_group_round_t(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cudaStream_t st) {
+  const int nj = (int)jobs.size();
+  const size_t vb = sizeof(EssView<T>);
+  const size_t views_bytes = (nj * vb + 15) / 16 * 16;
+  char* hs = (char*)b.h_stage;
+  int64_t* tile_off = (int64_t*)(hs + views_bytes);
+  int64_t* chain_off = tile_off + (nj + 1);
+  tile_off[0] = chain_off[0] = 0;
+  for (int k = 0; k < nj; ++k) {
+    const fsmc_job* j = jobs[k];
+    const EssView<T> v = ess_view<T>(j);
+    std::memcpy(hs + k * vb, &v, vb);
+    tile_off[k + 1] = tile_off[k] + ((j->m + 63) / 64) * j->W * ((j->d + 255) / 256);
+    chain_off[k + 1] = chain_off[k] + j->m;
+  }
+  const size_t bytes = views_bytes + 2 * (nj + 1) * sizeof(int64_t);
+  cudaError_t e = cudaMemcpyAsync(b.d_buf, hs, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const EssView<T>* dv = (const EssView<T>*)b.d_buf;
+  const int64_t* d_tile = (const int64_t*)((char*)b.d_buf + views_bytes);
+  const int64_t* d_chain = d_tile + (nj + 1);
+  e = launch_ess_nu_gen_multi<T>(dv, d_tile, nj, tile_off[nj], st);
+  if (e != cudaSuccess) return e;
+  const fsmc_tuning& tu = jobs[0]->tun;
+  return launch_ess_fsm_multi<T>(ess_view<T>(jobs[0]), tu.lanes_per_chain, dv, d_chain, nj, chain_off[nj],
+                                 tu.steps_per_launch, tu.threads_per_block, st);
+}
+
+cudaError_t ess_group_round(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cudaStream_t st) {
+  if (jobs.empty()) return cudaSuccess;
+  return jobs[0]->prec == FSMC_FP64 ? ess_group_round_t<double>(jobs, b, st) : ess_group_round_t<float>(jobs, b, st);
+}
+
 // ---- checkpoint ---------------------------------------------------------------------------------------
 struct SnapHeader {
   uint64_t magic, bytes, m, n, d, algo, prec, flags;
@@ -892,6 +980,7 @@ extern "C" void fsmc_job_destroy(fsmc_job* j) {
   serving_forget(j);
   fsmc_engine* e = j->e;
   for (cudaEvent_t ev : j->event_pool) cudaEventDestroy(ev);
+  if (j->graph_exec) cudaGraphExecDestroy(j->graph_exec);
   if (j->dev) {
     cudaSetDevice(e->device);
     cudaFree(j->dev);

@@ -80,10 +80,15 @@ struct fsmc_job {
   double kernel_ms[4] = {0, 0, 0, 0};
   int64_t kernel_launches[4] = {0, 0, 0, 0};
   int64_t columns_generated = 0;
+  // captured burst of FSM rounds (replayed by run_fsm when kernel profiling is off)
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_rounds = 0;
   // serving
   bool submitted = false;
   fsmc_mode serve_mode = FSMC_MODE_FSM;
   std::atomic<int> finished{0};
+  std::atomic<int> cancel{0};
+  fsmc_status serve_status = FSMC_OK;
   std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
@@ -102,6 +107,20 @@ struct ProfScope {
   ProfScope(fsmc_job* job, int c, cudaStream_t s);
   ~ProfScope();
 };
+
+// Device table of job views for a fused multi-job launch, with its pinned host staging.
+struct MultiBuf {
+  void* d_buf = nullptr;
+  void* h_stage = nullptr;
+  size_t cap = 0;
+};
+fsmc_status multibuf_ensure(MultiBuf& b, size_t bytes);
+void multibuf_free(MultiBuf& b);
+// Group keys and fused rounds (one direction refill + one FSM launch for ESS groups).
+int ess_job_group(const fsmc_job* j);   // (lanes, E) code of an ESS job
+int nuts_group_E(int d);
+cudaError_t ess_group_round(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cudaStream_t st);
+cudaError_t nuts_group_round(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cudaStream_t st);
 
 // NUTS (nuts.cu)
 void nuts_layout(fsmc_job* j, size_t& off);

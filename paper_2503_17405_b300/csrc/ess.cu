@@ -25,15 +25,16 @@ enum EssState : int { ESS_INIT = 0, ESS_SHRINK = 1 };
 // nu = L z for a tile of (chain, sample) columns.  z is generated from the chain's Philox
 // stream (tag 0, draws 0..ceil(d/2)-1) directly into shared memory, so it never touches HBM.
 // Block: 256 threads = 32 row-groups x 8 column-groups, each thread an 8x8 register tile;
-// tile = 256 rows x 64 columns (64 chains at the same ring offset w = blockIdx.y); the
-// reduction dimension is streamed in chunks of 16 with L^T and z staged in shared memory.
-// Rows above the diagonal are skipped per warp (L is lower triangular).
-// One tile (bx = chain tile, by = ring offset, bz = row tile); called by all 256 threads.
+// tile = 256 rows x 64 columns (64 chains at the same ring offset w = by).  The reduction
+// dimension is streamed in chunks of 16 through two shared-memory buffers: while the block
+// multiplies chunk c, it stages chunk c+1 (L^T rows by one thread each, z by Philox), so one
+// barrier per chunk suffices.  Rows above the diagonal are skipped per warp (L is lower
+// triangular).  Both staging writes are bank-conflict free.
 template <typename T>
 __device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx, int by, int bz) {
   constexpr int BM = 256, BN = 64, BK = 16;
-  __shared__ __align__(16) T As[BK][BM];
-  __shared__ __align__(16) T Bs[BK][BN + 4];
+  __shared__ __align__(16) T As[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN + 4];
   __shared__ int col_sample[BN];
 
   const int d = v.tg.d;
@@ -59,48 +60,69 @@ __device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx,
 
   const int ty = tid >> 3, tx = tid & 7;
   const int warp = tid >> 5;
+  const int D = (d + 1) / 2;
+  const int kmax = min(d, r0 + BM);
+  // staging roles: z column zc and normals 4*zp .. 4*zp+3 of the chunk; L row lr
+  const int zc = tid & 63, zp = tid >> 6;
+  const int z_smp = col_sample[zc];
+  const Key zkey{(uint32_t)(v.chain0 + c0 + zc), v.seed_lo, v.seed_hi};
+  const int lr = r0 + tid;
+  const bool vec_rows = (d % 4) == 0 && sizeof(T) == 4;
+
+  auto stage = [&](int buf, int q0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int blk = q0 / 2 + 2 * zp + h;
+      T z0 = T(0), z1 = T(0);
+      if (z_smp >= 0 && blk < D) Conv<T>::normal_pair(zkey.block((uint32_t)z_smp, 0, (uint32_t)blk), z0, z1);
+      const int kk = 4 * zp + 2 * h;
+      Bs[buf][kk][zc] = (q0 + kk < d) ? z0 : T(0);
+      Bs[buf][kk + 1][zc] = (q0 + kk + 1 < d) ? z1 : T(0);
+    }
+    if (lr < d && q0 <= lr) {
+      const T* row = v.tg.L + (size_t)lr * d + q0;
+      if (vec_rows && q0 + BK <= d) {
+#pragma unroll
+        for (int q = 0; q < BK / 4; ++q) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(row) + q);
+          const int gq = q0 + 4 * q;
+          As[buf][4 * q + 0][tid] = gq + 0 <= lr ? (T)f.x : T(0);
+          As[buf][4 * q + 1][tid] = gq + 1 <= lr ? (T)f.y : T(0);
+          As[buf][4 * q + 2][tid] = gq + 2 <= lr ? (T)f.z : T(0);
+          As[buf][4 * q + 3][tid] = gq + 3 <= lr ? (T)f.w : T(0);
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+          const int gq = q0 + kk;
+          As[buf][kk][tid] = (gq < d && gq <= lr) ? row[kk] : T(0);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) As[buf][kk][tid] = T(0);
+    }
+  };
+
   T acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
 
-  const int kmax = min(d, r0 + BM);
-  const int D = (d + 1) / 2;
+  stage(0, 0);
+  __syncthreads();
+  int buf = 0;
   for (int q0 = 0; q0 < kmax; q0 += BK) {
-    // z chunk: column tid/4, Philox draws q0/2 + 2*(tid%4) + {0,1}
-    {
-      const int col = tid >> 2;
-      const int smp = col_sample[col];
-      const int64_t c = c0 + col;
-      Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int blk = q0 / 2 + 2 * (tid & 3) + h;
-        T z0 = T(0), z1 = T(0);
-        if (smp >= 0 && blk < D) Conv<T>::normal_pair(key.block((uint32_t)smp, 0, (uint32_t)blk), z0, z1);
-        const int kk = 2 * (2 * (tid & 3) + h);
-        Bs[kk][col] = (q0 + kk < d) ? z0 : T(0);
-        Bs[kk + 1][col] = (q0 + kk + 1 < d) ? z1 : T(0);
-      }
-    }
-    // L^T chunk: As[kk][r] = L[r0 + r][q0 + kk]
-#pragma unroll
-    for (int h = 0; h < (BK * BM) / 256; ++h) {
-      const int idx = tid + 256 * h;
-      const int r = idx / BK, kk = idx % BK;
-      const int gr = r0 + r, gq = q0 + kk;
-      As[kk][r] = (gr < d && gq < d && gq <= gr) ? v.tg.L[(size_t)gr * d + gq] : T(0);
-    }
-    __syncthreads();
+    if (q0 + BK < kmax) stage(buf ^ 1, q0 + BK);
     if (r0 + warp * 32 + 31 >= q0) {  // rows of this warp reach the chunk's columns
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         T a[8], b[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = As[kk][ty * 8 + i];
+        for (int i = 0; i < 8; ++i) a[i] = As[buf][kk][ty * 8 + i];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) b[j] = Bs[kk][tx * 8 + j];
+        for (int j = 0; j < 8; ++j) b[j] = Bs[buf][kk][tx * 8 + j];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -108,6 +130,7 @@ __device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx,
       }
     }
     __syncthreads();
+    buf ^= 1;
   }
   // write nu rows r0+ty*8.. of each active column to its ring slot
 #pragma unroll
@@ -149,6 +172,18 @@ __device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E
     return -group_sum<G>(part) / (T(2) * tg.s2);
   }
   return T(0);  // TGT_FLAT
+}
+
+// sin and cos of a bracket angle th in (-2 pi, 2 pi).  Single precision reduces th to
+// [-pi, pi], where __sincosf is accurate to ~5e-7; double precision calls sincos.
+template <typename T>
+__device__ __forceinline__ void ess_sincos(T th, T& sn, T& cs) {
+  if constexpr (sizeof(T) == 4) {
+    const float red = fmaf(-6.28318530717958647692f, rintf(th * 0.15915494309189533577f), th);
+    __sincosf(red, &sn, &cs);
+  } else {
+    sincos(th, &sn, &cs);
+  }
 }
 
 template <typename T>
@@ -214,13 +249,32 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
     }
     int steps = 0;
     int err = 0;
+    // Chain-per-warp: the 32 lanes draw 32 consecutive Philox blocks of the current sample at
+    // once (lane l holds draw D + cbase + l) and each state fetches its words by shuffle,
+    // instead of every lane computing the same block.
+    P4 cache{0u, 0u, 0u, 0u};
+    int cbase = -(1 << 30);
+    auto fetch = [&](int off) -> P4 {
+      if constexpr (G == 32) {
+        if (off - cbase >= 32 || off < cbase) {
+          cbase = off;
+          cache = key.block((uint32_t)t, 0, (uint32_t)(D + off + lane));
+        }
+        const int src = off - cbase;
+        return P4{__shfl_sync(0xffffffffu, cache.w0, src), __shfl_sync(0xffffffffu, cache.w1, src),
+                  __shfl_sync(0xffffffffu, cache.w2, src), __shfl_sync(0xffffffffu, cache.w3, src)};
+      } else {
+        return key.block((uint32_t)t, 0, (uint32_t)(D + off));
+      }
+    };
     for (int b = 0; b < budget && t < v.n; ++b) {
       if (st == ESS_INIT) {
         if (t >= hi) break;  // direction not generated yet
         const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
 #pragma unroll
         for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) nu[e] = src[k]; }
-        const P4 r = key.block((uint32_t)t, 0, (uint32_t)D);
+        cbase = -(1 << 30);  // a new sample: its blocks are not cached yet
+        const P4 r = fetch(0);
         logy = ell + Conv<T>::log_u(r.w0, r.w1);
         th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
         thmin = th - T(kTwoPi);
@@ -228,12 +282,12 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
         s = 0;
       } else {
         if (th < T(0)) thmin = th; else thmax = th;
-        const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + 1 + s));
+        const P4 r = fetch(1 + s);
         th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
         ++s;
       }
       T sn, cs;
-      if constexpr (sizeof(T) == 4) sincosf(th, &sn, &cs); else sincos(th, &sn, &cs);
+      ess_sincos<T>(th, sn, cs);
 #pragma unroll
       for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
       T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv);
@@ -271,7 +325,8 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
 }
 
 template <typename T, int G, int E>
-__global__ void __launch_bounds__(256) ess_fsm_kernel(EssView<T> v, int budget) {
+__global__ void __launch_bounds__(256, ((sizeof(T) == 4 && E <= 8) || (sizeof(T) == 8 && E <= 2)) ? 3 : 2)
+ess_fsm_kernel(EssView<T> v, int budget) {
   const int lane = threadIdx.x % G;
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
@@ -376,7 +431,7 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
           ++s;
         }
         T sn, cs;
-        if constexpr (sizeof(T) == 4) sincosf(th, &sn, &cs); else sincos(th, &sn, &cs);
+        ess_sincos<T>(th, sn, cs);
 #pragma unroll
         for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
         T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv);

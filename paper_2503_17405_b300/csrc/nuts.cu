@@ -18,6 +18,7 @@
 //
 // Layout: one chain per warp; lane l holds coordinates l, l + 32, ....
 #include <algorithm>
+#include <cstring>
 #include "engine_internal.h"
 #include "fsmc_device.cuh"
 #include "fsmc_kernels.h"
@@ -440,31 +441,52 @@ __device__ void nuts_done(const NutsView<T>& v, int64_t c, int lane, Chain<T, E>
 
 // ---- FSM kernel: each chain advances `budget` leapfrog steps ---------------------------------------
 template <typename T, int E>
+__device__ __forceinline__ void nuts_advance_chain(const NutsView<T>& v, int64_t c, int budget, int lane,
+                                                   T* wsm) {
+  Chain<T, E> s;
+  chain_load<T, E>(v, c, lane, s);
+  if (s.t >= v.n) return;
+  const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  long long steps = 0;
+  for (int b = 0; b < budget && s.t < v.n; ++b) {
+    if (s.st == N_INIT) nuts_init<T, E>(v, key, lane, s);
+    if (s.st == N_DOUBLE) nuts_double<T, E>(key, s);
+    Sub<T, E> sb;
+    const int r = nuts_integrate<T, E>(v, key, c, lane, wsm, s, sb);
+    ++steps;
+    if (r == 1 && nuts_check<T, E>(v, key, s, sb)) continue;
+    if (r != 0) nuts_done<T, E>(v, c, lane, s);
+  }
+  chain_store<T, E>(v, c, lane, s);
+  if (lane == 0) v.steps[c] += steps;
+}
+
+template <typename T, int E>
 __global__ void __launch_bounds__(256) nuts_fsm_kernel(NutsView<T> v, int budget) {
   __shared__ T wsm_all[kWarpsMax][kWsm];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  T* wsm = wsm_all[wib];
+  T* wsm = wsm_all[threadIdx.x >> 5];
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = warp; c < v.m; c += nwarps) {
-    Chain<T, E> s;
-    chain_load<T, E>(v, c, lane, s);
-    if (s.t >= v.n) continue;
-    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
-    long long steps = 0;
-    for (int b = 0; b < budget && s.t < v.n; ++b) {
-      if (s.st == N_INIT) nuts_init<T, E>(v, key, lane, s);
-      if (s.st == N_DOUBLE) nuts_double<T, E>(key, s);
-      Sub<T, E> sb;
-      const int r = nuts_integrate<T, E>(v, key, c, lane, wsm, s, sb);
-      ++steps;
-      if (r == 1 && nuts_check<T, E>(v, key, s, sb)) continue;
-      if (r != 0) nuts_done<T, E>(v, c, lane, s);
-    }
-    chain_store<T, E>(v, c, lane, s);
-    if (lane == 0) v.steps[c] += steps;
+  for (int64_t c = warp; c < v.m; c += nwarps) nuts_advance_chain<T, E>(v, c, budget, lane, wsm);
+}
+
+// Fused launch over several NUTS jobs (serving): job k owns chains off[k] .. off[k+1].
+template <typename T, int E>
+__global__ void __launch_bounds__(256) nuts_fsm_multi_kernel(const NutsView<T>* views, const int64_t* off,
+                                                             int njobs, int64_t total, int budget) {
+  __shared__ T wsm_all[kWarpsMax][kWsm];
+  const int lane = threadIdx.x & 31;
+  T* wsm = wsm_all[threadIdx.x >> 5];
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (item >= total) return;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= item) lo = mid; else hi = mid - 1;
   }
+  const NutsView<T> v = views[lo];
+  nuts_advance_chain<T, E>(v, item - off[lo], budget, lane, wsm);
 }
 
 // ---- synchronised kernel (Alg. 6 with nested loops) --------------------------------------------------
@@ -715,6 +737,48 @@ fsmc_status nuts_init_state(fsmc_job* j, cudaStream_t st) {
 
 cudaError_t nuts_fsm_round(fsmc_job* j, cudaStream_t st) {
   return j->prec == FSMC_FP64 ? nuts_fsm_t<double>(j, st) : nuts_fsm_t<float>(j, st);
+}
+
+int nuts_group_E(int d) { return d <= 32 ? 1 : d <= 64 ? 2 : 4; }
+
+// One fused FSM launch over jobs that share precision and E (serving scheduler).
+template <typename T, int E>
+static cudaError_t nuts_multi_launch_t(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cudaStream_t st) {
+  const int nj = (int)jobs.size();
+  const size_t vb = sizeof(NutsView<T>);
+  const size_t views_bytes = (nj * vb + 15) / 16 * 16;
+  char* hs = (char*)b.h_stage;
+  int64_t* hoff = (int64_t*)(hs + views_bytes);
+  hoff[0] = 0;
+  for (int k = 0; k < nj; ++k) {
+    const NutsView<T> v = nuts_view<T>(jobs[k]);
+    std::memcpy(hs + k * vb, &v, vb);
+    hoff[k + 1] = hoff[k] + jobs[k]->m;
+  }
+  const size_t bytes = views_bytes + (nj + 1) * sizeof(int64_t);
+  cudaError_t e = cudaMemcpyAsync(b.d_buf, hs, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const int threads = 128;
+  const int64_t total = hoff[nj];
+  const int64_t blocks = (total * 32 + threads - 1) / threads;
+  nuts_fsm_multi_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(
+      (const NutsView<T>*)b.d_buf, (const int64_t*)((char*)b.d_buf + views_bytes), nj, total,
+      jobs[0]->tun.steps_per_launch);
+  return cudaGetLastError();
+}
+
+cudaError_t nuts_group_round(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cudaStream_t st) {
+  if (jobs.empty()) return cudaSuccess;
+  const bool f64 = jobs[0]->prec == FSMC_FP64;
+  const int E = nuts_group_E(jobs[0]->d);
+  if (f64) {
+    if (E == 1) return nuts_multi_launch_t<double, 1>(jobs, b, st);
+    if (E == 2) return nuts_multi_launch_t<double, 2>(jobs, b, st);
+    return nuts_multi_launch_t<double, 4>(jobs, b, st);
+  }
+  if (E == 1) return nuts_multi_launch_t<float, 1>(jobs, b, st);
+  if (E == 2) return nuts_multi_launch_t<float, 2>(jobs, b, st);
+  return nuts_multi_launch_t<float, 4>(jobs, b, st);
 }
 
 fsmc_status nuts_run_sync(fsmc_job* j, cudaStream_t st) {
