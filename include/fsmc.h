@@ -100,6 +100,8 @@ typedef struct fsmc_tuning {
   int ring_slots;        /* ESS: pre-generated ellipse directions kept per chain         */
   int threads_per_block; /* 32..256, multiple of 32                                      */
   int profile_kernels;   /* 1: time every launch with CUDA events (see fsmc_stats)        */
+  int generator;         /* ESS directions nu = L z: 0 auto, 1 CUDA cores, 2 tensor cores
+                            (tcgen05; FP32 jobs with d <= 256)                            */
 } fsmc_tuning;
 
 /* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */
@@ -216,7 +218,8 @@ fsmc_status fsmc_wait_all(fsmc_engine* e, double timeout_s);
  * synchronisation is not acceptable.
  * It runs FP32 elliptical slice sampling in FSM mode to completion -- the same kernels, and
  * the same samples and loop counts, as fsmc_job_run on an FP32 ESS job that stores its
- * samples, for equal inputs, seed and lanes_per_chain (1 or 32).  Every pointer is
+ * samples and uses the CUDA-core direction generator (tuning.generator = 1), for equal
+ * inputs, seed and lanes_per_chain (1 or 32).  Every pointer is
  * caller-owned device memory:
  *   L_dev       [d*d] lower Cholesky factor of the prior covariance (read)
  *   vec_dev     [d]   y for GAUSS_CONJ, labels s in {-1,+1} for GP_LOGIT, unused for FLAT (read)

@@ -228,6 +228,7 @@ extern "C" void fsmc_target_destroy(fsmc_target* t) {
   fsmc_engine* e = t->e;
   cudaSetDevice(e->device);
   for (void* b : t->bufs) cudaFree(b);
+  if (t->tc_img) cudaFree(t->tc_img);
   {
     std::lock_guard<std::mutex> g(e->mu);
     e->in_use -= std::min(t->bytes, e->in_use);
@@ -261,6 +262,7 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.steps_per_launch) tu.steps_per_launch = 64;
     if (!tu.ring_slots) tu.ring_slots = 32;
     if (!tu.threads_per_block) tu.threads_per_block = 256;
+    if (!tu.generator) tu.generator = (j->prec == FSMC_FP32 && j->d <= 256) ? 2 : 1;
   } else if (j->algo == FSMC_DR) {
     tu.lanes_per_chain = 1;
     if (!tu.steps_per_launch) tu.steps_per_launch = 256;
@@ -503,6 +505,9 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
     return fsmc_fail(FSMC_EINVAL, "threads_per_block must be a multiple of 32 in [32, 256]");
   if (t.steps_per_launch < 0 || t.ring_slots < 0 || t.ring_slots > 4096)
     return fsmc_fail(FSMC_EINVAL, "negative steps / ring slots");
+  if (t.generator < 0 || t.generator > 2) return fsmc_fail(FSMC_EINVAL, "generator must be 0, 1 or 2");
+  if (t.generator == 2 && (j->algo != FSMC_ESS || j->prec != FSMC_FP32 || j->d > 256))
+    return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   j->tun = t;
   default_tuning(j);
   return FSMC_OK;
@@ -517,6 +522,24 @@ extern "C" fsmc_status fsmc_job_get_tuning(const fsmc_job* j, fsmc_tuning* tu) {
 extern "C" size_t fsmc_job_bytes(const fsmc_job* j) { return j ? j->bytes : 0; }
 
 // ---- run loops -------------------------------------------------------------------------------------
+// Refills the ESS direction rings with the job's generator (tensor cores or CUDA cores).
+template <typename T>
+static cudaError_t ess_generate(fsmc_job* j, const EssView<T>& v, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (j->tun.generator == 2) {
+      fsmc_target* t = j->tg;
+      if (!t->tc_img) {
+        cudaError_t e = cudaMalloc((void**)&t->tc_img, ess_tc_image_bytes(t->d));
+        if (e != cudaSuccess) { t->tc_img = nullptr; return e; }
+        e = launch_ess_tc_build(t->tv32.L, t->d, t->tc_img, st);
+        if (e != cudaSuccess) return e;
+      }
+      return launch_ess_nu_gen_tc(v, t->tc_img, j->e->sms, st);
+    }
+  }
+  return launch_ess_nu_gen<T>(v, st);
+}
+
 // One FSM round: (ESS) refill the rings, then advance every chain by the step budget.
 template <typename T>
 static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
@@ -526,7 +549,7 @@ static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
     const EssView<T> v = ess_view<T>(j);
     {
       ProfScope p(j, 0, st);
-      if ((e = launch_ess_nu_gen<T>(v, st)) != cudaSuccess) return e;
+      if ((e = ess_generate<T>(j, v, st)) != cudaSuccess) return e;
     }
     ProfScope p(j, 1, st);
     e = launch_ess_fsm<T>(v, tu.lanes_per_chain, tu.steps_per_launch, tu.threads_per_block, st);
@@ -628,7 +651,7 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
       }
       {
         ProfScope p(j, 0, st);
-        CK(launch_ess_nu_gen<T>(v, st));
+        CK(ess_generate<T>(j, v, st));
       }
       CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
       ProfScope p(j, 2, st);
@@ -905,6 +928,9 @@ void multibuf_free(MultiBuf& b) {
 int ess_job_group(const fsmc_job* j) { return j->tun.lanes_per_chain * 64 + ess_group_E(j->tun.lanes_per_chain, j->d); }
 
 template <typename T>
+static cudaError_t ess_generate(fsmc_job* j, const EssView<T>& v, cudaStream_t st);
+
+template <typename T>
 static cudaError_t ess_group_round_t(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cudaStream_t st) {
   const int nj = (int)jobs.size();
   const size_t vb = sizeof(EssView<T>);
@@ -914,10 +940,17 @@ static cudaError_t ess_group_round_t(const std::vector<fsmc_job*>& jobs, MultiBu
   int64_t* chain_off = tile_off + (nj + 1);
   tile_off[0] = chain_off[0] = 0;
   for (int k = 0; k < nj; ++k) {
-    const fsmc_job* j = jobs[k];
+    fsmc_job* j = jobs[k];
     const EssView<T> v = ess_view<T>(j);
     std::memcpy(hs + k * vb, &v, vb);
-    tile_off[k + 1] = tile_off[k] + ((j->m + 63) / 64) * j->W * ((j->d + 255) / 256);
+    // jobs on the tensor-core generator refill their rings with it (identical directions to a
+    // job run alone); the others share one fused CUDA-core generator launch
+    const bool own = j->tun.generator == 2;
+    if (own) {
+      cudaError_t e = ess_generate<T>(j, v, st);
+      if (e != cudaSuccess) return e;
+    }
+    tile_off[k + 1] = tile_off[k] + (own ? 0 : ((j->m + 63) / 64) * j->W * ((j->d + 255) / 256));
     chain_off[k + 1] = chain_off[k] + j->m;
   }
   const size_t bytes = views_bytes + 2 * (nj + 1) * sizeof(int64_t);

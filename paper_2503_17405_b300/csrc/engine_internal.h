@@ -43,6 +43,7 @@ struct fsmc_target {
   size_t bytes = 0;
   fsmc::TargetView<float> tv32{};
   fsmc::TargetView<double> tv64{};
+  unsigned char* tc_img = nullptr;  // FP16 hi/lo image of L for the tensor-core generator
 };
 
 struct fsmc_job {

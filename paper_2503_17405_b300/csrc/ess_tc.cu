@@ -1,0 +1,332 @@
+// Ellipse directions nu = L z on the 5th-generation tensor cores (tcgen05), d <= 256, FP32 jobs.
+//
+// The contraction behind ESS's INIT state is dense: for every (chain, sample) column the
+// lower-triangular prior factor L (d x d) multiplies a fresh standard-normal z.  Here:
+//  * L is split once into two FP16 parts, L = L_hi + L_lo (11 + 11 significant bits), laid out
+//    in the tensor cores' K-major shared-memory layout and copied into shared memory once per
+//    CTA with a bulk TMA copy; it stays resident while the CTA walks over column tiles;
+//  * for each tile of 64 columns, all 256 threads draw z from Philox (Box-Muller, the same
+//    conversion as the SIMT path) straight into shared memory, split into z_hi + z_lo;
+//  * one elected thread issues tcgen05.mma (kind::f16, FP32 accumulation in tensor memory):
+//    L_hi z_hi + L_hi z_lo + L_lo z_hi per 16-wide k-step (the dropped L_lo z_lo term is
+//    ~2^-22 relative), for row tile 0 (rows 0..127, k < 128) and row tile 1 (rows 128..255);
+//  * the accumulators are read back with tcgen05.ld and stored to the chains' direction rings.
+// Every wait on an mbarrier is bounded; on expiry the kernel records ERR_BARRIER_TIMEOUT,
+// waits (bounded) for its outstanding MMAs, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+#include <algorithm>
+
+#include "fsmc_device.cuh"
+#include "fsmc_kernels.h"
+
+namespace fsmc {
+
+namespace {
+
+constexpr int TC_THREADS = 512;
+constexpr int TC_N = 64;          // columns per tile
+constexpr int TC_KC = 64;         // k per staged chunk
+constexpr int TC_STAGE = TC_N * TC_KC * 2;  // bytes of one FP16 part of a z chunk (8 KB)
+constexpr unsigned kWaitLimit = 1u << 20;  // polls; with the back-off below, well under 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = smem_u32(bar);
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+// tensor-core shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, swizzle mode 0 (none)
+}
+
+// instruction descriptor, kind::f16: A, B = F16, D = F32, both K-major
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+struct TcLayout {
+  int K0, K1;          // k extent of row tile 0 / 1 (K1 = 0: no row tile 1)
+  int kpad;            // k extent of z (multiple of TC_KC)
+  int a_bytes;         // whole A image
+};
+
+__host__ __device__ inline TcLayout tc_layout(int d) {
+  TcLayout L;
+  L.kpad = (d + TC_KC - 1) / TC_KC * TC_KC;
+  L.K0 = L.kpad < 128 ? L.kpad : 128;
+  L.K1 = d > 128 ? L.kpad : 0;
+  L.a_bytes = 128 * L.K0 * 2 * 2 + 128 * L.K1 * 2 * 2;
+  return L;
+}
+
+// byte offset of element (m, k) in a K-major no-swizzle image with k extent K
+__host__ __device__ inline int kmajor_off(int m, int k, int K) {
+  return (m >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2;
+}
+
+}  // namespace
+
+// Builds the FP16 hi/lo image of L in the tensor cores' layout:
+// [row tile 0 hi][row tile 0 lo][row tile 1 hi][row tile 1 lo].
+__global__ void ess_tc_build_a_kernel(const float* L, int d, unsigned char* img) {
+  const TcLayout lay = tc_layout(d);
+  const int total = 128 * lay.K0 + 128 * lay.K1;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int rt, m, k, K;
+    if (idx < 128 * lay.K0) { rt = 0; K = lay.K0; m = idx / K; k = idx % K; }
+    else { rt = 1; K = lay.K1; m = (idx - 128 * lay.K0) / K; k = (idx - 128 * lay.K0) % K; }
+    const int row = rt * 128 + m;
+    const float v = (row < d && k < d && k <= row) ? L[(size_t)row * d + k] : 0.f;
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(v - __half2float(hi));
+    const int base = rt == 0 ? 0 : 128 * lay.K0 * 4;
+    const int part = 128 * K * 2;
+    *reinterpret_cast<__half*>(img + base + kmajor_off(m, k, K)) = hi;
+    *reinterpret_cast<__half*>(img + base + part + kmajor_off(m, k, K)) = lo;
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<float> v, const unsigned char* a_img) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int d = v.tg.d;
+  const TcLayout lay = tc_layout(d);
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + lay.a_bytes;                 // 2 stages x (hi, lo)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 2 * 2 * TC_STAGE);
+  uint64_t* bar_a = bars;
+  uint64_t* bar_mma = bars + 1;  // [2]
+  uint64_t* bar_done = bars + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  int* col_sample = reinterpret_cast<int*>(bars + 5);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = (d + 1) / 2;
+  const int nchunks = lay.kpad / TC_KC;
+  const int nbx = (int)((v.m + TC_N - 1) / TC_N);
+  const int ntiles = nbx * v.W;
+
+  if (tid == 0) {
+    s_fail = 0;
+    mbar_init(bar_a, 1);
+    mbar_init(&bar_mma[0], 1);
+    mbar_init(&bar_mma[1], 1);
+    mbar_init(bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  // L image -> shared memory (bulk TMA copies of at most 48 KB, completion via tx count)
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar_a)),
+                 "r"(lay.a_bytes)
+                 : "memory");
+    for (int off = 0; off < lay.a_bytes; off += 48 * 1024) {
+      const int n = min(48 * 1024, lay.a_bytes - off);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(sA + off)),
+          "l"(a_img + off), "r"(n), "r"(smem_u32(bar_a))
+          : "memory");
+    }
+  }
+  if (!mbar_wait(bar_a, 0)) s_fail = 1;
+  __syncthreads();
+
+  const uint32_t idesc = idesc_f16(128, TC_N);
+  const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+  const uint32_t a_rt0 = sA_u, a_rt1 = sA_u + 128 * lay.K0 * 4;
+  unsigned stage_phase[2] = {0u, 0u};
+  unsigned done_phase = 0;
+  long long chunk_ctr = 0;
+  bool mma_pending = false;
+
+  for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
+    const int bx = tile % nbx, w = tile / nbx;
+    const int64_t c0 = (int64_t)bx * TC_N;
+    int active = 0;
+    if (tid < TC_N) {
+      const int64_t c = c0 + tid;
+      int smp = -1;
+      if (c < v.m) {
+        const int s = v.gen_lo[c] + w;
+        if (s < v.gen_hi[c]) smp = s;
+      }
+      col_sample[tid] = smp;
+      active = smp >= 0;
+    }
+    const int n_active = __syncthreads_count(active);
+    if (n_active == 0) continue;
+    if (tid == 0) atomicAdd(v.gen_cols, (unsigned long long)n_active);
+
+    for (int kc = 0; kc < nchunks; ++kc, ++chunk_ctr) {
+      const int s = (int)(chunk_ctr & 1);
+      if (chunk_ctr >= 2) {  // the MMAs that read this stage two chunks ago must be done
+        if (!mbar_wait(&bar_mma[s], stage_phase[s])) { s_fail = 1; }
+        stage_phase[s] ^= 1u;
+      }
+      // z chunk: warp w writes core matrices w, w+16, ... (8 columns x 8 k, 128 contiguous
+      // bytes each); four independent Philox chains per thread
+      unsigned char* zhi = sB + s * 2 * TC_STAGE;
+      unsigned char* zlo = zhi + TC_STAGE;
+#pragma unroll
+      for (int it = 0; it < 64 / (TC_THREADS / 32); ++it) {
+        const int core = warp + (TC_THREADS / 32) * it;
+        const int ng = core & 7, kg = core >> 3;
+        const int n = ng * 8 + (lane >> 2);
+        const int qq = lane & 3;
+        const int q = kc * (TC_KC / 2) + kg * 4 + qq;  // Philox draw = normal pair index
+        const int smp = col_sample[n];
+        float z0 = 0.f, z1 = 0.f;
+        if (smp >= 0 && q < D) {
+          const Key key{(uint32_t)(v.chain0 + c0 + n), v.seed_lo, v.seed_hi};
+          Conv<float>::normal_pair(key.block((uint32_t)smp, 0, (uint32_t)q), z0, z1);
+          if (2 * q + 1 >= d) z1 = 0.f;
+        }
+        const __half h0 = __float2half_rn(z0), h1 = __float2half_rn(z1);
+        const __half l0 = __float2half_rn(z0 - __half2float(h0)), l1 = __float2half_rn(z1 - __half2float(h1));
+        const int off = ng * (TC_KC / 8) * 128 + kg * 128 + (lane >> 2) * 16 + qq * 4;
+        *reinterpret_cast<__half2*>(zhi + off) = __halves2half2(h0, h1);
+        *reinterpret_cast<__half2*>(zlo + off) = __halves2half2(l0, l1);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (s_fail) break;
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t bh = sB_u + s * 2 * TC_STAGE, bl = bh + TC_STAGE;
+#pragma unroll
+        for (int ks = 0; ks < TC_KC / 16; ++ks) {
+          const int kglob = kc * TC_KC + ks * 16;
+          const uint64_t dbh = sdesc(bh + ks * 256, 128, (TC_KC / 8) * 128);
+          const uint64_t dbl = sdesc(bl + ks * 256, 128, (TC_KC / 8) * 128);
+          if (kglob < lay.K0) {
+            const uint32_t ah = a_rt0 + (kglob / 8) * 128, al = ah + 128 * lay.K0 * 2;
+            const uint32_t sbo = (lay.K0 / 8) * 128;
+            mma_f16(tmem, sdesc(ah, 128, sbo), dbh, idesc, kglob > 0);
+            mma_f16(tmem, sdesc(ah, 128, sbo), dbl, idesc, 1);
+            mma_f16(tmem, sdesc(al, 128, sbo), dbh, idesc, 1);
+          }
+          if (lay.K1) {
+            const uint32_t ah = a_rt1 + (kglob / 8) * 128, al = ah + 128 * lay.K1 * 2;
+            const uint32_t sbo = (lay.K1 / 8) * 128;
+            mma_f16(tmem + TC_N, sdesc(ah, 128, sbo), dbh, idesc, kglob > 0);
+            mma_f16(tmem + TC_N, sdesc(ah, 128, sbo), dbl, idesc, 1);
+            mma_f16(tmem + TC_N, sdesc(al, 128, sbo), dbh, idesc, 1);
+          }
+        }
+        mma_commit(&bar_mma[s]);
+        if (kc == nchunks - 1) mma_commit(bar_done);
+      }
+      mma_pending = true;
+    }
+    if (s_fail) break;
+    // accumulators complete -> registers -> direction rings
+    if (!mbar_wait(bar_done, done_phase)) { s_fail = 1; break; }
+    done_phase ^= 1u;
+    mma_pending = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // warp w: row tile (w >> 2) & 1, lane quadrant w & 3, column half w >> 3
+    const int rt = (warp >> 2) & 1;
+    if (rt == 0 || lay.K1) {
+      const int row = rt * 128 + (warp & 3) * 32 + lane;
+      const int jbeg = (warp >> 3) * (TC_N / 2);
+#pragma unroll
+      for (int j0 = jbeg; j0 < jbeg + TC_N / 2; j0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(rt * TC_N + j0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < d) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = j0 + jj;
+            const int smp = col_sample[j];
+            if (smp >= 0)
+              v.nu[((size_t)(c0 + j) * v.W + (smp % v.W)) * v.dstride + row] = __uint_as_float(r[jj]);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  // teardown: no MMA may still be writing tensor memory when it is freed
+  if (tid == 0 && mma_pending) mma_commit(bar_done);
+  if (mma_pending) mbar_wait(bar_done, done_phase);
+  if (s_fail && tid == 0) atomicOr(v.err, ERR_BARRIER_TIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+size_t ess_tc_image_bytes(int d) { return (size_t)tc_layout(d).a_bytes; }
+
+cudaError_t launch_ess_tc_build(const float* L, int d, unsigned char* img, cudaStream_t st) {
+  const TcLayout lay = tc_layout(d);
+  const int total = 128 * lay.K0 + 128 * lay.K1;
+  ess_tc_build_a_kernel<<<(total + 255) / 256, 256, 0, st>>>(L, d, img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ess_nu_gen_tc(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st) {
+  const TcLayout lay = tc_layout(v.tg.d);
+  const int smem = lay.a_bytes + 2 * 2 * TC_STAGE + 64 + TC_N * 4;
+  cudaError_t e = cudaFuncSetAttribute(ess_nu_gen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int nbx = (int)((v.m + TC_N - 1) / TC_N);
+  const int ntiles = nbx * v.W;
+  const int grid = std::max(1, std::min(ntiles, sms));
+  ess_nu_gen_tc_kernel<<<grid, TC_THREADS, smem, st>>>(v, img);
+  return cudaGetLastError();
+}
+
+}  // namespace fsmc

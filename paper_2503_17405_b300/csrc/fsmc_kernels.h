@@ -72,6 +72,11 @@ template <typename T>
 cudaError_t launch_ess_fsm_multi(const EssView<T>& any, int G, const EssView<T>* views, const int64_t* off,
                                  int njobs, int64_t total, int budget, int threads, cudaStream_t st);
 int ess_group_E(int G, int d);
+// Tensor-core direction generator (d <= 256, FP32): L image in the MMA layout, built once
+// per target, and the persistent generator kernel.
+size_t ess_tc_image_bytes(int d);
+cudaError_t launch_ess_tc_build(const float* L, int d, unsigned char* img, cudaStream_t st);
+cudaError_t launch_ess_nu_gen_tc(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_dr_fsm(const DrView<T>& v, int budget, int threads, cudaStream_t st);

@@ -60,6 +60,24 @@ def test_fp32_gp_logit_matches_oracle_until_branch_flip(eng):
     job.close()
 
 
+@pytest.mark.parametrize("d", [100, 200, 256])
+def test_tensor_core_generator_matches_oracle(eng, d):
+    """The tcgen05 direction generator (FP16 hi/lo splits, FP32 accumulation) and the CUDA-core
+    generator both follow the oracle to the FP32 tolerance."""
+    w = W.gp_logit(d)
+    m, n = 96, 150
+    x0 = W.x0_zeros(m, d)
+    ref = O.run("ess", "gp_logit", w["params"], x0, n, seed=1)
+    for gen in (2, 1):
+        job = _run(eng, w, m, n, x0, "fp32", tuning={"generator": gen})
+        assert job.tuning()["generator"] == gen
+        counts, _, _ = job.loop_counts()
+        r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp32")
+        print("generator", gen, "d", d, "flipped", r["flipped"], "max err", r["max_err"])
+        assert r["flipped"] <= m // 4
+        job.close()
+
+
 def test_sync_and_fsm_give_identical_samples(eng):
     w = W.gp_logit(256)
     m, n = 300, 64

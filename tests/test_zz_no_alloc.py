@@ -27,7 +27,9 @@ def test_static_scratch_run_matches_job_api_twice():
 
     eng = fsmc.Engine(0)
     tg = eng.target("gp_logit", d, w["params"])
-    job = eng.job(tg, "ess", m, n, x0=x0, seed=7, prec="fp32", tuning={"lanes_per_chain": 32})
+    # the static-scratch run uses the CUDA-core direction generator: compare like with like
+    job = eng.job(tg, "ess", m, n, x0=x0, seed=7, prec="fp32",
+                  tuning={"lanes_per_chain": 32, "generator": 1})
     job.run("fsm")
     ref_x = job.samples()
     ref_c, _, _ = job.loop_counts()
