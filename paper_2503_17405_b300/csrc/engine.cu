@@ -175,10 +175,18 @@ static fsmc_status upload_target(fsmc_target* t, std::vector<void*>& bufs, Targe
     case FSMC_TGT_FLAT:
       if ((st = up(p, (size_t)d * d, &tv.L))) return st;
       break;
-    case FSMC_TGT_LOGREG:
+    case FSMC_TGT_LOGREG: {
       if ((st = up(p, (size_t)t->n_data * d, &tv.X))) return st;
       if ((st = up(p + (size_t)t->n_data * d, t->n_data, &tv.vec))) return st;
+      // transposed copy for the batched gradient: [d][n_pad], zero rows beyond n_data
+      const int n = t->n_data, np = (n + 3) / 4 * 4;
+      std::vector<double> xt((size_t)d * np, 0.0);
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < d; ++k) xt[(size_t)k * np + i] = p[(size_t)i * d + k];
+      if ((st = up(xt.data(), xt.size(), &tv.XT))) return st;
+      tv.n_pad = np;
       break;
+    }
     case FSMC_TGT_GAUSS_DIAG:
       if ((st = up(p, d, &tv.vec))) return st;
       if ((st = up(p + d, d, &tv.vec2))) return st;

@@ -147,6 +147,8 @@ struct TargetView {
   const T* vec;   // y (GAUSS_CONJ), s (GP_LOGIT), mu (GAUSS_DIAG), y (LOGREG)
   const T* vec2;  // sigma (GAUSS_DIAG)
   const T* X;     // LOGREG design matrix [n_data][d]
+  const T* XT;    // LOGREG design matrix transposed, [d][n_pad] with zero rows >= n_data
+  int n_pad;      // n_data rounded up to a multiple of 4
   T s2;           // GAUSS_CONJ noise variance
 };
 

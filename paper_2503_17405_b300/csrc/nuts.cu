@@ -29,6 +29,7 @@ enum NutsState : int { N_INIT = 0, N_DOUBLE = 1, N_INTEGRATE = 2, N_CHECK = 3, N
 enum NutsVec : int { V_GX = 0, V_XL, V_PL, V_GL, V_XR, V_PR, V_GR, V_RHO, V_XP, V_GP, NV };
 enum NutsSc : int { S_LPX = 0, S_LPL, S_LPR, S_LPP, S_H0, S_LOGW, NSC };
 enum NutsInt : int { I_ST = 0, I_J, I_L, I_V, I_NLEAP, NI };
+constexpr int kBatchChains = 8;  // chains per block sharing one batched gradient
 constexpr int kLevels = 10;   // slots for levels 0..9
 constexpr int kWarpsMax = 8;  // warps per block (threads <= 256)
 constexpr int kWsm = 160;     // per-warp scratch: theta (<= 128) + 32 residuals
@@ -279,30 +280,60 @@ struct Sub {
   T lpp, logW;
 };
 
-// INTEGRATE (S3): one leapfrog from the edge on side v, then the merges this leaf completes.
+// INTEGRATE (S3), split around the gradient so that a block can batch it over its chains.
+// First half: the momentum half-kick and the position drift from the edge on side v.
+template <typename T, int E>
+struct Leaf {
+  T xe[E], pe[E], ge[E];
+  T half;
+  bool left;
+};
+
+template <typename T, int E>
+__device__ __forceinline__ void nuts_lf_pre(const NutsView<T>& v, const Chain<T, E>& s, Leaf<T, E>& lf) {
+  lf.left = s.v < 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    lf.xe[e] = lf.left ? s.xl[e] : s.xr[e];
+    lf.pe[e] = lf.left ? s.pl[e] : s.pr[e];
+    lf.ge[e] = lf.left ? s.gl[e] : s.gr[e];
+  }
+  const T es = s.v < 0 ? -v.eps : v.eps;
+  lf.half = T(0.5) * es;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    lf.pe[e] += lf.half * lf.ge[e];
+    lf.xe[e] += es * lf.pe[e];
+  }
+}
+
+template <typename T, int E>
+__device__ int nuts_lf_post(const NutsView<T>& v, const Key& key, int64_t c, int lane, Chain<T, E>& s,
+                            Leaf<T, E>& lf, T lpe, Sub<T, E>& out);
+
+// One leapfrog from the edge on side v, then the merges this leaf completes.
 // Returns 0: keep integrating; 1: subtree complete (summary in `out`); 2: subtree invalid.
 template <typename T, int E>
 __device__ int nuts_integrate(const NutsView<T>& v, const Key& key, int64_t c, int lane, T* wsm,
                               Chain<T, E>& s, Sub<T, E>& out) {
+  Leaf<T, E> lf;
+  nuts_lf_pre<T, E>(v, s, lf);
+  const T lpe = logp_grad<T, E>(v.tg, lf.xe, lf.ge, lane, wsm);
+  return nuts_lf_post<T, E>(v, key, c, lane, s, lf, lpe, out);
+}
+
+// Second half: the closing half-kick with the new gradient, the divergence test and the
+// merges of every block this leaf completes.
+template <typename T, int E>
+__device__ int nuts_lf_post(const NutsView<T>& v, const Key& key, int64_t c, int lane, Chain<T, E>& s,
+                            Leaf<T, E>& lf, T lpe, Sub<T, E>& out) {
   const int d = v.tg.d;
-  T xe[E], pe[E], ge[E];
-  const bool left = s.v < 0;
+  T (&xe)[E] = lf.xe;
+  T (&pe)[E] = lf.pe;
+  T (&ge)[E] = lf.ge;
+  const bool left = lf.left;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    xe[e] = left ? s.xl[e] : s.xr[e];
-    pe[e] = left ? s.pl[e] : s.pr[e];
-    ge[e] = left ? s.gl[e] : s.gr[e];
-  }
-  const T es = s.v < 0 ? -v.eps : v.eps;
-  const T half = T(0.5) * es;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    pe[e] += half * ge[e];
-    xe[e] += es * pe[e];
-  }
-  T lpe = logp_grad<T, E>(v.tg, xe, ge, lane, wsm);
-#pragma unroll
-  for (int e = 0; e < E; ++e) pe[e] += half * ge[e];
+  for (int e = 0; e < E; ++e) pe[e] += lf.half * ge[e];
   s.nleap += 1;
   if (!(lpe == lpe)) { lpe = neg_inf<T>(); atomicOr(v.err, ERR_NONFINITE); }
   // the new leaf becomes the trajectory's edge on side v
@@ -487,6 +518,208 @@ __global__ void __launch_bounds__(256) nuts_fsm_multi_kernel(const NutsView<T>* 
   }
   const NutsView<T> v = views[lo];
   nuts_advance_chain<T, E>(v, item - off[lo], budget, lane, wsm);
+}
+
+// ---- block-batched gradient (logistic regression) ------------------------------------------------------
+// Every FSM step makes exactly one gradient evaluation per chain, so the C chains of a block
+// share one evaluation: eta = X Theta (n x C) with rows split over the threads (4 rows x C chains
+// register tile per thread, X^T read as 4-row vectors), r = y - sigmoid(eta), then
+// g = X^T R (d x C) with (coordinate, row-range) pairs split over the threads, and the prior
+// term -theta.  Rows are processed in chunks of 4 x blockDim rows through shared memory.
+template <typename T, int C>
+struct GradSmem {
+  T* th;     // [128][C] positions of the block's chains
+  T* G;      // [128][C] gradients
+  T* lp;     // [C] log densities
+  T* R;      // [4 * 32 C][C] residuals of one row chunk
+  T* part;   // [32 C][C] per-thread partial gradients
+  T* lpart;  // [C][C] per-warp partial log densities
+};
+
+template <typename T, int C>
+__device__ __forceinline__ GradSmem<T, C> grad_smem(T* base) {
+  constexpr int NT = 32 * C;
+  GradSmem<T, C> g;
+  g.th = base;
+  g.G = g.th + 128 * C;
+  g.lp = g.G + 128 * C;
+  g.R = g.lp + C;
+  g.part = g.R + 4 * NT * C;
+  g.lpart = g.part + NT * C;
+  return g;
+}
+
+template <typename T, int C>
+constexpr size_t grad_smem_bytes() {
+  constexpr int NT = 32 * C;
+  return sizeof(T) * ((size_t)128 * C * 2 + C + 4 * NT * C + NT * C + C * C);
+}
+
+template <typename T, int C>
+__device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>& sm) {
+  constexpr int NT = 32 * C;
+  constexpr int RPT = 4;
+  constexpr int RC = RPT * NT;
+  const int n = tg.n_data, d = tg.d, np = tg.n_pad;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int nsub = NT / d;
+  const int kk = t % d, sub = t / d;
+  const bool c_role = sub < nsub;
+  T gacc[C], lpacc[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) { gacc[c] = T(0); lpacc[c] = T(0); }
+  for (int i0 = 0; i0 < n; i0 += RC) {
+    // eta for rows ib .. ib+3 and all C chains
+    const int ib = i0 + RPT * t;
+    T eta[RPT][C];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) eta[r][c] = T(0);
+    if (ib < np) {
+      for (int k = 0; k < d; ++k) {
+        const T* xr = tg.XT + (size_t)k * np + ib;
+        T x4[RPT];
+        if constexpr (sizeof(T) == 4) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(xr));
+          x4[0] = f.x; x4[1] = f.y; x4[2] = f.z; x4[3] = f.w;
+        } else {
+          const double2 a = __ldg(reinterpret_cast<const double2*>(xr));
+          const double2 b = __ldg(reinterpret_cast<const double2*>(xr) + 1);
+          x4[0] = a.x; x4[1] = a.y; x4[2] = b.x; x4[3] = b.y;
+        }
+        T th[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) th[c] = sm.th[k * C + c];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+          for (int c = 0; c < C; ++c) eta[r][c] = fma(x4[r], th[c], eta[r][c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i = ib + r;
+      const bool ok = i < n;
+      const T yi = ok ? tg.vec[i] : T(0);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T e = eta[r][c];
+        const T sig = T(1) / (T(1) + t_exp(-e));
+        sm.R[(RPT * t + r) * C + c] = ok ? yi - sig : T(0);
+        if (ok) lpacc[c] += yi * e - softplus<T>(e);
+      }
+    }
+    __syncthreads();
+    if (c_role) {
+      const int rows = min(RC, n - i0);
+      const int seg = (rows + nsub - 1) / nsub;
+      const int r_beg = sub * seg, r_end = min(rows, r_beg + seg);
+      for (int rr = r_beg; rr < r_end; ++rr) {
+        const T x = tg.X[(size_t)(i0 + rr) * d + kk];
+#pragma unroll
+        for (int c = 0; c < C; ++c) gacc[c] = fma(x, sm.R[rr * C + c], gacc[c]);
+      }
+    }
+    __syncthreads();
+  }
+  // reduce the gradient partials over row ranges, the log-density partials over warps
+#pragma unroll
+  for (int c = 0; c < C; ++c) sm.part[t * C + c] = c_role ? gacc[c] : T(0);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const T s = group_sum<32>(lpacc[c]);
+    if (lane == 0) sm.lpart[warp * C + c] = s;
+  }
+  __syncthreads();
+  for (int o = t; o < d * C; o += NT) {
+    const int k = o / C, c = o % C;
+    T acc = T(0);
+    for (int sb = 0; sb < nsub; ++sb) acc += sm.part[(sb * d + k) * C + c];
+    sm.G[k * C + c] = acc - sm.th[k * C + c];
+  }
+  if (t < C) {
+    T acc = T(0), sq = T(0);
+    for (int w = 0; w < C; ++w) acc += sm.lpart[w * C + t];
+    for (int k = 0; k < d; ++k) sq = fma(sm.th[k * C + t], sm.th[k * C + t], sq);
+    sm.lp[t] = acc - T(0.5) * sq;
+  }
+  __syncthreads();
+}
+
+// FSM kernel with the batched gradient: C chains per block (one per warp), every warp runs its
+// chain's cheap states, the block evaluates the C gradients together, and every warp finishes
+// its leapfrog step; blocks whose chains are all finished stop early.
+template <typename T, int E, int C>
+__device__ __forceinline__ void nuts_batched_block(const NutsView<T>& v, int64_t block, int budget,
+                                                   const GradSmem<T, C>& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = v.tg.d;
+  const int64_t c = block * C + warp;
+  const bool has_chain = c < v.m;
+  Chain<T, E> s;
+  if (has_chain) chain_load<T, E>(v, c, lane, s);
+  else s.t = v.n;
+  const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  long long steps = 0;
+  for (int b = 0; b < budget; ++b) {
+    const bool act = has_chain && s.t < v.n;
+    if (!__syncthreads_or(act)) break;
+    Leaf<T, E> lf;
+    if (act) {
+      if (s.st == N_INIT) nuts_init<T, E>(v, key, lane, s);
+      if (s.st == N_DOUBLE) nuts_double<T, E>(key, s);
+      nuts_lf_pre<T, E>(v, s, lf);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      if (k < d) sm.th[k * C + warp] = act ? lf.xe[e] : T(0);
+    }
+    __syncthreads();
+    block_logreg_grad<T, C>(v.tg, sm);
+    if (act) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = lane + 32 * e;
+        lf.ge[e] = k < d ? sm.G[k * C + warp] : T(0);
+      }
+      Sub<T, E> sb;
+      const int r = nuts_lf_post<T, E>(v, key, c, lane, s, lf, sm.lp[warp], sb);
+      ++steps;
+      if (r == 1 && nuts_check<T, E>(v, key, s, sb)) continue;
+      if (r != 0) nuts_done<T, E>(v, c, lane, s);
+    }
+  }
+  if (has_chain) {
+    chain_store<T, E>(v, c, lane, s);
+    if (lane == 0) v.steps[c] += steps;
+  }
+}
+
+template <typename T, int E, int C>
+__global__ void __launch_bounds__(32 * C) nuts_fsm_batched_kernel(NutsView<T> v, int budget) {
+  extern __shared__ __align__(16) unsigned char nb_smem[];
+  const GradSmem<T, C> sm = grad_smem<T, C>(reinterpret_cast<T*>(nb_smem));
+  nuts_batched_block<T, E, C>(v, blockIdx.x, budget, sm);
+}
+
+// Fused launch over several logistic-regression NUTS jobs (serving): job k owns blocks
+// off[k] .. off[k+1], so every block's chains share one design matrix.
+template <typename T, int E, int C>
+__global__ void __launch_bounds__(32 * C) nuts_fsm_batched_multi_kernel(const NutsView<T>* views,
+                                                                        const int64_t* off, int njobs,
+                                                                        int budget) {
+  extern __shared__ __align__(16) unsigned char nb_smem[];
+  const GradSmem<T, C> sm = grad_smem<T, C>(reinterpret_cast<T*>(nb_smem));
+  const int64_t item = blockIdx.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  const NutsView<T> v = views[lo];
+  nuts_batched_block<T, E, C>(v, item - off[lo], budget, sm);
 }
 
 // ---- synchronised kernel (Alg. 6 with nested loops) --------------------------------------------------
@@ -690,6 +923,16 @@ static cudaError_t nuts_init_launch(fsmc_job* j, cudaStream_t st) {
 template <typename T, int E>
 static cudaError_t nuts_fsm_launch(fsmc_job* j, cudaStream_t st) {
   const NutsView<T> v = nuts_view<T>(j);
+  if (j->tg->kind == FSMC_TGT_LOGREG && j->tun.lanes_per_chain == 32) {
+    constexpr int C = kBatchChains;
+    auto kern = nuts_fsm_batched_kernel<T, E, C>;
+    const size_t smem = grad_smem_bytes<T, C>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (j->m + C - 1) / C;
+    kern<<<(unsigned)blocks, 32 * C, smem, st>>>(v, j->tun.steps_per_launch);
+    return cudaGetLastError();
+  }
   const int threads = j->tun.threads_per_block;
   const int64_t blocks = (j->m * 32 + threads - 1) / threads;
   nuts_fsm_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, j->tun.steps_per_launch);
@@ -755,15 +998,30 @@ static cudaError_t nuts_multi_launch_t(const std::vector<fsmc_job*>& jobs, Multi
     std::memcpy(hs + k * vb, &v, vb);
     hoff[k + 1] = hoff[k] + jobs[k]->m;
   }
+  const bool batched = jobs[0]->tg->kind == FSMC_TGT_LOGREG && jobs[0]->tun.lanes_per_chain == 32;
+  if (batched) {  // offsets in blocks of kBatchChains chains, as the single-job launch uses
+    hoff[0] = 0;
+    for (int k = 0; k < nj; ++k) hoff[k + 1] = hoff[k] + (jobs[k]->m + kBatchChains - 1) / kBatchChains;
+  }
   const size_t bytes = views_bytes + (nj + 1) * sizeof(int64_t);
   cudaError_t e = cudaMemcpyAsync(b.d_buf, hs, bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
+  const NutsView<T>* dv = (const NutsView<T>*)b.d_buf;
+  const int64_t* doff = (const int64_t*)((char*)b.d_buf + views_bytes);
+  if (batched) {
+    constexpr int C = kBatchChains;
+    auto kern = nuts_fsm_batched_multi_kernel<T, E, C>;
+    const size_t smem = grad_smem_bytes<T, C>();
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)hoff[nj], 32 * C, smem, st>>>(dv, doff, nj, jobs[0]->tun.steps_per_launch);
+    return cudaGetLastError();
+  }
   const int threads = 128;
   const int64_t total = hoff[nj];
   const int64_t blocks = (total * 32 + threads - 1) / threads;
-  nuts_fsm_multi_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(
-      (const NutsView<T>*)b.d_buf, (const int64_t*)((char*)b.d_buf + views_bytes), nj, total,
-      jobs[0]->tun.steps_per_launch);
+  nuts_fsm_multi_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(dv, doff, nj, total,
+                                                                    jobs[0]->tun.steps_per_launch);
   return cudaGetLastError();
 }
 

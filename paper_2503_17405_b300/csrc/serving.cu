@@ -117,7 +117,8 @@ void scheduler_main(fsmc_engine* e) {
     for (fsmc_job* j : active) {
       if (j->serve_mode != FSMC_MODE_FSM) continue;
       long long key = ((long long)j->algo << 40) | ((long long)j->prec << 32);
-      key |= j->algo == FSMC_ESS ? (long long)ess_job_group(j) : (long long)nuts_group_E(j->d);
+      key |= j->algo == FSMC_ESS ? (long long)ess_job_group(j)
+                                 : (long long)nuts_group_E(j->d) | ((long long)j->tg->kind << 8);
       if (j->algo == FSMC_DR) key |= 1LL << 20;
       groups[key].push_back(j);
     }

@@ -46,17 +46,22 @@ def test_fp64_gauss_diag_matches_oracle(eng, mode):
     job.close()
 
 
-def test_fp64_logreg_and_funnel_match_oracle(eng):
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_logreg_and_funnel_match_oracle(eng, mode):
     w = W.logreg(100, 5)
     nuts = {"eps": 0.05, "max_depth": 10, "max_dH": 1000.0}
     m, n = 32, 100
     x0 = W.x0_logreg(w, m)
-    job = _run(eng, "logreg", 5, w["params"], m, n, x0, "fp64", nuts, n_data=100)
+    job = _run(eng, "logreg", 5, w["params"], m, n, x0, "fp64", nuts, mode, n_data=100)
     ref = _oracle("logreg", w["params"], x0, n, nuts, n_data=100)
-    counts, depth, _ = job.loop_counts()
+    counts, depth, steps = job.loop_counts()
     compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
     assert np.array_equal(depth, ref["aux"])
+    if mode == "fsm":
+        assert np.array_equal(steps, counts.sum(1))
     job.close()
+    if mode == "sync":
+        return
     nuts = {"eps": 0.2, "max_depth": 6, "max_dH": 1000.0}
     x0 = W.x0_funnel_exact(32)
     job = _run(eng, "funnel", 10, None, 32, 100, x0, "fp64", nuts)
@@ -94,7 +99,10 @@ def test_fp32_logreg_matches_oracle_until_branch_flip(eng):
     job.close()
 
 
-def test_sync_and_fsm_identical_fp32(eng):
+def test_sync_and_fsm_agree_fp32(eng):
+    # the FSM kernel batches the logistic gradient over a block's chains, the synchronised
+    # kernel evaluates it per warp: same arithmetic, different summation order, so the two
+    # agree to the FP32 tolerance rather than bit for bit
     w = W.logreg(1000, 25)
     nuts = {"eps": 0.05, "max_depth": 10, "max_dH": 1000.0}
     m, n = 256, 20
@@ -103,8 +111,8 @@ def test_sync_and_fsm_identical_fp32(eng):
     b = _run(eng, "logreg", 25, w["params"], m, n, x0, "fp32", nuts, "sync", n_data=1000)
     ca, da, _ = a.loop_counts()
     cb, db, _ = b.loop_counts()
-    assert np.array_equal(ca, cb) and np.array_equal(da, db)
-    assert np.array_equal(a.samples(), b.samples())
+    r = compare(a.samples(), ca, b.samples(), cb, "fp32")
+    assert r["flipped"] <= m // 8
     st = b.stats()
     # the nested synchronised loops run at least max_j N_ij leapfrog iterations per sample
     assert st["sync_iterations"] >= int(cb.max(0).sum())
