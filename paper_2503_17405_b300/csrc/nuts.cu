@@ -597,28 +597,52 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
           for (int c = 0; c < C; ++c) eta[r][c] = fma(x4[r], th[c], eta[r][c]);
       }
     }
+    // residuals, chain-major [C][RC]: each thread stores its 4 rows of a chain as one vector
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int i = ib + r;
-      const bool ok = i < n;
-      const T yi = ok ? tg.vec[i] : T(0);
+    for (int c = 0; c < C; ++c) {
+      T rv[RPT];
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
+      for (int r = 0; r < RPT; ++r) {
+        const int i = ib + r;
+        const bool ok = i < n;
+        const T yi = ok ? tg.vec[i] : T(0);
         const T e = eta[r][c];
         const T sig = T(1) / (T(1) + t_exp(-e));
-        sm.R[(RPT * t + r) * C + c] = ok ? yi - sig : T(0);
+        rv[r] = ok ? yi - sig : T(0);
         if (ok) lpacc[c] += yi * e - softplus<T>(e);
+      }
+      T* dst = sm.R + c * RC + RPT * t;
+      if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+      } else {
+        reinterpret_cast<double2*>(dst)[0] = make_double2(rv[0], rv[1]);
+        reinterpret_cast<double2*>(dst)[1] = make_double2(rv[2], rv[3]);
       }
     }
     __syncthreads();
     if (c_role) {
+      // rows of this chunk in 4-row groups: g_k += X^T[k][rows] . R[c][rows]
       const int rows = min(RC, n - i0);
-      const int seg = (rows + nsub - 1) / nsub;
-      const int r_beg = sub * seg, r_end = min(rows, r_beg + seg);
-      for (int rr = r_beg; rr < r_end; ++rr) {
-        const T x = tg.X[(size_t)(i0 + rr) * d + kk];
+      const int groups = (rows + RPT - 1) / RPT;
+      const int gseg = (groups + nsub - 1) / nsub;
+      const int g_beg = sub * gseg, g_end = min(groups, g_beg + gseg);
+      const T* xk = tg.XT + (size_t)kk * np + i0;
+      for (int gi = g_beg; gi < g_end; ++gi) {
+        T x4[RPT];
+        if constexpr (sizeof(T) == 4) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(xk + RPT * gi));
+          x4[0] = f.x; x4[1] = f.y; x4[2] = f.z; x4[3] = f.w;
+        } else {
+          const double2 a = __ldg(reinterpret_cast<const double2*>(xk + RPT * gi));
+          const double2 b = __ldg(reinterpret_cast<const double2*>(xk + RPT * gi) + 1);
+          x4[0] = a.x; x4[1] = a.y; x4[2] = b.x; x4[3] = b.y;
+        }
 #pragma unroll
-        for (int c = 0; c < C; ++c) gacc[c] = fma(x, sm.R[rr * C + c], gacc[c]);
+        for (int c = 0; c < C; ++c) {
+          const T* rc = sm.R + c * RC + RPT * gi;
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) gacc[c] = fma(x4[r], rc[r], gacc[c]);
+        }
       }
     }
     __syncthreads();
