@@ -148,6 +148,22 @@ def oracle_throughput(cfg, target_s=10.0):
             "sample": f"{m} chains x {n_s} samples of {cfg['name']} (FP64, {t:.1f} s)"}
 
 
+# ---- multi-GPU aggregation (independent chains per rank: weak scaling) -----------------------------
+def max_over_ranks(value, dist=None, device="cpu"):
+    """Slowest rank's timed region: the all-reduce MAX is the only collective of the run."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, chains, samples, total_ms):
+    """Samples of all ranks' jobs divided by the slowest rank's time."""
+    return world * steps * chains * samples / (total_ms / 1e3)
+
+
 # ---- our arm ---------------------------------------------------------------------------------------
 def run_ours(args, rank, world):
     import torch
@@ -201,12 +217,8 @@ def run_ours(args, rank, world):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(fsm_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * m * n / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(fsm_ms), dist, "cuda")
+    value = job_throughput(world, args.steps, m, n, total_ms)
 
     # synchronised kernel on the same job (Alg. 6), fewer steps: it is the slow baseline
     sync = None

@@ -153,6 +153,16 @@ fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo algo,
                             const void* algo_params, fsmc_precision prec, int64_t n_chains,
                             int64_t n_samples, const double* x0_host, uint64_t seed,
                             int store_samples, fsmc_job** out);
+/* Autotuner: picks the launch shape for jobs like (t, algo, algo_params, prec, n_chains) by
+ * timing short FSM runs of candidate shapes (lanes per chain, states per launch, ring depth,
+ * threads per block, direction generator) on scratch jobs, and returns the fastest in *best
+ * (lowest device time per FSM state).  The choice is cached in a text file keyed by device
+ * name, sampler, target kind, d, n_data, precision and log2(n_chains): cache_path, else the
+ * file named by $FSMC_TUNE_CACHE, else no cache.  Scratch jobs keep moments only and are
+ * freed before returning.  Errors: EINVAL, EADMIT, ENOMEM, ECUDA. */
+fsmc_status fsmc_autotune(fsmc_engine* e, fsmc_target* t, fsmc_algo algo, const void* algo_params,
+                          fsmc_precision prec, int64_t n_chains, const char* cache_path,
+                          fsmc_tuning* best);
 /* Overrides the launch shape before the first run (EINVAL for unsupported values). */
 fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tuning);
 fsmc_status fsmc_job_get_tuning(const fsmc_job* j, fsmc_tuning* tuning);

@@ -19,17 +19,20 @@ constexpr unsigned kBarrierSpinLimit = 1u << 24;  // ~1-2 s of nanosleep(64) pol
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -----------------------------------
 struct P4 { uint32_t w0, w1, w2, w3; };
 
+// Each round takes one 32x32 -> 64-bit product per multiplier (high and low halves together)
+// and the round keys are the seed key plus multiples of the Weyl constants.
 __device__ __forceinline__ P4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                      uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    c0 = hi1 ^ c1 ^ k0;
-    c1 = lo1;
-    c2 = hi0 ^ c3 ^ k1;
-    c3 = lo0;
+    const uint32_t rk0 = k0 + (uint32_t)r * 0x9E3779B9u;
+    const uint32_t rk1 = k1 + (uint32_t)r * 0xBB67AE85u;
+    const unsigned long long p0 = (unsigned long long)c0 * 0xD2511F53u;
+    const unsigned long long p1 = (unsigned long long)c2 * 0xCD9E8D57u;
+    c0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0;
+    c1 = (uint32_t)p1;
+    c2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1;
+    c3 = (uint32_t)p0;
   }
   return P4{c0, c1, c2, c3};
 }

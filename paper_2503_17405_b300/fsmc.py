@@ -70,6 +70,8 @@ SIGNATURES = [
     ("fsmc_job_create", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
                                        ctypes.c_int64, _dp, ctypes.c_uint64, ctypes.c_int,
                                        ctypes.POINTER(_vp)]),
+    ("fsmc_autotune", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64,
+                                     ctypes.c_char_p, ctypes.POINTER(Tuning)]),
     ("fsmc_job_set_tuning", ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
     ("fsmc_job_get_tuning", ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
     ("fsmc_job_bytes", ctypes.c_size_t, [_vp]),
@@ -147,6 +149,22 @@ class Engine:
     def job(self, target, algo, n_chains, n_samples, x0=None, seed=1, prec="fp32", store=True,
             dr=None, nuts=None, tuning=None):
         return Job(self, target, algo, n_chains, n_samples, x0, seed, prec, store, dr, nuts, tuning)
+
+    def autotune(self, target, algo, n_chains, prec="fp32", dr=None, nuts=None, cache_path=None):
+        """fsmc_autotune: the fastest launch shape for such jobs, as a tuning dict."""
+        ap = None
+        if algo == "dr":
+            dr = dr or {}
+            keep = DRParams(dr.get("n_stages", 3), dr.get("scale0", 1.0), dr.get("factor", 0.5))
+            ap = ctypes.cast(ctypes.byref(keep), _vp)
+        elif algo == "nuts":
+            nuts = nuts or {}
+            keep = NUTSParams(nuts.get("eps", 0.05), nuts.get("max_depth", 10), nuts.get("max_dH", 1000.0))
+            ap = ctypes.cast(ctypes.byref(keep), _vp)
+        t = Tuning()
+        _check(load().fsmc_autotune(self._h, target._h, ALGO[algo], ap, PREC[prec], n_chains,
+                                    cache_path.encode() if cache_path else None, ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def wait_all(self, timeout_s=600.0):
         _check(load().fsmc_wait_all(self._h, timeout_s))
