@@ -187,7 +187,8 @@ def run_ours(args, rank, world):
     tuning = {"profile_kernels": 1}
     job = eng.job(tg, cfg["algo"], m, n, x0=cfg["x0"], seed=1 + rank, prec=cfg["prec"], store=True,
                   dr=dr, nuts=nuts, tuning=tuning)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # a real stream: graph capture needs one
+    torch.cuda.set_stream(stream)
     sp = stream.cuda_stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 

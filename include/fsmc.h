@@ -102,6 +102,8 @@ typedef struct fsmc_tuning {
   int profile_kernels;   /* 1: time every launch with CUDA events (see fsmc_stats)        */
   int generator;         /* ESS directions nu = L z: 0 auto, 1 CUDA cores, 2 tensor cores
                             (tcgen05; FP32 jobs with d <= 256)                            */
+  int pipelined;         /* ESS whole runs: 0 auto (on), 1 refill directions for the next
+                            round on a second stream while the FSM kernel runs, 2 off      */
 } fsmc_tuning;
 
 /* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */

@@ -271,6 +271,7 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.ring_slots) tu.ring_slots = 32;
     if (!tu.threads_per_block) tu.threads_per_block = 256;
     if (!tu.generator) tu.generator = (j->prec == FSMC_FP32 && j->d <= 256) ? 2 : 1;
+    if (!tu.pipelined) tu.pipelined = 1;
   } else if (j->algo == FSMC_DR) {
     tu.lanes_per_chain = 1;
     if (!tu.steps_per_launch) tu.steps_per_launch = 256;
@@ -307,6 +308,7 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
     j->o_gen = L.take(2 * m * 4);
     j->o_nu = L.take(m * (size_t)j->W * j->dstride * es);
     j->o_gencols = L.take(8);
+    j->o_win = L.take(2 * m * 4);
   } else if (j->algo == FSMC_DR) {
     j->o_ell = L.take(m * es);        // log pi(x)
     j->o_y = L.take(2 * m * d * es);  // y1, y2
@@ -377,6 +379,7 @@ EssView<T> ess_view(const fsmc_job* j) {
   v.gen_hi = v.gen_lo + j->m;
   v.nu = (T*)(b + j->o_nu);
   v.gen_cols = (unsigned long long*)(b + j->o_gencols);
+  v.own_window = 1;
   return v;
 }
 
@@ -514,6 +517,7 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (t.steps_per_launch < 0 || t.ring_slots < 0 || t.ring_slots > 4096)
     return fsmc_fail(FSMC_EINVAL, "negative steps / ring slots");
   if (t.generator < 0 || t.generator > 2) return fsmc_fail(FSMC_EINVAL, "generator must be 0, 1 or 2");
+  if (t.pipelined < 0 || t.pipelined > 2) return fsmc_fail(FSMC_EINVAL, "pipelined must be 0, 1 or 2");
   if (t.generator == 2 && (j->algo != FSMC_ESS || j->prec != FSMC_FP32 || j->d > 256))
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   j->tun = t;
@@ -604,8 +608,75 @@ static fsmc_status capture_rounds(fsmc_job* j, int rounds, cudaStream_t st) {
   return FSMC_OK;
 }
 
+// Whole ESS run with the direction refill of round r+1 on a second stream, overlapping the FSM
+// kernel of round r.  Refill windows alternate between two buffers: buffer p holds the window
+// the FSM kernel of a round-p round consumes (it reads only its upper bound), buffer p^1 the
+// one being refilled.  The refill stream waits for the FSM kernel of round r-1 before writing
+// buffer p^1, so it runs at most one round ahead.
+template <typename T>
+static fsmc_status run_fsm_pipelined(fsmc_job* j, cudaStream_t st) {
+  if (!j->side) {
+    CK(cudaStreamCreateWithFlags(&j->side, cudaStreamNonBlocking));
+    for (int p = 0; p < 2; ++p) {
+      CK(cudaEventCreateWithFlags(&j->ev_gen[p], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&j->ev_fsm[p], cudaEventDisableTiming));
+    }
+  }
+  cudaStream_t sb = j->side;
+  EssView<T> v[2];
+  v[0] = ess_view<T>(j);  // buffer 0: the job's own window arrays
+  v[1] = v[0];
+  v[1].gen_lo = (int*)(j->dev + j->o_win);
+  v[1].gen_hi = v[1].gen_lo + j->m;
+  v[0].own_window = v[1].own_window = 0;
+  const fsmc_tuning& tu = j->tun;
+  // buffer 0 already holds the next window (set at init or by the last round of a previous run)
+  CK(cudaEventRecord(j->ev_fsm[1], st));  // the caller's prior work on st
+  CK(cudaStreamWaitEvent(sb, j->ev_fsm[1], 0));
+  {
+    ProfScope p(j, 0, sb);
+    CK(ess_generate<T>(j, v[0], sb));
+  }
+  CK(cudaEventRecord(j->ev_gen[0], sb));
+  int p = 0;
+  int64_t r = 0;
+  while (true) {
+    CK(cudaStreamWaitEvent(st, j->ev_gen[p], 0));
+    {
+      ProfScope ps(j, 1, st);
+      CK(launch_ess_fsm<T>(v[p], tu.lanes_per_chain, tu.steps_per_launch, tu.threads_per_block, st));
+    }
+    CK(cudaEventRecord(j->ev_fsm[p], st));
+    if (r >= 1) CK(cudaStreamWaitEvent(sb, j->ev_fsm[p ^ 1], 0));
+    CK(launch_ess_window<T>(v[p ^ 1], v[p].gen_hi, sb));
+    {
+      ProfScope ps(j, 0, sb);
+      CK(ess_generate<T>(j, v[p ^ 1], sb));
+    }
+    CK(cudaEventRecord(j->ev_gen[p ^ 1], sb));
+    j->launches += 3;
+    ++r;
+    p ^= 1;
+    if (r % 8 == 0) {
+      int done = 0, err = 0;
+      fsmc_status s = read_done(j, st, &done, &err);
+      if (s != FSMC_OK) return s;
+      if (done >= j->m) break;
+    }
+  }
+  // the last refill may still run on the side stream: join it, and leave the job's own
+  // window arrays consistent for a later partial run
+  CK(cudaStreamWaitEvent(st, j->ev_gen[p], 0));
+  if (p == 1) {
+    CK(cudaMemcpyAsync(v[0].gen_lo, v[1].gen_lo, j->m * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(v[0].gen_hi, v[1].gen_hi, j->m * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  }
+  return FSMC_OK;
+}
+
 template <typename T>
 static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
+  if (j->algo == FSMC_ESS && max_steps <= 0 && j->tun.pipelined == 1) return run_fsm_pipelined<T>(j, st);
   const int check_every = 8;
   int64_t rounds_limit = -1;
   if (max_steps > 0) rounds_limit = (max_steps + j->tun.steps_per_launch - 1) / j->tun.steps_per_launch;
@@ -1022,6 +1093,11 @@ extern "C" void fsmc_job_destroy(fsmc_job* j) {
   fsmc_engine* e = j->e;
   for (cudaEvent_t ev : j->event_pool) cudaEventDestroy(ev);
   if (j->graph_exec) cudaGraphExecDestroy(j->graph_exec);
+  for (int p = 0; p < 2; ++p) {
+    if (j->ev_gen[p]) cudaEventDestroy(j->ev_gen[p]);
+    if (j->ev_fsm[p]) cudaEventDestroy(j->ev_fsm[p]);
+  }
+  if (j->side) cudaStreamDestroy(j->side);
   if (j->dev) {
     cudaSetDevice(e->device);
     cudaFree(j->dev);

@@ -84,6 +84,10 @@ struct fsmc_job {
   // captured burst of FSM rounds (replayed by run_fsm when kernel profiling is off)
   cudaGraphExec_t graph_exec = nullptr;
   int graph_rounds = 0;
+  // pipelined ESS rounds: second stream and the events ordering the two
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_fsm[2] = {nullptr, nullptr};
+  size_t o_win = 0;  // second refill-window buffer [2][m]
   // serving
   bool submitted = false;
   fsmc_mode serve_mode = FSMC_MODE_FSM;

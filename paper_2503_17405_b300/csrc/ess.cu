@@ -317,8 +317,10 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
       v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
       v.t[c] = t; v.k[c] = st; v.s[c] = s;
       v.steps[c] += steps;
-      v.gen_lo[c] = hi;
-      v.gen_hi[c] = min(t + v.W, v.n);
+      if (v.own_window) {
+        v.gen_lo[c] = hi;
+        v.gen_hi[c] = min(t + v.W, v.n);
+      }
       if (err) atomicOr(v.err, err);
     }
   }
@@ -533,6 +535,28 @@ template cudaError_t launch_moments_from_samples<float>(const float*, const int*
                                                         cudaStream_t);
 template cudaError_t launch_moments_from_samples<double>(const double*, const int*, int64_t, int, int, double*,
                                                          cudaStream_t);
+
+// Refill window of the next pipelined round.  It runs while the FSM kernel of the current
+// round advances t, and may read either the old or the new t: the directions it asks for are
+// those of samples hi_cur .. t + W - 1, whose ring slots belong to samples below t, which the
+// running FSM kernel no longer reads.
+template <typename T>
+__global__ void ess_window_kernel(EssView<T> v, const int* hi_cur) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.m) return;
+  const int lo = hi_cur[c];
+  const int t = *(volatile const int*)&v.t[c];
+  v.gen_lo[c] = lo;
+  v.gen_hi[c] = max(lo, min(t + v.W, v.n));
+}
+
+template <typename T>
+cudaError_t launch_ess_window(const EssView<T>& v, const int* hi_cur, cudaStream_t st) {
+  ess_window_kernel<T><<<(unsigned)((v.m + 255) / 256), 256, 0, st>>>(v, hi_cur);
+  return cudaGetLastError();
+}
+template cudaError_t launch_ess_window<float>(const EssView<float>&, const int*, cudaStream_t);
+template cudaError_t launch_ess_window<double>(const EssView<double>&, const int*, cudaStream_t);
 
 __global__ void fill_int_kernel(int* p, int64_t n, int value) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -40,6 +40,7 @@ struct EssView : ChainsView<T> {
   int* gen_lo; int* gen_hi;   // [m] ring fill window [gen_lo, gen_hi) in samples
   T* nu;                 // [m][W][dstride] pre-generated ellipse directions
   unsigned long long* gen_cols;  // directions generated so far (statistics)
+  int own_window;        // 1: the FSM kernel sets the next refill window itself
 };
 
 template <typename T>
@@ -87,6 +88,10 @@ template <typename T>
 cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st);
 
 cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st);
+// Next refill window for the pipelined ESS rounds: lo = hi_cur, hi = max(lo, min(t + W, n)),
+// written to v's gen_lo / gen_hi.
+template <typename T>
+cudaError_t launch_ess_window(const EssView<T>& v, const int* hi_cur, cudaStream_t st);
 // Per-chain Kahan sums of x and x^2 over the first t[c] stored samples: out [4][m][d]
 // (sum, compensation, sum of squares, compensation).
 template <typename T>

@@ -142,6 +142,7 @@ extern "C" fsmc_status fsmc_ess_run_static(int target_kind, int d, const float* 
   v.gen_hi = v.gen_lo + n_chains;
   v.nu = (float*)(b + lay.nu);
   v.gen_cols = (unsigned long long*)((int*)(b + lay.misc) + 2);
+  v.own_window = 1;
 
 #define CKS(expr)                                             \
   do {                                                        \

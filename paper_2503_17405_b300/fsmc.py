@@ -37,7 +37,8 @@ class NUTSParams(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("lanes_per_chain", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("ring_slots", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-                ("profile_kernels", ctypes.c_int), ("generator", ctypes.c_int)]
+                ("profile_kernels", ctypes.c_int), ("generator", ctypes.c_int),
+                ("pipelined", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -220,7 +221,8 @@ class Job:
         if tuning:
             t = Tuning(tuning.get("lanes_per_chain", 0), tuning.get("steps_per_launch", 0),
                        tuning.get("ring_slots", 0), tuning.get("threads_per_block", 0),
-                       tuning.get("profile_kernels", 0), tuning.get("generator", 0))
+                       tuning.get("profile_kernels", 0), tuning.get("generator", 0),
+                       tuning.get("pipelined", 0))
             _check(load().fsmc_job_set_tuning(self._h, ctypes.byref(t)))
 
     @property
