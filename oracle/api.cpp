@@ -17,6 +17,7 @@ void ora_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) 
 }
 
 double ora_uniform(uint32_t hi, uint32_t lo) { return uniform(hi, lo); }
+double ora_uniform32(uint32_t w) { return uniform32(w); }
 
 void ora_normals(uint64_t seed, uint32_t chain, uint32_t sample, uint32_t tag, uint32_t draw0,
                  int d, double* z) {

@@ -38,9 +38,11 @@ struct Stream {
 
 // Uniform in (0,1) from two 32-bit words: ((hi:lo >> 12) + 1/2) * 2^-52.
 double uniform(uint32_t hi, uint32_t lo);
-// Box-Muller pair from one block: r = sqrt(-2 ln u(w0,w1)), phi = 2 pi u(w2,w3).
-void normal_pair(const Block& b, double* z0, double* z1);
-// z[0..d) from blocks draw0, draw0+1, ... of stream `tag` (normals 2q, 2q+1 from block q).
+// Uniform in (0,1) from one 32-bit word: (w + 1/2) * 2^-32.
+double uniform32(uint32_t w);
+// Four normals from one block: Box-Muller on (u32(w0), u32(w1)) and on (u32(w2), u32(w3)).
+void normal_quad(const Block& b, double* z);
+// z[0..d) from blocks draw0, draw0+1, ... of stream `tag` (normals 4q .. 4q+3 from block q).
 void normals(const Stream& s, uint32_t tag, uint32_t draw0, int d, double* z);
 
 // ---- targets ------------------------------------------------------------------

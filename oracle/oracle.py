@@ -44,6 +44,8 @@ def lib():
             L.ora_philox4x32_10.argtypes = [up, up, up]
             L.ora_uniform.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
             L.ora_uniform.restype = ctypes.c_double
+            L.ora_uniform32.argtypes = [ctypes.c_uint32]
+            L.ora_uniform32.restype = ctypes.c_double
             L.ora_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, dp]
             L.ora_logp.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
@@ -96,6 +98,10 @@ def philox4x32_10(ctr, key):
 
 def uniform(hi, lo):
     return lib().ora_uniform(hi, lo)
+
+
+def uniform32(w):
+    return lib().ora_uniform32(w)
 
 
 def normals(seed, chain, sample, tag, draw0, d):

@@ -32,22 +32,27 @@ double uniform(uint32_t hi, uint32_t lo) {
   return ((double)v + 0.5) * 0x1p-52;        // exact; in [2^-53, 1 - 2^-53]
 }
 
-void normal_pair(const Block& b, double* z0, double* z1) {
+double uniform32(uint32_t w) {
+  return ((double)w + 0.5) * 0x1p-32;        // exact; in [2^-33, 1 - 2^-33]
+}
+
+// Four normals from one block: the Box-Muller transform of (u(w0), u(w1)) and of
+// (u(w2), u(w3)), with r = sqrt(-2 ln u_a) and phi = 2 pi u_b giving (r cos phi, r sin phi).
+void normal_quad(const Block& b, double* z) {
   const double kPi = 3.14159265358979323846;
-  double u1 = uniform(b.w[0], b.w[1]);
-  double u2 = uniform(b.w[2], b.w[3]);
-  double r = std::sqrt(-2.0 * std::log(u1));
-  double phi = 2.0 * kPi * u2;
-  *z0 = r * std::cos(phi);
-  *z1 = r * std::sin(phi);
+  for (int h = 0; h < 2; ++h) {
+    double r = std::sqrt(-2.0 * std::log(uniform32(b.w[2 * h])));
+    double phi = 2.0 * kPi * uniform32(b.w[2 * h + 1]);
+    z[2 * h] = r * std::cos(phi);
+    z[2 * h + 1] = r * std::sin(phi);
+  }
 }
 
 void normals(const Stream& s, uint32_t tag, uint32_t draw0, int d, double* z) {
-  for (int q = 0; 2 * q < d; ++q) {
-    double a, b;
-    normal_pair(s.block(tag, draw0 + (uint32_t)q), &a, &b);
-    z[2 * q] = a;
-    if (2 * q + 1 < d) z[2 * q + 1] = b;
+  for (int q = 0; 4 * q < d; ++q) {
+    double v[4];
+    normal_quad(s.block(tag, draw0 + (uint32_t)q), v);
+    for (int i = 0; i < 4 && 4 * q + i < d; ++i) z[4 * q + i] = v[i];
   }
 }
 

@@ -12,7 +12,7 @@ static const double kPi = 3.14159265358979323846;
 static const double kNegInf = -std::numeric_limits<double>::infinity();
 static const int kMaxShrinks = 10000;  // safety cap; never reached in double precision
 
-static int ceil_half(int d) { return (d + 1) / 2; }
+static int normal_blocks(int d) { return (d + 3) / 4; }  // four normals per Philox block
 
 // ------------------------------------------------------------------------------------
 // Elliptical slice sampling (appendix Alg. 8), with these readings:
@@ -22,14 +22,14 @@ static int ceil_half(int d) { return (d + 1) / 2; }
 //  * acceptance is strict (>), ties shrink;
 //  * N counts bracket shrinks (the paper's "sub-iterations"), so N can be 0.
 // Random numbers for sample i of a chain (tag 0):
-//   draws 0..D-1       : z for nu = L z   (D = ceil(d/2), Box-Muller pairs)
+//   draws 0..D-1       : z for nu = L z   (D = ceil(d/4), four normals per draw)
 //   draw D, words 0-1  : u for the threshold log y = log f(x) + log u
 //   draw D, words 2-3  : u' for the initial angle theta = 2 pi u'
 //   draw D+1+s         : u_s for the s-th shrink, theta ~ U[theta_min, theta_max]
 int ess_transition(const Target& t, const Stream& s, double* x, double* ell,
                    double* trace, int trace_cap) {
   const int d = t.d;
-  const int D = ceil_half(d);
+  const int D = normal_blocks(d);
   const double* L = t.prior_chol();
   std::vector<double> z(d), nu(d, 0.0), xp(d);
 
@@ -141,7 +141,7 @@ double dr_stage_log_alpha(int k, int d, const double* x, const double* ys, const
 // draws k(D+1) .. k(D+1)+D-1 and its acceptance uniform from words 0-1 of draw k(D+1)+D.
 int dr_transition(const Target& t, const Stream& s, const DRParams& P, double* x, double* lp) {
   const int d = t.d;
-  const int D = ceil_half(d);
+  const int D = normal_blocks(d);
   const int K = P.n_stages;
   std::vector<double> ys((size_t)K * d), lps(K + 1), sig(K), eps(d);
   for (int k = 0; k < K; ++k) sig[k] = P.scale0 * std::pow(P.factor, (double)k);

@@ -124,21 +124,17 @@ template <typename T, int E>
 __device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E],
                                         T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, int& err) {
   const int d = v.tg.d;
-  const int D = (d + 1) / 2;
+  const int D = (d + 3) / 4;  // Philox blocks per stage (four normals each)
   const uint32_t base = (uint32_t)(k * (D + 1));
   T y[E];
   const T sg = v.sig[k];
 #pragma unroll
-  for (int q = 0; q < (E + 1) / 2; ++q) {
-    if (q < D) {
-      T z0, z1;
-      Conv<T>::normal_pair(key.block((uint32_t)t, 0, base + q), z0, z1);
-      y[2 * q] = fma(sg, z0, x[2 * q]);
-      if (2 * q + 1 < E) y[2 * q + 1] = fma(sg, z1, x[2 * q + 1]);
-    } else {
-      y[2 * q] = T(0);
-      if (2 * q + 1 < E) y[2 * q + 1] = T(0);
-    }
+  for (int q = 0; q < (E + 3) / 4; ++q) {
+    T z[4] = {T(0), T(0), T(0), T(0)};
+    if (q < D) Conv<T>::normal_quad(key.block((uint32_t)t, 0, base + q), z);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (4 * q + i < E) y[4 * q + i] = q < D ? fma(sg, z[i], x[4 * q + i]) : T(0);
   }
   T lpy = full_logp<T, E>(v.tg, y);
   if (!(lpy == lpy)) { lpy = neg_inf<T>(); err |= ERR_NONFINITE; }

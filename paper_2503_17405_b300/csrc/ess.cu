@@ -60,7 +60,7 @@ __device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx,
 
   const int ty = tid >> 3, tx = tid & 7;
   const int warp = tid >> 5;
-  const int D = (d + 1) / 2;
+  const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const int kmax = min(d, r0 + BM);
   // staging roles: z column zc and normals 4*zp .. 4*zp+3 of the chunk; L row lr
   const int zc = tid & 63, zp = tid >> 6;
@@ -70,14 +70,15 @@ __device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx,
   const bool vec_rows = (d % 4) == 0 && sizeof(T) == 4;
 
   auto stage = [&](int buf, int q0) {
+    {
+      const int blk = q0 / 4 + zp;  // one Philox block: normals q0 + 4 zp .. q0 + 4 zp + 3
+      T z[4] = {T(0), T(0), T(0), T(0)};
+      if (z_smp >= 0 && blk < D) Conv<T>::normal_quad(zkey.block((uint32_t)z_smp, 0, (uint32_t)blk), z);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int blk = q0 / 2 + 2 * zp + h;
-      T z0 = T(0), z1 = T(0);
-      if (z_smp >= 0 && blk < D) Conv<T>::normal_pair(zkey.block((uint32_t)z_smp, 0, (uint32_t)blk), z0, z1);
-      const int kk = 4 * zp + 2 * h;
-      Bs[buf][kk][zc] = (q0 + kk < d) ? z0 : T(0);
-      Bs[buf][kk + 1][zc] = (q0 + kk + 1 < d) ? z1 : T(0);
+      for (int i = 0; i < 4; ++i) {
+        const int kk = 4 * zp + i;
+        Bs[buf][kk][zc] = (q0 + kk < d) ? z[i] : T(0);
+      }
     }
     if (lr < d && q0 <= lr) {
       const T* row = v.tg.L + (size_t)lr * d + q0;
@@ -174,6 +175,19 @@ __device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E
   return T(0);  // TGT_FLAT
 }
 
+// Slice threshold log y = log f(x) + log u.  In single precision a u within ~1e-5 of 1 makes
+// the sum round back to log f(x); the bracket would then shrink onto theta = 0 without ever
+// finding log f(x') > log y.  The threshold is therefore kept at least one ulp below log f(x),
+// which moves it by at most one ulp and makes theta -> 0 always accept.
+template <typename T>
+__device__ __forceinline__ T ess_threshold(T ell, T log_u) {
+  T logy = ell + log_u;
+  if constexpr (sizeof(T) == 4) {
+    if (!(logy < ell) && ell > -INFINITY) logy = nextafterf(ell, -INFINITY);
+  }
+  return logy;
+}
+
 // sin and cos of a bracket angle th in (-2 pi, 2 pi).  Single precision reduces th to
 // [-pi, pi], where __sincosf is accurate to ~5e-7; double precision calls sincos.
 template <typename T>
@@ -228,7 +242,7 @@ __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, 
 template <typename T, int G, int E>
 __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c, int budget, int lane) {
   const int d = v.tg.d;
-  const int D = (d + 1) / 2;
+  const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   {
     T x[E], nu[E], xp[E], yv[E];
 #pragma unroll
@@ -275,7 +289,7 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
         for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) nu[e] = src[k]; }
         cbase = -(1 << 30);  // a new sample: its blocks are not cached yet
         const P4 r = fetch(0);
-        logy = ell + Conv<T>::log_u(r.w0, r.w1);
+        logy = ess_threshold<T>(ell, Conv<T>::log_u(r.w0, r.w1));
         th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
         thmin = th - T(kTwoPi);
         thmax = th;
@@ -387,7 +401,7 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   const int d = v.tg.d;
-  const int D = (d + 1) / 2;
+  const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   __shared__ unsigned blk_active;
   int iter = 0;
@@ -420,7 +434,7 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
         int s;
         if (first) {  // INIT (S1)
           const P4 r = key.block((uint32_t)t, 0, (uint32_t)D);
-          logy = v.ell[c] + Conv<T>::log_u(r.w0, r.w1);
+          logy = ess_threshold<T>(v.ell[c], Conv<T>::log_u(r.w0, r.w1));
           th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
           thmin = th - T(kTwoPi);
           thmax = th;

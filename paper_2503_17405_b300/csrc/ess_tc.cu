@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int D = (d + 1) / 2;
+  const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const int nchunks = lay.kpad / TC_KC;
   const int nbx = (int)((v.m + TC_N - 1) / TC_N);
   const int ntiles = nbx * v.W;
@@ -209,29 +209,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         if (!mbar_wait(&bar_mma[s], stage_phase[s])) { s_fail = 1; }
         stage_phase[s] ^= 1u;
       }
-      // z chunk: warp w writes core matrices w, w+16, ... (8 columns x 8 k, 128 contiguous
-      // bytes each); four independent Philox chains per thread
+      // z chunk: a core matrix is 8 columns x 8 k (128 contiguous bytes) = 16 Philox blocks of
+      // four normals; a warp fills two core matrices per pass (lane: core half, column, k half)
       unsigned char* zhi = sB + s * 2 * TC_STAGE;
       unsigned char* zlo = zhi + TC_STAGE;
 #pragma unroll
-      for (int it = 0; it < 64 / (TC_THREADS / 32); ++it) {
-        const int core = warp + (TC_THREADS / 32) * it;
+      for (int it = 0; it < 64 / (2 * (TC_THREADS / 32)); ++it) {
+        const int core = 2 * (warp + (TC_THREADS / 32) * it) + (lane >> 4);
         const int ng = core & 7, kg = core >> 3;
-        const int n = ng * 8 + (lane >> 2);
-        const int qq = lane & 3;
-        const int q = kc * (TC_KC / 2) + kg * 4 + qq;  // Philox draw = normal pair index
+        const int nr = (lane >> 1) & 7, kh = lane & 1;
+        const int n = ng * 8 + nr;
+        const int q = kc * (TC_KC / 4) + kg * 2 + kh;  // Philox draw: normals 4q .. 4q+3
         const int smp = col_sample[n];
-        float z0 = 0.f, z1 = 0.f;
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (smp >= 0 && q < D) {
           const Key key{(uint32_t)(v.chain0 + c0 + n), v.seed_lo, v.seed_hi};
-          Conv<float>::normal_pair(key.block((uint32_t)smp, 0, (uint32_t)q), z0, z1);
-          if (2 * q + 1 >= d) z1 = 0.f;
+          Conv<float>::normal_quad(key.block((uint32_t)smp, 0, (uint32_t)q), z);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (4 * q + i >= d) z[i] = 0.f;
         }
-        const __half h0 = __float2half_rn(z0), h1 = __float2half_rn(z1);
-        const __half l0 = __float2half_rn(z0 - __half2float(h0)), l1 = __float2half_rn(z1 - __half2float(h1));
-        const int off = ng * (TC_KC / 8) * 128 + kg * 128 + (lane >> 2) * 16 + qq * 4;
-        *reinterpret_cast<__half2*>(zhi + off) = __halves2half2(h0, h1);
-        *reinterpret_cast<__half2*>(zlo + off) = __halves2half2(l0, l1);
+        __half h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          h[i] = __float2half_rn(z[i]);
+          l[i] = __float2half_rn(z[i] - __half2float(h[i]));
+        }
+        const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
+        const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
+        const int off = ng * (TC_KC / 8) * 128 + kg * 128 + nr * 16 + kh * 8;
+        *reinterpret_cast<uint2*>(zhi + off) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+        *reinterpret_cast<uint2*>(zlo + off) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();

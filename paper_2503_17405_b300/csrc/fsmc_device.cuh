@@ -56,13 +56,20 @@ template <> struct Conv<double> {
     return ((double)v + 0.5) * 0x1p-52;
   }
   static __device__ __forceinline__ double log_u(uint32_t hi, uint32_t lo) { return log(u(hi, lo)); }
-  // Box-Muller pair: r = sqrt(-2 ln u(w0,w1)), phi = 2 pi u(w2,w3)
-  static __device__ __forceinline__ void normal_pair(const P4& b, double& z0, double& z1) {
-    const double r = sqrt(-2.0 * log_u(b.w0, b.w1));
+  // one-word uniform (w + 1/2) 2^-32, exact
+  static __device__ __forceinline__ double u32(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+  // Box-Muller pair: r = sqrt(-2 ln u32(a)), phi = 2 pi u32(b)
+  static __device__ __forceinline__ void bm(uint32_t a, uint32_t b, double& z0, double& z1) {
+    const double r = sqrt(-2.0 * log(u32(a)));
     double s, c;
-    sincospi(2.0 * u(b.w2, b.w3), &s, &c);
+    sincospi(2.0 * u32(b), &s, &c);
     z0 = r * c;
     z1 = r * s;
+  }
+  // four normals per block: pairs from (w0, w1) and (w2, w3)
+  static __device__ __forceinline__ void normal_quad(const P4& b, double (&z)[4]) {
+    bm(b.w0, b.w1, z[0], z[1]);
+    bm(b.w2, b.w3, z[2], z[3]);
   }
 };
 
@@ -75,16 +82,23 @@ template <> struct Conv<float> {
   static __device__ __forceinline__ float log_u(uint32_t hi, uint32_t lo) {
     return (hi & 0x80000000u) ? log1pf(-u(~hi, ~lo)) : logf(u(hi, lo));
   }
+  // single-precision rounding of the one-word uniform (w + 1/2) 2^-32
+  static __device__ __forceinline__ float u32(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
   // Box-Muller with the hardware approximations: the radius from __logf (absolute error
   // ~4e-7 in log u) and the angle phi = 2 pi u written as psi + pi with psi in [-pi, pi),
   // where __sincosf is accurate to ~5e-7 (cos phi = -cos psi, sin phi = -sin psi).
-  static __device__ __forceinline__ void normal_pair(const P4& b, float& z0, float& z1) {
-    const float r = sqrtf(fmaxf(-2.0f * __logf(u(b.w0, b.w1)), 0.f));
-    const float psi = fmaf(6.28318530717958647692f, u(b.w2, b.w3), -3.14159265358979323846f);
+  static __device__ __forceinline__ void bm(uint32_t a, uint32_t b, float& z0, float& z1) {
+    const float r = sqrtf(fmaxf(-2.0f * __logf(u32(a)), 0.f));
+    const float psi = fmaf(6.28318530717958647692f, u32(b), -3.14159265358979323846f);
     float s, c;
     __sincosf(psi, &s, &c);
     z0 = -r * c;
     z1 = -r * s;
+  }
+  // four normals per block: pairs from (w0, w1) and (w2, w3)
+  static __device__ __forceinline__ void normal_quad(const P4& b, float (&z)[4]) {
+    bm(b.w0, b.w1, z[0], z[1]);
+    bm(b.w2, b.w3, z[2], z[3]);
   }
 };
 

@@ -245,9 +245,10 @@ __device__ void nuts_init(const NutsView<T>& v, const Key& key, int lane, Chain<
     const int k = lane + 32 * e;
     p[e] = T(0);
     if (k < d) {
-      T z0, z1;
-      Conv<T>::normal_pair(key.block((uint32_t)s.t, 0, (uint32_t)(k >> 1)), z0, z1);
-      p[e] = (k & 1) ? z1 : z0;
+      T z[4];
+      Conv<T>::normal_quad(key.block((uint32_t)s.t, 0, (uint32_t)(k >> 2)), z);
+      const int i = k & 3;
+      p[e] = i == 0 ? z[0] : i == 1 ? z[1] : i == 2 ? z[2] : z[3];
     }
   }
   s.H0 = -s.lpx + T(0.5) * wdot<T, E>(p, p);

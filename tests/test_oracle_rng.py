@@ -28,7 +28,7 @@ def test_uniform_is_uniform():
 
 def test_box_muller_normals():
     # 40000 normals: mean 0, variance 1, normal CDF (Kolmogorov-Smirnov), and the
-    # two members of a pair are uncorrelated
+    # two members of a Box-Muller pair are uncorrelated
     z = np.concatenate([O.normals(5, c, 3, 0, 0, 40) for c in range(1000)])
     assert abs(z.mean()) < 4 / np.sqrt(z.size)
     assert abs(z.var() - 1) < 4 * np.sqrt(2 / z.size)
@@ -42,5 +42,10 @@ def test_streams_are_keyed_by_chain_sample_tag_draw():
     assert np.array_equal(base, O.normals(9, 1, 2, 0, 0, 8))
     for args in [(9, 2, 2, 0, 0), (9, 1, 3, 0, 0), (9, 1, 2, 1, 0), (9, 1, 2, 0, 4), (10, 1, 2, 0, 0)]:
         assert not np.allclose(base, O.normals(*args, 8))
-    # normals 2q, 2q+1 come from draw q: starting at draw 1 shifts by one pair
-    assert np.array_equal(base[2:], O.normals(9, 1, 2, 0, 1, 6))
+    # normals 4q .. 4q+3 come from draw q: starting at draw 1 shifts by one block
+    assert np.array_equal(base[4:], O.normals(9, 1, 2, 0, 1, 4))
+
+
+def test_uniform32_endpoints():
+    assert O.uniform32(0) == 2.0 ** -33
+    assert O.uniform32(0xFFFFFFFF) == 1.0 - 2.0 ** -33
