@@ -165,6 +165,15 @@ def job_throughput(world, steps, chains, samples, total_ms):
 
 
 # ---- our arm ---------------------------------------------------------------------------------------
+def parse_tuning(spec):
+    """'lanes_per_chain=16,steps_per_launch=64' -> dict of launch-shape overrides."""
+    out = {}
+    for item in filter(None, (spec or "").split(",")):
+        k, v = item.split("=")
+        out[k.strip()] = int(v)
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2503_17405_b300 import fsmc
@@ -184,7 +193,7 @@ def run_ours(args, rank, world):
         dr = dict(zip(["n_stages", "scale0", "factor"], cfg["algo_params"]))
     if cfg["algo"] == "nuts":
         nuts = dict(zip(["eps", "max_depth", "max_dH"], cfg["algo_params"]))
-    tuning = {"profile_kernels": 1}
+    tuning = {"profile_kernels": 1, **parse_tuning(args.tuning)}
     job = eng.job(tg, cfg["algo"], m, n, x0=cfg["x0"], seed=1 + rank, prec=cfg["prec"], store=True,
                   dr=dr, nuts=nuts, tuning=tuning)
     stream = torch.cuda.Stream()          # a real stream: graph capture needs one
@@ -247,7 +256,8 @@ def run_ours(args, rank, world):
 
     peaks = _peaks()
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    gen = job.tuning().get("generator", 0)
+    tun = job.tuning()
+    gen = tun.get("generator", 0)
     d = w["d"]
     if cfg["algo"] == "ess" and kms[0] >= kms[1]:
         achieved = cols * cfg["flops_per_column"] / (kms[0] / 1e3) / 1e12
@@ -289,7 +299,7 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         tg2 = eng.target(w["kind"], w["d"], params_h.numpy(), n_data=w["n_data"])
         job2 = eng.job(tg2, cfg["algo"], m, n, x0=x0_h.numpy(), seed=1 + rank, prec=cfg["prec"],
-                       store=True, dr=dr, nuts=nuts)
+                       store=True, dr=dr, nuts=nuts, tuning=parse_tuning(args.tuning) or None)
         job2.run("fsm", stream=sp)
         sx, sx2, nk = job2.moments()
         t1 = time.perf_counter()
@@ -312,7 +322,10 @@ def run_ours(args, rank, world):
             "fsm": {"value": value, "R_hat": st["R_hat"], "mean_N": st["mean_N"],
                     "mean_max_N": st["mean_max_N"], "E_pred": E_pred,
                     "kernel_ms_per_step": [k / args.steps for k in kms],
-                    "kernel_launches_per_step": [k / args.steps for k in kl]},
+                    "kernel_launches_per_step": [k / args.steps for k in kl],
+                    "columns_generated_per_step": cols / max(1, len(stats)),
+                    "tuning": {k: tun[k] for k in ("lanes_per_chain", "steps_per_launch", "ring_slots",
+                                                   "threads_per_block", "generator", "pipelined")}},
             "sync": sync,
             "speedup_fsm_over_sync": (value / world / sync["value"]) if sync else None,
             "roofline": roof,
@@ -438,6 +451,7 @@ def main():
     ap.add_argument("--samples", type=int, default=None, help="samples per chain (profiling only)")
     ap.add_argument("--serve-jobs", type=int, default=40)
     ap.add_argument("--serve-scale", type=float, default=0.25)
+    ap.add_argument("--tuning", default="", help="launch-shape overrides, e.g. lanes_per_chain=16")
     args = ap.parse_args()
     if args.config == "serving":
         print(json.dumps(run_serving(args)))

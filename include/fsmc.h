@@ -54,7 +54,8 @@ typedef enum fsmc_status {
 
 /* Targets.  params_host layouts (doubles, row-major):
  *   GAUSS_CONJ  ESS likelihood -|y - x|^2 / (2 s2):  L[d*d] (prior Cholesky), y[d], s2
- *   GP_LOGIT    ESS likelihood -sum_k softplus(-s_k x_k): L[d*d], s[d] (labels in {-1,+1})
+ *   GP_LOGIT    ESS likelihood -sum_k softplus(-s_k x_k): L[d*d], s[d] (labels in {-1,+1};
+ *               fsmc_target_create returns FSMC_EINVAL for any other label value)
  *   FLAT        ESS likelihood f == 1 (prior draws):    L[d*d]
  *   FUNNEL      Neal funnel, v ~ N(0,9), x_i|v ~ N(0,e^v): no params (n_params = 0)
  *   LOGREG      beta ~ N(0,I), y_i ~ Bern(sigmoid(X_i beta)): X[n_data*d], y[n_data]
@@ -95,7 +96,8 @@ typedef struct fsmc_nuts_params {
 /* Launch shape.  Zero fields mean "choose automatically" (the autotuner's cached
  * choice, else a heuristic on the log-density cost). */
 typedef struct fsmc_tuning {
-  int lanes_per_chain;   /* 1 = chain-per-thread, 32 = chain-per-warp, 0 = auto          */
+  int lanes_per_chain;   /* 1 = chain-per-thread, 16 = two chains per warp (ESS,
+                            32 < d <= 512), 32 = chain-per-warp, 0 = auto               */
   int steps_per_launch;  /* FSM states each chain advances per launch                    */
   int ring_slots;        /* ESS: pre-generated ellipse directions kept per chain         */
   int threads_per_block; /* 32..256, multiple of 32                                      */

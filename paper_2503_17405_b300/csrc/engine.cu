@@ -207,6 +207,11 @@ extern "C" fsmc_status fsmc_target_create(fsmc_engine* e, fsmc_target_kind kind,
     return fsmc_fail(FSMC_EINVAL, "invalid target kind / d / n_data");
   if (n_params != need) return fsmc_fail(FSMC_EINVAL, "n_params does not match the target layout");
   if (need && !params_host) return fsmc_fail(FSMC_EINVAL, "params_host is NULL");
+  if (kind == FSMC_TGT_GP_LOGIT)
+    for (int k = 0; k < d; ++k) {
+      const double s = params_host[(size_t)d * d + k];
+      if (s != 1.0 && s != -1.0) return fsmc_fail(FSMC_EINVAL, "GP_LOGIT labels must be -1 or +1");
+    }
   CK(cudaSetDevice(e->device));
   auto* t = new (std::nothrow) fsmc_target();
   if (!t) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");
@@ -309,6 +314,8 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
     j->o_nu = L.take(m * (size_t)j->W * j->dstride * es);
     j->o_gencols = L.take(8);
     j->o_win = L.take(2 * m * 4);
+    j->o_colbase = L.take((m + 1) * 8);
+    j->o_colmap = L.take(m * (size_t)j->W * 8);
   } else if (j->algo == FSMC_DR) {
     j->o_ell = L.take(m * es);        // log pi(x)
     j->o_y = L.take(2 * m * d * es);  // y1, y2
@@ -380,6 +387,8 @@ EssView<T> ess_view(const fsmc_job* j) {
   v.nu = (T*)(b + j->o_nu);
   v.gen_cols = (unsigned long long*)(b + j->o_gencols);
   v.own_window = 1;
+  v.col_base = (long long*)(b + j->o_colbase);
+  v.colmap = (int2*)(b + j->o_colmap);
   return v;
 }
 
@@ -507,9 +516,13 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (!j || !tu) return fsmc_fail(FSMC_EINVAL, "NULL argument");
   if (j->dev) return fsmc_fail(FSMC_ESTATE, "tuning must be set before the first run");
   fsmc_tuning t = *tu;
-  if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 32)
-    return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1 or 32");
-  if (j->algo == FSMC_DR && t.lanes_per_chain == 32) return fsmc_fail(FSMC_EINVAL, "DR is chain-per-thread");
+  if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 16 && t.lanes_per_chain != 32)
+    return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1, 16 or 32");
+  if (j->algo == FSMC_DR && t.lanes_per_chain > 1) return fsmc_fail(FSMC_EINVAL, "DR is chain-per-thread");
+  if (t.lanes_per_chain == 16 && (j->algo != FSMC_ESS || j->d <= 32 || j->d > 512))
+    return fsmc_fail(FSMC_EINVAL, "16 lanes per chain: ESS jobs with 32 < d <= 512");
+  if (j->algo == FSMC_NUTS && t.lanes_per_chain && t.lanes_per_chain != 32)
+    return fsmc_fail(FSMC_EINVAL, "NUTS is chain-per-warp (32 lanes)");
   if (j->algo == FSMC_ESS && t.lanes_per_chain == 1 && j->d > 32)
     return fsmc_fail(FSMC_EINVAL, "chain-per-thread ESS supports d <= 32");
   if (t.threads_per_block && (t.threads_per_block % 32 || t.threads_per_block < 32 || t.threads_per_block > 256))

@@ -88,6 +88,7 @@ struct fsmc_job {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_fsm[2] = {nullptr, nullptr};
   size_t o_win = 0;  // second refill-window buffer [2][m]
+  size_t o_colbase = 0, o_colmap = 0;  // compacted refill list: [m+1] prefix sums, [m*W] (chain, sample)
   // serving
   bool submitted = false;
   fsmc_mode serve_mode = FSMC_MODE_FSM;

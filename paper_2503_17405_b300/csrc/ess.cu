@@ -156,24 +156,52 @@ __global__ void __launch_bounds__(256) ess_nu_gen_kernel(EssView<T> v) {
 }
 
 // ------------------------------------------------------------------------------------------
-// log-likelihood contribution of this lane's coordinates of x'
+// log-likelihood of x' summed over the chain group (each lane its coordinates)
 template <typename T, int G, int E>
 __device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E], int lane,
-                                        const T (&yv)[E]) {
+                                        const T (&yv)[E], unsigned gmask) {
   T part = T(0);
   if (tg.kind == TGT_GP_LOGIT) {
 #pragma unroll
     for (int e = 0; e < E; ++e)
       if (e * G + lane < tg.d) part += softplus<T>(-yv[e] * xp[e]);
-    return -group_sum<G>(part);
+    return -group_sum<G>(part, gmask);
   } else if (tg.kind == TGT_GAUSS_CONJ) {
 #pragma unroll
     for (int e = 0; e < E; ++e)
       if (e * G + lane < tg.d) { const T r = yv[e] - xp[e]; part = fma(r, r, part); }
-    return -group_sum<G>(part) / (T(2) * tg.s2);
+    return -group_sum<G>(part, gmask) / (T(2) * tg.s2);
   }
   return T(0);  // TGT_FLAT
 }
+
+// GP-logit likelihood in single precision, in base 2.  With labels s_i = +-1 and
+// c_i = -s_i log2(e), the lanes keep xs = c x and ns = c nu, so that t' = c x' =
+// xs cos(th) + ns sin(th) needs no per-coordinate scaling, and
+//   softplus(-s_i x'_i) = ln 2 [max(t', 0) + log2(1 + 2^-|t'|)].
+// Two hardware approximations per coordinate (ex2, lg2), both with absolute error ~2e-7 here.
+constexpr float kLn2f = 0.693147180559945309417f;
+constexpr float kLog2ef = 1.44269504088896340736f;
+
+template <int G, int E>
+__device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const float (&ns)[E], float cs, float sn,
+                                                 int lane, int d, unsigned gmask) {
+  float a = 0.f, b = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (e * G + lane < d) {
+      const float t = fmaf(xs[e], cs, ns[e] * sn);
+      a += fmaxf(t, 0.f);
+      b += lg2_approx(1.f + ex2_approx(-fabsf(t)));
+    }
+  }
+  return -kLn2f * group_sum<G>(a + b, gmask);
+}
+
+// The fast GP-logit path is taken for single-precision GP-logit jobs whose lanes hold at most
+// 16 coordinates (the extra per-lane arrays then stay in registers).
+template <typename T, int E>
+constexpr bool kEssGpFast = sizeof(T) == 4 && E <= 16;
 
 // Slice threshold log y = log f(x) + log u.  In single precision a u within ~1e-5 of 1 makes
 // the sum round back to log f(x); the bracket would then shrink onto theta = 0 without ever
@@ -239,44 +267,57 @@ __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, 
 // ------------------------------------------------------------------------------------------
 // FSM kernel: every chain advances `budget` states (fewer if its ring runs dry or it
 // finishes).  Chain-group layout: G lanes own one chain, lane l holds coordinates l, l+G, ...
-template <typename T, int G, int E>
+// GP: single-precision GP-logit likelihood in base 2 (ess_loglik_gp32); the lanes then also
+// keep xs = c x and ns = c nu, and yv holds c = -s log2(e) instead of the labels s.
+template <typename T, int G, int E, bool GP>
 __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c, int budget, int lane) {
   const int d = v.tg.d;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
+  const unsigned gmask = group_mask<G>();
   {
-    T x[E], nu[E], xp[E], yv[E];
+    T x[E], nu[E], yv[E], xs[E], ns[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = e * G + lane;
       x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
       yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
+      if constexpr (GP) {
+        yv[e] = -yv[e] * T(kLog2ef);
+        xs[e] = x[e] * yv[e];
+      }
       nu[e] = T(0);
+      ns[e] = T(0);
     }
     T ell = v.ell[c], logy = v.logy[c], th = v.th[c], thmin = v.thmin[c], thmax = v.thmax[c];
     int t = v.t[c], st = v.k[c], s = v.s[c];
     const int hi = v.gen_hi[c];
     const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
-    if (st == ESS_SHRINK && t < v.n) {
+    auto load_nu = [&]() {
       const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
 #pragma unroll
-      for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) nu[e] = src[k]; }
-    }
+      for (int e = 0; e < E; ++e) {
+        const int k = e * G + lane;
+        if (k < d) nu[e] = src[k];
+        if constexpr (GP) ns[e] = nu[e] * yv[e];
+      }
+    };
+    if (st == ESS_SHRINK && t < v.n) load_nu();
     int steps = 0;
     int err = 0;
-    // Chain-per-warp: the 32 lanes draw 32 consecutive Philox blocks of the current sample at
+    // Chain groups of 16 or 32 lanes draw G consecutive Philox blocks of the current sample at
     // once (lane l holds draw D + cbase + l) and each state fetches its words by shuffle,
     // instead of every lane computing the same block.
     P4 cache{0u, 0u, 0u, 0u};
     int cbase = -(1 << 30);
     auto fetch = [&](int off) -> P4 {
-      if constexpr (G == 32) {
-        if (off - cbase >= 32 || off < cbase) {
+      if constexpr (G >= 16) {
+        if (off - cbase >= G || off < cbase) {
           cbase = off;
           cache = key.block((uint32_t)t, 0, (uint32_t)(D + off + lane));
         }
         const int src = off - cbase;
-        return P4{__shfl_sync(0xffffffffu, cache.w0, src), __shfl_sync(0xffffffffu, cache.w1, src),
-                  __shfl_sync(0xffffffffu, cache.w2, src), __shfl_sync(0xffffffffu, cache.w3, src)};
+        return P4{__shfl_sync(gmask, cache.w0, src, G), __shfl_sync(gmask, cache.w1, src, G),
+                  __shfl_sync(gmask, cache.w2, src, G), __shfl_sync(gmask, cache.w3, src, G)};
       } else {
         return key.block((uint32_t)t, 0, (uint32_t)(D + off));
       }
@@ -284,9 +325,7 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
     for (int b = 0; b < budget && t < v.n; ++b) {
       if (st == ESS_INIT) {
         if (t >= hi) break;  // direction not generated yet
-        const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
-#pragma unroll
-        for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) nu[e] = src[k]; }
+        load_nu();
         cbase = -(1 << 30);  // a new sample: its blocks are not cached yet
         const P4 r = fetch(0);
         logy = ess_threshold<T>(ell, Conv<T>::log_u(r.w0, r.w1));
@@ -302,16 +341,25 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
       }
       T sn, cs;
       ess_sincos<T>(th, sn, cs);
+      T ellp;
+      if constexpr (GP) {
+        ellp = ess_loglik_gp32<G, E>(xs, ns, cs, sn, lane, d, gmask);
+      } else {
+        T xp[E];
 #pragma unroll
-      for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
-      T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv);
+        for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
+        ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
+      }
       if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
       ++steps;
       const bool accept = ellp > logy;
       if (accept || s >= kMaxShrinks) {
         if (accept) {
 #pragma unroll
-          for (int e = 0; e < E; ++e) x[e] = xp[e];
+          for (int e = 0; e < E; ++e) {
+            x[e] = fma(x[e], cs, nu[e] * sn);
+            if constexpr (GP) xs[e] = x[e] * yv[e];
+          }
           ell = ellp;
         } else {
           err |= ERR_SHRINK_CAP;
@@ -340,13 +388,20 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
   }
 }
 
+// registers per thread allowed by the launch bounds: chain-per-warp FP32 rows of up to 8
+// coordinates per lane fit three 256-thread blocks per SM, longer rows two
 template <typename T, int G, int E>
-__global__ void __launch_bounds__(256, ((sizeof(T) == 4 && E <= 8) || (sizeof(T) == 8 && E <= 2)) ? 3 : 2)
+__host__ __device__ constexpr int ess_min_blocks() {
+  return ((sizeof(T) == 4 && E <= 8) || (sizeof(T) == 8 && E <= 2)) ? 3 : 2;
+}
+
+template <typename T, int G, int E, bool GP>
+__global__ void __launch_bounds__(256, (ess_min_blocks<T, G, E>()))
 ess_fsm_kernel(EssView<T> v, int budget) {
   const int lane = threadIdx.x % G;
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E>(v, c, budget, lane);
+  for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, GP>(v, c, budget, lane);
 }
 
 // ---- fused launches over several jobs (serving) --------------------------------------------------
@@ -384,7 +439,13 @@ __global__ void __launch_bounds__(256) ess_fsm_multi_kernel(const EssView<T>* vi
   if (item >= total) return;
   const int k = find_job(off, njobs, item);
   const EssView<T> v = views[k];
-  ess_advance_chain<T, G, E>(v, item - off[k], budget, lane);
+  if constexpr (kEssGpFast<T, E>) {
+    if (v.tg.kind == TGT_GP_LOGIT) {
+      ess_advance_chain<T, G, E, true>(v, item - off[k], budget, lane);
+      return;
+    }
+  }
+  ess_advance_chain<T, G, E, false>(v, item - off[k], budget, lane);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -393,11 +454,12 @@ __global__ void __launch_bounds__(256) ess_fsm_multi_kernel(const EssView<T>* vi
 // after every iteration, until no chain anywhere is active; then the next sample.
 // Chains are assigned statically to groups; chain state lives in global memory.
 // Launched cooperatively (co-residency guaranteed), barrier waits are bounded.
-template <typename T, int G, int E>
+template <typename T, int G, int E, bool GP>
 __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin, int t_end,
                                                        GridBarrier bar, unsigned* active_cnt,
                                                        unsigned long long* iterations) {
   const int lane = threadIdx.x % G;
+  const unsigned gmask = group_mask<G>();
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   const int d = v.tg.d;
@@ -411,6 +473,7 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
   for (int e = 0; e < E; ++e) {
     const int k = e * G + lane;
     yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
+    if constexpr (GP) yv[e] = -yv[e] * T(kLog2ef);  // c = -s log2(e), as in the FSM kernel
   }
 
   for (int t = t_begin; t < t_end; ++t) {
@@ -450,7 +513,15 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
         ess_sincos<T>(th, sn, cs);
 #pragma unroll
         for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
-        T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv);
+        T ellp;
+        if constexpr (GP) {
+          T xs[E], ns[E];
+#pragma unroll
+          for (int e = 0; e < E; ++e) { xs[e] = x[e] * yv[e]; ns[e] = nu[e] * yv[e]; }
+          ellp = ess_loglik_gp32<G, E>(xs, ns, cs, sn, lane, d, gmask);
+        } else {
+          ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
+        }
         if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
         const bool accept = ellp > logy;
         if (accept || s >= kMaxShrinks) {  // DONE (S3)
@@ -605,7 +676,13 @@ template <typename T, int G, int E>
 static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cudaStream_t st) {
   const int64_t groups_per_block = threads / G;
   const int64_t blocks = (v.m + groups_per_block - 1) / groups_per_block;
-  ess_fsm_kernel<T, G, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  if constexpr (kEssGpFast<T, E>) {
+    if (v.tg.kind == TGT_GP_LOGIT) {
+      ess_fsm_kernel<T, G, E, true><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+      return cudaGetLastError();
+    }
+  }
+  ess_fsm_kernel<T, G, E, false><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
   return cudaGetLastError();
 }
 
@@ -613,7 +690,10 @@ template <typename T, int G, int E>
 static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier bar,
                                unsigned* active_cnt, unsigned long long* iters, int threads,
                                cudaStream_t st) {
-  auto kern = ess_sync_kernel<T, G, E>;
+  auto kern = ess_sync_kernel<T, G, E, false>;
+  if constexpr (kEssGpFast<T, E>) {
+    if (v.tg.kind == TGT_GP_LOGIT) kern = ess_sync_kernel<T, G, E, true>;
+  }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
   if (e != cudaSuccess) return e;
@@ -637,6 +717,11 @@ static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier 
       if (d <= 8) return FN<T, 1, 8>(__VA_ARGS__);                              \
       if (d <= 16) return FN<T, 1, 16>(__VA_ARGS__);                            \
       if (d <= 32) return FN<T, 1, 32>(__VA_ARGS__);                            \
+    } else if (G == 16) {                                                       \
+      if (d <= 64) return FN<T, 16, 4>(__VA_ARGS__);                            \
+      if (d <= 128) return FN<T, 16, 8>(__VA_ARGS__);                           \
+      if (d <= 256) return FN<T, 16, 16>(__VA_ARGS__);                          \
+      if (d <= 512) return FN<T, 16, 32>(__VA_ARGS__);                          \
     } else if (G == 32) {                                                       \
       if (d <= 32) return FN<T, 32, 1>(__VA_ARGS__);                            \
       if (d <= 64) return FN<T, 32, 2>(__VA_ARGS__);                            \
@@ -681,6 +766,7 @@ cudaError_t launch_ess_nu_gen_multi(const EssView<T>* views, const int64_t* off,
 // shape of the group an ESS job belongs to: jobs with equal (lanes, E) share a fused launch
 int ess_group_E(int G, int d) {
   if (G == 1) return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32;
+  if (G == 16) return d <= 64 ? 4 : d <= 128 ? 8 : d <= 256 ? 16 : 32;
   return d <= 32 ? 1 : d <= 64 ? 2 : d <= 128 ? 4 : d <= 256 ? 8 : d <= 512 ? 16 : 32;
 }
 

@@ -11,6 +11,10 @@
 //    L_hi z_hi + L_hi z_lo + L_lo z_hi per 16-wide k-step (the dropped L_lo z_lo term is
 //    ~2^-22 relative), for row tile 0 (rows 0..127, k < 128) and row tile 1 (rows 128..255);
 //  * the accumulators are read back with tcgen05.ld and stored to the chains' direction rings.
+// The columns of one refill are compacted first (a prefix sum over the chains' refill counts and
+// a (chain, sample) list), so every tile holds 64 columns that are actually needed: chains
+// consume different numbers of directions per round, and tiles over fixed chain blocks and ring
+// offsets were on average about half empty.
 // Every wait on an mbarrier is bounded; on expiry the kernel records ERR_BARRIER_TIMEOUT,
 // waits (bounded) for its outstanding MMAs, frees its tensor memory and returns.
 #include <cuda_fp16.h>
@@ -134,14 +138,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
   uint64_t* bar_mma = bars + 1;  // [2]
   uint64_t* bar_done = bars + 3;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  int* col_sample = reinterpret_cast<int*>(bars + 5);
-  __shared__ int s_fail;
+  int* s_fail_p = reinterpret_cast<int*>(bars + 5);
+  long long* col_dst = reinterpret_cast<long long*>(bars + 8);  // [TC_N] ring row offset, -1: none
+  int* col_sample = reinterpret_cast<int*>(col_dst + TC_N);      // [TC_N]
+  int* col_chain = col_sample + TC_N;                              // [TC_N]
+  volatile int& s_fail = *s_fail_p;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const int nchunks = lay.kpad / TC_KC;
   const int nbx = (int)((v.m + TC_N - 1) / TC_N);
-  const int ntiles = nbx * v.W;
+  const long long total = v.colmap ? v.col_base[v.m] : 0;
+  const long long ntiles = v.colmap ? (total + TC_N - 1) / TC_N : (long long)nbx * v.W;
+  if (v.colmap && blockIdx.x == 0 && tid == 0 && total > 0) atomicAdd(v.gen_cols, (unsigned long long)total);
 
   if (tid == 0) {
     s_fail = 0;
@@ -185,46 +194,66 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
   long long chunk_ctr = 0;
   bool mma_pending = false;
 
-  for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
-    const int bx = tile % nbx, w = tile / nbx;
-    const int64_t c0 = (int64_t)bx * TC_N;
+  // z-generation roles: this lane's column and k half are the same for every chunk; a warp
+  // fills two core matrices (8 columns x 8 k, 128 contiguous bytes each) per pass
+  const int zn = (((2 * warp + (lane >> 4)) & 7) << 3) + ((lane >> 1) & 7);  // column 0..63
+  const int zkh = lane & 1;
+  constexpr int kPasses = 64 / (2 * (TC_THREADS / 32));  // core-matrix pairs per warp per chunk
+
+  for (long long tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
     int active = 0;
     if (tid < TC_N) {
-      const int64_t c = c0 + tid;
-      int smp = -1;
-      if (c < v.m) {
-        const int s = v.gen_lo[c] + w;
-        if (s < v.gen_hi[c]) smp = s;
+      int c = -1, smp = -1;
+      if (v.colmap) {
+        const long long jc = tile * TC_N + tid;
+        if (jc < total) {
+          const int2 e = v.colmap[jc];
+          c = e.x;
+          smp = e.y;
+        }
+      } else {
+        const int bx = (int)(tile % nbx), w = (int)(tile / nbx);
+        const int64_t cc = (int64_t)bx * TC_N + tid;
+        if (cc < v.m) {
+          const int s = v.gen_lo[cc] + w;
+          if (s < v.gen_hi[cc]) { c = (int)cc; smp = s; }
+        }
       }
+      col_chain[tid] = c;
       col_sample[tid] = smp;
+      col_dst[tid] = smp >= 0 ? ((long long)c * v.W + smp % v.W) * v.dstride : -1;
       active = smp >= 0;
     }
     const int n_active = __syncthreads_count(active);
     if (n_active == 0) continue;
-    if (tid == 0) atomicAdd(v.gen_cols, (unsigned long long)n_active);
+    if (!v.colmap && tid == 0) atomicAdd(v.gen_cols, (unsigned long long)n_active);
+    const int z_smp = col_sample[zn];
+    const Key zkey{(uint32_t)(v.chain0 + col_chain[zn]), v.seed_lo, v.seed_hi};
 
     for (int kc = 0; kc < nchunks; ++kc, ++chunk_ctr) {
       const int s = (int)(chunk_ctr & 1);
       if (chunk_ctr >= 2) {  // the MMAs that read this stage two chunks ago must be done
-        if (!mbar_wait(&bar_mma[s], stage_phase[s])) { s_fail = 1; }
+        if (!mbar_wait(&bar_mma[s], stage_phase[s])) s_fail = 1;
         stage_phase[s] ^= 1u;
       }
-      // z chunk: a core matrix is 8 columns x 8 k (128 contiguous bytes) = 16 Philox blocks of
-      // four normals; a warp fills two core matrices per pass (lane: core half, column, k half)
       unsigned char* zhi = sB + s * 2 * TC_STAGE;
       unsigned char* zlo = zhi + TC_STAGE;
+      // all Philox blocks of the pass first (independent, so their rounds interleave), then
+      // Box-Muller, the FP16 hi/lo split and the stores
+      P4 blk[kPasses];
 #pragma unroll
-      for (int it = 0; it < 64 / (2 * (TC_THREADS / 32)); ++it) {
-        const int core = 2 * (warp + (TC_THREADS / 32) * it) + (lane >> 4);
-        const int ng = core & 7, kg = core >> 3;
-        const int nr = (lane >> 1) & 7, kh = lane & 1;
-        const int n = ng * 8 + nr;
-        const int q = kc * (TC_KC / 4) + kg * 2 + kh;  // Philox draw: normals 4q .. 4q+3
-        const int smp = col_sample[n];
+      for (int it = 0; it < kPasses; ++it) {
+        const int kg = (2 * (warp + (TC_THREADS / 32) * it) + (lane >> 4)) >> 3;
+        const int q = kc * (TC_KC / 4) + kg * 2 + zkh;  // Philox draw: normals 4q .. 4q+3
+        blk[it] = (z_smp >= 0 && q < D) ? zkey.block((uint32_t)z_smp, 0, (uint32_t)q) : P4{0u, 0u, 0u, 0u};
+      }
+#pragma unroll
+      for (int it = 0; it < kPasses; ++it) {
+        const int kg = (2 * (warp + (TC_THREADS / 32) * it) + (lane >> 4)) >> 3;
+        const int q = kc * (TC_KC / 4) + kg * 2 + zkh;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
-        if (smp >= 0 && q < D) {
-          const Key key{(uint32_t)(v.chain0 + c0 + n), v.seed_lo, v.seed_hi};
-          Conv<float>::normal_quad(key.block((uint32_t)smp, 0, (uint32_t)q), z);
+        if (z_smp >= 0 && q < D) {
+          Conv<float>::normal_quad(blk[it], z);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
             if (4 * q + i >= d) z[i] = 0.f;
@@ -237,7 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         }
         const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
         const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
-        const int off = ng * (TC_KC / 8) * 128 + kg * 128 + nr * 16 + kh * 8;
+        const int off = (zn >> 3) * (TC_KC / 8) * 128 + kg * 128 + (zn & 7) * 16 + zkh * 8;
         *reinterpret_cast<uint2*>(zhi + off) =
             make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
         *reinterpret_cast<uint2*>(zlo + off) =
@@ -276,8 +305,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
     }
     if (s_fail) break;
     // accumulators complete -> registers -> direction rings
-    if (!mbar_wait(bar_done, done_phase)) { s_fail = 1; break; }
+    if (!mbar_wait(bar_done, done_phase)) s_fail = 1;
     done_phase ^= 1u;
+    __syncthreads();
+    if (s_fail) break;
     mma_pending = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // warp w: row tile (w >> 2) & 1, lane quadrant w & 3, column half w >> 3
@@ -298,10 +329,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         if (row < d) {
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            const int j = j0 + jj;
-            const int smp = col_sample[j];
-            if (smp >= 0)
-              v.nu[((size_t)(c0 + j) * v.W + (smp % v.W)) * v.dstride + row] = __uint_as_float(r[jj]);
+            const long long dst = col_dst[j0 + jj];
+            if (dst >= 0) v.nu[dst + row] = __uint_as_float(r[jj]);
           }
         }
       }
@@ -318,6 +347,64 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+// Refill counts -> exclusive prefix sum col_base[0..m] (one block, chains in passes of
+// 1024 x 8, each thread a run of 8 consecutive chains).
+__global__ void __launch_bounds__(1024) ess_col_scan_kernel(const int* gen_lo, const int* gen_hi, int64_t m,
+                                                            long long* base) {
+  constexpr int SEG = 8;
+  __shared__ long long warp_tot[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  long long run = 0;
+  for (int64_t p0 = 0; p0 < m; p0 += 1024 * SEG) {
+    int cnt[SEG];
+    long long local = 0;
+#pragma unroll
+    for (int s = 0; s < SEG; ++s) {
+      const int64_t c = p0 + (int64_t)tid * SEG + s;
+      cnt[s] = c < m ? max(0, gen_hi[c] - gen_lo[c]) : 0;
+      local += cnt[s];
+    }
+    long long incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      long long wt = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, wt, o);
+        if (lane >= o) wt += y;
+      }
+      warp_tot[lane] = wt;  // inclusive over warps
+    }
+    __syncthreads();
+    long long excl = run + (warp > 0 ? warp_tot[warp - 1] : 0) + incl - local;
+#pragma unroll
+    for (int s = 0; s < SEG; ++s) {
+      const int64_t c = p0 + (int64_t)tid * SEG + s;
+      if (c < m) base[c] = excl;
+      excl += cnt[s];
+    }
+    run += warp_tot[31];
+    __syncthreads();
+  }
+  if (tid == 0) base[m] = run;
+}
+
+// (chain, sample) of every refill column, in chain order
+__global__ void ess_col_fill_kernel(const int* gen_lo, const int* gen_hi, const long long* base, int64_t m,
+                                    int2* colmap) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  const int lo = gen_lo[c], cnt = gen_hi[c] - lo;
+  const long long b = base[c];
+  for (int k = 0; k < cnt; ++k) colmap[b + k] = make_int2((int)c, lo + k);
+}
+
 size_t ess_tc_image_bytes(int d) { return (size_t)tc_layout(d).a_bytes; }
 
 cudaError_t launch_ess_tc_build(const float* L, int d, unsigned char* img, cudaStream_t st) {
@@ -329,12 +416,18 @@ cudaError_t launch_ess_tc_build(const float* L, int d, unsigned char* img, cudaS
 
 cudaError_t launch_ess_nu_gen_tc(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st) {
   const TcLayout lay = tc_layout(v.tg.d);
-  const int smem = lay.a_bytes + 2 * 2 * TC_STAGE + 64 + TC_N * 4;
+  const int smem = lay.a_bytes + 2 * 2 * TC_STAGE + 64 + TC_N * (8 + 4 + 4);
   cudaError_t e = cudaFuncSetAttribute(ess_nu_gen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  if (v.colmap) {
+    ess_col_scan_kernel<<<1, 1024, 0, st>>>(v.gen_lo, v.gen_hi, v.m, v.col_base);
+    ess_col_fill_kernel<<<(unsigned)((v.m + 255) / 256), 256, 0, st>>>(v.gen_lo, v.gen_hi, v.col_base, v.m,
+                                                                       v.colmap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const int nbx = (int)((v.m + TC_N - 1) / TC_N);
-  const int ntiles = nbx * v.W;
-  const int grid = std::max(1, std::min(ntiles, sms));
+  const long long ntiles = v.colmap ? ((long long)v.m * v.W + TC_N - 1) / TC_N : (long long)nbx * v.W;
+  const int grid = (int)std::max(1LL, std::min<long long>(ntiles, sms));
   ess_nu_gen_tc_kernel<<<grid, TC_THREADS, smem, st>>>(v, img);
   return cudaGetLastError();
 }

@@ -45,6 +45,24 @@ struct Key {
   }
 };
 
+// Hardware base-2 exponential and logarithm and square root (PTX ex2.approx,
+// lg2.approx, sqrt.approx; single precision, relative error ~2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---- conversions ----------------------------------------------------------------------------
 // Uniform in (0,1): u = ((hi:lo >> 12) + 1/2) 2^-52, exact in double.  1 - u is the same map of
 // the complemented words, which gives log u accurately near 1 in single precision.
@@ -84,11 +102,12 @@ template <> struct Conv<float> {
   }
   // single-precision rounding of the one-word uniform (w + 1/2) 2^-32
   static __device__ __forceinline__ float u32(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
-  // Box-Muller with the hardware approximations: the radius from __logf (absolute error
-  // ~4e-7 in log u) and the angle phi = 2 pi u written as psi + pi with psi in [-pi, pi),
-  // where __sincosf is accurate to ~5e-7 (cos phi = -cos psi, sin phi = -sin psi).
+  // Box-Muller with the hardware approximations: the radius r = sqrt(-2 ln 2 log2 u) from
+  // lg2.approx and sqrt.approx (relative error ~2^-22 each), and the angle phi = 2 pi u written
+  // as psi + pi with psi in [-pi, pi), where __sincosf is accurate to ~5e-7
+  // (cos phi = -cos psi, sin phi = -sin psi).
   static __device__ __forceinline__ void bm(uint32_t a, uint32_t b, float& z0, float& z1) {
-    const float r = sqrtf(fmaxf(-2.0f * __logf(u32(a)), 0.f));
+    const float r = sqrt_approx(fmaxf(lg2_approx(u32(a)) * -1.38629436111989061883f, 0.f));
     const float psi = fmaf(6.28318530717958647692f, u32(b), -3.14159265358979323846f);
     float s, c;
     __sincosf(psi, &s, &c);
@@ -103,14 +122,23 @@ template <> struct Conv<float> {
 };
 
 // ---- chain-group reductions -------------------------------------------------------------------
-// A chain is owned by G consecutive lanes (G = 1 chain-per-thread, G = 32 chain-per-warp).
-// Butterfly sums give every lane of the group the same bits.
+// A chain is owned by G consecutive lanes (G = 1 chain-per-thread, G = 16 two chains per warp,
+// G = 32 chain-per-warp).  Butterfly sums give every lane of the group the same bits.  `mask`
+// names the lanes of the calling group (group_mask<G>()): groups of one warp may be at
+// different points of their loops, so a sub-warp group never names the other group's lanes.
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (G >= 32) return 0xffffffffu;
+  else return ((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(G - 1));
+}
+
 template <int G, typename T>
-__device__ __forceinline__ T group_sum(T v) {
+__device__ __forceinline__ T group_sum(T v, unsigned mask = 0xffffffffu) {
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
   return v;
 }
+
 
 // ---- bounded grid barrier (cooperative launches only) ----------------------------------------
 // Sense-free generation barrier.  Every wait is bounded: after kBarrierSpinLimit polls the

@@ -41,6 +41,11 @@ struct EssView : ChainsView<T> {
   T* nu;                 // [m][W][dstride] pre-generated ellipse directions
   unsigned long long* gen_cols;  // directions generated so far (statistics)
   int own_window;        // 1: the FSM kernel sets the next refill window itself
+  // Compacted refill list (tensor-core generator): col_base[c] = sum over chains c' < c of
+  // gen_hi - gen_lo, col_base[m] = total; colmap[j] = (chain, sample) of refill column j.
+  // Null: the generator walks (chain block, ring offset) tiles instead.
+  long long* col_base = nullptr;
+  int2* colmap = nullptr;
 };
 
 template <typename T>

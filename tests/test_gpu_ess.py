@@ -78,6 +78,55 @@ def test_tensor_core_generator_matches_oracle(eng, d):
         job.close()
 
 
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_two_chains_per_warp_fp64_matches_oracle(eng, mode):
+    # 16 lanes per chain (two chains share a warp), d = 48 (ragged: 3 coordinates per lane),
+    # 100 chains (ragged last warp); FP64 gives the oracle's loop counts exactly
+    w = W.gauss_conj(48)
+    m, n = 100, 300
+    x0 = W.x0_normal(m, 48, scale=0.3)
+    job = _run(eng, w, m, n, x0, "fp64", mode, tuning={"lanes_per_chain": 16, "steps_per_launch": 24})
+    assert job.tuning()["lanes_per_chain"] == 16
+    ref = O.run("ess", "gauss_conj", w["params"], x0, n, seed=1)
+    counts, _, steps = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    if mode == "fsm":
+        assert np.array_equal(steps, (counts + 1).sum(1))
+    job.close()
+
+
+@pytest.mark.parametrize("lanes", [16, 32])
+def test_fp32_gp_logit_lanes_match_oracle_and_sync(eng, lanes):
+    # the single-precision base-2 GP-logit likelihood: FSM and synchronised kernels agree bit
+    # for bit, and both follow the oracle to the FP32 tolerance (d = 200: ragged rows)
+    w = W.gp_logit(200)
+    m, n = 72, 150
+    x0 = W.x0_normal(m, 200, scale=0.1)
+    tu = {"lanes_per_chain": lanes, "generator": 2}
+    a = _run(eng, w, m, n, x0, "fp32", "fsm", tuning=tu)
+    b = _run(eng, w, m, n, x0, "fp32", "sync", tuning=tu)
+    ca, _, _ = a.loop_counts()
+    cb, _, _ = b.loop_counts()
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(a.samples(), b.samples())
+    ref = O.run("ess", "gp_logit", w["params"], x0, n, seed=1)
+    r = compare(a.samples(), ca, ref["samples"], ref["counts"], "fp32")
+    print("lanes", lanes, "flipped", r["flipped"], "max err", r["max_err"])
+    assert r["flipped"] <= m // 4
+    a.close()
+    b.close()
+
+
+def test_gp_logit_labels_must_be_signs(eng):
+    from paper_2503_17405_b300 import fsmc
+    w = W.gp_logit(8)
+    p = np.array(w["params"], dtype=np.float64)
+    p[8 * 8 + 3] = 0.5
+    with pytest.raises(fsmc.FsmcError):
+        eng.target("gp_logit", 8, p)
+
+
 def test_sync_and_fsm_give_identical_samples(eng):
     w = W.gp_logit(256)
     m, n = 300, 64
