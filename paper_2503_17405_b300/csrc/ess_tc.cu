@@ -27,8 +27,10 @@ namespace fsmc {
 
 namespace {
 
-constexpr int TC_THREADS = 512;
+constexpr int TC_PRODUCER_WARPS = 16;
+constexpr int TC_THREADS = (TC_PRODUCER_WARPS + 1) * 32;  // + the MMA / column-list warp
 constexpr int TC_N = 64;          // columns per tile
+constexpr int TC_TMEM_COLS = 256; // two accumulator buffers of (row tile 0, row tile 1) x 64 columns
 constexpr int TC_KC = 64;         // k per staged chunk
 constexpr int TC_STAGE = TC_N * TC_KC * 2;  // bytes of one FP16 part of a z chunk (8 KB)
 constexpr unsigned kWaitLimit = 1u << 20;  // polls; with the back-off below, well under 2 s
@@ -41,8 +43,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// bounded wait for the phase with the given parity to complete; gives up early once another
+// warp has recorded a failure in *fail (when fail is not null)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volatile int* fail) {
   const uint32_t a = smem_u32(bar);
   for (unsigned it = 0; it < kWaitLimit; ++it) {
     uint32_t done;
@@ -52,9 +55,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (it > 64) __nanosleep(32);
+    if (it > 64) {
+      if (fail && (it & 255) == 0 && *fail) return false;
+      __nanosleep(32);
+    }
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// warp-uniform forms: every lane polls, and the warp proceeds only if every lane saw the phase
+// complete; the failure flag is read once (lane 0) for the whole warp
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, volatile int* fail) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, fail));
+}
+__device__ __forceinline__ bool warp_failed(volatile int* fail) {
+  return __shfl_sync(0xffffffffu, *fail, 0) != 0;
 }
 
 // tensor-core shared-memory matrix descriptor: K-major, no swizzle
@@ -127,224 +146,295 @@ __global__ void ess_tc_build_a_kernel(const float* L, int d, unsigned char* img)
   }
 }
 
+// Shared-memory layout after the A image and the two z stages.
+struct TcBars {
+  uint64_t a;              // L image loaded (TMA transaction count)
+  uint64_t full[2];        // z stage written (one arrival per producer warp)
+  uint64_t empty[2];       // z stage consumed (tcgen05.commit)
+  uint64_t acc_full[2];    // accumulator buffer complete (tcgen05.commit)
+  uint64_t acc_empty[2];   // accumulator buffer read out (one arrival per producer warp)
+  uint64_t cols_full[2];   // column list of a tile written (MMA warp)
+  uint64_t cols_empty[2];  // column list no longer read (one arrival per producer warp)
+  uint64_t drain;          // teardown: every issued MMA has completed
+  uint32_t tmem;
+  int fail;
+};
+struct TcCols {
+  long long dst[2][TC_N];  // ring row offset of each column, -1: no column
+  int sample[2][TC_N];
+  int chain[2][TC_N];
+};
+
+__host__ __device__ inline int tc_smem_bytes(int d) {
+  return tc_layout(d).a_bytes + 2 * 2 * TC_STAGE + (int)sizeof(TcBars) + (int)sizeof(TcCols);
+}
+
+// Warp-specialised pipeline over tiles of 64 refill columns:
+//  * warps 0..15 (producers) write z chunks into two shared-memory stages, and read out the
+//    accumulators of the previous tile (right after the first chunk of the next one, so the
+//    last MMAs of a tile overlap with the next tile's first chunk);
+//  * warp 16 issues the tcgen05 MMAs (one elected lane) into one of two tensor-memory
+//    accumulator buffers, and loads the next tile's column list while the producers work.
+// Every handoff is an mbarrier; every wait is bounded and also ends when another warp has
+// recorded a failure.
 __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<float> v, const unsigned char* a_img) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int d = v.tg.d;
   const TcLayout lay = tc_layout(d);
   unsigned char* sA = sm;
-  unsigned char* sB = sm + lay.a_bytes;                 // 2 stages x (hi, lo)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 2 * 2 * TC_STAGE);
-  uint64_t* bar_a = bars;
-  uint64_t* bar_mma = bars + 1;  // [2]
-  uint64_t* bar_done = bars + 3;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  int* s_fail_p = reinterpret_cast<int*>(bars + 5);
-  long long* col_dst = reinterpret_cast<long long*>(bars + 8);  // [TC_N] ring row offset, -1: none
-  int* col_sample = reinterpret_cast<int*>(col_dst + TC_N);      // [TC_N]
-  int* col_chain = col_sample + TC_N;                              // [TC_N]
-  volatile int& s_fail = *s_fail_p;
+  unsigned char* sB = sm + lay.a_bytes;  // 2 stages x (hi, lo)
+  TcBars* bars = reinterpret_cast<TcBars*>(sB + 2 * 2 * TC_STAGE);
+  TcCols* cols = reinterpret_cast<TcCols*>(bars + 1);
+  volatile int* fail = &bars->fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool mma_warp = warp == TC_PRODUCER_WARPS;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const int nchunks = lay.kpad / TC_KC;
-  const int nbx = (int)((v.m + TC_N - 1) / TC_N);
-  const long long total = v.colmap ? v.col_base[v.m] : 0;
-  const long long ntiles = v.colmap ? (total + TC_N - 1) / TC_N : (long long)nbx * v.W;
-  if (v.colmap && blockIdx.x == 0 && tid == 0 && total > 0) atomicAdd(v.gen_cols, (unsigned long long)total);
+  const long long total = v.col_base[v.m];
+  const long long ntiles = (total + TC_N - 1) / TC_N;
+  if (blockIdx.x == 0 && tid == 0 && total > 0) atomicAdd(v.gen_cols, (unsigned long long)total);
 
   if (tid == 0) {
-    s_fail = 0;
-    mbar_init(bar_a, 1);
-    mbar_init(&bar_mma[0], 1);
-    mbar_init(&bar_mma[1], 1);
-    mbar_init(bar_done, 1);
+    bars->fail = 0;
+    mbar_init(&bars->a, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bars->full[i], TC_PRODUCER_WARPS);
+      mbar_init(&bars->empty[i], 1);
+      mbar_init(&bars->acc_full[i], 1);
+      mbar_init(&bars->acc_empty[i], TC_PRODUCER_WARPS);
+      mbar_init(&bars->cols_full[i], 1);
+      mbar_init(&bars->cols_empty[i], TC_PRODUCER_WARPS);
+    }
+    mbar_init(&bars->drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tmem_slot)));
+  if (mma_warp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tmem)),
+                 "r"(TC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = bars->tmem;
 
-  // L image -> shared memory (bulk TMA copies of at most 48 KB, completion via tx count)
-  if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar_a)),
-                 "r"(lay.a_bytes)
-                 : "memory");
-    for (int off = 0; off < lay.a_bytes; off += 48 * 1024) {
-      const int n = min(48 * 1024, lay.a_bytes - off);
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              smem_u32(sA + off)),
-          "l"(a_img + off), "r"(n), "r"(smem_u32(bar_a))
-          : "memory");
-    }
-  }
-  if (!mbar_wait(bar_a, 0)) s_fail = 1;
-  __syncthreads();
-
-  const uint32_t idesc = idesc_f16(128, TC_N);
-  const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
-  const uint32_t a_rt0 = sA_u, a_rt1 = sA_u + 128 * lay.K0 * 4;
-  unsigned stage_phase[2] = {0u, 0u};
-  unsigned done_phase = 0;
-  long long chunk_ctr = 0;
-  bool mma_pending = false;
-
-  // z-generation roles: this lane's column and k half are the same for every chunk; a warp
-  // fills two core matrices (8 columns x 8 k, 128 contiguous bytes each) per pass
-  const int zn = (((2 * warp + (lane >> 4)) & 7) << 3) + ((lane >> 1) & 7);  // column 0..63
-  const int zkh = lane & 1;
-  constexpr int kPasses = 64 / (2 * (TC_THREADS / 32));  // core-matrix pairs per warp per chunk
-
-  for (long long tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
-    int active = 0;
-    if (tid < TC_N) {
-      int c = -1, smp = -1;
-      if (v.colmap) {
-        const long long jc = tile * TC_N + tid;
+  if (mma_warp) {
+    // ---------------------------------------------------------------- MMA / column-list warp
+    // column list of local tile i (tile blockIdx.x + i * gridDim.x) into buffer i & 1
+    auto load_cols = [&](long long i) {
+      const int bb = (int)(i & 1);
+      const long long tile = blockIdx.x + i * gridDim.x;
+#pragma unroll
+      for (int r = 0; r < TC_N / 32; ++r) {
+        const int n = lane + 32 * r;
+        const long long jc = tile * TC_N + n;
+        int c = -1, smp = -1;
         if (jc < total) {
           const int2 e = v.colmap[jc];
           c = e.x;
           smp = e.y;
         }
-      } else {
-        const int bx = (int)(tile % nbx), w = (int)(tile / nbx);
-        const int64_t cc = (int64_t)bx * TC_N + tid;
-        if (cc < v.m) {
-          const int s = v.gen_lo[cc] + w;
-          if (s < v.gen_hi[cc]) { c = (int)cc; smp = s; }
-        }
+        cols->chain[bb][n] = c;
+        cols->sample[bb][n] = smp;
+        cols->dst[bb][n] = smp >= 0 ? ((long long)c * v.W + smp % v.W) * v.dstride : -1;
       }
-      col_chain[tid] = c;
-      col_sample[tid] = smp;
-      col_dst[tid] = smp >= 0 ? ((long long)c * v.W + smp % v.W) * v.dstride : -1;
-      active = smp >= 0;
-    }
-    const int n_active = __syncthreads_count(active);
-    if (n_active == 0) continue;
-    if (!v.colmap && tid == 0) atomicAdd(v.gen_cols, (unsigned long long)n_active);
-    const int z_smp = col_sample[zn];
-    const Key zkey{(uint32_t)(v.chain0 + col_chain[zn]), v.seed_lo, v.seed_hi};
-
-    for (int kc = 0; kc < nchunks; ++kc, ++chunk_ctr) {
-      const int s = (int)(chunk_ctr & 1);
-      if (chunk_ctr >= 2) {  // the MMAs that read this stage two chunks ago must be done
-        if (!mbar_wait(&bar_mma[s], stage_phase[s])) s_fail = 1;
-        stage_phase[s] ^= 1u;
-      }
-      unsigned char* zhi = sB + s * 2 * TC_STAGE;
-      unsigned char* zlo = zhi + TC_STAGE;
-      // all Philox blocks of the pass first (independent, so their rounds interleave), then
-      // Box-Muller, the FP16 hi/lo split and the stores
-      P4 blk[kPasses];
-#pragma unroll
-      for (int it = 0; it < kPasses; ++it) {
-        const int kg = (2 * (warp + (TC_THREADS / 32) * it) + (lane >> 4)) >> 3;
-        const int q = kc * (TC_KC / 4) + kg * 2 + zkh;  // Philox draw: normals 4q .. 4q+3
-        blk[it] = (z_smp >= 0 && q < D) ? zkey.block((uint32_t)z_smp, 0, (uint32_t)q) : P4{0u, 0u, 0u, 0u};
-      }
-#pragma unroll
-      for (int it = 0; it < kPasses; ++it) {
-        const int kg = (2 * (warp + (TC_THREADS / 32) * it) + (lane >> 4)) >> 3;
-        const int q = kc * (TC_KC / 4) + kg * 2 + zkh;
-        float z[4] = {0.f, 0.f, 0.f, 0.f};
-        if (z_smp >= 0 && q < D) {
-          Conv<float>::normal_quad(blk[it], z);
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (4 * q + i >= d) z[i] = 0.f;
-        }
-        __half h[4], l[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          h[i] = __float2half_rn(z[i]);
-          l[i] = __float2half_rn(z[i] - __half2float(h[i]));
-        }
-        const __half2 h01 = __halves2half2(h[0], h[1]), h23 = __halves2half2(h[2], h[3]);
-        const __half2 l01 = __halves2half2(l[0], l[1]), l23 = __halves2half2(l[2], l[3]);
-        const int off = (zn >> 3) * (TC_KC / 8) * 128 + kg * 128 + (zn & 7) * 16 + zkh * 8;
-        *reinterpret_cast<uint2*>(zhi + off) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
-        *reinterpret_cast<uint2*>(zlo + off) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (s_fail) break;
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t bh = sB_u + s * 2 * TC_STAGE, bl = bh + TC_STAGE;
-#pragma unroll
-        for (int ks = 0; ks < TC_KC / 16; ++ks) {
-          const int kglob = kc * TC_KC + ks * 16;
-          const uint64_t dbh = sdesc(bh + ks * 256, 128, (TC_KC / 8) * 128);
-          const uint64_t dbl = sdesc(bl + ks * 256, 128, (TC_KC / 8) * 128);
-          if (kglob < lay.K0) {
-            const uint32_t ah = a_rt0 + (kglob / 8) * 128, al = ah + 128 * lay.K0 * 2;
-            const uint32_t sbo = (lay.K0 / 8) * 128;
-            mma_f16(tmem, sdesc(ah, 128, sbo), dbh, idesc, kglob > 0);
-            mma_f16(tmem, sdesc(ah, 128, sbo), dbl, idesc, 1);
-            mma_f16(tmem, sdesc(al, 128, sbo), dbh, idesc, 1);
-          }
-          if (lay.K1) {
-            const uint32_t ah = a_rt1 + (kglob / 8) * 128, al = ah + 128 * lay.K1 * 2;
-            const uint32_t sbo = (lay.K1 / 8) * 128;
-            mma_f16(tmem + TC_N, sdesc(ah, 128, sbo), dbh, idesc, kglob > 0);
-            mma_f16(tmem + TC_N, sdesc(ah, 128, sbo), dbl, idesc, 1);
-            mma_f16(tmem + TC_N, sdesc(al, 128, sbo), dbh, idesc, 1);
-          }
-        }
-        mma_commit(&bar_mma[s]);
-        if (kc == nchunks - 1) mma_commit(bar_done);
-      }
-      mma_pending = true;
-    }
-    if (s_fail) break;
-    // accumulators complete -> registers -> direction rings
-    if (!mbar_wait(bar_done, done_phase)) s_fail = 1;
-    done_phase ^= 1u;
-    __syncthreads();
-    if (s_fail) break;
-    mma_pending = false;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // warp w: row tile (w >> 2) & 1, lane quadrant w & 3, column half w >> 3
-    const int rt = (warp >> 2) & 1;
-    if (rt == 0 || lay.K1) {
-      const int row = rt * 128 + (warp & 3) * 32 + lane;
-      const int jbeg = (warp >> 3) * (TC_N / 2);
-#pragma unroll
-      for (int j0 = jbeg; j0 < jbeg + TC_N / 2; j0 += 16) {
-        uint32_t r[16];
-        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(rt * TC_N + j0);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->cols_full[bb]);
+    };
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (my_tiles > 0) load_cols(0);
+    if (lane == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars->a)),
+                   "r"(lay.a_bytes)
+                   : "memory");
+      for (int off = 0; off < lay.a_bytes; off += 48 * 1024) {
+        const int n = min(48 * 1024, lay.a_bytes - off);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < d) {
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sA + off)),
+            "l"(a_img + off), "r"(n), "r"(smem_u32(&bars->a))
+            : "memory");
+      }
+    }
+    if (!warp_wait(&bars->a, 0, fail)) *fail = 1;
+    const uint32_t idesc = idesc_f16(128, TC_N);
+    const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+    const uint32_t a_rt0 = sA_u, a_rt1 = sA_u + 128 * lay.K0 * 4;
+    long long chunk_ctr = 0;
+    bool issued = false;
+    for (long long i = 0; i < my_tiles && !warp_failed(fail); ++i) {
+      const int bb = (int)(i & 1);
+      const uint32_t acc = tmem + (uint32_t)(bb * 2 * TC_N);
+      if (i >= 2 && !warp_wait(&bars->acc_empty[bb], (unsigned)(((i >> 1) - 1) & 1), fail)) {
+        *fail = 1;
+        break;
+      }
+      for (int kc = 0; kc < nchunks && !warp_failed(fail); ++kc, ++chunk_ctr) {
+        const int s = (int)(chunk_ctr & 1);
+        if (!warp_wait(&bars->full[s], (unsigned)((chunk_ctr >> 1) & 1), fail)) {
+          *fail = 1;
+          break;
+        }
+        if (lane == 0) {
+          {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t bh = sB_u + s * 2 * TC_STAGE, bl = bh + TC_STAGE;
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const long long dst = col_dst[j0 + jj];
-            if (dst >= 0) v.nu[dst + row] = __uint_as_float(r[jj]);
+            for (int ks = 0; ks < TC_KC / 16; ++ks) {
+              const int kglob = kc * TC_KC + ks * 16;
+              const uint64_t dbh = sdesc(bh + ks * 256, 128, (TC_KC / 8) * 128);
+              const uint64_t dbl = sdesc(bl + ks * 256, 128, (TC_KC / 8) * 128);
+              if (kglob < lay.K0) {
+                const uint32_t ah = a_rt0 + (kglob / 8) * 128, al = ah + 128 * lay.K0 * 2;
+                const uint32_t sbo = (lay.K0 / 8) * 128;
+                mma_f16(acc, sdesc(ah, 128, sbo), dbh, idesc, kglob > 0);
+                mma_f16(acc, sdesc(ah, 128, sbo), dbl, idesc, 1);
+                mma_f16(acc, sdesc(al, 128, sbo), dbh, idesc, 1);
+              }
+              if (lay.K1) {
+                const uint32_t ah = a_rt1 + (kglob / 8) * 128, al = ah + 128 * lay.K1 * 2;
+                const uint32_t sbo = (lay.K1 / 8) * 128;
+                mma_f16(acc + TC_N, sdesc(ah, 128, sbo), dbh, idesc, kglob > 0);
+                mma_f16(acc + TC_N, sdesc(ah, 128, sbo), dbl, idesc, 1);
+                mma_f16(acc + TC_N, sdesc(al, 128, sbo), dbh, idesc, 1);
+              }
+            }
+            issued = true;
+            mma_commit(&bars->empty[s]);
+            if (kc == nchunks - 1) mma_commit(&bars->acc_full[bb]);
           }
+        }
+        __syncwarp();
+        // the next tile's column list, once the producers have read out tile i-1 (its buffer)
+        if (kc == 0 && i + 1 < my_tiles) {
+          if (i >= 1 && !warp_wait(&bars->cols_empty[bb ^ 1], (unsigned)(((i - 1) >> 1) & 1), fail)) {
+            *fail = 1;
+            break;
+          }
+          load_cols(i + 1);
         }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    // teardown: every issued MMA must have completed before tensor memory is freed
+    if (lane == 0 && issued) {
+      mma_commit(&bars->drain);
+      mbar_wait(&bars->drain, 0, nullptr);
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- producer warps
+    // z roles: this lane's column and k half are the same for every chunk; a warp fills two
+    // core matrices (8 columns x 8 k, 128 contiguous bytes each) per pass
+    const int zn = (((2 * warp + (lane >> 4)) & 7) << 3) + ((lane >> 1) & 7);  // column 0..63
+    const int zkh = lane & 1;
+    constexpr int kPasses = 64 / (2 * TC_PRODUCER_WARPS);  // core-matrix pairs per warp per chunk
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // accumulators of local tile i -> the chains' direction rings
+    // (warp w: row tile (w >> 2) & 1, tensor-memory lane quadrant w & 3, column half w >> 3)
+    auto epilogue = [&](long long i) {
+      const int bb = (int)(i & 1);
+      if (!warp_wait(&bars->acc_full[bb], (unsigned)((i >> 1) & 1), fail)) { *fail = 1; return; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int rt = (warp >> 2) & 1;
+      if (rt == 0 || lay.K1) {
+        const int row = rt * 128 + (warp & 3) * 32 + lane;
+        const int jbeg = (warp >> 3) * (TC_N / 2);
+#pragma unroll
+        for (int j0 = jbeg; j0 < jbeg + TC_N / 2; j0 += 16) {
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                 (uint32_t)(bb * 2 * TC_N + rt * TC_N + j0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (row < d) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const long long dst = cols->dst[bb][j0 + jj];
+              if (dst >= 0) v.nu[dst + row] = __uint_as_float(r[jj]);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars->acc_empty[bb]);
+        mbar_arrive(&bars->cols_empty[bb]);
+      }
+    };
+    long long chunk_ctr = 0;
+    long long i = 0;
+    for (; i < my_tiles && !warp_failed(fail); ++i) {
+      const int bb = (int)(i & 1);
+      if (!warp_wait(&bars->cols_full[bb], (unsigned)((i >> 1) & 1), fail)) { *fail = 1; break; }
+      const int z_smp = cols->sample[bb][zn];
+      const Key zkey{(uint32_t)(v.chain0 + cols->chain[bb][zn]), v.seed_lo, v.seed_hi};
+      bool broke = false;
+      for (int kc = 0; kc < nchunks; ++kc, ++chunk_ctr) {
+        const int s = (int)(chunk_ctr & 1);
+        if (warp_failed(fail) ||
+            (chunk_ctr >= 2 && !warp_wait(&bars->empty[s], (unsigned)(((chunk_ctr >> 1) - 1) & 1), fail))) {
+          *fail = 1;
+          broke = true;
+          break;
+        }
+        unsigned char* zhi = sB + s * 2 * TC_STAGE;
+        unsigned char* zlo = zhi + TC_STAGE;
+        const bool whole = (kc + 1) * TC_KC <= d;  // no coordinate of the chunk lies beyond d
+        // all Philox blocks of the chunk first (independent, so their rounds interleave), then
+        // Box-Muller, the FP16 hi/lo split and the stores
+        P4 blk[kPasses];
+#pragma unroll
+        for (int it = 0; it < kPasses; ++it) {
+          const int kg = (2 * (warp + TC_PRODUCER_WARPS * it) + (lane >> 4)) >> 3;
+          const int q = kc * (TC_KC / 4) + kg * 2 + zkh;  // Philox draw: normals 4q .. 4q+3
+          blk[it] = (z_smp >= 0 && q < D) ? zkey.block((uint32_t)z_smp, 0, (uint32_t)q) : P4{0u, 0u, 0u, 0u};
+        }
+#pragma unroll
+        for (int it = 0; it < kPasses; ++it) {
+          const int kg = (2 * (warp + TC_PRODUCER_WARPS * it) + (lane >> 4)) >> 3;
+          const int q = kc * (TC_KC / 4) + kg * 2 + zkh;
+          float z[4] = {0.f, 0.f, 0.f, 0.f};
+          if (z_smp >= 0 && q < D) {
+            Conv<float>::normal_quad(blk[it], z);
+            if (!whole) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (4 * q + e >= d) z[e] = 0.f;
+            }
+          }
+          const __half2 h01 = __float22half2_rn(make_float2(z[0], z[1]));
+          const __half2 h23 = __float22half2_rn(make_float2(z[2], z[3]));
+          const float2 b01 = __half22float2(h01), b23 = __half22float2(h23);
+          const __half2 l01 = __float22half2_rn(make_float2(z[0] - b01.x, z[1] - b01.y));
+          const __half2 l23 = __float22half2_rn(make_float2(z[2] - b23.x, z[3] - b23.y));
+          const int off = (zn >> 3) * (TC_KC / 8) * 128 + kg * 128 + (zn & 7) * 16 + zkh * 8;
+          *reinterpret_cast<uint2*>(zhi + off) =
+              make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+          *reinterpret_cast<uint2*>(zlo + off) =
+              make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->full[s]);
+        if (kc == 0 && i >= 1) epilogue(i - 1);
+      }
+      if (broke) break;
+    }
+    if (i == my_tiles && my_tiles > 0 && !warp_failed(fail)) epilogue(my_tiles - 1);
   }
-  // teardown: no MMA may still be writing tensor memory when it is freed
-  if (tid == 0 && mma_pending) mma_commit(bar_done);
-  if (mma_pending) mbar_wait(bar_done, done_phase);
-  if (s_fail && tid == 0) atomicOr(v.err, ERR_BARRIER_TIMEOUT);
+  if (*fail && tid == 0) atomicOr(v.err, ERR_BARRIER_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+  if (mma_warp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
 // Refill counts -> exclusive prefix sum col_base[0..m] (one block, chains in passes of
@@ -415,18 +505,15 @@ cudaError_t launch_ess_tc_build(const float* L, int d, unsigned char* img, cudaS
 }
 
 cudaError_t launch_ess_nu_gen_tc(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st) {
-  const TcLayout lay = tc_layout(v.tg.d);
-  const int smem = lay.a_bytes + 2 * 2 * TC_STAGE + 64 + TC_N * (8 + 4 + 4);
+  if (!v.colmap || !v.col_base) return cudaErrorInvalidValue;  // the generator walks the compacted list
+  const int smem = tc_smem_bytes(v.tg.d);
   cudaError_t e = cudaFuncSetAttribute(ess_nu_gen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if (v.colmap) {
-    ess_col_scan_kernel<<<1, 1024, 0, st>>>(v.gen_lo, v.gen_hi, v.m, v.col_base);
-    ess_col_fill_kernel<<<(unsigned)((v.m + 255) / 256), 256, 0, st>>>(v.gen_lo, v.gen_hi, v.col_base, v.m,
-                                                                       v.colmap);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  const int nbx = (int)((v.m + TC_N - 1) / TC_N);
-  const long long ntiles = v.colmap ? ((long long)v.m * v.W + TC_N - 1) / TC_N : (long long)nbx * v.W;
+  ess_col_scan_kernel<<<1, 1024, 0, st>>>(v.gen_lo, v.gen_hi, v.m, v.col_base);
+  ess_col_fill_kernel<<<(unsigned)((v.m + 255) / 256), 256, 0, st>>>(v.gen_lo, v.gen_hi, v.col_base, v.m,
+                                                                     v.colmap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long ntiles = ((long long)v.m * v.W + TC_N - 1) / TC_N;
   const int grid = (int)std::max(1LL, std::min<long long>(ntiles, sms));
   ess_nu_gen_tc_kernel<<<grid, TC_THREADS, smem, st>>>(v, img);
   return cudaGetLastError();
