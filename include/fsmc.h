@@ -96,8 +96,9 @@ typedef struct fsmc_nuts_params {
 /* Launch shape.  Zero fields mean "choose automatically" (the autotuner's cached
  * choice, else a heuristic on the log-density cost). */
 typedef struct fsmc_tuning {
-  int lanes_per_chain;   /* 1 = chain-per-thread, 16 = two chains per warp (ESS,
-                            32 < d <= 512), 32 = chain-per-warp, 0 = auto               */
+  int lanes_per_chain;   /* 1 = chain-per-thread, 8 = four chains per warp (ESS,
+                            32 < d <= 256), 16 = two chains per warp (ESS, 32 < d <= 512),
+                            32 = chain-per-warp, 0 = auto                                */
   int steps_per_launch;  /* FSM states each chain advances per launch                    */
   int ring_slots;        /* ESS: pre-generated ellipse directions kept per chain         */
   int threads_per_block; /* 32..256, multiple of 32                                      */

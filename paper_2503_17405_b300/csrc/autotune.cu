@@ -59,6 +59,7 @@ std::vector<fsmc_tuning> candidates(fsmc_target* t, fsmc_algo algo, fsmc_precisi
     std::vector<int> lanes = {32};
     if (t->d <= 32) lanes.push_back(1);
     if (t->d > 32 && t->d <= 512) lanes.push_back(16);
+    if (t->d > 32 && t->d <= 256) lanes.push_back(8);
     std::vector<int> gens = {1};
     if (prec == FSMC_FP32 && t->d <= 256) gens.push_back(2);
     for (int G : lanes)

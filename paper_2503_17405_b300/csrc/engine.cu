@@ -516,11 +516,14 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (!j || !tu) return fsmc_fail(FSMC_EINVAL, "NULL argument");
   if (j->dev) return fsmc_fail(FSMC_ESTATE, "tuning must be set before the first run");
   fsmc_tuning t = *tu;
-  if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 16 && t.lanes_per_chain != 32)
-    return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1, 16 or 32");
+  if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 8 && t.lanes_per_chain != 16 &&
+      t.lanes_per_chain != 32)
+    return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1, 8, 16 or 32");
   if (j->algo == FSMC_DR && t.lanes_per_chain > 1) return fsmc_fail(FSMC_EINVAL, "DR is chain-per-thread");
   if (t.lanes_per_chain == 16 && (j->algo != FSMC_ESS || j->d <= 32 || j->d > 512))
     return fsmc_fail(FSMC_EINVAL, "16 lanes per chain: ESS jobs with 32 < d <= 512");
+  if (t.lanes_per_chain == 8 && (j->algo != FSMC_ESS || j->d <= 32 || j->d > 256))
+    return fsmc_fail(FSMC_EINVAL, "8 lanes per chain: ESS jobs with 32 < d <= 256");
   if (j->algo == FSMC_NUTS && t.lanes_per_chain && t.lanes_per_chain != 32)
     return fsmc_fail(FSMC_EINVAL, "NUTS is chain-per-warp (32 lanes)");
   if (j->algo == FSMC_ESS && t.lanes_per_chain == 1 && j->d > 32)

@@ -175,22 +175,23 @@ __device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E
   return T(0);  // TGT_FLAT
 }
 
-// GP-logit likelihood in single precision, in base 2.  With labels s_i = +-1 and
-// c_i = -s_i log2(e), the lanes keep xs = c x and ns = c nu, so that t' = c x' =
-// xs cos(th) + ns sin(th) needs no per-coordinate scaling, and
+// GP-logit likelihood in single precision, in base 2.  With labels s_i = +-1 the lanes keep the
+// sign-folded coordinates xs = -s x and ns = -s nu (exact), and the step scales cos(th) and
+// sin(th) by log2(e) once, so that t' = log2(e) (-s_i x'_i) = xs cs2 + ns sn2 costs one
+// multiply-add per coordinate and
 //   softplus(-s_i x'_i) = ln 2 [max(t', 0) + log2(1 + 2^-|t'|)].
 // Two hardware approximations per coordinate (ex2, lg2), both with absolute error ~2e-7 here.
 constexpr float kLn2f = 0.693147180559945309417f;
 constexpr float kLog2ef = 1.44269504088896340736f;
 
-template <int G, int E>
-__device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const float (&ns)[E], float cs, float sn,
+template <int G, int E, bool FULL = false>
+__device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const float (&ns)[E], float cs2, float sn2,
                                                  int lane, int d, unsigned gmask) {
   float a = 0.f, b = 0.f;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    if (e * G + lane < d) {
-      const float t = fmaf(xs[e], cs, ns[e] * sn);
+    if (FULL || e * G + lane < d) {
+      const float t = fmaf(xs[e], cs2, ns[e] * sn2);
       a += fmaxf(t, 0.f);
       b += lg2_approx(1.f + ex2_approx(-fabsf(t)));
     }
@@ -198,10 +199,14 @@ __device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const flo
   return -kLn2f * group_sum<G>(a + b, gmask);
 }
 
-// The fast GP-logit path is taken for single-precision GP-logit jobs whose lanes hold at most
-// 16 coordinates (the extra per-lane arrays then stay in registers).
+// sign of coordinate e flipped where bit e of mask is set (exact)
+__device__ __forceinline__ float flip_sign(float v, uint32_t mask, int e) {
+  return __int_as_float(__float_as_int(v) ^ (int)((mask >> e) << 31));
+}
+
+// The base-2 GP-logit path is taken for every single-precision GP-logit job.
 template <typename T, int E>
-constexpr bool kEssGpFast = sizeof(T) == 4 && E <= 16;
+constexpr bool kEssGpFast = sizeof(T) == 4;
 
 // Slice threshold log y = log f(x) + log u.  In single precision a u within ~1e-5 of 1 makes
 // the sum round back to log f(x); the bracket would then shrink onto theta = 0 without ever
@@ -236,16 +241,16 @@ __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
   sum = t;
 }
 
-template <typename T, int G, int E>
+template <typename T, int G, int E, bool FULL = false>
 __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, int lane,
                                          const T (&x)[E]) {
-  const int d = v.tg.d;
+  const int d = FULL ? E * G : v.tg.d;
   if (v.out) {
     T* dst = v.out + ((size_t)c * v.n + t) * d;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = e * G + lane;
-      if (k < d) dst[k] = x[e];
+      if (FULL || k < d) dst[k] = x[e];
     }
   } else {
 #pragma unroll
@@ -267,141 +272,238 @@ __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, 
 // ------------------------------------------------------------------------------------------
 // FSM kernel: every chain advances `budget` states (fewer if its ring runs dry or it
 // finishes).  Chain-group layout: G lanes own one chain, lane l holds coordinates l, l+G, ...
-// GP: single-precision GP-logit likelihood in base 2 (ess_loglik_gp32); the lanes then also
-// keep xs = c x and ns = c nu, and yv holds c = -s log2(e) instead of the labels s.
-template <typename T, int G, int E, bool GP>
-__device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c, int budget, int lane) {
+// Chain groups of 8 or more lanes draw G consecutive Philox blocks of the current sample at
+// once (lane l holds draw D + cbase + l) and each state fetches its words by shuffle, instead
+// of every lane computing the same block; chain-per-thread computes the block it needs.
+template <int G>
+struct PhiloxLaneCache {
+  P4 cache{0u, 0u, 0u, 0u};
+  int cbase = -(1 << 30);
+  __device__ __forceinline__ void reset() { cbase = -(1 << 30); }
+  __device__ __forceinline__ P4 fetch(const Key& key, int t, int D, int off, int lane, unsigned gmask) {
+    if constexpr (G >= 8) {
+      if (off - cbase >= G || off < cbase) {
+        cbase = off;
+        cache = key.block((uint32_t)t, 0, (uint32_t)(D + off + lane));
+      }
+      const int src = off - cbase;
+      return P4{__shfl_sync(gmask, cache.w0, src, G), __shfl_sync(gmask, cache.w1, src, G),
+                __shfl_sync(gmask, cache.w2, src, G), __shfl_sync(gmask, cache.w3, src, G)};
+    } else {
+      return key.block((uint32_t)t, 0, (uint32_t)(D + off));
+    }
+  }
+};
+
+// Any target, any precision: x, nu and x' per lane.
+template <typename T, int G, int E>
+__device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, int64_t c, int budget, int lane) {
   const int d = v.tg.d;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const unsigned gmask = group_mask<G>();
-  {
-    T x[E], nu[E], yv[E], xs[E], ns[E];
+  T x[E], nu[E], yv[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * G + lane;
+    x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
+    yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
+    nu[e] = T(0);
+  }
+  T ell = v.ell[c], logy = v.logy[c], th = v.th[c], thmin = v.thmin[c], thmax = v.thmax[c];
+  int t = v.t[c], st = v.k[c], s = v.s[c];
+  const int hi = v.gen_hi[c];
+  const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  auto load_nu = [&]() {
+    const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = e * G + lane;
-      x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
-      yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
-      if constexpr (GP) {
-        yv[e] = -yv[e] * T(kLog2ef);
-        xs[e] = x[e] * yv[e];
-      }
-      nu[e] = T(0);
-      ns[e] = T(0);
+      if (k < d) nu[e] = src[k];
     }
-    T ell = v.ell[c], logy = v.logy[c], th = v.th[c], thmin = v.thmin[c], thmax = v.thmax[c];
-    int t = v.t[c], st = v.k[c], s = v.s[c];
-    const int hi = v.gen_hi[c];
-    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
-    auto load_nu = [&]() {
-      const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int k = e * G + lane;
-        if (k < d) nu[e] = src[k];
-        if constexpr (GP) ns[e] = nu[e] * yv[e];
-      }
-    };
-    if (st == ESS_SHRINK && t < v.n) load_nu();
-    int steps = 0;
-    int err = 0;
-    // Chain groups of 16 or 32 lanes draw G consecutive Philox blocks of the current sample at
-    // once (lane l holds draw D + cbase + l) and each state fetches its words by shuffle,
-    // instead of every lane computing the same block.
-    P4 cache{0u, 0u, 0u, 0u};
-    int cbase = -(1 << 30);
-    auto fetch = [&](int off) -> P4 {
-      if constexpr (G >= 16) {
-        if (off - cbase >= G || off < cbase) {
-          cbase = off;
-          cache = key.block((uint32_t)t, 0, (uint32_t)(D + off + lane));
-        }
-        const int src = off - cbase;
-        return P4{__shfl_sync(gmask, cache.w0, src, G), __shfl_sync(gmask, cache.w1, src, G),
-                  __shfl_sync(gmask, cache.w2, src, G), __shfl_sync(gmask, cache.w3, src, G)};
-      } else {
-        return key.block((uint32_t)t, 0, (uint32_t)(D + off));
-      }
-    };
-    for (int b = 0; b < budget && t < v.n; ++b) {
-      if (st == ESS_INIT) {
-        if (t >= hi) break;  // direction not generated yet
-        load_nu();
-        cbase = -(1 << 30);  // a new sample: its blocks are not cached yet
-        const P4 r = fetch(0);
-        logy = ess_threshold<T>(ell, Conv<T>::log_u(r.w0, r.w1));
-        th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
-        thmin = th - T(kTwoPi);
-        thmax = th;
-        s = 0;
-      } else {
-        if (th < T(0)) thmin = th; else thmax = th;
-        const P4 r = fetch(1 + s);
-        th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
-        ++s;
-      }
-      T sn, cs;
-      ess_sincos<T>(th, sn, cs);
-      T ellp;
-      if constexpr (GP) {
-        ellp = ess_loglik_gp32<G, E>(xs, ns, cs, sn, lane, d, gmask);
-      } else {
-        T xp[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
-        ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
-      }
-      if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
-      ++steps;
-      const bool accept = ellp > logy;
-      if (accept || s >= kMaxShrinks) {
-        if (accept) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            x[e] = fma(x[e], cs, nu[e] * sn);
-            if constexpr (GP) xs[e] = x[e] * yv[e];
-          }
-          ell = ellp;
-        } else {
-          err |= ERR_SHRINK_CAP;
-        }
-        ess_emit<T, G, E>(v, c, t, lane, x);
-        if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
-        ++t;
-        st = ESS_INIT;
-        if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
-      } else {
-        st = ESS_SHRINK;
-      }
+  };
+  if (st == ESS_SHRINK && t < v.n) load_nu();
+  int steps = 0;
+  int err = 0;
+  PhiloxLaneCache<G> pc;
+  for (int b = 0; b < budget && t < v.n; ++b) {
+    if (st == ESS_INIT) {
+      if (t >= hi) break;  // direction not generated yet
+      load_nu();
+      pc.reset();  // a new sample: its blocks are not cached yet
+      const P4 r = pc.fetch(key, t, D, 0, lane, gmask);
+      logy = ess_threshold<T>(ell, Conv<T>::log_u(r.w0, r.w1));
+      th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
+      thmin = th - T(kTwoPi);
+      thmax = th;
+      s = 0;
+    } else {
+      if (th < T(0)) thmin = th; else thmax = th;
+      const P4 r = pc.fetch(key, t, D, 1 + s, lane, gmask);
+      th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
+      ++s;
     }
+    T sn, cs;
+    ess_sincos<T>(th, sn, cs);
+    T xp[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) v.x[(size_t)c * d + k] = x[e]; }
-    if (lane == 0) {
-      v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
-      v.t[c] = t; v.k[c] = st; v.s[c] = s;
-      v.steps[c] += steps;
-      if (v.own_window) {
-        v.gen_lo[c] = hi;
-        v.gen_hi[c] = min(t + v.W, v.n);
+    for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
+    T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
+    if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
+    ++steps;
+    const bool accept = ellp > logy;
+    if (accept || s >= kMaxShrinks) {
+      if (accept) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = xp[e];
+        ell = ellp;
+      } else {
+        err |= ERR_SHRINK_CAP;
       }
-      if (err) atomicOr(v.err, err);
+      ess_emit<T, G, E>(v, c, t, lane, x);
+      if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
+      ++t;
+      st = ESS_INIT;
+      if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
+    } else {
+      st = ESS_SHRINK;
     }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) { const int k = e * G + lane; if (k < d) v.x[(size_t)c * d + k] = x[e]; }
+  if (lane == 0) {
+    v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
+    v.t[c] = t; v.k[c] = st; v.s[c] = s;
+    v.steps[c] += steps;
+    if (v.own_window) {
+      v.gen_lo[c] = hi;
+      v.gen_hi[c] = min(t + v.W, v.n);
+    }
+    if (err) atomicOr(v.err, err);
   }
 }
 
-// registers per thread allowed by the launch bounds: chain-per-warp FP32 rows of up to 8
-// coordinates per lane fit three 256-thread blocks per SM, longer rows two
-template <typename T, int G, int E>
-__host__ __device__ constexpr int ess_min_blocks() {
-  return ((sizeof(T) == 4 && E <= 8) || (sizeof(T) == 8 && E <= 2)) ? 3 : 2;
+// Single-precision GP-logit: the lanes hold only the sign-folded coordinates xs = -s x and
+// ns = -s nu (exact; bit e of smask marks the coordinates whose sign is flipped), so the
+// likelihood is one multiply-add per coordinate (ess_loglik_gp32), the accepted state is
+// xs' = xs cos + ns sin (exactly -s x'), and x is recovered exactly for the emitted samples.
+// FULL: d = E * G (no ragged lanes).
+template <int G, int E, bool FULL>
+__device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, int64_t c, int budget, int lane) {
+  const int d = FULL ? E * G : v.tg.d;
+  const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
+  const unsigned gmask = group_mask<G>();
+  float xs[E], ns[E];
+  uint32_t smask = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * G + lane;
+    float x = 0.f;
+    if (FULL || k < d) {
+      x = v.x[(size_t)c * d + k];
+      if (v.tg.vec[k] > 0.f) smask |= 1u << e;
+    }
+    xs[e] = flip_sign(x, smask, e);
+    ns[e] = 0.f;
+  }
+  float ell = v.ell[c], logy = v.logy[c], th = v.th[c], thmin = v.thmin[c], thmax = v.thmax[c];
+  int t = v.t[c], st = v.k[c], s = v.s[c];
+  const int hi = v.gen_hi[c];
+  const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  auto load_nu = [&]() {
+    const float* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = e * G + lane;
+      if (FULL || k < d) ns[e] = flip_sign(src[k], smask, e);
+    }
+  };
+  if (st == ESS_SHRINK && t < v.n) load_nu();
+  int steps = 0;
+  int err = 0;
+  PhiloxLaneCache<G> pc;
+  for (int b = 0; b < budget && t < v.n; ++b) {
+    if (st == ESS_INIT) {
+      if (t >= hi) break;  // direction not generated yet
+      load_nu();
+      pc.reset();
+      const P4 r = pc.fetch(key, t, D, 0, lane, gmask);
+      logy = ess_threshold<float>(ell, Conv<float>::log_u(r.w0, r.w1));
+      th = float(kTwoPi) * Conv<float>::u(r.w2, r.w3);
+      thmin = th - float(kTwoPi);
+      thmax = th;
+      s = 0;
+    } else {
+      if (th < 0.f) thmin = th; else thmax = th;
+      const P4 r = pc.fetch(key, t, D, 1 + s, lane, gmask);
+      th = thmin + (thmax - thmin) * Conv<float>::u(r.w0, r.w1);
+      ++s;
+    }
+    float sn, cs;
+    ess_sincos<float>(th, sn, cs);
+    float ellp = ess_loglik_gp32<G, E, FULL>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
+    if (!(ellp == ellp)) { ellp = neg_inf<float>(); err |= ERR_NONFINITE; }
+    ++steps;
+    const bool accept = ellp > logy;
+    if (accept || s >= kMaxShrinks) {
+      if (accept) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) xs[e] = fmaf(xs[e], cs, ns[e] * sn);
+        ell = ellp;
+      } else {
+        err |= ERR_SHRINK_CAP;
+      }
+      float x[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[e] = flip_sign(xs[e], smask, e);
+      ess_emit<float, G, E, FULL>(v, c, t, lane, x);
+      if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
+      ++t;
+      st = ESS_INIT;
+      if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
+    } else {
+      st = ESS_SHRINK;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * G + lane;
+    if (FULL || k < d) v.x[(size_t)c * d + k] = flip_sign(xs[e], smask, e);
+  }
+  if (lane == 0) {
+    v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
+    v.t[c] = t; v.k[c] = st; v.s[c] = s;
+    v.steps[c] += steps;
+    if (v.own_window) {
+      v.gen_lo[c] = hi;
+      v.gen_hi[c] = min(t + v.W, v.n);
+    }
+    if (err) atomicOr(v.err, err);
+  }
 }
 
-template <typename T, int G, int E, bool GP>
-__global__ void __launch_bounds__(256, (ess_min_blocks<T, G, E>()))
+// MODE 0: any target (ess_advance_chain_generic).  MODE 1: single-precision GP-logit
+// (ess_advance_chain_gp).  MODE 2: MODE 1 with d = E * G.
+template <typename T, int G, int E, int MODE>
+__device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c, int budget, int lane) {
+  if constexpr (MODE >= 1 && sizeof(T) == 4) ess_advance_chain_gp<G, E, MODE == 2>(v, c, budget, lane);
+  else ess_advance_chain_generic<T, G, E>(v, c, budget, lane);
+}
+
+// registers per thread allowed by the launch bounds: three 256-thread blocks per SM for FP32
+// rows of up to 8 coordinates per lane (16 on the GP-logit path, which keeps two arrays
+// instead of three), two otherwise
+template <typename T, int G, int E, int MODE>
+__host__ __device__ constexpr int ess_min_blocks() {
+  return ((sizeof(T) == 4 && (E <= 8 || (MODE >= 1 && E <= 16))) || (sizeof(T) == 8 && E <= 2)) ? 3 : 2;
+}
+
+template <typename T, int G, int E, int MODE>
+__global__ void __launch_bounds__(256, (ess_min_blocks<T, G, E, MODE>()))
 ess_fsm_kernel(EssView<T> v, int budget) {
   const int lane = threadIdx.x % G;
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, GP>(v, c, budget, lane);
+  for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, MODE>(v, c, budget, lane);
 }
 
 // ---- fused launches over several jobs (serving) --------------------------------------------------
@@ -441,11 +543,11 @@ __global__ void __launch_bounds__(256) ess_fsm_multi_kernel(const EssView<T>* vi
   const EssView<T> v = views[k];
   if constexpr (kEssGpFast<T, E>) {
     if (v.tg.kind == TGT_GP_LOGIT) {
-      ess_advance_chain<T, G, E, true>(v, item - off[k], budget, lane);
+      ess_advance_chain<T, G, E, 1>(v, item - off[k], budget, lane);
       return;
     }
   }
-  ess_advance_chain<T, G, E, false>(v, item - off[k], budget, lane);
+  ess_advance_chain<T, G, E, 0>(v, item - off[k], budget, lane);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -473,7 +575,6 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
   for (int e = 0; e < E; ++e) {
     const int k = e * G + lane;
     yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
-    if constexpr (GP) yv[e] = -yv[e] * T(kLog2ef);  // c = -s log2(e), as in the FSM kernel
   }
 
   for (int t = t_begin; t < t_end; ++t) {
@@ -515,10 +616,14 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
         for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
         T ellp;
         if constexpr (GP) {
+          // sign-folded coordinates, as in the FSM kernel (ess_advance_chain_gp)
           T xs[E], ns[E];
 #pragma unroll
-          for (int e = 0; e < E; ++e) { xs[e] = x[e] * yv[e]; ns[e] = nu[e] * yv[e]; }
-          ellp = ess_loglik_gp32<G, E>(xs, ns, cs, sn, lane, d, gmask);
+          for (int e = 0; e < E; ++e) {
+            xs[e] = yv[e] > T(0) ? -x[e] : x[e];
+            ns[e] = yv[e] > T(0) ? -nu[e] : nu[e];
+          }
+          ellp = ess_loglik_gp32<G, E>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
         } else {
           ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
         }
@@ -678,11 +783,12 @@ static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cuda
   const int64_t blocks = (v.m + groups_per_block - 1) / groups_per_block;
   if constexpr (kEssGpFast<T, E>) {
     if (v.tg.kind == TGT_GP_LOGIT) {
-      ess_fsm_kernel<T, G, E, true><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+      if (v.tg.d == E * G) ess_fsm_kernel<T, G, E, 2><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+      else ess_fsm_kernel<T, G, E, 1><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
       return cudaGetLastError();
     }
   }
-  ess_fsm_kernel<T, G, E, false><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  ess_fsm_kernel<T, G, E, 0><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
   return cudaGetLastError();
 }
 
@@ -717,6 +823,10 @@ static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier 
       if (d <= 8) return FN<T, 1, 8>(__VA_ARGS__);                              \
       if (d <= 16) return FN<T, 1, 16>(__VA_ARGS__);                            \
       if (d <= 32) return FN<T, 1, 32>(__VA_ARGS__);                            \
+    } else if (G == 8) {                                                        \
+      if (d <= 64) return FN<T, 8, 8>(__VA_ARGS__);                             \
+      if (d <= 128) return FN<T, 8, 16>(__VA_ARGS__);                           \
+      if (d <= 256) return FN<T, 8, 32>(__VA_ARGS__);                           \
     } else if (G == 16) {                                                       \
       if (d <= 64) return FN<T, 16, 4>(__VA_ARGS__);                            \
       if (d <= 128) return FN<T, 16, 8>(__VA_ARGS__);                           \
@@ -766,6 +876,7 @@ cudaError_t launch_ess_nu_gen_multi(const EssView<T>* views, const int64_t* off,
 // shape of the group an ESS job belongs to: jobs with equal (lanes, E) share a fused launch
 int ess_group_E(int G, int d) {
   if (G == 1) return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32;
+  if (G == 8) return d <= 64 ? 8 : d <= 128 ? 16 : 32;
   if (G == 16) return d <= 64 ? 4 : d <= 128 ? 8 : d <= 256 ? 16 : 32;
   return d <= 32 ? 1 : d <= 64 ? 2 : d <= 128 ? 4 : d <= 256 ? 8 : d <= 512 ? 16 : 32;
 }

@@ -96,9 +96,11 @@ template <> struct Conv<float> {
   static __device__ __forceinline__ float u(uint32_t hi, uint32_t lo) {
     return fmaf((float)hi, 0x1p-32f, fmaf((float)(lo >> 12), 0x1p-52f, 0x1p-53f));
   }
-  // log u without cancellation: log1p(-(1-u)) with 1-u from the complemented words when u >= 1/2
+  // log u = ln 2 log2 u with lg2.approx: absolute error ~1e-7, which moves a comparison of log u
+  // with a log acceptance ratio, or a slice threshold log f + log u, by far less than the FP32
+  // rounding of the log-densities involved
   static __device__ __forceinline__ float log_u(uint32_t hi, uint32_t lo) {
-    return (hi & 0x80000000u) ? log1pf(-u(~hi, ~lo)) : logf(u(hi, lo));
+    return lg2_approx(u(hi, lo)) * 0.693147180559945309417f;
   }
   // single-precision rounding of the one-word uniform (w + 1/2) 2^-32
   static __device__ __forceinline__ float u32(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }

@@ -78,15 +78,16 @@ def test_tensor_core_generator_matches_oracle(eng, d):
         job.close()
 
 
+@pytest.mark.parametrize("lanes", [8, 16])
 @pytest.mark.parametrize("mode", ["fsm", "sync"])
-def test_two_chains_per_warp_fp64_matches_oracle(eng, mode):
-    # 16 lanes per chain (two chains share a warp), d = 48 (ragged: 3 coordinates per lane),
+def test_several_chains_per_warp_fp64_matches_oracle(eng, mode, lanes):
+    # 8 or 16 lanes per chain (four or two chains share a warp), d = 48 (ragged lanes),
     # 100 chains (ragged last warp); FP64 gives the oracle's loop counts exactly
     w = W.gauss_conj(48)
     m, n = 100, 300
     x0 = W.x0_normal(m, 48, scale=0.3)
-    job = _run(eng, w, m, n, x0, "fp64", mode, tuning={"lanes_per_chain": 16, "steps_per_launch": 24})
-    assert job.tuning()["lanes_per_chain"] == 16
+    job = _run(eng, w, m, n, x0, "fp64", mode, tuning={"lanes_per_chain": lanes, "steps_per_launch": 24})
+    assert job.tuning()["lanes_per_chain"] == lanes
     ref = O.run("ess", "gauss_conj", w["params"], x0, n, seed=1)
     counts, _, steps = job.loop_counts()
     r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
@@ -96,7 +97,7 @@ def test_two_chains_per_warp_fp64_matches_oracle(eng, mode):
     job.close()
 
 
-@pytest.mark.parametrize("lanes", [16, 32])
+@pytest.mark.parametrize("lanes", [8, 16, 32])
 def test_fp32_gp_logit_lanes_match_oracle_and_sync(eng, lanes):
     # the single-precision base-2 GP-logit likelihood: FSM and synchronised kernels agree bit
     # for bit, and both follow the oracle to the FP32 tolerance (d = 200: ragged rows)

@@ -19,7 +19,7 @@ def test_autotune_ess_dr_nuts_and_cache(tmp_path):
     w = W.gp_logit(64)
     tg = eng.target("gp_logit", 64, w["params"])
     t1 = eng.autotune(tg, "ess", 2048, cache_path=cache)
-    assert t1["lanes_per_chain"] in (1, 16, 32) and t1["steps_per_launch"] > 0
+    assert t1["lanes_per_chain"] in (1, 8, 16, 32) and t1["steps_per_launch"] > 0
     assert t1["generator"] in (1, 2) and t1["ring_slots"] > 0
     assert os.path.exists(cache)
     assert eng.autotune(tg, "ess", 2048, cache_path=cache) == t1   # served from the cache
