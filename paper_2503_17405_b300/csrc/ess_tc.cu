@@ -33,7 +33,7 @@ constexpr int TC_N = 64;          // columns per tile
 constexpr int TC_TMEM_COLS = 256; // two accumulator buffers of (row tile 0, row tile 1) x 64 columns
 constexpr int TC_KC = 64;         // k per staged chunk
 constexpr int TC_STAGE = TC_N * TC_KC * 2;  // bytes of one FP16 part of a z chunk (8 KB)
-constexpr unsigned kWaitLimit = 1u << 20;  // polls; with the back-off below, well under 2 s
+constexpr unsigned kWaitLimit = 1u << 20;  // polls of at most ~1 us each
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -49,16 +49,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, volati
   const uint32_t a = smem_u32(bar);
   for (unsigned it = 0; it < kWaitLimit; ++it) {
     uint32_t done;
+    // the thread is suspended until the phase completes or about 1 us has passed
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(1000u)
         : "memory");
     if (done) return true;
-    if (it > 64) {
-      if (fail && (it & 255) == 0 && *fail) return false;
-      __nanosleep(32);
-    }
+    if (fail && (it & 15) == 15 && *fail) return false;
   }
   return false;
 }
@@ -160,7 +158,7 @@ struct TcBars {
   int fail;
 };
 struct TcCols {
-  long long dst[2][TC_N];  // ring row offset of each column, -1: no column
+  float* dst[2][TC_N];     // ring row of each column, null: no column
   int sample[2][TC_N];
   int chain[2][TC_N];
 };
@@ -237,7 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         }
         cols->chain[bb][n] = c;
         cols->sample[bb][n] = smp;
-        cols->dst[bb][n] = smp >= 0 ? ((long long)c * v.W + smp % v.W) * v.dstride : -1;
+        cols->dst[bb][n] = smp >= 0 ? v.nu + ((size_t)c * v.W + smp % v.W) * v.dstride : nullptr;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->cols_full[bb]);
@@ -340,25 +338,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
       if (rt == 0 || lay.K1) {
         const int row = rt * 128 + (warp & 3) * 32 + lane;
         const int jbeg = (warp >> 3) * (TC_N / 2);
+        // both 16-column loads in flight before the single wait
+        uint32_t r[TC_N / 2];
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                               (uint32_t)(bb * 2 * TC_N + rt * TC_N + jbeg);
 #pragma unroll
-        for (int j0 = jbeg; j0 < jbeg + TC_N / 2; j0 += 16) {
-          uint32_t r[16];
-          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                 (uint32_t)(bb * 2 * TC_N + rt * TC_N + j0);
+        for (int h = 0; h < 2; ++h) {
+          uint32_t* q = r + 16 * h;
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
               "[%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (row < d) {
+              : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+                "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]),
+                "=r"(q[15])
+              : "r"(taddr + 16 * h));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < d) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const long long dst = cols->dst[bb][j0 + jj];
-              if (dst >= 0) v.nu[dst + row] = __uint_as_float(r[jj]);
-            }
+          for (int jj = 0; jj < TC_N / 2; ++jj) {
+            float* dst = cols->dst[bb][jbeg + jj];
+            if (dst) dst[row] = __uint_as_float(r[jj]);
           }
         }
       }
