@@ -28,7 +28,7 @@ namespace fsmc {
 namespace {
 
 constexpr int TC_PRODUCER_WARPS = 16;
-constexpr int TC_THREADS = (TC_PRODUCER_WARPS + 1) * 32;  // + the MMA / column-list warp
+constexpr int TC_THREADS = (TC_PRODUCER_WARPS + 2) * 32;  // + the MMA warp and the column-list warp
 constexpr int TC_N = 64;          // columns per tile
 constexpr int TC_TMEM_COLS = 256; // two accumulator buffers of (row tile 0, row tile 1) x 64 columns
 constexpr int TC_KC = 64;         // k per staged chunk
@@ -168,11 +168,12 @@ __host__ __device__ inline int tc_smem_bytes(int d) {
 }
 
 // Warp-specialised pipeline over tiles of 64 refill columns:
-//  * warps 0..15 (producers) write z chunks into two shared-memory stages, and read out the
-//    accumulators of the previous tile (right after the first chunk of the next one, so the
-//    last MMAs of a tile overlap with the next tile's first chunk);
+//  * warps 0..15 (producers, two groups of eight, one per shared-memory stage) write z chunks,
+//    and read out the accumulators of the previous tile (after their first chunk of the next
+//    one, so the last MMAs of a tile overlap with the next tile's first chunks);
 //  * warp 16 issues the tcgen05 MMAs (one elected lane) into one of two tensor-memory
-//    accumulator buffers, and loads the next tile's column list while the producers work.
+//    accumulator buffers;
+//  * warp 17 loads the column lists of coming tiles into a double-buffered table.
 // Every handoff is an mbarrier; every wait is bounded and also ends when another warp has
 // recorded a failure.
 __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<float> v, const unsigned char* a_img) {
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool mma_warp = warp == TC_PRODUCER_WARPS;
+  const bool cols_warp = warp == TC_PRODUCER_WARPS + 1;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const int nchunks = lay.kpad / TC_KC;
   const long long total = v.col_base[v.m];
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
     bars->fail = 0;
     mbar_init(&bars->a, 1);
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&bars->full[i], TC_PRODUCER_WARPS);
+      mbar_init(&bars->full[i], TC_PRODUCER_WARPS / 2);  // the stage's producer group
       mbar_init(&bars->empty[i], 1);
       mbar_init(&bars->acc_full[i], 1);
       mbar_init(&bars->acc_empty[i], TC_PRODUCER_WARPS);
@@ -217,11 +219,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = bars->tmem;
 
-  if (mma_warp) {
-    // ---------------------------------------------------------------- MMA / column-list warp
-    // column list of local tile i (tile blockIdx.x + i * gridDim.x) into buffer i & 1
-    auto load_cols = [&](long long i) {
+  const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (cols_warp) {
+    // ---------------------------------------------------------------- column-list warp
+    // column list of local tile i (tile blockIdx.x + i * gridDim.x) into buffer i & 1, once the
+    // producers have read out tile i-2 (the buffer's previous user)
+    for (long long i = 0; i < my_tiles && !warp_failed(fail); ++i) {
       const int bb = (int)(i & 1);
+      if (i >= 2 && !warp_wait(&bars->cols_empty[bb], (unsigned)(((i >> 1) - 1) & 1), fail)) {
+        *fail = 1;
+        break;
+      }
       const long long tile = blockIdx.x + i * gridDim.x;
 #pragma unroll
       for (int r = 0; r < TC_N / 32; ++r) {
@@ -239,9 +247,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->cols_full[bb]);
-    };
-    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    if (my_tiles > 0) load_cols(0);
+    }
+  } else if (mma_warp) {
+    // ---------------------------------------------------------------- MMA warp
     if (lane == 0) {
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars->a)),
                    "r"(lay.a_bytes)
@@ -304,14 +312,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
           }
         }
         __syncwarp();
-        // the next tile's column list, once the producers have read out tile i-1 (its buffer)
-        if (kc == 0 && i + 1 < my_tiles) {
-          if (i >= 1 && !warp_wait(&bars->cols_empty[bb ^ 1], (unsigned)(((i - 1) >> 1) & 1), fail)) {
-            *fail = 1;
-            break;
-          }
-          load_cols(i + 1);
-        }
       }
     }
     // teardown: every issued MMA must have completed before tensor memory is freed
@@ -322,12 +322,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
     __syncwarp();
   } else {
     // ---------------------------------------------------------------- producer warps
-    // z roles: this lane's column and k half are the same for every chunk; a warp fills two
-    // core matrices (8 columns x 8 k, 128 contiguous bytes each) per pass
-    const int zn = (((2 * warp + (lane >> 4)) & 7) << 3) + ((lane >> 1) & 7);  // column 0..63
+    // Two groups of eight warps; group g fills the chunks that land in stage g, so each group
+    // has a whole chunk time of slack and every thread draws four independent Philox blocks
+    // per chunk.  z roles: this lane's column and k half are the same for every chunk; a warp
+    // fills two core matrices (8 columns x 8 k, 128 contiguous bytes each) per pass.
+    constexpr int kGroupWarps = TC_PRODUCER_WARPS / 2;
+    const int grp = warp / kGroupWarps, gw = warp % kGroupWarps;
+    const int zn = (((2 * gw + (lane >> 4)) & 7) << 3) + ((lane >> 1) & 7);  // column 0..63
     const int zkh = lane & 1;
-    constexpr int kPasses = 64 / (2 * TC_PRODUCER_WARPS);  // core-matrix pairs per warp per chunk
-    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    constexpr int kPasses = 64 / (2 * kGroupWarps);  // core-matrix pairs per warp per chunk
     // accumulators of local tile i -> the chains' direction rings
     // (warp w: row tile (w >> 2) & 1, tensor-memory lane quadrant w & 3, column half w >> 3)
     auto epilogue = [&](long long i) {
@@ -376,9 +379,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
       if (!warp_wait(&bars->cols_full[bb], (unsigned)((i >> 1) & 1), fail)) { *fail = 1; break; }
       const int z_smp = cols->sample[bb][zn];
       const Key zkey{(uint32_t)(v.chain0 + cols->chain[bb][zn]), v.seed_lo, v.seed_hi};
-      bool broke = false;
+      bool broke = false, drained = i == 0;  // drained: tile i-1 has been read out
       for (int kc = 0; kc < nchunks; ++kc, ++chunk_ctr) {
         const int s = (int)(chunk_ctr & 1);
+        if (s != grp) continue;  // the other group's stage
         if (warp_failed(fail) ||
             (chunk_ctr >= 2 && !warp_wait(&bars->empty[s], (unsigned)(((chunk_ctr >> 1) - 1) & 1), fail))) {
           *fail = 1;
@@ -393,13 +397,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         P4 blk[kPasses];
 #pragma unroll
         for (int it = 0; it < kPasses; ++it) {
-          const int kg = (2 * (warp + TC_PRODUCER_WARPS * it) + (lane >> 4)) >> 3;
+          const int kg = (2 * (gw + kGroupWarps * it) + (lane >> 4)) >> 3;
           const int q = kc * (TC_KC / 4) + kg * 2 + zkh;  // Philox draw: normals 4q .. 4q+3
           blk[it] = (z_smp >= 0 && q < D) ? zkey.block((uint32_t)z_smp, 0, (uint32_t)q) : P4{0u, 0u, 0u, 0u};
         }
 #pragma unroll
         for (int it = 0; it < kPasses; ++it) {
-          const int kg = (2 * (warp + TC_PRODUCER_WARPS * it) + (lane >> 4)) >> 3;
+          const int kg = (2 * (gw + kGroupWarps * it) + (lane >> 4)) >> 3;
           const int q = kc * (TC_KC / 4) + kg * 2 + zkh;
           float z[4] = {0.f, 0.f, 0.f, 0.f};
           if (z_smp >= 0 && q < D) {
@@ -424,9 +428,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->full[s]);
-        if (kc == 0 && i >= 1) epilogue(i - 1);
+        if (!drained) {  // after this group's first chunk of tile i
+          epilogue(i - 1);
+          drained = true;
+        }
       }
       if (broke) break;
+      if (!drained) epilogue(i - 1);  // the group had no chunk in this tile
     }
     if (i == my_tiles && my_tiles > 0 && !warp_failed(fail)) epilogue(my_tiles - 1);
   }
