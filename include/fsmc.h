@@ -175,9 +175,11 @@ fsmc_status fsmc_job_get_tuning(const fsmc_job* j, fsmc_tuning* tuning);
 size_t fsmc_job_bytes(const fsmc_job* j);
 
 /* Advances the job on `cuda_stream` (cudaStream_t as void*) and returns when done.
- * FSM mode: runs until every chain has n_samples samples, or, if max_fsm_steps > 0,
- * until every unfinished chain has advanced at least max_fsm_steps states more (a
- * resumable partial run).  SYNC mode runs to completion (max_fsm_steps ignored).
+ * FSM mode: runs until every chain has n_samples samples, or, if max_fsm_steps > 0, for
+ * ceil(max_fsm_steps / steps_per_launch) rounds (a resumable partial run); a round advances
+ * every unfinished chain by steps_per_launch states, or fewer when an ESS chain's direction
+ * ring runs dry, and by at least one.  Results do not depend on how a run is split into
+ * rounds or calls.  SYNC mode runs to completion (max_fsm_steps ignored).
  * A job can be run several times in FSM mode to resume; SYNC requires a fresh or
  * reset job.  Errors: ESTATE, ECUDA, ETIMEOUT, EDEVICE. */
 fsmc_status fsmc_job_run(fsmc_job* j, fsmc_mode mode, int64_t max_fsm_steps, void* cuda_stream);

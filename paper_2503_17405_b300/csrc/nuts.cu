@@ -589,13 +589,30 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
           const double2 b = __ldg(reinterpret_cast<const double2*>(xr) + 1);
           x4[0] = a.x; x4[1] = a.y; x4[2] = b.x; x4[3] = b.y;
         }
-        T th[C];
+        if constexpr (sizeof(T) == 4 && C % 2 == 0) {
+          // chain pairs with the packed FP32 multiply-add (each lane of the pair rounds as fmaf)
+          float2 th2[C / 2];
 #pragma unroll
-        for (int c = 0; c < C; ++c) th[c] = sm.th[k * C + c];
+          for (int c = 0; c < C / 2; ++c) th2[c] = reinterpret_cast<const float2*>(sm.th + k * C)[c];
 #pragma unroll
-        for (int r = 0; r < RPT; ++r)
+          for (int r = 0; r < RPT; ++r) {
+            const float2 xr = make_float2(x4[r], x4[r]);
 #pragma unroll
-          for (int c = 0; c < C; ++c) eta[r][c] = fma(x4[r], th[c], eta[r][c]);
+            for (int c = 0; c < C / 2; ++c) {
+              const float2 e2 = __ffma2_rn(xr, th2[c], make_float2(eta[r][2 * c], eta[r][2 * c + 1]));
+              eta[r][2 * c] = e2.x;
+              eta[r][2 * c + 1] = e2.y;
+            }
+          }
+        } else {
+          T th[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) th[c] = sm.th[k * C + c];
+#pragma unroll
+          for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int c = 0; c < C; ++c) eta[r][c] = fma(x4[r], th[c], eta[r][c]);
+        }
       }
     }
     // residuals, chain-major [C][RC]: each thread stores its 4 rows of a chain as one vector
