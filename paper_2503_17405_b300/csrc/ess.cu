@@ -332,8 +332,9 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
   int t = v.t[c], st = v.k[c], s = v.s[c];
   const int hi = v.gen_hi[c];
   const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  int slot = t % v.W;  // ring slot of sample t, advanced with t
   auto load_nu = [&]() {
-    const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+    const T* src = v.nu + ((size_t)c * v.W + slot) * v.dstride;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = e * G + lane;
@@ -381,6 +382,7 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
       ess_emit<T, G, E>(v, c, t, lane, x);
       if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
       ++t;
+      if (++slot == v.W) slot = 0;
       st = ESS_INIT;
       if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
     } else {
@@ -428,8 +430,9 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
   int t = v.t[c], st = v.k[c], s = v.s[c];
   const int hi = v.gen_hi[c];
   const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  int slot = t % v.W;  // ring slot of sample t, advanced with t
   auto load_nu = [&]() {
-    const float* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+    const float* src = v.nu + ((size_t)c * v.W + slot) * v.dstride;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = e * G + lane;
@@ -488,6 +491,7 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
       ess_emit<float, G, E, FULL>(v, c, t, lane, x);
       if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
       ++t;
+      if (++slot == v.W) slot = 0;
       st = ESS_INIT;
       if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
     } else {
