@@ -179,42 +179,42 @@ __device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E
 // sign-folded coordinates xs = -s x and ns = -s nu (exact), and the step scales cos(th) and
 // sin(th) by log2(e) once, so that t' = log2(e) (-s_i x'_i) = xs cs2 + ns sn2 costs one
 // multiply-add per coordinate and
-//   softplus(-s_i x'_i) = ln 2 [max(t', 0) + log2(1 + 2^-|t'|)].
-// Two hardware approximations per coordinate (ex2, lg2), both with absolute error ~2e-7 here.
+//   softplus(-s_i x'_i) = ln 2 log2(1 + 2^t').
+// 1 + 2^t' rounds to 2^t' for t' > 24, where log2 returns t' itself; t' is capped at 126 so that
+// 2^t' stays finite (|x'_i| > 87 would be needed to reach it).  Two hardware approximations per
+// coordinate (ex2, lg2); the absolute error per coordinate is ~2e-7.
+// Coordinates are processed in pairs with the packed FP32 instructions (FFMA2 / FMUL2 / FADD2:
+// two single-precision operations, each rounded as its scalar form, per instruction); the even
+// and odd coordinates of a lane accumulate separately.  Padded coordinates (beyond d) contribute
+// exact zeros, so ragged and full rows give the same bits.
 constexpr float kLn2f = 0.693147180559945309417f;
 constexpr float kLog2ef = 1.44269504088896340736f;
 
-// Coordinates are processed in pairs with the packed FP32 instructions (FFMA2 / FMUL2 / FADD2:
-// two single-precision operations, each rounded as its scalar form, per instruction); the
-// even and odd coordinates of a lane accumulate separately.  Padded coordinates (beyond d)
-// contribute exact zeros, so ragged and full rows give the same bits.
 template <int G, int E, bool FULL = false>
 __device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const float (&ns)[E], float cs2, float sn2,
                                                  int lane, int d, unsigned gmask) {
   if constexpr (E % 2 == 0) {
     const float2 c2 = make_float2(cs2, cs2), s2 = make_float2(sn2, sn2), one = make_float2(1.f, 1.f);
-    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int e = 0; e < E; e += 2) {
       const bool v0 = FULL || e * G + lane < d, v1 = FULL || (e + 1) * G + lane < d;
       const float2 t = __ffma2_rn(make_float2(xs[e], xs[e + 1]), c2,
                                   __fmul2_rn(make_float2(ns[e], ns[e + 1]), s2));
-      a = __fadd2_rn(a, make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f)));
-      const float2 y = __fadd2_rn(make_float2(ex2_approx(-fabsf(t.x)), ex2_approx(-fabsf(t.y))), one);
-      b = __fadd2_rn(b, make_float2(v0 ? lg2_approx(y.x) : 0.f, v1 ? lg2_approx(y.y) : 0.f));
+      const float2 y = __fadd2_rn(make_float2(ex2_approx(fminf(t.x, 126.f)), ex2_approx(fminf(t.y, 126.f))), one);
+      acc = __fadd2_rn(acc, make_float2(v0 ? lg2_approx(y.x) : 0.f, v1 ? lg2_approx(y.y) : 0.f));
     }
-    return -kLn2f * group_sum<G>((a.x + a.y) + (b.x + b.y), gmask);
+    return -kLn2f * group_sum<G>(acc.x + acc.y, gmask);
   } else {
-    float a = 0.f, b = 0.f;
+    float acc = 0.f;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if (FULL || e * G + lane < d) {
         const float t = fmaf(xs[e], cs2, ns[e] * sn2);
-        a += fmaxf(t, 0.f);
-        b += lg2_approx(1.f + ex2_approx(-fabsf(t)));
+        acc += lg2_approx(1.f + ex2_approx(fminf(t, 126.f)));
       }
     }
-    return -kLn2f * group_sum<G>(a + b, gmask);
+    return -kLn2f * group_sum<G>(acc, gmask);
   }
 }
 

@@ -567,8 +567,11 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
   const int kk = t % d, sub = t / d;
   const bool c_role = sub < nsub;
   T gacc[C], lpacc[C];
+  // FP32: each chain's gradient partial as an (even rows, odd rows) pair for the packed
+  // multiply-add; the two halves are added at the end
+  float2 gacc2[C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) { gacc[c] = T(0); lpacc[c] = T(0); }
+  for (int c = 0; c < C; ++c) { gacc[c] = T(0); lpacc[c] = T(0); gacc2[c] = make_float2(0.f, 0.f); }
   for (int i0 = 0; i0 < n; i0 += RC) {
     // eta for rows ib .. ib+3 and all C chains
     const int ib = i0 + RPT * t;
@@ -655,17 +658,31 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
           const double2 b = __ldg(reinterpret_cast<const double2*>(xk + RPT * gi) + 1);
           x4[0] = a.x; x4[1] = a.y; x4[2] = b.x; x4[3] = b.y;
         }
+        if constexpr (sizeof(T) == 4) {
+          const float2 x01 = make_float2(x4[0], x4[1]), x23 = make_float2(x4[2], x4[3]);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const T* rc = sm.R + c * RC + RPT * gi;
+          for (int c = 0; c < C; ++c) {
+            const float4 r4 = *reinterpret_cast<const float4*>(sm.R + c * RC + RPT * gi);
+            gacc2[c] = __ffma2_rn(x01, make_float2(r4.x, r4.y), gacc2[c]);
+            gacc2[c] = __ffma2_rn(x23, make_float2(r4.z, r4.w), gacc2[c]);
+          }
+        } else {
 #pragma unroll
-          for (int r = 0; r < RPT; ++r) gacc[c] = fma(x4[r], rc[r], gacc[c]);
+          for (int c = 0; c < C; ++c) {
+            const T* rc = sm.R + c * RC + RPT * gi;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) gacc[c] = fma(x4[r], rc[r], gacc[c]);
+          }
         }
       }
     }
     __syncthreads();
   }
   // reduce the gradient partials over row ranges, the log-density partials over warps
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) gacc[c] = gacc2[c].x + gacc2[c].y;
+  }
 #pragma unroll
   for (int c = 0; c < C; ++c) sm.part[t * C + c] = c_role ? gacc[c] : T(0);
 #pragma unroll

@@ -107,10 +107,12 @@ def test_fp32_gp_logit_lanes_match_oracle_and_sync(eng, lanes):
     tu = {"lanes_per_chain": lanes, "generator": 2}
     a = _run(eng, w, m, n, x0, "fp32", "fsm", tuning=tu)
     b = _run(eng, w, m, n, x0, "fp32", "sync", tuning=tu)
-    ca, _, _ = a.loop_counts()
+    ca, _, steps = a.loop_counts()
     cb, _, _ = b.loop_counts()
     assert np.array_equal(ca, cb)
     assert np.array_equal(a.samples(), b.samples())
+    # states counted one likelihood evaluation each, whatever the step evaluates ahead
+    assert np.array_equal(steps, (ca + 1).sum(1))
     ref = O.run("ess", "gp_logit", w["params"], x0, n, seed=1)
     r = compare(a.samples(), ca, ref["samples"], ref["counts"], "fp32")
     print("lanes", lanes, "flipped", r["flipped"], "max err", r["max_err"])
