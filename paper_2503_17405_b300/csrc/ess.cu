@@ -528,6 +528,7 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
 // instead of three), two otherwise
 template <typename T, int G, int E, int MODE>
 __host__ __device__ constexpr int ess_min_blocks() {
+  if (sizeof(T) == 4 && MODE >= 1 && E <= 8) return 4;
   return ((sizeof(T) == 4 && (E <= 8 || (MODE >= 1 && E <= 16))) || (sizeof(T) == 8 && E <= 2)) ? 3 : 2;
 }
 
