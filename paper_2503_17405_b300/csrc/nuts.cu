@@ -581,6 +581,8 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
 #pragma unroll
       for (int c = 0; c < C; ++c) eta[r][c] = T(0);
     if (ib < np) {
+      // unrolled so that several rows of X^T are in flight from L2 at once
+#pragma unroll 2
       for (int k = 0; k < d; ++k) {
         const T* xr = tg.XT + (size_t)k * np + ib;
         T x4[RPT];
@@ -648,6 +650,7 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
       const int gseg = (groups + nsub - 1) / nsub;
       const int g_beg = sub * gseg, g_end = min(groups, g_beg + gseg);
       const T* xk = tg.XT + (size_t)kk * np + i0;
+#pragma unroll 2
       for (int gi = g_beg; gi < g_end; ++gi) {
         T x4[RPT];
         if constexpr (sizeof(T) == 4) {
