@@ -533,7 +533,7 @@ struct GradSmem {
   T* G;      // [128][C] gradients
   T* lp;     // [C] log densities
   T* R;      // [4 * 32 C][C] residuals of one row chunk
-  T* part;   // [32 C][C] per-thread partial gradients
+  T* part;   // [C][32 C] per-thread partial gradients (chain-major)
   T* lpart;  // [C][C] per-warp partial log densities
 };
 
@@ -686,8 +686,9 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
 #pragma unroll
     for (int c = 0; c < C; ++c) gacc[c] = gacc2[c].x + gacc2[c].y;
   }
+  // chain-major [C][NT]: consecutive threads write consecutive words (no bank conflicts)
 #pragma unroll
-  for (int c = 0; c < C; ++c) sm.part[t * C + c] = c_role ? gacc[c] : T(0);
+  for (int c = 0; c < C; ++c) sm.part[c * NT + t] = c_role ? gacc[c] : T(0);
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     const T s = group_sum<32>(lpacc[c]);
@@ -695,9 +696,9 @@ __device__ void block_logreg_grad(const TargetView<T>& tg, const GradSmem<T, C>&
   }
   __syncthreads();
   for (int o = t; o < d * C; o += NT) {
-    const int k = o / C, c = o % C;
+    const int k = o % d, c = o / d;
     T acc = T(0);
-    for (int sb = 0; sb < nsub; ++sb) acc += sm.part[(sb * d + k) * C + c];
+    for (int sb = 0; sb < nsub; ++sb) acc += sm.part[c * NT + sb * d + k];
     sm.G[k * C + c] = acc - sm.th[k * C + c];
   }
   if (t < C) {
