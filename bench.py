@@ -384,6 +384,68 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---- step-form ablations ------------------------------------------------------------------------------
+def run_ablations(args):
+    """The paper's step-form ablations on the CUDA kernels (tuning.step_form = 2 against the
+    default 1): ESS with the log-density evaluated inside INIT and SHRINK instead of once per step
+    (not amortised), with one chain per thread (warps whose chains are in both states pay twice)
+    and one chain per warp; DR as the 4-state FSM with one state per step (not condensed).  The
+    two forms give identical samples (tests/test_gpu_ablation.py); this reports their device time."""
+    import torch
+    from paper_2503_17405_b300 import fsmc
+
+    torch.cuda.set_device(0)
+    eng = fsmc.Engine(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sp = stream.cuda_stream
+    scale = args.scale
+
+    def timed(tg, algo, m, n, x0, tuning, dr=None, reps=3):
+        job = eng.job(tg, algo, m, n, x0=x0, seed=1, prec="fp32", store=True, dr=dr, tuning=tuning)
+        ms = []
+        for r in range(reps + 1):
+            job.reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            job.run("fsm", stream=sp)
+            b.record(stream)
+            b.synchronize()
+            if r:
+                ms.append(a.elapsed_time(b))
+        st = job.stats()
+        job.close()
+        return {"ms_per_job": sum(ms) / len(ms), "fsm_states": st["fsm_steps"],
+                "samples_per_s": m * n / (sum(ms) / len(ms) / 1e3), "mean_N": st["mean_N"]}
+
+    out = {"metric": "step-form ablations: device ms per job, form 2 (paper's ablation) / form 1 (default)",
+           "unit": "ms", "data": "synthetic", "rows": []}
+    # ESS on the conjugate Gaussian: a cheap log-density (d = 16) and a dearer one (d = 256)
+    for d, lanes_list, n in ((16, (1, 32), 500), (256, (32,), 200)):
+        w = W.gauss_conj(d)
+        tg = eng.target("gauss_conj", d, w["params"])
+        m = int(16384 * scale)
+        x0 = W.x0_normal(m, d, scale=0.5)
+        for lanes in lanes_list:
+            a = timed(tg, "ess", m, n, x0, {"lanes_per_chain": lanes, "step_form": 1})
+            b = timed(tg, "ess", m, n, x0, {"lanes_per_chain": lanes, "step_form": 2})
+            out["rows"].append({"ablation": "ESS log-density not amortised", "workload":
+                                f"ess_gauss_conj_d{d}_m{m}_n{n}_fp32", "lanes_per_chain": lanes,
+                                "default": a, "ablation_form": b, "ratio": b["ms_per_job"] / a["ms_per_job"]})
+    w = W.funnel(10)
+    tg = eng.target("funnel", 10, w["params"])
+    m, n = int(65536 * scale), 1000
+    x0 = W.x0_funnel_exact(m)
+    dr = {"n_stages": 3, "scale0": 1.0, "factor": 0.5}
+    a = timed(tg, "dr", m, n, x0, {"step_form": 1}, dr=dr)
+    b = timed(tg, "dr", m, n, x0, {"step_form": 2}, dr=dr)
+    out["rows"].append({"ablation": "DR 4-state FSM (not condensed)", "workload": f"dr3_funnel_d10_m{m}_n{n}_fp32",
+                        "default": a, "ablation_form": b, "ratio": b["ms_per_job"] / a["ms_per_job"],
+                        "states_per_sample": [a["fsm_states"] / (m * n), b["fsm_states"] / (m * n)]})
+    eng.close()
+    return out
+
+
 # ---- serving stream (C5) ------------------------------------------------------------------------------
 def run_serving(args):
     """Poisson-arriving mixed jobs through fsmc_submit; FSM co-scheduled vs the synchronised
@@ -476,6 +538,11 @@ def main():
     args = ap.parse_args()
     if args.config == "serving":
         print(json.dumps(run_serving(args)))
+        return
+    if args.config == "ablations":
+        from paper_2503_17405_b300 import build
+        build.build()
+        print(json.dumps(run_ablations(args)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.impl == "reference" else 1))

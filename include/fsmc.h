@@ -107,6 +107,14 @@ typedef struct fsmc_tuning {
                             (tcgen05; FP32 jobs with d <= 256)                            */
   int pipelined;         /* ESS whole runs: 0 auto (on), 1 refill directions for the next
                             round on a second stream while the FSM kernel runs, 2 off      */
+  int step_form;         /* FSM step (ablation of Sec. 3 / App. B): 0 auto = 1; 1 bundled
+                            and amortised (ESS), condensed single state (DR); 2 the paper's
+                            ablations: ESS as the bundled step without amortisation, which
+                            calls the log-density in both INIT and SHRINK every step (one of
+                            the two calls masked, as vmap runs it); DR as the 4-state FSM
+                            INIT, PROPOSE, ..., DONE with one state per step (not condensed).
+                            Samples and loop counts are the same in both forms; NUTS and
+                            submitted (serving) jobs use form 1 only                       */
 } fsmc_tuning;
 
 /* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */

@@ -198,8 +198,16 @@ __device__ __forceinline__ void dr_store(const DrView<T>& v, int64_t c, const T 
   }
 }
 
-// FSM kernel: chain-per-thread, every chain advances `budget` PROPOSE steps.
-template <typename T, int E>
+// FSM kernel: chain-per-thread, every chain advances `budget` FSM steps.
+// CONDENSED (Sec. 7.1): the single PROPOSE state, with INIT and DONE run inline -- a sample takes
+// as many steps as stages tried; k is the next stage.  !CONDENSED (the paper's ablation): the
+// 4-state FSM of Fig. 2 with one state per step -- INIT (k = 0), PROPOSE stage j (k = 1 + j),
+// DONE after j + 1 stages (k = kDrDone + j + 1) -- so a sample takes two more steps, and a warp
+// whose chains are in different states runs each state's code.  Both forms compute the same
+// samples.
+constexpr int kDrDone = 16;
+
+template <typename T, int E, bool CONDENSED>
 __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < v.m; c += stride) {
@@ -211,17 +219,34 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
     int err = 0, steps = 0;
     for (int b = 0; b < budget && t < v.n; ++b) {
       ++steps;
-      if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, err)) {
-        dr_emit<T, E>(v, c, t, x);
-        v.counts[(size_t)c * v.n + t] = k + 1;
-        ++t;
-        k = 0;
-        if (t == v.n) atomicAdd(v.chains_done, 1);
+      if constexpr (CONDENSED) {
+        if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, err)) {
+          dr_emit<T, E>(v, c, t, x);
+          v.counts[(size_t)c * v.n + t] = k + 1;
+          ++t;
+          k = 0;
+          if (t == v.n) atomicAdd(v.chains_done, 1);
+        } else {
+          ++k;
+        }
       } else {
-        ++k;
+        if (k == 0) {  // INIT: the sample's stages start at stage 0
+          k = 1;
+        } else if (k < kDrDone) {  // PROPOSE stage k - 1
+          const int j = k - 1;
+          k = dr_step<T, E>(v, key, t, j, x, lp, y1, lp1, y2, lp2, err) ? kDrDone + j + 1 : k + 1;
+        } else {  // DONE: emit the sample
+          dr_emit<T, E>(v, c, t, x);
+          v.counts[(size_t)c * v.n + t] = k - kDrDone;
+          ++t;
+          k = 0;
+          if (t == v.n) atomicAdd(v.chains_done, 1);
+        }
       }
     }
-    dr_store<T, E>(v, c, x, y1, y2, k);
+    // y1 / y2 are live while stages 2 / 3 are pending
+    const int pending = CONDENSED ? k : (k >= 1 && k < kDrDone ? k - 1 : 0);
+    dr_store<T, E>(v, c, x, y1, y2, pending);
     v.lp[c] = lp; v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
     v.t[c] = t; v.k[c] = k;
     v.steps[c] += steps;
@@ -302,7 +327,8 @@ __global__ void dr_init_kernel(DrView<T> v) {
 template <typename T, int E>
 static cudaError_t fsm_launch(const DrView<T>& v, int budget, int threads, cudaStream_t st) {
   const int64_t blocks = (v.m + threads - 1) / threads;
-  dr_fsm_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  if (v.step_form == 2) dr_fsm_kernel<T, E, false><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  else dr_fsm_kernel<T, E, true><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
   return cudaGetLastError();
 }
 

@@ -265,6 +265,7 @@ struct Layout {
 // Decides the launch shape when the caller left it open.
 static void default_tuning(fsmc_job* j) {
   fsmc_tuning& tu = j->tun;
+  if (!tu.step_form) tu.step_form = 1;
   if (j->algo == FSMC_ESS) {
     if (!tu.lanes_per_chain) {
       // chain-per-warp when one chain's likelihood is wide (d >= 64) or when there are too
@@ -358,6 +359,7 @@ static void fill_chains(const fsmc_job* j, ChainsView<T>& v) {
   v.steps = (long long*)(b + j->o_steps);
   v.err = (int*)(b + j->o_err);
   v.chains_done = (int*)(b + j->o_done);
+  v.step_form = j->tun.step_form ? j->tun.step_form : 1;
 }
 
 template <typename T>
@@ -534,6 +536,8 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
     return fsmc_fail(FSMC_EINVAL, "negative steps / ring slots");
   if (t.generator < 0 || t.generator > 2) return fsmc_fail(FSMC_EINVAL, "generator must be 0, 1 or 2");
   if (t.pipelined < 0 || t.pipelined > 2) return fsmc_fail(FSMC_EINVAL, "pipelined must be 0, 1 or 2");
+  if (t.step_form < 0 || t.step_form > 2) return fsmc_fail(FSMC_EINVAL, "step_form must be 0, 1 or 2");
+  if (t.step_form == 2 && j->algo == FSMC_NUTS) return fsmc_fail(FSMC_EINVAL, "NUTS has step form 1 only");
   if (t.generator == 2 && (j->algo != FSMC_ESS || j->prec != FSMC_FP32 || j->d > 256))
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   j->tun = t;

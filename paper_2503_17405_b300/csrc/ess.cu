@@ -314,8 +314,19 @@ struct PhiloxLaneCache {
   }
 };
 
-// Any target, any precision: x, nu and x' per lane.
-template <typename T, int G, int E>
+// Keeps a value the program does not otherwise use (the masked branch's log-density).
+template <typename T>
+__device__ __forceinline__ void ess_keep(T v) {
+  if constexpr (sizeof(T) == 4) asm volatile("" ::"f"(v));
+  else asm volatile("" ::"d"(v));
+}
+
+// Any target, any precision: x, nu and x' per lane.  AMORT (the step form of Alg. 5 and
+// App. B.2): one log-density evaluation per step, after the state code.  !AMORT (the paper's
+// ablation): the bundled step without amortisation, as vmap runs it -- INIT and SHRINK each
+// call the log-density, so every step makes both calls, one of them for the state the chain
+// is not in (masked: its value is computed and dropped).  Both forms compute the same samples.
+template <typename T, int G, int E, bool AMORT = true>
 __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, int64_t c, int budget, int lane) {
   const int d = v.tg.d;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
@@ -346,6 +357,14 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
   int err = 0;
   PhiloxLaneCache<G> pc;
   for (int b = 0; b < budget && t < v.n; ++b) {
+    T sn, cs, ellp;
+    T xp[E];
+    auto evaluate = [&]() {  // x' on the ellipse at th, and log f(x')
+      ess_sincos<T>(th, sn, cs);
+#pragma unroll
+      for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
+      ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
+    };
     if (st == ESS_INIT) {
       if (t >= hi) break;  // direction not generated yet
       load_nu();
@@ -362,12 +381,15 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
       th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
       ++s;
     }
-    T sn, cs;
-    ess_sincos<T>(th, sn, cs);
-    T xp[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
-    T ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
+    if constexpr (!AMORT) {
+      // the other state's call, at the bracket's other end (masked)
+      const T th_real = th;
+      th = th < T(0) ? thmax : thmin;
+      evaluate();
+      ess_keep<T>(ellp);
+      th = th_real;
+    }
+    evaluate();
     if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
     ++steps;
     const bool accept = ellp > logy;
@@ -516,10 +538,12 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
 }
 
 // MODE 0: any target (ess_advance_chain_generic).  MODE 1: single-precision GP-logit
-// (ess_advance_chain_gp).  MODE 2: MODE 1 with d = E * G.
+// (ess_advance_chain_gp).  MODE 2: MODE 1 with d = E * G.  MODE 3: any target, log-density
+// not amortised (the ablation step form).
 template <typename T, int G, int E, int MODE>
 __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c, int budget, int lane) {
-  if constexpr (MODE >= 1 && sizeof(T) == 4) ess_advance_chain_gp<G, E, MODE == 2>(v, c, budget, lane);
+  if constexpr (MODE == 3) ess_advance_chain_generic<T, G, E, false>(v, c, budget, lane);
+  else if constexpr (MODE >= 1 && sizeof(T) == 4) ess_advance_chain_gp<G, E, MODE == 2>(v, c, budget, lane);
   else ess_advance_chain_generic<T, G, E>(v, c, budget, lane);
 }
 
@@ -528,8 +552,9 @@ __device__ __forceinline__ void ess_advance_chain(const EssView<T>& v, int64_t c
 // instead of three), two otherwise
 template <typename T, int G, int E, int MODE>
 __host__ __device__ constexpr int ess_min_blocks() {
-  if (sizeof(T) == 4 && MODE >= 1 && E <= 8) return 4;
-  return ((sizeof(T) == 4 && (E <= 8 || (MODE >= 1 && E <= 16))) || (sizeof(T) == 8 && E <= 2)) ? 3 : 2;
+  if (sizeof(T) == 4 && (MODE == 1 || MODE == 2) && E <= 8) return 4;
+  return ((sizeof(T) == 4 && (E <= 8 || ((MODE == 1 || MODE == 2) && E <= 16))) || (sizeof(T) == 8 && E <= 2)) ? 3
+                                                                                                           : 2;
 }
 
 template <typename T, int G, int E, int MODE>
@@ -816,6 +841,10 @@ template <typename T, int G, int E>
 static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cudaStream_t st) {
   const int64_t groups_per_block = threads / G;
   const int64_t blocks = (v.m + groups_per_block - 1) / groups_per_block;
+  if (v.step_form == 2) {
+    ess_fsm_kernel<T, G, E, 3><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+    return cudaGetLastError();
+  }
   if constexpr (kEssGpFast<T, E>) {
     if (v.tg.kind == TGT_GP_LOGIT) {
       if (v.tg.d == E * G) ess_fsm_kernel<T, G, E, 2><<<(unsigned)blocks, threads, 0, st>>>(v, budget);

@@ -25,6 +25,7 @@ struct ChainsView {
   long long* steps;      // [m] FSM states executed
   int* err;              // error word
   int* chains_done;      // chains that reached n
+  int step_form = 1;     // 1: bundled + amortised / condensed step; 2: the paper's ablation forms
 };
 
 template <typename T>

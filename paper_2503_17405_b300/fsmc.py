@@ -38,7 +38,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("lanes_per_chain", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("ring_slots", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("profile_kernels", ctypes.c_int), ("generator", ctypes.c_int),
-                ("pipelined", ctypes.c_int)]
+                ("pipelined", ctypes.c_int), ("step_form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -219,10 +219,7 @@ class Job:
                                       ctypes.byref(self._h)))
         engine._objs.append(self)
         if tuning:
-            t = Tuning(tuning.get("lanes_per_chain", 0), tuning.get("steps_per_launch", 0),
-                       tuning.get("ring_slots", 0), tuning.get("threads_per_block", 0),
-                       tuning.get("profile_kernels", 0), tuning.get("generator", 0),
-                       tuning.get("pipelined", 0))
+            t = Tuning(*(int(tuning.get(name, 0)) for name, _ in Tuning._fields_))
             _check(load().fsmc_job_set_tuning(self._h, ctypes.byref(t)))
 
     @property
