@@ -389,7 +389,8 @@ def run_ablations(args):
     """The paper's step-form ablations on the CUDA kernels (tuning.step_form = 2 against the
     default 1): ESS with the log-density evaluated inside INIT and SHRINK instead of once per step
     (not amortised), with one chain per thread (warps whose chains are in both states pay twice)
-    and one chain per warp; DR as the 4-state FSM with one state per step (not condensed).  The
+    and one chain per warp; DR with its PROPOSE body unrolled into four states run one per step
+    (not condensed).  The
     two forms give identical samples (tests/test_gpu_ablation.py); this reports their device time."""
     import torch
     from paper_2503_17405_b300 import fsmc
@@ -439,7 +440,8 @@ def run_ablations(args):
     dr = {"n_stages": 3, "scale0": 1.0, "factor": 0.5}
     a = timed(tg, "dr", m, n, x0, {"step_form": 1}, dr=dr)
     b = timed(tg, "dr", m, n, x0, {"step_form": 2}, dr=dr)
-    out["rows"].append({"ablation": "DR 4-state FSM (not condensed)", "workload": f"dr3_funnel_d10_m{m}_n{n}_fp32",
+    out["rows"].append({"ablation": "DR PROPOSE body as 4 states (not condensed)",
+                        "workload": f"dr3_funnel_d10_m{m}_n{n}_fp32",
                         "default": a, "ablation_form": b, "ratio": b["ms_per_job"] / a["ms_per_job"],
                         "states_per_sample": [a["fsm_states"] / (m * n), b["fsm_states"] / (m * n)]})
     eng.close()

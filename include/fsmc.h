@@ -111,8 +111,9 @@ typedef struct fsmc_tuning {
                             and amortised (ESS), condensed single state (DR); 2 the paper's
                             ablations: ESS as the bundled step without amortisation, which
                             calls the log-density in both INIT and SHRINK every step (one of
-                            the two calls masked, as vmap runs it); DR as the 4-state FSM
-                            INIT, PROPOSE, ..., DONE with one state per step (not condensed).
+                            the two calls masked, as vmap runs it); DR with the PROPOSE body
+                            unrolled into four states (draw, evaluate, ratio, decide) run one
+                            per step (not condensed).
                             Samples and loop counts are the same in both forms; NUTS and
                             submitted (serving) jobs use form 1 only                       */
 } fsmc_tuning;

@@ -118,15 +118,14 @@ __device__ __forceinline__ void dr_emit(const DrView<T>& v, int64_t c, int t, co
   }
 }
 
-// One PROPOSE step of stage k for one chain.  Returns true when the sample is finished
-// (accepted, or rejected at the last stage); then x/lp hold the sample.
+// The PROPOSE body of stage k in four parts: draw y_k ~ N(x, sigma_k^2 I); evaluate log pi(y_k);
+// the stage's acceptance ratio; the decision.  dr_step runs all four in one FSM step.
 template <typename T, int E>
-__device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E],
-                                        T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, int& err) {
+__device__ __forceinline__ void dr_draw(const DrView<T>& v, const Key& key, int t, int k, const T (&x)[E],
+                                        T (&y)[E]) {
   const int d = v.tg.d;
   const int D = (d + 3) / 4;  // Philox blocks per stage (four normals each)
   const uint32_t base = (uint32_t)(k * (D + 1));
-  T y[E];
   const T sg = v.sig[k];
 #pragma unroll
   for (int q = 0; q < (E + 3) / 4; ++q) {
@@ -136,22 +135,34 @@ __device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int 
     for (int i = 0; i < 4; ++i)
       if (4 * q + i < E) y[4 * q + i] = q < D ? fma(sg, z[i], x[4 * q + i]) : T(0);
   }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ T dr_eval(const DrView<T>& v, const T (&y)[E], int& err) {
   T lpy = full_logp<T, E>(v.tg, y);
   if (!(lpy == lpy)) { lpy = neg_inf<T>(); err |= ERR_NONFINITE; }
-  T la;
-  if (k == 0) {
-    la = la1(lp, lpy);
-  } else {
-    const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]);
-    if (k == 1) {
-      la = la2(lp, lp1, lpy, i1 * sqdist(x, y1, d), i1 * sqdist(y, y1, d));
-    } else {
-      const T i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
-      la = la3(lp, lp1, lp2, lpy, i1 * sqdist(x, y1, d), i2 * sqdist(x, y2, d),
-               i1 * sqdist(y, y2, d), i2 * sqdist(y, y1, d), i1 * sqdist(y1, y2, d));
-    }
-  }
-  const P4 r = key.block((uint32_t)t, 0, base + (uint32_t)D);
+  return lpy;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ T dr_ratio(const DrView<T>& v, int k, const T (&x)[E], T lp, const T (&y1)[E], T lp1,
+                                      const T (&y2)[E], T lp2, const T (&y)[E], T lpy) {
+  const int d = v.tg.d;
+  if (k == 0) return la1(lp, lpy);
+  const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]);
+  if (k == 1) return la2(lp, lp1, lpy, i1 * sqdist(x, y1, d), i1 * sqdist(y, y1, d));
+  const T i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
+  return la3(lp, lp1, lp2, lpy, i1 * sqdist(x, y1, d), i2 * sqdist(x, y2, d), i1 * sqdist(y, y2, d),
+             i2 * sqdist(y, y1, d), i1 * sqdist(y1, y2, d));
+}
+
+// Returns true when the sample is finished (accepted, or rejected at the last stage); then x/lp
+// hold the sample.  Otherwise y becomes y1 (stage 0) or y2 (stage 1).
+template <typename T, int E>
+__device__ __forceinline__ bool dr_decide(const DrView<T>& v, const Key& key, int t, int k, T la, T (&x)[E],
+                                          T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, const T (&y)[E], T lpy) {
+  const int D = (v.tg.d + 3) / 4;
+  const P4 r = key.block((uint32_t)t, 0, (uint32_t)(k * (D + 1) + D));
   if (Conv<T>::log_u(r.w0, r.w1) < la) {
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = y[e];
@@ -169,6 +180,17 @@ __device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int 
     lp2 = lpy;
   }
   return false;
+}
+
+// One PROPOSE step of stage k for one chain (all four parts).
+template <typename T, int E>
+__device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E],
+                                        T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, int& err) {
+  T y[E];
+  dr_draw<T, E>(v, key, t, k, x, y);
+  const T lpy = dr_eval<T, E>(v, y, err);
+  const T la = dr_ratio<T, E>(v, k, x, lp, y1, lp1, y2, lp2, y, lpy);
+  return dr_decide<T, E>(v, key, t, k, la, x, lp, y1, lp1, y2, lp2, y, lpy);
 }
 
 template <typename T, int E>
@@ -200,12 +222,11 @@ __device__ __forceinline__ void dr_store(const DrView<T>& v, int64_t c, const T 
 
 // FSM kernel: chain-per-thread, every chain advances `budget` FSM steps.
 // CONDENSED (Sec. 7.1): the single PROPOSE state, with INIT and DONE run inline -- a sample takes
-// as many steps as stages tried; k is the next stage.  !CONDENSED (the paper's ablation): the
-// 4-state FSM of Fig. 2 with one state per step -- INIT (k = 0), PROPOSE stage j (k = 1 + j),
-// DONE after j + 1 stages (k = kDrDone + j + 1) -- so a sample takes two more steps, and a warp
-// whose chains are in different states runs each state's code.  Both forms compute the same
-// samples.
-constexpr int kDrDone = 16;
+// as many steps as stages tried; k is the next stage.  !CONDENSED (the paper's ablation, Sec. 7.1):
+// the PROPOSE body unrolled into four states run one per step -- draw, evaluate, ratio, decide
+// (k = 4 j + u for stage j, part u) -- with the proposal, its log density and the ratio kept in
+// the chain state between steps; a warp whose chains are in different parts runs each part's code.
+// Both forms compute the same samples.
 
 template <typename T, int E, bool CONDENSED>
 __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
@@ -217,6 +238,15 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
     int t = v.t[c], k = v.k[c];
     const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
     int err = 0, steps = 0;
+    // !CONDENSED: the current stage's proposal, log density and ratio between parts
+    T yc[E], lpc = T(0), lac = T(0);
+    const size_t md = (size_t)v.m * v.tg.d;
+    if constexpr (!CONDENSED) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) yc[e] = e < v.tg.d ? v.y[2 * md + (size_t)c * v.tg.d + e] : T(0);
+      lpc = v.lpy[2 * v.m + c];
+      lac = v.lpy[3 * v.m + c];
+    }
     for (int b = 0; b < budget && t < v.n; ++b) {
       ++steps;
       if constexpr (CONDENSED) {
@@ -230,22 +260,36 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
           ++k;
         }
       } else {
-        if (k == 0) {  // INIT: the sample's stages start at stage 0
-          k = 1;
-        } else if (k < kDrDone) {  // PROPOSE stage k - 1
-          const int j = k - 1;
-          k = dr_step<T, E>(v, key, t, j, x, lp, y1, lp1, y2, lp2, err) ? kDrDone + j + 1 : k + 1;
-        } else {  // DONE: emit the sample
+        const int j = k >> 2, u = k & 3;
+        if (u == 0) {
+          dr_draw<T, E>(v, key, t, j, x, yc);
+          ++k;
+        } else if (u == 1) {
+          lpc = dr_eval<T, E>(v, yc, err);
+          ++k;
+        } else if (u == 2) {
+          lac = dr_ratio<T, E>(v, j, x, lp, y1, lp1, y2, lp2, yc, lpc);
+          ++k;
+        } else if (dr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, y2, lp2, yc, lpc)) {
           dr_emit<T, E>(v, c, t, x);
-          v.counts[(size_t)c * v.n + t] = k - kDrDone;
+          v.counts[(size_t)c * v.n + t] = j + 1;
           ++t;
           k = 0;
           if (t == v.n) atomicAdd(v.chains_done, 1);
+        } else {
+          k = 4 * (j + 1);
         }
       }
     }
+    if constexpr (!CONDENSED) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e < v.tg.d) v.y[2 * md + (size_t)c * v.tg.d + e] = yc[e];
+      v.lpy[2 * v.m + c] = lpc;
+      v.lpy[3 * v.m + c] = lac;
+    }
     // y1 / y2 are live while stages 2 / 3 are pending
-    const int pending = CONDENSED ? k : (k >= 1 && k < kDrDone ? k - 1 : 0);
+    const int pending = CONDENSED ? k : (k >> 2);
     dr_store<T, E>(v, c, x, y1, y2, pending);
     v.lp[c] = lp; v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
     v.t[c] = t; v.k[c] = k;

@@ -319,8 +319,8 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
     j->o_colmap = L.take(m * (size_t)j->W * 8);
   } else if (j->algo == FSMC_DR) {
     j->o_ell = L.take(m * es);        // log pi(x)
-    j->o_y = L.take(2 * m * d * es);  // y1, y2
-    j->o_lpy = L.take(2 * m * es);
+    j->o_y = L.take(3 * m * d * es);  // y1, y2 and (4-state ablation form) the current proposal
+    j->o_lpy = L.take(4 * m * es);    // log pi(y1), log pi(y2), current proposal's and its ratio
     j->o_k = L.take(m * 4);
   } else {
     nuts_layout(j, L.off);
@@ -436,8 +436,8 @@ static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
     CK(launch_ess_init<T>(ess_view<T>(j), st));
   } else if (j->algo == FSMC_DR) {
     CK(cudaMemsetAsync(b + j->o_k, 0, m * 4, st));
-    CK(cudaMemsetAsync(b + j->o_y, 0, 2 * m * d * sizeof(T), st));
-    CK(cudaMemsetAsync(b + j->o_lpy, 0, 2 * m * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_y, 0, 3 * m * d * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_lpy, 0, 4 * m * sizeof(T), st));
     CK(launch_dr_init<T>(dr_view<T>(j), st));
   } else {
     fsmc_status s = nuts_init_state(j, st);

@@ -55,8 +55,9 @@ struct DrView : ChainsView<T> {
   int n_stages;
   T sig[3];              // stage scales
   T* lp;                 // [m] log pi(x)
-  T* y;                  // [2][m][d] rejected proposals y1, y2 of the current sample
-  T* lpy;                // [2][m] their log pi
+  T* y;                  // [3][m][d] rejected proposals y1, y2 of the current sample; the
+                         // current proposal (4-state ablation form)
+  T* lpy;                // [4][m] log pi(y1), log pi(y2); the current proposal's log pi and ratio
   int* k;                // [m] next stage to try
 };
 

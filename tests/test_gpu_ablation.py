@@ -1,7 +1,8 @@
 """The paper's step-form ablations (tuning.step_form = 2) on the CUDA kernels: the ESS bundled
 step without amortisation (both states' log-density calls every step, one masked; Sec. 3.3 /
-App. B) and DR as the 4-state FSM with one state per step (not condensed, Sec. 7.1) compute
-exactly the samples and loop counts of the default forms; only the work per sample differs."""
+App. B) and DR with its PROPOSE body unrolled into four states run one per step (not condensed,
+Sec. 7.1) compute exactly the samples and loop counts of the default forms; only the work per
+sample differs."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,7 @@ def test_ess_not_amortised_gives_identical_samples(eng, lanes):
     assert np.array_equal(sa, (ca + 1).sum(1)) and np.array_equal(sb, sa)
 
 
-def test_dr_not_condensed_gives_identical_samples_with_two_more_states(eng):
+def test_dr_not_condensed_gives_identical_samples_in_four_states_per_stage(eng):
     m, n = 400, 300
     x0 = W.x0_funnel_exact(m)
     w = W.funnel(10)
@@ -62,7 +63,7 @@ def test_dr_not_condensed_gives_identical_samples_with_two_more_states(eng):
     assert np.array_equal(ca, cb)
     assert np.array_equal(xa, xb)
     assert np.array_equal(sa, ca.sum(1))             # condensed: one state per stage tried
-    assert np.array_equal(sb, ca.sum(1) + 2 * n)     # INIT and DONE are states of their own
+    assert np.array_equal(sb, 4 * ca.sum(1))         # draw, evaluate, ratio, decide per stage
     # and both follow the oracle (FP64: 1e-10, identical stage counts)
     ref = O.run("dr", "funnel", np.zeros(1), x0, n, seed=5, algo_params=[3, 1.0, 0.5])
     r = compare(xb, cb, ref["samples"], ref["counts"], "fp64")
