@@ -53,6 +53,8 @@ double ora_dr_stage_log_alpha(int k, int d, const double* x, const double* ys, c
   return dr_stage_log_alpha(k, d, x, ys, lps, sig);
 }
 
+double ora_sdr_log_alpha(double lp_x, double lp_star, double lp_y) { return sdr_log_alpha(lp_x, lp_star, lp_y); }
+
 // One ESS transition with its bracket recorded after every shrink.
 int ora_ess_trace(int kind, int d, int n_data, const double* params, double* x, uint64_t seed,
                   uint32_t chain, uint32_t sample, double* trace, int trace_cap) {
@@ -62,25 +64,28 @@ int ora_ess_trace(int kind, int d, int n_data, const double* params, double* x, 
   return ess_transition(t, s, x, &ell, trace, trace_cap);
 }
 
-// Run n_samples transitions of `algo` (0 ESS, 1 DR, 2 NUTS) on chains
+// Run n_samples transitions of `algo` (0 ESS, 1 DR, 2 NUTS, 3 symmetric DR) on chains
 // chain0 .. chain0+n_chains-1, starting from x0[n_chains][d].
 //   samples [n_chains][n_samples][d]  (nullable)
 //   counts  [n_chains][n_samples]     loop-body count N_ij (nullable)
 //   aux     [n_chains][n_samples]     NUTS tree depth (nullable)
 //   x_final [n_chains][d]             (nullable)
-// algo_params: DR {n_stages, scale0, factor}; NUTS {eps, max_depth, max_dH}; ESS unused.
+// algo_params: DR {n_stages, scale0, factor}; NUTS {eps, max_depth, max_dH}; symmetric DR
+// {n_stages = M, scale0 = sigma}; ESS unused.
 // Returns 0, or -1 for an invalid argument.
 int ora_run(int algo, int kind, int d, int n_data, const double* params, const double* algo_params,
             int64_t chain0, int64_t n_chains, int64_t n_samples, const double* x0, uint64_t seed,
             int n_threads, double* samples, int32_t* counts, int32_t* aux, double* x_final) {
-  if (d <= 0 || n_chains < 0 || n_samples < 0 || algo < 0 || algo > 2) return -1;
+  if (d <= 0 || n_chains < 0 || n_samples < 0 || algo < 0 || algo > 3) return -1;
   Target t{kind, d, n_data, params};
   if (algo == 0 && t.prior_chol() == nullptr) return -1;
   DRParams dp{3, 1.0, 0.5};
   NUTSParams np{0.05, 10, 1000.0};
   if (algo == 1 && algo_params) dp = DRParams{(int)algo_params[0], algo_params[1], algo_params[2]};
   if (algo == 2 && algo_params) np = NUTSParams{algo_params[0], (int)algo_params[1], algo_params[2]};
+  if (algo == 3) dp = algo_params ? DRParams{(int)algo_params[0], algo_params[1], 1.0} : DRParams{100, 0.1, 1.0};
   if (algo == 1 && (dp.n_stages < 1 || dp.n_stages > 3)) return -1;
+  if (algo == 3 && (dp.n_stages < 1 || dp.n_stages > 1000 || !(dp.scale0 > 0))) return -1;
 
   auto work = [&](int64_t c_begin, int64_t c_end) {
     std::vector<double> x(d), g(d);
@@ -92,6 +97,7 @@ int ora_run(int algo, int kind, int d, int n_data, const double* params, const d
         int n = 0, depth = 0;
         if (algo == 0) n = ess_transition(t, s, x.data(), &lp, nullptr, 0);
         else if (algo == 1) n = dr_transition(t, s, dp, x.data(), &lp);
+        else if (algo == 3) n = sdr_transition(t, s, dp, x.data(), &lp);
         else n = nuts_transition(t, s, np, x.data(), &lp, g.data(), &depth);
         if (samples) std::copy(x.begin(), x.end(), samples + (c * n_samples + i) * d);
         if (counts) counts[c * n_samples + i] = n;

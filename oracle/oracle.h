@@ -89,6 +89,13 @@ double log1mexp(double a);
 double dr_stage_log_alpha(int k, int d, const double* x, const double* ys, const double* lps,
                           const double* sig);
 
+// Symmetric delayed rejection (Mira 2001; Sec. 7.1's toy experiment): every try re-centres a
+// symmetric proposal y_k ~ N(y_{k-1}, sigma^2 I) (y_0 = x) on the last rejected point, at most
+// M = n_stages tries, constant sigma = scale0.  Returns the number of tries (1..M).
+int sdr_transition(const Target& t, const Stream& s, const DRParams& p, double* x, double* lp);
+// log alpha_k = min(0, log [(pi(y_k) - pi*)+ / (pi(x) - pi*)]), pi* = max over rejected tries
+double sdr_log_alpha(double lp_x, double lp_star, double lp_y);
+
 // Multinomial NUTS with momentum-sum U-turn criterion.  x[d] in/out,
 // *lp in/out caches log pi(x), grad[d] in/out caches its gradient.
 // Returns the number of leapfrog steps; *depth receives the number of doublings.

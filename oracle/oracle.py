@@ -16,7 +16,7 @@ _SOURCES = ["rng_targets.cpp", "samplers.cpp", "api.cpp"]
 _lock = threading.Lock()
 _lib = None
 
-ALGO = {"ess": 0, "dr": 1, "nuts": 2}
+ALGO = {"ess": 0, "dr": 1, "nuts": 2, "sdr": 3}
 TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5}
 
 
@@ -62,6 +62,8 @@ def lib():
             L.ora_dr_log_alpha3.restype = ctypes.c_double
             L.ora_dr_stage_log_alpha.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
             L.ora_dr_stage_log_alpha.restype = ctypes.c_double
+            L.ora_sdr_log_alpha.argtypes = [ctypes.c_double] * 3
+            L.ora_sdr_log_alpha.restype = ctypes.c_double
             L.ora_ess_trace.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, dp,
                                         ctypes.c_int]
@@ -184,6 +186,11 @@ def dr_log_alpha3(*a):
 
 def log1mexp(a):
     return lib().ora_log1mexp(a)
+
+
+def sdr_log_alpha(lp_x, lp_star, lp_y):
+    """log acceptance of a symmetric re-centred delayed-rejection try (oracle's function)."""
+    return lib().ora_sdr_log_alpha(lp_x, lp_star, lp_y)
 
 
 def dr_stage_log_alpha(k, x, ys, lps, sig):

@@ -163,6 +163,45 @@ int dr_transition(const Target& t, const Stream& s, const DRParams& P, double* x
   return K;
 }
 
+// Symmetric delayed rejection with re-centred proposals (Mira 2001), the sampler of the paper's
+// Sec. 7.1 toy experiment.  A try's proposal density is symmetric and depends only on the last
+// rejected point, so the forward path x -> y_1 -> .. -> y_k and its reverse have the same
+// proposal density, and the rejection factors telescope: pi(x) prod_{j<k} (1 - alpha_j) =
+// pi(x) - pi*, pi* the largest target value among the rejected tries.  Hence
+//   alpha_k = min(1, (pi(y_k) - pi*)+ / (pi(x) - pi*)),
+// written here in log space.  Random numbers as for dr_transition: try k (0-based) takes its
+// normals from draws k(D+1) .. k(D+1)+D-1 and its uniform from words 0-1 of draw k(D+1)+D.
+double sdr_log_alpha(double lp_x, double lp_star, double lp_y) {
+  if (!(lp_y > lp_star)) return kNegInf;                      // pi(y) <= pi*: never accepted
+  const double num = lp_y + log1mexp(lp_star - lp_y);         // log (pi(y) - pi*)
+  const double den = lp_x + log1mexp(lp_star - lp_x);         // log (pi(x) - pi*)
+  if (den == kNegInf) return 0.0;
+  return std::min(0.0, num - den);
+}
+
+int sdr_transition(const Target& t, const Stream& s, const DRParams& P, double* x, double* lp) {
+  const int d = t.d;
+  const int D = normal_blocks(d);
+  std::vector<double> centre(x, x + d), y(d), eps(d);
+  double lp_star = kNegInf;
+  for (int k = 0; k < P.n_stages; ++k) {
+    const uint32_t base = (uint32_t)(k * (D + 1));
+    normals(s, 0, base, d, eps.data());
+    for (int c = 0; c < d; ++c) y[c] = centre[c] + P.scale0 * eps[c];
+    const double lp_y = t.logp(y.data(), nullptr);
+    const double la = sdr_log_alpha(*lp, lp_star, lp_y);
+    Block b = s.block(0, base + (uint32_t)D);
+    if (std::log(uniform(b.w[0], b.w[1])) < la) {
+      std::copy(y.begin(), y.end(), x);
+      *lp = lp_y;
+      return k + 1;
+    }
+    lp_star = std::max(lp_star, lp_y);
+    centre = y;
+  }
+  return P.n_stages;
+}
+
 // ------------------------------------------------------------------------------------
 // NUTS (Hoffman & Gelman) in its multinomial form, built recursively.
 //  * momentum p ~ N(0, I) (identity mass), H = -log pi(x) + |p|^2 / 2;
