@@ -72,6 +72,14 @@ def _make_config(name, scale):
         m, n = int(65536 * scale), 5000
         return dict(name="dr3_funnel_d10_m65536_n5000", algo="dr", w=w, m=m, n=n, prec="fp32",
                     x0=W.x0_funnel_exact(m), algo_params=[3, 1.0, 0.5])
+    if name == "dr_sym":
+        # the paper's delayed-rejection toy (Sec. 7.1): symmetric DR on N(0, 1), re-centred tries of
+        # sd 0.1, at most M = 100 tries per sample
+        w = W.std_normal(1)
+        m, n = int(65536 * scale), 2000
+        return dict(name="sdr_std_normal_d1_M100_m65536_n2000", algo="dr", w=w, m=m, n=n, prec="fp32",
+                    x0=W.x0_gauss_diag_exact(w, m), algo_params=[100, 0.1, 1.0], dr_symmetric=1,
+                    oracle_algo="sdr", oracle_params=[100, 0.1])
     if name == "nuts_logreg":
         w = W.logreg(1000, 25)
         m, n = int(4096 * scale), 1000
@@ -138,8 +146,8 @@ def oracle_throughput(cfg, target_s=10.0):
     while True:
         x0 = cfg["x0"][:m] if len(cfg["x0"]) >= m else np.resize(cfg["x0"], (m, w["d"]))
         t0 = time.perf_counter()
-        O.run(cfg["algo"], w["kind"], w["params"], x0, n_s, seed=1, n_data=w["n_data"],
-              algo_params=cfg["algo_params"], n_threads=cores, store=False)
+        O.run(cfg.get("oracle_algo", cfg["algo"]), w["kind"], w["params"], x0, n_s, seed=1, n_data=w["n_data"],
+              algo_params=cfg.get("oracle_params", cfg["algo_params"]), n_threads=cores, store=False)
         t = time.perf_counter() - t0
         if t >= target_s / 4 or m >= 65536:
             break
@@ -190,7 +198,7 @@ def run_ours(args, rank, world):
     tg = eng.target(w["kind"], w["d"], w["params"], n_data=w["n_data"])
     dr = nuts = None
     if cfg["algo"] == "dr":
-        dr = dict(zip(["n_stages", "scale0", "factor"], cfg["algo_params"]))
+        dr = dict(zip(["n_stages", "scale0", "factor"], cfg["algo_params"]), symmetric=cfg.get("dr_symmetric", 0))
     if cfg["algo"] == "nuts":
         nuts = dict(zip(["eps", "max_depth", "max_dH"], cfg["algo_params"]))
     tuning = {"profile_kernels": 1, **parse_tuning(args.tuning)}
@@ -336,7 +344,7 @@ def run_ours(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if cfg["prec"] == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "chains_per_gpu": m, "samples_per_chain": n,
-                       "d": w["d"], "algo": cfg["algo"], "store": "all samples on device",
+                       "d": w["d"], "algo": cfg.get("oracle_algo", cfg["algo"]), "store": "all samples on device",
                        "l2": "flushed between steps (256 MiB write); outputs exceed L2",
                        "parallelism": f"replicas x{world} (independent chains)"},
             "fsm": {"value": value, "R_hat": st["R_hat"], "mean_N": st["mean_N"],
@@ -378,7 +386,7 @@ def run_reference(args, rank, world):
             "ms_per_step": cfg["m"] * cfg["n"] / value * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "chains_per_gpu": cfg["m"],
-                       "samples_per_chain": cfg["n"], "d": cfg["w"]["d"], "algo": cfg["algo"]},
+                       "samples_per_chain": cfg["n"], "d": cfg["w"]["d"], "algo": cfg.get("oracle_algo", cfg["algo"])},
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -387,11 +395,11 @@ def run_reference(args, rank, world):
 # ---- step-form ablations ------------------------------------------------------------------------------
 def run_ablations(args):
     """The paper's step-form ablations on the CUDA kernels (tuning.step_form = 2 against the
-    default 1): ESS with the log-density evaluated inside INIT and SHRINK instead of once per step
-    (not amortised), with one chain per thread (warps whose chains are in both states pay twice)
+    default 1): ESS as the bundled step without amortisation (both states' log-density calls every
+    step, one masked), with one chain per thread
     and one chain per warp; DR with its PROPOSE body unrolled into four states run one per step
-    (not condensed).  The
-    two forms give identical samples (tests/test_gpu_ablation.py); this reports their device time."""
+    (not condensed).  The two forms give identical samples (tests/test_gpu_ablation.py); this
+    reports their device time."""
     import torch
     from paper_2503_17405_b300 import fsmc
 

@@ -81,9 +81,14 @@ typedef enum fsmc_mode { FSMC_MODE_FSM = 0, FSMC_MODE_SYNC = 1 } fsmc_mode;
 
 /* Delayed rejection: stage k (k = 0..n_stages-1) proposes y ~ N(x, (scale0 factor^k)^2 I). */
 typedef struct fsmc_dr_params {
-  int n_stages;  /* 1..3 */
-  double scale0;
-  double factor;
+  int n_stages;  /* 1..3; symmetric: 1..1000 tries                                        */
+  double scale0; /* proposal sd of stage 0 (symmetric: of every try)                         */
+  double factor; /* stage k uses scale0 * factor^k (ignored when symmetric)                   */
+  int symmetric; /* 0: proposals centred at x, general acceptance (Sec. 7.1 reading, above);
+                    1: symmetric delayed rejection (Mira 2001, the paper's toy sampler): try k
+                    re-centres y_k ~ N(y_{k-1}, scale0^2 I) on the last rejected point and is
+                    accepted with min(1, (pi(y_k) - pi*)+ / (pi(x) - pi*)), pi* the largest
+                    target value among the rejected tries                                    */
 } fsmc_dr_params;
 
 /* NUTS: leapfrog step eps, at most max_depth doublings, divergence when H - H0 > max_dH. */

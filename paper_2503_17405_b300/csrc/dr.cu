@@ -126,7 +126,7 @@ __device__ __forceinline__ void dr_draw(const DrView<T>& v, const Key& key, int 
   const int d = v.tg.d;
   const int D = (d + 3) / 4;  // Philox blocks per stage (four normals each)
   const uint32_t base = (uint32_t)(k * (D + 1));
-  const T sg = v.sig[k];
+  const T sg = v.symmetric ? v.sig[0] : v.sig[k];
 #pragma unroll
   for (int q = 0; q < (E + 3) / 4; ++q) {
     T z[4] = {T(0), T(0), T(0), T(0)};
@@ -182,10 +182,53 @@ __device__ __forceinline__ bool dr_decide(const DrView<T>& v, const Key& key, in
   return false;
 }
 
-// One PROPOSE step of stage k for one chain (all four parts).
+// Symmetric delayed rejection (Mira 2001), try k: y ~ N(centre, sig[0]^2 I) with the centre the
+// last rejected point (x for the first try), accepted with
+//   alpha_k = min(1, (pi(y) - pi*)+ / (pi(x) - pi*)),
+// pi* the largest target value among the rejected tries (the rejection factors of a re-centred
+// symmetric proposal telescope to pi(x) - pi*).  centre and lp_star are kept in y1 and lp1.
+// Same random numbers as the staged sampler: try k's normals from draws k(D+1) + q, its uniform
+// from draw k(D+1) + D.
+template <typename T>
+__device__ __forceinline__ T sdr_log_alpha(T lp_x, T lp_star, T lp_y) {
+  if (!(lp_y > lp_star)) return neg_inf<T>();
+  const T num = lp_y + l1m(lp_star - lp_y);
+  const T den = lp_x + l1m(lp_star - lp_x);
+  if (den == neg_inf<T>()) return T(0);
+  return fmin(T(0), num - den);
+}
+
+template <typename T, int E>
+__device__ __forceinline__ bool sdr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E], T& lp,
+                                         T (&centre)[E], T& lp_star, int& err) {
+  if (k == 0) {  // a new sample: the first try is centred at x
+#pragma unroll
+    for (int e = 0; e < E; ++e) centre[e] = x[e];
+    lp_star = neg_inf<T>();
+  }
+  T y[E];
+  dr_draw<T, E>(v, key, t, k, centre, y);
+  const T lpy = dr_eval<T, E>(v, y, err);
+  const T la = sdr_log_alpha<T>(lp, lp_star, lpy);
+  const int D = (v.tg.d + 3) / 4;
+  const P4 r = key.block((uint32_t)t, 0, (uint32_t)(k * (D + 1) + D));
+  if (Conv<T>::log_u(r.w0, r.w1) < la) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = y[e];
+    lp = lpy;
+    return true;
+  }
+  lp_star = fmax(lp_star, lpy);
+#pragma unroll
+  for (int e = 0; e < E; ++e) centre[e] = y[e];
+  return k + 1 >= v.n_stages;
+}
+
+// One PROPOSE step of stage k for one chain (all four parts); the symmetric sampler's try k.
 template <typename T, int E>
 __device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E],
                                         T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, int& err) {
+  if (v.symmetric) return sdr_step<T, E>(v, key, t, k, x, lp, y1, lp1, err);
   T y[E];
   dr_draw<T, E>(v, key, t, k, x, y);
   const T lpy = dr_eval<T, E>(v, y, err);

@@ -401,7 +401,9 @@ DrView<T> dr_view(const fsmc_job* j) {
   char* b = j->dev;
   v.tg = target_view<T>(j->tg);
   v.n_stages = j->dr.n_stages;
-  for (int k = 0; k < 3; ++k) v.sig[k] = (T)(j->dr.scale0 * std::pow(j->dr.factor, (double)k));
+  v.symmetric = j->dr.symmetric;
+  for (int k = 0; k < 3; ++k)
+    v.sig[k] = (T)(j->dr.symmetric ? j->dr.scale0 : j->dr.scale0 * std::pow(j->dr.factor, (double)k));
   v.lp = (T*)(b + j->o_ell);
   v.y = (T*)(b + j->o_y);
   v.lpy = (T*)(b + j->o_lpy);
@@ -480,10 +482,12 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
   j->seed = seed;
   j->store = store_samples ? 1 : 0;
   if (algo == FSMC_DR) {
-    j->dr = algo_params ? *(const fsmc_dr_params*)algo_params : fsmc_dr_params{3, 1.0, 0.5};
-    if (j->dr.n_stages < 1 || j->dr.n_stages > 3 || !(j->dr.scale0 > 0) || !(j->dr.factor > 0)) {
+    j->dr = algo_params ? *(const fsmc_dr_params*)algo_params : fsmc_dr_params{3, 1.0, 0.5, 0};
+    const int max_stages = j->dr.symmetric ? 1000 : 3;
+    if (j->dr.n_stages < 1 || j->dr.n_stages > max_stages || !(j->dr.scale0 > 0) ||
+        !(j->dr.symmetric || j->dr.factor > 0) || (j->dr.symmetric != 0 && j->dr.symmetric != 1)) {
       delete j;
-      return fsmc_fail(FSMC_EINVAL, "DR params: 1..3 stages, positive scales");
+      return fsmc_fail(FSMC_EINVAL, "DR params: 1..3 stages (symmetric: 1..1000 tries), positive scales");
     }
   }
   if (algo == FSMC_NUTS) {
@@ -538,6 +542,8 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (t.pipelined < 0 || t.pipelined > 2) return fsmc_fail(FSMC_EINVAL, "pipelined must be 0, 1 or 2");
   if (t.step_form < 0 || t.step_form > 2) return fsmc_fail(FSMC_EINVAL, "step_form must be 0, 1 or 2");
   if (t.step_form == 2 && j->algo == FSMC_NUTS) return fsmc_fail(FSMC_EINVAL, "NUTS has step form 1 only");
+  if (t.step_form == 2 && j->algo == FSMC_DR && j->dr.symmetric)
+    return fsmc_fail(FSMC_EINVAL, "symmetric DR has step form 1 only");
   if (t.generator == 2 && (j->algo != FSMC_ESS || j->prec != FSMC_FP32 || j->d > 256))
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   j->tun = t;

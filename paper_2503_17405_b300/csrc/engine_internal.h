@@ -57,7 +57,7 @@ struct fsmc_job {
   uint32_t chain0 = 0;
   int store = 1;
   fsmc_tuning tun{};
-  fsmc_dr_params dr{3, 1.0, 0.5};
+  fsmc_dr_params dr{3, 1.0, 0.5, 0};
   fsmc_nuts_params nuts{0.05, 10, 1000.0};
   std::vector<double> x0;
   // device arena and offsets into it

@@ -53,6 +53,7 @@ template <typename T>
 struct DrView : ChainsView<T> {
   TargetView<T> tg;
   int n_stages;
+  int symmetric;         // 1: symmetric delayed rejection, re-centred tries (sig[0] each)
   T sig[3];              // stage scales
   T* lp;                 // [m] log pi(x)
   T* y;                  // [3][m][d] rejected proposals y1, y2 of the current sample; the

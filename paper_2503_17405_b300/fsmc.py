@@ -27,7 +27,8 @@ class FsmcError(RuntimeError):
 
 
 class DRParams(ctypes.Structure):
-    _fields_ = [("n_stages", ctypes.c_int), ("scale0", ctypes.c_double), ("factor", ctypes.c_double)]
+    _fields_ = [("n_stages", ctypes.c_int), ("scale0", ctypes.c_double), ("factor", ctypes.c_double),
+                ("symmetric", ctypes.c_int)]
 
 
 class NUTSParams(ctypes.Structure):
@@ -156,7 +157,8 @@ class Engine:
         ap = None
         if algo == "dr":
             dr = dr or {}
-            keep = DRParams(dr.get("n_stages", 3), dr.get("scale0", 1.0), dr.get("factor", 0.5))
+            keep = DRParams(dr.get("n_stages", 3), dr.get("scale0", 1.0), dr.get("factor", 0.5),
+                            int(dr.get("symmetric", 0)))
             ap = ctypes.cast(ctypes.byref(keep), _vp)
         elif algo == "nuts":
             nuts = nuts or {}
@@ -205,7 +207,8 @@ class Job:
         ap = None
         if algo == "dr":
             dr = dr or {}
-            self._ap = DRParams(dr.get("n_stages", 3), dr.get("scale0", 1.0), dr.get("factor", 0.5))
+            self._ap = DRParams(dr.get("n_stages", 3), dr.get("scale0", 1.0), dr.get("factor", 0.5),
+                                int(dr.get("symmetric", 0)))
             ap = ctypes.cast(ctypes.byref(self._ap), _vp)
         elif algo == "nuts":
             nuts = nuts or {}

@@ -77,6 +77,12 @@ def gauss_diag(d=8, seed=DATA_SEED):
     return dict(kind="gauss_diag", d=d, n_data=0, params=np.concatenate([mu, sd]), mu=mu, sd=sd)
 
 
+def std_normal(d=1):
+    """N(0, I_d) as a diagonal Gaussian (the target of the paper's delayed-rejection toy)."""
+    mu, sd = np.zeros(d), np.ones(d)
+    return dict(kind="gauss_diag", d=d, n_data=0, params=np.concatenate([mu, sd]), mu=mu, sd=sd)
+
+
 def flat(d=8, seed=DATA_SEED):
     r = _rng(seed, 5)
     A = r.standard_normal((d, d))

@@ -99,3 +99,57 @@ def test_full_size_funnel_sampled_chains(full_funnel_job, chain):
     r = compare(job.samples(chain, 1, 0, nref), counts[chain:chain + 1, :nref], ref["samples"],
                 ref["counts"], "fp32")
     print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
+
+
+SDR = {"n_stages": 100, "scale0": 0.1, "factor": 1.0, "symmetric": 1}
+
+
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_symmetric_dr_on_standard_normal_matches_oracle(eng, mode):
+    # the paper's toy experiment (Sec. 7.1): N(0, 1), re-centred tries of sd 0.1, M = 100
+    m, n = 256, 400
+    params = np.array([0.0, 1.0])
+    x0 = np.random.default_rng(5).standard_normal((m, 1))
+    tg = eng.target("gauss_diag", 1, params)
+    job = eng.job(tg, "dr", m, n, x0=x0, seed=2, prec="fp64", dr=SDR, tuning={"steps_per_launch": 40})
+    job.run(mode)
+    ref = O.run("sdr", "gauss_diag", params, x0, n, seed=2, algo_params=[100, 0.1])
+    counts, _, steps = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    assert counts.max() > 5  # some samples need many tries
+    if mode == "fsm":
+        assert np.array_equal(steps, counts.sum(1))
+    else:
+        assert job.stats()["sync_iterations"] == int(counts.max(0).sum())
+    job.close()
+
+
+def test_fp64_symmetric_dr_diag_gaussian_matches_oracle(eng):
+    w = W.gauss_diag(3)
+    m, n = 128, 300
+    x0 = W.x0_gauss_diag_exact(w, m)
+    sdr = {"n_stages": 20, "scale0": 0.5, "factor": 1.0, "symmetric": 1}
+    tg = eng.target("gauss_diag", 3, w["params"])
+    job = eng.job(tg, "dr", m, n, x0=x0, seed=4, prec="fp64", dr=sdr)
+    job.run("fsm")
+    ref = O.run("sdr", "gauss_diag", w["params"], x0, n, seed=4, algo_params=[20, 0.5])
+    counts, _, _ = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    job.close()
+
+
+def test_fp32_symmetric_dr_sync_and_fsm_identical(eng):
+    m, n = 2048, 300
+    params = np.array([0.0, 1.0])
+    x0 = np.random.default_rng(6).standard_normal((m, 1))
+    tg = eng.target("gauss_diag", 1, params)
+    out = []
+    for mode in ("fsm", "sync"):
+        job = eng.job(tg, "dr", m, n, x0=x0, seed=3, prec="fp32", dr=SDR)
+        job.run(mode)
+        out.append((job.samples(), job.loop_counts()[0]))
+        job.close()
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0], out[1][0])
