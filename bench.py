@@ -452,6 +452,17 @@ def run_ablations(args):
                         "workload": f"dr3_funnel_d10_m{m}_n{n}_fp32",
                         "default": a, "ablation_form": b, "ratio": b["ms_per_job"] / a["ms_per_job"],
                         "states_per_sample": [a["fsm_states"] / (m * n), b["fsm_states"] / (m * n)]})
+    # the paper's own ablation workload (Sec. 7.1): symmetric DR on N(0, 1), sd 0.1, M = 100
+    w = W.std_normal(1)
+    tg = eng.target(w["kind"], 1, w["params"])
+    x0 = W.x0_gauss_diag_exact(w, m)
+    dr = {"n_stages": 100, "scale0": 0.1, "factor": 1.0, "symmetric": 1}
+    a = timed(tg, "dr", m, n, x0, {"step_form": 1}, dr=dr)
+    b = timed(tg, "dr", m, n, x0, {"step_form": 2}, dr=dr)
+    out["rows"].append({"ablation": "symmetric DR try as 4 states (not condensed)",
+                        "workload": f"sdr_std_normal_d1_M100_m{m}_n{n}_fp32",
+                        "default": a, "ablation_form": b, "ratio": b["ms_per_job"] / a["ms_per_job"],
+                        "states_per_sample": [a["fsm_states"] / (m * n), b["fsm_states"] / (m * n)]})
     eng.close()
     return out
 

@@ -199,17 +199,16 @@ __device__ __forceinline__ T sdr_log_alpha(T lp_x, T lp_star, T lp_y) {
 }
 
 template <typename T, int E>
-__device__ __forceinline__ bool sdr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E], T& lp,
-                                         T (&centre)[E], T& lp_star, int& err) {
-  if (k == 0) {  // a new sample: the first try is centred at x
+__device__ __forceinline__ void sdr_begin(const T (&x)[E], T (&centre)[E], T& lp_star) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) centre[e] = x[e];
-    lp_star = neg_inf<T>();
-  }
-  T y[E];
-  dr_draw<T, E>(v, key, t, k, centre, y);
-  const T lpy = dr_eval<T, E>(v, y, err);
-  const T la = sdr_log_alpha<T>(lp, lp_star, lpy);
+  for (int e = 0; e < E; ++e) centre[e] = x[e];
+  lp_star = neg_inf<T>();
+}
+
+// Try k's decision; true when the sample is finished (accepted, or the M-th try rejected).
+template <typename T, int E>
+__device__ __forceinline__ bool sdr_decide(const DrView<T>& v, const Key& key, int t, int k, T la, T (&x)[E],
+                                           T& lp, T (&centre)[E], T& lp_star, const T (&y)[E], T lpy) {
   const int D = (v.tg.d + 3) / 4;
   const P4 r = key.block((uint32_t)t, 0, (uint32_t)(k * (D + 1) + D));
   if (Conv<T>::log_u(r.w0, r.w1) < la) {
@@ -222,6 +221,16 @@ __device__ __forceinline__ bool sdr_step(const DrView<T>& v, const Key& key, int
 #pragma unroll
   for (int e = 0; e < E; ++e) centre[e] = y[e];
   return k + 1 >= v.n_stages;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ bool sdr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E], T& lp,
+                                         T (&centre)[E], T& lp_star, int& err) {
+  if (k == 0) sdr_begin<T, E>(x, centre, lp_star);  // a new sample: the first try is centred at x
+  T y[E];
+  dr_draw<T, E>(v, key, t, k, centre, y);
+  const T lpy = dr_eval<T, E>(v, y, err);
+  return sdr_decide<T, E>(v, key, t, k, sdr_log_alpha<T>(lp, lp_star, lpy), x, lp, centre, lp_star, y, lpy);
 }
 
 // One PROPOSE step of stage k for one chain (all four parts); the symmetric sampler's try k.
@@ -267,9 +276,10 @@ __device__ __forceinline__ void dr_store(const DrView<T>& v, int64_t c, const T 
 // CONDENSED (Sec. 7.1): the single PROPOSE state, with INIT and DONE run inline -- a sample takes
 // as many steps as stages tried; k is the next stage.  !CONDENSED (the paper's ablation, Sec. 7.1):
 // the PROPOSE body unrolled into four states run one per step -- draw, evaluate, ratio, decide
-// (k = 4 j + u for stage j, part u) -- with the proposal, its log density and the ratio kept in
-// the chain state between steps; a warp whose chains are in different parts runs each part's code.
-// Both forms compute the same samples.
+// (k = 4 j + u for stage (try) j, part u) -- with the proposal, its log density and the ratio kept
+// in the chain state between steps; a warp whose chains are in different parts runs each part's
+// code.  Both forms compute the same samples, for the staged and the symmetric sampler (whose
+// centre and pi* are y1 and lp1).
 
 template <typename T, int E, bool CONDENSED>
 __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
@@ -305,15 +315,18 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
       } else {
         const int j = k >> 2, u = k & 3;
         if (u == 0) {
-          dr_draw<T, E>(v, key, t, j, x, yc);
+          if (v.symmetric && j == 0) sdr_begin<T, E>(x, y1, lp1);
+          dr_draw<T, E>(v, key, t, j, v.symmetric ? y1 : x, yc);
           ++k;
         } else if (u == 1) {
           lpc = dr_eval<T, E>(v, yc, err);
           ++k;
         } else if (u == 2) {
-          lac = dr_ratio<T, E>(v, j, x, lp, y1, lp1, y2, lp2, yc, lpc);
+          lac = v.symmetric ? sdr_log_alpha<T>(lp, lp1, lpc)
+                            : dr_ratio<T, E>(v, j, x, lp, y1, lp1, y2, lp2, yc, lpc);
           ++k;
-        } else if (dr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, y2, lp2, yc, lpc)) {
+        } else if (v.symmetric ? sdr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, yc, lpc)
+                               : dr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, y2, lp2, yc, lpc)) {
           dr_emit<T, E>(v, c, t, x);
           v.counts[(size_t)c * v.n + t] = j + 1;
           ++t;

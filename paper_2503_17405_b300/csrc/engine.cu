@@ -542,8 +542,6 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (t.pipelined < 0 || t.pipelined > 2) return fsmc_fail(FSMC_EINVAL, "pipelined must be 0, 1 or 2");
   if (t.step_form < 0 || t.step_form > 2) return fsmc_fail(FSMC_EINVAL, "step_form must be 0, 1 or 2");
   if (t.step_form == 2 && j->algo == FSMC_NUTS) return fsmc_fail(FSMC_EINVAL, "NUTS has step form 1 only");
-  if (t.step_form == 2 && j->algo == FSMC_DR && j->dr.symmetric)
-    return fsmc_fail(FSMC_EINVAL, "symmetric DR has step form 1 only");
   if (t.generator == 2 && (j->algo != FSMC_ESS || j->prec != FSMC_FP32 || j->d > 256))
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   j->tun = t;

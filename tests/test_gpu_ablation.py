@@ -70,6 +70,33 @@ def test_dr_not_condensed_gives_identical_samples_in_four_states_per_stage(eng):
     assert r["max_err"] <= 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_symmetric_dr_four_states_per_try_on_the_papers_toy(eng, prec):
+    # Sec. 7.1's toy: N(0, 1), re-centred tries of sd 0.1, at most M = 100 tries; a launch budget
+    # that splits samples and tries across launches
+    m, n = 512, 200
+    x0 = np.random.default_rng(5).standard_normal((m, 1))
+    tg = eng.target("gauss_diag", 1, np.array([0.0, 1.0]))
+    sdr = {"n_stages": 100, "scale0": 0.1, "factor": 1.0, "symmetric": 1}
+    out = []
+    for form in (1, 2):
+        job = eng.job(tg, "dr", m, n, x0=x0, seed=8, prec=prec, dr=sdr,
+                      tuning={"steps_per_launch": 41, "step_form": form})
+        job.run("fsm")
+        c, _, steps = job.loop_counts()
+        out.append((job.samples(), c, steps))
+        job.close()
+    (xa, ca, sa), (xb, cb, sb) = out
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(sa, ca.sum(1)) and np.array_equal(sb, 4 * ca.sum(1))
+    assert ca.max() > 5  # some samples need many tries
+    if prec == "fp64":
+        ref = O.run("sdr", "gauss_diag", np.array([0.0, 1.0]), x0, n, seed=8, algo_params=[100, 0.1])
+        r = compare(xb, cb, ref["samples"], ref["counts"], "fp64")
+        assert r["max_err"] <= 1e-10
+
+
 def test_step_form_limits(eng):
     from paper_2503_17405_b300 import fsmc
     lr = W.logreg(200, 5)
