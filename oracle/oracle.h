@@ -53,6 +53,9 @@ enum TargetKind {
   TGT_LOGREG = 3,      // logistic-regression log-posterior;         params: X[n*d], y[n]
   TGT_GAUSS_DIAG = 4,  // N(mu, diag sigma^2) log-density;           params: mu[d], sigma[d]
   TGT_FLAT = 5,        // ESS likelihood f == 1;                      params: L[d*d]
+  TGT_MOG = 6,         // mixture of K = n_data Gaussians N(mu_k, S), S = (1-rho) I + rho 1 1^T
+                       // (unit variances, correlation rho), weights w_k;
+                       //                                  params: rho, w[K], mu[K*d]
 };
 
 struct Target {

@@ -17,7 +17,7 @@ _lock = threading.Lock()
 _lib = None
 
 ALGO = {"ess": 0, "dr": 1, "nuts": 2, "sdr": 3}
-TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5}
+TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5, "mog": 6}
 
 
 def build(force=False):

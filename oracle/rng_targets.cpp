@@ -1,6 +1,8 @@
 // Oracle RNG and targets (test infrastructure; see oracle.h).
 #include "oracle.h"
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 namespace ora {
 
@@ -118,6 +120,40 @@ double Target::logp(const double* x, double* grad) const {
         }
       }
       return acc;
+    }
+    case TGT_MOG: {
+      // log pi(x) = log sum_k w_k exp(-q_k / 2), q_k = (x - mu_k)^T S^-1 (x - mu_k), with the
+      // Sherman-Morrison inverse S^-1 = (I - c 1 1^T) / (1 - rho), c = rho / (1 + (d - 1) rho).
+      // The Gaussian normaliser is the same for every component and is dropped.
+      // grad = -sum_k r_k S^-1 (x - mu_k), r_k the component responsibilities.
+      const int K = n_data;
+      const double rho = params[0];
+      const double* w = params + 1;
+      const double* mu = params + 1 + K;
+      const double c = rho / (1.0 + (d - 1) * rho);
+      std::vector<double> lw(K), sum_v(K);
+      double lmax = -INFINITY;
+      for (int k = 0; k < K; ++k) {
+        const double* m = mu + (size_t)k * d;
+        double vv = 0, sv = 0;
+        for (int i = 0; i < d; ++i) { const double v = x[i] - m[i]; vv += v * v; sv += v; }
+        const double q = (vv - c * sv * sv) / (1.0 - rho);
+        lw[k] = std::log(w[k]) - 0.5 * q;
+        sum_v[k] = sv;
+        lmax = std::max(lmax, lw[k]);
+      }
+      double z = 0;
+      for (int k = 0; k < K; ++k) z += std::exp(lw[k] - lmax);
+      const double lse = lmax + std::log(z);
+      if (grad) {
+        for (int i = 0; i < d; ++i) grad[i] = 0;
+        for (int k = 0; k < K; ++k) {
+          const double r = std::exp(lw[k] - lse);
+          const double* m = mu + (size_t)k * d;
+          for (int i = 0; i < d; ++i) grad[i] -= r * (x[i] - m[i] - c * sum_v[k]) / (1.0 - rho);
+        }
+      }
+      return lse;
     }
     case TGT_GAUSS_DIAG: {
       const double* mu = params;

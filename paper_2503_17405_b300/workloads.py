@@ -83,6 +83,27 @@ def std_normal(d=1):
     return dict(kind="gauss_diag", d=d, n_data=0, params=np.concatenate([mu, sd]), mu=mu, sd=sd)
 
 
+def mog(d=100, rho=0.99, offsets=(-10.0, 0.0, 10.0), weights=None):
+    """Sec. 7.3's NUTS target: an equal-weight mixture of Gaussians with unit variances and
+    correlation rho between every pair of coordinates, the modes on the principal direction at
+    offset * (1, ..., 1).  params = rho, w[K], mu[K * d] with n_data = K."""
+    K = len(offsets)
+    w = np.ones(K) if weights is None else np.asarray(weights, dtype=np.float64)
+    mu = np.outer(np.asarray(offsets, dtype=np.float64), np.ones(d))
+    return dict(kind="mog", d=d, n_data=K, params=np.concatenate([[rho], w, mu.ravel()]),
+                rho=rho, w=w, mu=mu)
+
+
+def x0_mog_exact(w, m, seed=DATA_SEED, stream=15):
+    """Exact draws: a component by weight, then mu_k + sqrt(1 - rho) z + sqrt(rho) zeta 1
+    (covariance (1 - rho) I + rho 1 1^T; rho >= 0)."""
+    r = _rng(seed, stream)
+    k = r.choice(len(w["w"]), size=m, p=w["w"] / w["w"].sum())
+    z = r.standard_normal((m, w["d"]))
+    zeta = r.standard_normal((m, 1))
+    return w["mu"][k] + np.sqrt(1.0 - w["rho"]) * z + np.sqrt(w["rho"]) * zeta
+
+
 def flat(d=8, seed=DATA_SEED):
     r = _rng(seed, 5)
     A = r.standard_normal((d, d))
