@@ -80,6 +80,13 @@ def _make_config(name, scale):
         return dict(name="sdr_std_normal_d1_M100_m65536_n2000", algo="dr", w=w, m=m, n=n, prec="fp32",
                     x0=W.x0_gauss_diag_exact(w, m), algo_params=[100, 0.1, 1.0], dr_symmetric=1,
                     oracle_algo="sdr", oracle_params=[100, 0.1])
+    if name == "nuts_mog":
+        # Sec. 7.3: NUTS on the 100-d mixture of Gaussians with correlation 0.99, modes at
+        # -10 * 1, 0, 10 * 1, identity mass, step 0.044 (acceptance statistic ~0.87), depth <= 10
+        w = W.mog(100)
+        m, n = int(4096 * scale), 1000
+        return dict(name="nuts_mog_d100_rho0.99_m4096_n1000", algo="nuts", w=w, m=m, n=n,
+                    prec="fp32", x0=W.x0_mog_exact(w, m), algo_params=[0.044, 10, 1000.0])
     if name == "nuts_logreg":
         w = W.logreg(1000, 25)
         m, n = int(4096 * scale), 1000
@@ -303,7 +310,8 @@ def run_ours(args, rank, world):
         if cfg["algo"] == "ess":
             per = 12 * d
         elif cfg["algo"] == "nuts":
-            per = 4 * w["n_data"] * d
+            # logistic regression: 4 n d; mixture: (7 K + 1) d (residual, its square, the gradient)
+            per = 4 * w["n_data"] * d if w["kind"] == "logreg" else (7 * w["n_data"] + 1) * d
         else:
             per = 20 * d
         achieved = steps_total * per / (kms_own[1] / 1e3) / 1e12 if kms_own[1] else None
@@ -316,7 +324,8 @@ def run_ours(args, rank, world):
                 "flops_per_step": per,
                 "limiter": {"ess": "instruction issue (~190 warp instructions per state; 2 MUFU per coordinate)",
                             "dr": "latency: one chain per thread, ~14 resident warps per SM at 65536 chains",
-                            "nuts": "latency and occupancy of the block-batched gradient"}[cfg["algo"]]}
+                            "nuts": "latency and occupancy of the block-batched gradient" if w["kind"] == "logreg"
+                            else "latency: one chain per warp, shuffle reductions per component and U-turn test"}[cfg["algo"]]}
 
     # end to end through the public API: host params and x0 in, posterior moments out
     e2e = None

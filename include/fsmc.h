@@ -60,15 +60,21 @@ typedef enum fsmc_status {
  *   FUNNEL      Neal funnel, v ~ N(0,9), x_i|v ~ N(0,e^v): no params (n_params = 0)
  *   LOGREG      beta ~ N(0,I), y_i ~ Bern(sigmoid(X_i beta)): X[n_data*d], y[n_data]
  *   GAUSS_DIAG  N(mu, diag(sigma^2)):                     mu[d], sigma[d]
+ *   MOG         mixture of K = n_data (1..64) Gaussians N(mu_k, S), S = (1 - rho) I + rho 1 1^T
+ *               (unit variances, every pair correlated rho; Sec. 7.3's NUTS target), weights w_k:
+ *               log pi(x) = log sum_k w_k exp(-(x - mu_k)^T S^-1 (x - mu_k) / 2) (the common
+ *               normaliser dropped):                       rho, w[K], mu[K*d]
+ *               (-1/(d-1) < rho < 1 and w_k > 0 finite, else FSMC_EINVAL)
  * ESS needs a kind with a prior factor L (GAUSS_CONJ, GP_LOGIT, FLAT); DR and NUTS need
- * a full log-density (FUNNEL, LOGREG, GAUSS_DIAG).  The ESS prior is N(0, L L^T) (Alg. 8). */
+ * a full log-density (FUNNEL, LOGREG, GAUSS_DIAG, MOG).  The ESS prior is N(0, L L^T) (Alg. 8). */
 typedef enum fsmc_target_kind {
   FSMC_TGT_GAUSS_CONJ = 0,
   FSMC_TGT_GP_LOGIT = 1,
   FSMC_TGT_FUNNEL = 2,
   FSMC_TGT_LOGREG = 3,
   FSMC_TGT_GAUSS_DIAG = 4,
-  FSMC_TGT_FLAT = 5
+  FSMC_TGT_FLAT = 5,
+  FSMC_TGT_MOG = 6
 } fsmc_target_kind;
 
 typedef enum fsmc_algo { FSMC_ESS = 0, FSMC_DR = 1, FSMC_NUTS = 2 } fsmc_algo;

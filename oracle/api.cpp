@@ -73,50 +73,96 @@ int ora_ess_trace(int kind, int d, int n_data, const double* params, double* x, 
 // algo_params: DR {n_stages, scale0, factor}; NUTS {eps, max_depth, max_dH}; symmetric DR
 // {n_stages = M, scale0 = sigma}; ESS unused.
 // Returns 0, or -1 for an invalid argument.
+// Sampler settings from the algo_params array (nullptr: defaults); false when invalid.
+static bool sampler_params(int algo, const double* algo_params, DRParams* dp, NUTSParams* np) {
+  *dp = DRParams{3, 1.0, 0.5};
+  *np = NUTSParams{0.05, 10, 1000.0};
+  if (algo == 1 && algo_params) *dp = DRParams{(int)algo_params[0], algo_params[1], algo_params[2]};
+  if (algo == 2 && algo_params) *np = NUTSParams{algo_params[0], (int)algo_params[1], algo_params[2]};
+  if (algo == 3) *dp = algo_params ? DRParams{(int)algo_params[0], algo_params[1], 1.0} : DRParams{100, 0.1, 1.0};
+  if (algo == 1 && (dp->n_stages < 1 || dp->n_stages > 3)) return false;
+  if (algo == 3 && (dp->n_stages < 1 || dp->n_stages > 1000 || !(dp->scale0 > 0))) return false;
+  return true;
+}
+
+// One transition of `algo` for sample index `sample` of chain `chain` (Alg. 1's loop body).
+static int transition(int algo, const Target& t, const DRParams& dp, const NUTSParams& np, uint64_t seed,
+                      uint32_t chain, uint32_t sample, double* x, double* lp, double* g, int* depth) {
+  Stream s{seed, chain, sample};
+  *depth = 0;
+  if (algo == 0) return ess_transition(t, s, x, lp, nullptr, 0);
+  if (algo == 1) return dr_transition(t, s, dp, x, lp);
+  if (algo == 3) return sdr_transition(t, s, dp, x, lp);
+  return nuts_transition(t, s, np, x, lp, g, depth);
+}
+
+}  // extern "C"
+
+template <typename F>
+static void parallel_for(int64_t n, int n_threads, F work) {
+  int nt = std::max(1, std::min<int>(n_threads, (int)std::max<int64_t>(1, n)));
+  if (nt == 1) {
+    work(0, n);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int k = 0; k < nt; ++k) pool.emplace_back(work, n * k / nt, n * (k + 1) / nt);
+  for (auto& th : pool) th.join();
+}
+
+extern "C" {
+
 int ora_run(int algo, int kind, int d, int n_data, const double* params, const double* algo_params,
             int64_t chain0, int64_t n_chains, int64_t n_samples, const double* x0, uint64_t seed,
             int n_threads, double* samples, int32_t* counts, int32_t* aux, double* x_final) {
   if (d <= 0 || n_chains < 0 || n_samples < 0 || algo < 0 || algo > 3) return -1;
   Target t{kind, d, n_data, params};
   if (algo == 0 && t.prior_chol() == nullptr) return -1;
-  DRParams dp{3, 1.0, 0.5};
-  NUTSParams np{0.05, 10, 1000.0};
-  if (algo == 1 && algo_params) dp = DRParams{(int)algo_params[0], algo_params[1], algo_params[2]};
-  if (algo == 2 && algo_params) np = NUTSParams{algo_params[0], (int)algo_params[1], algo_params[2]};
-  if (algo == 3) dp = algo_params ? DRParams{(int)algo_params[0], algo_params[1], 1.0} : DRParams{100, 0.1, 1.0};
-  if (algo == 1 && (dp.n_stages < 1 || dp.n_stages > 3)) return -1;
-  if (algo == 3 && (dp.n_stages < 1 || dp.n_stages > 1000 || !(dp.scale0 > 0))) return -1;
-
-  auto work = [&](int64_t c_begin, int64_t c_end) {
+  DRParams dp;
+  NUTSParams np;
+  if (!sampler_params(algo, algo_params, &dp, &np)) return -1;
+  parallel_for(n_chains, n_threads, [&](int64_t c_begin, int64_t c_end) {
     std::vector<double> x(d), g(d);
     for (int64_t c = c_begin; c < c_end; ++c) {
       std::copy(x0 + c * d, x0 + (c + 1) * d, x.begin());
       double lp = t.logp(x.data(), algo == 2 ? g.data() : nullptr);
       for (int64_t i = 0; i < n_samples; ++i) {
-        Stream s{seed, (uint32_t)(chain0 + c), (uint32_t)i};
-        int n = 0, depth = 0;
-        if (algo == 0) n = ess_transition(t, s, x.data(), &lp, nullptr, 0);
-        else if (algo == 1) n = dr_transition(t, s, dp, x.data(), &lp);
-        else if (algo == 3) n = sdr_transition(t, s, dp, x.data(), &lp);
-        else n = nuts_transition(t, s, np, x.data(), &lp, g.data(), &depth);
+        int depth = 0;
+        const int n = transition(algo, t, dp, np, seed, (uint32_t)(chain0 + c), (uint32_t)i, x.data(), &lp,
+                                 g.data(), &depth);
         if (samples) std::copy(x.begin(), x.end(), samples + (c * n_samples + i) * d);
         if (counts) counts[c * n_samples + i] = n;
         if (aux) aux[c * n_samples + i] = depth;
       }
       if (x_final) std::copy(x.begin(), x.end(), x_final + c * d);
     }
-  };
-  int nt = std::max(1, std::min<int>(n_threads, (int)std::max<int64_t>(1, n_chains)));
-  if (nt == 1) {
-    work(0, n_chains);
-  } else {
-    std::vector<std::thread> pool;
-    for (int k = 0; k < nt; ++k) {
-      int64_t b = n_chains * k / nt, e = n_chains * (k + 1) / nt;
-      pool.emplace_back(work, b, e);
+  });
+  return 0;
+}
+
+// Independent single transitions: item i starts at x_in[i] as sample sample[i] of chain chain[i]
+// (the same random numbers as in a run) and writes the state it moves to.
+int ora_transitions(int algo, int kind, int d, int n_data, const double* params, const double* algo_params,
+                    int64_t n_items, const uint32_t* chain, const uint32_t* sample, const double* x_in,
+                    uint64_t seed, int n_threads, double* x_out, int32_t* counts, int32_t* aux) {
+  if (d <= 0 || n_items < 0 || algo < 0 || algo > 3) return -1;
+  Target t{kind, d, n_data, params};
+  if (algo == 0 && t.prior_chol() == nullptr) return -1;
+  DRParams dp;
+  NUTSParams np;
+  if (!sampler_params(algo, algo_params, &dp, &np)) return -1;
+  parallel_for(n_items, n_threads, [&](int64_t b, int64_t e) {
+    std::vector<double> x(d), g(d);
+    for (int64_t i = b; i < e; ++i) {
+      std::copy(x_in + i * d, x_in + (i + 1) * d, x.begin());
+      double lp = t.logp(x.data(), algo == 2 ? g.data() : nullptr);
+      int depth = 0;
+      const int n = transition(algo, t, dp, np, seed, chain[i], sample[i], x.data(), &lp, g.data(), &depth);
+      std::copy(x.begin(), x.end(), x_out + i * d);
+      counts[i] = n;
+      aux[i] = depth;
     }
-    for (auto& th : pool) th.join();
-  }
+  });
   return 0;
 }
 

@@ -72,6 +72,11 @@ def lib():
                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, dp,
                                   ctypes.c_uint64, ctypes.c_int, dp, ip, ip, dp]
             L.ora_run.restype = ctypes.c_int
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            L.ora_transitions.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
+                                          ctypes.c_int64, u32p, u32p, dp, ctypes.c_uint64, ctypes.c_int,
+                                          dp, ip, ip]
+            L.ora_transitions.restype = ctypes.c_int
             L.ora_R_hat.argtypes = [ip, ctypes.c_int64, ctypes.c_int64]
             L.ora_R_hat.restype = ctypes.c_double
             _lib = L
@@ -164,6 +169,29 @@ def run(algo, kind, params, x0, n_samples, seed, chain0=0, n_data=0, algo_params
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return {"samples": samples, "counts": counts, "aux": aux, "x_final": xf}
+
+
+def transitions(algo, kind, params, x_in, chains, samples, seed, n_data=0, algo_params=None,
+                n_threads=None):
+    """One transition per item: item i starts at x_in[i] as sample samples[i] of chain chains[i],
+    with the random numbers a run uses there.  Returns dict(x[k,d], counts[k], aux[k])."""
+    x_in = _f64(x_in)
+    k, d = x_in.shape
+    params = _params(params)
+    ap = None if algo_params is None else _f64(algo_params)
+    ch = np.ascontiguousarray(chains, dtype=np.uint32)
+    sm = np.ascontiguousarray(samples, dtype=np.uint32)
+    assert ch.shape == (k,) and sm.shape == (k,)
+    xo = np.zeros((k, d))
+    counts = np.zeros(k, dtype=np.int32)
+    aux = np.zeros(k, dtype=np.int32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    rc = lib().ora_transitions(ALGO[algo], TARGET[kind], d, n_data, _dp(params), _dp(ap), k,
+                               ch.ctypes.data_as(u32p), sm.ctypes.data_as(u32p), _dp(x_in), seed,
+                               n_threads or os.cpu_count() or 1, _dp(xo), _ip(counts), _ip(aux))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return {"x": xo, "counts": counts, "aux": aux}
 
 
 def R_hat(counts):

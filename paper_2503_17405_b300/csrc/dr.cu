@@ -67,6 +67,32 @@ __device__ __forceinline__ T full_logp(const TargetView<T>& tg, const T (&y)[E])
     for (int e = 0; e < E; ++e)
       if (e < d) { const T z = (y[e] - tg.vec[e]) / tg.vec2[e]; acc = fma(z, z, acc); }
     return -T(0.5) * acc;
+  } else if (tg.kind == TGT_MOG) {
+    // log sum_k w_k exp(-q_k / 2), q_k = s_k^2 c_par / d + |u_k|^2 c_perp with s_k = 1^T (y - mu_k)
+    // (summed from the differences) and u_k = y - mu_k - (s_k / d) 1 (the covariance's two
+    // eigenspaces)
+    const T inv_d = T(1) / T(d);
+    T lmax = neg_inf<T>(), wsum = T(0);
+    for (int k = 0; k < tg.n_data; ++k) {
+      const T* mk = tg.X + (size_t)k * d;
+      T sk = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e < d) sk += y[e] - mk[e];
+      const T mean = sk * inv_d;
+      T uu = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e < d) { const T u = y[e] - mk[e] - mean; uu = fma(u, u, uu); }
+      const T lk = tg.vec[k] - T(0.5) * fma(sk * mean, tg.c_par, uu * tg.c_perp);
+      if (lk > lmax) {
+        wsum = wsum * (sizeof(T) == 4 ? (T)expf((float)(lmax - lk)) : (T)exp((double)(lmax - lk))) + T(1);
+        lmax = lk;
+      } else {
+        wsum += sizeof(T) == 4 ? (T)expf((float)(lk - lmax)) : (T)exp((double)(lk - lmax));
+      }
+    }
+    return lmax + (sizeof(T) == 4 ? (T)logf((float)wsum) : (T)log((double)wsum));
   } else if (tg.kind == TGT_LOGREG) {
     T acc = T(0);
 #pragma unroll

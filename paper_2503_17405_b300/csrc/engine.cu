@@ -138,6 +138,7 @@ static bool target_layout(int kind, int d, int n_data, size_t* n_params, bool* n
     case FSMC_TGT_FUNNEL: *n_params = 0; return n_data == 0 && d >= 2;
     case FSMC_TGT_LOGREG: *n_params = (size_t)n_data * d + n_data; return n_data >= 1;
     case FSMC_TGT_GAUSS_DIAG: *n_params = 2 * (size_t)d; return n_data == 0;
+    case FSMC_TGT_MOG: *n_params = 1 + (size_t)n_data * (d + 1); return n_data >= 1 && n_data <= 64;
   }
   return false;
 }
@@ -191,6 +192,17 @@ static fsmc_status upload_target(fsmc_target* t, std::vector<void*>& bufs, Targe
       if ((st = up(p, d, &tv.vec))) return st;
       if ((st = up(p + d, d, &tv.vec2))) return st;
       break;
+    case FSMC_TGT_MOG: {
+      const int K = t->n_data;
+      const double rho = p[0];
+      std::vector<double> lw(K);
+      for (int k = 0; k < K; ++k) lw[k] = std::log(p[1 + k]);
+      if ((st = up(p + 1 + K, (size_t)K * d, &tv.X))) return st;
+      if ((st = up(lw.data(), K, &tv.vec))) return st;
+      tv.c_par = (T)(1.0 / (1.0 + (d - 1) * rho));
+      tv.c_perp = (T)(1.0 / (1.0 - rho));
+      break;
+    }
     default:
       break;
   }
@@ -207,6 +219,17 @@ extern "C" fsmc_status fsmc_target_create(fsmc_engine* e, fsmc_target_kind kind,
     return fsmc_fail(FSMC_EINVAL, "invalid target kind / d / n_data");
   if (n_params != need) return fsmc_fail(FSMC_EINVAL, "n_params does not match the target layout");
   if (need && !params_host) return fsmc_fail(FSMC_EINVAL, "params_host is NULL");
+  if (kind == FSMC_TGT_MOG) {
+    const double rho = params_host[0];
+    if (!(rho < 1.0) || (d > 1 && !(rho > -1.0 / (d - 1))))
+      return fsmc_fail(FSMC_EINVAL, "MOG needs -1/(d-1) < rho < 1");
+    for (int k = 0; k < n_data; ++k) {
+      const double wk = params_host[1 + k];
+      if (!(wk > 0.0) || !std::isfinite(wk)) return fsmc_fail(FSMC_EINVAL, "MOG weights must be positive");
+    }
+    for (size_t i = 1 + (size_t)n_data; i < need; ++i)
+      if (!std::isfinite(params_host[i])) return fsmc_fail(FSMC_EINVAL, "MOG means must be finite");
+  }
   if (kind == FSMC_TGT_GP_LOGIT)
     for (int k = 0; k < d; ++k) {
       const double s = params_host[(size_t)d * d + k];

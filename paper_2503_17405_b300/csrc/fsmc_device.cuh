@@ -182,7 +182,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
 
 // ---- device-side target view ---------------------------------------------------------------------
 enum TargetKind : int {
-  TGT_GAUSS_CONJ = 0, TGT_GP_LOGIT = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3, TGT_GAUSS_DIAG = 4, TGT_FLAT = 5
+  TGT_GAUSS_CONJ = 0, TGT_GP_LOGIT = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3, TGT_GAUSS_DIAG = 4, TGT_FLAT = 5,
+  TGT_MOG = 6
 };
 
 template <typename T>
@@ -191,12 +192,16 @@ struct TargetView {
   int d;
   int n_data;
   const T* L;     // ESS prior Cholesky [d][d] (lower)
-  const T* vec;   // y (GAUSS_CONJ), s (GP_LOGIT), mu (GAUSS_DIAG), y (LOGREG)
+  const T* vec;   // y (GAUSS_CONJ), s (GP_LOGIT), mu (GAUSS_DIAG), y (LOGREG), log w_k (MOG)
   const T* vec2;  // sigma (GAUSS_DIAG)
-  const T* X;     // LOGREG design matrix [n_data][d]
+  const T* X;     // LOGREG design matrix [n_data][d]; MOG means mu_k [n_data][d]
   const T* XT;    // LOGREG design matrix transposed, [d][n_pad] with zero rows >= n_data
   int n_pad;      // n_data rounded up to a multiple of 4
   T s2;           // GAUSS_CONJ noise variance
+  // MOG: S^-1 = c_par P + c_perp (I - P) with P = 1 1^T / d, so for v = x - mu_k
+  // v^T S^-1 v = (1^T v)^2 c_par / d + |v - (1^T v / d) 1|^2 c_perp
+  T c_par;        // 1 / (1 + (d - 1) rho): the principal eigenvalue's inverse
+  T c_perp;       // 1 / (1 - rho)
 };
 
 template <typename T>

@@ -108,6 +108,59 @@ __device__ T logp_grad(const TargetView<T>& tg, const T (&x)[E], T (&g)[E], int 
     if (lane == 0) g[0] = -v / T(9) - m1 / T(2) + T(0.5) * ev * ss;
     return -v * v / T(18) - m1 * v / T(2) - T(0.5) * ev * ss;
   }
+  if (tg.kind == TGT_MOG) {
+    // Mixture of K Gaussians with the shared equicorrelated covariance S (Sec. 7.3).  For
+    // component k, with v = x - mu_k split into its mean part s_k / d (s_k = 1^T v) and the
+    // residual u = v - (s_k / d) 1:  q_k = s_k^2 c_par / d + |u|^2 c_perp and
+    // S^-1 v = (s_k c_par / d) 1 + c_perp u.  s_k is summed from v itself, not as 1^T x - 1^T mu_k:
+    // the residual force c_perp u is ~1 / (1 - rho) times stiffer than the force along 1, so the
+    // rounding of a difference of two large sums would swamp the latter in single precision.
+    // log pi = logsumexp_k (log w_k - q_k / 2) and grad = -sum_k r_k S^-1 v_k are accumulated in
+    // one pass over the components, rescaled whenever the running maximum of the log-terms grows.
+    const int K = tg.n_data;
+    const T inv_d = T(1) / T(d);
+    T lmax = neg_inf<T>(), wsum = T(0), gacc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) gacc[e] = T(0);
+    for (int k = 0; k < K; ++k) {
+      const T* mk = tg.X + (size_t)k * d;
+      T v[E], sk = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = lane + 32 * e;
+        v[e] = i < d ? x[e] - mk[i] : T(0);
+        sk += v[e];
+      }
+      sk = group_sum<32>(sk);
+      const T mean = sk * inv_d;
+      T u[E], uu = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        u[e] = lane + 32 * e < d ? v[e] - mean : T(0);
+        uu = fma(u[e], u[e], uu);
+      }
+      uu = group_sum<32>(uu);  // the same bits in every lane: the branch below is warp-uniform
+      const T lk = tg.vec[k] - T(0.5) * fma(sk * mean, tg.c_par, uu * tg.c_perp);
+      const T gpar = mean * tg.c_par;
+      T wk = T(1);
+      if (lk > lmax) {
+        const T sc = t_exp(lmax - lk);  // 0 for the first component
+        wsum *= sc;
+#pragma unroll
+        for (int e = 0; e < E; ++e) gacc[e] *= sc;
+        lmax = lk;
+      } else {
+        wk = t_exp(lk - lmax);
+      }
+      wsum += wk;
+#pragma unroll
+      for (int e = 0; e < E; ++e) gacc[e] = fma(wk, fma(u[e], tg.c_perp, gpar), gacc[e]);
+    }
+    const T inv_w = T(1) / wsum;
+#pragma unroll
+    for (int e = 0; e < E; ++e) g[e] = lane + 32 * e < d ? -gacc[e] * inv_w : T(0);
+    return lmax + t_log(wsum);
+  }
   // TGT_LOGREG: eta = X theta row by row (lanes over rows), then grad = X^T r (lanes over
   // coordinates), 32 rows at a time through the warp's shared scratch.
   const int n = tg.n_data;
