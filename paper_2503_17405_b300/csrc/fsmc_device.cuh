@@ -141,6 +141,15 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask = 0xffffffffu) {
   return v;
 }
 
+// N independent group sums with their shuffles interleaved (each result has group_sum's bits).
+template <int G, int N, typename T>
+__device__ __forceinline__ void group_sum_n(T (&v)[N], unsigned mask = 0xffffffffu) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int n = 0; n < N; ++n) v[n] += __shfl_xor_sync(mask, v[n], o);
+}
+
 
 // ---- bounded grid barrier (cooperative launches only) ----------------------------------------
 // Sense-free generation barrier.  Every wait is bounded: after kBarrierSpinLimit polls the

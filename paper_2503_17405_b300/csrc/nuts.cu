@@ -115,46 +115,74 @@ __device__ T logp_grad(const TargetView<T>& tg, const T (&x)[E], T (&g)[E], int 
     // S^-1 v = (s_k c_par / d) 1 + c_perp u.  s_k is summed from v itself, not as 1^T x - 1^T mu_k:
     // the residual force c_perp u is ~1 / (1 - rho) times stiffer than the force along 1, so the
     // rounding of a difference of two large sums would swamp the latter in single precision.
-    // log pi = logsumexp_k (log w_k - q_k / 2) and grad = -sum_k r_k S^-1 v_k are accumulated in
-    // one pass over the components, rescaled whenever the running maximum of the log-terms grows.
+    // For the same reason the residual is re-centred once more: the roundings of v_i - mean leave
+    // 1^T u ~ sqrt(d) ulp, which c_perp would turn into a spurious force along 1 (errors of ~1e-4
+    // after 1000 single-precision leapfrog steps, ~1e-6 re-centred).
+    // log pi = logsumexp_k (log w_k - q_k / 2) and grad = -sum_k r_k S^-1 v_k are accumulated over
+    // the components, rescaled whenever the running maximum of the log-terms grows; KC components
+    // at a time have their three warp reductions interleaved.
+    constexpr int KC = 4;
     const int K = tg.n_data;
     const T inv_d = T(1) / T(d);
     T lmax = neg_inf<T>(), wsum = T(0), gacc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) gacc[e] = T(0);
-    for (int k = 0; k < K; ++k) {
-      const T* mk = tg.X + (size_t)k * d;
-      T v[E], sk = T(0);
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      T u[KC][E], sk[KC], mean[KC], su[KC], uu[KC];
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int i = lane + 32 * e;
-        v[e] = i < d ? x[e] - mk[i] : T(0);
-        sk += v[e];
+      for (int c = 0; c < KC; ++c) {
+        const bool live = k0 + c < K;
+        const T* mk = tg.X + (size_t)(live ? k0 + c : 0) * d;
+        sk[c] = T(0);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane + 32 * e;
+          u[c][e] = live && i < d ? x[e] - mk[i] : T(0);
+          sk[c] += u[c][e];
+        }
       }
-      sk = group_sum<32>(sk);
-      const T mean = sk * inv_d;
-      T u[E], uu = T(0);
+      group_sum_n<32, KC>(sk);
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        u[e] = lane + 32 * e < d ? v[e] - mean : T(0);
-        uu = fma(u[e], u[e], uu);
+      for (int c = 0; c < KC; ++c) {
+        mean[c] = sk[c] * inv_d;
+        su[c] = T(0);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (lane + 32 * e < d) u[c][e] -= mean[c];
+          su[c] += u[c][e];
+        }
       }
-      uu = group_sum<32>(uu);  // the same bits in every lane: the branch below is warp-uniform
-      const T lk = tg.vec[k] - T(0.5) * fma(sk * mean, tg.c_par, uu * tg.c_perp);
-      const T gpar = mean * tg.c_par;
-      T wk = T(1);
-      if (lk > lmax) {
-        const T sc = t_exp(lmax - lk);  // 0 for the first component
-        wsum *= sc;
+      group_sum_n<32, KC>(su);
 #pragma unroll
-        for (int e = 0; e < E; ++e) gacc[e] *= sc;
-        lmax = lk;
-      } else {
-        wk = t_exp(lk - lmax);
+      for (int c = 0; c < KC; ++c) {
+        const T du = su[c] * inv_d;
+        uu[c] = T(0);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (lane + 32 * e < d) u[c][e] -= du;
+          uu[c] = fma(u[c][e], u[c][e], uu[c]);
+        }
       }
-      wsum += wk;
+      group_sum_n<32, KC>(uu);  // the same bits in every lane: the branches below are warp-uniform
 #pragma unroll
-      for (int e = 0; e < E; ++e) gacc[e] = fma(wk, fma(u[e], tg.c_perp, gpar), gacc[e]);
+      for (int c = 0; c < KC; ++c) {
+        if (k0 + c >= K) break;
+        const T lk = tg.vec[k0 + c] - T(0.5) * fma(sk[c] * mean[c], tg.c_par, uu[c] * tg.c_perp);
+        const T gpar = mean[c] * tg.c_par;
+        T wk = T(1);
+        if (lk > lmax) {
+          const T sc = t_exp(lmax - lk);  // 0 for the first component
+          wsum *= sc;
+#pragma unroll
+          for (int e = 0; e < E; ++e) gacc[e] *= sc;
+          lmax = lk;
+        } else {
+          wk = t_exp(lk - lmax);
+        }
+        wsum += wk;
+#pragma unroll
+        for (int e = 0; e < E; ++e) gacc[e] = fma(wk, fma(u[c][e], tg.c_perp, gpar), gacc[e]);
+      }
     }
     const T inv_w = T(1) / wsum;
 #pragma unroll

@@ -92,8 +92,8 @@ def test_fp32_papers_mixture_transition_by_transition(eng):
     ok = same & (err <= FP32_TOL)
     print("fp32 mog transitions: %d of %d within %g with equal counts; max err of those %.3g; others: %s"
           % (ok.sum(), ok.size, FP32_TOL, err[ok].max(), np.sort(err[~ok])[-8:]))
-    assert ok.mean() >= 0.99
-    assert np.median(err[ok]) <= 1e-5
+    assert ok.mean() >= 0.995           # anything else is a near-tie decision taken the other way
+    assert err[ok].max() <= 2e-5
 
 
 def test_fp32_fsm_and_sync_agree(eng):
