@@ -72,7 +72,7 @@ std::vector<fsmc_tuning> candidates(fsmc_target* t, fsmc_algo algo, fsmc_precisi
     for (int steps : {64, 128, 256, 512})
       for (int threads : {64, 128, 256}) c.push_back(fsmc_tuning{1, steps, 0, threads, 0, 0, 0});
   } else {
-    for (int steps : {16, 32, 64}) c.push_back(fsmc_tuning{32, steps, 0, 128, 0, 0, 0});
+    for (int steps : {32, 128, 256}) c.push_back(fsmc_tuning{32, steps, 0, 128, 0, 0, 0});
   }
   return c;
 }

@@ -307,7 +307,9 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.threads_per_block) tu.threads_per_block = 128;
   } else {
     if (!tu.lanes_per_chain) tu.lanes_per_chain = 32;
-    if (!tu.steps_per_launch) tu.steps_per_launch = 32;
+    // leapfrog steps per launch: enough that a launch's tail (its slowest warp) and the launch
+    // gaps stay small against its length; cheap log-densities take more
+    if (!tu.steps_per_launch) tu.steps_per_launch = j->tg->kind == FSMC_TGT_LOGREG ? 128 : 256;
     if (!tu.threads_per_block) tu.threads_per_block = 128;
   }
 }

@@ -50,16 +50,17 @@ struct NutsView : ChainsView<T> {
 };
 
 template <typename T>
-__device__ __forceinline__ T t_exp(T a) { if constexpr (sizeof(T) == 4) return expf(a); else return exp(a); }
+__device__ __forceinline__ T t_exp(T a) { if constexpr (sizeof(T) == 4) return __expf(a); else return exp(a); }
 template <typename T>
-__device__ __forceinline__ T t_log(T a) { if constexpr (sizeof(T) == 4) return logf(a); else return log(a); }
+__device__ __forceinline__ T t_log(T a) { if constexpr (sizeof(T) == 4) return __logf(a); else return log(a); }
 
 template <typename T>
 __device__ __forceinline__ T logaddexp(T a, T b) {
   if (a == neg_inf<T>()) return b;
   if (b == neg_inf<T>()) return a;
   const T m = a > b ? a : b;
-  return m + t_log(t_exp(a - m) + t_exp(b - m));
+  if constexpr (sizeof(T) == 4) return m + __logf(1.f + __expf(-fabsf(a - b)));
+  else return m + log(exp(a - m) + exp(b - m));
 }
 
 template <typename T, int E>
@@ -68,6 +69,77 @@ __device__ __forceinline__ T wdot(const T (&a)[E], const T (&b)[E]) {
 #pragma unroll
   for (int e = 0; e < E; ++e) s = fma(a[e], b[e], s);  // padded coordinates hold 0
   return group_sum<32>(s);
+}
+
+// Mixture of K Gaussians with the shared equicorrelated covariance S (Sec. 7.3), one chain per
+// warp.  For component k, with v = x - mu_k split into its mean part s_k / d (s_k = 1^T v) and the
+// residual u = v - (s_k / d) 1:  q_k = s_k^2 c_par / d + |u|^2 c_perp and
+// S^-1 v = (s_k c_par / d) 1 + c_perp u.  s_k is summed from v itself, not as 1^T x - 1^T mu_k:
+// the residual force c_perp u is ~1 / (1 - rho) times stiffer than the force along 1, so the
+// rounding of a difference of two large sums would swamp the latter in single precision.  For
+// the same reason the residual is re-centred once more: the roundings of v_i - mean leave
+// 1^T u ~ sqrt(d) ulp, which c_perp would turn into a spurious force along 1 (errors of ~1e-4
+// after 1000 single-precision leapfrog steps, ~1e-6 re-centred).
+// log pi = logsumexp_k (log w_k - q_k / 2) and grad = -sum_k r_k S^-1 v_k are accumulated over
+// the components, rescaled whenever the running maximum of the log-terms grows.  This adds the
+// KC components k0 .. k0 + KC - 1, their three warp reductions interleaved.
+template <typename T, int E, int KC>
+__device__ __forceinline__ void mog_terms(const TargetView<T>& tg, const T (&x)[E], int k0, int lane, T inv_d,
+                                          T& lmax, T& wsum, T (&gacc)[E]) {
+  const int d = tg.d;
+  T u[KC][E], sk[KC], mean[KC], su[KC], uu[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const T* mk = tg.X + (size_t)(k0 + c) * d;
+    sk[c] = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = lane + 32 * e;
+      u[c][e] = i < d ? x[e] - mk[i] : T(0);
+      sk[c] += u[c][e];
+    }
+  }
+  group_sum_n<32, KC>(sk);
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    mean[c] = sk[c] * inv_d;
+    su[c] = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (lane + 32 * e < d) u[c][e] -= mean[c];
+      su[c] += u[c][e];
+    }
+  }
+  group_sum_n<32, KC>(su);
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const T du = su[c] * inv_d;
+    uu[c] = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (lane + 32 * e < d) u[c][e] -= du;
+      uu[c] = fma(u[c][e], u[c][e], uu[c]);
+    }
+  }
+  group_sum_n<32, KC>(uu);  // the same bits in every lane: the branches below are warp-uniform
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const T lk = tg.vec[k0 + c] - T(0.5) * fma(sk[c] * mean[c], tg.c_par, uu[c] * tg.c_perp);
+    const T gpar = mean[c] * tg.c_par;
+    T wk = T(1);
+    if (lk > lmax) {
+      const T sc = t_exp(lmax - lk);  // 0 for the first component
+      wsum *= sc;
+#pragma unroll
+      for (int e = 0; e < E; ++e) gacc[e] *= sc;
+      lmax = lk;
+    } else {
+      wk = t_exp(lk - lmax);
+    }
+    wsum += wk;
+#pragma unroll
+    for (int e = 0; e < E; ++e) gacc[e] = fma(wk, fma(u[c][e], tg.c_perp, gpar), gacc[e]);
+  }
 }
 
 // log pi(x) and its gradient, one chain per warp.  wsm: this warp's shared scratch.
@@ -109,80 +181,18 @@ __device__ T logp_grad(const TargetView<T>& tg, const T (&x)[E], T (&g)[E], int 
     return -v * v / T(18) - m1 * v / T(2) - T(0.5) * ev * ss;
   }
   if (tg.kind == TGT_MOG) {
-    // Mixture of K Gaussians with the shared equicorrelated covariance S (Sec. 7.3).  For
-    // component k, with v = x - mu_k split into its mean part s_k / d (s_k = 1^T v) and the
-    // residual u = v - (s_k / d) 1:  q_k = s_k^2 c_par / d + |u|^2 c_perp and
-    // S^-1 v = (s_k c_par / d) 1 + c_perp u.  s_k is summed from v itself, not as 1^T x - 1^T mu_k:
-    // the residual force c_perp u is ~1 / (1 - rho) times stiffer than the force along 1, so the
-    // rounding of a difference of two large sums would swamp the latter in single precision.
-    // For the same reason the residual is re-centred once more: the roundings of v_i - mean leave
-    // 1^T u ~ sqrt(d) ulp, which c_perp would turn into a spurious force along 1 (errors of ~1e-4
-    // after 1000 single-precision leapfrog steps, ~1e-6 re-centred).
-    // log pi = logsumexp_k (log w_k - q_k / 2) and grad = -sum_k r_k S^-1 v_k are accumulated over
-    // the components, rescaled whenever the running maximum of the log-terms grows; KC components
-    // at a time have their three warp reductions interleaved.
-    constexpr int KC = 4;
     const int K = tg.n_data;
     const T inv_d = T(1) / T(d);
     T lmax = neg_inf<T>(), wsum = T(0), gacc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) gacc[e] = T(0);
-    for (int k0 = 0; k0 < K; k0 += KC) {
-      T u[KC][E], sk[KC], mean[KC], su[KC], uu[KC];
-#pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        const bool live = k0 + c < K;
-        const T* mk = tg.X + (size_t)(live ? k0 + c : 0) * d;
-        sk[c] = T(0);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = lane + 32 * e;
-          u[c][e] = live && i < d ? x[e] - mk[i] : T(0);
-          sk[c] += u[c][e];
-        }
-      }
-      group_sum_n<32, KC>(sk);
-#pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        mean[c] = sk[c] * inv_d;
-        su[c] = T(0);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          if (lane + 32 * e < d) u[c][e] -= mean[c];
-          su[c] += u[c][e];
-        }
-      }
-      group_sum_n<32, KC>(su);
-#pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        const T du = su[c] * inv_d;
-        uu[c] = T(0);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          if (lane + 32 * e < d) u[c][e] -= du;
-          uu[c] = fma(u[c][e], u[c][e], uu[c]);
-        }
-      }
-      group_sum_n<32, KC>(uu);  // the same bits in every lane: the branches below are warp-uniform
-#pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        if (k0 + c >= K) break;
-        const T lk = tg.vec[k0 + c] - T(0.5) * fma(sk[c] * mean[c], tg.c_par, uu[c] * tg.c_perp);
-        const T gpar = mean[c] * tg.c_par;
-        T wk = T(1);
-        if (lk > lmax) {
-          const T sc = t_exp(lmax - lk);  // 0 for the first component
-          wsum *= sc;
-#pragma unroll
-          for (int e = 0; e < E; ++e) gacc[e] *= sc;
-          lmax = lk;
-        } else {
-          wk = t_exp(lk - lmax);
-        }
-        wsum += wk;
-#pragma unroll
-        for (int e = 0; e < E; ++e) gacc[e] = fma(wk, fma(u[c][e], tg.c_perp, gpar), gacc[e]);
-      }
+    int k0 = 0;
+    for (; k0 + 4 <= K; k0 += 4) mog_terms<T, E, 4>(tg, x, k0, lane, inv_d, lmax, wsum, gacc);
+    switch (K - k0) {
+      case 3: mog_terms<T, E, 3>(tg, x, k0, lane, inv_d, lmax, wsum, gacc); break;
+      case 2: mog_terms<T, E, 2>(tg, x, k0, lane, inv_d, lmax, wsum, gacc); break;
+      case 1: mog_terms<T, E, 1>(tg, x, k0, lane, inv_d, lmax, wsum, gacc); break;
+      default: break;
     }
     const T inv_w = T(1) / wsum;
 #pragma unroll
