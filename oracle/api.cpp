@@ -85,12 +85,20 @@ static bool sampler_params(int algo, const double* algo_params, DRParams* dp, NU
   return true;
 }
 
+static bool slice_params(int algo, const double* algo_params, SliceParams* sp) {
+  *sp = SliceParams{1.0, 100};
+  if (algo == 4 && algo_params) *sp = SliceParams{algo_params[0], (int)algo_params[1]};
+  return algo != 4 || (sp->w > 0 && sp->m >= 1 && sp->m <= 1000000);
+}
+
 // One transition of `algo` for sample index `sample` of chain `chain` (Alg. 1's loop body).
-static int transition(int algo, const Target& t, const DRParams& dp, const NUTSParams& np, uint64_t seed,
-                      uint32_t chain, uint32_t sample, double* x, double* lp, double* g, int* depth) {
+static int transition(int algo, const Target& t, const DRParams& dp, const NUTSParams& np,
+                      const SliceParams& sp, uint64_t seed, uint32_t chain, uint32_t sample, double* x,
+                      double* lp, double* g, int* depth) {
   Stream s{seed, chain, sample};
   *depth = 0;
   if (algo == 0) return ess_transition(t, s, x, lp, nullptr, 0);
+  if (algo == 4) return slice_transition(t, s, sp, x, lp, depth);
   if (algo == 1) return dr_transition(t, s, dp, x, lp);
   if (algo == 3) return sdr_transition(t, s, dp, x, lp);
   return nuts_transition(t, s, np, x, lp, g, depth);
@@ -115,12 +123,13 @@ extern "C" {
 int ora_run(int algo, int kind, int d, int n_data, const double* params, const double* algo_params,
             int64_t chain0, int64_t n_chains, int64_t n_samples, const double* x0, uint64_t seed,
             int n_threads, double* samples, int32_t* counts, int32_t* aux, double* x_final) {
-  if (d <= 0 || n_chains < 0 || n_samples < 0 || algo < 0 || algo > 3) return -1;
+  if (d <= 0 || n_chains < 0 || n_samples < 0 || algo < 0 || algo > 4) return -1;
   Target t{kind, d, n_data, params};
   if (algo == 0 && t.prior_chol() == nullptr) return -1;
   DRParams dp;
   NUTSParams np;
-  if (!sampler_params(algo, algo_params, &dp, &np)) return -1;
+  SliceParams sp;
+  if (!sampler_params(algo, algo_params, &dp, &np) || !slice_params(algo, algo_params, &sp)) return -1;
   parallel_for(n_chains, n_threads, [&](int64_t c_begin, int64_t c_end) {
     std::vector<double> x(d), g(d);
     for (int64_t c = c_begin; c < c_end; ++c) {
@@ -128,7 +137,7 @@ int ora_run(int algo, int kind, int d, int n_data, const double* params, const d
       double lp = t.logp(x.data(), algo == 2 ? g.data() : nullptr);
       for (int64_t i = 0; i < n_samples; ++i) {
         int depth = 0;
-        const int n = transition(algo, t, dp, np, seed, (uint32_t)(chain0 + c), (uint32_t)i, x.data(), &lp,
+        const int n = transition(algo, t, dp, np, sp, seed, (uint32_t)(chain0 + c), (uint32_t)i, x.data(), &lp,
                                  g.data(), &depth);
         if (samples) std::copy(x.begin(), x.end(), samples + (c * n_samples + i) * d);
         if (counts) counts[c * n_samples + i] = n;
@@ -145,19 +154,20 @@ int ora_run(int algo, int kind, int d, int n_data, const double* params, const d
 int ora_transitions(int algo, int kind, int d, int n_data, const double* params, const double* algo_params,
                     int64_t n_items, const uint32_t* chain, const uint32_t* sample, const double* x_in,
                     uint64_t seed, int n_threads, double* x_out, int32_t* counts, int32_t* aux) {
-  if (d <= 0 || n_items < 0 || algo < 0 || algo > 3) return -1;
+  if (d <= 0 || n_items < 0 || algo < 0 || algo > 4) return -1;
   Target t{kind, d, n_data, params};
   if (algo == 0 && t.prior_chol() == nullptr) return -1;
   DRParams dp;
   NUTSParams np;
-  if (!sampler_params(algo, algo_params, &dp, &np)) return -1;
+  SliceParams sp;
+  if (!sampler_params(algo, algo_params, &dp, &np) || !slice_params(algo, algo_params, &sp)) return -1;
   parallel_for(n_items, n_threads, [&](int64_t b, int64_t e) {
     std::vector<double> x(d), g(d);
     for (int64_t i = b; i < e; ++i) {
       std::copy(x_in + i * d, x_in + (i + 1) * d, x.begin());
       double lp = t.logp(x.data(), algo == 2 ? g.data() : nullptr);
       int depth = 0;
-      const int n = transition(algo, t, dp, np, seed, chain[i], sample[i], x.data(), &lp, g.data(), &depth);
+      const int n = transition(algo, t, dp, np, sp, seed, chain[i], sample[i], x.data(), &lp, g.data(), &depth);
       std::copy(x.begin(), x.end(), x_out + i * d);
       counts[i] = n;
       aux[i] = depth;

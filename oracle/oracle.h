@@ -99,6 +99,15 @@ int sdr_transition(const Target& t, const Stream& s, const DRParams& p, double* 
 // log alpha_k = min(0, log [(pi(y_k) - pi*)+ / (pi(x) - pi*)]), pi* = max over rejected tries
 double sdr_log_alpha(double lp_x, double lp_star, double lp_y);
 
+// Slice sampling (Neal 2003) along a random direction: stepping-out with the expansion limit m
+// split into J = floor(m V) left and K = m - 1 - J right steps of width w, then shrinkage
+// (Fig. 2's slice sampler: an expansion loop followed by a shrink loop).  x[d] in/out, *lp in/out
+// caches log pi(x).  Returns the number of log-density evaluations N (expansion checks plus
+// proposals); *n_prop receives the number of proposals (>= 1).
+struct SliceParams { double w; int m; };
+int slice_transition(const Target& t, const Stream& s, const SliceParams& p, double* x, double* lp,
+                     int* n_prop);
+
 // Multinomial NUTS with momentum-sum U-turn criterion.  x[d] in/out,
 // *lp in/out caches log pi(x), grad[d] in/out caches its gradient.
 // Returns the number of leapfrog steps; *depth receives the number of doublings.

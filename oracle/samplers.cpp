@@ -179,6 +179,74 @@ double sdr_log_alpha(double lp_x, double lp_star, double lp_y) {
   return std::min(0.0, num - den);
 }
 
+// ------------------------------------------------------------------------------------
+// Slice sampling (Neal 2003, stepping-out and shrinkage procedures) on the line through x with
+// a random direction u (hit-and-run; for d = 1, u = +-1), with these readings:
+//  * "inside the slice" is log pi > log y (strict), as for ESS; an end or a proposal exactly on
+//    the threshold counts as outside;
+//  * the stepping-out loop is Neal's with the limit m: J = floor(m V') steps at most to the
+//    left, K = m - 1 - J to the right, the left end expanded before the right one;
+//  * N counts log-density evaluations: an end is evaluated only while its step budget is
+//    positive, and every proposal is one evaluation.
+// Random numbers for sample i (tag 0):
+//   draws 0..D-1       : z, u = z / |z|
+//   draw D, words 0-1  : U for the threshold log y = log pi(x) + log U
+//   draw D, words 2-3  : V for the initial interval L = -w V, R = L + w (in units along u)
+//   draw D+1, words 0-1: V' for the limit split J = floor(m V'), K = m - 1 - J
+//   draw D+2+s         : U_s for proposal s, theta = L + (R - L) U_s
+int slice_transition(const Target& t, const Stream& s, const SliceParams& P, double* x, double* lp,
+                     int* n_prop) {
+  const int d = t.d;
+  const int D = normal_blocks(d);
+  std::vector<double> u(d), xp(d);
+  normals(s, 0, 0, d, u.data());
+  double nrm = 0;
+  for (int k = 0; k < d; ++k) nrm += u[k] * u[k];
+  nrm = std::sqrt(nrm);
+  for (int k = 0; k < d; ++k) u[k] /= nrm;
+  auto at = [&](double th) {
+    for (int k = 0; k < d; ++k) xp[k] = x[k] + th * u[k];
+    return t.logp(xp.data(), nullptr);
+  };
+  const Block b = s.block(0, (uint32_t)D);
+  const double log_y = *lp + std::log(uniform(b.w[0], b.w[1]));
+  double L = -P.w * uniform(b.w[2], b.w[3]);
+  double R = L + P.w;
+  const Block bj = s.block(0, (uint32_t)(D + 1));
+  int J = (int)std::floor(P.m * uniform(bj.w[0], bj.w[1]));
+  int K = (P.m - 1) - J;
+  int n = 0;
+  // stepping out
+  while (J > 0) {
+    ++n;
+    if (!(at(L) > log_y)) break;
+    L -= P.w;
+    --J;
+  }
+  while (K > 0) {
+    ++n;
+    if (!(at(R) > log_y)) break;
+    R += P.w;
+    --K;
+  }
+  // shrinkage
+  for (int p = 0; p < kMaxShrinks; ++p) {
+    const Block bs = s.block(0, (uint32_t)(D + 2 + p));
+    const double th = L + (R - L) * uniform(bs.w[0], bs.w[1]);
+    const double lpp = at(th);
+    ++n;
+    if (lpp > log_y) {
+      std::copy(xp.begin(), xp.end(), x);
+      *lp = lpp;
+      *n_prop = p + 1;
+      return n;
+    }
+    if (th < 0) L = th; else R = th;
+  }
+  *n_prop = kMaxShrinks;  // keep x (never happens in double precision)
+  return n;
+}
+
 int sdr_transition(const Target& t, const Stream& s, const DRParams& P, double* x, double* lp) {
   const int d = t.d;
   const int D = normal_blocks(d);
