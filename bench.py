@@ -80,6 +80,13 @@ def _make_config(name, scale):
         return dict(name="sdr_std_normal_d1_M100_m65536_n2000", algo="dr", w=w, m=m, n=n, prec="fp32",
                     x0=W.x0_gauss_diag_exact(w, m), algo_params=[100, 0.1, 1.0], dr_symmetric=1,
                     oracle_algo="sdr", oracle_params=[100, 0.1])
+    if name == "slice_funnel":
+        # Fig. 2's slice sampler (stepping out, then shrinkage) on the 10-d funnel: interval
+        # widths needed range over orders of magnitude, so both loops' counts are heavy-tailed
+        w = W.funnel(10)
+        m, n = int(65536 * scale), 2000
+        return dict(name="slice_funnel_d10_w1_m100_m65536_n2000", algo="slice", w=w, m=m, n=n, prec="fp32",
+                    x0=W.x0_funnel_exact(m), algo_params=[1.0, 100])
     if name == "nuts_mog":
         # Sec. 7.3: NUTS on the 100-d mixture of Gaussians with correlation 0.99, modes at
         # -10 * 1, 0, 10 * 1, identity mass, step 0.044 (acceptance statistic ~0.87), depth <= 10
@@ -208,9 +215,10 @@ def run_ours(args, rank, world):
         dr = dict(zip(["n_stages", "scale0", "factor"], cfg["algo_params"]), symmetric=cfg.get("dr_symmetric", 0))
     if cfg["algo"] == "nuts":
         nuts = dict(zip(["eps", "max_depth", "max_dH"], cfg["algo_params"]))
+    sl = dict(zip(["w", "m"], cfg["algo_params"])) if cfg["algo"] == "slice" else None
     tuning = {"profile_kernels": 1, **parse_tuning(args.tuning)}
     job = eng.job(tg, cfg["algo"], m, n, x0=cfg["x0"], seed=1 + rank, prec=cfg["prec"], store=True,
-                  dr=dr, nuts=nuts, tuning=tuning)
+                  dr=dr, nuts=nuts, tuning=tuning, slice=sl)
     stream = torch.cuda.Stream()          # a real stream: graph capture needs one
     torch.cuda.set_stream(stream)
     sp = stream.cuda_stream
@@ -313,9 +321,11 @@ def run_ours(args, rank, world):
             # logistic regression: 4 n d; mixture: (7 K + 1) d (residual, its square, the gradient)
             per = 4 * w["n_data"] * d if w["kind"] == "logreg" else (7 * w["n_data"] + 1) * d
         else:
+            # DR: d normals' Box-Muller and the density (~20 d); slice: the point x + theta u and
+            # the density (about the same)
             per = 20 * d
         achieved = steps_total * per / (kms_own[1] / 1e3) / 1e12 if kms_own[1] else None
-        kname = {"ess": "ess_fsm_kernel", "dr": "dr_fsm_kernel",
+        kname = {"ess": "ess_fsm_kernel", "dr": "dr_fsm_kernel", "slice": "slice_fsm_kernel",
                  "nuts": "nuts_fsm_batched_kernel" if w["kind"] == "logreg" else "nuts_fsm_kernel"}[cfg["algo"]]
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s",
@@ -324,6 +334,7 @@ def run_ours(args, rank, world):
                 "flops_per_step": per,
                 "limiter": {"ess": "instruction issue (~190 warp instructions per state; 2 MUFU per coordinate)",
                             "dr": "latency: one chain per thread, ~14 resident warps per SM at 65536 chains",
+                            "slice": "latency: one chain per thread, 65536 chains",
                             "nuts": "latency and occupancy of the block-batched gradient" if w["kind"] == "logreg"
                             else "latency: one chain per warp, shuffle reductions per component and U-turn test"}[cfg["algo"]]}
 
@@ -336,7 +347,7 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         tg2 = eng.target(w["kind"], w["d"], params_h.numpy(), n_data=w["n_data"])
         job2 = eng.job(tg2, cfg["algo"], m, n, x0=x0_h.numpy(), seed=1 + rank, prec=cfg["prec"],
-                       store=True, dr=dr, nuts=nuts, tuning=parse_tuning(args.tuning) or None)
+                       store=True, dr=dr, nuts=nuts, tuning=parse_tuning(args.tuning) or None, slice=sl)
         job2.run("fsm", stream=sp)
         sx, sx2, nk = job2.moments()
         t1 = time.perf_counter()

@@ -77,7 +77,7 @@ typedef enum fsmc_target_kind {
   FSMC_TGT_MOG = 6
 } fsmc_target_kind;
 
-typedef enum fsmc_algo { FSMC_ESS = 0, FSMC_DR = 1, FSMC_NUTS = 2 } fsmc_algo;
+typedef enum fsmc_algo { FSMC_ESS = 0, FSMC_DR = 1, FSMC_NUTS = 2, FSMC_SLICE = 3 } fsmc_algo;
 
 /* FP64: every floating-point operation in double.  FP32: the production mode, single
  * precision throughout (see fsmc_job_create). */
@@ -96,6 +96,15 @@ typedef struct fsmc_dr_params {
                     accepted with min(1, (pi(y_k) - pi*)+ / (pi(x) - pi*)), pi* the largest
                     target value among the rejected tries                                    */
 } fsmc_dr_params;
+
+/* Slice sampling (Neal 2003; Fig. 2's slice sampler) on a random line through x: stepping out
+ * from an interval of width w placed uniformly around x, at most m - 1 steps in all (Neal's
+ * limit, split J = floor(m V) left, m - 1 - J right), then shrinkage.  N_ij counts log-density
+ * evaluations (end checks and proposals); the aux output counts proposals. */
+typedef struct fsmc_slice_params {
+  double w; /* > 0 */
+  int m;    /* 1..1000000 */
+} fsmc_slice_params;
 
 /* NUTS: leapfrog step eps, at most max_depth doublings, divergence when H - H0 > max_dH. */
 typedef struct fsmc_nuts_params {
@@ -167,7 +176,8 @@ void fsmc_target_destroy(fsmc_target* t);
 
 /* ---- jobs ------------------------------------------------------------------------------
  * m = n_chains chains of `algo` on target t, n_samples samples each (Alg. 3 / Alg. 7).
- * algo_params: NULL for ESS, const fsmc_dr_params* for DR, const fsmc_nuts_params* for NUTS.
+ * algo_params: NULL for ESS, const fsmc_dr_params* for DR, const fsmc_nuts_params* for NUTS,
+ * const fsmc_slice_params* for SLICE (NULL: w = 1, m = 100).  DR and SLICE: d <= 32.
  * x0_host: [n_chains][d] starting points (NULL = zeros).  seed keys the random numbers:
  * chain j, sample i, draw q use Philox4x32-10 with key (j, seed_lo) and counter
  * (q, i, tag, seed_hi).  store_samples: 1 keeps every sample on the device
@@ -217,8 +227,9 @@ fsmc_status fsmc_read_samples_dev(fsmc_job* j, int64_t chain0, int64_t n_chains,
                                   int64_t sample0, int64_t n_samp, void* dst_dev,
                                   void* cuda_stream);
 /* counts_host [n_chains][n_samples]: loop-body count N_ij (ESS shrinks, DR stages tried,
- * NUTS leapfrog steps); -1 where not yet sampled.  aux_host (nullable) [n_chains][n_samples]:
- * NUTS tree depth.  fsm_steps_host (nullable) [n_chains]: states executed per chain. */
+ * NUTS leapfrog steps, slice-sampling log-density evaluations); -1 where not yet sampled.
+ * aux_host (nullable) [n_chains][n_samples]: NUTS tree depth, slice-sampling proposals (0
+ * for ESS and DR).  fsm_steps_host (nullable) [n_chains]: states executed per chain. */
 fsmc_status fsmc_read_loop_counts(fsmc_job* j, int32_t* counts_host, int32_t* aux_host,
                                   int64_t* fsm_steps_host);
 /* Current state x of every chain, [n_chains][d]. */

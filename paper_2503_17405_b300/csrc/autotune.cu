@@ -68,7 +68,7 @@ std::vector<fsmc_tuning> candidates(fsmc_target* t, fsmc_algo algo, fsmc_precisi
           for (int gen : gens)
             for (int threads : (G == 1 ? std::vector<int>{128, 256} : std::vector<int>{256}))
               c.push_back(fsmc_tuning{G, steps, ring, threads, 0, gen, 0});
-  } else if (algo == FSMC_DR) {
+  } else if (algo == FSMC_DR || algo == FSMC_SLICE) {
     for (int steps : {64, 128, 256, 512})
       for (int threads : {64, 128, 256}) c.push_back(fsmc_tuning{1, steps, 0, threads, 0, 0, 0});
   } else {

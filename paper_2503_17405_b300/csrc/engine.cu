@@ -301,7 +301,7 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.threads_per_block) tu.threads_per_block = 256;
     if (!tu.generator) tu.generator = (j->prec == FSMC_FP32 && j->d <= 256) ? 2 : 1;
     if (!tu.pipelined) tu.pipelined = 1;
-  } else if (j->algo == FSMC_DR) {
+  } else if (j->algo == FSMC_DR || j->algo == FSMC_SLICE) {
     tu.lanes_per_chain = 1;
     if (!tu.steps_per_launch) tu.steps_per_launch = 256;
     if (!tu.threads_per_block) tu.threads_per_block = 128;
@@ -347,6 +347,13 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
     j->o_y = L.take(3 * m * d * es);  // y1, y2 and (4-state ablation form) the current proposal
     j->o_lpy = L.take(4 * m * es);    // log pi(y1), log pi(y2), current proposal's and its ratio
     j->o_k = L.take(m * 4);
+  } else if (j->algo == FSMC_SLICE) {
+    j->o_ell = L.take(m * es);        // log pi(x)
+    j->o_logy = L.take(m * es);
+    j->o_th = L.take(3 * m * es);     // L, R, theta
+    j->o_y = L.take(m * d * es);      // direction u
+    j->o_k = L.take(5 * m * 4);       // state, J, K, proposals, evaluations
+    j->o_aux = L.take(m * n * 4);
   } else {
     nuts_layout(j, L.off);
   }
@@ -437,6 +444,29 @@ DrView<T> dr_view(const fsmc_job* j) {
 }
 
 template <typename T>
+SliceView<T> slice_view(const fsmc_job* j) {
+  SliceView<T> v;
+  fill_chains<T>(j, v);
+  char* b = j->dev;
+  v.tg = target_view<T>(j->tg);
+  v.w = (T)j->slice.w;
+  v.mlim = j->slice.m;
+  v.lp = (T*)(b + j->o_ell);
+  v.logy = (T*)(b + j->o_logy);
+  v.L = (T*)(b + j->o_th);
+  v.R = v.L + j->m;
+  v.th = v.L + 2 * j->m;
+  v.u = (T*)(b + j->o_y);
+  v.k = (int*)(b + j->o_k);
+  v.J = v.k + j->m;
+  v.K = v.k + 2 * j->m;
+  v.s = v.k + 3 * j->m;
+  v.nev = v.k + 4 * j->m;
+  v.aux = (int*)(b + j->o_aux);
+  return v;
+}
+
+template <typename T>
 static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
   char* b = j->dev;
   const size_t m = (size_t)j->m, d = (size_t)j->d;
@@ -466,6 +496,11 @@ static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
     CK(cudaMemsetAsync(b + j->o_y, 0, 3 * m * d * sizeof(T), st));
     CK(cudaMemsetAsync(b + j->o_lpy, 0, 4 * m * sizeof(T), st));
     CK(launch_dr_init<T>(dr_view<T>(j), st));
+  } else if (j->algo == FSMC_SLICE) {
+    CK(cudaMemsetAsync(b + j->o_k, 0, 5 * m * 4, st));
+    CK(cudaMemsetAsync(b + j->o_th, 0, 3 * m * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_aux, 0xff, m * (size_t)j->n * 4, st));
+    CK(launch_slice_init<T>(slice_view<T>(j), st));
   } else {
     fsmc_status s = nuts_init_state(j, st);
     if (s != FSMC_OK) return s;
@@ -491,10 +526,12 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
   const bool ess_kind = t->kind == FSMC_TGT_GAUSS_CONJ || t->kind == FSMC_TGT_GP_LOGIT ||
                         t->kind == FSMC_TGT_FLAT;
   if (algo == FSMC_ESS && !ess_kind) return fsmc_fail(FSMC_EINVAL, "ESS needs a target with a Gaussian prior factor");
-  if ((algo == FSMC_DR || algo == FSMC_NUTS) && ess_kind)
-    return fsmc_fail(FSMC_EINVAL, "DR / NUTS need a full log-density target");
-  if (algo != FSMC_ESS && algo != FSMC_DR && algo != FSMC_NUTS) return fsmc_fail(FSMC_EINVAL, "bad algo");
+  if ((algo == FSMC_DR || algo == FSMC_NUTS || algo == FSMC_SLICE) && ess_kind)
+    return fsmc_fail(FSMC_EINVAL, "DR / NUTS / slice sampling need a full log-density target");
+  if (algo != FSMC_ESS && algo != FSMC_DR && algo != FSMC_NUTS && algo != FSMC_SLICE)
+    return fsmc_fail(FSMC_EINVAL, "bad algo");
   if (algo == FSMC_DR && t->d > 32) return fsmc_fail(FSMC_EINVAL, "DR supports d <= 32");
+  if (algo == FSMC_SLICE && t->d > 32) return fsmc_fail(FSMC_EINVAL, "slice sampling supports d <= 32");
   auto* j = new (std::nothrow) fsmc_job();
   if (!j) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");
   j->e = e;
@@ -513,6 +550,13 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
         !(j->dr.symmetric || j->dr.factor > 0) || (j->dr.symmetric != 0 && j->dr.symmetric != 1)) {
       delete j;
       return fsmc_fail(FSMC_EINVAL, "DR params: 1..3 stages (symmetric: 1..1000 tries), positive scales");
+    }
+  }
+  if (algo == FSMC_SLICE) {
+    j->slice = algo_params ? *(const fsmc_slice_params*)algo_params : fsmc_slice_params{1.0, 100};
+    if (!(j->slice.w > 0) || !std::isfinite(j->slice.w) || j->slice.m < 1 || j->slice.m > 1000000) {
+      delete j;
+      return fsmc_fail(FSMC_EINVAL, "slice params: w > 0, 1 <= m <= 1000000");
     }
   }
   if (algo == FSMC_NUTS) {
@@ -550,7 +594,8 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 8 && t.lanes_per_chain != 16 &&
       t.lanes_per_chain != 32)
     return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1, 8, 16 or 32");
-  if (j->algo == FSMC_DR && t.lanes_per_chain > 1) return fsmc_fail(FSMC_EINVAL, "DR is chain-per-thread");
+  if ((j->algo == FSMC_DR || j->algo == FSMC_SLICE) && t.lanes_per_chain > 1)
+    return fsmc_fail(FSMC_EINVAL, "DR and slice sampling are chain-per-thread");
   if (t.lanes_per_chain == 16 && (j->algo != FSMC_ESS || j->d <= 32 || j->d > 512))
     return fsmc_fail(FSMC_EINVAL, "16 lanes per chain: ESS jobs with 32 < d <= 512");
   if (t.lanes_per_chain == 8 && (j->algo != FSMC_ESS || j->d <= 32 || j->d > 256))
@@ -566,7 +611,8 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (t.generator < 0 || t.generator > 2) return fsmc_fail(FSMC_EINVAL, "generator must be 0, 1 or 2");
   if (t.pipelined < 0 || t.pipelined > 2) return fsmc_fail(FSMC_EINVAL, "pipelined must be 0, 1 or 2");
   if (t.step_form < 0 || t.step_form > 2) return fsmc_fail(FSMC_EINVAL, "step_form must be 0, 1 or 2");
-  if (t.step_form == 2 && j->algo == FSMC_NUTS) return fsmc_fail(FSMC_EINVAL, "NUTS has step form 1 only");
+  if (t.step_form == 2 && (j->algo == FSMC_NUTS || j->algo == FSMC_SLICE))
+    return fsmc_fail(FSMC_EINVAL, "NUTS and slice sampling have step form 1 only");
   if (t.generator == 2 && (j->algo != FSMC_ESS || j->prec != FSMC_FP32 || j->d > 256))
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   j->tun = t;
@@ -618,6 +664,10 @@ static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
   } else if (j->algo == FSMC_DR) {
     ProfScope p(j, 1, st);
     e = launch_dr_fsm<T>(dr_view<T>(j), tu.steps_per_launch, tu.threads_per_block, st);
+    j->launches += 1;
+  } else if (j->algo == FSMC_SLICE) {
+    ProfScope p(j, 1, st);
+    e = launch_slice_fsm<T>(slice_view<T>(j), tu.steps_per_launch, tu.threads_per_block, st);
     j->launches += 1;
   } else {
     ProfScope p(j, 1, st);
@@ -796,6 +846,16 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
       CK(launch_dr_sync<T>(v, (int)t0, t1, bar, active, iters, threads, st));
       j->launches += 1;
     }
+  } else if (j->algo == FSMC_SLICE) {
+    SliceView<T> v = slice_view<T>(j);
+    const int chunk = 1000;
+    for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
+      const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
+      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+      ProfScope p(j, 2, st);
+      CK(launch_slice_sync<T>(v, (int)t0, t1, bar, active, iters, threads, st));
+      j->launches += 1;
+    }
   } else {
     fsmc_status s = nuts_run_sync(j, st);
     if (s != FSMC_OK) return s;
@@ -931,7 +991,7 @@ extern "C" fsmc_status fsmc_read_loop_counts(fsmc_job* j, int32_t* counts, int32
   if (counts)
     CK(cudaMemcpy(counts, j->dev + j->o_counts, (size_t)j->m * j->n * 4, cudaMemcpyDeviceToHost));
   if (aux) {
-    if (j->algo == FSMC_NUTS)
+    if (j->algo == FSMC_NUTS || j->algo == FSMC_SLICE)
       CK(cudaMemcpy(aux, j->dev + j->o_aux, (size_t)j->m * j->n * 4, cudaMemcpyDeviceToHost));
     else
       std::fill(aux, aux + (size_t)j->m * j->n, 0);

@@ -59,6 +59,7 @@ struct fsmc_job {
   fsmc_tuning tun{};
   fsmc_dr_params dr{3, 1.0, 0.5, 0};
   fsmc_nuts_params nuts{0.05, 10, 1000.0};
+  fsmc_slice_params slice{1.0, 100};
   std::vector<double> x0;
   // device arena and offsets into it
   char* dev = nullptr;
@@ -69,7 +70,7 @@ struct fsmc_job {
   size_t o_ell = 0, o_logy = 0, o_th = 0, o_k = 0, o_s = 0, o_gen = 0, o_nu = 0,  // ESS (o_ell/o_k: DR too)
          o_gencols = 0;
   size_t o_y = 0, o_lpy = 0;                                                      // DR
-  size_t o_aux = 0, o_nuts = 0, o_nuts_end = 0;                                   // NUTS
+  size_t o_aux = 0, o_nuts = 0, o_nuts_end = 0;                                   // NUTS (o_aux: SLICE too)
   // run bookkeeping
   bool fsm_used = false, sync_used = false;
   int64_t launches = 0;

@@ -63,6 +63,22 @@ struct DrView : ChainsView<T> {
 };
 
 template <typename T>
+struct SliceView : ChainsView<T> {
+  TargetView<T> tg;
+  T w;                   // step-out width
+  int mlim;              // stepping-out limit m (J + K = m - 1 steps at most)
+  T* lp;                 // [m] log pi(x)
+  T* logy;               // [m] threshold of the current sample
+  T* L; T* R; T* th;     // [m] interval ends and the current proposal, along the line
+  T* u;                  // [m][d] the current sample's direction
+  int* k;                // [m] state: 0 start of a sample, 1 left end, 2 right end, 3 proposal
+  int* J; int* K;        // [m] stepping-out budgets left
+  int* s;                // [m] proposals made in the current sample
+  int* nev;              // [m] log-density evaluations in the current sample
+  int* aux;              // [m][n] proposals per sample
+};
+
+template <typename T>
 cudaError_t launch_ess_nu_gen(const EssView<T>& v, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ess_fsm(const EssView<T>& v, int G, int budget, int threads, cudaStream_t st);
@@ -94,6 +110,14 @@ cudaError_t launch_dr_sync(const DrView<T>& v, int t0, int t1, GridBarrier bar, 
                            unsigned long long* iters, int threads, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_slice_fsm(const SliceView<T>& v, int budget, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_slice_sync(const SliceView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                              unsigned long long* iters, int threads, cudaStream_t st);
+template <typename T>
+cudaError_t launch_slice_init(const SliceView<T>& v, cudaStream_t st);
 
 cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st);
 // Next refill window for the pipelined ESS rounds: lo = hi_cur, hi = max(lo, min(t + W, n)),

@@ -1,0 +1,351 @@
+// Slice sampling (Neal 2003) on a random line through x as a finite state machine.
+//
+// Fig. 2 ("Slice Sampling") has INIT-E, EXPAND (the stepping-out loop body), INIT-S, SHRINK
+// (the shrinkage loop body) and DONE: two while loops in sequence.  One FSM step is the bundled
+// and amortised step: it makes exactly one log-density evaluation -- at the left end while
+// stepping out to the left, at the right end while stepping out to the right, or at the current
+// proposal while shrinking -- and the cheap states (INIT-E, INIT-S, DONE) run inline between
+// evaluations.  A sample takes as many steps as it makes evaluations (N_ij).
+//
+// Stepping out is Neal's procedure with the limit m: the initial interval [L, R] = [-w V, w - w V]
+// (along the line, x at 0) is extended by w at most J = floor(m V') times to the left, then at
+// most K = m - 1 - J times to the right, each end while it lies inside the slice
+// (log pi > log y).  Shrinkage draws theta ~ U(L, R); a proposal outside the slice replaces the
+// end on its side of 0.  The direction is u = z / |z|, z ~ N(0, I_d).
+//
+// Random numbers of sample t (tag 0): draws 0..D-1 the normals z (D = ceil(d/4)); draw D words
+// 0-1 the threshold's uniform, words 2-3 V; draw D+1 words 0-1 V'; draw D+2+p proposal p.
+#include <algorithm>
+#include <cmath>
+#include "fsmc_device.cuh"
+#include "fsmc_kernels.h"
+#include "target_logp.cuh"
+
+namespace fsmc {
+
+enum SliceState : int { SL_START = 0, SL_LEFT = 1, SL_RIGHT = 2, SL_PROP = 3, SL_DONE = 4 };
+
+template <typename T, int E>
+struct SliceChain {
+  T x[E], u[E];
+  T lp, logy, L, R, th;
+  int k, J, K, s, nev, t;
+};
+
+// log y = log pi(x) + log U.  Single precision keeps the threshold at least one ulp below
+// log pi(x): otherwise log U ~ -1e-8 rounds away, and the shrinking interval, whose limit x is
+// then not inside the slice, would never accept.
+template <typename T>
+__device__ __forceinline__ T slice_threshold(T lp, T log_u) {
+  T logy = lp + log_u;
+  if constexpr (sizeof(T) == 4) {
+    if (!(logy < lp) && lp > -INFINITY) logy = nextafterf(lp, -INFINITY);
+  }
+  return logy;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void slice_direction(const SliceView<T>& v, const Key& key, int t, T (&u)[E]) {
+  const int d = v.tg.d;
+  const int D = (d + 3) / 4;
+  T ss = T(0);
+#pragma unroll
+  for (int q = 0; q < (E + 3) / 4; ++q) {
+    T z[4] = {T(0), T(0), T(0), T(0)};
+    if (q < D) Conv<T>::normal_quad(key.block((uint32_t)t, 0, (uint32_t)q), z);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = 4 * q + i;
+      if (e < E) {
+        u[e] = e < d ? z[i] : T(0);
+        ss = fma(u[e], u[e], ss);
+      }
+    }
+  }
+  const T nrm = sqrt(ss);
+#pragma unroll
+  for (int e = 0; e < E; ++e) u[e] = u[e] / nrm;
+}
+
+// INIT-S / the next SHRINK proposal: theta ~ U(L, R) from draw D + 2 + s.
+template <typename T, int E>
+__device__ __forceinline__ void slice_propose(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c) {
+  const int D = (v.tg.d + 3) / 4;
+  const P4 b = key.block((uint32_t)c.t, 0, (uint32_t)(D + 2 + c.s));
+  c.th = c.L + (c.R - c.L) * Conv<T>::u(b.w0, b.w1);
+  c.k = SL_PROP;
+}
+
+// After the left end: step out to the right while its budget lasts, else start shrinking.
+template <typename T, int E>
+__device__ __forceinline__ void slice_after_left(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c) {
+  if (c.K > 0) c.k = SL_RIGHT;
+  else slice_propose<T, E>(v, key, c);
+}
+
+// INIT-E: direction, threshold, initial interval and the stepping-out budgets of sample c.t.
+template <typename T, int E>
+__device__ __forceinline__ void slice_begin(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c) {
+  const int D = (v.tg.d + 3) / 4;
+  slice_direction<T, E>(v, key, c.t, c.u);
+  const P4 b = key.block((uint32_t)c.t, 0, (uint32_t)D);
+  c.logy = slice_threshold<T>(c.lp, Conv<T>::log_u(b.w0, b.w1));
+  c.L = -v.w * Conv<T>::u(b.w2, b.w3);
+  c.R = c.L + v.w;
+  const P4 bj = key.block((uint32_t)c.t, 0, (uint32_t)(D + 1));
+  c.J = (int)floor((double)v.mlim * (double)Conv<T>::u(bj.w0, bj.w1));
+  c.K = v.mlim - 1 - c.J;
+  c.s = 0;
+  c.nev = 0;
+  if (c.J > 0) c.k = SL_LEFT;
+  else slice_after_left<T, E>(v, key, c);
+}
+
+// One FSM step: the log-density at the point the state names, then the state's decision.
+// Returns true when the sample is finished (x, lp hold it; after the shrink cap x is kept).
+template <typename T, int E>
+__device__ __forceinline__ bool slice_step(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c, int& err) {
+  const T th = c.k == SL_LEFT ? c.L : c.k == SL_RIGHT ? c.R : c.th;
+  T xp[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) xp[e] = fma(th, c.u[e], c.x[e]);
+  T lpp = full_logp<T, E>(v.tg, xp);
+  if (!(lpp == lpp)) { lpp = neg_inf<T>(); err |= ERR_NONFINITE; }
+  c.nev += 1;
+  const bool inside = lpp > c.logy;
+  if (c.k == SL_LEFT) {
+    if (inside) {
+      c.L -= v.w;
+      if (--c.J > 0) return false;
+    }
+    slice_after_left<T, E>(v, key, c);
+    return false;
+  }
+  if (c.k == SL_RIGHT) {
+    if (inside) {
+      c.R += v.w;
+      if (--c.K > 0) return false;
+    }
+    slice_propose<T, E>(v, key, c);
+    return false;
+  }
+  c.s += 1;
+  if (inside) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) c.x[e] = xp[e];
+    c.lp = lpp;
+    return true;
+  }
+  if (th < T(0)) c.L = th; else c.R = th;
+  if (c.s >= kMaxShrinks) {  // keep x
+    err |= ERR_SHRINK_CAP;
+    return true;
+  }
+  slice_propose<T, E>(v, key, c);
+  return false;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void slice_load(const SliceView<T>& v, int64_t c, SliceChain<T, E>& s) {
+  const int d = v.tg.d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) s.x[e] = e < d ? v.x[(size_t)c * d + e] : T(0);
+  s.lp = v.lp[c];
+  s.t = v.t[c];
+  s.k = v.k[c];
+  if (s.k != SL_START && s.k != SL_DONE) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) s.u[e] = e < d ? v.u[(size_t)c * d + e] : T(0);
+    s.logy = v.logy[c]; s.L = v.L[c]; s.R = v.R[c]; s.th = v.th[c];
+    s.J = v.J[c]; s.K = v.K[c]; s.s = v.s[c]; s.nev = v.nev[c];
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void slice_store(const SliceView<T>& v, int64_t c, const SliceChain<T, E>& s) {
+  const int d = v.tg.d;
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (e < d) v.x[(size_t)c * d + e] = s.x[e];
+  v.lp[c] = s.lp;
+  v.t[c] = s.t;
+  v.k[c] = s.k;
+  if (s.k != SL_START && s.k != SL_DONE) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e < d) v.u[(size_t)c * d + e] = s.u[e];
+    v.logy[c] = s.logy; v.L[c] = s.L; v.R[c] = s.R; v.th[c] = s.th;
+    v.J[c] = s.J; v.K[c] = s.K; v.s[c] = s.s; v.nev[c] = s.nev;
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void slice_finish(const SliceView<T>& v, int64_t c, SliceChain<T, E>& s) {
+  chain_emit<T, E>(v, v.tg.d, c, s.t, s.x);
+  v.counts[(size_t)c * v.n + s.t] = s.nev;
+  v.aux[(size_t)c * v.n + s.t] = s.s;
+  s.t += 1;
+  if (s.t == v.n) atomicAdd(v.chains_done, 1);
+}
+
+// FSM kernel: chain-per-thread, every chain advances `budget` evaluations.
+template <typename T, int E>
+__global__ void __launch_bounds__(256) slice_fsm_kernel(SliceView<T> v, int budget) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < v.m; c += stride) {
+    SliceChain<T, E> s;
+    slice_load<T, E>(v, c, s);
+    if (s.t >= v.n) continue;
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    int err = 0, steps = 0;
+    if (s.k == SL_START) slice_begin<T, E>(v, key, s);
+    for (int b = 0; b < budget; ++b) {
+      ++steps;
+      if (slice_step<T, E>(v, key, s, err)) {
+        slice_finish<T, E>(v, c, s);
+        if (s.t == v.n) { s.k = SL_DONE; break; }
+        slice_begin<T, E>(v, key, s);
+      }
+    }
+    slice_store<T, E>(v, c, s);
+    v.steps[c] += steps;
+    if (err) atomicOr(v.err, err);
+  }
+}
+
+// Synchronised kernel (Alg. 6 with two loops in sequence): for every sample, INIT-E for all
+// chains; then the left stepping-out loop, the right one and the shrink loop, each iterated with a
+// grid barrier until no chain is left in it (chains that left a loop wait, masked).
+template <typename T, int E>
+__global__ void __launch_bounds__(256) slice_sync_kernel(SliceView<T> v, int t_begin, int t_end,
+                                                         GridBarrier bar, unsigned* active_cnt,
+                                                         unsigned long long* iterations) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t c_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  __shared__ unsigned blk_active;
+  int iter = 0, err = 0;
+  for (int t = t_begin; t < t_end; ++t) {
+    for (int64_t c = c_first; c < v.m; c += stride) {
+      SliceChain<T, E> s;
+      slice_load<T, E>(v, c, s);
+      const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+      slice_begin<T, E>(v, key, s);
+      slice_store<T, E>(v, c, s);
+    }
+    for (int phase = SL_LEFT; phase <= SL_PROP; ++phase) {
+      while (true) {
+        if (threadIdx.x == 0) blk_active = 0;
+        __syncthreads();
+        unsigned mine = 0;
+        for (int64_t c = c_first; c < v.m; c += stride) {
+          if (v.k[c] != phase) continue;  // masked: not in this loop (yet, or any more)
+          SliceChain<T, E> s;
+          slice_load<T, E>(v, c, s);
+          const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+          v.steps[c] += 1;
+          if (slice_step<T, E>(v, key, s, err)) {
+            slice_finish<T, E>(v, c, s);
+            s.k = SL_DONE;
+          }
+          slice_store<T, E>(v, c, s);
+          if (s.k == phase) mine = 1;
+        }
+        if (mine) atomicAdd(&blk_active, 1u);
+        __syncthreads();
+        const int slot = iter % 3;
+        if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+        if (!grid_sync(bar, v.err)) return;
+        const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+        if (leader) {
+          active_cnt[(iter + 2) % 3] = 0;
+          *iterations += 1;
+        }
+        ++iter;
+        if (total == 0) break;
+      }
+    }
+  }
+  if (err) atomicOr(v.err, err);
+}
+
+template <typename T, int E>
+__global__ void slice_init_kernel(SliceView<T> v) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= v.m) return;
+  T x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) x[e] = e < v.tg.d ? v.x[(size_t)c * v.tg.d + e] : T(0);
+  T lp = full_logp<T, E>(v.tg, x);
+  if (!(lp == lp)) { lp = neg_inf<T>(); atomicOr(v.err, ERR_NONFINITE); }
+  v.lp[c] = lp;
+  v.k[c] = SL_START;
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename T, int E>
+static cudaError_t fsm_launch(const SliceView<T>& v, int budget, int threads, cudaStream_t st) {
+  const int64_t blocks = (v.m + threads - 1) / threads;
+  slice_fsm_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
+static cudaError_t sync_launch(const SliceView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                               unsigned long long* iters, int threads, cudaStream_t st) {
+  auto kern = slice_sync_kernel<T, E>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (v.m + threads - 1) / threads);
+  if (blocks < 1) blocks = 1;
+  SliceView<T> vv = v;
+  void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+}
+
+template <typename T, int E>
+static cudaError_t init_launch(const SliceView<T>& v, cudaStream_t st) {
+  slice_init_kernel<T, E><<<(unsigned)((v.m + 127) / 128), 128, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+#define FSMC_SLICE_DISPATCH(FN, ...)                         \
+  do {                                                       \
+    const int d = v.tg.d;                                    \
+    if (d <= 2) return FN<T, 2>(__VA_ARGS__);                \
+    if (d <= 4) return FN<T, 4>(__VA_ARGS__);                \
+    if (d <= 8) return FN<T, 8>(__VA_ARGS__);                \
+    if (d <= 10) return FN<T, 10>(__VA_ARGS__);              \
+    if (d <= 16) return FN<T, 16>(__VA_ARGS__);              \
+    if (d <= 32) return FN<T, 32>(__VA_ARGS__);              \
+    return cudaErrorInvalidValue;                            \
+  } while (0)
+
+template <typename T>
+cudaError_t launch_slice_fsm(const SliceView<T>& v, int budget, int threads, cudaStream_t st) {
+  FSMC_SLICE_DISPATCH(fsm_launch, v, budget, threads, st);
+}
+template <typename T>
+cudaError_t launch_slice_sync(const SliceView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                              unsigned long long* iters, int threads, cudaStream_t st) {
+  FSMC_SLICE_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
+}
+template <typename T>
+cudaError_t launch_slice_init(const SliceView<T>& v, cudaStream_t st) {
+  FSMC_SLICE_DISPATCH(init_launch, v, st);
+}
+
+template cudaError_t launch_slice_fsm<float>(const SliceView<float>&, int, int, cudaStream_t);
+template cudaError_t launch_slice_fsm<double>(const SliceView<double>&, int, int, cudaStream_t);
+template cudaError_t launch_slice_sync<float>(const SliceView<float>&, int, int, GridBarrier, unsigned*,
+                                              unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_slice_sync<double>(const SliceView<double>&, int, int, GridBarrier, unsigned*,
+                                               unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_slice_init<float>(const SliceView<float>&, cudaStream_t);
+template cudaError_t launch_slice_init<double>(const SliceView<double>&, cudaStream_t);
+
+}  // namespace fsmc

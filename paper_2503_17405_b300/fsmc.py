@@ -15,7 +15,7 @@ OK, EINVAL, ENOMEM, EADMIT, ECUDA, ETIMEOUT, ESTATE, EDEVICE = 0, -1, -2, -3, -4
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EADMIT", -4: "ECUDA", -5: "ETIMEOUT",
            -6: "ESTATE", -7: "EDEVICE"}
 TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5, "mog": 6}
-ALGO = {"ess": 0, "dr": 1, "nuts": 2}
+ALGO = {"ess": 0, "dr": 1, "nuts": 2, "slice": 3}
 PREC = {"fp64": 0, "fp32": 1}
 MODE = {"fsm": 0, "sync": 1}
 
@@ -33,6 +33,10 @@ class DRParams(ctypes.Structure):
 
 class NUTSParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_depth", ctypes.c_int), ("max_dH", ctypes.c_double)]
+
+
+class SliceParams(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_double), ("m", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
@@ -149,10 +153,11 @@ class Engine:
         return Target(self, kind, d, params, n_data)
 
     def job(self, target, algo, n_chains, n_samples, x0=None, seed=1, prec="fp32", store=True,
-            dr=None, nuts=None, tuning=None):
-        return Job(self, target, algo, n_chains, n_samples, x0, seed, prec, store, dr, nuts, tuning)
+            dr=None, nuts=None, tuning=None, slice=None):
+        return Job(self, target, algo, n_chains, n_samples, x0, seed, prec, store, dr, nuts, tuning,
+                   slice)
 
-    def autotune(self, target, algo, n_chains, prec="fp32", dr=None, nuts=None, cache_path=None):
+    def autotune(self, target, algo, n_chains, prec="fp32", dr=None, nuts=None, cache_path=None, slice=None):
         """fsmc_autotune: the fastest launch shape for such jobs, as a tuning dict."""
         ap = None
         if algo == "dr":
@@ -163,6 +168,10 @@ class Engine:
         elif algo == "nuts":
             nuts = nuts or {}
             keep = NUTSParams(nuts.get("eps", 0.05), nuts.get("max_depth", 10), nuts.get("max_dH", 1000.0))
+            ap = ctypes.cast(ctypes.byref(keep), _vp)
+        elif algo == "slice":
+            sl = slice or {}
+            keep = SliceParams(sl.get("w", 1.0), int(sl.get("m", 100)))
             ap = ctypes.cast(ctypes.byref(keep), _vp)
         t = Tuning()
         _check(load().fsmc_autotune(self._h, target._h, ALGO[algo], ap, PREC[prec], n_chains,
@@ -200,7 +209,7 @@ class Target:
 
 class Job:
     def __init__(self, engine, target, algo, n_chains, n_samples, x0, seed, prec, store, dr, nuts,
-                 tuning):
+                 tuning, slice=None):
         self.engine, self.target = engine, target
         self.m, self.n, self.d = n_chains, n_samples, target.d
         self.prec = prec
@@ -214,6 +223,10 @@ class Job:
             nuts = nuts or {}
             self._ap = NUTSParams(nuts.get("eps", 0.05), nuts.get("max_depth", 10),
                                   nuts.get("max_dH", 1000.0))
+            ap = ctypes.cast(ctypes.byref(self._ap), _vp)
+        elif algo == "slice":
+            sl = slice or {}
+            self._ap = SliceParams(sl.get("w", 1.0), int(sl.get("m", 100)))
             ap = ctypes.cast(ctypes.byref(self._ap), _vp)
         x0a = None if x0 is None else _f64(x0).reshape(n_chains, target.d)
         self._h = _vp()

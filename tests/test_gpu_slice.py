@@ -1,0 +1,116 @@
+"""The slice sampler (Fig. 2's two-loop FSM: stepping out, then shrinkage) on the CUDA kernels
+against the FP64 oracle, through the C ABI: FSM and synchronised kernels, loop counts, partial
+runs, the synchronised loop structure, and argument checks."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_17405_b300 import workloads as W
+from parity import FP32_TOL, compare, sample_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2503_17405_b300 import build, fsmc
+    build.build()
+    e = fsmc.Engine(0)
+    yield e
+    e.close()
+
+
+def _cases():
+    g = W.gauss_diag(3)
+    mg = W.mog(5, rho=0.6, offsets=(-2.0, 2.0), weights=(1.0, 2.0))
+    return {
+        "gauss_diag": (g, W.x0_gauss_diag_exact(g, 96), {"w": 1.0, "m": 20}),
+        "funnel": (dict(kind="funnel", d=10, n_data=0, params=np.zeros(0)), W.x0_funnel_exact(96),
+                   {"w": 1.0, "m": 100}),
+        "mog": (mg, W.x0_mog_exact(mg, 96), {"w": 2.0, "m": 8}),
+    }
+
+
+def _job(eng, w, x0, sl, n, prec, mode, tuning=None, seed=3):
+    tg = eng.target(w["kind"], w["d"], w["params"] if w["params"].size else None, n_data=w["n_data"])
+    job = eng.job(tg, "slice", x0.shape[0], n, x0=x0, seed=seed, prec=prec, slice=sl, tuning=tuning)
+    job.run(mode)
+    return job
+
+
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+@pytest.mark.parametrize("name", ["gauss_diag", "funnel", "mog"])
+def test_fp64_matches_oracle(eng, name, mode):
+    w, x0, sl = _cases()[name]
+    n = 120
+    job = _job(eng, w, x0, sl, n, "fp64", mode)
+    ref = O.run("slice", w["kind"], w["params"], x0, n, seed=3, n_data=w["n_data"], algo_params=[sl["w"], sl["m"]])
+    counts, props, steps = job.loop_counts()
+    compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert np.array_equal(props, ref["aux"])
+    if mode == "fsm":
+        assert np.array_equal(steps, counts.sum(1))   # one log-density evaluation per FSM step
+    else:
+        # three loops in sequence per sample, each run until its slowest chain leaves it
+        assert job.stats()["sync_iterations"] >= int(counts.max(0).sum())
+    job.close()
+
+
+def test_fp32_fsm_equals_sync_and_partial_runs(eng):
+    w, x0, sl = _cases()["funnel"]
+    n = 200
+    a = _job(eng, w, x0, sl, n, "fp32", "fsm")
+    b = _job(eng, w, x0, sl, n, "fp32", "sync")
+    c = _job(eng, w, x0, sl, n, "fp32", "fsm", tuning={"steps_per_launch": 3})
+    xa, xb, xc = a.samples(), b.samples(), c.samples()
+    (ca, pa, _), (cb, pb, _), (cc, pc, _) = a.loop_counts(), b.loop_counts(), c.loop_counts()
+    assert np.array_equal(ca, cb) and np.array_equal(pa, pb) and np.array_equal(xa, xb)
+    assert np.array_equal(ca, cc) and np.array_equal(xa, xc)
+    for j in (a, b, c):
+        j.close()
+
+
+def test_fp32_transition_by_transition_against_the_oracle(eng):
+    w, x0, sl = _cases()["funnel"]
+    x0 = x0.astype(np.float32).astype(np.float64)
+    m, n = x0.shape[0], 150
+    job = _job(eng, w, x0, sl, n, "fp32", "fsm")
+    xs = job.samples().astype(np.float64)
+    counts, _, _ = job.loop_counts()
+    job.close()
+    starts = np.concatenate([x0[:, None, :], xs[:, :-1, :]], axis=1).reshape(m * n, -1)
+    ref = O.transitions("slice", "funnel", w["params"], starts, np.repeat(np.arange(m), n), np.tile(np.arange(n), m),
+                        seed=3, algo_params=[sl["w"], sl["m"]])
+    err = sample_errors(xs.reshape(m * n, -1), ref["x"])
+    ok = (ref["counts"] == counts.ravel()) & (err <= FP32_TOL)
+    print("fp32 slice transitions: %d of %d agree; max err of those %.3g" % (ok.sum(), ok.size, err[ok].max()))
+    assert ok.mean() >= 0.99
+
+
+def test_flat_target_takes_every_expansion_step(eng):
+    flat = dict(kind="gauss_diag", d=2, n_data=0, params=np.array([0.0, 0.0, 1e9, 1e9]))
+    x0 = np.zeros((64, 2))
+    for m_lim in (1, 5, 40):
+        job = _job(eng, flat, x0, {"w": 1.0, "m": m_lim}, 6, "fp64", "fsm")
+        counts, props, _ = job.loop_counts()
+        assert np.all(counts == m_lim) and np.all(props == 1)
+        job.close()
+
+
+def test_argument_checks(eng):
+    from paper_2503_17405_b300 import fsmc
+    g = W.gauss_diag(3)
+    tg = eng.target("gauss_diag", 3, g["params"])
+    for bad in ({"w": 0.0, "m": 10}, {"w": -1.0, "m": 10}, {"w": 1.0, "m": 0}):
+        with pytest.raises(fsmc.FsmcError):
+            eng.job(tg, "slice", 8, 4, slice=bad)
+    with pytest.raises(fsmc.FsmcError):
+        eng.job(tg, "slice", 8, 4, tuning={"step_form": 2})
+    job = eng.job(tg, "slice", 8, 4)
+    with pytest.raises(fsmc.FsmcError):
+        job.submit("fsm")
+    job.close()
+    wide = W.gauss_diag(40)
+    tw = eng.target("gauss_diag", 40, wide["params"])
+    with pytest.raises(fsmc.FsmcError):
+        eng.job(tw, "slice", 8, 4)
