@@ -56,6 +56,9 @@ enum TargetKind {
   TGT_MOG = 6,         // mixture of K = n_data Gaussians N(mu_k, S), S = (1-rho) I + rho 1 1^T
                        // (unit variances, correlation rho), weights w_k;
                        //                                  params: rho, w[K], mu[K*d]
+  TGT_GP_REG = 7,      // ESS likelihood of GP-regression hyperparameters x = (sigma, tau, lambda)
+                       // (d = 3): log N(y; 0, tau^2 exp(-lambda^2 D) + sigma^2 I) over n = n_data
+                       // points;                          params: L[3*3], D[n*n], y[n]
 };
 
 struct Target {

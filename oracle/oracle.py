@@ -17,7 +17,8 @@ _lock = threading.Lock()
 _lib = None
 
 ALGO = {"ess": 0, "dr": 1, "nuts": 2, "sdr": 3, "slice": 4}
-TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5, "mog": 6}
+TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5, "mog": 6,
+          "gp_reg": 7}
 
 
 def build(force=False):

@@ -63,9 +63,11 @@ static double softplus(double t) {
   return t > 0 ? t + std::log1p(std::exp(-t)) : std::log1p(std::exp(t));
 }
 
+static const double kPiOracle = 3.14159265358979323846;
+
 const double* Target::prior_chol() const {
   switch (kind) {
-    case TGT_GAUSS_CONJ: case TGT_GP_LOGIT: case TGT_FLAT: return params;
+    case TGT_GAUSS_CONJ: case TGT_GP_LOGIT: case TGT_FLAT: case TGT_GP_REG: return params;
     default: return nullptr;
   }
 }
@@ -154,6 +156,43 @@ double Target::logp(const double* x, double* grad) const {
         }
       }
       return lse;
+    }
+    case TGT_GP_REG: {
+      // Sec. 7.2: y = f(x) + eps, f ~ GP(0, tau^2 exp(-lambda^2 |x - x'|^2)), eps ~ N(0, sigma^2):
+      // the marginal likelihood log N(y; 0, C) with C_ij = tau^2 exp(-lambda^2 D_ij) + sigma^2
+      // delta_ij, D_ij = |x_i - x_j|^2, by the Cholesky factorisation C = G G^T:
+      // log f = -|G^-1 y|^2 / 2 - sum_i log G_ii - n log(2 pi) / 2.  -inf if C is not positive
+      // definite in double precision.
+      const int n = n_data;
+      const double* D = params + (size_t)d * d;
+      const double* y = D + (size_t)n * n;
+      const double s2 = x[0] * x[0], t2 = x[1] * x[1], l2 = x[2] * x[2];
+      std::vector<double> G((size_t)n * n, 0.0);
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j)
+          G[(size_t)i * n + j] = t2 * std::exp(-l2 * D[(size_t)i * n + j]) + (i == j ? s2 : 0.0);
+      for (int j = 0; j < n; ++j) {  // Cholesky-Crout, column by column
+        double dj = G[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) dj -= G[(size_t)j * n + k] * G[(size_t)j * n + k];
+        if (!(dj > 0)) return -INFINITY;
+        const double gjj = std::sqrt(dj);
+        G[(size_t)j * n + j] = gjj;
+        for (int i = j + 1; i < n; ++i) {
+          double v = G[(size_t)i * n + j];
+          for (int k = 0; k < j; ++k) v -= G[(size_t)i * n + k] * G[(size_t)j * n + k];
+          G[(size_t)i * n + j] = v / gjj;
+        }
+      }
+      double quad = 0, logdet_half = 0;
+      std::vector<double> a(n);
+      for (int i = 0; i < n; ++i) {  // forward substitution G a = y
+        double v = y[i];
+        for (int k = 0; k < i; ++k) v -= G[(size_t)i * n + k] * a[k];
+        a[i] = v / G[(size_t)i * n + i];
+        quad += a[i] * a[i];
+        logdet_half += std::log(G[(size_t)i * n + i]);
+      }
+      return -0.5 * quad - logdet_half - 0.5 * n * std::log(2.0 * kPiOracle);
     }
     case TGT_GAUSS_DIAG: {
       const double* mu = params;

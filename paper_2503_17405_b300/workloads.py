@@ -104,6 +104,29 @@ def x0_mog_exact(w, m, seed=DATA_SEED, stream=15):
     return w["mu"][k] + np.sqrt(1.0 - w["rho"]) * z + np.sqrt(w["rho"]) * zeta
 
 
+def gp_reg(n=100, p=6, seed=DATA_SEED, theta_true=(0.3, 1.0, 0.4)):
+    """Sec. 7.2's GP-regression hyperparameter posterior on synthetic data shaped like its
+    house-price task: n points with p = 6 standardised features, y drawn from the model at
+    theta_true = (sigma, tau, lambda) and standardised.  ESS target over x = (sigma, tau, lambda)
+    with the N(0, I_3) prior (L = I_3); params = L[9], D[n*n] (squared distances), y[n]."""
+    r = _rng(seed, 7)
+    X = r.standard_normal((n, p))
+    X = (X - X.mean(0)) / X.std(0)
+    D = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    s, t, l = theta_true
+    C = t * t * np.exp(-l * l * D) + s * s * np.eye(n)
+    y = np.linalg.cholesky(C) @ r.standard_normal(n)
+    y = (y - y.mean()) / y.std()
+    L = np.eye(3)
+    return dict(kind="gp_reg", d=3, n_data=n, params=np.concatenate([L.ravel(), D.ravel(), y]),
+                X=X, D=D, y=y, theta_true=np.array(theta_true))
+
+
+def x0_gp_reg(w, m, seed=DATA_SEED, stream=16):
+    """Starts near the data-generating hyperparameters: theta_true + 0.05 z."""
+    return w["theta_true"][None, :] + 0.05 * _rng(seed, stream).standard_normal((m, 3))
+
+
 def flat(d=8, seed=DATA_SEED):
     r = _rng(seed, 5)
     A = r.standard_normal((d, d))
