@@ -65,8 +65,14 @@ typedef enum fsmc_status {
  *               log pi(x) = log sum_k w_k exp(-(x - mu_k)^T S^-1 (x - mu_k) / 2) (the common
  *               normaliser dropped):                       rho, w[K], mu[K*d]
  *               (-1/(d-1) < rho < 1 and w_k > 0 finite, else FSMC_EINVAL)
- * ESS needs a kind with a prior factor L (GAUSS_CONJ, GP_LOGIT, FLAT); DR and NUTS need
- * a full log-density (FUNNEL, LOGREG, GAUSS_DIAG, MOG).  The ESS prior is N(0, L L^T) (Alg. 8). */
+ *   GP_REG      ESS likelihood of GP-regression hyperparameters x = (sigma, tau, lambda), d = 3
+ *               (Sec. 7.2): log N(y; 0, tau^2 exp(-lambda^2 D) + sigma^2 I) over n = n_data
+ *               points (1..336; FP64 jobs 1..232), D the squared distances between inputs:
+ *                                                          L[3*3], D[n*n], y[n]
+ *               (-inf where the covariance is not positive definite in the job's precision)
+ * ESS needs a kind with a prior factor L (GAUSS_CONJ, GP_LOGIT, FLAT, GP_REG); DR, NUTS and
+ * SLICE need a full log-density (FUNNEL, LOGREG, GAUSS_DIAG, MOG).  The ESS prior is
+ * N(0, L L^T) (Alg. 8).  GP_REG jobs run a chain per warp (the likelihood warp-wide). */
 typedef enum fsmc_target_kind {
   FSMC_TGT_GAUSS_CONJ = 0,
   FSMC_TGT_GP_LOGIT = 1,
@@ -74,7 +80,8 @@ typedef enum fsmc_target_kind {
   FSMC_TGT_LOGREG = 3,
   FSMC_TGT_GAUSS_DIAG = 4,
   FSMC_TGT_FLAT = 5,
-  FSMC_TGT_MOG = 6
+  FSMC_TGT_MOG = 6,
+  FSMC_TGT_GP_REG = 7
 } fsmc_target_kind;
 
 typedef enum fsmc_algo { FSMC_ESS = 0, FSMC_DR = 1, FSMC_NUTS = 2, FSMC_SLICE = 3 } fsmc_algo;

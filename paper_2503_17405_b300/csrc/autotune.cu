@@ -55,7 +55,9 @@ void cache_store(const std::string& path, const std::string& key, const fsmc_tun
 
 std::vector<fsmc_tuning> candidates(fsmc_target* t, fsmc_algo algo, fsmc_precision prec) {
   std::vector<fsmc_tuning> c;
-  if (algo == FSMC_ESS) {
+  if (algo == FSMC_ESS && t->kind == FSMC_TGT_GP_REG) {
+    for (int steps : {4, 8, 16}) c.push_back(fsmc_tuning{32, steps, 0, 32, 0, 0, 2});
+  } else if (algo == FSMC_ESS) {
     std::vector<int> lanes = {32};
     if (t->d <= 32) lanes.push_back(1);
     if (t->d > 32 && t->d <= 512) lanes.push_back(16);

@@ -139,6 +139,10 @@ static bool target_layout(int kind, int d, int n_data, size_t* n_params, bool* n
     case FSMC_TGT_LOGREG: *n_params = (size_t)n_data * d + n_data; return n_data >= 1;
     case FSMC_TGT_GAUSS_DIAG: *n_params = 2 * (size_t)d; return n_data == 0;
     case FSMC_TGT_MOG: *n_params = 1 + (size_t)n_data * (d + 1); return n_data >= 1 && n_data <= 64;
+    case FSMC_TGT_GP_REG:
+      *n_params = (size_t)d * d + (size_t)n_data * n_data + n_data;
+      *needs_L = true;
+      return d == 3 && n_data >= 1 && n_data <= kGpRegMaxN32;
   }
   return false;
 }
@@ -192,6 +196,13 @@ static fsmc_status upload_target(fsmc_target* t, std::vector<void*>& bufs, Targe
       if ((st = up(p, d, &tv.vec))) return st;
       if ((st = up(p + d, d, &tv.vec2))) return st;
       break;
+    case FSMC_TGT_GP_REG: {
+      const size_t n = (size_t)t->n_data;
+      if ((st = up(p, (size_t)d * d, &tv.L))) return st;
+      if ((st = up(p + (size_t)d * d, n * n, &tv.X))) return st;
+      if ((st = up(p + (size_t)d * d + n * n, n, &tv.vec))) return st;
+      break;
+    }
     case FSMC_TGT_MOG: {
       const int K = t->n_data;
       const double rho = p[0];
@@ -285,11 +296,21 @@ struct Layout {
   }
 };
 
+// ESS on a target whose likelihood is one dense problem per evaluation: a chain per CTA.
+static bool ess_block(const fsmc_job* j) { return j->algo == FSMC_ESS && j->tg->kind == FSMC_TGT_GP_REG; }
+
 // Decides the launch shape when the caller left it open.
 static void default_tuning(fsmc_job* j) {
   fsmc_tuning& tu = j->tun;
   if (!tu.step_form) tu.step_form = 1;
-  if (j->algo == FSMC_ESS) {
+  if (ess_block(j)) {
+    tu.lanes_per_chain = 32;  // a warp (and CTA) per chain
+    tu.ring_slots = 0;
+    tu.generator = 0;
+    tu.pipelined = 2;
+    tu.threads_per_block = 32;  // a warp per chain
+    if (!tu.steps_per_launch) tu.steps_per_launch = 8;
+  } else if (j->algo == FSMC_ESS) {
     if (!tu.lanes_per_chain) {
       // chain-per-warp when one chain's likelihood is wide (d >= 64) or when there are too
       // few chains to fill the machine one per thread
@@ -328,7 +349,16 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
   j->o_mom = j->store ? 0 : L.take(4 * m * d * es);
   j->o_bar = L.take(64);
   j->o_iters = L.take(8);
-  if (j->algo == FSMC_ESS) {
+  if (ess_block(j)) {
+    j->o_ell = L.take(m * es);
+    j->o_logy = L.take(m * es);
+    j->o_th = L.take(3 * m * es);
+    j->o_k = L.take(m * 4);
+    j->o_s = L.take(m * 4);
+    j->o_nu = L.take(m * d * es);
+    j->o_gencols = L.take(8);
+    j->o_work = L.take(8);
+  } else if (j->algo == FSMC_ESS) {
     j->W = j->tun.ring_slots;
     j->dstride = (int)align_up(d, 32);
     j->o_ell = L.take(m * es);
@@ -444,6 +474,24 @@ DrView<T> dr_view(const fsmc_job* j) {
 }
 
 template <typename T>
+EssBlockView<T> ess_block_view(const fsmc_job* j) {
+  EssBlockView<T> v;
+  fill_chains<T>(j, v);
+  char* b = j->dev;
+  v.tg = target_view<T>(j->tg);
+  v.ell = (T*)(b + j->o_ell);
+  v.logy = (T*)(b + j->o_logy);
+  v.th = (T*)(b + j->o_th);
+  v.thmin = v.th + j->m;
+  v.thmax = v.th + 2 * j->m;
+  v.nu = (T*)(b + j->o_nu);
+  v.k = (int*)(b + j->o_k);
+  v.s = (int*)(b + j->o_s);
+  v.work = (unsigned*)(b + j->o_work);
+  return v;
+}
+
+template <typename T>
 SliceView<T> slice_view(const fsmc_job* j) {
   SliceView<T> v;
   fill_chains<T>(j, v);
@@ -481,7 +529,14 @@ static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
   CK(cudaMemsetAsync(b + j->o_bar, 0, 64, st));
   CK(cudaMemsetAsync(b + j->o_iters, 0, 8, st));
   if (!j->store) CK(cudaMemsetAsync(b + j->o_mom, 0, 4 * m * d * sizeof(T), st));
-  if (j->algo == FSMC_ESS) {
+  if (ess_block(j)) {
+    CK(cudaMemsetAsync(b + j->o_s, 0, m * 4, st));
+    CK(cudaMemsetAsync(b + j->o_th, 0, 3 * m * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_logy, 0, m * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_nu, 0, m * d * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_gencols, 0, 8, st));
+    CK(launch_ess_block_init<T>(ess_block_view<T>(j), st));
+  } else if (j->algo == FSMC_ESS) {
     CK(cudaMemsetAsync(b + j->o_k, 0, m * 4, st));
     CK(cudaMemsetAsync(b + j->o_s, 0, m * 4, st));
     CK(cudaMemsetAsync(b + j->o_th, 0, 3 * m * sizeof(T), st));
@@ -524,13 +579,15 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
     return fsmc_fail(FSMC_EINVAL, "n_chains / n_samples out of range");
   if (prec != FSMC_FP32 && prec != FSMC_FP64) return fsmc_fail(FSMC_EINVAL, "bad precision");
   const bool ess_kind = t->kind == FSMC_TGT_GAUSS_CONJ || t->kind == FSMC_TGT_GP_LOGIT ||
-                        t->kind == FSMC_TGT_FLAT;
+                        t->kind == FSMC_TGT_FLAT || t->kind == FSMC_TGT_GP_REG;
   if (algo == FSMC_ESS && !ess_kind) return fsmc_fail(FSMC_EINVAL, "ESS needs a target with a Gaussian prior factor");
   if ((algo == FSMC_DR || algo == FSMC_NUTS || algo == FSMC_SLICE) && ess_kind)
     return fsmc_fail(FSMC_EINVAL, "DR / NUTS / slice sampling need a full log-density target");
   if (algo != FSMC_ESS && algo != FSMC_DR && algo != FSMC_NUTS && algo != FSMC_SLICE)
     return fsmc_fail(FSMC_EINVAL, "bad algo");
   if (algo == FSMC_DR && t->d > 32) return fsmc_fail(FSMC_EINVAL, "DR supports d <= 32");
+  if (t->kind == FSMC_TGT_GP_REG && prec == FSMC_FP64 && t->n_data > kGpRegMaxN64)
+    return fsmc_fail(FSMC_EINVAL, "FP64 GP_REG jobs support n_data <= 232");
   if (algo == FSMC_SLICE && t->d > 32) return fsmc_fail(FSMC_EINVAL, "slice sampling supports d <= 32");
   auto* j = new (std::nothrow) fsmc_job();
   if (!j) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");
@@ -591,6 +648,9 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (!j || !tu) return fsmc_fail(FSMC_EINVAL, "NULL argument");
   if (j->dev) return fsmc_fail(FSMC_ESTATE, "tuning must be set before the first run");
   fsmc_tuning t = *tu;
+  if (ess_block(j) && ((t.lanes_per_chain && t.lanes_per_chain != 32) || t.generator || t.ring_slots ||
+                       t.step_form == 2 || (t.threads_per_block && t.threads_per_block != 32)))
+    return fsmc_fail(FSMC_EINVAL, "GP_REG jobs run a warp per chain; only steps_per_launch is tunable");
   if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 8 && t.lanes_per_chain != 16 &&
       t.lanes_per_chain != 32)
     return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1, 8, 16 or 32");
@@ -652,7 +712,11 @@ template <typename T>
 static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
   const fsmc_tuning& tu = j->tun;
   cudaError_t e;
-  if (j->algo == FSMC_ESS) {
+  if (ess_block(j)) {
+    ProfScope p(j, 1, st);
+    e = launch_ess_block_fsm<T>(ess_block_view<T>(j), tu.steps_per_launch, j->e->sms, st);
+    j->launches += 1;
+  } else if (j->algo == FSMC_ESS) {
     const EssView<T> v = ess_view<T>(j);
     {
       ProfScope p(j, 0, st);
@@ -775,7 +839,8 @@ static fsmc_status run_fsm_pipelined(fsmc_job* j, cudaStream_t st) {
 
 template <typename T>
 static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
-  if (j->algo == FSMC_ESS && max_steps <= 0 && j->tun.pipelined == 1) return run_fsm_pipelined<T>(j, st);
+  if (j->algo == FSMC_ESS && !ess_block(j) && max_steps <= 0 && j->tun.pipelined == 1)
+    return run_fsm_pipelined<T>(j, st);
   const int check_every = 8;
   int64_t rounds_limit = -1;
   if (max_steps > 0) rounds_limit = (max_steps + j->tun.steps_per_launch - 1) / j->tun.steps_per_launch;
@@ -785,7 +850,7 @@ static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
     fsmc_status s = capture_rounds<T>(j, check_every, st);
     if (s != FSMC_OK) return s;
   }
-  const int per_round = j->algo == FSMC_ESS ? 2 : 1;
+  const int per_round = j->algo == FSMC_ESS && !ess_block(j) ? 2 : 1;
   int64_t r = 0;
   while (true) {
     int done = 0, err = 0;
@@ -818,7 +883,17 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
   unsigned* active = (unsigned*)(b + j->o_bar) + 4;
   unsigned long long* iters = (unsigned long long*)(b + j->o_iters);
   const int threads = j->tun.threads_per_block;
-  if (j->algo == FSMC_ESS) {
+  if (ess_block(j)) {
+    EssBlockView<T> v = ess_block_view<T>(j);
+    const int chunk = 1000;
+    for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
+      const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
+      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+      ProfScope p(j, 2, st);
+      CK(launch_ess_block_sync<T>(v, (int)t0, t1, bar, active, iters, st));
+      j->launches += 1;
+    }
+  } else if (j->algo == FSMC_ESS) {
     EssView<T> v = ess_view<T>(j);
     for (int64_t t0 = 0; t0 < j->n; t0 += j->W) {
       const int t1 = (int)std::min<int64_t>(t0 + j->W, j->n);

@@ -90,6 +90,7 @@ struct fsmc_job {
   cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_fsm[2] = {nullptr, nullptr};
   size_t o_win = 0;  // second refill-window buffer [2][m]
   size_t o_colbase = 0, o_colmap = 0;  // compacted refill list: [m+1] prefix sums, [m*W] (chain, sample)
+  size_t o_work = 0;  // block-likelihood ESS: chain counter of the current FSM launch
   // serving
   bool submitted = false;
   fsmc_mode serve_mode = FSMC_MODE_FSM;

@@ -13,13 +13,12 @@
 // (ess_nu_gen) into a per-chain ring of W slots; this is the paper's amortisation of an
 // expensive state-independent computation, moved out of the step altogether.
 #include <algorithm>
+#include "ess_common.cuh"
 #include "fsmc_device.cuh"
 #include "fsmc_kernels.h"
 
 namespace fsmc {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-enum EssState : int { ESS_INIT = 0, ESS_SHRINK = 1 };
 
 // ------------------------------------------------------------------------------------------
 // nu = L z for a tile of (chain, sample) columns.  z is generated from the chain's Philox
@@ -226,31 +225,6 @@ __device__ __forceinline__ float flip_sign(float v, uint32_t mask, int e) {
 // The base-2 GP-logit path is taken for every single-precision GP-logit job.
 template <typename T, int E>
 constexpr bool kEssGpFast = sizeof(T) == 4;
-
-// Slice threshold log y = log f(x) + log u.  In single precision a u within ~1e-5 of 1 makes
-// the sum round back to log f(x); the bracket would then shrink onto theta = 0 without ever
-// finding log f(x') > log y.  The threshold is therefore kept at least one ulp below log f(x),
-// which moves it by at most one ulp and makes theta -> 0 always accept.
-template <typename T>
-__device__ __forceinline__ T ess_threshold(T ell, T log_u) {
-  T logy = ell + log_u;
-  if constexpr (sizeof(T) == 4) {
-    if (!(logy < ell) && ell > -INFINITY) logy = nextafterf(ell, -INFINITY);
-  }
-  return logy;
-}
-
-// sin and cos of a bracket angle th in (-2 pi, 2 pi).  Single precision reduces th to
-// [-pi, pi], where __sincosf is accurate to ~5e-7; double precision calls sincos.
-template <typename T>
-__device__ __forceinline__ void ess_sincos(T th, T& sn, T& cs) {
-  if constexpr (sizeof(T) == 4) {
-    const float red = fmaf(-6.28318530717958647692f, rintf(th * 0.15915494309189533577f), th);
-    __sincosf(red, &sn, &cs);
-  } else {
-    sincos(th, &sn, &cs);
-  }
-}
 
 template <typename T>
 __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {

@@ -192,7 +192,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
 // ---- device-side target view ---------------------------------------------------------------------
 enum TargetKind : int {
   TGT_GAUSS_CONJ = 0, TGT_GP_LOGIT = 1, TGT_FUNNEL = 2, TGT_LOGREG = 3, TGT_GAUSS_DIAG = 4, TGT_FLAT = 5,
-  TGT_MOG = 6
+  TGT_MOG = 6, TGT_GP_REG = 7
 };
 
 template <typename T>
@@ -201,9 +201,10 @@ struct TargetView {
   int d;
   int n_data;
   const T* L;     // ESS prior Cholesky [d][d] (lower)
-  const T* vec;   // y (GAUSS_CONJ), s (GP_LOGIT), mu (GAUSS_DIAG), y (LOGREG), log w_k (MOG)
+  const T* vec;   // y (GAUSS_CONJ), s (GP_LOGIT), mu (GAUSS_DIAG), y (LOGREG), log w_k (MOG), y (GP_REG)
   const T* vec2;  // sigma (GAUSS_DIAG)
-  const T* X;     // LOGREG design matrix [n_data][d]; MOG means mu_k [n_data][d]
+  const T* X;     // LOGREG design matrix [n_data][d]; MOG means mu_k [n_data][d]; GP_REG squared
+                  // distances D [n_data][n_data]
   const T* XT;    // LOGREG design matrix transposed, [d][n_pad] with zero rows >= n_data
   int n_pad;      // n_data rounded up to a multiple of 4
   T s2;           // GAUSS_CONJ noise variance

@@ -62,6 +62,20 @@ struct DrView : ChainsView<T> {
   int* k;                // [m] next stage to try
 };
 
+// ESS on a target whose likelihood is one dense linear-algebra problem per evaluation (GP
+// regression, Sec. 7.2): a chain per warp, the likelihood warp-wide.
+template <typename T>
+struct EssBlockView : ChainsView<T> {
+  TargetView<T> tg;      // prior factor L [d][d]; GP_REG: X = D [n][n], vec = y [n], n_data = n
+  T* ell;                // [m] log f(x)
+  T* logy;               // [m] threshold
+  T* th; T* thmin; T* thmax;  // [m] angle and bracket
+  T* nu;                 // [m][d] the current sample's ellipse direction
+  int* k;                // [m] FSM state
+  int* s;                // [m] shrinks in the current sample
+  unsigned* work;        // chain counter of the current FSM launch (zeroed before each launch)
+};
+
 template <typename T>
 struct SliceView : ChainsView<T> {
   TargetView<T> tg;
@@ -110,6 +124,17 @@ cudaError_t launch_dr_sync(const DrView<T>& v, int t0, int t1, GridBarrier bar, 
                            unsigned long long* iters, int threads, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st);
+
+// GP_REG likelihood in shared memory (the packed lower triangle): n <= kGpRegMaxN32 (FP32) /
+// kGpRegMaxN64 (FP64).
+constexpr int kGpRegMaxN32 = 336, kGpRegMaxN64 = 232;
+template <typename T>
+cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, int sms, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ess_block_sync(const EssBlockView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                                  unsigned long long* iters, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ess_block_init(const EssBlockView<T>& v, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_slice_fsm(const SliceView<T>& v, int budget, int threads, cudaStream_t st);

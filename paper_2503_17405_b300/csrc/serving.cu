@@ -208,7 +208,8 @@ extern "C" fsmc_status fsmc_submit(fsmc_engine* e, fsmc_job* j, fsmc_mode mode) 
   if (mode != FSMC_MODE_FSM && mode != FSMC_MODE_SYNC) return fsmc_fail(FSMC_EINVAL, "bad mode");
   if (j->submitted || j->dev) return fsmc_fail(FSMC_ESTATE, "job was already submitted or run");
   if (j->tun.step_form == 2) return fsmc_fail(FSMC_EINVAL, "ablation step forms run through fsmc_job_run only");
-  if (j->algo == FSMC_SLICE) return fsmc_fail(FSMC_EINVAL, "slice-sampling jobs run through fsmc_job_run only");
+  if (j->algo == FSMC_SLICE || j->tg->kind == FSMC_TGT_GP_REG)
+    return fsmc_fail(FSMC_EINVAL, "slice-sampling and GP_REG jobs run through fsmc_job_run only");
   j->submitted = true;
   j->serve_mode = mode;
   j->t_submit = Clock::now();

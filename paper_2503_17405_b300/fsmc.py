@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(_HERE, "libfsmc.so")
 OK, EINVAL, ENOMEM, EADMIT, ECUDA, ETIMEOUT, ESTATE, EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EADMIT", -4: "ECUDA", -5: "ETIMEOUT",
            -6: "ESTATE", -7: "EDEVICE"}
-TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5, "mog": 6}
+TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5, "mog": 6,
+          "gp_reg": 7}
 ALGO = {"ess": 0, "dr": 1, "nuts": 2, "slice": 3}
 PREC = {"fp64": 0, "fp32": 1}
 MODE = {"fsm": 0, "sync": 1}

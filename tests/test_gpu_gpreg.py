@@ -1,0 +1,103 @@
+"""ESS on Sec. 7.2's GP-regression hyperparameters with the likelihood evaluated warp-wide (a
+chain per warp, the n x n covariance factorised in shared memory) against the FP64 oracle,
+through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_17405_b300 import workloads as W
+from parity import FP32_TOL, compare, sample_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2503_17405_b300 import build, fsmc
+    build.build()
+    e = fsmc.Engine(0)
+    yield e
+    e.close()
+
+
+def _job(eng, w, x0, n, prec, mode, tuning=None, seed=2):
+    tg = eng.target("gp_reg", 3, w["params"], n_data=w["n_data"])
+    job = eng.job(tg, "ess", x0.shape[0], n, x0=x0, seed=seed, prec=prec, tuning=tuning)
+    job.run(mode)
+    return job
+
+
+@pytest.mark.parametrize("n_data", [25, 100, 231])
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_matches_oracle(eng, n_data, mode):
+    w = W.gp_reg(n_data)
+    x0 = W.x0_gp_reg(w, 20)
+    n = 25
+    job = _job(eng, w, x0, n, "fp64", mode)
+    ref = O.run("ess", "gp_reg", w["params"], x0, n, seed=2, n_data=n_data)
+    counts, _, steps = job.loop_counts()
+    compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    if mode == "fsm":
+        assert np.array_equal(steps, (counts + 1).sum(1))   # one likelihood per FSM step
+    else:
+        assert job.stats()["sync_iterations"] >= int((counts.max(0) + 1).sum())
+    job.close()
+
+
+def test_fp32_fsm_equals_sync_and_partial_runs(eng):
+    w = W.gp_reg(100)
+    x0 = W.x0_gp_reg(w, 40)
+    n = 40
+    a = _job(eng, w, x0, n, "fp32", "fsm")
+    b = _job(eng, w, x0, n, "fp32", "sync")
+    c = _job(eng, w, x0, n, "fp32", "fsm", tuning={"steps_per_launch": 3})
+    (ca, _, _), (cb, _, _), (cc, _, _) = a.loop_counts(), b.loop_counts(), c.loop_counts()
+    assert np.array_equal(ca, cb) and np.array_equal(a.samples(), b.samples())
+    assert np.array_equal(ca, cc) and np.array_equal(a.samples(), c.samples())
+    for j in (a, b, c):
+        j.close()
+
+
+@pytest.mark.parametrize("n_data", [25, 100, 336])
+def test_fp32_transition_by_transition_against_the_oracle(eng, n_data):
+    w = W.gp_reg(n_data)
+    x0 = W.x0_gp_reg(w, 32).astype(np.float32).astype(np.float64)
+    m, n = x0.shape[0], 40
+    job = _job(eng, w, x0, n, "fp32", "fsm")
+    xs = job.samples().astype(np.float64)
+    counts, _, _ = job.loop_counts()
+    job.close()
+    starts = np.concatenate([x0[:, None, :], xs[:, :-1, :]], axis=1).reshape(m * n, -1)
+    ref = O.transitions("ess", "gp_reg", w["params"], starts, np.repeat(np.arange(m), n), np.tile(np.arange(n), m),
+                        seed=2, n_data=n_data)
+    err = sample_errors(xs.reshape(m * n, -1), ref["x"])
+    ok = (ref["counts"] == counts.ravel()) & (err <= FP32_TOL)
+    print("fp32 gp_reg n=%d transitions: %d of %d agree; max err of those %.3g"
+          % (n_data, ok.sum(), ok.size, err[ok].max()))
+    assert ok.mean() >= 0.98
+
+
+def test_limits_and_argument_checks(eng):
+    from paper_2503_17405_b300 import fsmc
+    w = W.gp_reg(233)
+    tg = eng.target("gp_reg", 3, w["params"], n_data=233)
+    with pytest.raises(fsmc.FsmcError):
+        eng.job(tg, "ess", 4, 4, prec="fp64")                     # FP64 covariance over 232 rows
+    job = eng.job(tg, "ess", 4, 4, x0=W.x0_gp_reg(w, 4), prec="fp32")
+    job.run("fsm")
+    job.close()
+    big = W.gp_reg(337)
+    with pytest.raises(fsmc.FsmcError):
+        eng.target("gp_reg", 3, big["params"], n_data=337)        # over the shared-memory limit
+    w = W.gp_reg(25)
+    with pytest.raises(fsmc.FsmcError):
+        eng.target("gp_reg", 2, w["params"][1:], n_data=25)      # d must be 3
+    tg = eng.target("gp_reg", 3, w["params"], n_data=25)
+    with pytest.raises(fsmc.FsmcError):
+        eng.job(tg, "ess", 4, 4, tuning={"lanes_per_chain": 16})
+    with pytest.raises(fsmc.FsmcError):
+        eng.job(tg, "nuts", 4, 4)
+    job = eng.job(tg, "ess", 4, 4)
+    with pytest.raises(fsmc.FsmcError):
+        job.submit("fsm")
+    job.close()
