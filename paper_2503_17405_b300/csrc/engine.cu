@@ -587,7 +587,7 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
     return fsmc_fail(FSMC_EINVAL, "bad algo");
   if (algo == FSMC_DR && t->d > 32) return fsmc_fail(FSMC_EINVAL, "DR supports d <= 32");
   if (t->kind == FSMC_TGT_GP_REG && prec == FSMC_FP64 && t->n_data > kGpRegMaxN64)
-    return fsmc_fail(FSMC_EINVAL, "FP64 GP_REG jobs support n_data <= 232");
+    return fsmc_fail(FSMC_EINVAL, "FP64 GP_REG jobs support n_data <= 220");
   if (algo == FSMC_SLICE && t->d > 32) return fsmc_fail(FSMC_EINVAL, "slice sampling supports d <= 32");
   auto* j = new (std::nothrow) fsmc_job();
   if (!j) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");

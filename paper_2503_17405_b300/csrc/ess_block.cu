@@ -29,11 +29,22 @@ __device__ __forceinline__ T blk_exp(T a) { if constexpr (sizeof(T) == 4) return
 template <typename T>
 __device__ __forceinline__ T blk_log(T a) { if constexpr (sizeof(T) == 4) return logf(a); else return log(a); }
 
-__host__ __device__ __forceinline__ size_t tri_off(int i) { return (size_t)i * (i + 1) / 2; }
+// Row i of the packed lower triangle (length i + 1; row n is y, length n) starts at off(i), with
+// gaps so that off(i + 1) = off(i) + 17 (mod 32): the threads of a warp read the same column k of
+// 32 consecutive rows, which then fall in 32 different banks (17 is odd).
+__host__ __device__ __forceinline__ int row_gap(int i) { return (17 - (i + 1)) & 31; }
+__host__ __device__ __forceinline__ size_t gpreg_rows_elems(int n) {
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) off += (size_t)(i + 1) + row_gap(i);
+  return off + (size_t)n;  // the y row
+}
 
-// Shared-memory elements one chain needs: the packed lower triangle (n (n + 1) / 2), the y row
-// (n), the column vector v, the pivots d and the running sums s (n each).
-__host__ __device__ __forceinline__ size_t gpreg_smem_elems(int n) { return tri_off(n) + 4 * (size_t)n; }
+// Shared-memory bytes one chain needs: the rows, the column vector v, the pivots d and the
+// running sums s (n elements each), and the row offsets (n + 1 ints).
+template <typename T>
+__host__ __device__ __forceinline__ size_t gpreg_smem_bytes(int n) {
+  return (gpreg_rows_elems(n) + 3 * (size_t)n) * sizeof(T) + ((size_t)n + 1) * sizeof(int);
+}
 
 template <int WPC>
 __device__ __forceinline__ void cta_sync() {
@@ -48,16 +59,16 @@ __device__ __forceinline__ void cta_sync() {
 // (so d_j needs no reduction).  Storage: M[i][j] = L_ij, d and s in their own arrays.  Every
 // thread returns the same value.
 template <typename T, int WPC>
-__device__ T gpreg_loglik_cta(const TargetView<T>& tg, const T (&x)[kBlkE], T* M, T* red) {
+__device__ T gpreg_loglik_cta(const TargetView<T>& tg, const T (&x)[kBlkE], T* M, const int* off, T* red) {
   constexpr int NT = 32 * WPC;
   const int n = tg.n_data, tid = threadIdx.x;
   const T s2 = x[0] * x[0], t2 = x[1] * x[1], l2 = x[2] * x[2];
-  T* ry = M + tri_off(n);  // the y row
+  T* ry = M + off[n];      // the y row
   T* V = ry + n;           // v of the current column
   T* Dp = V + n;           // pivots d
   T* S = Dp + n;           // s_i
   for (int i = 0; i < n; ++i) {
-    T* ri = M + tri_off(i);
+    T* ri = M + off[i];
     const T* Dr = tg.X + (size_t)i * n;
     for (int j = tid; j <= i; j += NT) ri[j] = t2 * blk_exp<T>(-l2 * Dr[j]) + (i == j ? s2 : T(0));
   }
@@ -69,7 +80,7 @@ __device__ T gpreg_loglik_cta(const TargetView<T>& tg, const T (&x)[kBlkE], T* M
   T quad = T(0);
   bool pd = true;
   for (int j = 0; j < n; ++j) {
-    const T* rj = M + tri_off(j);
+    const T* rj = M + off[j];
     const T dj = rj[j] - S[j];  // the same smem values in every thread
     if (!(dj > T(0))) { pd = false; break; }
     const T inv = T(1) / dj;
@@ -77,7 +88,7 @@ __device__ T gpreg_loglik_cta(const TargetView<T>& tg, const T (&x)[kBlkE], T* M
     if (tid == 0) Dp[j] = dj;
     cta_sync<WPC>();  // V complete
     for (int i = j + 1 + tid; i <= n; i += NT) {
-      T* ri = i < n ? M + tri_off(i) : ry;
+      T* ri = M + off[i];  // row n is y
       T a0 = ri[j], a1 = T(0), a2 = T(0), a3 = T(0);
       int k = 0;
       for (; k + 4 <= j; k += 4) {
@@ -153,7 +164,8 @@ __device__ __forceinline__ void blk_store(const EssBlockView<T>& v, int64_t c, c
 // bracket, next angle), the likelihood at the proposal, and DONE when it clears the threshold.
 // Returns true while the chain stays in SHRINK.
 template <typename T, int WPC>
-__device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, T* M, T* red, int& err) {
+__device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, T* M, const int* off, T* red,
+                         int& err) {
   const int d = v.tg.d;
   const bool lead = threadIdx.x == 0;
   const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
@@ -185,7 +197,7 @@ __device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, T*
   ess_sincos<T>(s.th, sn, cs);
 #pragma unroll
   for (int e = 0; e < kBlkE; ++e) xp[e] = fma(s.x[e], cs, s.nu[e] * sn);
-  T ellp = gpreg_loglik_cta<T, WPC>(v.tg, xp, M, red);
+  T ellp = gpreg_loglik_cta<T, WPC>(v.tg, xp, M, off, red);
   if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
   const bool accept = ellp > s.logy;
   if (accept || s.s >= kMaxShrinks) {
@@ -224,12 +236,28 @@ __device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, T*
   return true;
 }
 
+// The chain's matrix at the start of shared memory, the row offsets after the T arrays.
+template <typename T, int WPC>
+__device__ __forceinline__ void blk_layout(const EssBlockView<T>& v, unsigned char* raw, T*& M, int*& off) {
+  const int n = v.tg.n_data;
+  M = (T*)raw;
+  off = (int*)(raw + (gpreg_rows_elems(n) + 3 * (size_t)n) * sizeof(T));
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int i = 0; i < n; ++i) { off[i] = o; o += i + 1 + row_gap(i); }
+    off[n] = o;
+  }
+  cta_sync<WPC>();
+}
+
 template <typename T, int WPC>
 __global__ void __launch_bounds__(32 * WPC) ess_block_fsm_kernel(EssBlockView<T> v, int budget) {
   extern __shared__ __align__(16) unsigned char blk_smem[];
   __shared__ T red[2 * WPC];
   __shared__ unsigned cur;
-  T* M = (T*)blk_smem;
+  T* M;
+  int* off;
+  blk_layout<T, WPC>(v, blk_smem, M, off);
   int err = 0;
   for (;;) {
     if (threadIdx.x == 0) cur = atomicAdd(v.work, 1u);
@@ -241,7 +269,7 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_fsm_kernel(EssBlockView<T>
     blk_load<T>(v, c, s);
     int steps = 0;
     for (int b = 0; b < budget && s.t < v.n; ++b) {
-      blk_step<T, WPC>(v, c, s, M, red, err);
+      blk_step<T, WPC>(v, c, s, M, off, red, err);
       ++steps;
     }
     blk_store<T>(v, c, s);
@@ -259,7 +287,9 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_sync_kernel(EssBlockView<T
                                                                   unsigned long long* iterations) {
   extern __shared__ __align__(16) unsigned char blk_smem[];
   __shared__ T red[2 * WPC];
-  T* M = (T*)blk_smem;
+  T* M;
+  int* off;
+  blk_layout<T, WPC>(v, blk_smem, M, off);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int iter = 0, err = 0;
   for (int t = t_begin; t < t_end; ++t) {
@@ -270,7 +300,7 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_sync_kernel(EssBlockView<T
         cta_sync<WPC>();  // every thread has read k[c] before thread 0 may store it
         BlkChain<T> s;
         blk_load<T>(v, c, s);
-        const bool more = blk_step<T, WPC>(v, c, s, M, red, err);
+        const bool more = blk_step<T, WPC>(v, c, s, M, off, red, err);
         blk_store<T>(v, c, s);
         if (threadIdx.x == 0) v.steps[c] += 1;
         mine += more ? 1u : 0u;
@@ -295,13 +325,15 @@ template <typename T, int WPC>
 __global__ void __launch_bounds__(32 * WPC) ess_block_init_kernel(EssBlockView<T> v) {
   extern __shared__ __align__(16) unsigned char blk_smem[];
   __shared__ T red[2 * WPC];
-  T* M = (T*)blk_smem;
+  T* M;
+  int* off;
+  blk_layout<T, WPC>(v, blk_smem, M, off);
   const int d = v.tg.d;
   for (int64_t c = blockIdx.x; c < v.m; c += gridDim.x) {
     T x[kBlkE];
 #pragma unroll
     for (int e = 0; e < kBlkE; ++e) x[e] = e < d ? v.x[(size_t)c * d + e] : T(0);
-    T ell = gpreg_loglik_cta<T, WPC>(v.tg, x, M, red);
+    T ell = gpreg_loglik_cta<T, WPC>(v.tg, x, M, off, red);
     if (threadIdx.x == 0) {
       if (!(ell == ell)) { ell = neg_inf<T>(); atomicOr(v.err, ERR_NONFINITE); }
       v.ell[c] = ell;
@@ -333,7 +365,7 @@ static int blk_wpc(int64_t m, int sms) {
 template <typename T, int WPC>
 static cudaError_t fsm_launch(const EssBlockView<T>& v, int budget, cudaStream_t st) {
   auto kern = ess_block_fsm_kernel<T, WPC>;
-  const size_t smem = gpreg_smem_elems(v.tg.n_data) * sizeof(T);
+  const size_t smem = gpreg_smem_bytes<T>(v.tg.n_data);
   int per_sm = 0, sms = 0;
   cudaError_t e = blk_prepare(kern, 32 * WPC, smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;
@@ -348,7 +380,7 @@ template <typename T, int WPC>
 static cudaError_t sync_launch(const EssBlockView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
                                unsigned long long* iters, cudaStream_t st) {
   auto kern = ess_block_sync_kernel<T, WPC>;
-  const size_t smem = gpreg_smem_elems(v.tg.n_data) * sizeof(T);
+  const size_t smem = gpreg_smem_bytes<T>(v.tg.n_data);
   int per_sm = 0, sms = 0;
   cudaError_t e = blk_prepare(kern, 32 * WPC, smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;
@@ -361,7 +393,7 @@ static cudaError_t sync_launch(const EssBlockView<T>& v, int t0, int t1, GridBar
 template <typename T, int WPC>
 static cudaError_t init_launch(const EssBlockView<T>& v, cudaStream_t st) {
   auto kern = ess_block_init_kernel<T, WPC>;
-  const size_t smem = gpreg_smem_elems(v.tg.n_data) * sizeof(T);
+  const size_t smem = gpreg_smem_bytes<T>(v.tg.n_data);
   int per_sm = 0, sms = 0;
   cudaError_t e = blk_prepare(kern, 32 * WPC, smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;

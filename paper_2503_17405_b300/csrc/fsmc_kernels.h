@@ -127,7 +127,7 @@ cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st);
 
 // GP_REG likelihood in shared memory (the packed lower triangle): n <= kGpRegMaxN32 (FP32) /
 // kGpRegMaxN64 (FP64).
-constexpr int kGpRegMaxN32 = 336, kGpRegMaxN64 = 232;
+constexpr int kGpRegMaxN32 = 319, kGpRegMaxN64 = 220;
 template <typename T>
 cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, int sms, cudaStream_t st);
 template <typename T>

@@ -27,7 +27,7 @@ def _job(eng, w, x0, n, prec, mode, tuning=None, seed=2):
     return job
 
 
-@pytest.mark.parametrize("n_data", [25, 100, 231])
+@pytest.mark.parametrize("n_data", [25, 100, 219])
 @pytest.mark.parametrize("mode", ["fsm", "sync"])
 def test_fp64_matches_oracle(eng, n_data, mode):
     w = W.gp_reg(n_data)
@@ -58,7 +58,7 @@ def test_fp32_fsm_equals_sync_and_partial_runs(eng):
         j.close()
 
 
-@pytest.mark.parametrize("n_data", [25, 100, 336])
+@pytest.mark.parametrize("n_data", [25, 100, 319])
 def test_fp32_transition_by_transition_against_the_oracle(eng, n_data):
     w = W.gp_reg(n_data)
     x0 = W.x0_gp_reg(w, 32).astype(np.float32).astype(np.float64)
@@ -79,16 +79,16 @@ def test_fp32_transition_by_transition_against_the_oracle(eng, n_data):
 
 def test_limits_and_argument_checks(eng):
     from paper_2503_17405_b300 import fsmc
-    w = W.gp_reg(233)
-    tg = eng.target("gp_reg", 3, w["params"], n_data=233)
+    w = W.gp_reg(221)
+    tg = eng.target("gp_reg", 3, w["params"], n_data=221)
     with pytest.raises(fsmc.FsmcError):
-        eng.job(tg, "ess", 4, 4, prec="fp64")                     # FP64 covariance over 232 rows
+        eng.job(tg, "ess", 4, 4, prec="fp64")                     # FP64 covariance over 220 rows
     job = eng.job(tg, "ess", 4, 4, x0=W.x0_gp_reg(w, 4), prec="fp32")
     job.run("fsm")
     job.close()
-    big = W.gp_reg(337)
+    big = W.gp_reg(320)
     with pytest.raises(fsmc.FsmcError):
-        eng.target("gp_reg", 3, big["params"], n_data=337)        # over the shared-memory limit
+        eng.target("gp_reg", 3, big["params"], n_data=320)        # over the shared-memory limit
     w = W.gp_reg(25)
     with pytest.raises(fsmc.FsmcError):
         eng.target("gp_reg", 2, w["params"][1:], n_data=25)      # d must be 3
