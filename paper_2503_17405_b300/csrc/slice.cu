@@ -44,27 +44,37 @@ __device__ __forceinline__ T slice_threshold(T lp, T log_u) {
   return logy;
 }
 
+// The random numbers a sample's INIT-E needs -- blocks 0..D-1 (the normals z), D (threshold and
+// V) and D+1 (V') of its stream -- drawn ahead of time, one block per FSM step, while the chain
+// is still busy with the previous sample: INIT-E then runs in the few threads of a warp whose
+// chains just finished a sample, and only the blocks not yet drawn are left for it.  The values
+// are those the blocks give whenever they are drawn.
 template <typename T, int E>
-__device__ __forceinline__ void slice_direction(const SliceView<T>& v, const Key& key, int t, T (&u)[E]) {
-  const int d = v.tg.d;
-  const int D = (d + 3) / 4;
-  T ss = T(0);
+struct SlicePrefetch {
+  T z[E];
+  uint32_t w[6];  // block D words 0-3, block D+1 words 0-1
+  int q;          // blocks drawn so far
+};
+
+template <typename T, int E>
+__device__ __forceinline__ void slice_draw_block(const Key& key, int t, int D, SlicePrefetch<T, E>& pf) {
+  const P4 b = key.block((uint32_t)t, 0, (uint32_t)pf.q);
+  if (pf.q < D) {
+    T z[4];
+    Conv<T>::normal_quad(b, z);
 #pragma unroll
-  for (int q = 0; q < (E + 3) / 4; ++q) {
-    T z[4] = {T(0), T(0), T(0), T(0)};
-    if (q < D) Conv<T>::normal_quad(key.block((uint32_t)t, 0, (uint32_t)q), z);
+    for (int qq = 0; qq < (E + 3) / 4; ++qq)
+      if (qq == pf.q) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = 4 * q + i;
-      if (e < E) {
-        u[e] = e < d ? z[i] : T(0);
-        ss = fma(u[e], u[e], ss);
+        for (int i = 0; i < 4; ++i)
+          if (4 * qq + i < E) pf.z[4 * qq + i] = z[i];
       }
-    }
+  } else if (pf.q == D) {
+    pf.w[0] = b.w0; pf.w[1] = b.w1; pf.w[2] = b.w2; pf.w[3] = b.w3;
+  } else {
+    pf.w[4] = b.w0; pf.w[5] = b.w1;
   }
-  const T nrm = sqrt(ss);
-#pragma unroll
-  for (int e = 0; e < E; ++e) u[e] = u[e] / nrm;
+  ++pf.q;
 }
 
 // INIT-S / the next SHRINK proposal: theta ~ U(L, R) from draw D + 2 + s.
@@ -83,20 +93,31 @@ __device__ __forceinline__ void slice_after_left(const SliceView<T>& v, const Ke
   else slice_propose<T, E>(v, key, c);
 }
 
-// INIT-E: direction, threshold, initial interval and the stepping-out budgets of sample c.t.
+// INIT-E: direction, threshold, initial interval and the stepping-out budgets of sample c.t, from
+// the prefetched blocks of that sample (the missing ones drawn here); pf then starts on c.t + 1.
 template <typename T, int E>
-__device__ __forceinline__ void slice_begin(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c) {
-  const int D = (v.tg.d + 3) / 4;
-  slice_direction<T, E>(v, key, c.t, c.u);
-  const P4 b = key.block((uint32_t)c.t, 0, (uint32_t)D);
-  c.logy = slice_threshold<T>(c.lp, Conv<T>::log_u(b.w0, b.w1));
-  c.L = -v.w * Conv<T>::u(b.w2, b.w3);
+__device__ __forceinline__ void slice_begin(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c,
+                                            SlicePrefetch<T, E>& pf) {
+  const int d = v.tg.d;
+  const int D = (d + 3) / 4;
+  while (pf.q < D + 2) slice_draw_block<T, E>(key, c.t, D, pf);
+  T ss = T(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    c.u[e] = e < d ? pf.z[e] : T(0);
+    ss = fma(c.u[e], c.u[e], ss);
+  }
+  const T rn = T(1) / sqrt(ss);
+#pragma unroll
+  for (int e = 0; e < E; ++e) c.u[e] *= rn;
+  c.logy = slice_threshold<T>(c.lp, Conv<T>::log_u(pf.w[0], pf.w[1]));
+  c.L = -v.w * Conv<T>::u(pf.w[2], pf.w[3]);
   c.R = c.L + v.w;
-  const P4 bj = key.block((uint32_t)c.t, 0, (uint32_t)(D + 1));
-  c.J = (int)floor((double)v.mlim * (double)Conv<T>::u(bj.w0, bj.w1));
+  c.J = min((int)floor(T(v.mlim) * Conv<T>::u(pf.w[4], pf.w[5])), v.mlim - 1);
   c.K = v.mlim - 1 - c.J;
   c.s = 0;
   c.nev = 0;
+  pf.q = 0;
   if (c.J > 0) c.k = SL_LEFT;
   else slice_after_left<T, E>(v, key, c);
 }
@@ -197,14 +218,18 @@ __global__ void __launch_bounds__(256) slice_fsm_kernel(SliceView<T> v, int budg
     slice_load<T, E>(v, c, s);
     if (s.t >= v.n) continue;
     const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    const int D = (v.tg.d + 3) / 4;
     int err = 0, steps = 0;
-    if (s.k == SL_START) slice_begin<T, E>(v, key, s);
+    SlicePrefetch<T, E> pf;
+    pf.q = 0;  // for sample t if it has not started, else for t + 1
+    if (s.k == SL_START) slice_begin<T, E>(v, key, s, pf);
     for (int b = 0; b < budget; ++b) {
       ++steps;
+      if (pf.q < D + 2 && s.t + 1 < v.n) slice_draw_block<T, E>(key, s.t + 1, D, pf);
       if (slice_step<T, E>(v, key, s, err)) {
         slice_finish<T, E>(v, c, s);
         if (s.t == v.n) { s.k = SL_DONE; break; }
-        slice_begin<T, E>(v, key, s);
+        slice_begin<T, E>(v, key, s, pf);
       }
     }
     slice_store<T, E>(v, c, s);
@@ -230,7 +255,9 @@ __global__ void __launch_bounds__(256) slice_sync_kernel(SliceView<T> v, int t_b
       SliceChain<T, E> s;
       slice_load<T, E>(v, c, s);
       const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
-      slice_begin<T, E>(v, key, s);
+      SlicePrefetch<T, E> pf;
+      pf.q = 0;
+      slice_begin<T, E>(v, key, s, pf);
       slice_store<T, E>(v, c, s);
     }
     for (int phase = SL_LEFT; phase <= SL_PROP; ++phase) {
