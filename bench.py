@@ -355,20 +355,32 @@ def run_ours(args, rank, world):
                             else "latency: one chain per warp, shuffle reductions per component and U-turn test"}[cfg["algo"]]}
 
     # end to end through the public API: host params and x0 in, posterior moments out
+    # every step: target and job created from pinned host arrays (params, x0), the whole run, the
+    # per-chain moments read back into pinned host arrays, the job closed; one untimed warm-up
     e2e = None
     if not args.no_e2e:
         params_h = torch.from_numpy(np.ascontiguousarray(w["params"], dtype=np.float64)).pin_memory()
         x0_h = torch.from_numpy(np.ascontiguousarray(cfg["x0"], dtype=np.float64)).pin_memory()
+        sx = torch.empty((m, w["d"]), dtype=torch.float64).pin_memory().numpy()
+        sx2 = torch.empty((m, w["d"]), dtype=torch.float64).pin_memory().numpy()
+        nk = torch.empty((m,), dtype=torch.int64).pin_memory().numpy()
+
+        def e2e_step():
+            tg2 = eng.target(w["kind"], w["d"], params_h.numpy(), n_data=w["n_data"])
+            job2 = eng.job(tg2, cfg["algo"], m, n, x0=x0_h.numpy(), seed=1 + rank, prec=cfg["prec"],
+                           store=True, dr=dr, nuts=nuts, tuning=parse_tuning(args.tuning) or None, slice=sl)
+            job2.run("fsm", stream=sp)
+            job2.moments(sx, sx2, nk)
+            job2.close()
+            tg2.close()
+
+        e2e_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tg2 = eng.target(w["kind"], w["d"], params_h.numpy(), n_data=w["n_data"])
-        job2 = eng.job(tg2, cfg["algo"], m, n, x0=x0_h.numpy(), seed=1 + rank, prec=cfg["prec"],
-                       store=True, dr=dr, nuts=nuts, tuning=parse_tuning(args.tuning) or None, slice=sl)
-        job2.run("fsm", stream=sp)
-        sx, sx2, nk = job2.moments()
+        for _ in range(args.steps):
+            e2e_step()
         t1 = time.perf_counter()
-        job2.close()
-        e2e = {"value": m * n / (t1 - t0), "unit": "samples/s",
+        e2e = {"value": m * n * args.steps / (t1 - t0), "unit": "samples/s",
                "h2d_bytes_per_step": int(params_h.numel() * 8 + x0_h.numel() * 8),
                "d2h_bytes_per_step": int(sx.nbytes + sx2.nbytes + nk.nbytes)}
     out = None

@@ -53,6 +53,8 @@ extern "C" fsmc_status fsmc_engine_create(int device, size_t hbm_budget_bytes, f
   return FSMC_OK;
 }
 
+static void arena_trim(fsmc_engine* e);
+
 extern "C" void fsmc_engine_destroy(fsmc_engine* e) {
   if (!e) return;
   serving_shutdown(e);
@@ -65,6 +67,7 @@ extern "C" void fsmc_engine_destroy(fsmc_engine* e) {
   }
   for (auto* j : jobs) fsmc_job_destroy(j);
   for (auto* t : tgts) fsmc_target_destroy(t);
+  arena_trim(e);
   delete e;
 }
 
@@ -72,6 +75,48 @@ extern "C" size_t fsmc_engine_bytes_in_use(const fsmc_engine* e) {
   if (!e) return 0;
   std::lock_guard<std::mutex> g(e->mu);
   return e->in_use;
+}
+
+// Device blocks of destroyed jobs are kept (at most two) and handed to the next job they fit
+// (up to twice its size): back-to-back jobs then skip cudaMalloc and cudaFree of their arenas.
+static void arena_trim(fsmc_engine* e) {
+  std::lock_guard<std::mutex> g(e->mu);
+  for (auto& b : e->spare) cudaFree(b.first);
+  e->spare.clear();
+}
+
+static cudaError_t arena_take(fsmc_engine* e, size_t bytes, char** out, size_t* got) {
+  {
+    std::lock_guard<std::mutex> g(e->mu);
+    int best = -1;
+    for (int i = 0; i < (int)e->spare.size(); ++i) {
+      const size_t sz = e->spare[i].second;
+      if (sz >= bytes && sz <= 2 * bytes && (best < 0 || sz < e->spare[best].second)) best = i;
+    }
+    if (best >= 0) {
+      *out = e->spare[best].first;
+      *got = e->spare[best].second;
+      e->spare.erase(e->spare.begin() + best);
+      return cudaSuccess;
+    }
+  }
+  cudaError_t ce = cudaMalloc((void**)out, bytes);
+  if (ce != cudaSuccess) {  // the cached blocks may be what is missing
+    cudaGetLastError();
+    arena_trim(e);
+    ce = cudaMalloc((void**)out, bytes);
+  }
+  if (ce == cudaSuccess) *got = bytes;
+  return ce;
+}
+
+static void arena_give(fsmc_engine* e, char* p, size_t bytes) {
+  std::lock_guard<std::mutex> g(e->mu);
+  e->spare.emplace_back(p, bytes);
+  while (e->spare.size() > 2) {
+    cudaFree(e->spare.front().first);
+    e->spare.erase(e->spare.begin());
+  }
 }
 
 bool engine_reserve(fsmc_engine* e, size_t bytes) {
@@ -346,7 +391,8 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
   j->o_err = L.take(4);
   j->o_done = L.take(4);
   j->o_out = j->store ? L.take(m * n * d * es) : 0;
-  j->o_mom = j->store ? 0 : L.take(4 * m * d * es);
+  j->o_mom = L.take(4 * m * d * es);  // running sums (moments-only jobs) or their reduction
+  j->o_momd = L.take(2 * m * d * 8);  // the sums as doubles, for the host read
   j->o_bar = L.take(64);
   j->o_iters = L.take(8);
   if (ess_block(j)) {
@@ -394,7 +440,7 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
              j->bytes, j->e->budget, fsmc_engine_bytes_in_use(j->e));
     return fsmc_fail(FSMC_EADMIT, msg);
   }
-  cudaError_t ce = cudaMalloc((void**)&j->dev, j->bytes);
+  cudaError_t ce = arena_take(j->e, j->bytes, &j->dev, &j->arena_bytes);
   if (ce != cudaSuccess) {
     engine_release(j->e, j->bytes);
     j->dev = nullptr;
@@ -1101,32 +1147,24 @@ extern "C" fsmc_status fsmc_read_moments(fsmc_job* j, double* sx, double* sx2, i
   std::vector<int> t((size_t)j->m);
   CK(cudaMemcpy(t.data(), j->dev + j->o_t, t.size() * 4, cudaMemcpyDeviceToHost));
   if (n_kept) for (size_t c = 0; c < t.size(); ++c) n_kept[c] = t[c];
-  if (j->store) {
-    // reduce the stored samples on the device into a temporary [4][m][d] buffer
-    void* tmp = nullptr;
-    CK(cudaMalloc(&tmp, 4 * md * es));
+  (void)es;
+  char* m0 = j->dev + j->o_mom;
+  if (j->store) {  // reduce the stored samples on the device into the [4][m][d] buffer
     cudaError_t ce = j->prec == FSMC_FP64
         ? launch_moments_from_samples<double>((const double*)(j->dev + j->o_out), (const int*)(j->dev + j->o_t),
-                                              j->m, (int)j->n, j->d, (double*)tmp, 0)
+                                              j->m, (int)j->n, j->d, (double*)m0, 0)
         : launch_moments_from_samples<float>((const float*)(j->dev + j->o_out), (const int*)(j->dev + j->o_t),
-                                             j->m, (int)j->n, j->d, (float*)tmp, 0);
-    fsmc_status s = FSMC_OK;
-    if (ce != cudaSuccess) s = fsmc_cuda_fail(ce, "moments kernel");
-    if (s == FSMC_OK && sx)
-      s = j->prec == FSMC_FP64 ? read_vec<double>((const char*)tmp, md, sx) : read_vec<float>((const char*)tmp, md, sx);
-    if (s == FSMC_OK && sx2)
-      s = j->prec == FSMC_FP64 ? read_vec<double>((const char*)tmp + 2 * md * es, md, sx2)
-                               : read_vec<float>((const char*)tmp + 2 * md * es, md, sx2);
-    cudaFree(tmp);
-    return s;
+                                             j->m, (int)j->n, j->d, (float*)m0, 0);
+    if (ce != cudaSuccess) return fsmc_cuda_fail(ce, "moments kernel");
   }
-  const char* m0 = j->dev + j->o_mom;
-  fsmc_status s = FSMC_OK;
-  if (sx) s = j->prec == FSMC_FP64 ? read_vec<double>(m0, md, sx) : read_vec<float>(m0, md, sx);
-  if (s == FSMC_OK && sx2)
-    s = j->prec == FSMC_FP64 ? read_vec<double>(m0 + 2 * md * es, md, sx2)
-                             : read_vec<float>(m0 + 2 * md * es, md, sx2);
-  return s;
+  // converted to double on the device, then copied straight into the caller's buffers (fast
+  // when they are pinned)
+  double* md2 = (double*)(j->dev + j->o_momd);
+  CK(j->prec == FSMC_FP64 ? launch_moments_to_double<double>((const double*)m0, (int64_t)md, md2, 0)
+                          : launch_moments_to_double<float>((const float*)m0, (int64_t)md, md2, 0));
+  if (sx) CK(cudaMemcpy(sx, md2, md * 8, cudaMemcpyDeviceToHost));
+  if (sx2) CK(cudaMemcpy(sx2, md2 + md, md * 8, cudaMemcpyDeviceToHost));
+  return FSMC_OK;
 }
 
 extern "C" fsmc_status fsmc_read_stats(fsmc_job* j, fsmc_stats* o) {
@@ -1284,7 +1322,10 @@ extern "C" void fsmc_job_destroy(fsmc_job* j) {
   if (j->side) cudaStreamDestroy(j->side);
   if (j->dev) {
     cudaSetDevice(e->device);
-    cudaFree(j->dev);
+    // a job run through fsmc_job_run has no work in flight; one the scheduler ran is freed
+    // (cudaFree waits for the device)
+    if (j->submitted) cudaFree(j->dev);
+    else arena_give(e, j->dev, j->arena_bytes);
     engine_release(e, j->bytes);
   }
   {

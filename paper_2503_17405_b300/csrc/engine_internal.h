@@ -22,6 +22,7 @@ struct fsmc_engine {
   size_t in_use = 0;
   mutable std::mutex mu;
   std::vector<fsmc_job*> jobs;        // materialised jobs (hold device memory)
+  std::vector<std::pair<char*, size_t>> spare;  // device blocks of destroyed jobs, kept for reuse
   std::vector<fsmc_target*> targets;
   // serving scheduler
   std::thread sched;
@@ -91,6 +92,8 @@ struct fsmc_job {
   size_t o_win = 0;  // second refill-window buffer [2][m]
   size_t o_colbase = 0, o_colmap = 0;  // compacted refill list: [m+1] prefix sums, [m*W] (chain, sample)
   size_t o_work = 0;  // block-likelihood ESS: chain counter of the current FSM launch
+  size_t o_momd = 0;  // [2][m][d] doubles: the moment sums for the host read
+  size_t arena_bytes = 0;  // size of the device block behind dev (>= bytes when reused)
   // serving
   bool submitted = false;
   fsmc_mode serve_mode = FSMC_MODE_FSM;

@@ -757,6 +757,23 @@ cudaError_t launch_moments_from_samples(const T* samples, const int* t, int64_t 
 }
 template cudaError_t launch_moments_from_samples<float>(const float*, const int*, int64_t, int, int, float*,
                                                         cudaStream_t);
+
+// The sums of x and x^2 ([4][m d] running sums with their compensations) as doubles, [2][m d].
+template <typename T>
+__global__ void moments_to_double_kernel(const T* mom, int64_t md, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= md) return;
+  out[i] = (double)mom[i];
+  out[md + i] = (double)mom[2 * md + i];
+}
+
+template <typename T>
+cudaError_t launch_moments_to_double(const T* mom, int64_t md, double* out, cudaStream_t st) {
+  moments_to_double_kernel<T><<<(unsigned)((md + 255) / 256), 256, 0, st>>>(mom, md, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_moments_to_double<float>(const float*, int64_t, double*, cudaStream_t);
+template cudaError_t launch_moments_to_double<double>(const double*, int64_t, double*, cudaStream_t);
 template cudaError_t launch_moments_from_samples<double>(const double*, const int*, int64_t, int, int, double*,
                                                          cudaStream_t);
 

@@ -154,5 +154,8 @@ cudaError_t launch_ess_window(const EssView<T>& v, const int* hi_cur, cudaStream
 template <typename T>
 cudaError_t launch_moments_from_samples(const T* samples, const int* t, int64_t m, int n, int d, T* out,
                                         cudaStream_t st);
+// Sums of x and x^2 from the [4][md] moment buffer as doubles into out [2][md].
+template <typename T>
+cudaError_t launch_moments_to_double(const T* mom, int64_t md, double* out, cudaStream_t st);
 
 }  // namespace fsmc

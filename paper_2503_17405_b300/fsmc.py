@@ -207,6 +207,14 @@ class Target:
                                          _p(p) if p.size else None, p.size, ctypes.byref(self._h)))
         engine._objs.append(self)
 
+    def close(self):
+        """Frees the target's device copies (jobs on it must be closed first)."""
+        if self._h:
+            load().fsmc_target_destroy(self._h)
+            self._h = _vp()
+            if self in self.engine._objs:
+                self.engine._objs.remove(self)
+
 
 class Job:
     def __init__(self, engine, target, algo, n_chains, n_samples, x0, seed, prec, store, dr, nuts,
@@ -286,10 +294,16 @@ class Job:
         _check(load().fsmc_read_state(self._h, _p(x)))
         return x
 
-    def moments(self):
-        sx = np.zeros((self.m, self.d))
-        sx2 = np.zeros((self.m, self.d))
-        nk = np.zeros(self.m, dtype=np.int64)
+    def moments(self, sx=None, sx2=None, nk=None):
+        """Per-chain sums of x and x^2 over the samples so far, and the sample counts.  Callers
+        may pass their own (e.g. pinned) float64 / int64 arrays of shapes [m, d], [m, d], [m]."""
+        sx = np.zeros((self.m, self.d)) if sx is None else sx
+        sx2 = np.zeros((self.m, self.d)) if sx2 is None else sx2
+        nk = np.zeros(self.m, dtype=np.int64) if nk is None else nk
+        for a, shape, dt in ((sx, (self.m, self.d), np.float64), (sx2, (self.m, self.d), np.float64),
+                             (nk, (self.m,), np.int64)):
+            if a.shape != shape or a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("moments: output arrays must be C-contiguous %s of shape %s" % (dt, shape))
         _check(load().fsmc_read_moments(self._h, _p(sx), _p(sx2), _p(nk, _lp)))
         return sx, sx2, nk
 
@@ -322,6 +336,8 @@ class Job:
         if self._h:
             load().fsmc_job_destroy(self._h)
             self._h = _vp()
+            if self in self.engine._objs:
+                self.engine._objs.remove(self)
 
 
 def ess_run_static(kind, d, L_ptr, vec_ptr, noise_var, n_chains, n_samples, x0_ptr, seed,
