@@ -185,7 +185,8 @@ void fsmc_target_destroy(fsmc_target* t);
  * m = n_chains chains of `algo` on target t, n_samples samples each (Alg. 3 / Alg. 7).
  * algo_params: NULL for ESS, const fsmc_dr_params* for DR, const fsmc_nuts_params* for NUTS,
  * const fsmc_slice_params* for SLICE (NULL: w = 1, m = 100).  DR and SLICE: d <= 32.
- * x0_host: [n_chains][d] starting points (NULL = zeros).  seed keys the random numbers:
+ * x0_host: [n_chains][d] starting points (NULL = zeros), copied to device memory before the
+ * call returns (one DMA when the buffer is pinned).  seed keys the random numbers:
  * chain j, sample i, draw q use Philox4x32-10 with key (j, seed_lo) and counter
  * (q, i, tag, seed_hi).  store_samples: 1 keeps every sample on the device
  * (n_chains*n_samples*d values), 0 keeps per-chain running sums of x and x^2 only.

@@ -77,8 +77,9 @@ extern "C" size_t fsmc_engine_bytes_in_use(const fsmc_engine* e) {
   return e->in_use;
 }
 
-// Device blocks of destroyed jobs are kept (at most two) and handed to the next job they fit
-// (up to twice its size): back-to-back jobs then skip cudaMalloc and cudaFree of their arenas.
+// Device blocks of destroyed jobs (arenas and starting points) are kept, at most four, and handed
+// to the next job they fit (up to twice its size): back-to-back jobs then skip cudaMalloc and
+// cudaFree.
 static void arena_trim(fsmc_engine* e) {
   std::lock_guard<std::mutex> g(e->mu);
   for (auto& b : e->spare) cudaFree(b.first);
@@ -113,7 +114,7 @@ static cudaError_t arena_take(fsmc_engine* e, size_t bytes, char** out, size_t* 
 static void arena_give(fsmc_engine* e, char* p, size_t bytes) {
   std::lock_guard<std::mutex> g(e->mu);
   e->spare.emplace_back(p, bytes);
-  while (e->spare.size() > 2) {
+  while (e->spare.size() > 4) {
     cudaFree(e->spare.front().first);
     e->spare.erase(e->spare.begin());
   }
@@ -564,9 +565,7 @@ template <typename T>
 static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
   char* b = j->dev;
   const size_t m = (size_t)j->m, d = (size_t)j->d;
-  std::vector<T> hx(m * d);
-  for (size_t i = 0; i < m * d; ++i) hx[i] = (T)j->x0[i];
-  CK(cudaMemcpyAsync(b + j->o_x, hx.data(), m * d * sizeof(T), cudaMemcpyHostToDevice, st));
+  CK(launch_from_double<T>((const double*)j->x0_dev, (int64_t)(m * d), (T*)(b + j->o_x), st));
   CK(cudaMemsetAsync(b + j->o_t, 0, m * 4, st));
   CK(cudaMemsetAsync(b + j->o_counts, 0xff, m * (size_t)j->n * 4, st));
   CK(cudaMemsetAsync(b + j->o_steps, 0, m * 8, st));
@@ -669,8 +668,19 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
       return fsmc_fail(FSMC_EINVAL, "NUTS params: eps > 0, 1 <= max_depth <= 10, max_dH > 0");
     }
   }
-  j->x0.assign((size_t)n_chains * t->d, 0.0);
-  if (x0_host) std::copy(x0_host, x0_host + (size_t)n_chains * t->d, j->x0.begin());
+  {  // the starting points go to the device now (one copy; fast from pinned memory)
+    const size_t xb = (size_t)n_chains * t->d * sizeof(double);
+    CK(cudaSetDevice(e->device));
+    cudaError_t ce = arena_take(e, xb, &j->x0_dev, &j->x0_block);
+    if (ce == cudaSuccess)
+      ce = x0_host ? cudaMemcpy(j->x0_dev, x0_host, xb, cudaMemcpyHostToDevice) : cudaMemset(j->x0_dev, 0, xb);
+    if (ce != cudaSuccess) {
+      if (j->x0_dev) arena_give(e, j->x0_dev, j->x0_block);
+      delete j;
+      cudaGetLastError();
+      return fsmc_fail(FSMC_ENOMEM, std::string("starting points: ") + cudaGetErrorString(ce));
+    }
+  }
   default_tuning(j);
   {
     std::lock_guard<std::mutex> g(e->mu);
@@ -1132,7 +1142,7 @@ static fsmc_status read_vec(const char* src, size_t n, double* dst) {
 extern "C" fsmc_status fsmc_read_state(fsmc_job* j, double* x) {
   if (!j || !x) return fsmc_fail(FSMC_EINVAL, "NULL argument");
   if (!j->dev) {
-    std::copy(j->x0.begin(), j->x0.end(), x);
+    CK(cudaMemcpy(x, j->x0_dev, (size_t)j->m * j->d * sizeof(double), cudaMemcpyDeviceToHost));
     return FSMC_OK;
   }
   const size_t n = (size_t)j->m * j->d;
@@ -1327,6 +1337,11 @@ extern "C" void fsmc_job_destroy(fsmc_job* j) {
     if (j->submitted) cudaFree(j->dev);
     else arena_give(e, j->dev, j->arena_bytes);
     engine_release(e, j->bytes);
+  }
+  if (j->x0_dev) {
+    cudaSetDevice(e->device);
+    if (j->submitted) cudaFree(j->x0_dev);
+    else arena_give(e, j->x0_dev, j->x0_block);
   }
   {
     std::lock_guard<std::mutex> g(e->mu);

@@ -61,7 +61,8 @@ struct fsmc_job {
   fsmc_dr_params dr{3, 1.0, 0.5, 0};
   fsmc_nuts_params nuts{0.05, 10, 1000.0};
   fsmc_slice_params slice{1.0, 100};
-  std::vector<double> x0;
+  char* x0_dev = nullptr;  // [n_chains][d] starting points (double), copied in at creation
+  size_t x0_block = 0;     // size of the device block behind x0_dev
   // device arena and offsets into it
   char* dev = nullptr;
   size_t bytes = 0;

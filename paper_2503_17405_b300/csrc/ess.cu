@@ -804,6 +804,20 @@ __global__ void fill_int_kernel(int* p, int64_t n, int value) {
     p[i] = value;
 }
 
+template <typename T>
+__global__ void from_double_kernel(const double* src, int64_t n, T* dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)src[i];
+}
+
+template <typename T>
+cudaError_t launch_from_double(const double* src, int64_t n, T* dst, cudaStream_t st) {
+  from_double_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, n, dst);
+  return cudaGetLastError();
+}
+template cudaError_t launch_from_double<float>(const double*, int64_t, float*, cudaStream_t);
+template cudaError_t launch_from_double<double>(const double*, int64_t, double*, cudaStream_t);
+
 cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);

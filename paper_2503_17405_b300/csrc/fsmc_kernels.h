@@ -145,6 +145,9 @@ template <typename T>
 cudaError_t launch_slice_init(const SliceView<T>& v, cudaStream_t st);
 
 cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st);
+// dst[i] = (T) src[i], i < n (device arrays).
+template <typename T>
+cudaError_t launch_from_double(const double* src, int64_t n, T* dst, cudaStream_t st);
 // Next refill window for the pipelined ESS rounds: lo = hi_cur, hi = max(lo, min(t + W, n)),
 // written to v's gen_lo / gen_hi.
 template <typename T>
