@@ -770,7 +770,7 @@ static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
   cudaError_t e;
   if (ess_block(j)) {
     ProfScope p(j, 1, st);
-    e = launch_ess_block_fsm<T>(ess_block_view<T>(j), tu.steps_per_launch, j->e->sms, st);
+    e = launch_ess_block_fsm<T>(ess_block_view<T>(j), tu.steps_per_launch, st);
     j->launches += 1;
   } else if (j->algo == FSMC_ESS) {
     const EssView<T> v = ess_view<T>(j);
@@ -1153,11 +1153,9 @@ extern "C" fsmc_status fsmc_read_moments(fsmc_job* j, double* sx, double* sx2, i
   if (!j) return fsmc_fail(FSMC_EINVAL, "job is NULL");
   if (!j->dev) return fsmc_fail(FSMC_ESTATE, "job has not run");
   const size_t md = (size_t)j->m * j->d;
-  const size_t es = j->prec == FSMC_FP64 ? 8 : 4;
   std::vector<int> t((size_t)j->m);
   CK(cudaMemcpy(t.data(), j->dev + j->o_t, t.size() * 4, cudaMemcpyDeviceToHost));
   if (n_kept) for (size_t c = 0; c < t.size(); ++c) n_kept[c] = t[c];
-  (void)es;
   char* m0 = j->dev + j->o_mom;
   if (j->store) {  // reduce the stored samples on the device into the [4][m][d] buffer
     cudaError_t ce = j->prec == FSMC_FP64

@@ -415,8 +415,7 @@ static cudaError_t init_launch(const EssBlockView<T>& v, cudaStream_t st) {
   } while (0)
 
 template <typename T>
-cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, int sms_hint, cudaStream_t st) {
-  (void)sms_hint;
+cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, cudaStream_t st) {
   FSMC_BLK_DISPATCH(fsm_launch, v, budget, st);
 }
 
@@ -431,8 +430,8 @@ cudaError_t launch_ess_block_init(const EssBlockView<T>& v, cudaStream_t st) {
   FSMC_BLK_DISPATCH(init_launch, v, st);
 }
 
-template cudaError_t launch_ess_block_fsm<float>(const EssBlockView<float>&, int, int, cudaStream_t);
-template cudaError_t launch_ess_block_fsm<double>(const EssBlockView<double>&, int, int, cudaStream_t);
+template cudaError_t launch_ess_block_fsm<float>(const EssBlockView<float>&, int, cudaStream_t);
+template cudaError_t launch_ess_block_fsm<double>(const EssBlockView<double>&, int, cudaStream_t);
 template cudaError_t launch_ess_block_sync<float>(const EssBlockView<float>&, int, int, GridBarrier, unsigned*,
                                                   unsigned long long*, cudaStream_t);
 template cudaError_t launch_ess_block_sync<double>(const EssBlockView<double>&, int, int, GridBarrier, unsigned*,

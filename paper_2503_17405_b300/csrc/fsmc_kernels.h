@@ -129,7 +129,7 @@ cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st);
 // kGpRegMaxN64 (FP64).
 constexpr int kGpRegMaxN32 = 319, kGpRegMaxN64 = 220;
 template <typename T>
-cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, int sms, cudaStream_t st);
+cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ess_block_sync(const EssBlockView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
                                   unsigned long long* iters, cudaStream_t st);

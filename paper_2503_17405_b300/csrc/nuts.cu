@@ -1121,9 +1121,7 @@ static cudaError_t nuts_sync_t(fsmc_job* j, int t0, int t1, GridBarrier bar, uns
 fsmc_status nuts_init_state(fsmc_job* j, cudaStream_t st) {
   if (j->d > 128) return fsmc_fail(FSMC_EINVAL, "NUTS supports d <= 128");
   char* b = j->dev;
-  const size_t es = j->prec == FSMC_FP64 ? 8 : 4;
-  const size_t m = (size_t)j->m, d = (size_t)j->d;
-  (void)es; (void)d;
+  const size_t m = (size_t)j->m;
   // the NUTS state block starts zeroed (state INIT = 0)
   cudaError_t e = cudaMemsetAsync(b + j->o_nuts, 0, j->o_nuts_end - j->o_nuts, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b + j->o_aux, 0, m * (size_t)j->n * 4, st);
