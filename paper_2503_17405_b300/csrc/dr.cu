@@ -21,11 +21,15 @@
 
 namespace fsmc {
 
+// log(1 - e^a), a < 0.  Single precision takes log(-expm1(a)) for every a: for a << 0 the
+// argument rounds near 1 and the result keeps an absolute error of ~1e-7, which is what matters
+// where it is added to the other log terms, and one branch-free form keeps a warp's chains on
+// one path whatever their values.
 template <typename T>
 __device__ __forceinline__ T l1m(T a) {
   if (!(a < T(0))) return neg_inf<T>();
   if constexpr (sizeof(T) == 4)
-    return a > -0.693147181f ? logf(-expm1f(a)) : log1pf(-expf(a));
+    return logf(-expm1f(a));
   else
     return a > -0.6931471805599453 ? log(-expm1(a)) : log1p(-exp(a));
 }
@@ -90,23 +94,52 @@ __device__ __forceinline__ T dr_eval(const DrView<T>& v, const T (&y)[E], int& e
   return lpy;
 }
 
+// The terms of a sample's later-stage ratios that do not involve the new proposal, kept from the
+// stage where they first appear: after stage 1 rejects, l1m(a1(x, y1)); after stage 2 rejects,
+// the stage-2 ratio's l1m(a2(x, y1, y2)), l1m(a1(y1, y2)) and the proposal-density terms between
+// x, y1 and y2.  Stage 3 then evaluates two l1m instead of eight (and stage 2 one instead of
+// two), on the values the full formulas (la2, la3) would recompute.
+template <typename T>
+struct DrCache {
+  T a1;       // l1m(a1(x, y1))
+  T q1xy1;    // lq1(x -> y1)
+  T q1y1y2;   // lq1(y1 -> y2)
+  T a2;       // l1m(a2(x, y1, y2))
+  T a1y1y2;   // l1m(a1(y1, y2))
+  T q2xy2;    // lq2(x -> y2)
+};
+
 template <typename T, int E>
 __device__ __forceinline__ T dr_ratio(const DrView<T>& v, int k, const T (&x)[E], T lp, const T (&y1)[E], T lp1,
-                                      const T (&y2)[E], T lp2, const T (&y)[E], T lpy) {
+                                      const T (&y2)[E], T lp2, const T (&y)[E], T lpy, const DrCache<T>& cc) {
   const int d = v.tg.d;
   if (k == 0) return la1(lp, lpy);
   const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]);
-  if (k == 1) return la2(lp, lp1, lpy, i1 * sqdist(x, y1, d), i1 * sqdist(y, y1, d));
+  if (k == 1) {  // la2(lp, lp1, lpy, lq1(x -> y1), lq1(y -> y1)) with its l1m(a1(x, y1)) kept
+    const T num = lpy + i1 * sqdist(y, y1, d) + l1m(la1(lpy, lp1));
+    const T den = lp + i1 * sqdist(x, y1, d) + cc.a1;
+    if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
+    return fmin(T(0), num - den);
+  }
+  // la3(lp, lp1, lp2, lpy, ...) with the terms of x, y1, y2 kept
   const T i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
-  return la3(lp, lp1, lp2, lpy, i1 * sqdist(x, y1, d), i2 * sqdist(x, y2, d), i1 * sqdist(y, y2, d),
-             i2 * sqdist(y, y1, d), i1 * sqdist(y1, y2, d));
+  const T q1_y3_y2 = i1 * sqdist(y, y2, d);
+  const T a1_32 = l1m(la1(lpy, lp2));
+  const T n2 = lp1 + cc.q1y1y2 + cc.a1y1y2;  // la2(lpy, lp2, lp1, q1_y3_y2, q1_y1_y2)
+  const T d2 = lpy + q1_y3_y2 + a1_32;
+  const T a2_321 = (n2 == neg_inf<T>() || d2 == neg_inf<T>()) ? neg_inf<T>() : fmin(T(0), n2 - d2);
+  const T num = lpy + q1_y3_y2 + i2 * sqdist(y, y1, d) + a1_32 + l1m(a2_321);
+  const T den = lp + cc.q1xy1 + cc.q2xy2 + cc.a1 + cc.a2;
+  if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
+  return fmin(T(0), num - den);
 }
 
 // Returns true when the sample is finished (accepted, or rejected at the last stage); then x/lp
 // hold the sample.  Otherwise y becomes y1 (stage 0) or y2 (stage 1).
 template <typename T, int E>
 __device__ __forceinline__ bool dr_decide(const DrView<T>& v, const Key& key, int t, int k, T la, T (&x)[E],
-                                          T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, const T (&y)[E], T lpy) {
+                                          T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, const T (&y)[E], T lpy,
+                                          DrCache<T>& cc) {
   const int D = (v.tg.d + 3) / 4;
   const P4 r = key.block((uint32_t)t, 0, (uint32_t)(k * (D + 1) + D));
   if (Conv<T>::log_u(r.w0, r.w1) < la) {
@@ -116,11 +149,19 @@ __device__ __forceinline__ bool dr_decide(const DrView<T>& v, const Key& key, in
     return true;
   }
   if (k + 1 >= v.n_stages) return true;
+  const int d = v.tg.d;
   if (k == 0) {
 #pragma unroll
     for (int e = 0; e < E; ++e) y1[e] = y[e];
     lp1 = lpy;
+    cc.a1 = l1m(la);
   } else {
+    const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]), i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
+    cc.q1xy1 = i1 * sqdist(x, y1, d);
+    cc.q1y1y2 = i1 * sqdist(y, y1, d);
+    cc.a2 = l1m(la);
+    cc.a1y1y2 = l1m(la1(lp1, lpy));
+    cc.q2xy2 = i2 * sqdist(x, y, d);
 #pragma unroll
     for (int e = 0; e < E; ++e) y2[e] = y[e];
     lp2 = lpy;
@@ -182,13 +223,27 @@ __device__ __forceinline__ bool sdr_step(const DrView<T>& v, const Key& key, int
 // One PROPOSE step of stage k for one chain (all four parts); the symmetric sampler's try k.
 template <typename T, int E>
 __device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E],
-                                        T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, int& err) {
+                                        T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, DrCache<T>& cc, int& err) {
   if (v.symmetric) return sdr_step<T, E>(v, key, t, k, x, lp, y1, lp1, err);
   T y[E];
   dr_draw<T, E>(v, key, t, k, x, y);
   const T lpy = dr_eval<T, E>(v, y, err);
-  const T la = dr_ratio<T, E>(v, k, x, lp, y1, lp1, y2, lp2, y, lpy);
-  return dr_decide<T, E>(v, key, t, k, la, x, lp, y1, lp1, y2, lp2, y, lpy);
+  const T la = dr_ratio<T, E>(v, k, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
+  return dr_decide<T, E>(v, key, t, k, la, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
+}
+
+// The kept terms live in lpy[4 + i][m] between launches (and between synchronised iterations).
+template <typename T>
+__device__ __forceinline__ DrCache<T> dr_cache_load(const DrView<T>& v, int64_t c) {
+  const T* q = v.lpy + 4 * v.m + c;
+  return DrCache<T>{q[0], q[v.m], q[2 * v.m], q[3 * v.m], q[4 * v.m], q[5 * v.m]};
+}
+
+template <typename T>
+__device__ __forceinline__ void dr_cache_store(const DrView<T>& v, int64_t c, const DrCache<T>& cc) {
+  T* q = v.lpy + 4 * v.m + c;
+  q[0] = cc.a1; q[v.m] = cc.q1xy1; q[2 * v.m] = cc.q1y1y2; q[3 * v.m] = cc.a2; q[4 * v.m] = cc.a1y1y2;
+  q[5 * v.m] = cc.q2xy2;
 }
 
 template <typename T, int E>
@@ -234,6 +289,7 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
     T x[E], y1[E], y2[E];
     dr_load<T, E>(v, c, x, y1, y2);
     T lp = v.lp[c], lp1 = v.lpy[c], lp2 = v.lpy[v.m + c];
+    DrCache<T> cc = dr_cache_load<T>(v, c);
     int t = v.t[c], k = v.k[c];
     const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
     int err = 0, steps = 0;
@@ -249,7 +305,7 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
     for (int b = 0; b < budget && t < v.n; ++b) {
       ++steps;
       if constexpr (CONDENSED) {
-        if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, err)) {
+        if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, err)) {
           dr_emit<T, E>(v, c, t, x);
           v.counts[(size_t)c * v.n + t] = k + 1;
           ++t;
@@ -269,10 +325,10 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
           ++k;
         } else if (u == 2) {
           lac = v.symmetric ? sdr_log_alpha<T>(lp, lp1, lpc)
-                            : dr_ratio<T, E>(v, j, x, lp, y1, lp1, y2, lp2, yc, lpc);
+                            : dr_ratio<T, E>(v, j, x, lp, y1, lp1, y2, lp2, yc, lpc, cc);
           ++k;
         } else if (v.symmetric ? sdr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, yc, lpc)
-                               : dr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, y2, lp2, yc, lpc)) {
+                               : dr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, y2, lp2, yc, lpc, cc)) {
           dr_emit<T, E>(v, c, t, x);
           v.counts[(size_t)c * v.n + t] = j + 1;
           ++t;
@@ -294,6 +350,7 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
     const int pending = CONDENSED ? k : (k >> 2);
     dr_store<T, E>(v, c, x, y1, y2, pending);
     v.lp[c] = lp; v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
+    if (pending) dr_cache_store<T>(v, c, cc);
     v.t[c] = t; v.k[c] = k;
     v.steps[c] += steps;
     if (err) atomicOr(v.err, err);
@@ -321,9 +378,10 @@ __global__ void __launch_bounds__(256) dr_sync_kernel(DrView<T> v, int t_begin, 
         T x[E], y1[E], y2[E];
         dr_load<T, E>(v, c, x, y1, y2);
         T lp = v.lp[c], lp1 = v.lpy[c], lp2 = v.lpy[v.m + c];
+        DrCache<T> cc = dr_cache_load<T>(v, c);
         const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
         v.steps[c] += 1;
-        if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, err)) {
+        if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, err)) {
           dr_emit<T, E>(v, c, t, x);
           v.counts[(size_t)c * v.n + t] = k + 1;
           dr_store<T, E>(v, c, x, y1, y2, 0);
@@ -334,6 +392,7 @@ __global__ void __launch_bounds__(256) dr_sync_kernel(DrView<T> v, int t_begin, 
         } else {
           dr_store<T, E>(v, c, x, y1, y2, k + 1);
           v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
+          dr_cache_store<T>(v, c, cc);
           v.k[c] = k + 1;
           mine = 1;
         }

@@ -422,7 +422,8 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
   } else if (j->algo == FSMC_DR) {
     j->o_ell = L.take(m * es);        // log pi(x)
     j->o_y = L.take(3 * m * d * es);  // y1, y2 and (4-state ablation form) the current proposal
-    j->o_lpy = L.take(4 * m * es);    // log pi(y1), log pi(y2), current proposal's and its ratio
+    j->o_lpy = L.take(10 * m * es);   // log pi(y1), log pi(y2), current proposal's and its ratio,
+                                      // then the kept terms of the later stages' ratios
     j->o_k = L.take(m * 4);
   } else if (j->algo == FSMC_SLICE) {
     j->o_ell = L.take(m * es);        // log pi(x)
@@ -594,7 +595,7 @@ static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
   } else if (j->algo == FSMC_DR) {
     CK(cudaMemsetAsync(b + j->o_k, 0, m * 4, st));
     CK(cudaMemsetAsync(b + j->o_y, 0, 3 * m * d * sizeof(T), st));
-    CK(cudaMemsetAsync(b + j->o_lpy, 0, 4 * m * sizeof(T), st));
+    CK(cudaMemsetAsync(b + j->o_lpy, 0, 10 * m * sizeof(T), st));
     CK(launch_dr_init<T>(dr_view<T>(j), st));
   } else if (j->algo == FSMC_SLICE) {
     CK(cudaMemsetAsync(b + j->o_k, 0, 5 * m * 4, st));

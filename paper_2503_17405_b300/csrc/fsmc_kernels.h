@@ -58,7 +58,8 @@ struct DrView : ChainsView<T> {
   T* lp;                 // [m] log pi(x)
   T* y;                  // [3][m][d] rejected proposals y1, y2 of the current sample; the
                          // current proposal (4-state ablation form)
-  T* lpy;                // [4][m] log pi(y1), log pi(y2); the current proposal's log pi and ratio
+  T* lpy;                // [10][m] log pi(y1), log pi(y2); the current proposal's log pi and ratio;
+                         // the later stages' kept ratio terms (DrCache in dr.cu)
   int* k;                // [m] next stage to try
 };
 
