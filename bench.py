@@ -80,14 +80,14 @@ def _make_config(name, scale):
         return dict(name="sdr_std_normal_d1_M100_m65536_n2000", algo="dr", w=w, m=m, n=n, prec="fp32",
                     x0=W.x0_gauss_diag_exact(w, m), algo_params=[100, 0.1, 1.0], dr_symmetric=1,
                     oracle_algo="sdr", oracle_params=[100, 0.1])
-    if name == "ess_gpreg":
+    if name in ("ess_gpreg", "ess_gpreg400"):
         # Sec. 7.2: ESS on GP-regression hyperparameters, n = 100 points with 6 features (the
-        # middle of the paper's 25 / 100 / 400), 1024 chains; the likelihood is an n x n
-        # Cholesky factorisation per evaluation (flops_per_column: n^3 / 3 + 3 n^2)
-        nd = 100
+        # middle of the paper's 25 / 100 / 400; ess_gpreg400: the largest, 100 samples per chain),
+        # 1024 chains; the likelihood is an n x n factorisation per evaluation
+        nd, n = (100, 1000) if name == "ess_gpreg" else (400, 100)
         w = W.gp_reg(nd)
-        m, n = int(1024 * scale), 1000
-        return dict(name=f"ess_gpreg_n{nd}_m1024_n1000", algo="ess", w=w, m=m, n=n, prec="fp32",
+        m = int(1024 * scale)
+        return dict(name=f"ess_gpreg_n{nd}_m1024_n{n}", algo="ess", w=w, m=m, n=n, prec="fp32",
                     x0=W.x0_gp_reg(w, m), algo_params=None, flops_per_column=0)
     if name == "slice_funnel":
         # Fig. 2's slice sampler (stepping out, then shrinkage) on the 10-d funnel: interval

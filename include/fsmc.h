@@ -67,7 +67,7 @@ typedef enum fsmc_status {
  *               (-1/(d-1) < rho < 1 and w_k > 0 finite, else FSMC_EINVAL)
  *   GP_REG      ESS likelihood of GP-regression hyperparameters x = (sigma, tau, lambda), d = 3
  *               (Sec. 7.2): log N(y; 0, tau^2 exp(-lambda^2 D) + sigma^2 I) over n = n_data
- *               points (1..319; FP64 jobs 1..220), D the squared distances between inputs:
+ *               points (1..512), D the squared distances between inputs:
  *                                                          L[3*3], D[n*n], y[n]
  *               (-inf where the covariance is not positive definite in the job's precision)
  * ESS needs a kind with a prior factor L (GAUSS_CONJ, GP_LOGIT, FLAT, GP_REG); DR, NUTS and

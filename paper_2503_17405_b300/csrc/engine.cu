@@ -405,6 +405,13 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
     j->o_nu = L.take(m * d * es);
     j->o_gencols = L.take(8);
     j->o_work = L.take(8);
+    // scratch for covariance rows beyond shared memory: one block per CTA that can be resident
+    // (shared memory bounds CTAs per SM)
+    const size_t spill = es == 8 ? gpreg_spill_elems<double>(j->tg->n_data) : gpreg_spill_elems<float>(j->tg->n_data);
+    j->spill_stride = spill;
+    j->rows_smem = es == 8 ? gpreg_smem_rows<double>(j->tg->n_data) : gpreg_smem_rows<float>(j->tg->n_data);
+    j->spill_ctas = spill ? (int64_t)j->e->sms * 2 : 0;
+    j->o_spill = spill ? L.take((size_t)j->spill_ctas * spill * es) : 0;
   } else if (j->algo == FSMC_ESS) {
     j->W = j->tun.ring_slots;
     j->dstride = (int)align_up(d, 32);
@@ -536,6 +543,10 @@ EssBlockView<T> ess_block_view(const fsmc_job* j) {
   v.k = (int*)(b + j->o_k);
   v.s = (int*)(b + j->o_s);
   v.work = (unsigned*)(b + j->o_work);
+  v.spill = j->spill_stride ? (T*)(b + j->o_spill) : nullptr;
+  v.spill_stride = j->spill_stride;
+  v.max_ctas = j->spill_stride ? j->spill_ctas : INT64_MAX;
+  v.rows_smem = j->rows_smem;
   return v;
 }
 
@@ -633,7 +644,7 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
     return fsmc_fail(FSMC_EINVAL, "bad algo");
   if (algo == FSMC_DR && t->d > 32) return fsmc_fail(FSMC_EINVAL, "DR supports d <= 32");
   if (t->kind == FSMC_TGT_GP_REG && prec == FSMC_FP64 && t->n_data > kGpRegMaxN64)
-    return fsmc_fail(FSMC_EINVAL, "FP64 GP_REG jobs support n_data <= 220");
+    return fsmc_fail(FSMC_EINVAL, "FP64 GP_REG jobs support n_data <= 512");
   if (algo == FSMC_SLICE && t->d > 32) return fsmc_fail(FSMC_EINVAL, "slice sampling supports d <= 32");
   auto* j = new (std::nothrow) fsmc_job();
   if (!j) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");

@@ -93,6 +93,9 @@ struct fsmc_job {
   size_t o_win = 0;  // second refill-window buffer [2][m]
   size_t o_colbase = 0, o_colmap = 0;  // compacted refill list: [m+1] prefix sums, [m*W] (chain, sample)
   size_t o_work = 0;  // block-likelihood ESS: chain counter of the current FSM launch
+  size_t o_spill = 0, spill_stride = 0;  // block-likelihood ESS: per-CTA scratch for rows
+  int64_t spill_ctas = 0;                // beyond shared memory
+  int rows_smem = 0;                     // covariance rows kept in shared memory
   size_t o_momd = 0;  // [2][m][d] doubles: the moment sums for the host read
   size_t arena_bytes = 0;  // size of the device block behind dev (>= bytes when reused)
   // serving

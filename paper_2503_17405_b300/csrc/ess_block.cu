@@ -29,21 +29,39 @@ __device__ __forceinline__ T blk_exp(T a) { if constexpr (sizeof(T) == 4) return
 template <typename T>
 __device__ __forceinline__ T blk_log(T a) { if constexpr (sizeof(T) == 4) return logf(a); else return log(a); }
 
-// Row i of the packed lower triangle (length i + 1; row n is y, length n) starts at off(i), with
-// gaps so that off(i + 1) = off(i) + 17 (mod 32): the threads of a warp read the same column k of
-// 32 consecutive rows, which then fall in 32 different banks (17 is odd).
+// Row i of the packed lower triangle (length i + 1) starts at off(i) in shared memory, with gaps
+// so that off(i + 1) = off(i) + 17 (mod 32): the threads of a warp read the same column k of 32
+// consecutive rows, which then fall in 32 different banks (17 is odd).  Rows r .. n-1 that do
+// not fit live in a per-CTA scratch block in device memory (L2-resident: a few hundred KB per
+// resident CTA), contiguous; the y row, v, the pivots d, the running sums s and the row offsets
+// stay in shared memory.
 __host__ __device__ __forceinline__ int row_gap(int i) { return (17 - (i + 1)) & 31; }
-__host__ __device__ __forceinline__ size_t gpreg_rows_elems(int n) {
+__host__ __device__ __forceinline__ size_t gpreg_rows_elems(int r) {
   size_t off = 0;
-  for (int i = 0; i < n; ++i) off += (size_t)(i + 1) + row_gap(i);
-  return off + (size_t)n;  // the y row
+  for (int i = 0; i < r; ++i) off += (size_t)(i + 1) + row_gap(i);
+  return off;
 }
 
-// Shared-memory bytes one chain needs: the rows, the column vector v, the pivots d and the
-// running sums s (n elements each), and the row offsets (n + 1 ints).
+constexpr size_t kGpRegSmemBudget = 220 * 1024;
+
+// Shared-memory bytes with the first r rows in shared memory: the rows, the y row, v, d, s (n
+// elements each) and the n + 1 row offsets.
+template <typename T>
+__host__ __device__ __forceinline__ size_t gpreg_smem_bytes_r(int n, int r) {
+  return (gpreg_rows_elems(r) + 4 * (size_t)n) * sizeof(T) + ((size_t)n + 1) * sizeof(int);
+}
+
+// Rows kept in shared memory: all of them when they fit the budget.
+template <typename T>
+__host__ __device__ __forceinline__ int gpreg_rows_in_smem(int n) {
+  int r = n;
+  while (r > 0 && gpreg_smem_bytes_r<T>(n, r) > kGpRegSmemBudget) --r;
+  return r;
+}
+
 template <typename T>
 __host__ __device__ __forceinline__ size_t gpreg_smem_bytes(int n) {
-  return (gpreg_rows_elems(n) + 3 * (size_t)n) * sizeof(T) + ((size_t)n + 1) * sizeof(int);
+  return gpreg_smem_bytes_r<T>(n, gpreg_rows_in_smem<T>(n));
 }
 
 template <int WPC>
@@ -58,8 +76,32 @@ __device__ __forceinline__ void cta_sync() {
 // (L^-1 y)_j), where s_i = sum_{k<j} L_ik^2 d_k is kept per row by the thread that computes L_ij
 // (so d_j needs no reduction).  Storage: M[i][j] = L_ij, d and s in their own arrays.  Every
 // thread returns the same value.
+// Dot product sum_{k<j} r[k] v[k] subtracted from r[j] (4 accumulators).
+template <typename T>
+__device__ __forceinline__ T row_residual(const T* r, const T* V, int j) {
+  T a0 = r[j], a1 = T(0), a2 = T(0), a3 = T(0);
+  int k = 0;
+  for (; k + 4 <= j; k += 4) {
+    a0 = fma(-r[k], V[k], a0);
+    a1 = fma(-r[k + 1], V[k + 1], a1);
+    a2 = fma(-r[k + 2], V[k + 2], a2);
+    a3 = fma(-r[k + 3], V[k + 3], a3);
+  }
+  for (; k < j; ++k) a0 = fma(-r[k], V[k], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Offset of scratch row i (i >= r) in the CTA's scratch block: rows r .. i-1 before it.
+__device__ __forceinline__ size_t spill_off(int i, int r) {
+  return (size_t)i * (i + 1) / 2 - (size_t)r * (r + 1) / 2;
+}
+
+// M: the shared rows (row i < r at M + off[i]; the y row at M + off[n], followed by v, d, s);
+// G: this CTA's scratch block (rows r .. n-1).  Shared and scratch rows are read by separate
+// loops so that the shared ones stay shared-memory loads.
 template <typename T, int WPC>
-__device__ T gpreg_loglik_cta(const TargetView<T>& tg, const T (&x)[kBlkE], T* M, const int* off, T* red) {
+__device__ T gpreg_loglik_cta(const TargetView<T>& tg, const T (&x)[kBlkE], T* M, const int* off, T* G, int r,
+                              T* red) {
   constexpr int NT = 32 * WPC;
   const int n = tg.n_data, tid = threadIdx.x;
   const T s2 = x[0] * x[0], t2 = x[1] * x[1], l2 = x[2] * x[2];
@@ -68,42 +110,55 @@ __device__ T gpreg_loglik_cta(const TargetView<T>& tg, const T (&x)[kBlkE], T* M
   T* Dp = V + n;           // pivots d
   T* S = Dp + n;           // s_i
   for (int i = 0; i < n; ++i) {
-    T* ri = M + off[i];
     const T* Dr = tg.X + (size_t)i * n;
-    for (int j = tid; j <= i; j += NT) ri[j] = t2 * blk_exp<T>(-l2 * Dr[j]) + (i == j ? s2 : T(0));
+    if (i < r) {
+      T* ri = M + off[i];
+      for (int j = tid; j <= i; j += NT) ri[j] = t2 * blk_exp<T>(-l2 * Dr[j]) + (i == j ? s2 : T(0));
+    } else {
+      T* ri = G + spill_off(i, r);
+      for (int j = tid; j <= i; j += NT) ri[j] = t2 * blk_exp<T>(-l2 * Dr[j]) + (i == j ? s2 : T(0));
+    }
   }
   for (int j = tid; j < n; j += NT) {
     ry[j] = tg.vec[j];
     S[j] = T(0);
   }
+  if (r < n) __threadfence_block();  // scratch rows written by one thread are read by others
   cta_sync<WPC>();
   T quad = T(0);
   bool pd = true;
   for (int j = 0; j < n; ++j) {
-    const T* rj = M + off[j];
-    const T dj = rj[j] - S[j];  // the same smem values in every thread
+    T dj;
+    if (j < r) {  // the same values in every thread
+      const T* rj = M + off[j];
+      dj = rj[j] - S[j];
+      for (int k = tid; k < j; k += NT) V[k] = rj[k] * Dp[k];
+    } else {
+      const T* rj = G + spill_off(j, r);
+      dj = rj[j] - S[j];
+      for (int k = tid; k < j; k += NT) V[k] = rj[k] * Dp[k];
+    }
     if (!(dj > T(0))) { pd = false; break; }
     const T inv = T(1) / dj;
-    for (int k = tid; k < j; k += NT) V[k] = rj[k] * Dp[k];
     if (tid == 0) Dp[j] = dj;
     cta_sync<WPC>();  // V complete
     for (int i = j + 1 + tid; i <= n; i += NT) {
-      T* ri = M + off[i];  // row n is y
-      T a0 = ri[j], a1 = T(0), a2 = T(0), a3 = T(0);
-      int k = 0;
-      for (; k + 4 <= j; k += 4) {
-        a0 = fma(-ri[k], V[k], a0);
-        a1 = fma(-ri[k + 1], V[k + 1], a1);
-        a2 = fma(-ri[k + 2], V[k + 2], a2);
-        a3 = fma(-ri[k + 3], V[k + 3], a3);
+      if (i < r || i == n) {
+        T* ri = i < n ? M + off[i] : ry;
+        const T cij = row_residual<T>(ri, V, j);
+        const T lij = cij * inv;
+        ri[j] = lij;
+        if (i < n) S[i] = fma(lij, cij, S[i]);  // += L_ij^2 d_j
+        else quad = fma(cij, lij, quad);
+      } else {
+        T* ri = G + spill_off(i, r);
+        const T cij = row_residual<T>(ri, V, j);
+        const T lij = cij * inv;
+        ri[j] = lij;
+        S[i] = fma(lij, cij, S[i]);
       }
-      for (; k < j; ++k) a0 = fma(-ri[k], V[k], a0);
-      const T cij = (a0 + a1) + (a2 + a3);
-      const T lij = cij * inv;
-      ri[j] = lij;
-      if (i < n) S[i] = fma(lij, cij, S[i]);  // += L_ij^2 d_j
-      else quad = fma(cij, lij, quad);
     }
+    if (r < n) __threadfence_block();
     cta_sync<WPC>();  // every thread has read V and the rows before V is rewritten
   }
   if (!pd) {
@@ -163,9 +218,17 @@ __device__ __forceinline__ void blk_store(const EssBlockView<T>& v, int64_t c, c
 // One FSM step of chain c: INIT (new ellipse, threshold, first angle) or SHRINK (narrow the
 // bracket, next angle), the likelihood at the proposal, and DONE when it clears the threshold.
 // Returns true while the chain stays in SHRINK.
+// The CTA's covariance storage (see gpreg_loglik_cta).
+template <typename T>
+struct BlkMat {
+  T* M;
+  const int* off;
+  T* G;
+  int r;
+};
+
 template <typename T, int WPC>
-__device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, T* M, const int* off, T* red,
-                         int& err) {
+__device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, const BlkMat<T>& mt, T* red, int& err) {
   const int d = v.tg.d;
   const bool lead = threadIdx.x == 0;
   const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
@@ -197,7 +260,7 @@ __device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, T*
   ess_sincos<T>(s.th, sn, cs);
 #pragma unroll
   for (int e = 0; e < kBlkE; ++e) xp[e] = fma(s.x[e], cs, s.nu[e] * sn);
-  T ellp = gpreg_loglik_cta<T, WPC>(v.tg, xp, M, off, red);
+  T ellp = gpreg_loglik_cta<T, WPC>(v.tg, xp, mt.M, mt.off, mt.G, mt.r, red);
   if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
   const bool accept = ellp > s.logy;
   if (accept || s.s >= kMaxShrinks) {
@@ -236,18 +299,21 @@ __device__ bool blk_step(const EssBlockView<T>& v, int64_t c, BlkChain<T>& s, T*
   return true;
 }
 
-// The chain's matrix at the start of shared memory, the row offsets after the T arrays.
+// This CTA's matrix: the first r rows, then the y row, v, d and s in shared memory, then the
+// row offsets (n + 1 ints); rows r .. n-1 in the CTA's scratch block.
 template <typename T, int WPC>
-__device__ __forceinline__ void blk_layout(const EssBlockView<T>& v, unsigned char* raw, T*& M, int*& off) {
+__device__ __forceinline__ BlkMat<T> blk_layout(const EssBlockView<T>& v, unsigned char* raw) {
   const int n = v.tg.n_data;
-  M = (T*)raw;
-  off = (int*)(raw + (gpreg_rows_elems(n) + 3 * (size_t)n) * sizeof(T));
+  const int r = v.rows_smem;
+  int* off = (int*)(raw + (gpreg_rows_elems(r) + 4 * (size_t)n) * sizeof(T));
   if (threadIdx.x == 0) {
     int o = 0;
-    for (int i = 0; i < n; ++i) { off[i] = o; o += i + 1 + row_gap(i); }
+    for (int i = 0; i < r; ++i) { off[i] = o; o += i + 1 + row_gap(i); }
+    for (int i = r; i < n; ++i) off[i] = 0;  // scratch rows: spill_off
     off[n] = o;
   }
   cta_sync<WPC>();
+  return BlkMat<T>{(T*)raw, off, v.spill ? v.spill + (size_t)blockIdx.x * v.spill_stride : nullptr, r};
 }
 
 template <typename T, int WPC>
@@ -255,9 +321,7 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_fsm_kernel(EssBlockView<T>
   extern __shared__ __align__(16) unsigned char blk_smem[];
   __shared__ T red[2 * WPC];
   __shared__ unsigned cur;
-  T* M;
-  int* off;
-  blk_layout<T, WPC>(v, blk_smem, M, off);
+  const BlkMat<T> mt = blk_layout<T, WPC>(v, blk_smem);
   int err = 0;
   for (;;) {
     if (threadIdx.x == 0) cur = atomicAdd(v.work, 1u);
@@ -269,7 +333,7 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_fsm_kernel(EssBlockView<T>
     blk_load<T>(v, c, s);
     int steps = 0;
     for (int b = 0; b < budget && s.t < v.n; ++b) {
-      blk_step<T, WPC>(v, c, s, M, off, red, err);
+      blk_step<T, WPC>(v, c, s, mt, red, err);
       ++steps;
     }
     blk_store<T>(v, c, s);
@@ -287,9 +351,7 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_sync_kernel(EssBlockView<T
                                                                   unsigned long long* iterations) {
   extern __shared__ __align__(16) unsigned char blk_smem[];
   __shared__ T red[2 * WPC];
-  T* M;
-  int* off;
-  blk_layout<T, WPC>(v, blk_smem, M, off);
+  const BlkMat<T> mt = blk_layout<T, WPC>(v, blk_smem);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int iter = 0, err = 0;
   for (int t = t_begin; t < t_end; ++t) {
@@ -300,7 +362,7 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_sync_kernel(EssBlockView<T
         cta_sync<WPC>();  // every thread has read k[c] before thread 0 may store it
         BlkChain<T> s;
         blk_load<T>(v, c, s);
-        const bool more = blk_step<T, WPC>(v, c, s, M, off, red, err);
+        const bool more = blk_step<T, WPC>(v, c, s, mt, red, err);
         blk_store<T>(v, c, s);
         if (threadIdx.x == 0) v.steps[c] += 1;
         mine += more ? 1u : 0u;
@@ -325,15 +387,13 @@ template <typename T, int WPC>
 __global__ void __launch_bounds__(32 * WPC) ess_block_init_kernel(EssBlockView<T> v) {
   extern __shared__ __align__(16) unsigned char blk_smem[];
   __shared__ T red[2 * WPC];
-  T* M;
-  int* off;
-  blk_layout<T, WPC>(v, blk_smem, M, off);
+  const BlkMat<T> mt = blk_layout<T, WPC>(v, blk_smem);
   const int d = v.tg.d;
   for (int64_t c = blockIdx.x; c < v.m; c += gridDim.x) {
     T x[kBlkE];
 #pragma unroll
     for (int e = 0; e < kBlkE; ++e) x[e] = e < d ? v.x[(size_t)c * d + e] : T(0);
-    T ell = gpreg_loglik_cta<T, WPC>(v.tg, x, M, off, red);
+    T ell = gpreg_loglik_cta<T, WPC>(v.tg, x, mt.M, mt.off, mt.G, mt.r, red);
     if (threadIdx.x == 0) {
       if (!(ell == ell)) { ell = neg_inf<T>(); atomicOr(v.err, ERR_NONFINITE); }
       v.ell[c] = ell;
@@ -365,11 +425,11 @@ static int blk_wpc(int64_t m, int sms) {
 template <typename T, int WPC>
 static cudaError_t fsm_launch(const EssBlockView<T>& v, int budget, cudaStream_t st) {
   auto kern = ess_block_fsm_kernel<T, WPC>;
-  const size_t smem = gpreg_smem_bytes<T>(v.tg.n_data);
+  const size_t smem = gpreg_smem_bytes_r<T>(v.tg.n_data, v.rows_smem);
   int per_sm = 0, sms = 0;
   cudaError_t e = blk_prepare(kern, 32 * WPC, smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, v.m);
+  const int64_t blocks = std::min<int64_t>(std::min<int64_t>((int64_t)per_sm * sms, v.m), v.max_ctas);
   e = cudaMemsetAsync(v.work, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)blocks, 32 * WPC, smem, st>>>(v, budget);
@@ -380,11 +440,11 @@ template <typename T, int WPC>
 static cudaError_t sync_launch(const EssBlockView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
                                unsigned long long* iters, cudaStream_t st) {
   auto kern = ess_block_sync_kernel<T, WPC>;
-  const size_t smem = gpreg_smem_bytes<T>(v.tg.n_data);
+  const size_t smem = gpreg_smem_bytes_r<T>(v.tg.n_data, v.rows_smem);
   int per_sm = 0, sms = 0;
   cudaError_t e = blk_prepare(kern, 32 * WPC, smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, v.m);
+  const int64_t blocks = std::min<int64_t>(std::min<int64_t>((int64_t)per_sm * sms, v.m), v.max_ctas);
   EssBlockView<T> vv = v;
   void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
   return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(32 * WPC), args, smem, st);
@@ -393,11 +453,11 @@ static cudaError_t sync_launch(const EssBlockView<T>& v, int t0, int t1, GridBar
 template <typename T, int WPC>
 static cudaError_t init_launch(const EssBlockView<T>& v, cudaStream_t st) {
   auto kern = ess_block_init_kernel<T, WPC>;
-  const size_t smem = gpreg_smem_bytes<T>(v.tg.n_data);
+  const size_t smem = gpreg_smem_bytes_r<T>(v.tg.n_data, v.rows_smem);
   int per_sm = 0, sms = 0;
   cudaError_t e = blk_prepare(kern, 32 * WPC, smem, &per_sm, &sms);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, v.m);
+  const int64_t blocks = std::min<int64_t>(std::min<int64_t>((int64_t)per_sm * sms, v.m), v.max_ctas);
   kern<<<(unsigned)blocks, 32 * WPC, smem, st>>>(v);
   return cudaGetLastError();
 }
@@ -429,6 +489,22 @@ template <typename T>
 cudaError_t launch_ess_block_init(const EssBlockView<T>& v, cudaStream_t st) {
   FSMC_BLK_DISPATCH(init_launch, v, st);
 }
+
+// Rows of an n-point covariance kept in shared memory, and the scratch elements per CTA for the
+// rest (0 when all fit).
+template <typename T>
+int gpreg_smem_rows(int n) { return gpreg_rows_in_smem<T>(n); }
+template <typename T>
+size_t gpreg_spill_elems(int n) {
+  const int r = gpreg_rows_in_smem<T>(n);
+  size_t e = 0;
+  for (int i = r; i < n; ++i) e += (size_t)(i + 1);
+  return e;
+}
+template int gpreg_smem_rows<float>(int);
+template int gpreg_smem_rows<double>(int);
+template size_t gpreg_spill_elems<float>(int);
+template size_t gpreg_spill_elems<double>(int);
 
 template cudaError_t launch_ess_block_fsm<float>(const EssBlockView<float>&, int, cudaStream_t);
 template cudaError_t launch_ess_block_fsm<double>(const EssBlockView<double>&, int, cudaStream_t);

@@ -75,6 +75,10 @@ struct EssBlockView : ChainsView<T> {
   int* k;                // [m] FSM state
   int* s;                // [m] shrinks in the current sample
   unsigned* work;        // chain counter of the current FSM launch (zeroed before each launch)
+  T* spill;              // per-CTA scratch for covariance rows beyond shared memory
+  size_t spill_stride;   // its elements per CTA
+  int64_t max_ctas;      // CTAs the scratch has room for (launches use at most this many)
+  int rows_smem;         // covariance rows kept in shared memory (the rest in the scratch)
 };
 
 template <typename T>
@@ -126,9 +130,13 @@ cudaError_t launch_dr_sync(const DrView<T>& v, int t0, int t1, GridBarrier bar, 
 template <typename T>
 cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st);
 
-// GP_REG likelihood in shared memory (the packed lower triangle): n <= kGpRegMaxN32 (FP32) /
-// kGpRegMaxN64 (FP64).
-constexpr int kGpRegMaxN32 = 319, kGpRegMaxN64 = 220;
+// GP_REG likelihood: the packed lower triangle in shared memory, the rows that do not fit in a
+// per-CTA scratch block; n <= kGpRegMaxN32 (FP32) / kGpRegMaxN64 (FP64).
+constexpr int kGpRegMaxN32 = 512, kGpRegMaxN64 = 512;
+template <typename T>
+size_t gpreg_spill_elems(int n);
+template <typename T>
+int gpreg_smem_rows(int n);
 template <typename T>
 cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, cudaStream_t st);
 template <typename T>

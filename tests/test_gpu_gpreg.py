@@ -77,18 +77,41 @@ def test_fp32_transition_by_transition_against_the_oracle(eng, n_data):
     assert ok.mean() >= 0.98
 
 
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_papers_largest_size_matches_oracle(eng, mode):
+    # n = 400 (Sec. 7.2's largest): the rows beyond shared memory live in the CTA's scratch block
+    w = W.gp_reg(400)
+    x0 = W.x0_gp_reg(w, 6)
+    n = 6
+    job = _job(eng, w, x0, n, "fp64", mode)
+    ref = O.run("ess", "gp_reg", w["params"], x0, n, seed=2, n_data=400)
+    counts, _, _ = job.loop_counts()
+    compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    job.close()
+
+
+def test_fp32_papers_largest_size_transitions(eng):
+    w = W.gp_reg(400)
+    x0 = W.x0_gp_reg(w, 8).astype(np.float32).astype(np.float64)
+    m, n = x0.shape[0], 8
+    job = _job(eng, w, x0, n, "fp32", "fsm")
+    xs = job.samples().astype(np.float64)
+    counts, _, _ = job.loop_counts()
+    job.close()
+    starts = np.concatenate([x0[:, None, :], xs[:, :-1, :]], axis=1).reshape(m * n, -1)
+    ref = O.transitions("ess", "gp_reg", w["params"], starts, np.repeat(np.arange(m), n), np.tile(np.arange(n), m),
+                        seed=2, n_data=400)
+    err = sample_errors(xs.reshape(m * n, -1), ref["x"])
+    ok = (ref["counts"] == counts.ravel()) & (err <= FP32_TOL)
+    print("fp32 gp_reg n=400 transitions: %d of %d agree; max err %.3g" % (ok.sum(), ok.size, err[ok].max()))
+    assert ok.mean() >= 0.95
+
+
 def test_limits_and_argument_checks(eng):
     from paper_2503_17405_b300 import fsmc
-    w = W.gp_reg(221)
-    tg = eng.target("gp_reg", 3, w["params"], n_data=221)
+    big = W.gp_reg(513)
     with pytest.raises(fsmc.FsmcError):
-        eng.job(tg, "ess", 4, 4, prec="fp64")                     # FP64 covariance over 220 rows
-    job = eng.job(tg, "ess", 4, 4, x0=W.x0_gp_reg(w, 4), prec="fp32")
-    job.run("fsm")
-    job.close()
-    big = W.gp_reg(320)
-    with pytest.raises(fsmc.FsmcError):
-        eng.target("gp_reg", 3, big["params"], n_data=320)        # over the shared-memory limit
+        eng.target("gp_reg", 3, big["params"], n_data=513)        # over the size limit
     w = W.gp_reg(25)
     with pytest.raises(fsmc.FsmcError):
         eng.target("gp_reg", 2, w["params"][1:], n_data=25)      # d must be 3
