@@ -179,42 +179,68 @@ __device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E
 // sin(th) by log2(e) once, so that t' = log2(e) (-s_i x'_i) = xs cs2 + ns sn2 costs one
 // multiply-add per coordinate and
 //   softplus(-s_i x'_i) = ln 2 log2(1 + 2^t').
-// 1 + 2^t' rounds to 2^t' for t' > 24, where log2 returns t' itself; t' is capped at 126 so that
-// 2^t' stays finite (|x'_i| > 87 would be needed to reach it).  Two hardware approximations per
-// coordinate (ex2, lg2); the absolute error per coordinate is ~2e-7.
+// A lane's coordinates are taken in groups of eight: the group's factors 1 + 2^t' (ex2.approx,
+// one add each) are multiplied together and the group contributes log2 of the product
+// (lg2.approx), one base-2 logarithm per eight coordinates instead of one per coordinate.  Every
+// factor is >= 1, so the product cannot underflow; it overflows only when the group's t' sum to
+// more than ~126 (|x'_i| of ~11 on every coordinate, or ~87 on one), and a product above 2^126,
+// infinite or NaN sends the group to the per-coordinate form sum log2(1 + 2^min(t', 126)), whose
+// terms are finite for finite t'.  Relative error of a product of eight rounded factors: ~1e-6,
+// i.e. ~1.5e-6 in its log2, of the order of the per-coordinate form's summed errors (~2e-7 per
+// coordinate).
 // Coordinates are processed in pairs with the packed FP32 instructions (FFMA2 / FMUL2 / FADD2:
-// two single-precision operations, each rounded as its scalar form, per instruction); the even
-// and odd coordinates of a lane accumulate separately.  Padded coordinates (beyond d) contribute
-// exact zeros, so ragged and full rows give the same bits.
+// two single-precision operations, each rounded as its scalar form, per instruction).  Padded
+// coordinates (beyond d) contribute the factor 1 exactly, so ragged and full rows give the same
+// bits.
 constexpr float kLn2f = 0.693147180559945309417f;
 constexpr float kLog2ef = 1.44269504088896340736f;
 
 template <int G, int E, bool FULL = false>
 __device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const float (&ns)[E], float cs2, float sn2,
                                                  int lane, int d, unsigned gmask) {
-  if constexpr (E % 2 == 0) {
-    const float2 c2 = make_float2(cs2, cs2), s2 = make_float2(sn2, sn2), one = make_float2(1.f, 1.f);
-    float2 acc = make_float2(0.f, 0.f);
+  constexpr int kGrp = 8;
+  const float2 c2 = make_float2(cs2, cs2), s2 = make_float2(sn2, sn2), one = make_float2(1.f, 1.f);
+  float acc = 0.f;
 #pragma unroll
-    for (int e = 0; e < E; e += 2) {
-      const bool v0 = FULL || e * G + lane < d, v1 = FULL || (e + 1) * G + lane < d;
-      const float2 t = __ffma2_rn(make_float2(xs[e], xs[e + 1]), c2,
-                                  __fmul2_rn(make_float2(ns[e], ns[e + 1]), s2));
-      const float2 y = __fadd2_rn(make_float2(ex2_approx(fminf(t.x, 126.f)), ex2_approx(fminf(t.y, 126.f))), one);
-      acc = __fadd2_rn(acc, make_float2(v0 ? lg2_approx(y.x) : 0.f, v1 ? lg2_approx(y.y) : 0.f));
-    }
-    return -kLn2f * group_sum<G>(acc.x + acc.y, gmask);
-  } else {
-    float acc = 0.f;
+  for (int g = 0; g < E; g += kGrp) {
+    const int n = E - g < kGrp ? E - g : kGrp;  // a constant once the loop is unrolled
+    float f[kGrp];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      if (FULL || e * G + lane < d) {
-        const float t = fmaf(xs[e], cs2, ns[e] * sn2);
-        acc += lg2_approx(1.f + ex2_approx(fminf(t, 126.f)));
-      }
+    for (int e = 0; e + 1 < n; e += 2) {
+      const int k0 = (g + e) * G + lane, k1 = (g + e + 1) * G + lane;
+      const float2 tt = __ffma2_rn(make_float2(xs[g + e], xs[g + e + 1]), c2,
+                                   __fmul2_rn(make_float2(ns[g + e], ns[g + e + 1]), s2));
+      const float2 y = __fadd2_rn(make_float2(ex2_approx(tt.x), ex2_approx(tt.y)), one);
+      f[e] = (FULL || k0 < d) ? y.x : 1.f;
+      f[e + 1] = (FULL || k1 < d) ? y.y : 1.f;
     }
-    return -kLn2f * group_sum<G>(acc, gmask);
+    if (n % 2) {
+      const int e = n - 1, k = (g + e) * G + lane;
+      f[e] = (FULL || k < d) ? ex2_approx(fmaf(xs[g + e], cs2, ns[g + e] * sn2)) + 1.f : 1.f;
+    }
+    // product of the group's factors: pairwise in packed form, then the two halves
+    float q;
+    if (n >= 2) {
+      float2 p = make_float2(f[0], f[1]);
+#pragma unroll
+      for (int e = 2; e + 1 < n; e += 2) p = __fmul2_rn(p, make_float2(f[e], f[e + 1]));
+      q = p.x * p.y;
+      if (n % 2) q *= f[n - 1];
+    } else {
+      q = f[0];
+    }
+    if (q <= 0x1p126f) {
+      acc += lg2_approx(q);
+    } else {  // overflowed (or NaN): the per-coordinate form, t' recomputed
+      float r = 0.f;
+#pragma unroll
+      for (int e = 0; e < n; ++e)
+        if (FULL || (g + e) * G + lane < d)
+          r += lg2_approx(1.f + ex2_approx(fminf(fmaf(xs[g + e], cs2, ns[g + e] * sn2), 126.f)));
+      acc += r;
+    }
   }
+  return -kLn2f * group_sum<G>(acc, gmask);
 }
 
 // sign of coordinate e flipped where bit e of mask is set (exact)
@@ -265,21 +291,41 @@ __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, 
 // ------------------------------------------------------------------------------------------
 // FSM kernel: every chain advances `budget` states (fewer if its ring runs dry or it
 // finishes).  Chain-group layout: G lanes own one chain, lane l holds coordinates l, l+G, ...
-// Chain groups of 8 or more lanes draw G consecutive Philox blocks of the current sample at
-// once (lane l holds draw D + cbase + l) and each state fetches its words by shuffle, instead
-// of every lane computing the same block; chain-per-thread computes the block it needs.
+// Chain groups of 8 or more lanes compute G Philox blocks at once and each state fetches its
+// words by shuffle, instead of every lane computing the same block; chain-per-thread computes
+// the block it needs.  A sample t uses draws D + off, off = 0 for its INIT and 1 + s for its
+// s-th shrink, so the cache holds either
+//   narrow: the first kOff offsets of kSamp consecutive samples tb, tb + 1, ...
+//           (lane l: sample tb + l / kOff, draw D + l % kOff), or
+//   wide:   G consecutive offsets ob, ob + 1, ... of sample tb (lane l: draw D + ob + l),
+// refilled when a state asks for a (sample, offset) outside it.  With 32 lanes the narrow layout
+// covers two samples of up to 15 shrinks each, so most samples cost half a refill.
 template <int G>
 struct PhiloxLaneCache {
+  static constexpr int kOff = G < 16 ? G : 16;
+  static constexpr int kSamp = G >= 8 ? G / kOff : 1;
   P4 cache{0u, 0u, 0u, 0u};
-  int cbase = -(1 << 30);
-  __device__ __forceinline__ void reset() { cbase = -(1 << 30); }
+  int tb = -(1 << 30), ob = 0;
+  bool wide = false;
   __device__ __forceinline__ P4 fetch(const Key& key, int t, int D, int off, int lane, unsigned gmask) {
     if constexpr (G >= 8) {
-      if (off - cbase >= G || off < cbase) {
-        cbase = off;
+      int src;
+      if (!wide && (unsigned)t - (unsigned)tb < (unsigned)kSamp && off < kOff) {
+        src = (t - tb) * kOff + off;
+      } else if (wide && t == tb && (unsigned)(off - ob) < (unsigned)G) {
+        src = off - ob;
+      } else if (off < kOff) {
+        tb = t;
+        wide = false;
+        cache = key.block((uint32_t)(t + lane / kOff), 0, (uint32_t)(D + lane % kOff));
+        src = off;
+      } else {
+        tb = t;
+        ob = off;
+        wide = true;
         cache = key.block((uint32_t)t, 0, (uint32_t)(D + off + lane));
+        src = 0;
       }
-      const int src = off - cbase;
       return P4{__shfl_sync(gmask, cache.w0, src, G), __shfl_sync(gmask, cache.w1, src, G),
                 __shfl_sync(gmask, cache.w2, src, G), __shfl_sync(gmask, cache.w3, src, G)};
     } else {
@@ -342,7 +388,6 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
     if (st == ESS_INIT) {
       if (t >= hi) break;  // direction not generated yet
       load_nu();
-      pc.reset();  // a new sample: its blocks are not cached yet
       const P4 r = pc.fetch(key, t, D, 0, lane, gmask);
       logy = ess_threshold<T>(ell, Conv<T>::log_u(r.w0, r.w1));
       th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
@@ -443,7 +488,6 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
     if (st == ESS_INIT) {
       if (t >= hi) break;  // direction not generated yet
       load_nu();
-      pc.reset();
       const P4 r = pc.fetch(key, t, D, 0, lane, gmask);
       logy = ess_threshold<float>(ell, Conv<float>::log_u(r.w0, r.w1));
       th = float(kTwoPi) * Conv<float>::u(r.w2, r.w3);
