@@ -449,8 +449,14 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
 // likelihood is one multiply-add per coordinate (ess_loglik_gp32), the accepted state is
 // xs' = xs cos + ns sin (exactly -s x'), and x is recovered exactly for the emitted samples.
 // FULL: d = E * G (no ragged lanes).
-template <int G, int E, bool FULL>
-__device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, int64_t c, int budget, int lane) {
+// PF (32-lane groups, FULL, E a multiple of 4): the direction of sample t + 1 is copied into the
+// group's shared-memory row `pf` (cp.async, 16 bytes per copy, L2 only) when sample t starts,
+// so that its ring row is on chip when t + 1 starts.  Only samples below gen_hi, whose
+// directions were generated before this launch, are copied.
+template <int G, int E, bool FULL, bool PF = false>
+__device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, int64_t c, int budget, int lane,
+                                                     float* pf = nullptr) {
+  static_assert(!PF || (G == 32 && FULL && E % 4 == 0), "prefetch needs full 32-lane rows");
   const int d = FULL ? E * G : v.tg.d;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const unsigned gmask = group_mask<G>();
@@ -472,7 +478,17 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
   const int hi = v.gen_hi[c];
   const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
   int slot = t % v.W;  // ring slot of sample t, advanced with t
+  int pf_t = -1;  // sample whose direction is in pf (copy issued)
   auto load_nu = [&]() {
+    if constexpr (PF) {
+      if (pf_t == t) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < E; ++e) ns[e] = flip_sign(pf[e * G + lane], smask, e);
+        return;
+      }
+    }
     const float* src = v.nu + ((size_t)c * v.W + slot) * v.dstride;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -488,6 +504,22 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
     if (st == ESS_INIT) {
       if (t >= hi) break;  // direction not generated yet
       load_nu();
+      if constexpr (PF) {
+        if (t + 1 < hi && b + 1 < budget) {
+          __syncwarp();  // every lane has read pf
+          const int nslot = slot + 1 == v.W ? 0 : slot + 1;
+          const float* src = v.nu + ((size_t)c * v.W + nslot) * v.dstride;
+          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(pf);
+#pragma unroll
+          for (int j = 0; j < E / 4; ++j) {
+            const int q = (j * G + lane) * 4;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 4u * (uint32_t)q), "l"(src + q)
+                         : "memory");
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          pf_t = t + 1;
+        }
+      }
       const P4 r = pc.fetch(key, t, D, 0, lane, gmask);
       logy = ess_threshold<float>(ell, Conv<float>::log_u(r.w0, r.w1));
       th = float(kTwoPi) * Conv<float>::u(r.w2, r.w3);
@@ -538,6 +570,10 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
       st = ESS_SHRINK;
     }
   }
+  if constexpr (PF) {
+    if (pf_t >= 0) asm volatile("cp.async.wait_all;" ::: "memory");  // pf is reused by the next chain
+    __syncwarp();
+  }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = e * G + lane;
@@ -575,13 +611,24 @@ __host__ __device__ constexpr int ess_min_blocks() {
                                                                                                            : 2;
 }
 
+// MODE 2 with 32-lane groups and E % 4 == 0 prefetches directions through shared memory
+// (one row of d floats per warp; at most 256 threads, 8 warps, per block).
+template <typename T, int G, int E, int MODE>
+constexpr bool kEssPrefetch = sizeof(T) == 4 && MODE == 2 && G == 32 && E % 4 == 0;
+
 template <typename T, int G, int E, int MODE>
 __global__ void __launch_bounds__(256, (ess_min_blocks<T, G, E, MODE>()))
 ess_fsm_kernel(EssView<T> v, int budget) {
   const int lane = threadIdx.x % G;
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, MODE>(v, c, budget, lane);
+  if constexpr (kEssPrefetch<T, G, E, MODE>) {
+    __shared__ __align__(16) float pf_rows[8][E * G];
+    float* pf = pf_rows[threadIdx.x / 32];
+    for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain_gp<G, E, true, true>(v, c, budget, lane, pf);
+  } else {
+    for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, MODE>(v, c, budget, lane);
+  }
 }
 
 // ---- fused launches over several jobs (serving) --------------------------------------------------
