@@ -844,6 +844,11 @@ static fsmc_status capture_rounds(fsmc_job* j, int rounds, cudaStream_t st) {
 // the FSM kernel of a round-p round consumes (it reads only its upper bound), buffer p^1 the
 // one being refilled.  The refill stream waits for the FSM kernel of round r-1 before writing
 // buffer p^1, so it runs at most one round ahead.
+// With the tensor-core generator the refill's small kernels (next window, prefix sum, column
+// list) run on a third stream of the highest priority, after the generator of round r (the
+// column list's previous reader) and the FSM kernel of round r-1: their blocks then take the
+// first SM slots that FSM blocks of round r free, and only the generator kernel is left
+// between round r's last FSM blocks and round r+1.
 template <typename T>
 static fsmc_status run_fsm_pipelined(fsmc_job* j, cudaStream_t st) {
   if (!j->side) {
@@ -852,6 +857,13 @@ static fsmc_status run_fsm_pipelined(fsmc_job* j, cudaStream_t st) {
       CK(cudaEventCreateWithFlags(&j->ev_gen[p], cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&j->ev_fsm[p], cudaEventDisableTiming));
     }
+  }
+  const bool split = sizeof(T) == 4 && j->tun.generator == 2;
+  if (split && !j->side_hi) {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&j->side_hi, cudaStreamNonBlocking, greatest));
+    CK(cudaEventCreateWithFlags(&j->ev_cols, cudaEventDisableTiming));
   }
   cudaStream_t sb = j->side;
   EssView<T> v[2];
@@ -878,11 +890,27 @@ static fsmc_status run_fsm_pipelined(fsmc_job* j, cudaStream_t st) {
       CK(launch_ess_fsm<T>(v[p], tu.lanes_per_chain, tu.steps_per_launch, tu.threads_per_block, st));
     }
     CK(cudaEventRecord(j->ev_fsm[p], st));
-    if (r >= 1) CK(cudaStreamWaitEvent(sb, j->ev_fsm[p ^ 1], 0));
-    CK(launch_ess_window<T>(v[p ^ 1], v[p].gen_hi, sb));
-    {
-      ProfScope ps(j, 0, sb);
-      CK(ess_generate<T>(j, v[p ^ 1], sb));
+    if (split) {
+      if constexpr (sizeof(T) == 4) {
+        cudaStream_t sh = j->side_hi;
+        if (r >= 1) CK(cudaStreamWaitEvent(sh, j->ev_fsm[p ^ 1], 0));
+        CK(cudaStreamWaitEvent(sh, j->ev_gen[p], 0));
+        CK(launch_ess_window<T>(v[p ^ 1], v[p].gen_hi, sh));
+        CK(launch_ess_tc_cols(v[p ^ 1], sh));
+        CK(cudaEventRecord(j->ev_cols, sh));
+        CK(cudaStreamWaitEvent(sb, j->ev_cols, 0));
+        {
+          ProfScope ps(j, 0, sb);
+          CK(launch_ess_tc_gen(v[p ^ 1], j->tg->tc_img, j->e->sms, sb));
+        }
+      }
+    } else {
+      if (r >= 1) CK(cudaStreamWaitEvent(sb, j->ev_fsm[p ^ 1], 0));
+      CK(launch_ess_window<T>(v[p ^ 1], v[p].gen_hi, sb));
+      {
+        ProfScope ps(j, 0, sb);
+        CK(ess_generate<T>(j, v[p ^ 1], sb));
+      }
     }
     CK(cudaEventRecord(j->ev_gen[p ^ 1], sb));
     j->launches += 3;
@@ -1340,6 +1368,8 @@ extern "C" void fsmc_job_destroy(fsmc_job* j) {
     if (j->ev_fsm[p]) cudaEventDestroy(j->ev_fsm[p]);
   }
   if (j->side) cudaStreamDestroy(j->side);
+  if (j->ev_cols) cudaEventDestroy(j->ev_cols);
+  if (j->side_hi) cudaStreamDestroy(j->side_hi);
   if (j->dev) {
     cudaSetDevice(e->device);
     // a job run through fsmc_job_run has no work in flight; one the scheduler ran is freed

@@ -90,6 +90,8 @@ struct fsmc_job {
   // pipelined ESS rounds: second stream and the events ordering the two
   cudaStream_t side = nullptr;
   cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_fsm[2] = {nullptr, nullptr};
+  cudaStream_t side_hi = nullptr;  // high-priority stream of the refills' column lists
+  cudaEvent_t ev_cols = nullptr;
   size_t o_win = 0;  // second refill-window buffer [2][m]
   size_t o_colbase = 0, o_colmap = 0;  // compacted refill list: [m+1] prefix sums, [m*W] (chain, sample)
   size_t o_work = 0;  // block-likelihood ESS: chain counter of the current FSM launch

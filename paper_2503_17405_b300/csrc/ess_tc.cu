@@ -512,19 +512,29 @@ cudaError_t launch_ess_tc_build(const float* L, int d, unsigned char* img, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_ess_nu_gen_tc(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st) {
+cudaError_t launch_ess_tc_cols(const EssView<float>& v, cudaStream_t st) {
   if (!v.colmap || !v.col_base) return cudaErrorInvalidValue;  // the generator walks the compacted list
-  const int smem = tc_smem_bytes(v.tg.d);
-  cudaError_t e = cudaFuncSetAttribute(ess_nu_gen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   ess_col_scan_kernel<<<1, 1024, 0, st>>>(v.gen_lo, v.gen_hi, v.m, v.col_base);
   ess_col_fill_kernel<<<(unsigned)((v.m + 255) / 256), 256, 0, st>>>(v.gen_lo, v.gen_hi, v.col_base, v.m,
                                                                      v.colmap);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ess_tc_gen(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st) {
+  if (!v.colmap || !v.col_base) return cudaErrorInvalidValue;
+  const int smem = tc_smem_bytes(v.tg.d);
+  cudaError_t e = cudaFuncSetAttribute(ess_nu_gen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   const long long ntiles = ((long long)v.m * v.W + TC_N - 1) / TC_N;
   const int grid = (int)std::max(1LL, std::min<long long>(ntiles, sms));
   ess_nu_gen_tc_kernel<<<grid, TC_THREADS, smem, st>>>(v, img);
   return cudaGetLastError();
+}
+
+cudaError_t launch_ess_nu_gen_tc(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st) {
+  cudaError_t e = launch_ess_tc_cols(v, st);
+  if (e != cudaSuccess) return e;
+  return launch_ess_tc_gen(v, img, sms, st);
 }
 
 }  // namespace fsmc

@@ -121,6 +121,10 @@ int ess_group_E(int G, int d);
 size_t ess_tc_image_bytes(int d);
 cudaError_t launch_ess_tc_build(const float* L, int d, unsigned char* img, cudaStream_t st);
 cudaError_t launch_ess_nu_gen_tc(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st);
+// its two halves: the compacted column list of the refill (prefix sum over the chains' refill
+// counts, then the (chain, sample) list), and the generator kernel that walks it
+cudaError_t launch_ess_tc_cols(const EssView<float>& v, cudaStream_t st);
+cudaError_t launch_ess_tc_gen(const EssView<float>& v, const unsigned char* img, int sms, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_dr_fsm(const DrView<T>& v, int budget, int threads, cudaStream_t st);
