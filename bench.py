@@ -342,13 +342,21 @@ def run_ours(args, rank, world):
         kname = {"ess": "ess_block_fsm_kernel" if w["kind"] == "gp_reg" else "ess_fsm_kernel",
                  "dr": "dr_fsm_kernel", "slice": "slice_fsm_kernel",
                  "nuts": "nuts_fsm_batched_kernel" if w["kind"] == "logreg" else "nuts_fsm_kernel"}[cfg["algo"]]
+        traffic, traffic_src = None, None
+        if cfg["algo"] == "ess" and w["kind"] == "gp_logit" and d == 256 and tun.get("lanes_per_chain") == 32:
+            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FSM-step launch on 4096
+            # chains (60.5 MB + 12.5 MB, 64 states per chain), scaled by the chains of a launch
+            traffic = (60.5e6 + 12.5e6) * m / 4096
+            traffic_src = "bytes per launch: ncu capture on 4096 chains x 400 samples, scaled to the launch's chains"
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
+                "traffic_source": traffic_src,
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (nominal)",
                 "flops_per_step": per,
                 "limiter": {"ess": "a warp per chain: length-j dot products per covariance column, shared-memory bound" if w["kind"] == "gp_reg"
-                            else "instruction issue (~190 warp instructions per state; 2 MUFU per coordinate)",
+                            else "instruction issue (~145 warp instructions per state; one ex2 per coordinate, one lg2 per eight)"
+                            if w["kind"] == "gp_logit" else "latency: few chains (one warp each), short rows",
                             "dr": "latency: one chain per thread, ~14 resident warps per SM at 65536 chains",
                             "slice": "latency: one chain per thread, 65536 chains",
                             "nuts": "latency and occupancy of the block-batched gradient" if w["kind"] == "logreg"
