@@ -345,9 +345,10 @@ def run_ours(args, rank, world):
         traffic, traffic_src = None, None
         if cfg["algo"] == "ess" and w["kind"] == "gp_logit" and d == 256 and tun.get("lanes_per_chain") == 32:
             # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FSM-step launch on 4096
-            # chains (60.5 MB + 12.5 MB, 64 states per chain), scaled by the chains of a launch
-            traffic = (60.5e6 + 12.5e6) * m / 4096
-            traffic_src = "bytes per launch: ncu capture on 4096 chains x 400 samples, scaled to the launch's chains"
+            # chains at 64 states per chain (60.5 MB + 12.5 MB), scaled by the states of a launch
+            traffic = (60.5e6 + 12.5e6) * (m / 4096) * (tun.get("steps_per_launch", 64) / 64)
+            traffic_src = ("bytes per launch: ncu capture on 4096 chains x 64 states, scaled by chains and "
+                           "states per launch")
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,

@@ -363,10 +363,17 @@ static void default_tuning(fsmc_job* j) {
       const int64_t thread_slots = (int64_t)j->e->sms * 1024;
       tu.lanes_per_chain = (j->d > 32 || j->d >= 64 || j->m * 8 < thread_slots) ? 32 : 1;
     }
-    if (!tu.steps_per_launch) tu.steps_per_launch = 64;
-    if (!tu.ring_slots) tu.ring_slots = 32;
-    if (!tu.threads_per_block) tu.threads_per_block = 256;
     if (!tu.generator) tu.generator = (j->prec == FSMC_FP32 && j->d <= 256) ? 2 : 1;
+    // Large jobs on the tensor-core generator take long rounds: each refill launch pays a fixed
+    // cost (the L image's copy into every CTA, tensor-memory set-up, pipeline fill and drain)
+    // and each FSM launch a tail, so fewer, larger rounds are faster (16384 chains, d = 256:
+    // 51.2 ms per job at 64 states per launch and 32 ring slots, 47.5 at 192 / 64, 46.6 at
+    // 384 / 128).  The ring grows with them (m x 128 x d x 4 bytes, 2.1 GB at 16384 x 256).
+    // Smaller jobs keep short rounds, which also bound a serving round's length.
+    const bool long_rounds = tu.generator == 2 && j->m >= 4096;
+    if (!tu.steps_per_launch) tu.steps_per_launch = long_rounds ? 384 : 64;
+    if (!tu.ring_slots) tu.ring_slots = long_rounds ? 128 : 32;
+    if (!tu.threads_per_block) tu.threads_per_block = 256;
     if (!tu.pipelined) tu.pipelined = 1;
   } else if (j->algo == FSMC_DR || j->algo == FSMC_SLICE) {
     tu.lanes_per_chain = 1;
