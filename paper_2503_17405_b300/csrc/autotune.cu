@@ -64,14 +64,16 @@ std::vector<fsmc_tuning> candidates(fsmc_target* t, fsmc_algo algo, fsmc_precisi
     if (t->d > 32 && t->d <= 256) lanes.push_back(8);
     std::vector<int> gens = {1};
     if (prec == FSMC_FP32 && t->d <= 256) gens.push_back(2);
+    // (states per launch, ring slots): short rounds, and the long rounds that amortise the
+    // refill and FSM launches' fixed costs on large jobs
+    const int shapes[][2] = {{32, 32}, {32, 64}, {64, 32}, {64, 64}, {128, 32}, {128, 64}, {384, 128}};
     for (int G : lanes)
-      for (int steps : {32, 64, 128})
-        for (int ring : {32, 64})
-          for (int gen : gens)
-            for (int threads : (G == 1 ? std::vector<int>{128, 256} : std::vector<int>{256}))
-              c.push_back(fsmc_tuning{G, steps, ring, threads, 0, gen, 0});
+      for (const auto& sr : shapes)
+        for (int gen : gens)
+          for (int threads : (G == 1 ? std::vector<int>{128, 256} : std::vector<int>{256}))
+            c.push_back(fsmc_tuning{G, sr[0], sr[1], threads, 0, gen, 0});
   } else if (algo == FSMC_DR || algo == FSMC_SLICE) {
-    for (int steps : {64, 128, 256, 512})
+    for (int steps : {64, 128, 256, 512, 1024})
       for (int threads : {64, 128, 256}) c.push_back(fsmc_tuning{1, steps, 0, threads, 0, 0, 0});
   } else {
     for (int steps : {32, 128, 256}) c.push_back(fsmc_tuning{32, steps, 0, 128, 0, 0, 0});

@@ -377,7 +377,9 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.pipelined) tu.pipelined = 1;
   } else if (j->algo == FSMC_DR || j->algo == FSMC_SLICE) {
     tu.lanes_per_chain = 1;
-    if (!tu.steps_per_launch) tu.steps_per_launch = 256;
+    // long launches: fewer kernel tails (funnel, 65536 chains: DR 48.8 -> 48.0 ms, slice 47.4 ->
+    // 45.9 ms per job from 256 to 1024 states per launch)
+    if (!tu.steps_per_launch) tu.steps_per_launch = 1024;
     if (!tu.threads_per_block) tu.threads_per_block = 128;
   } else {
     if (!tu.lanes_per_chain) tu.lanes_per_chain = 32;
