@@ -345,9 +345,9 @@ def run_ours(args, rank, world):
         traffic, traffic_src = None, None
         if cfg["algo"] == "ess" and w["kind"] == "gp_logit" and d == 256 and tun.get("lanes_per_chain") == 32:
             # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FSM-step launch on 4096
-            # chains at 64 states per chain (60.5 MB + 12.5 MB), scaled by the states of a launch
-            traffic = (60.5e6 + 12.5e6) * (m / 4096) * (tun.get("steps_per_launch", 64) / 64)
-            traffic_src = ("bytes per launch: ncu capture on 4096 chains x 64 states, scaled by chains and "
+            # chains at 384 states per chain (304.6 MB + 255.5 MB), scaled by the states of a launch
+            traffic = (304.6e6 + 255.5e6) * (m / 4096) * (tun.get("steps_per_launch", 384) / 384)
+            traffic_src = ("bytes per launch: ncu capture on 4096 chains x 384 states, scaled by chains and "
                            "states per launch")
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s",
