@@ -60,6 +60,30 @@ def test_fp32_gp_logit_matches_oracle_until_branch_flip(eng):
     job.close()
 
 
+def test_fp32_gp_logit_overflowing_group_products_match_oracle(eng):
+    # Chains start at x = -20 s: every coordinate has t' = 20 log2(e) ~ 28.9, so each lane's
+    # group of eight factors 1 + 2^t' (coordinates l, l + 32, ..., l + 224) exceeds 2^126 in single
+    # precision and the likelihood takes its per-coordinate form until the chains move inwards.
+    w = W.gp_logit(256)
+    m, n = 32, 60
+    x0 = np.tile(-20.0 * w["s"][None, :], (m, 1))
+    t = (-w["s"] * x0[0] * np.log2(np.e)).astype(np.float32)
+    with np.errstate(over="ignore"):
+        groups = (1.0 + np.exp2(t)).reshape(8, 32).prod(axis=0, dtype=np.float32)
+    assert (groups > np.float32(2.0 ** 126)).all()
+    a = _run(eng, w, m, n, x0, "fp32", "fsm")
+    b = _run(eng, w, m, n, x0, "fp32", "sync")
+    ref = O.run("ess", "gp_logit", w["params"], x0, n, seed=1)
+    ca, _, _ = a.loop_counts()
+    cb, _, _ = b.loop_counts()
+    assert np.array_equal(ca, cb) and np.array_equal(a.samples(), b.samples())
+    r = compare(a.samples(), ca, ref["samples"], ref["counts"], "fp32")
+    print("overflowing products: flipped", r["flipped"], "of", m, "max err", r["max_err"])
+    assert r["flipped"] <= m // 4
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("d", [100, 200, 256])
 def test_tensor_core_generator_matches_oracle(eng, d):
     """The tcgen05 direction generator (FP16 hi/lo splits, FP32 accumulation) and the CUDA-core
