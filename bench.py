@@ -342,17 +342,20 @@ def run_ours(args, rank, world):
         kname = {"ess": "ess_block_fsm_kernel" if w["kind"] == "gp_reg" else "ess_fsm_kernel",
                  "dr": "dr_fsm_kernel", "slice": "slice_fsm_kernel",
                  "nuts": "nuts_fsm_batched_kernel" if w["kind"] == "logreg" else "nuts_fsm_kernel"}[cfg["algo"]]
-        traffic, traffic_src = None, None
+        traffic, traffic_src, issue = None, None, None
         if cfg["algo"] == "ess" and w["kind"] == "gp_logit" and d == 256 and tun.get("lanes_per_chain") == 32:
             # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FSM-step launch on 4096
             # chains at 384 states per chain (304.6 MB + 255.5 MB), scaled by the states of a launch
             traffic = (304.6e6 + 255.5e6) * (m / 4096) * (tun.get("steps_per_launch", 384) / 384)
             traffic_src = ("bytes per launch: ncu capture on 4096 chains x 384 states, scaled by chains and "
                            "states per launch")
+            issue = {"issue_active": 0.740, "eligible_warps_per_scheduler": 1.98,
+                     "source": "ncu --set full, FSM step on 4096 chains x 384 states (profiles/)"}
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
                 "traffic_source": traffic_src,
+                "ncu_issue": issue,
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (nominal)",
                 "flops_per_step": per,
                 "limiter": {"ess": "a warp per chain: length-j dot products per covariance column, shared-memory bound" if w["kind"] == "gp_reg"

@@ -784,6 +784,12 @@ static cudaError_t ess_generate(fsmc_job* j, const EssView<T>& v, cudaStream_t s
   return launch_ess_nu_gen<T>(v, st);
 }
 
+// kernels one ess_generate call launches: prefix sum, column list and generator on the tensor
+// cores, the generator alone on the CUDA cores
+static int ess_generate_kernels(const fsmc_job* j) {
+  return (j->prec == FSMC_FP32 && j->tun.generator == 2) ? 3 : 1;
+}
+
 // One FSM round: (ESS) refill the rings, then advance every chain by the step budget.
 template <typename T>
 static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
@@ -801,7 +807,7 @@ static cudaError_t fsm_round(fsmc_job* j, cudaStream_t st) {
     }
     ProfScope p(j, 1, st);
     e = launch_ess_fsm<T>(v, tu.lanes_per_chain, tu.steps_per_launch, tu.threads_per_block, st);
-    j->launches += 2;
+    j->launches += ess_generate_kernels(j) + 1;
   } else if (j->algo == FSMC_DR) {
     ProfScope p(j, 1, st);
     e = launch_dr_fsm<T>(dr_view<T>(j), tu.steps_per_launch, tu.threads_per_block, st);
@@ -889,6 +895,7 @@ static fsmc_status run_fsm_pipelined(fsmc_job* j, cudaStream_t st) {
     ProfScope p(j, 0, sb);
     CK(ess_generate<T>(j, v[0], sb));
   }
+  j->launches += ess_generate_kernels(j);
   CK(cudaEventRecord(j->ev_gen[0], sb));
   int p = 0;
   int64_t r = 0;
@@ -922,7 +929,7 @@ static fsmc_status run_fsm_pipelined(fsmc_job* j, cudaStream_t st) {
       }
     }
     CK(cudaEventRecord(j->ev_gen[p ^ 1], sb));
-    j->launches += 3;
+    j->launches += 2 + ess_generate_kernels(j);  // FSM step, window, refill
     ++r;
     p ^= 1;
     if (r % 8 == 0) {
@@ -955,7 +962,7 @@ static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
     fsmc_status s = capture_rounds<T>(j, check_every, st);
     if (s != FSMC_OK) return s;
   }
-  const int per_round = j->algo == FSMC_ESS && !ess_block(j) ? 2 : 1;
+  const int per_round = j->algo == FSMC_ESS && !ess_block(j) ? ess_generate_kernels(j) + 1 : 1;
   int64_t r = 0;
   while (true) {
     int done = 0, err = 0;
@@ -1014,7 +1021,7 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
       CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
       ProfScope p(j, 2, st);
       CK(launch_ess_sync<T>(v, j->tun.lanes_per_chain, (int)t0, t1, bar, active, iters, threads, st));
-      j->launches += 4;
+      j->launches += 3 + ess_generate_kernels(j);  // two window fills, the refill, the sync kernel
     }
   } else if (j->algo == FSMC_DR) {
     DrView<T> v = dr_view<T>(j);
