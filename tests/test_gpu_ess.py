@@ -47,6 +47,24 @@ def test_fp64_conjugate_gaussian_matches_oracle(eng, lanes, mode):
     job.close()
 
 
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_long_shrink_sequences_match_oracle(eng, mode):
+    # A likelihood 250 times narrower than the prior (noise sd 0.002) makes most samples shrink
+    # the bracket more than 15 times, so chain-per-warp runs take their random numbers from
+    # the lane cache's wide layout (draws 16 and beyond of a sample) as well as the two-sample
+    # narrow one.
+    w = W.gauss_conj(16, noise_sd=0.002)
+    m, n = 64, 100
+    x0 = np.tile(w["post_mean"][None, :], (m, 1))
+    job = _run(eng, w, m, n, x0, "fp64", mode, tuning={"lanes_per_chain": 32})
+    ref = O.run("ess", "gauss_conj", w["params"], x0, n, seed=1)
+    counts, _, _ = job.loop_counts()
+    assert (ref["counts"] >= 16).mean() > 0.25
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    job.close()
+
+
 def test_fp32_gp_logit_matches_oracle_until_branch_flip(eng):
     w = W.gp_logit(256)
     m, n = 48, 400
