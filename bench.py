@@ -181,7 +181,7 @@ def oracle_throughput(cfg, target_s=10.0):
 
 # ---- multi-GPU aggregation (independent chains per rank: weak scaling) -----------------------------
 def max_over_ranks(value, dist=None, device="cpu"):
-    """Slowest rank's timed region: the all-reduce MAX is the only collective of the run."""
+    """Slowest rank's time for a timed region (an all-reduce MAX, the only kind of collective of the run)."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
         return float(value)
     import torch
@@ -272,6 +272,32 @@ def run_ours(args, rank, world):
             sms.append(ms)
         sync = {"value": m * n / (sum(sms) / len(sms) / 1e3), "ms_per_step": sum(sms) / len(sms),
                 "sync_iterations": sst["sync_iterations"], "mean_max_N": sst["mean_max_N"]}
+
+    # moments-only mode (store = 0): the same job with every sample folded into per-chain
+    # compensated sums of x and x^2 as it is drawn instead of stored; timed like the store-all
+    # steps above (L2 flushed, CUDA events), after them, with one warm-up
+    mom_only = None
+    if not args.no_moments:
+        mjob = eng.job(tg, cfg["algo"], m, n, x0=cfg["x0"], seed=1 + rank, prec=cfg["prec"], store=False,
+                       dr=dr, nuts=nuts, tuning=tuning, slice=sl)
+
+        def mone():
+            mjob.reset()
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mjob.run("fsm", stream=sp)
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b)
+
+        mone()
+        mms = [mone() for _ in range(args.steps)]
+        mms_total = max_over_ranks(sum(mms), dist, "cuda")
+        mom_only = {"value": job_throughput(world, args.steps, m, n, mms_total), "unit": "samples/s",
+                    "ms_per_step": mms_total / args.steps,
+                    "store": "per-chain compensated sums of x and x^2 only"}
+        mjob.close()
 
     # Pipelined ESS refills run on a second stream and overlap the FSM kernel, so their event
     # times include waiting for SMs.  One extra job (outside the timed region) with the refills
@@ -417,6 +443,7 @@ def run_ours(args, rank, world):
                                                    "threads_per_block", "generator", "pipelined")}},
             "sync": sync,
             "speedup_fsm_over_sync": (value / world / sync["value"]) if sync else None,
+            "moments_only": mom_only,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -611,6 +638,7 @@ def main():
     ap.add_argument("--no-sync", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-moments", action="store_true", help="skip the moments-only (store = 0) leg")
     ap.add_argument("--scale", type=float, default=1.0, help="chains x scale (profiling only)")
     ap.add_argument("--samples", type=int, default=None, help="samples per chain (profiling only)")
     ap.add_argument("--serve-jobs", type=int, default=40)
