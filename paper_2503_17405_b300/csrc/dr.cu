@@ -64,8 +64,9 @@ __device__ __forceinline__ T sqdist(const T (&a)[E], const T (&b)[E], int d) {
 }
 
 template <typename T, int E>
-__device__ __forceinline__ void dr_emit(const DrView<T>& v, int64_t c, int t, const T (&x)[E]) {
-  chain_emit<T, E>(v, v.tg.d, c, t, x);
+__device__ __forceinline__ void dr_emit(const DrView<T>& v, int64_t c, int t, const T (&x)[E],
+                                        const MomSmem<T, E>& ms = MomSmem<T, E>{nullptr}) {
+  chain_emit<T, E>(v, v.tg.d, c, t, x, ms);
 }
 
 // The PROPOSE body of stage k in four parts: draw y_k ~ N(x, sigma_k^2 I); evaluate log pi(y_k);
@@ -282,10 +283,15 @@ __device__ __forceinline__ void dr_store(const DrView<T>& v, int64_t c, const T 
 // code.  Both forms compute the same samples, for the staged and the symmetric sampler (whose
 // centre and pi* are y1 and lp1).
 
-template <typename T, int E, bool CONDENSED>
+// MOMC: a moments-only job whose chains keep their running sums in dynamic shared memory
+// during the launch (MomSmem); the other instantiations update device memory per sample.
+template <typename T, int E, bool CONDENSED, bool MOMC = false>
 __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
+  extern __shared__ __align__(16) unsigned char dr_mom_smem[];
+  const MomSmem<T, E> ms{MOMC ? reinterpret_cast<T*>(dr_mom_smem) + (size_t)threadIdx.x * MomSmem<T, E>::kSlot : nullptr};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < v.m; c += stride) {
+    if constexpr (MOMC) mom_smem_load<T, E>(v, v.tg.d, c, ms);
     T x[E], y1[E], y2[E];
     dr_load<T, E>(v, c, x, y1, y2);
     T lp = v.lp[c], lp1 = v.lpy[c], lp2 = v.lpy[v.m + c];
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
       ++steps;
       if constexpr (CONDENSED) {
         if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, err)) {
-          dr_emit<T, E>(v, c, t, x);
+          dr_emit<T, E>(v, c, t, x, ms);
           v.counts[(size_t)c * v.n + t] = k + 1;
           ++t;
           k = 0;
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
           ++k;
         } else if (v.symmetric ? sdr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, yc, lpc)
                                : dr_decide<T, E>(v, key, t, j, lac, x, lp, y1, lp1, y2, lp2, yc, lpc, cc)) {
-          dr_emit<T, E>(v, c, t, x);
+          dr_emit<T, E>(v, c, t, x, ms);
           v.counts[(size_t)c * v.n + t] = j + 1;
           ++t;
           k = 0;
@@ -354,6 +360,7 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
     v.t[c] = t; v.k[c] = k;
     v.steps[c] += steps;
     if (err) atomicOr(v.err, err);
+    if constexpr (MOMC) mom_smem_store<T, E>(v, v.tg.d, c, ms);
   }
 }
 
@@ -432,8 +439,14 @@ __global__ void dr_init_kernel(DrView<T> v) {
 template <typename T, int E>
 static cudaError_t fsm_launch(const DrView<T>& v, int budget, int threads, cudaStream_t st) {
   const int64_t blocks = (v.m + threads - 1) / threads;
-  if (v.step_form == 2) dr_fsm_kernel<T, E, false><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
-  else dr_fsm_kernel<T, E, true><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  const size_t smem = mom_smem_bytes<T, E>(v, threads);
+  if (v.step_form == 2) {
+    if (smem) dr_fsm_kernel<T, E, false, true><<<(unsigned)blocks, threads, smem, st>>>(v, budget);
+    else dr_fsm_kernel<T, E, false><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  } else {
+    if (smem) dr_fsm_kernel<T, E, true, true><<<(unsigned)blocks, threads, smem, st>>>(v, budget);
+    else dr_fsm_kernel<T, E, true><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  }
   return cudaGetLastError();
 }
 

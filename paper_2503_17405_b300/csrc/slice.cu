@@ -201,8 +201,9 @@ __device__ __forceinline__ void slice_store(const SliceView<T>& v, int64_t c, co
 }
 
 template <typename T, int E>
-__device__ __forceinline__ void slice_finish(const SliceView<T>& v, int64_t c, SliceChain<T, E>& s) {
-  chain_emit<T, E>(v, v.tg.d, c, s.t, s.x);
+__device__ __forceinline__ void slice_finish(const SliceView<T>& v, int64_t c, SliceChain<T, E>& s,
+                                             const MomSmem<T, E>& ms = MomSmem<T, E>{nullptr}) {
+  chain_emit<T, E>(v, v.tg.d, c, s.t, s.x, ms);
   v.counts[(size_t)c * v.n + s.t] = s.nev;
   v.aux[(size_t)c * v.n + s.t] = s.s;
   s.t += 1;
@@ -210,13 +211,18 @@ __device__ __forceinline__ void slice_finish(const SliceView<T>& v, int64_t c, S
 }
 
 // FSM kernel: chain-per-thread, every chain advances `budget` evaluations.
-template <typename T, int E>
+// MOMC: a moments-only job whose chains keep their running sums in dynamic shared memory
+// during the launch (MomSmem); the other instantiation updates device memory per sample.
+template <typename T, int E, bool MOMC = false>
 __global__ void __launch_bounds__(256) slice_fsm_kernel(SliceView<T> v, int budget) {
+  extern __shared__ __align__(16) unsigned char slice_mom_smem[];
+  const MomSmem<T, E> ms{MOMC ? reinterpret_cast<T*>(slice_mom_smem) + (size_t)threadIdx.x * MomSmem<T, E>::kSlot : nullptr};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < v.m; c += stride) {
     SliceChain<T, E> s;
     slice_load<T, E>(v, c, s);
     if (s.t >= v.n) continue;
+    if constexpr (MOMC) mom_smem_load<T, E>(v, v.tg.d, c, ms);
     const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
     const int D = (v.tg.d + 3) / 4;
     int err = 0, steps = 0;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(256) slice_fsm_kernel(SliceView<T> v, int budg
       ++steps;
       if (pf.q < D + 2 && s.t + 1 < v.n) slice_draw_block<T, E>(key, s.t + 1, D, pf);
       if (slice_step<T, E>(v, key, s, err)) {
-        slice_finish<T, E>(v, c, s);
+        slice_finish<T, E>(v, c, s, ms);
         if (s.t == v.n) { s.k = SL_DONE; break; }
         slice_begin<T, E>(v, key, s, pf);
       }
@@ -235,6 +241,7 @@ __global__ void __launch_bounds__(256) slice_fsm_kernel(SliceView<T> v, int budg
     slice_store<T, E>(v, c, s);
     v.steps[c] += steps;
     if (err) atomicOr(v.err, err);
+    if constexpr (MOMC) mom_smem_store<T, E>(v, v.tg.d, c, ms);
   }
 }
 
@@ -313,7 +320,9 @@ __global__ void slice_init_kernel(SliceView<T> v) {
 template <typename T, int E>
 static cudaError_t fsm_launch(const SliceView<T>& v, int budget, int threads, cudaStream_t st) {
   const int64_t blocks = (v.m + threads - 1) / threads;
-  slice_fsm_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  const size_t smem = mom_smem_bytes<T, E>(v, threads);
+  if (smem) slice_fsm_kernel<T, E, true><<<(unsigned)blocks, threads, smem, st>>>(v, budget);
+  else slice_fsm_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
   return cudaGetLastError();
 }
 

@@ -70,26 +70,84 @@ __device__ __forceinline__ T full_logp(const TargetView<T>& tg, const T (&y)[E])
   return neg_inf<T>();
 }
 
+// One compensated (Kahan) step for the sum and the sum of squares of a coordinate; the square
+// is rounded on its own (no contraction into the subtraction), so every caller gets the same bits.
+template <typename T>
+__device__ __forceinline__ void kahan_moments(T& s, T& cs, T& s2, T& c2, T x) {
+  T y = x - cs;
+  T tt = s + y;
+  cs = (tt - s) - y;
+  s = tt;
+  T x2;
+  if constexpr (sizeof(T) == 4) x2 = __fmul_rn(x, x);
+  else x2 = __dmul_rn(x, x);
+  y = x2 - c2;
+  tt = s2 + y;
+  c2 = (tt - s2) - y;
+  s2 = tt;
+}
+
+// Moments-only jobs, one chain per thread: a chain's four running sums (sum and compensation of
+// x and of x^2, per coordinate) can be held in shared memory while a kernel advances the chain
+// -- loaded when it starts, written back when it stops -- so that device memory sees one read
+// and one write per chain and launch instead of one of each per sample.  Each thread owns a
+// slot of 4 E + 1 values ([4][E], padded to an odd stride so that the slots of a warp's 32
+// threads start in 32 different banks); every access is the slot base plus a constant.
+// slot null: the sums are updated in device memory.
 template <typename T, int E>
-__device__ __forceinline__ void chain_emit(const ChainsView<T>& v, int d, int64_t c, int t, const T (&x)[E]) {
+struct MomSmem {
+  T* slot;
+  static constexpr int kSlot = 4 * E + 1;
+  __device__ __forceinline__ T& at(int q, int e) const { return slot[q * E + e]; }
+};
+
+template <typename T, int E>
+__device__ __forceinline__ void mom_smem_load(const ChainsView<T>& v, int d, int64_t c, const MomSmem<T, E>& ms) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e < d) ms.at(q, e) = v.mom[q * v.mom_stride + (size_t)c * d + e];
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void mom_smem_store(const ChainsView<T>& v, int d, int64_t c, const MomSmem<T, E>& ms) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e < d) v.mom[q * v.mom_stride + (size_t)c * d + e] = ms.at(q, e);
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void chain_emit(const ChainsView<T>& v, int d, int64_t c, int t, const T (&x)[E],
+                                           const MomSmem<T, E>& ms = MomSmem<T, E>{nullptr}) {
   if (v.out) {
     T* dst = v.out + ((size_t)c * v.n + t) * d;
 #pragma unroll
     for (int e = 0; e < E; ++e)
       if (e < d) dst[e] = x[e];
+  } else if (ms.slot) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e < d) kahan_moments<T>(ms.at(0, e), ms.at(1, e), ms.at(2, e), ms.at(3, e), x[e]);
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if (e >= d) continue;
-      const size_t o = (size_t)c * d + e;
+      const size_t o = (size_t)c * d + e, st = v.mom_stride;
       T* mo = v.mom;
-      const size_t st = v.mom_stride;
-      T y = x[e] - mo[o + st]; T tt = mo[o] + y; mo[o + st] = (tt - mo[o]) - y; mo[o] = tt;
-      const T x2 = x[e] * x[e];
-      y = x2 - mo[o + 3 * st]; tt = mo[o + 2 * st] + y; mo[o + 3 * st] = (tt - mo[o + 2 * st]) - y;
-      mo[o + 2 * st] = tt;
+      kahan_moments<T>(mo[o], mo[o + st], mo[o + 2 * st], mo[o + 3 * st], x[e]);
     }
   }
+}
+
+// Dynamic shared memory for the moment sums of a chain-per-thread FSM launch: 0 (device memory)
+// for jobs that store their samples or when the block's slots would exceed 48 KB.
+template <typename T, int E>
+inline size_t mom_smem_bytes(const ChainsView<T>& v, int threads) {
+  const size_t b = (size_t)MomSmem<T, E>::kSlot * threads * sizeof(T);
+  return (v.out || b > 48 * 1024) ? 0 : b;
 }
 
 }  // namespace fsmc

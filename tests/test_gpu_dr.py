@@ -153,3 +153,24 @@ def test_fp32_symmetric_dr_sync_and_fsm_identical(eng):
         job.close()
     assert np.array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_moments_only_mode_matches_stored_samples(eng, prec, rtol):
+    # moments-only DR jobs keep each chain's compensated sums in shared memory during a launch
+    # (one device-memory read and write per chain and launch); short launches make the sums
+    # cross many launches
+    m, n = 512, 400
+    x0 = W.x0_funnel_exact(m)
+    tg = eng.target("funnel", 10)
+    a = eng.job(tg, "dr", m, n, x0=x0, seed=5, prec=prec, dr=DR, tuning={"steps_per_launch": 64})
+    b = eng.job(tg, "dr", m, n, x0=x0, seed=5, prec=prec, dr=DR, store=False, tuning={"steps_per_launch": 64})
+    a.run("fsm")
+    b.run("fsm")
+    xs = a.samples()
+    sx, sx2, nk = b.moments()
+    assert np.all(nk == n)
+    assert np.allclose(sx, xs.sum(1), rtol=rtol, atol=rtol * n)
+    assert np.allclose(sx2, (xs ** 2).sum(1), rtol=rtol, atol=rtol * n)
+    a.close()
+    b.close()

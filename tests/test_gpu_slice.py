@@ -114,3 +114,24 @@ def test_argument_checks(eng):
     tw = eng.target("gauss_diag", 40, wide["params"])
     with pytest.raises(fsmc.FsmcError):
         eng.job(tw, "slice", 8, 4)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_moments_only_mode_matches_stored_samples(eng, prec, rtol):
+    # moments-only slice jobs keep each chain's compensated sums in shared memory during a launch
+    w, x0, sl = _cases()["funnel"]
+    n = 300
+    tg = eng.target(w["kind"], w["d"], None)
+    jobs = []
+    for store in (True, False):
+        j = eng.job(tg, "slice", x0.shape[0], n, x0=x0, seed=3, prec=prec, store=store, slice=sl,
+                    tuning={"steps_per_launch": 64})
+        j.run("fsm")
+        jobs.append(j)
+    xs = jobs[0].samples()
+    sx, sx2, nk = jobs[1].moments()
+    assert np.all(nk == n)
+    assert np.allclose(sx, xs.sum(1), rtol=rtol, atol=rtol * n)
+    assert np.allclose(sx2, (xs ** 2).sum(1), rtol=rtol, atol=rtol * n)
+    for j in jobs:
+        j.close()
