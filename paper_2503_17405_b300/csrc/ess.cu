@@ -260,9 +260,12 @@ __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
   sum = t;
 }
 
+// mslot (moments-only jobs, optional): this lane's shared-memory copy of its coordinates'
+// running sums, [4][E] (sum, compensation, sum of squares, compensation), updated in place of
+// device memory with the same operations.
 template <typename T, int G, int E, bool FULL = false>
 __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, int lane,
-                                         const T (&x)[E]) {
+                                         const T (&x)[E], T* mslot = nullptr) {
   const int d = FULL ? E * G : v.tg.d;
   if (v.out) {
     T* dst = v.out + ((size_t)c * v.n + t) * d;
@@ -270,6 +273,19 @@ __device__ __forceinline__ void ess_emit(const EssView<T>& v, int64_t c, int t, 
     for (int e = 0; e < E; ++e) {
       const int k = e * G + lane;
       if (FULL || k < d) dst[k] = x[e];
+    }
+  } else if (mslot) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = e * G + lane;
+      if (k < d) {
+        T s = mslot[e], cs = mslot[E + e];
+        kahan_add(s, cs, x[e]);
+        mslot[e] = s; mslot[E + e] = cs;
+        T s2 = mslot[2 * E + e], c2 = mslot[3 * E + e];
+        kahan_add(s2, c2, x[e] * x[e]);
+        mslot[2 * E + e] = s2; mslot[3 * E + e] = c2;
+      }
     }
   } else {
 #pragma unroll
@@ -453,11 +469,22 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
 // group's shared-memory row `pf` (cp.async, 16 bytes per copy, L2 only) when sample t starts,
 // so that its ring row is on chip when t + 1 starts.  Only samples below gen_hi, whose
 // directions were generated before this launch, are copied.
-template <int G, int E, bool FULL, bool PF = false>
+// MOMC (moments-only jobs): the lane's running sums are held in its shared-memory slot mslot
+// ([4][E]) while the chain advances: loaded here, written back at the end.
+template <int G, int E, bool FULL, bool PF = false, bool MOMC = false>
 __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, int64_t c, int budget, int lane,
-                                                     float* pf = nullptr) {
+                                                     float* pf = nullptr, float* mslot = nullptr) {
   static_assert(!PF || (G == 32 && FULL && E % 4 == 0), "prefetch needs full 32-lane rows");
   const int d = FULL ? E * G : v.tg.d;
+  if constexpr (MOMC) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = e * G + lane;
+        if (FULL || k < d) mslot[q * E + e] = v.mom[q * v.mom_stride + (size_t)c * d + k];
+      }
+  }
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const unsigned gmask = group_mask<G>();
   float xs[E], ns[E];
@@ -560,7 +587,7 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
       float x[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) x[e] = flip_sign(xs[e], smask, e);
-      ess_emit<float, G, E, FULL>(v, c, t, lane, x);
+      ess_emit<float, G, E, FULL>(v, c, t, lane, x, MOMC ? mslot : nullptr);
       if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
       ++t;
       if (++slot == v.W) slot = 0;
@@ -573,6 +600,15 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
   if constexpr (PF) {
     if (pf_t >= 0) asm volatile("cp.async.wait_all;" ::: "memory");  // pf is reused by the next chain
     __syncwarp();
+  }
+  if constexpr (MOMC) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = e * G + lane;
+        if (FULL || k < d) v.mom[q * v.mom_stride + (size_t)c * d + k] = mslot[q * E + e];
+      }
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -616,7 +652,9 @@ __host__ __device__ constexpr int ess_min_blocks() {
 template <typename T, int G, int E, int MODE>
 constexpr bool kEssPrefetch = sizeof(T) == 4 && MODE == 2 && G == 32 && E % 4 == 0;
 
-template <typename T, int G, int E, int MODE>
+// MOMC (with the prefetch form, moments-only jobs): each thread's running sums in a dynamic
+// shared-memory slot of 4 E + 1 floats (odd stride: a warp's slots start in 32 banks).
+template <typename T, int G, int E, int MODE, bool MOMC = false>
 __global__ void __launch_bounds__(256, (ess_min_blocks<T, G, E, MODE>()))
 ess_fsm_kernel(EssView<T> v, int budget) {
   const int lane = threadIdx.x % G;
@@ -625,7 +663,14 @@ ess_fsm_kernel(EssView<T> v, int budget) {
   if constexpr (kEssPrefetch<T, G, E, MODE>) {
     __shared__ __align__(16) float pf_rows[8][E * G];
     float* pf = pf_rows[threadIdx.x / 32];
-    for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain_gp<G, E, true, true>(v, c, budget, lane, pf);
+    if constexpr (MOMC) {
+      extern __shared__ __align__(16) float ess_mom_smem[];
+      float* mslot = ess_mom_smem + (size_t)threadIdx.x * (4 * E + 1);
+      for (int64_t c = group; c < v.m; c += ngroups)
+        ess_advance_chain_gp<G, E, true, true, true>(v, c, budget, lane, pf, mslot);
+    } else {
+      for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain_gp<G, E, true, true>(v, c, budget, lane, pf);
+    }
   } else {
     for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, MODE>(v, c, budget, lane);
   }
@@ -955,8 +1000,15 @@ static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cuda
   }
   if constexpr (kEssGpFast<T, E>) {
     if (v.tg.kind == TGT_GP_LOGIT) {
-      if (v.tg.d == E * G) ess_fsm_kernel<T, G, E, 2><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
-      else ess_fsm_kernel<T, G, E, 1><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+      if (v.tg.d == E * G) {
+        const size_t momb = (size_t)threads * (4 * E + 1) * sizeof(float);
+        if (kEssPrefetch<T, G, E, 2> && !v.out && momb <= 48 * 1024)
+          ess_fsm_kernel<T, G, E, 2, true><<<(unsigned)blocks, threads, momb, st>>>(v, budget);
+        else
+          ess_fsm_kernel<T, G, E, 2><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+      } else {
+        ess_fsm_kernel<T, G, E, 1><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+      }
       return cudaGetLastError();
     }
   }

@@ -239,6 +239,24 @@ def test_moments_only_mode_matches_stored_samples(eng):
     b.close()
 
 
+def test_fp32_gp_logit_moments_only_matches_stored_samples(eng):
+    # full 32-lane rows (d = 256): the moments-only FSM kernel keeps each lane's sums in shared
+    # memory for the length of a launch; short launches make the sums cross many of them
+    w = W.gp_logit(256)
+    m, n = 128, 150
+    x0 = W.x0_normal(m, 256, scale=0.3)
+    tu = {"steps_per_launch": 32}
+    a = _run(eng, w, m, n, x0, "fp32", store=True, tuning=tu)
+    b = _run(eng, w, m, n, x0, "fp32", store=False, tuning=tu)
+    xs = a.samples()
+    sx, sx2, nk = b.moments()
+    assert np.all(nk == n)
+    assert np.allclose(sx, xs.sum(1), rtol=2e-5, atol=2e-5 * n)
+    assert np.allclose(sx2, (xs ** 2).sum(1), rtol=2e-5, atol=2e-5 * n)
+    a.close()
+    b.close()
+
+
 def test_admission_and_argument_errors(eng):
     from paper_2503_17405_b300 import fsmc
     small = fsmc.Engine(0, hbm_budget_bytes=1 << 20)
