@@ -392,6 +392,17 @@ def run_ours(args, rank, world):
                             "nuts": "latency and occupancy of the block-batched gradient" if w["kind"] == "logreg"
                             else "latency: one chain per warp, shuffle reductions per component and U-turn test"}[cfg["algo"]]}
 
+    # measured multiply-add rates of this device (outside the timed regions): context for the
+    # nominal FP32 peak the roofline fraction is taken against
+    try:
+        f32m, f64m = fsmc.probe_fma_peaks(dev)
+        roof["fp32_ffma_measured_tflops"] = f32m
+        roof["fp64_dfma_measured_tflops"] = f64m
+        if roof.get("unit") == "TFLOP/s" and roof.get("bound") == "alu" and roof.get("achieved"):
+            roof["frac_of_measured_ffma"] = roof["achieved"] / f32m
+    except fsmc.FsmcError as ex:
+        roof["fma_probe"] = str(ex)
+
     # end to end through the public API: host params and x0 in, posterior moments out
     # every step: target and job created from pinned host arrays (params, x0), the whole run, the
     # per-chain moments read back into pinned host arrays, the job closed; one untimed warm-up
