@@ -287,11 +287,15 @@ fsmc_status fsmc_wait_all(fsmc_engine* e, double timeout_s);
  * loads the library holds until the process exits.  A run needs about
  * n_chains * (4 d + 4 W roundup(d, 32) + 48) bytes, with W = 16 ring slots per chain lowered
  * to 8, 4 or 2 when needed to fit; larger runs fail with FSMC_EINVAL and a message stating
- * the limit.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.  The call
- * allocates nothing and returns when the run is complete.  All calls on a device share the
- * one array; each call first resets the parts that must start from zero, and calls that
- * overlap on the GPU (from other threads or streams) race with each other.
+ * the limit (n_chains above 32 MiB / 48 bytes is rejected before anything else is sized).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and keeps it for the life of the process, which assumes the device's primary context is
+ * not reset (cudaDeviceReset) while the library is loaded.  The call is synchronous: between
+ * bursts of launches it copies a device counter to the host and waits on the stream, so it
+ * cannot be issued while that stream is being captured into a graph.  It allocates nothing
+ * and returns when the run is complete.  All calls on a device share the one array; each
+ * call first resets the parts that must start from zero, and calls that overlap on the GPU
+ * (from other threads or streams) race with each other.
  * Errors: EINVAL, ECUDA, ETIMEOUT, EDEVICE. */
 fsmc_status fsmc_ess_run_static(int target_kind, int d, const float* L_dev, const float* vec_dev,
                                 float noise_var, int64_t n_chains, int64_t n_samples,

@@ -30,9 +30,16 @@ def build(force=False, verbose=False, jobs=None):
     os.makedirs(objdir, exist_ok=True)
     procs = []
     objs = []
+    hdr_time = max(os.path.getmtime(p) for p in
+                   [os.path.join(CSRC, f) for f in HEADERS] +
+                   [os.path.join(HERE, "..", "include", "fsmc.h"), os.path.abspath(__file__)])
     for src in SOURCES:
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
         objs.append(obj)
+        # an object newer than its source and every header is up to date
+        if (not force and not verbose and os.path.exists(obj) and
+                os.path.getmtime(obj) > max(hdr_time, os.path.getmtime(os.path.join(CSRC, src)))):
+            continue
         cmd = [nvcc] + FLAGS + ARCH + ["-I", os.path.join(HERE, "..", "include"), "-c",
                                        os.path.join(CSRC, src), "-o", obj]
         if verbose:

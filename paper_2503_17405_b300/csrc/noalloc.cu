@@ -19,6 +19,9 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB per device
 constexpr int kMaxDevices = 64;
+// Lower bound on a chain's scratch bytes at any d >= 1 and W >= 2: its state (x, t, k, s, the two
+// window bounds, ell, logy, three angles, steps: at least 52 bytes) plus two 32-float ring rows.
+constexpr size_t kMinChainBytes = 48;
 
 // Shared by every call on a device.  Host code must not take its address directly: in
 // host code this name denotes a host-side shadow, not device memory.
@@ -70,6 +73,17 @@ extern "C" fsmc_status fsmc_ess_run_static(int target_kind, int d, const float* 
     return fsmc_fail(FSMC_EINVAL, "fsmc_ess_run_static: NULL device pointer");
   if (target_kind == FSMC_TGT_GAUSS_CONJ && !(noise_var > 0))
     return fsmc_fail(FSMC_EINVAL, "fsmc_ess_run_static: noise_var must be > 0");
+
+  // Every chain needs more than kMinChainBytes of scratch whatever W is, so a larger n_chains
+  // can never fit; rejecting it here also keeps the layout sums below from overflowing.
+  if (n_chains > (int64_t)(kStaticScratchBytes / kMinChainBytes)) {
+    char msg[256];
+    snprintf(msg, sizeof msg,
+             "fsmc_ess_run_static: %lld chains cannot fit the %zu-byte static scratch (at most %zu "
+             "chains of any d)",
+             (long long)n_chains, kStaticScratchBytes, kStaticScratchBytes / kMinChainBytes);
+    return fsmc_fail(FSMC_EINVAL, msg);
+  }
 
   // Ring depth: 16 directions per chain, fewer if that is what makes the run fit.
   const int dstride = (d + 31) / 32 * 32;

@@ -44,3 +44,15 @@ def test_errors_without_a_gpu_are_reported_not_raised():
     with pytest.raises(fsmc.FsmcError) as ei:
         fsmc.Engine(0)
     assert ei.value.status in (fsmc.ECUDA, fsmc.EINVAL)
+
+
+def test_static_scratch_entry_rejects_impossible_chain_counts_before_any_device_work():
+    # No chain fits in fewer than 48 bytes of the 32 MiB static scratch, so a chain count above
+    # 32 MiB / 48 is refused before the scratch layout is sized (its byte sums would otherwise
+    # wrap around) and before any CUDA call; the pointers are never dereferenced.
+    from paper_2503_17405_b300 import fsmc
+    fake = 1 << 20
+    for m in (1 << 62, (32 << 20) // 48 + 1):
+        st = fsmc.load().fsmc_ess_run_static(0, 1, fake, fake, 1.0, m, 1, fake, 1, 1, fake, fake, None)
+        assert st == fsmc.EINVAL
+        assert b"cannot fit" in fsmc.load().fsmc_last_error()
