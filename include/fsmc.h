@@ -49,7 +49,8 @@ typedef enum fsmc_status {
   FSMC_ECUDA = -4,    /* a CUDA runtime call failed; see fsmc_last_error()        */
   FSMC_ETIMEOUT = -5, /* a bounded device-side wait expired (error word set)      */
   FSMC_ESTATE = -6,   /* call not valid in the object's current state             */
-  FSMC_EDEVICE = -7   /* a kernel raised its error word (e.g. shrink cap reached) */
+  FSMC_EDEVICE = -7,  /* a kernel raised its error word (e.g. shrink cap reached) */
+  FSMC_ECANCELED = -8 /* a submitted job was cancelled (fsmc_cancel)              */
 } fsmc_status;
 
 /* Targets.  params_host layouts (doubles, row-major):
@@ -143,6 +144,12 @@ typedef struct fsmc_tuning {
                             per step (not condensed).
                             Samples and loop counts are the same in both forms; NUTS and
                             submitted (serving) jobs use form 1 only                       */
+  int barrier_spin_limit; /* SYNC mode: polls (each ~64 ns of sleep) a grid-barrier wait makes
+                            before it gives up with FSMC_ETIMEOUT; 0 = 2^24 (about 1-2 s)   */
+  int barrier_test_missing; /* test hook, 0 in production: 1 makes every grid barrier of a
+                            SYNC run wait for one block more than the grid has, so that the
+                            first wait of every block runs out, the kernel returns and the
+                            run fails with FSMC_ETIMEOUT (failure detection without a fault) */
 } fsmc_tuning;
 
 /* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */
@@ -263,6 +270,12 @@ void fsmc_job_destroy(fsmc_job* j);
 fsmc_status fsmc_submit(fsmc_engine* e, fsmc_job* j, fsmc_mode mode);
 /* *done = 1 when the job has finished; *latency_s = completion - submit (seconds). */
 fsmc_status fsmc_poll(fsmc_job* j, int* done, double* latency_s);
+/* Asks the scheduler to drop a submitted job: a queued job is never admitted, a running one is
+ * retired between rounds (no kernel of it is interrupted).  Returns at once; the job then
+ * finishes with status FSMC_ECANCELED (fsmc_poll reports done and returns that status) and its
+ * device memory is returned when it is destroyed.  A job that has already finished keeps its
+ * result and status.  Errors: EINVAL, ESTATE (the job was not submitted). */
+fsmc_status fsmc_cancel(fsmc_job* j);
 /* Blocks until every submitted job has finished or timeout_s elapses (ETIMEOUT). */
 fsmc_status fsmc_wait_all(fsmc_engine* e, double timeout_s);
 

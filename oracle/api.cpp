@@ -151,9 +151,11 @@ int ora_run(int algo, int kind, int d, int n_data, const double* params, const d
 
 // Independent single transitions: item i starts at x_in[i] as sample sample[i] of chain chain[i]
 // (the same random numbers as in a run) and writes the state it moves to.
+// margin (nullable) [n_items]: the smallest decision margin of each transition (oracle.h).
 int ora_transitions(int algo, int kind, int d, int n_data, const double* params, const double* algo_params,
                     int64_t n_items, const uint32_t* chain, const uint32_t* sample, const double* x_in,
-                    uint64_t seed, int n_threads, double* x_out, int32_t* counts, int32_t* aux) {
+                    uint64_t seed, int n_threads, double* x_out, int32_t* counts, int32_t* aux,
+                    double* margin) {
   if (d <= 0 || n_items < 0 || algo < 0 || algo > 4) return -1;
   Target t{kind, d, n_data, params};
   if (algo == 0 && t.prior_chol() == nullptr) return -1;
@@ -167,10 +169,12 @@ int ora_transitions(int algo, int kind, int d, int n_data, const double* params,
       std::copy(x_in + i * d, x_in + (i + 1) * d, x.begin());
       double lp = t.logp(x.data(), algo == 2 ? g.data() : nullptr);
       int depth = 0;
+      margin_reset();
       const int n = transition(algo, t, dp, np, sp, seed, chain[i], sample[i], x.data(), &lp, g.data(), &depth);
       std::copy(x.begin(), x.end(), x_out + i * d);
       counts[i] = n;
       aux[i] = depth;
+      if (margin) margin[i] = margin_min();
     }
   });
   return 0;

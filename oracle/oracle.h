@@ -119,4 +119,15 @@ int nuts_transition(const Target& t, const Stream& s, const NUTSParams& p, doubl
                     double* lp, double* grad, int* depth);
 void leapfrog(const Target& t, double* x, double* p, double* grad, double* lp, double eps);
 
+// ---- decision margins (instrumentation for single-precision comparisons) -----------
+// Every accept/reject, shrink/stop, merge and U-turn decision of a transition compares a
+// computed value with its threshold.  The samplers record, per thread, the smallest margin
+// they met: |a - b| / max(1, |b|) for a value a tested against a threshold b (log densities
+// against log y, log u against log alpha, H - H0 against the divergence bound), and
+// |rho . p| / (|rho| |p|) for a U-turn test.  A transition whose smallest margin lies within
+// the rounding error of single precision can take the other branch there; the values of the
+// transition do not depend on this bookkeeping.
+void margin_reset();
+double margin_min();
+
 }  // namespace ora

@@ -76,7 +76,7 @@ def lib():
             u32p = ctypes.POINTER(ctypes.c_uint32)
             L.ora_transitions.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
                                           ctypes.c_int64, u32p, u32p, dp, ctypes.c_uint64, ctypes.c_int,
-                                          dp, ip, ip]
+                                          dp, ip, ip, dp]
             L.ora_transitions.restype = ctypes.c_int
             L.ora_R_hat.argtypes = [ip, ctypes.c_int64, ctypes.c_int64]
             L.ora_R_hat.restype = ctypes.c_double
@@ -175,7 +175,9 @@ def run(algo, kind, params, x0, n_samples, seed, chain0=0, n_data=0, algo_params
 def transitions(algo, kind, params, x_in, chains, samples, seed, n_data=0, algo_params=None,
                 n_threads=None):
     """One transition per item: item i starts at x_in[i] as sample samples[i] of chain chains[i],
-    with the random numbers a run uses there.  Returns dict(x[k,d], counts[k], aux[k])."""
+    with the random numbers a run uses there.  Returns dict(x[k,d], counts[k], aux[k], margin[k]):
+    margin is the smallest relative distance between a compared value and its threshold over the
+    transition's decisions (accept/reject, stop/shrink, merge, U-turn; see oracle.h)."""
     x_in = _f64(x_in)
     k, d = x_in.shape
     params = _params(params)
@@ -186,13 +188,15 @@ def transitions(algo, kind, params, x_in, chains, samples, seed, n_data=0, algo_
     xo = np.zeros((k, d))
     counts = np.zeros(k, dtype=np.int32)
     aux = np.zeros(k, dtype=np.int32)
+    margin = np.zeros(k)
     u32p = ctypes.POINTER(ctypes.c_uint32)
     rc = lib().ora_transitions(ALGO[algo], TARGET[kind], d, n_data, _dp(params), _dp(ap), k,
                                ch.ctypes.data_as(u32p), sm.ctypes.data_as(u32p), _dp(x_in), seed,
-                               n_threads or os.cpu_count() or 1, _dp(xo), _ip(counts), _ip(aux))
+                               n_threads or os.cpu_count() or 1, _dp(xo), _ip(counts), _ip(aux),
+                               _dp(margin))
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
-    return {"x": xo, "counts": counts, "aux": aux}
+    return {"x": xo, "counts": counts, "aux": aux, "margin": margin}
 
 
 def R_hat(counts):

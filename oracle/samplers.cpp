@@ -14,6 +14,22 @@ static const int kMaxShrinks = 10000;  // safety cap; never reached in double pr
 
 static int normal_blocks(int d) { return (d + 3) / 4; }  // four normals per Philox block
 
+// smallest decision margin of the current transition on this thread (see oracle.h)
+static thread_local double t_margin = std::numeric_limits<double>::infinity();
+void margin_reset() { t_margin = std::numeric_limits<double>::infinity(); }
+double margin_min() { return t_margin; }
+static void note(double a, double b) {
+  const double m = std::fabs(a - b) / std::max(1.0, std::fabs(b));
+  if (m < t_margin) t_margin = m;  // NaN margins (non-finite values) are not recorded
+}
+static void note_cos(double dt, double nr, double np) {
+  const double den = std::sqrt(nr) * std::sqrt(np);
+  if (den > 0) {
+    const double m = std::fabs(dt) / den;
+    if (m < t_margin) t_margin = m;
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // Elliptical slice sampling (appendix Alg. 8), with these readings:
 //  * the loop continues while the proposal is NOT above the threshold (the printed
@@ -54,6 +70,7 @@ int ess_transition(const Target& t, const Stream& s, double* x, double* ell,
   };
   double ellp = propose(theta);
   int n = 0;
+  note(ellp, log_y);
   while (!(ellp > log_y)) {
     if (n == kMaxShrinks) return n;  // keep x (never happens in double precision)
     if (theta < 0) theta_min = theta; else theta_max = theta;
@@ -63,6 +80,7 @@ int ess_transition(const Target& t, const Stream& s, double* x, double* ell,
       trace[3 * n] = theta; trace[3 * n + 1] = theta_min; trace[3 * n + 2] = theta_max;
     }
     ellp = propose(theta);
+    note(ellp, log_y);
     ++n;
   }
   for (int k = 0; k < d; ++k) x[k] = xp[k];
@@ -83,8 +101,10 @@ double log1mexp(double a) {
   return a > -0.6931471805599453 ? std::log(-std::expm1(a)) : std::log1p(-std::exp(a));
 }
 
-// alpha_1(cur -> prop) = min(1, pi(prop) / pi(cur))
+// alpha_1(cur -> prop) = min(1, pi(prop) / pi(cur)); a proposal of zero density is never
+// accepted, also from a current state of zero density (where the ratio would be 0 / 0)
 double dr_log_alpha1(double lp_cur, double lp_prop) {
+  if (lp_prop == kNegInf) return kNegInf;
   return std::min(0.0, lp_prop - lp_cur);
 }
 
@@ -154,6 +174,7 @@ int dr_transition(const Target& t, const Stream& s, const DRParams& P, double* x
     lps[k + 1] = t.logp(yk, nullptr);
     double la = dr_stage_log_alpha(k, d, x, ys.data(), lps.data(), sig.data());
     Block b = s.block(0, base + (uint32_t)D);
+    note(std::log(uniform(b.w[0], b.w[1])), la);
     if (std::log(uniform(b.w[0], b.w[1])) < la) {
       for (int c = 0; c < d; ++c) x[c] = yk[c];
       *lp = lps[k + 1];
@@ -219,13 +240,17 @@ int slice_transition(const Target& t, const Stream& s, const SliceParams& P, dou
   // stepping out
   while (J > 0) {
     ++n;
-    if (!(at(L) > log_y)) break;
+    const double lpl = at(L);
+    note(lpl, log_y);
+    if (!(lpl > log_y)) break;
     L -= P.w;
     --J;
   }
   while (K > 0) {
     ++n;
-    if (!(at(R) > log_y)) break;
+    const double lpr = at(R);
+    note(lpr, log_y);
+    if (!(lpr > log_y)) break;
     R += P.w;
     --K;
   }
@@ -235,6 +260,7 @@ int slice_transition(const Target& t, const Stream& s, const SliceParams& P, dou
     const double th = L + (R - L) * uniform(bs.w[0], bs.w[1]);
     const double lpp = at(th);
     ++n;
+    note(lpp, log_y);
     if (lpp > log_y) {
       std::copy(xp.begin(), xp.end(), x);
       *lp = lpp;
@@ -259,6 +285,8 @@ int sdr_transition(const Target& t, const Stream& s, const DRParams& P, double* 
     const double lp_y = t.logp(y.data(), nullptr);
     const double la = sdr_log_alpha(*lp, lp_star, lp_y);
     Block b = s.block(0, base + (uint32_t)D);
+    note(std::log(uniform(b.w[0], b.w[1])), la);
+    note(lp_y, lp_star);
     if (std::log(uniform(b.w[0], b.w[1])) < la) {
       std::copy(y.begin(), y.end(), x);
       *lp = lp_y;
@@ -342,6 +370,7 @@ struct Builder {
       tr.rho = tr.edge.p;
       tr.prop = tr.edge;
       tr.logW = -H;
+      note(H - H0, P.max_dH);
       tr.valid = (H - H0 <= P.max_dH);  // false for NaN too
       return tr;
     }
@@ -353,11 +382,15 @@ struct Builder {
     tr.logW = logaddexp(left.logW, right.logW);
     uint32_t draw = ((uint32_t)j << 16) | ((uint32_t)(leaf0 >> level) << 4) | (uint32_t)level;
     Block b = s.block(2, draw);
+    note(std::log(uniform(b.w[0], b.w[1])), right.logW - tr.logW);
     tr.prop = (std::log(uniform(b.w[0], b.w[1])) < right.logW - tr.logW) ? right.prop : left.prop;
     tr.rho = left.rho;
     for (size_t k = 0; k < tr.rho.size(); ++k) tr.rho[k] += right.rho[k];
     tr.p_first = left.p_first;
     tr.edge = right.edge;
+    const double rr = dot(tr.rho, tr.rho);
+    note_cos(dot(tr.rho, tr.p_first), rr, dot(tr.p_first, tr.p_first));
+    note_cos(dot(tr.rho, tr.edge.p), rr, dot(tr.edge.p, tr.edge.p));
     tr.valid = dot(tr.rho, tr.p_first) > 0 && dot(tr.rho, tr.edge.p) > 0;
     return tr;
   }
@@ -387,10 +420,14 @@ int nuts_transition(const Target& t, const Stream& s, const NUTSParams& P, doubl
     double log_u = std::log(uniform(b.w[2], b.w[3]));
     Tree sub = B.build(v < 0 ? left : right, v, j, j, 0);
     if (!sub.valid) { ++j; break; }
+    note(log_u, sub.logW - logW);
     if (log_u < sub.logW - logW) prop = sub.prop;
     logW = logaddexp(logW, sub.logW);
     for (int k = 0; k < d; ++k) rho[k] += sub.rho[k];
     if (v < 0) left = sub.edge; else right = sub.edge;
+    const double rr = dot(rho, rho);
+    note_cos(dot(rho, left.p), rr, dot(left.p, left.p));
+    note_cos(dot(rho, right.p), rr, dot(right.p, right.p));
     if (!(dot(rho, left.p) > 0 && dot(rho, right.p) > 0)) { ++j; break; }
   }
   for (int k = 0; k < d; ++k) { x[k] = prop.x[k]; grad[k] = prop.g[k]; }

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfsmc.so")
 SOURCES = ["engine.cu", "ess.cu", "ess_block.cu", "ess_tc.cu", "dr.cu", "nuts.cu", "slice.cu", "serving.cu",
-           "noalloc.cu", "autotune.cu", "probe.cu"]
+           "noalloc.cu", "autotune.cu", "probe.cu", "stats.cu"]
 HEADERS = ["fsmc_device.cuh", "fsmc_kernels.h", "engine_internal.h", "target_logp.cuh", "ess_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread"]

@@ -34,8 +34,12 @@ __device__ __forceinline__ T l1m(T a) {
     return a > -0.6931471805599453 ? log(-expm1(a)) : log1p(-exp(a));
 }
 
+// alpha_1 = min(1, pi(prop) / pi(cur)), and 0 for a proposal of zero density even when the current
+// state has zero density too (0 / 0: a proposal outside the support is never accepted)
 template <typename T>
-__device__ __forceinline__ T la1(T lp_cur, T lp_prop) { return fmin(T(0), lp_prop - lp_cur); }
+__device__ __forceinline__ T la1(T lp_cur, T lp_prop) {
+  return lp_prop == neg_inf<T>() ? neg_inf<T>() : fmin(T(0), lp_prop - lp_cur);
+}
 
 template <typename T>
 __device__ __forceinline__ T la2(T pc, T pf, T ps, T q1_cf, T q1_sf) {

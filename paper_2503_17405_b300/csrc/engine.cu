@@ -405,6 +405,7 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
   j->o_momd = L.take(2 * m * d * 8);  // the sums as doubles, for the host read
   j->o_bar = L.take(64);
   j->o_iters = L.take(8);
+  j->o_stats = L.take(align_up(n * 4, 64) + sizeof(fsmc::DevStats));
   if (ess_block(j)) {
     j->o_ell = L.take(m * es);
     j->o_logy = L.take(m * es);
@@ -752,6 +753,8 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
     return fsmc_fail(FSMC_EINVAL, "NUTS and slice sampling have step form 1 only");
   if (t.generator == 2 && (j->algo != FSMC_ESS || j->prec != FSMC_FP32 || j->d > 256))
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
+  if (t.barrier_spin_limit < 0 || t.barrier_test_missing < 0 || t.barrier_test_missing > 1)
+    return fsmc_fail(FSMC_EINVAL, "barrier_spin_limit must be >= 0 and barrier_test_missing 0 or 1");
   j->tun = t;
   default_tuning(j);
   return FSMC_OK;
@@ -991,7 +994,7 @@ static fsmc_status run_fsm(fsmc_job* j, int64_t max_steps, cudaStream_t st) {
 template <typename T>
 static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
   char* b = j->dev;
-  GridBarrier bar{(unsigned*)(b + j->o_bar), (unsigned*)(b + j->o_bar) + 1};
+  GridBarrier bar = job_grid_barrier(j);
   unsigned* active = (unsigned*)(b + j->o_bar) + 4;
   unsigned long long* iters = (unsigned long long*)(b + j->o_iters);
   const int threads = j->tun.threads_per_block;
@@ -1236,37 +1239,28 @@ extern "C" fsmc_status fsmc_read_stats(fsmc_job* j, fsmc_stats* o) {
   *o = fsmc_stats{};
   o->R_hat = 1.0;
   if (!j->dev) return FSMC_OK;
-  const size_t m = (size_t)j->m, n = (size_t)j->n;
-  std::vector<int> counts(m * n), t(m);
-  std::vector<long long> steps(m);
-  CK(cudaMemcpy(counts.data(), j->dev + j->o_counts, m * n * 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(t.data(), j->dev + j->o_t, m * 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(steps.data(), j->dev + j->o_steps, m * 8, cudaMemcpyDeviceToHost));
-  unsigned long long iters = 0;
-  CK(cudaMemcpy(&iters, j->dev + j->o_iters, 8, cudaMemcpyDeviceToHost));
-  int err = 0;
-  CK(cudaMemcpy(&err, j->dev + j->o_err, 4, cudaMemcpyDeviceToHost));
-  const int tmin = *std::min_element(t.begin(), t.end());
-  double sum_all = 0, sum_max = 0;
-  for (int i = 0; i < tmin; ++i) {
-    int mx = 0;
-    for (size_t c = 0; c < m; ++c) {
-      const int v = counts[c * n + i];
-      mx = std::max(mx, v);
-      sum_all += v;
-    }
-    sum_max += mx;
-  }
+  CK(cudaSetDevice(j->e->device));
+  // reduced on the device (stats.cu); the host copies one record back
+  unsigned* colmax = (unsigned*)(j->dev + j->o_stats);
+  fsmc::DevStats* rec = (fsmc::DevStats*)(j->dev + j->o_stats + align_up((size_t)j->n * 4, 64));
+  CK(fsmc::launch_job_stats((const int*)(j->dev + j->o_counts), (const int*)(j->dev + j->o_t),
+                            (const long long*)(j->dev + j->o_steps), j->m, (int)j->n,
+                            (const unsigned long long*)(j->dev + j->o_iters), (const int*)(j->dev + j->o_err),
+                            colmax, rec, 0));
+  fsmc::DevStats h{};
+  CK(cudaMemcpy(&h, rec, sizeof h, cudaMemcpyDeviceToHost));
+  const long long tmin = h.tmin;
   if (tmin > 0) {
-    o->mean_N = sum_all / ((double)tmin * m);
-    o->mean_max_N = sum_max / tmin;
-    o->R_hat = sum_all > 0 ? o->mean_max_N / o->mean_N : 1.0;
+    o->mean_N = (double)h.sum_all / ((double)tmin * (double)j->m);
+    o->mean_max_N = (double)h.sum_max / (double)tmin;
+    o->R_hat = h.sum_all > 0 ? o->mean_max_N / o->mean_N : 1.0;
   }
-  for (size_t c = 0; c < m; ++c) { o->samples_done += t[c]; o->fsm_steps += steps[c]; }
-  o->sync_iterations = (int64_t)iters;
+  o->samples_done = h.samples_done;
+  o->fsm_steps = h.fsm_steps;
+  o->sync_iterations = h.iters;
   o->launches = j->launches;
   o->device_ms = j->device_ms;
-  o->error_word = err;
+  o->error_word = h.err;
   for (int k = 0; k < 4; ++k) { o->kernel_ms[k] = j->kernel_ms[k]; o->kernel_launches[k] = j->kernel_launches[k]; }
   o->columns_generated = j->columns_generated;
   return FSMC_OK;

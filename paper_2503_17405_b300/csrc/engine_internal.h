@@ -99,6 +99,7 @@ struct fsmc_job {
   int64_t spill_ctas = 0;                // beyond shared memory
   int rows_smem = 0;                     // covariance rows kept in shared memory
   size_t o_momd = 0;  // [2][m][d] doubles: the moment sums for the host read
+  size_t o_stats = 0;  // device statistics: [n] column maxima, then the DevStats record
   size_t arena_bytes = 0;  // size of the device block behind dev (>= bytes when reused)
   // serving
   bool submitted = false;
@@ -108,6 +109,14 @@ struct fsmc_job {
   fsmc_status serve_status = FSMC_OK;
   std::chrono::steady_clock::time_point t_submit, t_done;
 };
+
+// The job's grid barrier for synchronised launches, with the tuning's wait limit and test hook.
+inline fsmc::GridBarrier job_grid_barrier(const fsmc_job* j) {
+  fsmc::GridBarrier bar{(unsigned*)(j->dev + j->o_bar), (unsigned*)(j->dev + j->o_bar) + 1};
+  if (j->tun.barrier_spin_limit > 0) bar.spin_limit = (unsigned)j->tun.barrier_spin_limit;
+  bar.missing = (unsigned)j->tun.barrier_test_missing;
+  return bar;
+}
 
 fsmc_status fsmc_fail(fsmc_status st, const std::string& msg);
 fsmc_status fsmc_cuda_fail(cudaError_t e, const char* what);

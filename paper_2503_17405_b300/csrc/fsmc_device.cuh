@@ -152,11 +152,15 @@ __device__ __forceinline__ void group_sum_n(T (&v)[N], unsigned mask = 0xfffffff
 
 
 // ---- bounded grid barrier (cooperative launches only) ----------------------------------------
-// Sense-free generation barrier.  Every wait is bounded: after kBarrierSpinLimit polls the
-// block records ERR_BARRIER_TIMEOUT and returns false; callers then leave the kernel.
+// Sense-free generation barrier.  Every wait is bounded: after spin_limit polls (default
+// kBarrierSpinLimit) the block records ERR_BARRIER_TIMEOUT and returns false, and a block that
+// sees the bit set by another gives up at once; callers then leave the kernel.
 struct GridBarrier {
   unsigned* count;
   unsigned* generation;
+  unsigned spin_limit = kBarrierSpinLimit;  // polls before a wait gives up
+  unsigned missing = 0;  // test hook: arrivals every wait expects beyond the grid's blocks (0 in
+                         // production); with missing > 0 no barrier completes and every wait runs out
 };
 
 __device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
@@ -168,14 +172,14 @@ __device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
     volatile unsigned* gen = b.generation;
     const unsigned g = *gen;
     __threadfence();
-    if (atomicAdd(b.count, 1u) == nblocks - 1) {
+    if (atomicAdd(b.count, 1u) == nblocks - 1 + b.missing) {
       *b.count = 0;
       __threadfence();
       atomicAdd(b.generation, 1u);
     } else {
       unsigned spins = 0;
       while (*gen == g) {
-        if (++spins > kBarrierSpinLimit || *(volatile int*)err & ERR_BARRIER_TIMEOUT) {
+        if (++spins > b.spin_limit || *(volatile int*)err & ERR_BARRIER_TIMEOUT) {
           atomicOr(err, ERR_BARRIER_TIMEOUT);
           ok = 0;
           break;

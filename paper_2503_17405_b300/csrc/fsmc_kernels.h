@@ -158,6 +158,22 @@ template <typename T>
 cudaError_t launch_slice_init(const SliceView<T>& v, cudaStream_t st);
 
 cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st);
+
+// Device reduction of a job's run statistics (stats.cu): one record the host copies back.
+struct DevStats {
+  long long tmin;                // min_j t_j: samples every chain has completed
+  long long samples_done;        // sum_j t_j
+  long long fsm_steps;           // sum_j FSM states executed
+  unsigned long long sum_all;    // sum over i < tmin, all j, of N_ij
+  unsigned long long sum_max;    // sum over i < tmin of max_j N_ij
+  long long iters;               // synchronised loop-body iterations
+  long long err;                 // error word
+  long long pad;
+};
+// colmax: [n] scratch; out: the record (device memory).
+cudaError_t launch_job_stats(const int* counts, const int* t, const long long* steps, int64_t m, int n,
+                             const unsigned long long* iters, const int* err, unsigned* colmax,
+                             DevStats* out, cudaStream_t st);
 // dst[i] = (T) src[i], i < n (device arrays).
 template <typename T>
 cudaError_t launch_from_double(const double* src, int64_t n, T* dst, cudaStream_t st);

@@ -1193,7 +1193,7 @@ cudaError_t nuts_group_round(const std::vector<fsmc_job*>& jobs, MultiBuf& b, cu
 
 fsmc_status nuts_run_sync(fsmc_job* j, cudaStream_t st) {
   char* b = j->dev;
-  GridBarrier bar{(unsigned*)(b + j->o_bar), (unsigned*)(b + j->o_bar) + 1};
+  GridBarrier bar = job_grid_barrier(j);
   unsigned* active = (unsigned*)(b + j->o_bar) + 4;
   unsigned long long* iters = (unsigned long long*)(b + j->o_iters);
   const int chunk = 100;

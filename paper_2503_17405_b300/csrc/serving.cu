@@ -2,8 +2,10 @@
 //
 // fsmc_submit queues a job; a scheduler thread admits queued jobs in arrival order as
 // soon as their device footprint fits the engine's HBM budget (device memory is
-// allocated at admission, not at submission), then runs rounds.  In a round every admitted
-// FSM job advances by one fused launch per group of jobs that share a kernel shape
+// allocated at admission, not at submission), then runs rounds.  A job that does not fit
+// yet does not hold back the smaller jobs behind it, unless it has waited longer than
+// kAgingSeconds: then nothing behind it is admitted until it fits (no starvation).  In a
+// round every admitted FSM job advances by one fused launch per group of jobs that share a kernel shape
 // (sampler, precision, lanes per chain, coordinates per lane): all jobs of a group are one
 // launch over their concatenated chains, and groups go to separate streams so that their
 // work overlaps on the device.  After the round, finished jobs are retired (their latency
@@ -20,8 +22,18 @@ namespace {
 
 constexpr int kMaxActive = 128;
 constexpr int kStreams = 8;
+constexpr double kAgingSeconds = 1.0;
 
 using Clock = std::chrono::steady_clock;
+
+// A cancelled job leaves the scheduler (caller holds e->mu).
+void cancel_finish_locked(fsmc_engine* e, fsmc_job* j) {
+  j->serve_status = FSMC_ECANCELED;
+  j->t_done = Clock::now();
+  j->finished.store(1);
+  e->pending -= 1;
+  e->cv.notify_all();
+}
 
 void finish_job(fsmc_engine* e, fsmc_job* j, fsmc_status st) {
   j->serve_status = st;
@@ -47,10 +59,8 @@ void scheduler_main(fsmc_engine* e) {
       std::unique_lock<std::mutex> lk(e->mu);
       for (auto it = active.begin(); it != active.end();) {
         if ((*it)->cancel.load()) {
-          (*it)->finished.store(1);
-          e->pending -= 1;
+          cancel_finish_locked(e, *it);
           it = active.erase(it);
-          e->cv.notify_all();
         } else {
           ++it;
         }
@@ -60,14 +70,12 @@ void scheduler_main(fsmc_engine* e) {
         e->cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
-      // arrival order; a job whose footprint does not fit yet blocks the ones behind it
+      // arrival order; every queued job is tried (see the admission loop below)
       while (!e->queue.empty() && active.size() + to_admit.size() < (size_t)kMaxActive) {
         fsmc_job* j = e->queue.front();
         if (j->cancel.load()) {
           e->queue.pop_front();
-          j->finished.store(1);
-          e->pending -= 1;
-          e->cv.notify_all();
+          cancel_finish_locked(e, j);
           continue;
         }
         // the footprint is known only after layout: materialisation refuses with EADMIT
@@ -77,10 +85,18 @@ void scheduler_main(fsmc_engine* e) {
       }
     }
     std::vector<fsmc_job*> refused;
+    bool hold = false;  // an aged job ahead did not fit: keep every later job queued
+    const auto now = Clock::now();
     for (fsmc_job* j : to_admit) {
+      if (hold) {
+        refused.push_back(j);
+        continue;
+      }
       fsmc_status st = job_materialize(j, streams[0]);
       if (st == FSMC_EADMIT) {
         refused.push_back(j);
+        if (std::chrono::duration<double>(now - j->t_submit).count() > kAgingSeconds && j->bytes <= e->budget)
+          hold = true;
       } else if (st != FSMC_OK) {
         finish_job(e, j, st);
       } else {
@@ -232,6 +248,23 @@ extern "C" fsmc_status fsmc_poll(fsmc_job* j, int* done, double* latency_s) {
   if (done) *done = f;
   if (latency_s) *latency_s = f ? std::chrono::duration<double>(j->t_done - j->t_submit).count() : 0.0;
   if (f && j->serve_status != FSMC_OK) return fsmc_fail(j->serve_status, "job failed in the scheduler");
+  return FSMC_OK;
+}
+
+extern "C" fsmc_status fsmc_cancel(fsmc_job* j) {
+  if (!j) return fsmc_fail(FSMC_EINVAL, "job is NULL");
+  if (!j->submitted) return fsmc_fail(FSMC_ESTATE, "job was not submitted");
+  fsmc_engine* e = j->e;
+  std::lock_guard<std::mutex> g(e->mu);
+  if (j->finished.load()) return FSMC_OK;
+  auto it = std::find(e->queue.begin(), e->queue.end(), j);
+  if (it != e->queue.end()) {
+    e->queue.erase(it);
+    cancel_finish_locked(e, j);
+    return FSMC_OK;
+  }
+  j->cancel.store(1);  // admitted (or being admitted): retired before the next round
+  e->cv.notify_all();
   return FSMC_OK;
 }
 

@@ -11,9 +11,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfsmc.so")
 
-OK, EINVAL, ENOMEM, EADMIT, ECUDA, ETIMEOUT, ESTATE, EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, EADMIT, ECUDA, ETIMEOUT, ESTATE, EDEVICE, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7, -8
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EADMIT", -4: "ECUDA", -5: "ETIMEOUT",
-           -6: "ESTATE", -7: "EDEVICE"}
+           -6: "ESTATE", -7: "EDEVICE", -8: "ECANCELED"}
 TARGET = {"gauss_conj": 0, "gp_logit": 1, "funnel": 2, "logreg": 3, "gauss_diag": 4, "flat": 5, "mog": 6,
           "gp_reg": 7}
 ALGO = {"ess": 0, "dr": 1, "nuts": 2, "slice": 3}
@@ -44,7 +44,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("lanes_per_chain", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("ring_slots", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("profile_kernels", ctypes.c_int), ("generator", ctypes.c_int),
-                ("pipelined", ctypes.c_int), ("step_form", ctypes.c_int)]
+                ("pipelined", ctypes.c_int), ("step_form", ctypes.c_int),
+                ("barrier_spin_limit", ctypes.c_int), ("barrier_test_missing", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -99,6 +100,7 @@ SIGNATURES = [
     ("fsmc_probe_fma_peaks", ctypes.c_int, [ctypes.c_int, _dp, _dp]),
     ("fsmc_submit", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     ("fsmc_poll", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _dp]),
+    ("fsmc_cancel", ctypes.c_int, [_vp]),
     ("fsmc_wait_all", ctypes.c_int, [_vp, ctypes.c_double]),
     ("fsmc_ess_run_static", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_float,
                                            ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_uint64,
@@ -326,6 +328,9 @@ class Job:
 
     def submit(self, mode="fsm"):
         _check(load().fsmc_submit(self.engine.handle, self._h, MODE[mode]))
+
+    def cancel(self):
+        _check(load().fsmc_cancel(self._h))
 
     def poll(self):
         done = ctypes.c_int()

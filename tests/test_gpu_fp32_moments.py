@@ -1,0 +1,162 @@
+"""Single-precision (production mode) posterior moments against closed forms and against the
+double-precision runs, within 4 Monte Carlo standard errors.
+
+The FP32 trajectory tests compare samples with the FP64 oracle only up to a rounding-induced
+branch flip.  These tests check what remains after flips: that the FP32 chains still sample the
+right distribution.  Every chain is independent (its own keyed random numbers), so the mean over
+chains of each chain's average of a statistic has standard error sd(chain averages) / sqrt(m)
+whatever the autocorrelation within chains; chains that start at exact draws (or after the
+stated burn-in) make every chain average an unbiased estimate of the posterior expectation.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_17405_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+Z = 4.0  # bound in Monte Carlo standard errors
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2503_17405_b300 import build, fsmc
+    build.build()
+    e = fsmc.Engine(0)
+    yield e
+    e.close()
+
+
+def _within(name, est, se, truth):
+    z = np.abs(est - truth) / se
+    print("%s: max |z| = %.2f over %d statistics" % (name, z.max(), z.size))
+    assert np.all(np.isfinite(z)) and z.max() <= Z, (name, z.max(), est, truth, se)
+
+
+def _chain_averages(job, fns, burn=0, chunk=2048):
+    """Per-chain averages over samples burn.. of each statistic fn(x[c, i, :]) -> [c, i, k], read
+    from the job's device samples chunk by chunk (float64 accumulation on the GPU)."""
+    import torch
+    m, n, d = job.m, job.n, job.d
+    outs = []
+    for c0 in range(0, m, chunk):
+        nc = min(chunk, m - c0)
+        buf = torch.empty((nc, n, d), dtype=torch.float32, device="cuda")
+        job.samples_dev(buf.data_ptr(), c0, nc, 0, n, torch.cuda.current_stream().cuda_stream)
+        x = buf[:, burn:, :].double()
+        outs.append(torch.cat([f(x) for f in fns], dim=-1).mean(dim=1).cpu().numpy())
+        del buf, x
+    return np.concatenate(outs, axis=0)
+
+
+def _mean_se(avg):
+    return avg.mean(axis=0), avg.std(axis=0, ddof=1) / np.sqrt(avg.shape[0])
+
+
+def test_fp32_conjugate_gaussian_closed_form_from_zero(eng):
+    # Alg. 8 on the conjugate Gaussian exactly as configured (d = 16, 128 chains x 1000 samples
+    # from x0 = 0), in single precision; the first 10 % of samples are dropped
+    w = W.gauss_conj(16)
+    m, n = 128, 1000
+    tg = eng.target("gauss_conj", 16, w["params"])
+    job = eng.job(tg, "ess", m, n, x0=W.x0_zeros(m, 16), seed=1, prec="fp32")
+    job.run("fsm")
+    xs = job.samples()[:, n // 10:, :]
+    mu, var = w["post_mean"], np.diag(w["post_cov"])
+    avg = np.concatenate([xs.mean(1), ((xs - mu) ** 2).mean(1)], axis=1)
+    est, se = _mean_se(avg)
+    _within("FP32 ESS conj. Gaussian, 128 x 1000", est, se, np.concatenate([mu, var]))
+    job.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 32])
+def test_fp32_conjugate_gaussian_exact_start(eng, lanes):
+    # 16384 chains from exact posterior draws: every sample is a posterior draw, so the first and
+    # second moments and the cross moment of the two most correlated coordinates must hold
+    w = W.gauss_conj(16)
+    m, n = 16384, 200
+    C = np.linalg.cholesky(w["post_cov"])
+    x0 = w["post_mean"] + np.random.default_rng(11).standard_normal((m, 16)) @ C.T
+    tg = eng.target("gauss_conj", 16, w["params"])
+    job = eng.job(tg, "ess", m, n, x0=x0, seed=5, prec="fp32", tuning={"lanes_per_chain": lanes})
+    job.run("fsm")
+    mu, S = w["post_mean"], w["post_cov"]
+    off = np.abs(S - np.diag(np.diag(S)))
+    a, b = np.unravel_index(np.argmax(off), off.shape)
+    mu_t = mu.tolist()
+
+    def first(x):
+        return x
+
+    def second(x):
+        import torch
+        return (x - torch.tensor(mu_t, dtype=x.dtype, device=x.device)) ** 2
+
+    def cross(x):
+        return ((x[..., a] - mu_t[a]) * (x[..., b] - mu_t[b]))[..., None]
+
+    avg = _chain_averages(job, [first, second, cross])
+    est, se = _mean_se(avg)
+    truth = np.concatenate([mu, np.diag(S), [S[a, b]]])
+    _within("FP32 ESS conj. Gaussian exact start, lanes %d" % lanes, est, se, truth)
+    job.close()
+
+
+def _funnel_stats():
+    import torch
+
+    def f(x):
+        v = x[..., :1]
+        z = x[..., 1:] * torch.exp(-0.5 * v)
+        return torch.cat([v, v * v, (v < 0).double(), z, z * z], dim=-1)
+    return f, np.concatenate([[0.0, 9.0, 0.5], np.zeros(9), np.ones(9)])
+
+
+def test_fp32_dr_funnel_marginals_full_size(eng):
+    # the delayed-rejection configuration at full size (65536 chains x 5000 samples, FP32) from
+    # exact funnel draws: v ~ N(0, 9) (mean, second moment, P(v < 0) = 1/2) and the standardised
+    # z_i = x_i e^{-v/2} ~ N(0, 1)
+    m, n = 65536, 5000
+    tg = eng.target("funnel", 10)
+    job = eng.job(tg, "dr", m, n, x0=W.x0_funnel_exact(m), seed=1, prec="fp32",
+                  dr={"n_stages": 3, "scale0": 1.0, "factor": 0.5})
+    job.run("fsm")
+    f, truth = _funnel_stats()
+    est, se = _mean_se(_chain_averages(job, [f], chunk=1024))
+    _within("FP32 DR funnel 65536 x 5000", est, se, truth)
+    job.close()
+
+
+def test_fp32_slice_funnel_marginals_full_size(eng):
+    # the slice-sampling configuration (65536 chains x 2000 samples, w = 1, m = 100, FP32) from
+    # exact funnel draws
+    m, n = 65536, 2000
+    tg = eng.target("funnel", 10)
+    job = eng.job(tg, "slice", m, n, x0=W.x0_funnel_exact(m), seed=1, prec="fp32",
+                  slice={"w": 1.0, "m": 100})
+    job.run("fsm")
+    f, truth = _funnel_stats()
+    est, se = _mean_se(_chain_averages(job, [f], chunk=2048))
+    _within("FP32 slice funnel 65536 x 2000", est, se, truth)
+    job.close()
+
+
+def test_fp32_nuts_logreg_moments_match_fp64(eng):
+    # Logistic regression has no closed-form posterior: the FP32 run of the NUTS configuration
+    # (4096 chains x 1000 draws) against an independent double-precision run (other seed) of the
+    # same sampler, both after 100 burn-in draws from beta_true + 0.05 z; the difference of the
+    # two estimates has standard error sqrt(se32^2 + se64^2)
+    w = W.logreg(1000, 25)
+    nuts = {"eps": 0.05, "max_depth": 10, "max_dH": 1000.0}
+    tg = eng.target("logreg", 25, w["params"], n_data=1000)
+    burn = 100
+    res = []
+    for prec, m, n, seed in (("fp32", 4096, 1000, 1), ("fp64", 1024, 400, 77)):
+        job = eng.job(tg, "nuts", m, n, x0=W.x0_logreg(w, m), seed=seed, prec=prec, nuts=nuts)
+        job.run("fsm")
+        xs = job.samples()[:, burn:, :]
+        job.close()
+        avg = np.concatenate([xs.mean(1), (xs ** 2).mean(1)], axis=1)
+        res.append(_mean_se(avg))
+    (e32, s32), (e64, s64) = res
+    _within("FP32 vs FP64 NUTS logreg moments", e32 - e64, np.sqrt(s32 ** 2 + s64 ** 2), 0.0)

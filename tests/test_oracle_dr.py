@@ -224,3 +224,12 @@ def test_continuous_path_reversal_identity(seed):
                 assert abs(f - r) < 1e-9 * max(1.0, abs(f)), (k, f, r)
                 checked[k] += 1
     assert checked[1] > 50 and checked[2] > 50, checked
+
+
+def test_a_proposal_of_zero_density_is_never_accepted():
+    # alpha_1 = min(1, pi(y) / pi(x)) is 0 when pi(y) = 0, also from a state of zero density
+    # (0 / 0); the later stages inherit it through their numerators
+    assert O.dr_log_alpha1(-1.0, -np.inf) == -np.inf
+    assert O.dr_log_alpha1(-np.inf, -np.inf) == -np.inf
+    assert O.dr_log_alpha1(-np.inf, -3.0) == 0.0
+    assert O.dr_log_alpha2(-np.inf, -np.inf, -np.inf, -1.0, -1.0) == -np.inf

@@ -110,3 +110,50 @@ def test_logreg_short_run_deterministic():
               algo_params=[0.05, 10, 1000.0], n_threads=2)
     assert np.array_equal(a["samples"], b["samples"])
     assert a["counts"].min() >= 1
+
+
+def test_nuts_logreg_posterior_matches_importance_sampling():
+    # Logistic regression has no closed-form posterior, so the oracle's NUTS (the configuration's
+    # eps = 0.05, depth <= 10) is checked against a different estimator of the same posterior
+    # expectations: self-normalised importance sampling from a multivariate t (10 degrees of
+    # freedom) centred at the posterior mode with the Laplace covariance H^-1 widened by 1.2^2,
+    # H = X^T W X + I, W = diag(s (1 - s)), s = sigmoid(X beta_MAP).  The mode comes from Newton's
+    # method on the oracle's log density and gradient; the importance weights use the log
+    # posterior written with numpy.  NUTS chain means and second moments must agree with the
+    # importance-sampling estimates within 4 combined Monte Carlo standard errors (the posterior
+    # is visibly skewed here, its mean up to ~0.5 sd from the mode, so the mode itself is no pin).
+    w = W.logreg(1000, 25)
+    X, y = w["X"], w["y"]
+    b = np.zeros(25)
+    for _ in range(30):
+        _, g = O.logp("logreg", w["params"], b, n_data=1000, grad=True)
+        s = 1.0 / (1.0 + np.exp(-(X @ b)))
+        H = X.T @ (X * (s * (1 - s))[:, None]) + np.eye(25)
+        b = b + np.linalg.solve(H, g)
+    _, g = O.logp("logreg", w["params"], b, n_data=1000, grad=True)
+    assert np.abs(g).max() < 1e-9
+    s = 1.0 / (1.0 + np.exp(-(X @ b)))
+    H = X.T @ (X * (s * (1 - s))[:, None]) + np.eye(25)
+    C = np.linalg.cholesky(np.linalg.inv(H) * 1.2 ** 2)
+    rng = np.random.default_rng(17)
+    N, nu = 200_000, 10.0
+    zt = rng.standard_normal((N, 25)) / np.sqrt(rng.chisquare(nu, (N, 1)) / nu)
+    beta = b + zt @ C.T
+    eta = beta @ X.T
+    logpost = eta @ y - np.logaddexp(0.0, eta).sum(1) - 0.5 * (beta ** 2).sum(1)
+    logq = -0.5 * (nu + 25) * np.log1p((zt ** 2).sum(1) / nu)
+    lw = logpost - logq
+    wt = np.exp(lw - lw.max())
+    wt /= wt.sum()
+    assert 1.0 / (wt ** 2).sum() > 0.1 * N          # the proposal covers the posterior
+    f = np.concatenate([beta, beta ** 2], axis=1)
+    is_mean = wt @ f
+    is_se = np.sqrt((wt[:, None] ** 2 * (f - is_mean) ** 2).sum(0))
+    m, n, burn = 48, 250, 50
+    r = O.run("nuts", "logreg", w["params"], W.x0_logreg(w, m), n, seed=3, n_data=1000,
+              algo_params=[0.05, 10, 1000.0])
+    xs = r["samples"][:, burn:, :]
+    cm = np.concatenate([xs.mean(1), (xs ** 2).mean(1)], axis=1)
+    mean, mcse = cm.mean(0), cm.std(0, ddof=1) / np.sqrt(m)
+    z = np.abs(mean - is_mean) / np.sqrt(mcse ** 2 + is_se ** 2)
+    assert z.max() <= 4.0, z

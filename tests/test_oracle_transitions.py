@@ -32,3 +32,33 @@ def test_single_transitions_reproduce_a_run(case):
     assert np.array_equal(t["x"], run["samples"].reshape(m * n, -1))
     assert np.array_equal(t["counts"], run["counts"].ravel())
     assert np.array_equal(t["aux"], run["aux"].ravel())
+
+
+def test_decision_margin_of_a_one_stage_dr_transition():
+    # One delayed-rejection stage makes exactly one decision, log u < log alpha_1 with
+    # alpha_1 = min(1, pi(y) / pi(x)); the recorded margin is |log u - log alpha_1| /
+    # max(1, |log alpha_1|), rebuilt here from the oracle's own random numbers and log density.
+    w = W.gauss_diag(3)
+    x = W.x0_gauss_diag_exact(w, 5)
+    chains, samples = np.arange(5), np.array([0, 4, 9, 2, 7])
+    t = O.transitions("dr", "gauss_diag", w["params"], x, chains, samples, seed=8, algo_params=[1, 0.7, 1.0])
+    D = 1  # ceil(3 / 4) normal blocks
+    for i in range(5):
+        z = O.normals(8, int(chains[i]), int(samples[i]), 0, 0, 3)
+        y = x[i] + 0.7 * z
+        la = min(0.0, O.logp("gauss_diag", w["params"], y) - O.logp("gauss_diag", w["params"], x[i]))
+        b = O.philox4x32_10([D, int(samples[i]), 0, 0], [int(chains[i]), 8])
+        lu = np.log(O.uniform(b[0], b[1]))
+        assert t["margin"][i] == pytest.approx(abs(lu - la) / max(1.0, abs(la)), rel=1e-12)
+        assert t["counts"][i] == 1
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+def test_margins_are_recorded_and_do_not_change_the_transition(case):
+    # the transitions above reproduce runs bit for bit with the margin bookkeeping on; every
+    # transition makes at least one decision, so every margin is finite and non-negative
+    algo, kind, params, n_data, ap, x0 = case
+    m = x0.shape[0]
+    t = O.transitions(algo, kind, params, x0, np.arange(m), np.zeros(m, dtype=int), seed=5,
+                      n_data=n_data, algo_params=ap)
+    assert np.all(np.isfinite(t["margin"])) and np.all(t["margin"] >= 0)
