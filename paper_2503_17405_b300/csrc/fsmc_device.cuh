@@ -172,7 +172,9 @@ __device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
     volatile unsigned* gen = b.generation;
     const unsigned g = *gen;
     __threadfence();
-    if (atomicAdd(b.count, 1u) == nblocks - 1 + b.missing) {
+    if (*(volatile int*)err & ERR_BARRIER_TIMEOUT) {
+      ok = 0;  // a wait of this run already gave up: leave without arriving
+    } else if (atomicAdd(b.count, 1u) == nblocks - 1 + b.missing) {
       *b.count = 0;
       __threadfence();
       atomicAdd(b.generation, 1u);
