@@ -4,7 +4,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2503_17405_b300 import workloads as W
-from parity import compare
+from parity import FLIP_ALLOW, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +63,7 @@ def test_fp32_funnel_matches_oracle_until_branch_flip(eng):
     counts, _, _ = job.loop_counts()
     r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp32")
     print("fp32 funnel parity", r["flipped"], "flipped of", m, "max err", r["max_err"])
-    assert r["flipped"] <= m // 4
+    assert r["flipped"] <= FLIP_ALLOW
     job.close()
 
 
@@ -88,17 +88,23 @@ def full_funnel_job(eng):
     job.close()
 
 
-@pytest.mark.parametrize("chain", [0, 32767, 65535])
-def test_full_size_funnel_sampled_chains(full_funnel_job, chain):
+def test_full_size_funnel_sampled_chains(full_funnel_job):
+    """The oracle recomputes 64 chains of the full-size run over their first 1000 samples."""
     x0, job = full_funnel_job
     nref = 1000
-    ref = O.run("dr", "funnel", np.zeros(1), x0[chain:chain + 1], nref, seed=1, chain0=chain,
-                algo_params=DR_ARGS)
     counts, _, _ = job.loop_counts()
     assert counts.min() >= 1 and counts.max() <= 3
-    r = compare(job.samples(chain, 1, 0, nref), counts[chain:chain + 1, :nref], ref["samples"],
-                ref["counts"], "fp32")
-    print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
+    flipped = 0
+    for chain in np.linspace(0, 65535, 64).astype(int):
+        ref = O.run("dr", "funnel", np.zeros(1), x0[chain:chain + 1], nref, seed=1, chain0=int(chain),
+                    algo_params=DR_ARGS)
+        r = compare(job.samples(int(chain), 1, 0, nref), counts[chain:chain + 1, :nref], ref["samples"],
+                    ref["counts"], "fp32")
+        flipped += r["flipped"]
+        if r["flipped"]:
+            print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
+    print("DR full size: %d of 64 sampled chains flipped in 1000 samples" % flipped)
+    assert flipped <= FLIP_ALLOW
 
 
 SDR = {"n_stages": 100, "scale0": 0.1, "factor": 1.0, "symmetric": 1}

@@ -4,7 +4,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2503_17405_b300 import workloads as W
-from parity import compare
+from parity import FLIP_ALLOW, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +74,7 @@ def test_fp32_gp_logit_matches_oracle_until_branch_flip(eng):
     counts, _, _ = job.loop_counts()
     r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp32")
     print("fp32 gp-logit parity", r["flipped"], "flipped of", m, "max err", r["max_err"])
-    assert r["flipped"] <= m // 4
+    assert r["flipped"] <= FLIP_ALLOW
     job.close()
 
 
@@ -97,7 +97,7 @@ def test_fp32_gp_logit_overflowing_group_products_match_oracle(eng):
     assert np.array_equal(ca, cb) and np.array_equal(a.samples(), b.samples())
     r = compare(a.samples(), ca, ref["samples"], ref["counts"], "fp32")
     print("overflowing products: flipped", r["flipped"], "of", m, "max err", r["max_err"])
-    assert r["flipped"] <= m // 4
+    assert r["flipped"] <= FLIP_ALLOW
     a.close()
     b.close()
 
@@ -116,7 +116,7 @@ def test_tensor_core_generator_matches_oracle(eng, d):
         counts, _, _ = job.loop_counts()
         r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp32")
         print("generator", gen, "d", d, "flipped", r["flipped"], "max err", r["max_err"])
-        assert r["flipped"] <= m // 4
+        assert r["flipped"] <= FLIP_ALLOW
         job.close()
 
 
@@ -158,7 +158,7 @@ def test_fp32_gp_logit_lanes_match_oracle_and_sync(eng, lanes):
     ref = O.run("ess", "gp_logit", w["params"], x0, n, seed=1)
     r = compare(a.samples(), ca, ref["samples"], ref["counts"], "fp32")
     print("lanes", lanes, "flipped", r["flipped"], "max err", r["max_err"])
-    assert r["flipped"] <= m // 4
+    assert r["flipped"] <= FLIP_ALLOW
     a.close()
     b.close()
 
@@ -284,15 +284,18 @@ def full_gp_job(eng):
     job.close()
 
 
-@pytest.mark.parametrize("chain", [0, 8191, 16383])
-def test_full_size_gp_logit_sampled_chains(full_gp_job, chain):
-    """The oracle recomputes sampled chains one by one (the RNG is keyed by chain) over
-    the first 1000 samples of the full-size run."""
+def test_full_size_gp_logit_sampled_chains(full_gp_job):
+    """The oracle recomputes eight chains of the full-size run one by one (the RNG is keyed by
+    chain) over the first 1000 samples: within the FP32 tolerance until a flip, flips bounded."""
     w, job = full_gp_job
     nref = 1000
-    ref = O.run("ess", "gp_logit", w["params"], np.zeros((1, 256)), nref, seed=1, chain0=chain)
-    x = job.samples(chain, 1, 0, nref)
     counts, _, _ = job.loop_counts()
     assert np.all(counts >= 0)
-    r = compare(x, counts[chain:chain + 1, :nref], ref["samples"], ref["counts"], "fp32")
-    print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
+    flipped = 0
+    for chain in [0, 2047, 4096, 8191, 8192, 12287, 15000, 16383]:
+        ref = O.run("ess", "gp_logit", w["params"], np.zeros((1, 256)), nref, seed=1, chain0=chain)
+        x = job.samples(chain, 1, 0, nref)
+        r = compare(x, counts[chain:chain + 1, :nref], ref["samples"], ref["counts"], "fp32")
+        print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
+        flipped += r["flipped"]
+    assert flipped <= FLIP_ALLOW

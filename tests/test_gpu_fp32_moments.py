@@ -54,19 +54,24 @@ def _mean_se(avg):
 
 
 def test_fp32_conjugate_gaussian_closed_form_from_zero(eng):
-    # Alg. 8 on the conjugate Gaussian exactly as configured (d = 16, 128 chains x 1000 samples
-    # from x0 = 0), in single precision; the first 10 % of samples are dropped
+    # Alg. 8 on the conjugate Gaussian as configured (d = 16, 128 chains x 1000 samples from x0 = 0),
+    # in single precision, the first 10 % of samples dropped, repeated with chain seeds 1..8 and
+    # pooled (1024 chains).  With seed 1 alone the second moment of coordinate 0 lies 4.0 MCSE
+    # below the closed form -- in the FP64 oracle's run of that seed as much as in this one (the
+    # two follow the same trajectories), i.e. a fluctuation of that seed, not of the precision.
     w = W.gauss_conj(16)
     m, n = 128, 1000
     tg = eng.target("gauss_conj", 16, w["params"])
-    job = eng.job(tg, "ess", m, n, x0=W.x0_zeros(m, 16), seed=1, prec="fp32")
-    job.run("fsm")
-    xs = job.samples()[:, n // 10:, :]
     mu, var = w["post_mean"], np.diag(w["post_cov"])
-    avg = np.concatenate([xs.mean(1), ((xs - mu) ** 2).mean(1)], axis=1)
-    est, se = _mean_se(avg)
-    _within("FP32 ESS conj. Gaussian, 128 x 1000", est, se, np.concatenate([mu, var]))
-    job.close()
+    avgs = []
+    for seed in range(1, 9):
+        job = eng.job(tg, "ess", m, n, x0=W.x0_zeros(m, 16), seed=seed, prec="fp32")
+        job.run("fsm")
+        xs = job.samples()[:, n // 10:, :]
+        job.close()
+        avgs.append(np.concatenate([xs.mean(1), ((xs - mu) ** 2).mean(1)], axis=1))
+    est, se = _mean_se(np.concatenate(avgs, axis=0))
+    _within("FP32 ESS conj. Gaussian, 8 x (128 x 1000)", est, se, np.concatenate([mu, var]))
 
 
 @pytest.mark.parametrize("lanes", [1, 32])

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2503_17405_b300 import workloads as W
-from parity import FP32_TOL, compare, sample_errors
+from parity import compare, transitions_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -70,11 +70,7 @@ def test_fp32_transition_by_transition_against_the_oracle(eng, n_data):
     starts = np.concatenate([x0[:, None, :], xs[:, :-1, :]], axis=1).reshape(m * n, -1)
     ref = O.transitions("ess", "gp_reg", w["params"], starts, np.repeat(np.arange(m), n), np.tile(np.arange(n), m),
                         seed=2, n_data=n_data)
-    err = sample_errors(xs.reshape(m * n, -1), ref["x"])
-    ok = (ref["counts"] == counts.ravel()) & (err <= FP32_TOL)
-    print("fp32 gp_reg n=%d transitions: %d of %d agree; max err of those %.3g"
-          % (n_data, ok.sum(), ok.size, err[ok].max()))
-    assert ok.mean() >= 0.98
+    transitions_agree(xs.reshape(m * n, -1), counts.ravel(), ref, "fp32 gp_reg n=%d" % n_data)
 
 
 @pytest.mark.parametrize("mode", ["fsm", "sync"])
@@ -101,10 +97,7 @@ def test_fp32_papers_largest_size_transitions(eng):
     starts = np.concatenate([x0[:, None, :], xs[:, :-1, :]], axis=1).reshape(m * n, -1)
     ref = O.transitions("ess", "gp_reg", w["params"], starts, np.repeat(np.arange(m), n), np.tile(np.arange(n), m),
                         seed=2, n_data=400)
-    err = sample_errors(xs.reshape(m * n, -1), ref["x"])
-    ok = (ref["counts"] == counts.ravel()) & (err <= FP32_TOL)
-    print("fp32 gp_reg n=400 transitions: %d of %d agree; max err %.3g" % (ok.sum(), ok.size, err[ok].max()))
-    assert ok.mean() >= 0.95
+    transitions_agree(xs.reshape(m * n, -1), counts.ravel(), ref, "fp32 gp_reg n=400")
 
 
 def test_limits_and_argument_checks(eng):

@@ -4,7 +4,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2503_17405_b300 import workloads as W
-from parity import compare
+from parity import FLIP_ALLOW, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -95,7 +95,7 @@ def test_fp32_logreg_matches_oracle_until_branch_flip(eng):
     r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp32")
     print("fp32 logreg parity", r["flipped"], "flipped of", m, "max err", r["max_err"],
           "first flips", r["first_flip"])
-    assert r["flipped"] <= m // 2
+    assert r["flipped"] <= FLIP_ALLOW
     job.close()
 
 
@@ -112,6 +112,7 @@ def test_sync_and_fsm_agree_fp32(eng):
     ca, da, _ = a.loop_counts()
     cb, db, _ = b.loop_counts()
     r = compare(a.samples(), ca, b.samples(), cb, "fp32")
+    print("fp32 logreg FSM vs sync:", r["flipped"], "flipped of", m)
     assert r["flipped"] <= m // 8
     st = b.stats()
     # the nested synchronised loops run at least max_j N_ij leapfrog iterations per sample
@@ -131,13 +132,21 @@ def full_nuts_job(eng):
     job.close()
 
 
-@pytest.mark.parametrize("chain", [0, 2047, 4095])
-def test_full_size_logreg_sampled_chains(full_nuts_job, chain):
+SAMPLED = [0, 511, 1024, 2047, 2048, 3071, 3584, 4095]
+
+
+def test_full_size_logreg_sampled_chains(full_nuts_job):
+    """The oracle recomputes eight chains of the full-size run one by one (the RNG is keyed by
+    chain) over all 1000 draws: within the FP32 tolerance until a flip, flips bounded."""
     w, nuts, x0, job = full_nuts_job
-    nref = 300
-    ref = _oracle("logreg", w["params"], x0[chain:chain + 1], nref, nuts, n_data=1000, chain0=chain)
+    nref = 1000
     counts, _, _ = job.loop_counts()
     assert counts.min() >= 1 and counts.max() <= 1023
-    r = compare(job.samples(chain, 1, 0, nref), counts[chain:chain + 1, :nref], ref["samples"],
-                ref["counts"], "fp32")
-    print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
+    flipped = 0
+    for chain in SAMPLED:
+        ref = _oracle("logreg", w["params"], x0[chain:chain + 1], nref, nuts, n_data=1000, chain0=chain)
+        r = compare(job.samples(chain, 1, 0, nref), counts[chain:chain + 1, :nref], ref["samples"],
+                    ref["counts"], "fp32")
+        print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
+        flipped += r["flipped"]
+    assert flipped <= FLIP_ALLOW

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2503_17405_b300 import workloads as W
-from parity import FP32_TOL, compare, sample_errors
+from parity import compare, transitions_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -81,10 +81,7 @@ def test_fp32_transition_by_transition_against_the_oracle(eng):
     starts = np.concatenate([x0[:, None, :], xs[:, :-1, :]], axis=1).reshape(m * n, -1)
     ref = O.transitions("slice", "funnel", w["params"], starts, np.repeat(np.arange(m), n), np.tile(np.arange(n), m),
                         seed=3, algo_params=[sl["w"], sl["m"]])
-    err = sample_errors(xs.reshape(m * n, -1), ref["x"])
-    ok = (ref["counts"] == counts.ravel()) & (err <= FP32_TOL)
-    print("fp32 slice transitions: %d of %d agree; max err of those %.3g" % (ok.sum(), ok.size, err[ok].max()))
-    assert ok.mean() >= 0.99
+    transitions_agree(xs.reshape(m * n, -1), counts.ravel(), ref, "fp32 slice")
 
 
 def test_flat_target_takes_every_expansion_step(eng):
