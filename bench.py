@@ -33,6 +33,11 @@ METRIC = "samples/s FSM vs synchronized kernel on 1 B300 at oracle tolerance; p5
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
+# ncu --set full of one FSM-step launch of the headline workload's kernel (ESS-GP, d = 256, 32 lanes
+# per chain) on a small case; the summary and its command are in profiles/
+ESS_GP_STEP_NCU = {"chains": 4096, "states": 384, "dram_bytes": 304.6e6 + 255.5e6, "issue_active": 0.740,
+                   "warp_instructions_per_state": 219.6e6 / (4096 * 384),
+                   "source": "profiles/ess_gp_d256_m4096_n400_kernels.md (ncu --set full, 4096 chains x 384 states)"}
 
 
 def _peaks():
@@ -41,6 +46,23 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def probe_rates(device):
+    """Measured peak rates of this device (libfsmc_probe.so, built beside libfsmc.so): FP32 and
+    FP64 multiply-add TFLOP/s, ex2.approx and lg2.approx tera-operations/s."""
+    import ctypes
+    from paper_2503_17405_b300 import build
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.fsmc_bench_probe.argtypes = [ctypes.c_int, dp, dp, dp, dp]
+    lib.fsmc_bench_probe.restype = ctypes.c_int
+    r = [ctypes.c_double(0.0) for _ in range(4)]
+    rc = lib.fsmc_bench_probe(device, *[ctypes.byref(x) for x in r])
+    if rc != 0:
+        raise RuntimeError("fsmc_bench_probe returned %d" % rc)
+    return {"fp32_ffma_tflops": r[0].value, "fp64_dfma_tflops": r[1].value,
+            "mufu_ex2_tops": r[2].value, "mufu_lg2_tops": r[3].value}
 
 
 # ---- workloads ------------------------------------------------------------------------------
@@ -179,6 +201,34 @@ def oracle_throughput(cfg, target_s=10.0):
             "sample": f"{m} chains x {n_s} samples of {cfg['name']} (FP64, {t:.1f} s)"}
 
 
+def oracle_branch_flips(cfg, chains, x_gpu, c_gpu, tol=1e-4, flip_err=1e-2):
+    """Part of the CPU-baseline leg: the oracle recomputes the sampled chains of the timed job (the
+    RNG is keyed by chain, so one chain can be rerun alone) and each GPU trajectory is compared
+    with it up to its first branch flip -- the first sample whose loop count differs or whose
+    norm-wise relative error exceeds flip_err (a decision taken the other way moves a chain by a
+    proposal's size, rounding by ~1e-6).  Errors before the flip must stay within tol."""
+    from oracle import oracle as O
+    w = cfg["w"]
+    nref = x_gpu.shape[1]
+    firsts, mx = [], 0.0
+    for k, c in enumerate(chains):
+        ref = O.run(cfg.get("oracle_algo", cfg["algo"]), w["kind"], w["params"], cfg["x0"][c:c + 1], nref, seed=1,
+                    chain0=int(c), n_data=w["n_data"], algo_params=cfg.get("oracle_params", cfg["algo_params"]))
+        xo, co = ref["samples"][0], ref["counts"][0]
+        err = np.abs(x_gpu[k] - xo).max(-1) / np.maximum(1.0, np.abs(xo).max(-1))
+        bad = np.nonzero((c_gpu[k] != co) | (err > flip_err))[0]
+        end = int(bad[0]) if bad.size else nref
+        if bad.size:
+            firsts.append([int(c), end])
+        if end:
+            mx = max(mx, float(err[:end].max()))
+    return {"chains_checked": len(chains), "samples_per_chain": nref, "flipped_chains": len(firsts),
+            "first_flip_sample": firsts, "max_rel_err_before_flip": mx, "tolerance": tol,
+            "within_tolerance": mx <= tol,
+            "definition": "first sample whose loop count differs from the FP64 oracle's or whose norm-wise "
+                          "relative error exceeds %g" % flip_err}
+
+
 # ---- multi-GPU aggregation (independent chains per rank: weak scaling) -----------------------------
 def max_over_ranks(value, dist=None, device="cpu"):
     """Slowest rank's time for a timed region (an all-reduce MAX, the only kind of collective of the run)."""
@@ -259,6 +309,12 @@ def run_ours(args, rank, world):
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    clk_mhz = clk.get("sm_mhz")
+    # sampled chains of the last timed job, kept for the branch-flip check of the CPU-baseline leg
+    flip_chains = sorted({int(c) for c in np.linspace(0, m - 1, 8)})
+    nflip = min(n, 1000)
+    flip_x = np.stack([job.samples(c, 1, 0, nflip)[0] for c in flip_chains])
+    flip_c = job.loop_counts()[0][flip_chains, :nflip]
     total_ms = max_over_ranks(sum(fsm_ms), dist, "cuda")
     value = job_throughput(world, args.steps, m, n, total_ms)
 
@@ -348,21 +404,29 @@ def run_ours(args, rank, world):
                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (nominal)"}
     else:
-        # FSM step kernel: algorithmic flops per step -- ESS: x' (3 d) + likelihood (~9 d);
-        # NUTS: one gradient, 4 n d; DR: d normals' Box-Muller + density (~20 d)
+        # FSM step kernel: algorithmic work per step (one log-density evaluation) as the hot-path
+        # scope table counts it -- ESS-GP: x' = x cos + nu sin and the softplus sum, 3 d flops plus
+        # 2 d multi-function operations (an exp and a log per coordinate); NUTS: one logistic
+        # gradient, 4 n d flops; DR: the stage's density, ~40 flops (+ 5 Philox blocks for its
+        # normals); the slice sampler: the point x + theta u and the density (~20 d)
+        mufu = None
         if cfg["algo"] == "ess" and w["kind"] == "gp_reg":
             # the covariance (n^2 / 2 exponentials, counted as 2 flops each), the LDL^T sweep with
             # y folded in (n^3 / 3 + n^2 multiply-adds, 2 flops each)
             nd = w["n_data"]
             per = nd * nd + 2 * (nd ** 3 / 3 + nd * nd)
         elif cfg["algo"] == "ess":
-            per = 12 * d
+            per = 3 * d
+            if w["kind"] == "gp_logit":
+                mufu = {"algorithmic_per_step": 2 * d,
+                        "issued_per_step": d + d // 8,
+                        "issued_note": "one ex2 per coordinate, one lg2 per group of eight (grouped-product softplus)"}
         elif cfg["algo"] == "nuts":
             # logistic regression: 4 n d; mixture: (7 K + 1) d (residual, its square, the gradient)
             per = 4 * w["n_data"] * d if w["kind"] == "logreg" else (7 * w["n_data"] + 1) * d
+        elif cfg["algo"] == "dr":
+            per = 40
         else:
-            # DR: d normals' Box-Muller and the density (~20 d); slice: the point x + theta u and
-            # the density (about the same)
             per = 20 * d
         achieved = steps_total * per / (kms_own[1] / 1e3) / 1e12 if kms_own[1] else None
         kname = {"ess": "ess_block_fsm_kernel" if w["kind"] == "gp_reg" else "ess_fsm_kernel",
@@ -370,13 +434,19 @@ def run_ours(args, rank, world):
                  "nuts": "nuts_fsm_batched_kernel" if w["kind"] == "logreg" else "nuts_fsm_kernel"}[cfg["algo"]]
         traffic, traffic_src, issue = None, None, None
         if cfg["algo"] == "ess" and w["kind"] == "gp_logit" and d == 256 and tun.get("lanes_per_chain") == 32:
-            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FSM-step launch on 4096
-            # chains at 384 states per chain (304.6 MB + 255.5 MB), scaled by the states of a launch
-            traffic = (304.6e6 + 255.5e6) * (m / 4096) * (tun.get("steps_per_launch", 384) / 384)
-            traffic_src = ("bytes per launch: ncu capture on 4096 chains x 384 states, scaled by chains and "
-                           "states per launch")
-            issue = {"issue_active": 0.740, "eligible_warps_per_scheduler": 1.98,
-                     "source": "ncu --set full, FSM step on 4096 chains x 384 states (profiles/)"}
+            prof = ESS_GP_STEP_NCU
+            # DRAM bytes of one FSM-step launch in the ncu capture, scaled by chains and states per launch
+            traffic = prof["dram_bytes"] * (m / prof["chains"]) * (tun.get("steps_per_launch", 384) / prof["states"])
+            traffic_src = ("bytes per launch: ncu capture on %d chains x %d states, scaled by chains and "
+                           "states per launch" % (prof["chains"], prof["states"]))
+            # instruction issue: a chain is one warp, so a state costs warp_instructions_per_state issue
+            # slots of one of the 4 x 148 schedulers
+            clk = (clk_mhz or SM_MAX_MHZ) * 1e6
+            floor_ms = steps_total * prof["warp_instructions_per_state"] / (4 * SM_COUNT * clk) * 1e3
+            issue = {"issue_active": prof["issue_active"], "warp_instructions_per_state": prof["warp_instructions_per_state"],
+                     "issue_floor_ms_per_step": floor_ms / args.steps,
+                     "kernel_ms_per_step": kms_own[1] / args.steps,
+                     "source": prof["source"]}
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
@@ -385,27 +455,34 @@ def run_ours(args, rank, world):
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (nominal)",
                 "flops_per_step": per,
                 "limiter": {"ess": "a warp per chain: length-j dot products per covariance column, shared-memory bound" if w["kind"] == "gp_reg"
-                            else "instruction issue (~145 warp instructions per state; one ex2 per coordinate, one lg2 per eight)"
+                            else "instruction issue (warp instructions per state in ncu_issue), then the multi-function unit"
                             if w["kind"] == "gp_logit" else "latency: few chains (one warp each), short rows",
                             "dr": "latency: one chain per thread, ~14 resident warps per SM at 65536 chains",
                             "slice": "latency: one chain per thread, 65536 chains",
                             "nuts": "latency and occupancy of the block-batched gradient" if w["kind"] == "logreg"
                             else "latency: one chain per warp, shuffle reductions per component and U-turn test"}[cfg["algo"]]}
+        if mufu and kms_own[1]:
+            mufu["achieved_issued_tops"] = steps_total * mufu["issued_per_step"] / (kms_own[1] / 1e3) / 1e12
+            roof["mufu"] = mufu
 
-    # measured multiply-add rates of this device (outside the timed regions): context for the
-    # nominal FP32 peak the roofline fraction is taken against
+    # measured peak rates of this device (outside the timed regions): context for the nominal
+    # FP32 peak the roofline fraction is taken against
     try:
-        f32m, f64m = fsmc.probe_fma_peaks(dev)
-        roof["fp32_ffma_measured_tflops"] = f32m
-        roof["fp64_dfma_measured_tflops"] = f64m
+        rates = probe_rates(dev)
+        roof["measured_rates"] = rates
         if roof.get("unit") == "TFLOP/s" and roof.get("bound") == "alu" and roof.get("achieved"):
-            roof["frac_of_measured_ffma"] = roof["achieved"] / f32m
-    except fsmc.FsmcError as ex:
-        roof["fma_probe"] = str(ex)
+            roof["frac_of_measured_ffma"] = roof["achieved"] / rates["fp32_ffma_tflops"]
+        if roof.get("mufu", {}).get("achieved_issued_tops"):
+            roof["mufu"]["frac_of_measured_ex2"] = roof["mufu"]["achieved_issued_tops"] / rates["mufu_ex2_tops"]
+    except (OSError, RuntimeError) as ex:
+        roof["probe"] = str(ex)
 
-    # end to end through the public API: host params and x0 in, posterior moments out
-    # every step: target and job created from pinned host arrays (params, x0), the whole run, the
-    # per-chain moments read back into pinned host arrays, the job closed; one untimed warm-up
+    # end to end through the public API: host params and x0 in, posterior moments out.  Every
+    # step: target and job created from pinned host arrays (params, x0), the whole run as a
+    # moments-only job (each sample folded into per-chain sums of x and x^2 as it is drawn, the
+    # job's declared result), those sums read back into pinned host arrays, the job closed; one
+    # untimed warm-up.  (Reading back every stored sample instead would move m n d values per step,
+    # 33.5 GB at the headline size, and time the host link rather than the sampler.)
     e2e = None
     if not args.no_e2e:
         params_h = torch.from_numpy(np.ascontiguousarray(w["params"], dtype=np.float64)).pin_memory()
@@ -417,7 +494,7 @@ def run_ours(args, rank, world):
         def e2e_step():
             tg2 = eng.target(w["kind"], w["d"], params_h.numpy(), n_data=w["n_data"])
             job2 = eng.job(tg2, cfg["algo"], m, n, x0=x0_h.numpy(), seed=1 + rank, prec=cfg["prec"],
-                           store=True, dr=dr, nuts=nuts, tuning=parse_tuning(args.tuning) or None, slice=sl)
+                           store=False, dr=dr, nuts=nuts, tuning=parse_tuning(args.tuning) or None, slice=sl)
             job2.run("fsm", stream=sp)
             job2.moments(sx, sx2, nk)
             job2.close()
@@ -430,11 +507,15 @@ def run_ours(args, rank, world):
             e2e_step()
         t1 = time.perf_counter()
         e2e = {"value": m * n * args.steps / (t1 - t0), "unit": "samples/s",
+               "result": "per-chain sums of x and x^2 over all samples (moments-only job), read to host",
                "h2d_bytes_per_step": int(params_h.numel() * 8 + x0_h.numel() * 8),
                "d2h_bytes_per_step": int(sx.nbytes + sx2.nbytes + nk.nbytes)}
     out = None
     if rank == 0:
-        cpu = None if (args.no_cpu or world > 1) else oracle_throughput(cfg)
+        cpu = flips = None
+        if not (args.no_cpu or world > 1):
+            cpu = oracle_throughput(cfg)
+            flips = oracle_branch_flips(cfg, flip_chains, flip_x, flip_c)
         out = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -457,12 +538,20 @@ def run_ours(args, rank, world):
             "moments_only": mom_only,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "branch_flips": flips,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
         }
     eng.close()
+    # the mixed request stream (continuous batching) at a stated scale, after the job's engine is
+    # closed: p50 / p99 job latency beside throughput (the full-size stream: --config serving)
+    if out is not None and world == 1 and not args.no_serve and cfg["name"].startswith("ess_gp_logit"):
+        try:
+            out["serving"] = serve_stream(args.serve_jobs, args.serve_scale, sync_jobs=0, device=dev)
+        except Exception as ex:  # noqa: BLE001 -- reported, not fatal to the headline line
+            out["serving"] = {"error": str(ex)}
     if dist:
         dist.destroy_process_group()
     return out
@@ -566,14 +655,17 @@ def run_ablations(args):
 
 
 # ---- serving stream (C5) ------------------------------------------------------------------------------
-def run_serving(args):
-    """Poisson-arriving mixed jobs through fsmc_submit; FSM co-scheduled vs the synchronised
-    kernel one job at a time.  Latency = completion - submit, as the library records it."""
+def serve_stream(n_jobs, scale, sync_jobs=0, device=0):
+    """Poisson-arriving mixed jobs through fsmc_submit (ESS-GP and NUTS-logistic, sizes log-uniform
+    as workloads.serving_jobs draws them, times `scale` chains and draws).  A capacity pass submits
+    every job at t = 0; the measured pass offers 0.8 of that capacity as Poisson arrivals; the
+    synchronised kernel then serves the first `sync_jobs` jobs of the same stream one at a time.
+    Latency = completion - submit, as the library records it."""
     import torch
     from paper_2503_17405_b300 import fsmc
 
-    torch.cuda.set_device(0)
-    base = W.serving_jobs(args.serve_jobs, rate_hz=1.0, scale=args.serve_scale)
+    torch.cuda.set_device(device)
+    base = W.serving_jobs(n_jobs, rate_hz=1.0, scale=scale)
     cache = {}
 
     def target(eng, j):
@@ -586,9 +678,9 @@ def run_serving(args):
         w = cache[key]
         return w, eng.target(w["kind"], w["d"], w["params"], n_data=w["n_data"])
 
-    def one_pass(mode, rate_hz):
-        eng = fsmc.Engine(0)
-        jobs = [dict(j) for j in base]
+    def one_pass(mode, rate_hz, jobs_in):
+        eng = fsmc.Engine(device)
+        jobs = [dict(j) for j in jobs_in]
         t = 0.0
         rng = np.random.default_rng(7)
         for j in jobs:
@@ -625,17 +717,33 @@ def run_serving(args):
                 "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "jobs": len(lat)}
 
-    cap = one_pass("fsm", 0.0)                 # all jobs at t = 0: capacity
+    cap = one_pass("fsm", 0.0, base)                 # all jobs at t = 0: capacity
     rate = 0.8 * cap["jobs"] / cap["makespan_s"]
-    fsm = one_pass("fsm", rate)
-    sync = one_pass("sync", rate) if not args.no_sync else None
-    return {"metric": METRIC, "value": fsm["samples_per_s"], "unit": "samples/s", "n_gpus": 1,
+    fsm = one_pass("fsm", rate, base)
+    sync = one_pass("sync", rate, base[:sync_jobs]) if sync_jobs else None
+    return {"scale": scale, "jobs": n_jobs, "rate_jobs_per_s": rate, "arrivals": "Poisson",
+            "offered_load": "0.8 x measured FSM capacity",
+            "p50_latency_s": fsm["p50_latency_s"], "p99_latency_s": fsm["p99_latency_s"],
+            "samples_per_s": fsm["samples_per_s"], "fsm": fsm, "capacity_pass": cap,
+            "sync_one_at_a_time": sync,
+            "sync_subset": "first %d jobs of the same stream and arrival times" % sync_jobs if sync_jobs else None}
+
+
+def run_serving(args):
+    """--config serving: the mixed request stream on its own line (default: the full stream of 200
+    jobs at full sizes, the synchronised baseline on the first --serve-sync-jobs of them)."""
+    from paper_2503_17405_b300 import build
+    build.build()
+    sj = args.serve_sync_jobs if args.serve_sync_jobs is not None else args.serve_jobs
+    r = serve_stream(args.serve_jobs, args.serve_scale, sync_jobs=0 if args.no_sync else sj)
+    return {"metric": METRIC, "value": r["samples_per_s"], "unit": "samples/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving_{args.serve_jobs}_jobs_scale{args.serve_scale:g}",
                        "arrivals": "Poisson", "offered_load": "0.8 x measured FSM capacity",
-                       "rate_jobs_per_s": rate},
-            "p50_latency_s": fsm["p50_latency_s"], "p99_latency_s": fsm["p99_latency_s"],
-            "fsm": fsm, "sync_one_at_a_time": sync, "capacity_pass": cap}
+                       "rate_jobs_per_s": r["rate_jobs_per_s"]},
+            "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"],
+            "fsm": r["fsm"], "sync_one_at_a_time": r["sync_one_at_a_time"], "sync_subset": r["sync_subset"],
+            "capacity_pass": r["capacity_pass"]}
 
 
 def main():
@@ -652,10 +760,24 @@ def main():
     ap.add_argument("--no-moments", action="store_true", help="skip the moments-only (store = 0) leg")
     ap.add_argument("--scale", type=float, default=1.0, help="chains x scale (profiling only)")
     ap.add_argument("--samples", type=int, default=None, help="samples per chain (profiling only)")
-    ap.add_argument("--serve-jobs", type=int, default=40)
-    ap.add_argument("--serve-scale", type=float, default=0.25)
+    ap.add_argument("--serve-jobs", type=int, default=None,
+                    help="jobs of the serving stream (default: 200 for --config serving, 40 for the "
+                         "serving sub-object of the default line)")
+    ap.add_argument("--serve-scale", type=float, default=None,
+                    help="chains and draws scale of the serving stream (default: 1 for --config serving, "
+                         "0.25 for the default line's sub-object)")
+    ap.add_argument("--serve-sync-jobs", type=int, default=None,
+                    help="--config serving: jobs the synchronised one-at-a-time baseline serves (default 20)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sub-object of the default line")
     ap.add_argument("--tuning", default="", help="launch-shape overrides, e.g. lanes_per_chain=16")
     args = ap.parse_args()
+    full_stream = args.config == "serving"
+    if args.serve_jobs is None:
+        args.serve_jobs = 200 if full_stream else 40
+    if args.serve_scale is None:
+        args.serve_scale = 1.0 if full_stream else 0.25
+    if args.serve_sync_jobs is None and full_stream:
+        args.serve_sync_jobs = 20
     if args.config == "serving":
         print(json.dumps(run_serving(args)))
         return

@@ -315,17 +315,6 @@ fsmc_status fsmc_ess_run_static(int target_kind, int d, const float* L_dev, cons
                                 const float* x0_dev, uint64_t seed, int lanes_per_chain,
                                 float* samples_dev, int32_t* counts_dev, void* cuda_stream);
 
-/* ---- fused multiply-add throughput probe ---------------------------------------------------
- * The paper has no counterpart to this entry point: it measures the denominators of the
- * roofline for kernels bound by CUDA-core arithmetic.  On `device` it times, with CUDA events
- * after one untimed launch, eight independent multiply-add chains per thread on 2048 threads
- * per SM, in single and in double precision, and returns the rates in TFLOP/s (two flops per
- * multiply-add) at whatever clocks the device runs.  It allocates one 8-byte device buffer and
- * one stream, frees both, and leaves the caller's current device as it was.  About 0.3 s of
- * device time on a B300.
- * Errors: EINVAL (NULL outputs), ECUDA. */
-fsmc_status fsmc_probe_fma_peaks(int device, double* fp32_tflops, double* fp64_tflops);
-
 const char* fsmc_last_error(void);
 
 #ifdef __cplusplus

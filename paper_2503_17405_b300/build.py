@@ -1,4 +1,4 @@
-"""Builds libfsmc.so in-tree with nvcc for sm_103a (B300)."""
+"""Builds libfsmc.so (and the benchmark's probe library) in-tree with nvcc for sm_103a (B300)."""
 import os
 import subprocess
 import sys
@@ -7,33 +7,37 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfsmc.so")
 SOURCES = ["engine.cu", "ess.cu", "ess_block.cu", "ess_tc.cu", "dr.cu", "nuts.cu", "slice.cu", "serving.cu",
-           "noalloc.cu", "autotune.cu", "probe.cu", "stats.cu"]
+           "noalloc.cu", "autotune.cu", "stats.cu"]
+# the benchmark's throughput probe: a separate library, not part of libfsmc.so or its C ABI
+PROBE_LIB = os.path.join(HERE, "libfsmc_probe.so")
+PROBE_SOURCES = ["bench_probe.cu"]
 HEADERS = ["fsmc_device.cuh", "fsmc_kernels.h", "engine_internal.h", "target_logp.cuh", "ess_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread"]
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _header_time():
+    return max(os.path.getmtime(p) for p in
+               [os.path.join(CSRC, f) for f in HEADERS] +
+               [os.path.join(HERE, "..", "include", "fsmc.h"), os.path.abspath(__file__)])
+
+
+def _stale(lib, sources):
+    if not os.path.exists(lib):
         return True
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
-    deps.append(os.path.join(HERE, "..", "include", "fsmc.h"))
-    deps.append(os.path.abspath(__file__))
-    return max(os.path.getmtime(p) for p in deps) > os.path.getmtime(LIB)
+    newest = max([_header_time()] + [os.path.getmtime(os.path.join(CSRC, f)) for f in sources])
+    return newest > os.path.getmtime(lib)
 
 
-def build(force=False, verbose=False, jobs=None):
-    if not force and not _stale():
-        return LIB
+def _build_lib(lib, sources, force, verbose):
+    if not force and not _stale(lib, sources):
+        return lib
     nvcc = os.environ.get("NVCC", "nvcc")
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    procs = []
-    objs = []
-    hdr_time = max(os.path.getmtime(p) for p in
-                   [os.path.join(CSRC, f) for f in HEADERS] +
-                   [os.path.join(HERE, "..", "include", "fsmc.h"), os.path.abspath(__file__)])
-    for src in SOURCES:
+    procs, objs = [], []
+    hdr_time = _header_time()
+    for src in sources:
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
         objs.append(obj)
         # an object newer than its source and every header is up to date
@@ -54,10 +58,16 @@ def build(force=False, verbose=False, jobs=None):
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force=False, verbose=False, jobs=None):
+    """Builds libfsmc.so and libfsmc_probe.so where stale; returns the path of libfsmc.so."""
+    _build_lib(PROBE_LIB, PROBE_SOURCES, force, verbose)
+    return _build_lib(LIB, SOURCES, force, verbose)
 
 
 if __name__ == "__main__":

@@ -97,7 +97,6 @@ SIGNATURES = [
     ("fsmc_job_snapshot", ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     ("fsmc_job_restore", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("fsmc_job_destroy", None, [_vp]),
-    ("fsmc_probe_fma_peaks", ctypes.c_int, [ctypes.c_int, _dp, _dp]),
     ("fsmc_submit", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     ("fsmc_poll", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _dp]),
     ("fsmc_cancel", ctypes.c_int, [_vp]),
@@ -352,10 +351,3 @@ def ess_run_static(kind, d, L_ptr, vec_ptr, noise_var, n_chains, n_samples, x0_p
     _check(load().fsmc_ess_run_static(TARGET[kind], d, L_ptr, vec_ptr, noise_var, n_chains,
                                       n_samples, x0_ptr, seed, lanes_per_chain, samples_ptr,
                                       counts_ptr, stream))
-
-
-def probe_fma_peaks(device=0):
-    """fsmc_probe_fma_peaks: measured (FP32, FP64) multiply-add rates of a device, TFLOP/s."""
-    f32, f64 = ctypes.c_double(0.0), ctypes.c_double(0.0)
-    _check(load().fsmc_probe_fma_peaks(device, ctypes.byref(f32), ctypes.byref(f64)))
-    return f32.value, f64.value
