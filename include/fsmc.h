@@ -150,6 +150,14 @@ typedef struct fsmc_tuning {
                             SYNC run wait for one block more than the grid has, so that the
                             first wait of every block runs out, the kernel returns and the
                             run fails with FSMC_ETIMEOUT (failure detection without a fault) */
+  int sync_form;         /* SYNC mode, ESS jobs (Alg. 6 programs; identical samples): 0 auto = 2;
+                            1 sweep: one cooperative kernel, every group walks all its chains each
+                            loop iteration and skips those already done, a grid barrier per
+                            iteration; 2 list: the chains still in the loop kept in a compacted
+                            list shared by the whole grid, a grid barrier per iteration; 3 graph:
+                            the list iterations as kernel launches in a CUDA graph whose while
+                            loops (conditional nodes) test their conditions on the device.
+                            DR, slice and NUTS jobs run the sweep form                         */
 } fsmc_tuning;
 
 /* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */

@@ -375,6 +375,7 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.ring_slots) tu.ring_slots = long_rounds ? 128 : 32;
     if (!tu.threads_per_block) tu.threads_per_block = 256;
     if (!tu.pipelined) tu.pipelined = 1;
+    if (!tu.sync_form) tu.sync_form = 2;
   } else if (j->algo == FSMC_DR || j->algo == FSMC_SLICE) {
     tu.lanes_per_chain = 1;
     // long launches: fewer kernel tails (funnel, 65536 chains: DR 48.8 -> 48.0 ms, slice 47.4 ->
@@ -436,6 +437,7 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
     j->o_win = L.take(2 * m * 4);
     j->o_colbase = L.take((m + 1) * 8);
     j->o_colmap = L.take(m * (size_t)j->W * 8);
+    j->o_slist = L.take(2 * m * 4 + fsmc::kEssCgStateBytes);
   } else if (j->algo == FSMC_DR) {
     j->o_ell = L.take(m * es);        // log pi(x)
     j->o_y = L.take(3 * m * d * es);  // y1, y2 and (4-state ablation form) the current proposal
@@ -755,6 +757,9 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   if (t.barrier_spin_limit < 0 || t.barrier_test_missing < 0 || t.barrier_test_missing > 1)
     return fsmc_fail(FSMC_EINVAL, "barrier_spin_limit must be >= 0 and barrier_test_missing 0 or 1");
+  if (t.sync_form < 0 || t.sync_form > 3) return fsmc_fail(FSMC_EINVAL, "sync_form must be 0, 1, 2 or 3");
+  if (t.sync_form == 3 && t.barrier_test_missing)
+    return fsmc_fail(FSMC_EINVAL, "the graph form of the synchronised program has no grid barrier");
   j->tun = t;
   default_tuning(j);
   return FSMC_OK;
@@ -1010,6 +1015,8 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
     }
   } else if (j->algo == FSMC_ESS) {
     EssView<T> v = ess_view<T>(j);
+    unsigned long long it0 = 0;
+    if (j->tun.sync_form == 3) CK(cudaMemcpyAsync(&it0, iters, 8, cudaMemcpyDeviceToHost, st));
     for (int64_t t0 = 0; t0 < j->n; t0 += j->W) {
       const int t1 = (int)std::min<int64_t>(t0 + j->W, j->n);
       {
@@ -1021,10 +1028,27 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
         ProfScope p(j, 0, st);
         CK(ess_generate<T>(j, v, st));
       }
-      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
-      ProfScope p(j, 2, st);
-      CK(launch_ess_sync<T>(v, j->tun.lanes_per_chain, (int)t0, t1, bar, active, iters, threads, st));
-      j->launches += 3 + ess_generate_kernels(j);  // two window fills, the refill, the sync kernel
+      int* lists = (int*)(b + j->o_slist);
+      void* cg = b + j->o_slist + 2 * (size_t)j->m * 4;
+      if (j->tun.sync_form == 3) {
+        if (!j->sync_graph)
+          CK(build_ess_sync_graph<T>(v, j->tun.lanes_per_chain, threads, cg, lists, iters, &j->sync_graph));
+        ProfScope p(j, 2, st);
+        CK(launch_ess_sync_graph(j->sync_graph, cg, (int)t0, t1, st));
+        j->launches += 3 + ess_generate_kernels(j);  // two window fills, the refill, the loop-state reset
+      } else {
+        CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+        ProfScope p(j, 2, st);
+        CK(launch_ess_sync<T>(v, j->tun.lanes_per_chain, (int)t0, t1, bar, active, iters, threads,
+                              j->tun.sync_form, lists, st));
+        j->launches += 3 + ess_generate_kernels(j);  // two window fills, the refill, the sync kernel
+      }
+    }
+    if (j->tun.sync_form == 3) {  // the graph's launches: init, ctrl, next per sample, iter + ctrl per iteration
+      unsigned long long it1 = 0;
+      CK(cudaMemcpyAsync(&it1, iters, 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      j->launches += 3 * j->n + 2 * (int64_t)(it1 - it0);
     }
   } else if (j->algo == FSMC_DR) {
     DrView<T> v = dr_view<T>(j);
@@ -1373,6 +1397,7 @@ extern "C" void fsmc_job_destroy(fsmc_job* j) {
   fsmc_engine* e = j->e;
   for (cudaEvent_t ev : j->event_pool) cudaEventDestroy(ev);
   if (j->graph_exec) cudaGraphExecDestroy(j->graph_exec);
+  if (j->sync_graph) cudaGraphExecDestroy(j->sync_graph);
   for (int p = 0; p < 2; ++p) {
     if (j->ev_gen[p]) cudaEventDestroy(j->ev_gen[p]);
     if (j->ev_fsm[p]) cudaEventDestroy(j->ev_fsm[p]);

@@ -721,11 +721,114 @@ __global__ void __launch_bounds__(256) ess_fsm_multi_kernel(const EssView<T>* vi
 }
 
 // ------------------------------------------------------------------------------------------
-// Synchronised kernel (Alg. 6, vmap(sample)): for every sample, INIT for all chains, then
-// the loop body for all chains still below their threshold, with a grid-wide barrier
-// after every iteration, until no chain anywhere is active; then the next sample.
-// Chains are assigned statically to groups; chain state lives in global memory.
-// Launched cooperatively (co-residency guaranteed), barrier waits are bounded.
+// Synchronised program (Alg. 6, vmap(sample)): for every sample, INIT for all chains, then the
+// loop body for all chains still below their threshold, every iteration a grid-wide step, until
+// no chain is left in the loop; then the next sample.  Chain state lives in device memory
+// between visits.  Three forms run the same visits in the same order per chain, so they give the
+// same samples as each other and as the FSM kernels:
+//   sweep  (ess_sync_kernel): every group walks all its chains each iteration, skipping those
+//          already done -- the masked loop of vmap with the masked work skipped;
+//   list   (ess_sync_list_kernel): the chains still in the loop are kept in a compacted list
+//          that every group shares, so an iteration's work is spread over the whole grid and
+//          costs only the chains that are left plus the barrier;
+//   graph  (ess_cg_* kernels in a CUDA graph with conditional while nodes): the same list
+//          iterations as separate kernel launches, the loop conditions evaluated on the device,
+//          no grid barrier.
+// The cooperative kernels are launched with every block resident; barrier waits are bounded.
+
+// One visit of chain c at sample t: INIT (first) or SHRINK, the likelihood of the proposal, DONE
+// when it clears the threshold (or at the shrink cap).  Returns true while sample t of the chain
+// is still open (the chain stays in the loop).
+template <typename T, int G, int E, bool GP>
+__device__ __forceinline__ bool ess_sync_visit(const EssView<T>& v, int64_t c, int t, bool first,
+                                               const T (&yv)[E], int lane, unsigned gmask, int& err) {
+  const int d = v.tg.d;
+  const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
+  T x[E], nu[E], xp[E];
+  const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * G + lane;
+    x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
+    nu[e] = k < d ? src[k] : T(0);
+  }
+  const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  T logy, th, thmin, thmax;
+  int s;
+  if (first) {  // INIT (S1)
+    const P4 r = key.block((uint32_t)t, 0, (uint32_t)D);
+    logy = ess_threshold<T>(v.ell[c], Conv<T>::log_u(r.w0, r.w1));
+    th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
+    thmin = th - T(kTwoPi);
+    thmax = th;
+    s = 0;
+  } else {      // SHRINK (S2)
+    logy = v.logy[c]; th = v.th[c]; thmin = v.thmin[c]; thmax = v.thmax[c]; s = v.s[c];
+    if (th < T(0)) thmin = th; else thmax = th;
+    const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + 1 + s));
+    th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
+    ++s;
+  }
+  T sn, cs;
+  ess_sincos<T>(th, sn, cs);
+#pragma unroll
+  for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
+  T ellp;
+  if constexpr (GP) {
+    // sign-folded coordinates, as in the FSM kernel (ess_advance_chain_gp)
+    T xs[E], ns[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      xs[e] = yv[e] > T(0) ? -x[e] : x[e];
+      ns[e] = yv[e] > T(0) ? -nu[e] : nu[e];
+    }
+    ellp = ess_loglik_gp32<G, E>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
+  } else {
+    ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
+  }
+  if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
+  const bool accept = ellp > logy;
+  if (accept || s >= kMaxShrinks) {  // DONE (S3)
+    if (accept) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = e * G + lane;
+        if (k < d) v.x[(size_t)c * d + k] = xp[e];
+        x[e] = xp[e];
+      }
+    } else {
+      err |= ERR_SHRINK_CAP;
+    }
+    ess_emit<T, G, E>(v, c, t, lane, x);
+    if (lane == 0) {
+      if (accept) v.ell[c] = ellp;
+      v.counts[(size_t)c * v.n + t] = s;
+      v.k[c] = ESS_INIT;
+      v.t[c] = t + 1;
+      v.steps[c] += 1;
+      if (t + 1 == v.n) atomicAdd(v.chains_done, 1);
+    }
+    return false;
+  }
+  if (lane == 0) {
+    v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax; v.s[c] = s;
+    v.k[c] = ESS_SHRINK;
+    v.steps[c] += 1;
+  }
+  return true;
+}
+
+// the likelihood's per-lane data: y (GAUSS_CONJ) or the labels (GP_LOGIT)
+template <typename T, int G, int E>
+__device__ __forceinline__ void ess_sync_lane_data(const EssView<T>& v, int lane, T (&yv)[E]) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * G + lane;
+    yv[e] = (k < v.tg.d && v.tg.vec) ? v.tg.vec[k] : T(0);
+  }
+}
+
+// Sweep form.  Chains are assigned statically to groups.
 template <typename T, int G, int E, bool GP>
 __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin, int t_end,
                                                        GridBarrier bar, unsigned* active_cnt,
@@ -734,18 +837,12 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
   const unsigned gmask = group_mask<G>();
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-  const int d = v.tg.d;
-  const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   __shared__ unsigned blk_active;
   int iter = 0;
   int err = 0;
   T yv[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int k = e * G + lane;
-    yv[e] = (k < d && v.tg.vec) ? v.tg.vec[k] : T(0);
-  }
+  ess_sync_lane_data<T, G, E>(v, lane, yv);
 
   for (int t = t_begin; t < t_end; ++t) {
     bool first = true;
@@ -755,78 +852,7 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
       unsigned my_active = 0;
       for (int64_t c = group; c < v.m; c += ngroups) {
         if (!first && v.k[c] != ESS_SHRINK) continue;  // masked: already done with sample t
-        T x[E], nu[E], xp[E];
-        const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int k = e * G + lane;
-          x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
-          nu[e] = k < d ? src[k] : T(0);
-        }
-        const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
-        T logy, th, thmin, thmax;
-        int s;
-        if (first) {  // INIT (S1)
-          const P4 r = key.block((uint32_t)t, 0, (uint32_t)D);
-          logy = ess_threshold<T>(v.ell[c], Conv<T>::log_u(r.w0, r.w1));
-          th = T(kTwoPi) * Conv<T>::u(r.w2, r.w3);
-          thmin = th - T(kTwoPi);
-          thmax = th;
-          s = 0;
-        } else {      // SHRINK (S2)
-          logy = v.logy[c]; th = v.th[c]; thmin = v.thmin[c]; thmax = v.thmax[c]; s = v.s[c];
-          if (th < T(0)) thmin = th; else thmax = th;
-          const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + 1 + s));
-          th = thmin + (thmax - thmin) * Conv<T>::u(r.w0, r.w1);
-          ++s;
-        }
-        T sn, cs;
-        ess_sincos<T>(th, sn, cs);
-#pragma unroll
-        for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
-        T ellp;
-        if constexpr (GP) {
-          // sign-folded coordinates, as in the FSM kernel (ess_advance_chain_gp)
-          T xs[E], ns[E];
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            xs[e] = yv[e] > T(0) ? -x[e] : x[e];
-            ns[e] = yv[e] > T(0) ? -nu[e] : nu[e];
-          }
-          ellp = ess_loglik_gp32<G, E>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
-        } else {
-          ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
-        }
-        if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
-        const bool accept = ellp > logy;
-        if (accept || s >= kMaxShrinks) {  // DONE (S3)
-          if (accept) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-              const int k = e * G + lane;
-              if (k < d) v.x[(size_t)c * d + k] = xp[e];
-              x[e] = xp[e];
-            }
-          } else {
-            err |= ERR_SHRINK_CAP;
-          }
-          ess_emit<T, G, E>(v, c, t, lane, x);
-          if (lane == 0) {
-            if (accept) v.ell[c] = ellp;
-            v.counts[(size_t)c * v.n + t] = s;
-            v.k[c] = ESS_INIT;
-            v.t[c] = t + 1;
-            v.steps[c] += 1;
-            if (t + 1 == v.n) atomicAdd(v.chains_done, 1);
-          }
-        } else {
-          if (lane == 0) {
-            v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax; v.s[c] = s;
-            v.k[c] = ESS_SHRINK;
-            v.steps[c] += 1;
-          }
-          my_active = 1;
-        }
+        if (ess_sync_visit<T, G, E, GP>(v, c, t, first, yv, lane, gmask, err)) my_active = 1;
       }
       if (my_active && lane == 0) atomicAdd(&blk_active, 1u);
       __syncthreads();
@@ -844,6 +870,130 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
     }
   }
   if (err && lane == 0) atomicOr(v.err, err);
+}
+
+// List form.  Iteration `it` (counted over the whole launch) appends the chains that stay in the
+// loop to list it % 2 with counter it % 3; after the barrier every group reads that counter and
+// takes list entries i = group, group + ngroups, ...  The leader clears counter (it + 2) % 3,
+// whose last reads happened before this barrier and whose next appends come after the next one.
+// lists: [2][m] chain indices.
+template <typename T, int G, int E, bool GP>
+__global__ void __launch_bounds__(256) ess_sync_list_kernel(EssView<T> v, int t_begin, int t_end,
+                                                            GridBarrier bar, unsigned* cnt, int* lists,
+                                                            unsigned long long* iterations) {
+  const int lane = threadIdx.x % G;
+  const unsigned gmask = group_mask<G>();
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  int it = 0;
+  int err = 0;
+  T yv[E];
+  ess_sync_lane_data<T, G, E>(v, lane, yv);
+  for (int t = t_begin; t < t_end; ++t) {
+    // INIT of every chain
+    int* out = lists + (size_t)(it & 1) * v.m;
+    for (int64_t c = group; c < v.m; c += ngroups) {
+      if (ess_sync_visit<T, G, E, GP>(v, c, t, true, yv, lane, gmask, err) && lane == 0)
+        out[atomicAdd(&cnt[it % 3], 1u)] = (int)c;
+    }
+    while (true) {
+      if (!grid_sync(bar, v.err)) return;
+      const unsigned n_act = *(volatile unsigned*)&cnt[it % 3];
+      const int* in = lists + (size_t)(it & 1) * v.m;
+      if (leader) cnt[(it + 2) % 3] = 0;
+      ++it;
+      if (n_act == 0) break;
+      if (leader) *iterations += 1;  // one loop-body iteration of the batched while
+      out = lists + (size_t)(it & 1) * v.m;
+      for (int64_t i = group; i < (int64_t)n_act; i += ngroups) {
+        const int64_t c = in[i];
+        if (ess_sync_visit<T, G, E, GP>(v, c, t, false, yv, lane, gmask, err) && lane == 0)
+          out[atomicAdd(&cnt[it % 3], 1u)] = (int)c;
+      }
+    }
+  }
+  if (err && lane == 0) atomicOr(v.err, err);
+}
+
+// Graph form: device-side state of the loops.  The kernels below run one after another in a
+// graph (no barrier inside a launch); ess_cg_ctrl_kernel evaluates the inner while condition,
+// ess_cg_next_kernel the outer one.
+struct EssCgState {
+  int t;              // current sample
+  int t_end;          // samples of this graph launch end here
+  int phase;          // list / counter the next iteration reads
+  int pad;
+  unsigned cnt[2];    // appended chains per list
+};
+
+// INIT of every chain at sample st->t; the chains that stay in the loop go to list st->phase.
+template <typename T, int G, int E, bool GP>
+__global__ void __launch_bounds__(256) ess_cg_init_kernel(EssView<T> v, EssCgState* st, int* lists) {
+  const int lane = threadIdx.x % G;
+  const unsigned gmask = group_mask<G>();
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int t = st->t, p = st->phase;
+  int err = 0;
+  T yv[E];
+  ess_sync_lane_data<T, G, E>(v, lane, yv);
+  int* out = lists + (size_t)p * v.m;
+  for (int64_t c = group; c < v.m; c += ngroups)
+    if (ess_sync_visit<T, G, E, GP>(v, c, t, true, yv, lane, gmask, err) && lane == 0)
+      out[atomicAdd(&st->cnt[p], 1u)] = (int)c;
+  if (err && lane == 0) atomicOr(v.err, err);
+}
+
+// One loop-body iteration over list st->phase; the chains that stay go to the other list.
+template <typename T, int G, int E, bool GP>
+__global__ void __launch_bounds__(256) ess_cg_iter_kernel(EssView<T> v, EssCgState* st, int* lists) {
+  const int lane = threadIdx.x % G;
+  const unsigned gmask = group_mask<G>();
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int t = st->t, p = st->phase;
+  const int64_t n_act = st->cnt[p];
+  int err = 0;
+  T yv[E];
+  ess_sync_lane_data<T, G, E>(v, lane, yv);
+  const int* in = lists + (size_t)p * v.m;
+  int* out = lists + (size_t)(p ^ 1) * v.m;
+  for (int64_t i = group; i < n_act; i += ngroups) {
+    const int64_t c = in[i];
+    if (ess_sync_visit<T, G, E, GP>(v, c, t, false, yv, lane, gmask, err) && lane == 0)
+      out[atomicAdd(&st->cnt[p ^ 1], 1u)] = (int)c;
+  }
+  if (err && lane == 0) atomicOr(v.err, err);
+}
+
+// After INIT (init = 1) or an iteration: the list just written becomes the next iteration's
+// input; the inner loop continues while it is not empty.
+__global__ void ess_cg_ctrl_kernel(EssCgState* st, int init, cudaGraphConditionalHandle inner,
+                                   unsigned long long* iterations) {
+  const int p = st->phase;
+  if (init) {
+    cudaGraphSetConditional(inner, st->cnt[p] > 0 ? 1u : 0u);
+    return;
+  }
+  *iterations += 1;  // the iteration that just ran
+  st->cnt[p] = 0;
+  st->phase = p ^ 1;
+  cudaGraphSetConditional(inner, st->cnt[p ^ 1] > 0 ? 1u : 0u);
+}
+
+// After a sample: the next one, while samples remain; its INIT writes list st->phase, cleared here.
+__global__ void ess_cg_next_kernel(EssCgState* st, cudaGraphConditionalHandle outer) {
+  st->cnt[st->phase] = 0;
+  st->t += 1;
+  cudaGraphSetConditional(outer, st->t < st->t_end ? 1u : 0u);
+}
+
+__global__ void ess_cg_begin_kernel(EssCgState* st, int t_begin, int t_end) {
+  st->t = t_begin;
+  st->t_end = t_end;
+  st->phase = 0;
+  st->cnt[0] = st->cnt[1] = 0;
 }
 
 // log f(x) of every chain's starting point
@@ -1018,11 +1168,12 @@ static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cuda
 
 template <typename T, int G, int E>
 static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier bar,
-                               unsigned* active_cnt, unsigned long long* iters, int threads,
-                               cudaStream_t st) {
-  auto kern = ess_sync_kernel<T, G, E, false>;
+                               unsigned* active_cnt, unsigned long long* iters, int threads, int form,
+                               int* lists, cudaStream_t st) {
+  void* kern = form == 2 ? (void*)ess_sync_list_kernel<T, G, E, false> : (void*)ess_sync_kernel<T, G, E, false>;
   if constexpr (kEssGpFast<T, E>) {
-    if (v.tg.kind == TGT_GP_LOGIT) kern = ess_sync_kernel<T, G, E, true>;
+    if (v.tg.kind == TGT_GP_LOGIT)
+      kern = form == 2 ? (void*)ess_sync_list_kernel<T, G, E, true> : (void*)ess_sync_kernel<T, G, E, true>;
   }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -1034,8 +1185,91 @@ static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier 
   int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (v.m + groups_per_block - 1) / groups_per_block);
   if (blocks < 1) blocks = 1;
   EssView<T> vv = v;
+  if (form == 2) {
+    void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&lists,
+                    (void*)&iters};
+    return cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+  }
   void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
-  return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+  return cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+}
+
+// The graph form of the synchronised program for samples [t_begin, t_end) of a launch:
+//   while (t < t_end) {              -- outer conditional node, condition set by ess_cg_next_kernel
+//     init; ctrl(init)               -- INIT of every chain, inner condition = list not empty
+//     while (list not empty) {       -- inner conditional node
+//       iter; ctrl                   -- one loop-body iteration over the list, condition updated
+//     }
+//     next                           -- t += 1, outer condition = t < t_end
+//   }
+// The sample range is read from the EssCgState that ess_cg_begin_kernel writes before each launch,
+// so one executable graph serves every chunk of samples of the job.
+template <typename T, int G, int E>
+static cudaError_t sync_graph_build(const EssView<T>& v, int threads, EssCgState* cg, int* lists,
+                                    unsigned long long* iters, cudaGraphExec_t* out) {
+  void* kinit = (void*)ess_cg_init_kernel<T, G, E, false>;
+  void* kiter = (void*)ess_cg_iter_kernel<T, G, E, false>;
+  if constexpr (kEssGpFast<T, E>) {
+    if (v.tg.kind == TGT_GP_LOGIT) {
+      kinit = (void*)ess_cg_init_kernel<T, G, E, true>;
+      kiter = (void*)ess_cg_iter_kernel<T, G, E, true>;
+    }
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kinit, threads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t groups_per_block = threads / G;
+  int64_t blocks = std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, (v.m + groups_per_block - 1) / groups_per_block);
+  if (blocks < 1) blocks = 1;
+
+  cudaGraph_t g = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+  EssView<T> vv = v;
+  int one = 1, zero = 0;
+  auto kernel_node = [&](cudaGraph_t graph, const cudaGraphNode_t* dep, void* fn, dim3 grid, dim3 block,
+                         void** args, cudaGraphNode_t* node) {
+    cudaKernelNodeParams kp{};
+    kp.func = fn;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &kp);
+  };
+  auto while_node = [&](cudaGraph_t graph, const cudaGraphNode_t* dep, cudaGraphConditionalHandle h,
+                        cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaError_t r = cudaGraphAddNode(node, graph, dep, nullptr, dep ? 1 : 0, &np);
+    if (r == cudaSuccess) *body = np.conditional.phGraph_out[0];
+    return r;
+  };
+  cudaGraphConditionalHandle h_out = 0, h_in = 0;
+  cudaGraphNode_t n_out, n_init, n_ctrl0, n_in, n_next, n_iter, n_ctrl;
+  cudaGraph_t outer = nullptr, inner = nullptr;
+  e = cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = while_node(g, nullptr, h_out, &n_out, &outer);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_in, outer, 0, cudaGraphCondAssignDefault);
+  void* a_init[] = {(void*)&vv, (void*)&cg, (void*)&lists};
+  void* a_ctrl0[] = {(void*)&cg, (void*)&one, (void*)&h_in, (void*)&iters};
+  void* a_ctrl[] = {(void*)&cg, (void*)&zero, (void*)&h_in, (void*)&iters};
+  void* a_next[] = {(void*)&cg, (void*)&h_out};
+  if (e == cudaSuccess) e = kernel_node(outer, nullptr, kinit, dim3((unsigned)blocks), dim3(threads), a_init, &n_init);
+  if (e == cudaSuccess) e = kernel_node(outer, &n_init, (void*)ess_cg_ctrl_kernel, dim3(1), dim3(1), a_ctrl0, &n_ctrl0);
+  if (e == cudaSuccess) e = while_node(outer, &n_ctrl0, h_in, &n_in, &inner);
+  if (e == cudaSuccess) e = kernel_node(outer, &n_in, (void*)ess_cg_next_kernel, dim3(1), dim3(1), a_next, &n_next);
+  if (e == cudaSuccess) e = kernel_node(inner, nullptr, kiter, dim3((unsigned)blocks), dim3(threads), a_init, &n_iter);
+  if (e == cudaSuccess) e = kernel_node(inner, &n_iter, (void*)ess_cg_ctrl_kernel, dim3(1), dim3(1), a_ctrl, &n_ctrl);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
 }
 
 #define FSMC_ESS_DISPATCH(FN, ...)                                              \
@@ -1107,9 +1341,23 @@ int ess_group_E(int G, int d) {
 
 template <typename T>
 cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarrier bar,
-                            unsigned* active_cnt, unsigned long long* iters, int threads,
-                            cudaStream_t st) {
-  FSMC_ESS_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
+                            unsigned* active_cnt, unsigned long long* iters, int threads, int form,
+                            int* lists, cudaStream_t st) {
+  FSMC_ESS_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, form, lists, st);
+}
+
+template <typename T>
+cudaError_t build_ess_sync_graph(const EssView<T>& v, int G, int threads, void* cg_state, int* lists,
+                                 unsigned long long* iters, cudaGraphExec_t* out) {
+  EssCgState* cg = (EssCgState*)cg_state;
+  FSMC_ESS_DISPATCH(sync_graph_build, v, threads, cg, lists, iters, out);
+}
+
+cudaError_t launch_ess_sync_graph(cudaGraphExec_t exec, void* cg_state, int t0, int t1, cudaStream_t st) {
+  ess_cg_begin_kernel<<<1, 1, 0, st>>>((EssCgState*)cg_state, t0, t1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaGraphLaunch(exec, st);
 }
 
 template cudaError_t launch_ess_fsm_multi<float>(const EssView<float>&, int, const EssView<float>*,
@@ -1125,8 +1373,12 @@ template cudaError_t launch_ess_nu_gen<double>(const EssView<double>&, cudaStrea
 template cudaError_t launch_ess_fsm<float>(const EssView<float>&, int, int, int, cudaStream_t);
 template cudaError_t launch_ess_fsm<double>(const EssView<double>&, int, int, int, cudaStream_t);
 template cudaError_t launch_ess_sync<float>(const EssView<float>&, int, int, int, GridBarrier,
-                                            unsigned*, unsigned long long*, int, cudaStream_t);
+                                            unsigned*, unsigned long long*, int, int, int*, cudaStream_t);
 template cudaError_t launch_ess_sync<double>(const EssView<double>&, int, int, int, GridBarrier,
-                                             unsigned*, unsigned long long*, int, cudaStream_t);
+                                             unsigned*, unsigned long long*, int, int, int*, cudaStream_t);
+template cudaError_t build_ess_sync_graph<float>(const EssView<float>&, int, int, void*, int*,
+                                                 unsigned long long*, cudaGraphExec_t*);
+template cudaError_t build_ess_sync_graph<double>(const EssView<double>&, int, int, void*, int*,
+                                                  unsigned long long*, cudaGraphExec_t*);
 
 }  // namespace fsmc

@@ -101,10 +101,20 @@ template <typename T>
 cudaError_t launch_ess_nu_gen(const EssView<T>& v, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ess_fsm(const EssView<T>& v, int G, int budget, int threads, cudaStream_t st);
+// Synchronised ESS program (Alg. 6) for samples [t0, t1): form 1 the sweep kernel, form 2 the
+// kernel with a compacted list of the chains still in the loop (lists: [2][m] ints); both
+// cooperative, one grid barrier per loop iteration.
 template <typename T>
 cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarrier bar,
-                            unsigned* active_cnt, unsigned long long* iters, int threads,
-                            cudaStream_t st);
+                            unsigned* active_cnt, unsigned long long* iters, int threads, int form,
+                            int* lists, cudaStream_t st);
+// Form 3: the list iterations as kernels of a graph with conditional while nodes; cg_state is
+// kEssCgStateBytes of device memory, built once per job and launched per chunk of samples.
+constexpr size_t kEssCgStateBytes = 64;
+template <typename T>
+cudaError_t build_ess_sync_graph(const EssView<T>& v, int G, int threads, void* cg_state, int* lists,
+                                 unsigned long long* iters, cudaGraphExec_t* out);
+cudaError_t launch_ess_sync_graph(cudaGraphExec_t exec, void* cg_state, int t0, int t1, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ess_init(const EssView<T>& v, cudaStream_t st);
 // Fused launches over several ESS jobs: views[k] is job k's view in device memory and

@@ -45,7 +45,8 @@ class Tuning(ctypes.Structure):
                 ("ring_slots", ctypes.c_int), ("threads_per_block", ctypes.c_int),
                 ("profile_kernels", ctypes.c_int), ("generator", ctypes.c_int),
                 ("pipelined", ctypes.c_int), ("step_form", ctypes.c_int),
-                ("barrier_spin_limit", ctypes.c_int), ("barrier_test_missing", ctypes.c_int)]
+                ("barrier_spin_limit", ctypes.c_int), ("barrier_test_missing", ctypes.c_int),
+                ("sync_form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -299,3 +299,30 @@ def test_full_size_gp_logit_sampled_chains(full_gp_job):
         print("chain", chain, "flip at", r["first_flip"], "max err", r["max_err"])
         flipped += r["flipped"]
     assert flipped <= FLIP_ALLOW
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("case", ["gp_fp32", "gauss_fp64_lanes1", "gauss_fp64_lanes32"])
+def test_synchronised_forms_equal_the_fsm(eng, form, case):
+    # the three forms of the synchronised program (sweep, compacted list with a grid barrier, graph
+    # with conditional while nodes) run the same visits: samples and loop counts equal the FSM
+    # run's bit for bit, and the loop ran max_j N_ij iterations per sample
+    if case == "gp_fp32":
+        w, m, n, prec, tu = W.gp_logit(256), 300, 64, "fp32", {}
+        x0 = W.x0_normal(m, 256, scale=0.1)
+    else:
+        lanes = 1 if case.endswith("1") else 32
+        w, m, n, prec, tu = W.gauss_conj(16), 200, 150, "fp64", {"lanes_per_chain": lanes}
+        x0 = W.x0_normal(m, 16)
+    a = _run(eng, w, m, n, x0, prec, "fsm", tuning=tu)
+    b = _run(eng, w, m, n, x0, prec, "sync", tuning={**tu, "sync_form": form})
+    assert b.tuning()["sync_form"] == form
+    ca, _, _ = a.loop_counts()
+    cb, _, _ = b.loop_counts()
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(a.samples(), b.samples())
+    st = b.stats()
+    assert st["sync_iterations"] == int(cb.max(0).sum())
+    assert st["error_word"] == 0
+    a.close()
+    b.close()
