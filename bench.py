@@ -318,16 +318,48 @@ def run_ours(args, rank, world):
     total_ms = max_over_ranks(sum(fsm_ms), dist, "cuda")
     value = job_throughput(world, args.steps, m, n, total_ms)
 
-    # synchronised kernel on the same job (Alg. 6), fewer steps: it is the slow baseline
+    # synchronised program (Alg. 6) on the same workload, fewer steps: it is the slow baseline.
+    # ESS runs each of its three forms (sweep, compacted list, conditional graph) on a job of its
+    # own and the fastest is the baseline; the others run their one (sweep) form.
     sync = None
     if not args.no_sync:
-        one("sync")  # warm-up
-        sms, sst = [], None
-        for _ in range(args.sync_steps):
-            ms, sst = one("sync")
-            sms.append(ms)
-        sync = {"value": m * n / (sum(sms) / len(sms) / 1e3), "ms_per_step": sum(sms) / len(sms),
-                "sync_iterations": sst["sync_iterations"], "mean_max_N": sst["mean_max_N"]}
+        forms = [1, 2, 3] if cfg["algo"] == "ess" and w["kind"] != "gp_reg" else [0]
+        per_form = {}
+        for f in forms:
+            if f:
+                sj = eng.job(tg, cfg["algo"], m, n, x0=cfg["x0"], seed=1 + rank, prec=cfg["prec"], store=True,
+                             dr=dr, nuts=nuts, tuning={**tuning, "sync_form": f}, slice=sl)
+            else:
+                sj = job
+
+            def one_sync():
+                sj.reset()
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sj.run("sync", stream=sp)
+                b.record(stream)
+                b.synchronize()
+                return a.elapsed_time(b), sj.stats()
+
+            one_sync()  # warm-up (builds the graph form's executable graph)
+            sms, sst = [], None
+            for _ in range(args.sync_steps):
+                ms, sst = one_sync()
+                sms.append(ms)
+            ms = sum(sms) / len(sms)
+            iters = sst["sync_iterations"]
+            per_form[{0: "sweep", 1: "sweep", 2: "list", 3: "graph"}[f]] = {
+                "value": m * n / (ms / 1e3), "ms_per_step": ms, "sync_iterations": iters,
+                "sync_kernel_ms": sst["kernel_ms"][2], "refill_ms": sst["kernel_ms"][0],
+                # the synchronised kernels' time per loop step (the loop-body iterations plus the
+                # INIT pass of every sample), refills excluded
+                "us_per_loop_step": sst["kernel_ms"][2] * 1e3 / max(1, iters + n),
+                "launches": sst["launches"]}
+            if f:
+                sj.close()
+        best = min(per_form, key=lambda k: per_form[k]["ms_per_step"])
+        sync = {**per_form[best], "form": best, "forms": per_form, "mean_max_N": sst["mean_max_N"]}
 
     # moments-only mode (store = 0): the same job with every sample folded into per-chain
     # compensated sums of x and x^2 as it is drawn instead of stored; timed like the store-all
@@ -535,6 +567,12 @@ def run_ours(args, rank, world):
                                                    "threads_per_block", "generator", "pipelined")}},
             "sync": sync,
             "speedup_fsm_over_sync": (value / world / sync["value"]) if sync else None,
+            # the paper's cost model (Sec. 4.1): a synchronised loop step costs one evaluation of every
+            # chain; here that is the FSM step kernel's time for one state of every chain
+            "cost_model": ({"us_per_all_chain_evaluation": kms_own[1] / args.steps * 1e3 / max(1.0, steps_total / args.steps / m),
+                            "sync_model_ms": (kms_own[1] / args.steps / max(1.0, steps_total / args.steps / m))
+                            * (sync["sync_iterations"] + n) + kms_own[0] / args.steps}
+                           if sync and kms_own[1] else None),
             "moments_only": mom_only,
             "roofline": roof,
             "cpu_baseline": cpu,

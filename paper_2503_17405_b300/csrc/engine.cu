@@ -1008,7 +1008,7 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
     const int chunk = 1000;
     for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
       const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
-      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+      CK(clear_sync_counters(j, st));
       ProfScope p(j, 2, st);
       CK(launch_ess_block_sync<T>(v, (int)t0, t1, bar, active, iters, st));
       j->launches += 1;
@@ -1037,25 +1037,25 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
         CK(launch_ess_sync_graph(j->sync_graph, cg, (int)t0, t1, st));
         j->launches += 3 + ess_generate_kernels(j);  // two window fills, the refill, the loop-state reset
       } else {
-        CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+        CK(clear_sync_counters(j, st));
         ProfScope p(j, 2, st);
         CK(launch_ess_sync<T>(v, j->tun.lanes_per_chain, (int)t0, t1, bar, active, iters, threads,
                               j->tun.sync_form, lists, st));
         j->launches += 3 + ess_generate_kernels(j);  // two window fills, the refill, the sync kernel
       }
     }
-    if (j->tun.sync_form == 3) {  // the graph's launches: init, ctrl, next per sample, iter + ctrl per iteration
+    if (j->tun.sync_form == 3) {  // the graph's launches: init and next per sample, one per iteration
       unsigned long long it1 = 0;
       CK(cudaMemcpyAsync(&it1, iters, 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      j->launches += 3 * j->n + 2 * (int64_t)(it1 - it0);
+      j->launches += 2 * j->n + (int64_t)(it1 - it0);
     }
   } else if (j->algo == FSMC_DR) {
     DrView<T> v = dr_view<T>(j);
     const int chunk = 1000;
     for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
       const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
-      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+      CK(clear_sync_counters(j, st));
       ProfScope p(j, 2, st);
       CK(launch_dr_sync<T>(v, (int)t0, t1, bar, active, iters, threads, st));
       j->launches += 1;
@@ -1065,7 +1065,7 @@ static fsmc_status run_sync(fsmc_job* j, cudaStream_t st) {
     const int chunk = 1000;
     for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
       const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
-      CK(cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st));
+      CK(clear_sync_counters(j, st));
       ProfScope p(j, 2, st);
       CK(launch_slice_sync<T>(v, (int)t0, t1, bar, active, iters, threads, st));
       j->launches += 1;

@@ -113,11 +113,17 @@ struct fsmc_job {
 };
 
 // The job's grid barrier for synchronised launches, with the tuning's wait limit and test hook.
+// Its arrival count and the loop's active-chain counters (o_bar: count at 0, counters at 16..27)
+// are zeroed before every synchronised launch (clear_sync_counters).
 inline fsmc::GridBarrier job_grid_barrier(const fsmc_job* j) {
-  fsmc::GridBarrier bar{(unsigned*)(j->dev + j->o_bar), (unsigned*)(j->dev + j->o_bar) + 1};
+  fsmc::GridBarrier bar{(unsigned*)(j->dev + j->o_bar)};
   if (j->tun.barrier_spin_limit > 0) bar.spin_limit = (unsigned)j->tun.barrier_spin_limit;
   bar.missing = (unsigned)j->tun.barrier_test_missing;
   return bar;
+}
+
+inline cudaError_t clear_sync_counters(const fsmc_job* j, cudaStream_t st) {
+  return cudaMemsetAsync(j->dev + j->o_bar, 0, 32, st);
 }
 
 fsmc_status fsmc_fail(fsmc_status st, const std::string& msg);

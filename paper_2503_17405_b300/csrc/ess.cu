@@ -917,19 +917,48 @@ __global__ void __launch_bounds__(256) ess_sync_list_kernel(EssView<T> v, int t_
 }
 
 // Graph form: device-side state of the loops.  The kernels below run one after another in a
-// graph (no barrier inside a launch); ess_cg_ctrl_kernel evaluates the inner while condition,
-// ess_cg_next_kernel the outer one.
+// graph (no barrier inside a launch).  The last block of the INIT and iteration kernels to finish
+// (counted in blocks_done) evaluates the inner while condition; ess_cg_next_kernel the outer one.
 struct EssCgState {
-  int t;              // current sample
-  int t_end;          // samples of this graph launch end here
-  int phase;          // list / counter the next iteration reads
-  int pad;
-  unsigned cnt[2];    // appended chains per list
+  int t;                // current sample
+  int t_end;            // samples of this graph launch end here
+  int phase;            // list / counter the next iteration reads
+  unsigned blocks_done; // blocks of the running kernel that have finished
+  unsigned cnt[2];      // appended chains per list
 };
+
+// Run by the last block of a kernel to finish: after INIT (init = 1) the list just written is the
+// first iteration's input; after an iteration it becomes the next one's, the consumed list is
+// cleared, and one loop-body iteration is counted.  The inner loop continues while the input list
+// is not empty.
+__device__ __forceinline__ void ess_cg_finish(EssCgState* st, bool init, cudaGraphConditionalHandle inner,
+                                              unsigned long long* iterations) {
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's appends before its count
+    last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();    // every block's appends are visible from here
+  st->blocks_done = 0;
+  const int p = st->phase;
+  if (init) {
+    cudaGraphSetConditional(inner, *(volatile unsigned*)&st->cnt[p] > 0 ? 1u : 0u);
+    return;
+  }
+  *iterations += 1;
+  st->cnt[p] = 0;
+  st->phase = p ^ 1;
+  cudaGraphSetConditional(inner, *(volatile unsigned*)&st->cnt[p ^ 1] > 0 ? 1u : 0u);
+}
 
 // INIT of every chain at sample st->t; the chains that stay in the loop go to list st->phase.
 template <typename T, int G, int E, bool GP>
-__global__ void __launch_bounds__(256) ess_cg_init_kernel(EssView<T> v, EssCgState* st, int* lists) {
+__global__ void __launch_bounds__(256) ess_cg_init_kernel(EssView<T> v, EssCgState* st, int* lists,
+                                                          cudaGraphConditionalHandle inner,
+                                                          unsigned long long* iterations) {
   const int lane = threadIdx.x % G;
   const unsigned gmask = group_mask<G>();
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -943,11 +972,14 @@ __global__ void __launch_bounds__(256) ess_cg_init_kernel(EssView<T> v, EssCgSta
     if (ess_sync_visit<T, G, E, GP>(v, c, t, true, yv, lane, gmask, err) && lane == 0)
       out[atomicAdd(&st->cnt[p], 1u)] = (int)c;
   if (err && lane == 0) atomicOr(v.err, err);
+  ess_cg_finish(st, true, inner, iterations);
 }
 
 // One loop-body iteration over list st->phase; the chains that stay go to the other list.
 template <typename T, int G, int E, bool GP>
-__global__ void __launch_bounds__(256) ess_cg_iter_kernel(EssView<T> v, EssCgState* st, int* lists) {
+__global__ void __launch_bounds__(256) ess_cg_iter_kernel(EssView<T> v, EssCgState* st, int* lists,
+                                                          cudaGraphConditionalHandle inner,
+                                                          unsigned long long* iterations) {
   const int lane = threadIdx.x % G;
   const unsigned gmask = group_mask<G>();
   const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -965,21 +997,7 @@ __global__ void __launch_bounds__(256) ess_cg_iter_kernel(EssView<T> v, EssCgSta
       out[atomicAdd(&st->cnt[p ^ 1], 1u)] = (int)c;
   }
   if (err && lane == 0) atomicOr(v.err, err);
-}
-
-// After INIT (init = 1) or an iteration: the list just written becomes the next iteration's
-// input; the inner loop continues while it is not empty.
-__global__ void ess_cg_ctrl_kernel(EssCgState* st, int init, cudaGraphConditionalHandle inner,
-                                   unsigned long long* iterations) {
-  const int p = st->phase;
-  if (init) {
-    cudaGraphSetConditional(inner, st->cnt[p] > 0 ? 1u : 0u);
-    return;
-  }
-  *iterations += 1;  // the iteration that just ran
-  st->cnt[p] = 0;
-  st->phase = p ^ 1;
-  cudaGraphSetConditional(inner, st->cnt[p ^ 1] > 0 ? 1u : 0u);
+  ess_cg_finish(st, false, inner, iterations);
 }
 
 // After a sample: the next one, while samples remain; its INIT writes list st->phase, cleared here.
@@ -993,6 +1011,7 @@ __global__ void ess_cg_begin_kernel(EssCgState* st, int t_begin, int t_end) {
   st->t = t_begin;
   st->t_end = t_end;
   st->phase = 0;
+  st->blocks_done = 0;
   st->cnt[0] = st->cnt[1] = 0;
 }
 
@@ -1196,9 +1215,11 @@ static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier 
 
 // The graph form of the synchronised program for samples [t_begin, t_end) of a launch:
 //   while (t < t_end) {              -- outer conditional node, condition set by ess_cg_next_kernel
-//     init; ctrl(init)               -- INIT of every chain, inner condition = list not empty
+//     init                           -- INIT of every chain; its last block: inner condition =
+//                                       list not empty
 //     while (list not empty) {       -- inner conditional node
-//       iter; ctrl                   -- one loop-body iteration over the list, condition updated
+//       iter                         -- one loop-body iteration over the list; its last block
+//                                       updates the condition
 //     }
 //     next                           -- t += 1, outer condition = t < t_end
 //   }
@@ -1228,7 +1249,6 @@ static cudaError_t sync_graph_build(const EssView<T>& v, int threads, EssCgState
   cudaGraph_t g = nullptr;
   if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
   EssView<T> vv = v;
-  int one = 1, zero = 0;
   auto kernel_node = [&](cudaGraph_t graph, const cudaGraphNode_t* dep, void* fn, dim3 grid, dim3 block,
                          void** args, cudaGraphNode_t* node) {
     cudaKernelNodeParams kp{};
@@ -1252,21 +1272,17 @@ static cudaError_t sync_graph_build(const EssView<T>& v, int threads, EssCgState
     return r;
   };
   cudaGraphConditionalHandle h_out = 0, h_in = 0;
-  cudaGraphNode_t n_out, n_init, n_ctrl0, n_in, n_next, n_iter, n_ctrl;
+  cudaGraphNode_t n_out, n_init, n_in, n_next, n_iter;
   cudaGraph_t outer = nullptr, inner = nullptr;
   e = cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) e = while_node(g, nullptr, h_out, &n_out, &outer);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_in, outer, 0, cudaGraphCondAssignDefault);
-  void* a_init[] = {(void*)&vv, (void*)&cg, (void*)&lists};
-  void* a_ctrl0[] = {(void*)&cg, (void*)&one, (void*)&h_in, (void*)&iters};
-  void* a_ctrl[] = {(void*)&cg, (void*)&zero, (void*)&h_in, (void*)&iters};
+  void* a_loop[] = {(void*)&vv, (void*)&cg, (void*)&lists, (void*)&h_in, (void*)&iters};
   void* a_next[] = {(void*)&cg, (void*)&h_out};
-  if (e == cudaSuccess) e = kernel_node(outer, nullptr, kinit, dim3((unsigned)blocks), dim3(threads), a_init, &n_init);
-  if (e == cudaSuccess) e = kernel_node(outer, &n_init, (void*)ess_cg_ctrl_kernel, dim3(1), dim3(1), a_ctrl0, &n_ctrl0);
-  if (e == cudaSuccess) e = while_node(outer, &n_ctrl0, h_in, &n_in, &inner);
+  if (e == cudaSuccess) e = kernel_node(outer, nullptr, kinit, dim3((unsigned)blocks), dim3(threads), a_loop, &n_init);
+  if (e == cudaSuccess) e = while_node(outer, &n_init, h_in, &n_in, &inner);
   if (e == cudaSuccess) e = kernel_node(outer, &n_in, (void*)ess_cg_next_kernel, dim3(1), dim3(1), a_next, &n_next);
-  if (e == cudaSuccess) e = kernel_node(inner, nullptr, kiter, dim3((unsigned)blocks), dim3(threads), a_init, &n_iter);
-  if (e == cudaSuccess) e = kernel_node(inner, &n_iter, (void*)ess_cg_ctrl_kernel, dim3(1), dim3(1), a_ctrl, &n_ctrl);
+  if (e == cudaSuccess) e = kernel_node(inner, nullptr, kiter, dim3((unsigned)blocks), dim3(threads), a_loop, &n_iter);
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   return e;

@@ -152,44 +152,50 @@ __device__ __forceinline__ void group_sum_n(T (&v)[N], unsigned mask = 0xfffffff
 
 
 // ---- bounded grid barrier (cooperative launches only) ----------------------------------------
-// Sense-free generation barrier.  Every wait is bounded: after spin_limit polls (default
-// kBarrierSpinLimit) the block records ERR_BARRIER_TIMEOUT and returns false, and a block that
-// sees the bit set by another gives up at once; callers then leave the kernel.
+// Counting barrier.  `count` holds the arrivals of the current launch (zeroed by the host before
+// every launch); with n = blocks (+ missing) per barrier, the arrival that sees count = old
+// belongs to barrier k = old / n, which completes when count reaches (k + 1) n.  Thread 0 of each
+// block releases the block's writes (fence), arrives with one atomic add and polls the count
+// with acquire loads; no block resets or bumps anything, so the last arrival completes the
+// barrier for everyone at once.  Every wait is bounded: after spin_limit polls (default
+// kBarrierSpinLimit) the block records ERR_BARRIER_TIMEOUT and returns false, a block that sees
+// the bit set by another gives up at once, and a block that finds it set before arriving leaves
+// without arriving; callers then leave the kernel.
 struct GridBarrier {
   unsigned* count;
-  unsigned* generation;
   unsigned spin_limit = kBarrierSpinLimit;  // polls before a wait gives up
   unsigned missing = 0;  // test hook: arrivals every wait expects beyond the grid's blocks (0 in
                          // production); with missing > 0 no barrier completes and every wait runs out
 };
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-    volatile unsigned* gen = b.generation;
-    const unsigned g = *gen;
-    __threadfence();
     if (*(volatile int*)err & ERR_BARRIER_TIMEOUT) {
       ok = 0;  // a wait of this run already gave up: leave without arriving
-    } else if (atomicAdd(b.count, 1u) == nblocks - 1 + b.missing) {
-      *b.count = 0;
-      __threadfence();
-      atomicAdd(b.generation, 1u);
     } else {
+      const unsigned n = gridDim.x * gridDim.y * gridDim.z + b.missing;
+      __threadfence();  // the block's writes (ordered before thread 0 by the block barrier) first
+      const unsigned old = atomicAdd(b.count, 1u);
+      const unsigned target = (old / n + 1) * n;
       unsigned spins = 0;
-      while (*gen == g) {
-        if (++spins > b.spin_limit || *(volatile int*)err & ERR_BARRIER_TIMEOUT) {
+      while ((int)(ld_acquire_gpu(b.count) - target) < 0) {
+        if (++spins > b.spin_limit || (*(volatile int*)err & ERR_BARRIER_TIMEOUT)) {
           atomicOr(err, ERR_BARRIER_TIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        if (spins > 64) __nanosleep(32);
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;

@@ -1199,7 +1199,7 @@ fsmc_status nuts_run_sync(fsmc_job* j, cudaStream_t st) {
   const int chunk = 100;
   for (int64_t t0 = 0; t0 < j->n; t0 += chunk) {
     const int t1 = (int)std::min<int64_t>(t0 + chunk, j->n);
-    cudaError_t e = cudaMemsetAsync(active, 0, 3 * sizeof(unsigned), st);
+    cudaError_t e = clear_sync_counters(j, st);
     if (e == cudaSuccess) {
       ProfScope p(j, 2, st);
       e = j->prec == FSMC_FP64 ? nuts_sync_t<double>(j, (int)t0, t1, bar, active, iters, st)
