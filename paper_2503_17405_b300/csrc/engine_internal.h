@@ -100,6 +100,7 @@ struct fsmc_job {
   int rows_smem = 0;                     // covariance rows kept in shared memory
   size_t o_momd = 0;  // [2][m][d] doubles: the moment sums for the host read
   size_t o_stats = 0;  // device statistics: [n] column maxima, then the DevStats record
+  size_t o_fsmq = 0;   // ESS persistent FSM schedule: work counter, [m] segments done
   size_t o_slist = 0;  // ESS synchronised list and graph forms: [2][m] chain lists, graph loop state
   cudaGraphExec_t sync_graph = nullptr;  // ESS synchronised graph form (built at the first SYNC run)
   size_t arena_bytes = 0;  // size of the device block behind dev (>= bytes when reused)

@@ -350,6 +350,58 @@ struct PhiloxLaneCache {
   }
 };
 
+// The same cache for the single-precision GP-logit path, holding each lane's block already
+// converted to the two uniforms the states use: a = u(w0, w1) (the threshold's u at INIT, the
+// shrink's u at SHRINK) and b = u(w2, w3) (the initial angle's u).  A state then moves one float
+// (SHRINK) or two (INIT) by shuffle instead of four words, and converts nothing; the values are
+// the bits Conv<float>::u gives.
+template <int G>
+struct UniformLaneCache {
+  static constexpr int kOff = G < 16 ? G : 16;
+  static constexpr int kSamp = G >= 8 ? G / kOff : 1;
+  float a = 0.f, b = 0.f;
+  int tb = -(1 << 30), ob = 0;
+  bool wide = false;
+  __device__ __forceinline__ void fill(const P4& r) {
+    a = Conv<float>::u(r.w0, r.w1);
+    b = Conv<float>::u(r.w2, r.w3);
+  }
+  // the source lane of (sample t, draw D + off), refilling the cache when it is not held
+  __device__ __forceinline__ int locate(const Key& key, int t, int D, int off, int lane) {
+    if (!wide && (unsigned)t - (unsigned)tb < (unsigned)kSamp && off < kOff) return (t - tb) * kOff + off;
+    if (wide && t == tb && (unsigned)(off - ob) < (unsigned)G) return off - ob;
+    if (off < kOff) {
+      tb = t;
+      wide = false;
+      fill(key.block((uint32_t)(t + lane / kOff), 0, (uint32_t)(D + lane % kOff)));
+      return off;
+    }
+    tb = t;
+    ob = off;
+    wide = true;
+    fill(key.block((uint32_t)t, 0, (uint32_t)(D + off + lane)));
+    return 0;
+  }
+  __device__ __forceinline__ float fetch_a(const Key& key, int t, int D, int off, int lane, unsigned gmask) {
+    if constexpr (G >= 8) {
+      const int src = locate(key, t, D, off, lane);
+      return __shfl_sync(gmask, a, src, G);
+    } else {
+      const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + off));
+      return Conv<float>::u(r.w0, r.w1);
+    }
+  }
+  __device__ __forceinline__ float2 fetch_ab(const Key& key, int t, int D, int off, int lane, unsigned gmask) {
+    if constexpr (G >= 8) {
+      const int src = locate(key, t, D, off, lane);
+      return make_float2(__shfl_sync(gmask, a, src, G), __shfl_sync(gmask, b, src, G));
+    } else {
+      const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + off));
+      return make_float2(Conv<float>::u(r.w0, r.w1), Conv<float>::u(r.w2, r.w3));
+    }
+  }
+};
+
 // Keeps a value the program does not otherwise use (the masked branch's log-density).
 template <typename T>
 __device__ __forceinline__ void ess_keep(T v) {
@@ -471,9 +523,12 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
 // directions were generated before this launch, are copied.
 // MOMC (moments-only jobs): the lane's running sums are held in its shared-memory slot mslot
 // ([4][E]) while the chain advances: loaded here, written back at the end.
+// update_window: the last piece of this launch's work on the chain (persistent schedule: its last
+// segment) sets the next refill window.
 template <int G, int E, bool FULL, bool PF = false, bool MOMC = false>
 __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, int64_t c, int budget, int lane,
-                                                     float* pf = nullptr, float* mslot = nullptr) {
+                                                     float* pf = nullptr, float* mslot = nullptr,
+                                                     bool update_window = true) {
   static_assert(!PF || (G == 32 && FULL && E % 4 == 0), "prefetch needs full 32-lane rows");
   const int d = FULL ? E * G : v.tg.d;
   if constexpr (MOMC) {
@@ -526,7 +581,7 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
   if (st == ESS_SHRINK && t < v.n) load_nu();
   int steps = 0;
   int err = 0;
-  PhiloxLaneCache<G> pc;
+  UniformLaneCache<G> pc;
   for (int b = 0; b < budget && t < v.n; ++b) {
     if (st == ESS_INIT) {
       if (t >= hi) break;  // direction not generated yet
@@ -547,16 +602,15 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
           pf_t = t + 1;
         }
       }
-      const P4 r = pc.fetch(key, t, D, 0, lane, gmask);
-      logy = ess_threshold<float>(ell, Conv<float>::log_u(r.w0, r.w1));
-      th = float(kTwoPi) * Conv<float>::u(r.w2, r.w3);
+      const float2 u = pc.fetch_ab(key, t, D, 0, lane, gmask);
+      logy = ess_threshold<float>(ell, Conv<float>::log_of(u.x));
+      th = float(kTwoPi) * u.y;
       thmin = th - float(kTwoPi);
       thmax = th;
       s = 0;
     } else {
       if (th < 0.f) thmin = th; else thmax = th;
-      const P4 r = pc.fetch(key, t, D, 1 + s, lane, gmask);
-      th = thmin + (thmax - thmin) * Conv<float>::u(r.w0, r.w1);
+      th = thmin + (thmax - thmin) * pc.fetch_a(key, t, D, 1 + s, lane, gmask);
       ++s;
     }
     float sn, cs;
@@ -619,7 +673,7 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
     v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
     v.t[c] = t; v.k[c] = st; v.s[c] = s;
     v.steps[c] += steps;
-    if (v.own_window) {
+    if (v.own_window && update_window) {
       v.gen_lo[c] = hi;
       v.gen_hi[c] = min(t + v.W, v.n);
     }
@@ -673,6 +727,59 @@ ess_fsm_kernel(EssView<T> v, int budget) {
     }
   } else {
     for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, MODE>(v, c, budget, lane);
+  }
+}
+
+// Persistent schedule of the prefetching GP-logit step (32-lane groups, full rows).  A launch
+// gives every chain `budget` states; with one thread block per eight chains the blocks of the
+// last wave leave SMs idle while the final chains finish, a tail of about one chain's share of
+// the launch.  Here a grid of resident blocks takes work items from a counter instead: item k is
+// segment q = k / m of chain c = k mod m, each segment a quarter (nseg = 4) of the chain's
+// states, so the tail is one segment long.  Items are handed out segment-major, so the previous
+// segment of a chain was handed out m items earlier to a group that is running; the group that
+// takes segment q waits (bounded) until seg_done[c] reaches q, then continues the chain from the
+// state that segment left in device memory.  The samples are those of any other split of the
+// chain's states into launches.
+template <int G, int E>
+__global__ void __launch_bounds__(256, (ess_min_blocks<float, G, E, 2>()))
+ess_fsm_seg_kernel(EssView<float> v, int budget) {
+  static_assert(G == 32 && E % 4 == 0, "the persistent schedule serves the prefetching form");
+  __shared__ __align__(16) float pf_rows[8][E * G];
+  float* pf = pf_rows[threadIdx.x / 32];
+  const int lane = threadIdx.x % 32;
+  const int nseg = v.nseg;
+  const int seg = (budget + nseg - 1) / nseg;
+  const unsigned long long items = (unsigned long long)v.m * nseg;
+  while (true) {
+    unsigned long long k = 0;
+    if (lane == 0) k = atomicAdd(v.work, 1ull);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= items) break;
+    const int q = (int)(k / (unsigned long long)v.m);
+    const int64_t c = (int64_t)(k - (unsigned long long)q * v.m);
+    if (q > 0) {  // the chain's previous segment first
+      int ok = 1;
+      if (lane == 0) {
+        unsigned spins = 0;
+        while ((int)ld_acquire_gpu((const unsigned*)&v.seg_done[c]) < q) {
+          if (++spins > kBarrierSpinLimit || (*(volatile int*)v.err & ERR_BARRIER_TIMEOUT)) {
+            atomicOr(v.err, ERR_BARRIER_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      __syncwarp();
+    }
+    const int len = q + 1 < nseg ? seg : budget - seg * (nseg - 1);
+    if (len > 0) ess_advance_chain_gp<G, E, true, true>(v, c, len, lane, pf, nullptr, q + 1 == nseg);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();  // the chain's state before its segment count
+      atomicExch(&v.seg_done[c], q + 1);
+    }
   }
 }
 
@@ -738,19 +845,35 @@ __global__ void __launch_bounds__(256) ess_fsm_multi_kernel(const EssView<T>* vi
 
 // One visit of chain c at sample t: INIT (first) or SHRINK, the likelihood of the proposal, DONE
 // when it clears the threshold (or at the shrink cap).  Returns true while sample t of the chain
-// is still open (the chain stays in the loop).
+// is still open (the chain stays in the loop).  `ld` is the lane's likelihood data
+// (ess_sync_lane_data).
+template <typename T, int E>
+struct EssLaneData {
+  T yv[E];         // y (GAUSS_CONJ) or labels (GP_LOGIT) of the lane's coordinates (generic path)
+  uint32_t smask;  // GP-logit path: bit e set where the label of coordinate e is +1
+};
+
 template <typename T, int G, int E, bool GP>
 __device__ __forceinline__ bool ess_sync_visit(const EssView<T>& v, int64_t c, int t, bool first,
-                                               const T (&yv)[E], int lane, unsigned gmask, int& err) {
+                                               const EssLaneData<T, E>& ld, int lane, unsigned gmask, int& err) {
   const int d = v.tg.d;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
-  T x[E], nu[E], xp[E];
   const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+  // GP path: the sign-folded coordinates xs = -s x, ns = -s nu, as in the FSM kernel
+  // (ess_advance_chain_gp); otherwise x and nu
+  T xa[E], na[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = e * G + lane;
-    x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
-    nu[e] = k < d ? src[k] : T(0);
+    const T x = k < d ? v.x[(size_t)c * d + k] : T(0);
+    const T nu = k < d ? src[k] : T(0);
+    if constexpr (GP) {
+      xa[e] = flip_sign(x, ld.smask, e);
+      na[e] = flip_sign(nu, ld.smask, e);
+    } else {
+      xa[e] = x;
+      na[e] = nu;
+    }
   }
   const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
   T logy, th, thmin, thmax;
@@ -771,34 +894,29 @@ __device__ __forceinline__ bool ess_sync_visit(const EssView<T>& v, int64_t c, i
   }
   T sn, cs;
   ess_sincos<T>(th, sn, cs);
-#pragma unroll
-  for (int e = 0; e < E; ++e) xp[e] = fma(x[e], cs, nu[e] * sn);
   T ellp;
   if constexpr (GP) {
-    // sign-folded coordinates, as in the FSM kernel (ess_advance_chain_gp)
-    T xs[E], ns[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      xs[e] = yv[e] > T(0) ? -x[e] : x[e];
-      ns[e] = yv[e] > T(0) ? -nu[e] : nu[e];
-    }
-    ellp = ess_loglik_gp32<G, E>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
+    ellp = ess_loglik_gp32<G, E>(xa, na, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
   } else {
-    ellp = ess_loglik<T, G, E>(v.tg, xp, lane, yv, gmask);
+    T xp[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) xp[e] = fma(xa[e], cs, na[e] * sn);
+    ellp = ess_loglik<T, G, E>(v.tg, xp, lane, ld.yv, gmask);
   }
   if (!(ellp == ellp)) { ellp = neg_inf<T>(); err |= ERR_NONFINITE; }
   const bool accept = ellp > logy;
   if (accept || s >= kMaxShrinks) {  // DONE (S3)
-    if (accept) {
+    T x[E];
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int k = e * G + lane;
-        if (k < d) v.x[(size_t)c * d + k] = xp[e];
-        x[e] = xp[e];
-      }
-    } else {
-      err |= ERR_SHRINK_CAP;
+    for (int e = 0; e < E; ++e) {
+      // the accepted point x' = x cos + nu sin (GP path: -s x', exactly, then unfolded)
+      const T xn = accept ? fma(xa[e], cs, na[e] * sn) : xa[e];
+      if constexpr (GP) x[e] = flip_sign(xn, ld.smask, e);
+      else x[e] = xn;
+      const int k = e * G + lane;
+      if (accept && k < d) v.x[(size_t)c * d + k] = x[e];
     }
+    if (!accept) err |= ERR_SHRINK_CAP;
     ess_emit<T, G, E>(v, c, t, lane, x);
     if (lane == 0) {
       if (accept) v.ell[c] = ellp;
@@ -818,19 +936,34 @@ __device__ __forceinline__ bool ess_sync_visit(const EssView<T>& v, int64_t c, i
   return true;
 }
 
-// the likelihood's per-lane data: y (GAUSS_CONJ) or the labels (GP_LOGIT)
-template <typename T, int G, int E>
-__device__ __forceinline__ void ess_sync_lane_data(const EssView<T>& v, int lane, T (&yv)[E]) {
+// the likelihood's per-lane data: y (GAUSS_CONJ) or the labels (GP_LOGIT); the GP-logit path keeps
+// only the labels' signs
+template <typename T, int G, int E, bool GP>
+__device__ __forceinline__ EssLaneData<T, E> ess_sync_lane_data(const EssView<T>& v, int lane) {
+  EssLaneData<T, E> ld;
+  ld.smask = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = e * G + lane;
-    yv[e] = (k < v.tg.d && v.tg.vec) ? v.tg.vec[k] : T(0);
+    const T y = (k < v.tg.d && v.tg.vec) ? v.tg.vec[k] : T(0);
+    if constexpr (GP) {
+      if (y > T(0)) ld.smask |= 1u << e;
+      ld.yv[e] = T(0);
+    } else {
+      ld.yv[e] = y;
+    }
   }
+  return ld;
 }
+
+// registers per thread for the synchronised kernels: three 256-thread blocks per SM in single
+// precision (85 registers), two in double
+template <typename T>
+__host__ __device__ constexpr int ess_sync_min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
 
 // Sweep form.  Chains are assigned statically to groups.
 template <typename T, int G, int E, bool GP>
-__global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin, int t_end,
+__global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_sync_kernel(EssView<T> v, int t_begin, int t_end,
                                                        GridBarrier bar, unsigned* active_cnt,
                                                        unsigned long long* iterations) {
   const int lane = threadIdx.x % G;
@@ -841,19 +974,30 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
   __shared__ unsigned blk_active;
   int iter = 0;
   int err = 0;
-  T yv[E];
-  ess_sync_lane_data<T, G, E>(v, lane, yv);
+  const EssLaneData<T, E> ld = ess_sync_lane_data<T, G, E, GP>(v, lane);
 
+  // With at most 32 chains per group, the group keeps a bit mask of its chains still in the loop
+  // (bit j: chain group + j ngroups), so a finished chain costs nothing in later iterations;
+  // otherwise it reads each chain's state id.
+  const bool use_mask = v.m <= 32 * ngroups;
   for (int t = t_begin; t < t_end; ++t) {
     bool first = true;
+    unsigned live = 0;
     while (true) {
       if (threadIdx.x == 0) blk_active = 0;
       __syncthreads();
       unsigned my_active = 0;
-      for (int64_t c = group; c < v.m; c += ngroups) {
-        if (!first && v.k[c] != ESS_SHRINK) continue;  // masked: already done with sample t
-        if (ess_sync_visit<T, G, E, GP>(v, c, t, first, yv, lane, gmask, err)) my_active = 1;
+      unsigned next = 0;
+      int j = 0;
+      for (int64_t c = group; c < v.m; c += ngroups, ++j) {
+        // masked: already done with sample t
+        const bool open = first || (use_mask ? ((live >> j) & 1u) != 0 : v.k[c] == ESS_SHRINK);
+        if (open && ess_sync_visit<T, G, E, GP>(v, c, t, first, ld, lane, gmask, err)) {
+          my_active = 1;
+          if (use_mask) next |= 1u << j;
+        }
       }
+      live = next;
       if (my_active && lane == 0) atomicAdd(&blk_active, 1u);
       __syncthreads();
       const int slot = iter % 3;
@@ -878,7 +1022,7 @@ __global__ void __launch_bounds__(256) ess_sync_kernel(EssView<T> v, int t_begin
 // whose last reads happened before this barrier and whose next appends come after the next one.
 // lists: [2][m] chain indices.
 template <typename T, int G, int E, bool GP>
-__global__ void __launch_bounds__(256) ess_sync_list_kernel(EssView<T> v, int t_begin, int t_end,
+__global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_sync_list_kernel(EssView<T> v, int t_begin, int t_end,
                                                             GridBarrier bar, unsigned* cnt, int* lists,
                                                             unsigned long long* iterations) {
   const int lane = threadIdx.x % G;
@@ -888,13 +1032,12 @@ __global__ void __launch_bounds__(256) ess_sync_list_kernel(EssView<T> v, int t_
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int it = 0;
   int err = 0;
-  T yv[E];
-  ess_sync_lane_data<T, G, E>(v, lane, yv);
+  const EssLaneData<T, E> ld = ess_sync_lane_data<T, G, E, GP>(v, lane);
   for (int t = t_begin; t < t_end; ++t) {
     // INIT of every chain
     int* out = lists + (size_t)(it & 1) * v.m;
     for (int64_t c = group; c < v.m; c += ngroups) {
-      if (ess_sync_visit<T, G, E, GP>(v, c, t, true, yv, lane, gmask, err) && lane == 0)
+      if (ess_sync_visit<T, G, E, GP>(v, c, t, true, ld, lane, gmask, err) && lane == 0)
         out[atomicAdd(&cnt[it % 3], 1u)] = (int)c;
     }
     while (true) {
@@ -908,7 +1051,7 @@ __global__ void __launch_bounds__(256) ess_sync_list_kernel(EssView<T> v, int t_
       out = lists + (size_t)(it & 1) * v.m;
       for (int64_t i = group; i < (int64_t)n_act; i += ngroups) {
         const int64_t c = in[i];
-        if (ess_sync_visit<T, G, E, GP>(v, c, t, false, yv, lane, gmask, err) && lane == 0)
+        if (ess_sync_visit<T, G, E, GP>(v, c, t, false, ld, lane, gmask, err) && lane == 0)
           out[atomicAdd(&cnt[it % 3], 1u)] = (int)c;
       }
     }
@@ -956,7 +1099,7 @@ __device__ __forceinline__ void ess_cg_finish(EssCgState* st, bool init, cudaGra
 
 // INIT of every chain at sample st->t; the chains that stay in the loop go to list st->phase.
 template <typename T, int G, int E, bool GP>
-__global__ void __launch_bounds__(256) ess_cg_init_kernel(EssView<T> v, EssCgState* st, int* lists,
+__global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_cg_init_kernel(EssView<T> v, EssCgState* st, int* lists,
                                                           cudaGraphConditionalHandle inner,
                                                           unsigned long long* iterations) {
   const int lane = threadIdx.x % G;
@@ -965,11 +1108,10 @@ __global__ void __launch_bounds__(256) ess_cg_init_kernel(EssView<T> v, EssCgSta
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   const int t = st->t, p = st->phase;
   int err = 0;
-  T yv[E];
-  ess_sync_lane_data<T, G, E>(v, lane, yv);
+  const EssLaneData<T, E> ld = ess_sync_lane_data<T, G, E, GP>(v, lane);
   int* out = lists + (size_t)p * v.m;
   for (int64_t c = group; c < v.m; c += ngroups)
-    if (ess_sync_visit<T, G, E, GP>(v, c, t, true, yv, lane, gmask, err) && lane == 0)
+    if (ess_sync_visit<T, G, E, GP>(v, c, t, true, ld, lane, gmask, err) && lane == 0)
       out[atomicAdd(&st->cnt[p], 1u)] = (int)c;
   if (err && lane == 0) atomicOr(v.err, err);
   ess_cg_finish(st, true, inner, iterations);
@@ -977,7 +1119,7 @@ __global__ void __launch_bounds__(256) ess_cg_init_kernel(EssView<T> v, EssCgSta
 
 // One loop-body iteration over list st->phase; the chains that stay go to the other list.
 template <typename T, int G, int E, bool GP>
-__global__ void __launch_bounds__(256) ess_cg_iter_kernel(EssView<T> v, EssCgState* st, int* lists,
+__global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_cg_iter_kernel(EssView<T> v, EssCgState* st, int* lists,
                                                           cudaGraphConditionalHandle inner,
                                                           unsigned long long* iterations) {
   const int lane = threadIdx.x % G;
@@ -987,13 +1129,12 @@ __global__ void __launch_bounds__(256) ess_cg_iter_kernel(EssView<T> v, EssCgSta
   const int t = st->t, p = st->phase;
   const int64_t n_act = st->cnt[p];
   int err = 0;
-  T yv[E];
-  ess_sync_lane_data<T, G, E>(v, lane, yv);
+  const EssLaneData<T, E> ld = ess_sync_lane_data<T, G, E, GP>(v, lane);
   const int* in = lists + (size_t)p * v.m;
   int* out = lists + (size_t)(p ^ 1) * v.m;
   for (int64_t i = group; i < n_act; i += ngroups) {
     const int64_t c = in[i];
-    if (ess_sync_visit<T, G, E, GP>(v, c, t, false, yv, lane, gmask, err) && lane == 0)
+    if (ess_sync_visit<T, G, E, GP>(v, c, t, false, ld, lane, gmask, err) && lane == 0)
       out[atomicAdd(&st->cnt[p ^ 1], 1u)] = (int)c;
   }
   if (err && lane == 0) atomicOr(v.err, err);
@@ -1171,6 +1312,21 @@ static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cuda
     if (v.tg.kind == TGT_GP_LOGIT) {
       if (v.tg.d == E * G) {
         const size_t momb = (size_t)threads * (4 * E + 1) * sizeof(float);
+        if constexpr (kEssPrefetch<T, G, E, 2>) {
+          if (v.work && v.out && budget >= v.nseg) {  // persistent schedule (store-all jobs)
+            cudaError_t e = cudaMemsetAsync(v.work, 0, sizeof(unsigned long long), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(v.seg_done, 0, (size_t)v.m * sizeof(int), st);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, dev = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ess_fsm_seg_kernel<G, E>, 256, 0);
+            if (e != cudaSuccess) return e;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int64_t grid = std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, (v.m + 7) / 8);
+            ess_fsm_seg_kernel<G, E><<<(unsigned)grid, 256, 0, st>>>(v, budget);
+            return cudaGetLastError();
+          }
+        }
         if (kEssPrefetch<T, G, E, 2> && !v.out && momb <= 48 * 1024)
           ess_fsm_kernel<T, G, E, 2, true><<<(unsigned)blocks, threads, momb, st>>>(v, budget);
         else

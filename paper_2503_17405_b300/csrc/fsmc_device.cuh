@@ -99,9 +99,9 @@ template <> struct Conv<float> {
   // log u = ln 2 log2 u with lg2.approx: absolute error ~1e-7, which moves a comparison of log u
   // with a log acceptance ratio, or a slice threshold log f + log u, by far less than the FP32
   // rounding of the log-densities involved
-  static __device__ __forceinline__ float log_u(uint32_t hi, uint32_t lo) {
-    return lg2_approx(u(hi, lo)) * 0.693147180559945309417f;
-  }
+  static __device__ __forceinline__ float log_u(uint32_t hi, uint32_t lo) { return log_of(u(hi, lo)); }
+  // log of a uniform already converted (the same bits as log_u of its words)
+  static __device__ __forceinline__ float log_of(float u) { return lg2_approx(u) * 0.693147180559945309417f; }
   // single-precision rounding of the one-word uniform (w + 1/2) 2^-32
   static __device__ __forceinline__ float u32(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
   // Box-Muller with the hardware approximations: the radius r = sqrt(-2 ln 2 log2 u) from
