@@ -158,12 +158,6 @@ typedef struct fsmc_tuning {
                             the list iterations as kernel launches in a CUDA graph whose while
                             loops (conditional nodes) test their conditions on the device.
                             DR, slice and NUTS jobs run the sweep form                         */
-  int fsm_schedule;      /* FSM launches of FP32 GP-logit ESS jobs with 32 lanes per chain and
-                            full rows (d a multiple of 128), storing samples: 0 auto = 2;
-                            1 one thread block per eight chains, scheduled by the hardware;
-                            2 persistent: resident blocks take (chain, quarter of the launch's
-                            states) items from a counter, so a launch ends within a quarter of a
-                            chain's share instead of a whole share (same samples)             */
 } fsmc_tuning;
 
 /* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */

@@ -376,7 +376,6 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.threads_per_block) tu.threads_per_block = 256;
     if (!tu.pipelined) tu.pipelined = 1;
     if (!tu.sync_form) tu.sync_form = 2;
-    if (!tu.fsm_schedule) tu.fsm_schedule = 2;
   } else if (j->algo == FSMC_DR || j->algo == FSMC_SLICE) {
     tu.lanes_per_chain = 1;
     // long launches: fewer kernel tails (funnel, 65536 chains: DR 48.8 -> 48.0 ms, slice 47.4 ->
@@ -406,6 +405,7 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
   j->o_mom = L.take(4 * m * d * es);  // running sums (moments-only jobs) or their reduction
   j->o_momd = L.take(2 * m * d * 8);  // the sums as doubles, for the host read
   j->o_bar = L.take(64);
+  j->o_gbar = L.take(fsmc::kGridBarrierBytes);
   j->o_iters = L.take(8);
   j->o_stats = L.take(align_up(n * 4, 64) + sizeof(fsmc::DevStats));
   if (ess_block(j)) {
@@ -439,7 +439,6 @@ static fsmc_status job_layout_and_alloc(fsmc_job* j) {
     j->o_colbase = L.take((m + 1) * 8);
     j->o_colmap = L.take(m * (size_t)j->W * 8);
     j->o_slist = L.take(2 * m * 4 + fsmc::kEssCgStateBytes);
-    j->o_fsmq = L.take(8 + m * 4);  // persistent FSM schedule: work counter, segments done per chain
   } else if (j->algo == FSMC_DR) {
     j->o_ell = L.take(m * es);        // log pi(x)
     j->o_y = L.take(3 * m * d * es);  // y1, y2 and (4-state ablation form) the current proposal
@@ -522,11 +521,6 @@ EssView<T> ess_view(const fsmc_job* j) {
   v.own_window = 1;
   v.col_base = (long long*)(b + j->o_colbase);
   v.colmap = (int2*)(b + j->o_colmap);
-  if (j->tun.fsm_schedule == 2) {  // used where the launch's shape allows it (launch_ess_fsm)
-    v.work = (unsigned long long*)(b + j->o_fsmq);
-    v.seg_done = (int*)(b + j->o_fsmq + 8);
-    v.nseg = 4;
-  }
   return v;
 }
 
@@ -603,6 +597,7 @@ static fsmc_status job_init_state(fsmc_job* j, cudaStream_t st) {
   CK(cudaMemsetAsync(b + j->o_err, 0, 4, st));
   CK(cudaMemsetAsync(b + j->o_done, 0, 4, st));
   CK(cudaMemsetAsync(b + j->o_bar, 0, 64, st));
+  CK(cudaMemsetAsync(b + j->o_gbar, 0, fsmc::kGridBarrierBytes, st));
   CK(cudaMemsetAsync(b + j->o_iters, 0, 8, st));
   if (!j->store) CK(cudaMemsetAsync(b + j->o_mom, 0, 4 * m * d * sizeof(T), st));
   if (ess_block(j)) {
@@ -765,7 +760,6 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (t.barrier_spin_limit < 0 || t.barrier_test_missing < 0 || t.barrier_test_missing > 1)
     return fsmc_fail(FSMC_EINVAL, "barrier_spin_limit must be >= 0 and barrier_test_missing 0 or 1");
   if (t.sync_form < 0 || t.sync_form > 3) return fsmc_fail(FSMC_EINVAL, "sync_form must be 0, 1, 2 or 3");
-  if (t.fsm_schedule < 0 || t.fsm_schedule > 2) return fsmc_fail(FSMC_EINVAL, "fsm_schedule must be 0, 1 or 2");
   if (t.sync_form == 3 && t.barrier_test_missing)
     return fsmc_fail(FSMC_EINVAL, "the graph form of the synchronised program has no grid barrier");
   j->tun = t;

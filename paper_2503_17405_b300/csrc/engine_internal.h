@@ -99,8 +99,8 @@ struct fsmc_job {
   int64_t spill_ctas = 0;                // beyond shared memory
   int rows_smem = 0;                     // covariance rows kept in shared memory
   size_t o_momd = 0;  // [2][m][d] doubles: the moment sums for the host read
+  size_t o_gbar = 0;   // grid barrier of synchronised launches (fsmc::kGridBarrierBytes)
   size_t o_stats = 0;  // device statistics: [n] column maxima, then the DevStats record
-  size_t o_fsmq = 0;   // ESS persistent FSM schedule: work counter, [m] segments done
   size_t o_slist = 0;  // ESS synchronised list and graph forms: [2][m] chain lists, graph loop state
   cudaGraphExec_t sync_graph = nullptr;  // ESS synchronised graph form (built at the first SYNC run)
   size_t arena_bytes = 0;  // size of the device block behind dev (>= bytes when reused)
@@ -114,17 +114,19 @@ struct fsmc_job {
 };
 
 // The job's grid barrier for synchronised launches, with the tuning's wait limit and test hook.
-// Its arrival count and the loop's active-chain counters (o_bar: count at 0, counters at 16..27)
-// are zeroed before every synchronised launch (clear_sync_counters).
+// Its counters (o_gbar) and the loop's active-chain counters (o_bar, at 16..27) are zeroed before
+// every synchronised launch (clear_sync_counters).
 inline fsmc::GridBarrier job_grid_barrier(const fsmc_job* j) {
-  fsmc::GridBarrier bar{(unsigned*)(j->dev + j->o_bar)};
+  fsmc::GridBarrier bar{(unsigned*)(j->dev + j->o_gbar)};
   if (j->tun.barrier_spin_limit > 0) bar.spin_limit = (unsigned)j->tun.barrier_spin_limit;
   bar.missing = (unsigned)j->tun.barrier_test_missing;
   return bar;
 }
 
 inline cudaError_t clear_sync_counters(const fsmc_job* j, cudaStream_t st) {
-  return cudaMemsetAsync(j->dev + j->o_bar, 0, 32, st);
+  cudaError_t e = cudaMemsetAsync(j->dev + j->o_bar, 0, 64, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->dev + j->o_gbar, 0, fsmc::kGridBarrierBytes, st);
+  return e;
 }
 
 fsmc_status fsmc_fail(fsmc_status st, const std::string& msg);

@@ -523,12 +523,9 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
 // directions were generated before this launch, are copied.
 // MOMC (moments-only jobs): the lane's running sums are held in its shared-memory slot mslot
 // ([4][E]) while the chain advances: loaded here, written back at the end.
-// update_window: the last piece of this launch's work on the chain (persistent schedule: its last
-// segment) sets the next refill window.
 template <int G, int E, bool FULL, bool PF = false, bool MOMC = false>
 __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, int64_t c, int budget, int lane,
-                                                     float* pf = nullptr, float* mslot = nullptr,
-                                                     bool update_window = true) {
+                                                     float* pf = nullptr, float* mslot = nullptr) {
   static_assert(!PF || (G == 32 && FULL && E % 4 == 0), "prefetch needs full 32-lane rows");
   const int d = FULL ? E * G : v.tg.d;
   if constexpr (MOMC) {
@@ -673,7 +670,7 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
     v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
     v.t[c] = t; v.k[c] = st; v.s[c] = s;
     v.steps[c] += steps;
-    if (v.own_window && update_window) {
+    if (v.own_window) {
       v.gen_lo[c] = hi;
       v.gen_hi[c] = min(t + v.W, v.n);
     }
@@ -727,59 +724,6 @@ ess_fsm_kernel(EssView<T> v, int budget) {
     }
   } else {
     for (int64_t c = group; c < v.m; c += ngroups) ess_advance_chain<T, G, E, MODE>(v, c, budget, lane);
-  }
-}
-
-// Persistent schedule of the prefetching GP-logit step (32-lane groups, full rows).  A launch
-// gives every chain `budget` states; with one thread block per eight chains the blocks of the
-// last wave leave SMs idle while the final chains finish, a tail of about one chain's share of
-// the launch.  Here a grid of resident blocks takes work items from a counter instead: item k is
-// segment q = k / m of chain c = k mod m, each segment a quarter (nseg = 4) of the chain's
-// states, so the tail is one segment long.  Items are handed out segment-major, so the previous
-// segment of a chain was handed out m items earlier to a group that is running; the group that
-// takes segment q waits (bounded) until seg_done[c] reaches q, then continues the chain from the
-// state that segment left in device memory.  The samples are those of any other split of the
-// chain's states into launches.
-template <int G, int E>
-__global__ void __launch_bounds__(256, (ess_min_blocks<float, G, E, 2>()))
-ess_fsm_seg_kernel(EssView<float> v, int budget) {
-  static_assert(G == 32 && E % 4 == 0, "the persistent schedule serves the prefetching form");
-  __shared__ __align__(16) float pf_rows[8][E * G];
-  float* pf = pf_rows[threadIdx.x / 32];
-  const int lane = threadIdx.x % 32;
-  const int nseg = v.nseg;
-  const int seg = (budget + nseg - 1) / nseg;
-  const unsigned long long items = (unsigned long long)v.m * nseg;
-  while (true) {
-    unsigned long long k = 0;
-    if (lane == 0) k = atomicAdd(v.work, 1ull);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k >= items) break;
-    const int q = (int)(k / (unsigned long long)v.m);
-    const int64_t c = (int64_t)(k - (unsigned long long)q * v.m);
-    if (q > 0) {  // the chain's previous segment first
-      int ok = 1;
-      if (lane == 0) {
-        unsigned spins = 0;
-        while ((int)ld_acquire_gpu((const unsigned*)&v.seg_done[c]) < q) {
-          if (++spins > kBarrierSpinLimit || (*(volatile int*)v.err & ERR_BARRIER_TIMEOUT)) {
-            atomicOr(v.err, ERR_BARRIER_TIMEOUT);
-            ok = 0;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      __syncwarp();
-    }
-    const int len = q + 1 < nseg ? seg : budget - seg * (nseg - 1);
-    if (len > 0) ess_advance_chain_gp<G, E, true, true>(v, c, len, lane, pf, nullptr, q + 1 == nseg);
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence();  // the chain's state before its segment count
-      atomicExch(&v.seg_done[c], q + 1);
-    }
   }
 }
 
@@ -1000,8 +944,10 @@ __global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_sync_kern
       live = next;
       if (my_active && lane == 0) atomicAdd(&blk_active, 1u);
       __syncthreads();
+      // whether any chain stays in the loop: a flag that blocks with live chains set (a store,
+      // not an atomic: only its being non-zero is read)
       const int slot = iter % 3;
-      if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+      if (threadIdx.x == 0 && blk_active) *(volatile unsigned*)&active_cnt[slot] = 1u;
       if (!grid_sync(bar, v.err)) return;
       const unsigned total = *(volatile unsigned*)&active_cnt[slot];
       if (leader) {
@@ -1312,21 +1258,6 @@ static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cuda
     if (v.tg.kind == TGT_GP_LOGIT) {
       if (v.tg.d == E * G) {
         const size_t momb = (size_t)threads * (4 * E + 1) * sizeof(float);
-        if constexpr (kEssPrefetch<T, G, E, 2>) {
-          if (v.work && v.out && budget >= v.nseg) {  // persistent schedule (store-all jobs)
-            cudaError_t e = cudaMemsetAsync(v.work, 0, sizeof(unsigned long long), st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(v.seg_done, 0, (size_t)v.m * sizeof(int), st);
-            if (e != cudaSuccess) return e;
-            int per_sm = 0, dev = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ess_fsm_seg_kernel<G, E>, 256, 0);
-            if (e != cudaSuccess) return e;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int64_t grid = std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, (v.m + 7) / 8);
-            ess_fsm_seg_kernel<G, E><<<(unsigned)grid, 256, 0, st>>>(v, budget);
-            return cudaGetLastError();
-          }
-        }
         if (kEssPrefetch<T, G, E, 2> && !v.out && momb <= 48 * 1024)
           ess_fsm_kernel<T, G, E, 2, true><<<(unsigned)blocks, threads, momb, st>>>(v, budget);
         else
@@ -1438,7 +1369,9 @@ static cudaError_t sync_graph_build(const EssView<T>& v, int threads, EssCgState
   if (e == cudaSuccess) e = kernel_node(outer, nullptr, kinit, dim3((unsigned)blocks), dim3(threads), a_loop, &n_init);
   if (e == cudaSuccess) e = while_node(outer, &n_init, h_in, &n_in, &inner);
   if (e == cudaSuccess) e = kernel_node(outer, &n_in, (void*)ess_cg_next_kernel, dim3(1), dim3(1), a_next, &n_next);
-  if (e == cudaSuccess) e = kernel_node(inner, nullptr, kiter, dim3((unsigned)blocks), dim3(threads), a_loop, &n_iter);
+  // after the first iterations few chains are left: one block per SM keeps the launches short
+  const int64_t iter_blocks = std::min<int64_t>(blocks, sms);
+  if (e == cudaSuccess) e = kernel_node(inner, nullptr, kiter, dim3((unsigned)iter_blocks), dim3(threads), a_loop, &n_iter);
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   return e;

@@ -152,20 +152,24 @@ __device__ __forceinline__ void group_sum_n(T (&v)[N], unsigned mask = 0xfffffff
 
 
 // ---- bounded grid barrier (cooperative launches only) ----------------------------------------
-// Counting barrier.  `count` holds the arrivals of the current launch (zeroed by the host before
-// every launch); with n = blocks (+ missing) per barrier, the arrival that sees count = old
-// belongs to barrier k = old / n, which completes when count reaches (k + 1) n.  Thread 0 of each
-// block releases the block's writes (fence), arrives with one atomic add and polls the count
-// with acquire loads; no block resets or bumps anything, so the last arrival completes the
-// barrier for everyone at once.  Every wait is bounded: after spin_limit polls (default
-// kBarrierSpinLimit) the block records ERR_BARRIER_TIMEOUT and returns false, a block that sees
-// the bit set by another gives up at once, and a block that finds it set before arriving leaves
-// without arriving; callers then leave the kernel.
+// Two-level counting barrier.  Blocks arrive on one of kBarrierGroups counters (block b on
+// counter b mod kBarrierGroups, each on its own 128-byte line), so at most ~blocks / 16 atomics
+// queue on any one address; the last block of a group to arrive at a barrier then arrives on the
+// top counter, which every block polls with acquire loads.  Counts only grow within a launch
+// (the host zeroes kGridBarrierBytes before every launch): with n_g blocks in a group, the arrival
+// that sees its group counter at old belongs to barrier k = old / n_g, and barrier k completes
+// when the top counter reaches (k + 1) (groups + missing).  Every wait is bounded: after
+// spin_limit polls (default kBarrierSpinLimit) the block records ERR_BARRIER_TIMEOUT and returns
+// false, a block that sees the bit set by another gives up at once, and a block that finds it set
+// before arriving leaves without arriving; callers then leave the kernel.
+constexpr int kBarrierGroups = 16;
+constexpr size_t kGridBarrierBytes = (kBarrierGroups + 1) * 128;
+
 struct GridBarrier {
-  unsigned* count;
+  unsigned* count;  // kGridBarrierBytes: group counters at 32-word strides, then the top counter
   unsigned spin_limit = kBarrierSpinLimit;  // polls before a wait gives up
-  unsigned missing = 0;  // test hook: arrivals every wait expects beyond the grid's blocks (0 in
-                         // production); with missing > 0 no barrier completes and every wait runs out
+  unsigned missing = 0;  // test hook: top-level arrivals every wait expects beyond the grid's
+                         // groups (0 in production); with missing > 0 every wait runs out
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -182,12 +186,22 @@ __device__ __forceinline__ bool grid_sync(GridBarrier b, int* err) {
     if (*(volatile int*)err & ERR_BARRIER_TIMEOUT) {
       ok = 0;  // a wait of this run already gave up: leave without arriving
     } else {
-      const unsigned n = gridDim.x * gridDim.y * gridDim.z + b.missing;
+      const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+      const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+      const unsigned groups = nb < (unsigned)kBarrierGroups ? nb : (unsigned)kBarrierGroups;
+      const unsigned g = bid % groups;
+      const unsigned ng = nb / groups + (g < nb % groups ? 1u : 0u);  // blocks of group g
+      unsigned* top = b.count + kBarrierGroups * 32;
       __threadfence();  // the block's writes (ordered before thread 0 by the block barrier) first
-      const unsigned old = atomicAdd(b.count, 1u);
-      const unsigned target = (old / n + 1) * n;
+      const unsigned old = atomicAdd(b.count + 32 * g, 1u);
+      const unsigned k = old / ng;
+      if (old % ng == ng - 1) {  // the group's last arrival at barrier k
+        __threadfence();
+        atomicAdd(top, 1u);
+      }
+      const unsigned target = (k + 1) * (groups + b.missing);
       unsigned spins = 0;
-      while ((int)(ld_acquire_gpu(b.count) - target) < 0) {
+      while ((int)(ld_acquire_gpu(top) - target) < 0) {
         if (++spins > b.spin_limit || (*(volatile int*)err & ERR_BARRIER_TIMEOUT)) {
           atomicOr(err, ERR_BARRIER_TIMEOUT);
           ok = 0;

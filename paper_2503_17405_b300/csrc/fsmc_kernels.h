@@ -47,13 +47,6 @@ struct EssView : ChainsView<T> {
   // Null: the generator walks (chain block, ring offset) tiles instead.
   long long* col_base = nullptr;
   int2* colmap = nullptr;
-  // Persistent FSM schedule (null: one thread block per chain group): resident chain groups take
-  // work items (chain, segment of the launch's states) from the counter `work`, segment-major;
-  // seg_done[c] counts the segments chain c has finished in this launch.  Both are zeroed
-  // before every launch.
-  unsigned long long* work = nullptr;
-  int* seg_done = nullptr;
-  int nseg = 0;
 };
 
 template <typename T>

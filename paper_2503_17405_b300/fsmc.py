@@ -46,7 +46,7 @@ class Tuning(ctypes.Structure):
                 ("profile_kernels", ctypes.c_int), ("generator", ctypes.c_int),
                 ("pipelined", ctypes.c_int), ("step_form", ctypes.c_int),
                 ("barrier_spin_limit", ctypes.c_int), ("barrier_test_missing", ctypes.c_int),
-                ("sync_form", ctypes.c_int), ("fsm_schedule", ctypes.c_int)]
+                ("sync_form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
