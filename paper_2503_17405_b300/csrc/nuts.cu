@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(256) nuts_sync_kernel(NutsView<T> v, int t_beg
     __syncthreads();
     const int slot = iter % 3;
     if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
-    if (!grid_sync(bar, v.err)) return false;
+    if (!grid_sync<kBarFlag>(bar, v.err)) return false;
     total = *(volatile unsigned*)&active_cnt[slot];
     if (leader) active_cnt[(iter + 2) % 3] = 0;
     ++iter;
