@@ -368,11 +368,12 @@ static void default_tuning(fsmc_job* j) {
     // cost (the L image's copy into every CTA, tensor-memory set-up, pipeline fill and drain)
     // and each FSM launch a tail, so fewer, larger rounds are faster (16384 chains, d = 256:
     // 51.2 ms per job at 64 states per launch and 32 ring slots, 47.5 at 192 / 64, 46.6 at
-    // 384 / 128).  The ring grows with them (m x 128 x d x 4 bytes, 2.1 GB at 16384 x 256).
-    // Smaller jobs keep short rounds, which also bound a serving round's length.
+    // 384 / 128, 44.3 at 512 / 256 with the current step).  The ring grows with them
+    // (m x 256 x d x 4 bytes, 4.3 GB at 16384 x 256).  Smaller jobs keep short rounds, which
+    // also bound a serving round's length.
     const bool long_rounds = tu.generator == 2 && j->m >= 4096;
-    if (!tu.steps_per_launch) tu.steps_per_launch = long_rounds ? 384 : 64;
-    if (!tu.ring_slots) tu.ring_slots = long_rounds ? 128 : 32;
+    if (!tu.steps_per_launch) tu.steps_per_launch = long_rounds ? 512 : 64;
+    if (!tu.ring_slots) tu.ring_slots = long_rounds ? 256 : 32;
     if (!tu.threads_per_block) tu.threads_per_block = 256;
     if (!tu.pipelined) tu.pipelined = 1;
     if (!tu.sync_form) tu.sync_form = 2;
