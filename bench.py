@@ -35,9 +35,9 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 # ncu --set full of one FSM-step launch of the headline workload's kernel (ESS-GP, d = 256, 32 lanes
 # per chain) on a small case; the summary and its command are in profiles/
-ESS_GP_STEP_NCU = {"chains": 4096, "states": 384, "dram_bytes": 304.6e6 + 255.5e6, "issue_active": 0.740,
-                   "warp_instructions_per_state": 219.6e6 / (4096 * 384),
-                   "source": "profiles/ess_gp_d256_m4096_n400_kernels.md (ncu --set full, 4096 chains x 384 states)"}
+ESS_GP_STEP_NCU = {"chains": 4096, "states": 512, "dram_bytes": 402.5e6 + 354.0e6, "issue_active": 0.731,
+                   "warp_instructions_per_state": 268.5e6 / (4096 * 512),
+                   "source": "profiles/ess_gp_d256_m4096_n400_kernels.md (ncu --set full, 4096 chains x 512 states)"}
 
 
 def _peaks():
@@ -468,13 +468,13 @@ def run_ours(args, rank, world):
         if cfg["algo"] == "ess" and w["kind"] == "gp_logit" and d == 256 and tun.get("lanes_per_chain") == 32:
             prof = ESS_GP_STEP_NCU
             # DRAM bytes of one FSM-step launch in the ncu capture, scaled by chains and states per launch
-            traffic = prof["dram_bytes"] * (m / prof["chains"]) * (tun.get("steps_per_launch", 384) / prof["states"])
+            traffic = prof["dram_bytes"] * (m / prof["chains"]) * (tun.get("steps_per_launch", prof["states"]) / prof["states"])
             traffic_src = ("bytes per launch: ncu capture on %d chains x %d states, scaled by chains and "
                            "states per launch" % (prof["chains"], prof["states"]))
             # instruction issue: a chain is one warp, so a state costs warp_instructions_per_state issue
             # slots of one of the 4 x 148 schedulers
-            clk = (clk_mhz or SM_MAX_MHZ) * 1e6
-            floor_ms = steps_total * prof["warp_instructions_per_state"] / (4 * SM_COUNT * clk) * 1e3
+            clk_hz = (clk_mhz or SM_MAX_MHZ) * 1e6
+            floor_ms = steps_total * prof["warp_instructions_per_state"] / (4 * SM_COUNT * clk_hz) * 1e3
             issue = {"issue_active": prof["issue_active"], "warp_instructions_per_state": prof["warp_instructions_per_state"],
                      "issue_floor_ms_per_step": floor_ms / args.steps,
                      "kernel_ms_per_step": kms_own[1] / args.steps,
