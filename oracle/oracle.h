@@ -14,8 +14,10 @@
 //                     funnel closed-form marginals
 //   nuts              pinned: harmonic-oscillator leapfrog closed form,
 //                     reversibility, Gaussian moments
-//   nuts on logistic regression: parity unpinned beyond the above (no closed
-//                     form for that posterior)
+//   nuts on logistic regression: no closed form; pinned by self-normalised
+//                     importance sampling of the same posterior expectations
+//   decision margins  pinned: a one-stage DR transition's margin rebuilt from the
+//                     oracle's own random numbers and density
 #pragma once
 #include <cstdint>
 #include <cstddef>

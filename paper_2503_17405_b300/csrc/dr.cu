@@ -439,6 +439,313 @@ __global__ void dr_init_kernel(DrView<T> v) {
   v.lp[c] = lp;
 }
 
+// ---- a chain per warp (32 < d <= 1024; the benchmark spec's layout for wider log-densities) -------------
+// Lane l holds coordinates k = e 32 + l (e < E) of x, y1, y2 and the proposal; every sum over
+// coordinates (the log density's, the proposal densities' squared distances) is a warp sum, and
+// the chain's scalars (log pi values, the kept ratio terms, the stage) are the same in every lane.
+// The random numbers are those of the chain-per-thread step: coordinate k's normal is element
+// k mod 4 of Philox block floor(k / 4) of the stage, and each lane draws the Box-Muller pair that
+// holds its coordinate.  Same stages, acceptance formulas and kept terms as above; the 4-state
+// ablation form is chain-per-thread only.
+template <typename T, int E>
+__device__ __forceinline__ void drw_draw(const DrView<T>& v, const Key& key, int t, int k, const T (&c)[E],
+                                         T (&y)[E], int lane) {
+  const int d = v.tg.d;
+  const int D = (d + 3) / 4;
+  const uint32_t base = (uint32_t)(k * (D + 1));
+  const T sg = v.symmetric ? v.sig[0] : v.sig[k];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int kk = e * 32 + lane;
+    y[e] = T(0);
+    if (kk < d) {
+      const P4 r = key.block((uint32_t)t, 0, base + (uint32_t)(kk >> 2));
+      T z0, z1;
+      if ((kk & 3) < 2) Conv<T>::bm(r.w0, r.w1, z0, z1);
+      else Conv<T>::bm(r.w2, r.w3, z0, z1);
+      y[e] = fma(sg, (kk & 1) ? z1 : z0, c[e]);
+    }
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ T drw_eval(const DrView<T>& v, const T (&y)[E], int lane, int& err) {
+  T lpy = warp_logp<T, E>(v.tg, y, lane);
+  if (!(lpy == lpy)) { lpy = neg_inf<T>(); err |= ERR_NONFINITE; }
+  return lpy;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ T drw_sqdist(const T (&a)[E], const T (&b)[E], int d, int lane) {
+  T acc = T(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (e * 32 + lane < d) { const T r = b[e] - a[e]; acc = fma(r, r, acc); }
+  return group_sum<32>(acc);
+}
+
+template <typename T, int E>
+__device__ __forceinline__ T drw_ratio(const DrView<T>& v, int k, const T (&x)[E], T lp, const T (&y1)[E], T lp1,
+                                       const T (&y2)[E], T lp2, const T (&y)[E], T lpy, const DrCache<T>& cc,
+                                       int lane) {
+  const int d = v.tg.d;
+  if (k == 0) return la1(lp, lpy);
+  const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]);
+  if (k == 1) {
+    const T num = lpy + i1 * drw_sqdist(y, y1, d, lane) + l1m(la1(lpy, lp1));
+    const T den = lp + i1 * drw_sqdist(x, y1, d, lane) + cc.a1;
+    if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
+    return fmin(T(0), num - den);
+  }
+  const T i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
+  const T q1_y3_y2 = i1 * drw_sqdist(y, y2, d, lane);
+  const T a1_32 = l1m(la1(lpy, lp2));
+  const T n2 = lp1 + cc.q1y1y2 + cc.a1y1y2;
+  const T d2 = lpy + q1_y3_y2 + a1_32;
+  const T a2_321 = (n2 == neg_inf<T>() || d2 == neg_inf<T>()) ? neg_inf<T>() : fmin(T(0), n2 - d2);
+  const T num = lpy + q1_y3_y2 + i2 * drw_sqdist(y, y1, d, lane) + a1_32 + l1m(a2_321);
+  const T den = lp + cc.q1xy1 + cc.q2xy2 + cc.a1 + cc.a2;
+  if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
+  return fmin(T(0), num - den);
+}
+
+template <typename T, int E>
+__device__ __forceinline__ bool drw_decide(const DrView<T>& v, const Key& key, int t, int k, T la, T (&x)[E],
+                                           T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, const T (&y)[E],
+                                           T lpy, DrCache<T>& cc, int lane) {
+  const int D = (v.tg.d + 3) / 4;
+  const P4 r = key.block((uint32_t)t, 0, (uint32_t)(k * (D + 1) + D));
+  if (Conv<T>::log_u(r.w0, r.w1) < la) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = y[e];
+    lp = lpy;
+    return true;
+  }
+  if (k + 1 >= v.n_stages) return true;
+  const int d = v.tg.d;
+  if (k == 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) y1[e] = y[e];
+    lp1 = lpy;
+    cc.a1 = l1m(la);
+  } else {
+    const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]), i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
+    cc.q1xy1 = i1 * drw_sqdist(x, y1, d, lane);
+    cc.q1y1y2 = i1 * drw_sqdist(y, y1, d, lane);
+    cc.a2 = l1m(la);
+    cc.a1y1y2 = l1m(la1(lp1, lpy));
+    cc.q2xy2 = i2 * drw_sqdist(x, y, d, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) y2[e] = y[e];
+    lp2 = lpy;
+  }
+  return false;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ bool drw_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E], T& lp,
+                                         T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, DrCache<T>& cc, int lane, int& err) {
+  T y[E];
+  if (v.symmetric) {  // y1 / lp1 hold the centre and pi*
+    if (k == 0) sdr_begin<T, E>(x, y1, lp1);
+    drw_draw<T, E>(v, key, t, k, y1, y, lane);
+    const T lpy = drw_eval<T, E>(v, y, lane, err);
+    return sdr_decide<T, E>(v, key, t, k, sdr_log_alpha<T>(lp, lp1, lpy), x, lp, y1, lp1, y, lpy);
+  }
+  drw_draw<T, E>(v, key, t, k, x, y, lane);
+  const T lpy = drw_eval<T, E>(v, y, lane, err);
+  const T la = drw_ratio<T, E>(v, k, x, lp, y1, lp1, y2, lp2, y, lpy, cc, lane);
+  return drw_decide<T, E>(v, key, t, k, la, x, lp, y1, lp1, y2, lp2, y, lpy, cc, lane);
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void drw_load(const DrView<T>& v, int64_t c, T (&x)[E], T (&y1)[E], T (&y2)[E],
+                                         int lane) {
+  const int d = v.tg.d;
+  const size_t md = (size_t)v.m * d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * 32 + lane;
+    x[e] = k < d ? v.x[(size_t)c * d + k] : T(0);
+    y1[e] = k < d ? v.y[(size_t)c * d + k] : T(0);
+    y2[e] = k < d ? v.y[md + (size_t)c * d + k] : T(0);
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void drw_store(const DrView<T>& v, int64_t c, const T (&x)[E], const T (&y1)[E],
+                                          const T (&y2)[E], int pending, int lane) {
+  const int d = v.tg.d;
+  const size_t md = (size_t)v.m * d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * 32 + lane;
+    if (k >= d) continue;
+    v.x[(size_t)c * d + k] = x[e];
+    if (pending >= 1) v.y[(size_t)c * d + k] = y1[e];
+    if (pending >= 2) v.y[md + (size_t)c * d + k] = y2[e];
+  }
+}
+
+// FSM kernel, a chain per warp, condensed step (one PROPOSE state per FSM step)
+template <typename T, int E>
+__global__ void __launch_bounds__(128) dr_fsm_warp_kernel(DrView<T> v, int budget) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < v.m; c += nwarps) {
+    T x[E], y1[E], y2[E];
+    drw_load<T, E>(v, c, x, y1, y2, lane);
+    T lp = v.lp[c], lp1 = v.lpy[c], lp2 = v.lpy[v.m + c];
+    DrCache<T> cc = dr_cache_load<T>(v, c);
+    int t = v.t[c], k = v.k[c];
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    int err = 0, steps = 0;
+    for (int b = 0; b < budget && t < v.n; ++b) {
+      ++steps;
+      if (drw_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, lane, err)) {
+        warp_chain_emit<T, E>(v, v.tg.d, c, t, x, lane);
+        if (lane == 0) v.counts[(size_t)c * v.n + t] = k + 1;
+        ++t;
+        k = 0;
+        if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
+      } else {
+        ++k;
+      }
+    }
+    drw_store<T, E>(v, c, x, y1, y2, k, lane);
+    if (lane == 0) {
+      v.lp[c] = lp; v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
+      if (k) dr_cache_store<T>(v, c, cc);
+      v.t[c] = t; v.k[c] = k;
+      v.steps[c] += steps;
+      if (err) atomicOr(v.err, err);
+    }
+  }
+}
+
+// Synchronised kernel (Alg. 6), a chain per warp: as dr_sync_kernel.
+template <typename T, int E>
+__global__ void __launch_bounds__(128) dr_sync_warp_kernel(DrView<T> v, int t_begin, int t_end,
+                                                           GridBarrier bar, unsigned* active_cnt,
+                                                           unsigned long long* iterations) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t c_first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  __shared__ unsigned blk_active;
+  int iter = 0, err = 0;
+  for (int t = t_begin; t < t_end; ++t) {
+    for (int k = 0; k < v.n_stages; ++k) {
+      if (threadIdx.x == 0) blk_active = 0;
+      __syncthreads();
+      unsigned mine = 0;
+      for (int64_t c = c_first; c < v.m; c += nwarps) {
+        if (v.k[c] != k) continue;  // masked: finished this sample at an earlier stage
+        T x[E], y1[E], y2[E];
+        drw_load<T, E>(v, c, x, y1, y2, lane);
+        T lp = v.lp[c], lp1 = v.lpy[c], lp2 = v.lpy[v.m + c];
+        DrCache<T> cc = dr_cache_load<T>(v, c);
+        const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+        const bool done = drw_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, lane, err);
+        __syncwarp();  // every lane has read the chain's state before lane 0 rewrites it
+        if (done) {
+          warp_chain_emit<T, E>(v, v.tg.d, c, t, x, lane);
+          drw_store<T, E>(v, c, x, y1, y2, 0, lane);
+          if (lane == 0) {
+            v.steps[c] += 1;
+            v.counts[(size_t)c * v.n + t] = k + 1;
+            v.lp[c] = lp;
+            v.k[c] = v.n_stages;  // done with sample t
+            v.t[c] = t + 1;
+            if (t + 1 == v.n) atomicAdd(v.chains_done, 1);
+          }
+        } else {
+          drw_store<T, E>(v, c, x, y1, y2, k + 1, lane);
+          if (lane == 0) {
+            v.steps[c] += 1;
+            v.lpy[c] = lp1; v.lpy[v.m + c] = lp2;
+            dr_cache_store<T>(v, c, cc);
+            v.k[c] = k + 1;
+          }
+          mine = 1;
+        }
+      }
+      if (mine && lane == 0) atomicAdd(&blk_active, 1u);
+      __syncthreads();
+      const int slot = iter % 3;
+      if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+      if (!grid_sync(bar, v.err)) return;
+      const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+      if (leader) {
+        active_cnt[(iter + 2) % 3] = 0;
+        *iterations += 1;
+      }
+      ++iter;
+      if (total == 0) break;
+    }
+    __syncwarp();
+    for (int64_t c = c_first; c < v.m; c += nwarps)
+      if (lane == 0) v.k[c] = 0;
+    __syncwarp();  // the reset is visible to every lane before the next sample's first stage
+  }
+  if (err && lane == 0) atomicOr(v.err, err);
+}
+
+template <typename T, int E>
+__global__ void dr_init_warp_kernel(DrView<T> v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= v.m) return;
+  T x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) x[e] = e * 32 + lane < v.tg.d ? v.x[(size_t)c * v.tg.d + e * 32 + lane] : T(0);
+  T lp = warp_logp<T, E>(v.tg, x, lane);
+  if (!(lp == lp)) { lp = neg_inf<T>(); if (lane == 0) atomicOr(v.err, ERR_NONFINITE); }
+  if (lane == 0) v.lp[c] = lp;
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename T, int E>
+static cudaError_t fsm_warp_launch(const DrView<T>& v, int budget, int threads, cudaStream_t st) {
+  const int64_t blocks = (v.m * 32 + threads - 1) / threads;
+  dr_fsm_warp_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
+static cudaError_t sync_warp_launch(const DrView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                                    unsigned long long* iters, int threads, cudaStream_t st) {
+  auto kern = dr_sync_warp_kernel<T, E>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (v.m * 32 + threads - 1) / threads);
+  if (blocks < 1) blocks = 1;
+  DrView<T> vv = v;
+  void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+}
+
+template <typename T, int E>
+static cudaError_t init_warp_launch(const DrView<T>& v, cudaStream_t st) {
+  dr_init_warp_kernel<T, E><<<(unsigned)((v.m * 32 + 127) / 128), 128, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+#define FSMC_DR_WARP_DISPATCH(FN, ...)                       \
+  do {                                                       \
+    const int d = v.tg.d;                                    \
+    if (d <= 64) return FN<T, 2>(__VA_ARGS__);               \
+    if (d <= 128) return FN<T, 4>(__VA_ARGS__);              \
+    if (d <= 256) return FN<T, 8>(__VA_ARGS__);              \
+    if (d <= 512) return FN<T, 16>(__VA_ARGS__);             \
+    if (d <= 1024) return FN<T, 32>(__VA_ARGS__);            \
+    return cudaErrorInvalidValue;                            \
+  } while (0)
+
 // ------------------------------------------------------------------------------------------
 template <typename T, int E>
 static cudaError_t fsm_launch(const DrView<T>& v, int budget, int threads, cudaStream_t st) {
@@ -492,15 +799,18 @@ static cudaError_t init_launch(const DrView<T>& v, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_dr_fsm(const DrView<T>& v, int budget, int threads, cudaStream_t st) {
+  if (v.lanes == 32) FSMC_DR_WARP_DISPATCH(fsm_warp_launch, v, budget, threads, st);
   FSMC_DR_DISPATCH(fsm_launch, v, budget, threads, st);
 }
 template <typename T>
 cudaError_t launch_dr_sync(const DrView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
                            unsigned long long* iters, int threads, cudaStream_t st) {
+  if (v.lanes == 32) FSMC_DR_WARP_DISPATCH(sync_warp_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
   FSMC_DR_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
 }
 template <typename T>
 cudaError_t launch_dr_init(const DrView<T>& v, cudaStream_t st) {
+  if (v.lanes == 32) FSMC_DR_WARP_DISPATCH(init_warp_launch, v, st);
   FSMC_DR_DISPATCH(init_launch, v, st);
 }
 

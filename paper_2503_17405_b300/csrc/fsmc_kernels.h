@@ -61,6 +61,7 @@ struct DrView : ChainsView<T> {
   T* lpy;                // [10][m] log pi(y1), log pi(y2); the current proposal's log pi and ratio;
                          // the later stages' kept ratio terms (DrCache in dr.cu)
   int* k;                // [m] next stage to try
+  int lanes = 1;         // 1: a chain per thread (d <= 32); 32: a chain per warp (d <= 1024)
 };
 
 // ESS on a target whose likelihood is one dense linear-algebra problem per evaluation (GP

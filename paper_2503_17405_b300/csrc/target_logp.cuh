@@ -70,6 +70,81 @@ __device__ __forceinline__ T full_logp(const TargetView<T>& tg, const T (&y)[E])
   return neg_inf<T>();
 }
 
+// log pi with a chain per warp: lane l holds coordinates k = e 32 + l (e < E, k < d) of y; every
+// sum over coordinates is a warp sum, and every lane returns the same value.
+template <typename T, int E>
+__device__ __forceinline__ T warp_logp(const TargetView<T>& tg, const T (&y)[E], int lane) {
+  const int d = tg.d;
+  if (tg.kind == TGT_FUNNEL) {
+    T ss = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = e * 32 + lane;
+      if (k >= 1 && k < d) ss = fma(y[e], y[e], ss);
+    }
+    ss = group_sum<32>(ss);
+    const T v = __shfl_sync(0xffffffffu, y[0], 0);
+    const T ev = sizeof(T) == 4 ? (T)expf(-(float)v) : (T)exp(-(double)v);
+    return -v * v / T(18) - T(d - 1) * v / T(2) - T(0.5) * ev * ss;
+  } else if (tg.kind == TGT_GAUSS_DIAG) {
+    T acc = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = e * 32 + lane;
+      if (k < d) { const T z = (y[e] - tg.vec[k]) / tg.vec2[k]; acc = fma(z, z, acc); }
+    }
+    return -T(0.5) * group_sum<32>(acc);
+  } else if (tg.kind == TGT_MOG) {
+    const T inv_d = T(1) / T(d);
+    T lmax = neg_inf<T>(), wsum = T(0);
+    for (int kk = 0; kk < tg.n_data; ++kk) {
+      const T* mk = tg.X + (size_t)kk * d;
+      T sk = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = e * 32 + lane;
+        if (k < d) sk += y[e] - mk[k];
+      }
+      sk = group_sum<32>(sk);
+      const T mean = sk * inv_d;
+      T uu = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = e * 32 + lane;
+        if (k < d) { const T u = y[e] - mk[k] - mean; uu = fma(u, u, uu); }
+      }
+      uu = group_sum<32>(uu);
+      const T lk = tg.vec[kk] - T(0.5) * fma(sk * mean, tg.c_par, uu * tg.c_perp);
+      if (lk > lmax) {
+        wsum = wsum * (sizeof(T) == 4 ? (T)expf((float)(lmax - lk)) : (T)exp((double)(lmax - lk))) + T(1);
+        lmax = lk;
+      } else {
+        wsum += sizeof(T) == 4 ? (T)expf((float)(lk - lmax)) : (T)exp((double)(lk - lmax));
+      }
+    }
+    return lmax + (sizeof(T) == 4 ? (T)logf((float)wsum) : (T)log((double)wsum));
+  } else if (tg.kind == TGT_LOGREG) {
+    T acc = T(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e * 32 + lane < d) acc = fma(y[e], y[e], acc);
+    acc = -T(0.5) * group_sum<32>(acc);
+    for (int i = 0; i < tg.n_data; ++i) {
+      const T* row = tg.X + (size_t)i * d;
+      T eta = T(0);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = e * 32 + lane;
+        if (k < d) eta = fma(row[k], y[e], eta);
+      }
+      eta = group_sum<32>(eta);
+      acc += tg.vec[i] * eta - softplus<T>(eta);
+    }
+    return acc;
+  }
+  return neg_inf<T>();
+}
+
 // One compensated (Kahan) step for the sum and the sum of squares of a coordinate; the square
 // is rounded on its own (no contraction into the subtraction), so every caller gets the same bits.
 template <typename T>
@@ -136,6 +211,25 @@ __device__ __forceinline__ void chain_emit(const ChainsView<T>& v, int d, int64_
     for (int e = 0; e < E; ++e) {
       if (e >= d) continue;
       const size_t o = (size_t)c * d + e, st = v.mom_stride;
+      T* mo = v.mom;
+      kahan_moments<T>(mo[o], mo[o + st], mo[o + 2 * st], mo[o + 3 * st], x[e]);
+    }
+  }
+}
+
+// A finished sample with a chain per warp (lane l: coordinates e 32 + l): stored, or folded into
+// the Kahan sums of x and x^2 in device memory.
+template <typename T, int E>
+__device__ __forceinline__ void warp_chain_emit(const ChainsView<T>& v, int d, int64_t c, int t, const T (&x)[E],
+                                                int lane) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * 32 + lane;
+    if (k >= d) continue;
+    if (v.out) {
+      v.out[((size_t)c * v.n + t) * d + k] = x[e];
+    } else {
+      const size_t o = (size_t)c * d + k, st = v.mom_stride;
       T* mo = v.mom;
       kahan_moments<T>(mo[o], mo[o + st], mo[o + 2 * st], mo[o + 3 * st], x[e]);
     }

@@ -180,3 +180,107 @@ def test_moments_only_mode_matches_stored_samples(eng, prec, rtol):
     assert np.allclose(sx2, (xs ** 2).sum(1), rtol=rtol, atol=rtol * n)
     a.close()
     b.close()
+
+
+# ---- a chain per warp (d > 32) ------------------------------------------------------------------
+WIDE = {
+    "gauss_diag_d100": lambda: (W.gauss_diag(100), None),
+    "funnel_d50": lambda: (W.funnel(50), None),
+    "mog_d100": lambda: (W.mog(100, rho=0.5, offsets=(-3.0, 0.0, 3.0), weights=(1.0, 2.0, 1.0)), 3),
+}
+
+
+def _wide_x0(name, w, m):
+    if name.startswith("gauss_diag"):
+        return W.x0_gauss_diag_exact(w, m)
+    if name.startswith("funnel"):
+        return W.x0_funnel_exact(m, d=w["d"])
+    return W.x0_mog_exact(w, m)
+
+
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+@pytest.mark.parametrize("name", list(WIDE))
+def test_fp64_chain_per_warp_matches_oracle(eng, name, mode):
+    # d > 32 runs a chain per warp (the density's sums across the warp); FP64 reproduces the oracle
+    # to 1e-10 with identical stage counts; 100 chains leave the last block ragged
+    w, n_data = WIDE[name]()
+    n_data = n_data or 0
+    m, n = 100, 120
+    x0 = _wide_x0(name, w, m)
+    tg = eng.target(w["kind"], w["d"], w["params"] if w["params"].size else None, n_data=n_data)
+    job = eng.job(tg, "dr", m, n, x0=x0, seed=2, prec="fp64", dr=DR, tuning={"steps_per_launch": 40})
+    assert job.tuning()["lanes_per_chain"] == 32
+    job.run(mode)
+    ref = O.run("dr", w["kind"], w["params"], x0, n, seed=2, n_data=n_data, algo_params=DR_ARGS)
+    counts, _, steps = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    assert counts.max() == 3  # every stage is exercised
+    if mode == "fsm":
+        assert np.array_equal(steps, counts.sum(1))
+    else:
+        assert job.stats()["sync_iterations"] == int(counts.max(0).sum())
+    job.close()
+
+
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+def test_fp64_symmetric_dr_chain_per_warp_matches_oracle(eng, mode):
+    w = W.gauss_diag(100)
+    m, n = 64, 80
+    x0 = W.x0_gauss_diag_exact(w, m)
+    sdr = {"n_stages": 30, "scale0": 0.05, "factor": 1.0, "symmetric": 1}
+    tg = eng.target("gauss_diag", 100, w["params"])
+    job = eng.job(tg, "dr", m, n, x0=x0, seed=6, prec="fp64", dr=sdr)
+    job.run(mode)
+    ref = O.run("sdr", "gauss_diag", w["params"], x0, n, seed=6, algo_params=[30, 0.05])
+    counts, _, _ = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    assert counts.max() > 2
+    job.close()
+
+
+def test_fp32_chain_per_warp_fsm_equals_sync_and_follows_oracle(eng):
+    w = W.gauss_diag(64)
+    m, n = 256, 300
+    x0 = W.x0_gauss_diag_exact(w, m)
+    tg = eng.target("gauss_diag", 64, w["params"])
+    a = eng.job(tg, "dr", m, n, x0=x0, seed=3, prec="fp32", dr=DR)
+    b = eng.job(tg, "dr", m, n, x0=x0, seed=3, prec="fp32", dr=DR)
+    a.run("fsm")
+    b.run("sync")
+    ca, cb = a.loop_counts()[0], b.loop_counts()[0]
+    assert np.array_equal(ca, cb) and np.array_equal(a.samples(), b.samples())
+    ref = O.run("dr", "gauss_diag", w["params"], x0, n, seed=3, algo_params=DR_ARGS)
+    r = compare(a.samples(), ca, ref["samples"], ref["counts"], "fp32")
+    print("fp32 DR chain per warp d=64:", r["flipped"], "flipped of", m, "max err", r["max_err"])
+    assert r["flipped"] <= FLIP_ALLOW
+    a.close()
+    b.close()
+
+
+def test_chain_per_warp_moments_only_matches_stored_samples(eng):
+    w = W.funnel(40)
+    m, n = 96, 200
+    x0 = W.x0_funnel_exact(m, d=40)
+    tg = eng.target("funnel", 40)
+    a = eng.job(tg, "dr", m, n, x0=x0, seed=5, prec="fp64", dr=DR)
+    b = eng.job(tg, "dr", m, n, x0=x0, seed=5, prec="fp64", dr=DR, store=False)
+    a.run("fsm")
+    b.run("fsm")
+    xs = a.samples()
+    sx, sx2, nk = b.moments()
+    assert np.all(nk == n)
+    assert np.allclose(sx, xs.sum(1), rtol=1e-12, atol=1e-10)
+    assert np.allclose(sx2, (xs ** 2).sum(1), rtol=1e-12, atol=1e-10)
+    a.close()
+    b.close()
+
+
+def test_chain_per_warp_shape_checks(eng):
+    from paper_2503_17405_b300 import fsmc
+    w = W.gauss_diag(40)
+    tg = eng.target("gauss_diag", 40, w["params"])
+    for bad in ({"lanes_per_chain": 1}, {"step_form": 2}, {"lanes_per_chain": 16}):
+        with pytest.raises(fsmc.FsmcError):
+            eng.job(tg, "dr", 8, 4, dr=DR, tuning=bad)
