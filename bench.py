@@ -94,6 +94,13 @@ def _make_config(name, scale):
         m, n = int(65536 * scale), 5000
         return dict(name="dr3_funnel_d10_m65536_n5000", algo="dr", w=w, m=m, n=n, prec="fp32",
                     x0=W.x0_funnel_exact(m), algo_params=[3, 1.0, 0.5])
+    if name == "dr_gauss100":
+        # 3-stage DR with a chain per warp (d > 32): N(mu, diag sigma^2) in d = 100, proposal scales
+        # 0.2, 0.1, 0.05 (stage-1 acceptance ~0.3)
+        w = W.gauss_diag(100)
+        m, n = int(16384 * scale), 1000
+        return dict(name="dr3_gauss_diag_d100_m16384_n1000", algo="dr", w=w, m=m, n=n, prec="fp32",
+                    x0=W.x0_gauss_diag_exact(w, m), algo_params=[3, 0.2, 0.5])
     if name == "dr_sym":
         # the paper's delayed-rejection toy (Sec. 7.1): symmetric DR on N(0, 1), re-centred tries of
         # sd 0.1, at most M = 100 tries per sample
@@ -457,7 +464,9 @@ def run_ours(args, rank, world):
             # logistic regression: 4 n d; mixture: (7 K + 1) d (residual, its square, the gradient)
             per = 4 * w["n_data"] * d if w["kind"] == "logreg" else (7 * w["n_data"] + 1) * d
         elif cfg["algo"] == "dr":
-            per = 40
+            # the stage's density: funnel 2 d + ~20 (its exponential and constants; ~40 at d = 10),
+            # diagonal Gaussian 3 d
+            per = 2 * d + 20 if w["kind"] == "funnel" else 3 * d
         else:
             per = 20 * d
         achieved = steps_total * per / (kms_own[1] / 1e3) / 1e12 if kms_own[1] else None
