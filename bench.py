@@ -125,6 +125,12 @@ def _make_config(name, scale):
         m, n = int(65536 * scale), 2000
         return dict(name="slice_funnel_d10_w1_m100_m65536_n2000", algo="slice", w=w, m=m, n=n, prec="fp32",
                     x0=W.x0_funnel_exact(m), algo_params=[1.0, 100])
+    if name == "slice_gauss100":
+        # the slice sampler with a chain per warp (d > 32): N(mu, diag sigma^2) in d = 100
+        w = W.gauss_diag(100)
+        m, n = int(16384 * scale), 1000
+        return dict(name="slice_gauss_diag_d100_w1_m100_m16384_n1000", algo="slice", w=w, m=m, n=n,
+                    prec="fp32", x0=W.x0_gauss_diag_exact(w, m), algo_params=[1.0, 100])
     if name == "nuts_mog":
         # Sec. 7.3: NUTS on the 100-d mixture of Gaussians with correlation 0.99, modes at
         # -10 * 1, 0, 10 * 1, identity mass, step 0.044 (acceptance statistic ~0.87), depth <= 10

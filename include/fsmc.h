@@ -126,7 +126,8 @@ typedef struct fsmc_nuts_params {
 typedef struct fsmc_tuning {
   int lanes_per_chain;   /* 1 = chain-per-thread, 8 = four chains per warp (ESS,
                             32 < d <= 256), 16 = two chains per warp (ESS, 32 < d <= 512),
-                            32 = chain-per-warp (ESS, NUTS; DR with d > 32), 0 = auto     */
+                            32 = chain-per-warp (ESS, NUTS; DR and slice with d > 32),
+                            0 = auto                                                      */
   int steps_per_launch;  /* FSM states each chain advances per launch                    */
   int ring_slots;        /* ESS: pre-generated ellipse directions kept per chain         */
   int threads_per_block; /* 32..256, multiple of 32                                      */
@@ -199,8 +200,8 @@ void fsmc_target_destroy(fsmc_target* t);
 /* ---- jobs ------------------------------------------------------------------------------
  * m = n_chains chains of `algo` on target t, n_samples samples each (Alg. 3 / Alg. 7).
  * algo_params: NULL for ESS, const fsmc_dr_params* for DR, const fsmc_nuts_params* for NUTS,
- * const fsmc_slice_params* for SLICE (NULL: w = 1, m = 100).  DR: d <= 1024 (a chain per thread
- * up to d = 32, a chain per warp above); SLICE: d <= 32.
+ * const fsmc_slice_params* for SLICE (NULL: w = 1, m = 100).  DR and SLICE: d <= 1024 (a chain per
+ * thread up to d = 32, a chain per warp above).
  * x0_host: [n_chains][d] starting points (NULL = zeros), copied to device memory before the
  * call returns (one DMA when the buffer is pinned).  seed keys the random numbers:
  * chain j, sample i, draw q use Philox4x32-10 with key (j, seed_lo) and counter

@@ -380,7 +380,7 @@ static void default_tuning(fsmc_job* j) {
   } else if (j->algo == FSMC_DR || j->algo == FSMC_SLICE) {
     // a chain per thread while its state fits a thread's registers (d <= 32), else a chain per
     // warp (DR), its density's sums taken across the warp
-    if (!tu.lanes_per_chain) tu.lanes_per_chain = (j->algo == FSMC_DR && j->d > 32) ? 32 : 1;
+    if (!tu.lanes_per_chain) tu.lanes_per_chain = j->d > 32 ? 32 : 1;
     // long launches: fewer kernel tails (funnel, 65536 chains: DR 48.8 -> 48.0 ms, slice 47.4 ->
     // 45.9 ms per job from 256 to 1024 states per launch)
     if (!tu.steps_per_launch) tu.steps_per_launch = 1024;
@@ -587,6 +587,7 @@ SliceView<T> slice_view(const fsmc_job* j) {
   v.s = v.k + 3 * j->m;
   v.nev = v.k + 4 * j->m;
   v.aux = (int*)(b + j->o_aux);
+  v.lanes = j->tun.lanes_per_chain;
   return v;
 }
 
@@ -663,7 +664,7 @@ extern "C" fsmc_status fsmc_job_create(fsmc_engine* e, fsmc_target* t, fsmc_algo
   if (algo == FSMC_DR && t->d > 1024) return fsmc_fail(FSMC_EINVAL, "DR supports d <= 1024");
   if (t->kind == FSMC_TGT_GP_REG && prec == FSMC_FP64 && t->n_data > kGpRegMaxN64)
     return fsmc_fail(FSMC_EINVAL, "FP64 GP_REG jobs support n_data <= 512");
-  if (algo == FSMC_SLICE && t->d > 32) return fsmc_fail(FSMC_EINVAL, "slice sampling supports d <= 32");
+  if (algo == FSMC_SLICE && t->d > 1024) return fsmc_fail(FSMC_EINVAL, "slice sampling supports d <= 1024");
   auto* j = new (std::nothrow) fsmc_job();
   if (!j) return fsmc_fail(FSMC_ENOMEM, "host allocation failed");
   j->e = e;
@@ -740,12 +741,10 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 8 && t.lanes_per_chain != 16 &&
       t.lanes_per_chain != 32)
     return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1, 8, 16 or 32");
-  if (j->algo == FSMC_SLICE && t.lanes_per_chain > 1)
-    return fsmc_fail(FSMC_EINVAL, "slice sampling is chain-per-thread");
-  if (j->algo == FSMC_DR && (t.lanes_per_chain == 8 || t.lanes_per_chain == 16))
-    return fsmc_fail(FSMC_EINVAL, "DR runs a chain per thread (d <= 32) or per warp");
-  if (j->algo == FSMC_DR && t.lanes_per_chain == 1 && j->d > 32)
-    return fsmc_fail(FSMC_EINVAL, "chain-per-thread DR supports d <= 32");
+  if ((j->algo == FSMC_DR || j->algo == FSMC_SLICE) && (t.lanes_per_chain == 8 || t.lanes_per_chain == 16))
+    return fsmc_fail(FSMC_EINVAL, "DR and slice sampling run a chain per thread (d <= 32) or per warp");
+  if ((j->algo == FSMC_DR || j->algo == FSMC_SLICE) && t.lanes_per_chain == 1 && j->d > 32)
+    return fsmc_fail(FSMC_EINVAL, "chain-per-thread DR and slice sampling support d <= 32");
   if (j->algo == FSMC_DR && t.step_form == 2 && (t.lanes_per_chain == 32 || j->d > 32))
     return fsmc_fail(FSMC_EINVAL, "the 4-state DR ablation form runs a chain per thread only");
   if (t.lanes_per_chain == 16 && (j->algo != FSMC_ESS || j->d <= 32 || j->d > 512))

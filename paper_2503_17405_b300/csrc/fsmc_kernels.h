@@ -96,6 +96,7 @@ struct SliceView : ChainsView<T> {
   int* s;                // [m] proposals made in the current sample
   int* nev;              // [m] log-density evaluations in the current sample
   int* aux;              // [m][n] proposals per sample
+  int lanes = 1;         // 1: a chain per thread (d <= 32); 32: a chain per warp (d <= 1024)
 };
 
 template <typename T>

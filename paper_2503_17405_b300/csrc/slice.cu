@@ -316,6 +316,282 @@ __global__ void slice_init_kernel(SliceView<T> v) {
   v.k[c] = SL_START;
 }
 
+// ---- a chain per warp (32 < d <= 1024) -----------------------------------------------------------
+// Lane l holds coordinates k = e 32 + l of x and of the direction u; the density and |z| are warp
+// sums, and the chain's scalars (threshold, interval, budgets, counts) are the same in every lane.
+// The random numbers are the chain-per-thread sampler's: coordinate k's normal is element k mod 4
+// of block floor(k / 4) (each lane draws the Box-Muller pair that holds its coordinate), the
+// threshold and V from block D, V' from block D + 1, proposal p from block D + 2 + p.
+template <typename T, int E>
+__device__ __forceinline__ void slicew_begin(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c,
+                                             int lane) {
+  const int d = v.tg.d;
+  const int D = (d + 3) / 4;
+  T ss = T(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int kk = e * 32 + lane;
+    c.u[e] = T(0);
+    if (kk < d) {
+      const P4 r = key.block((uint32_t)c.t, 0, (uint32_t)(kk >> 2));
+      T z0, z1;
+      if ((kk & 3) < 2) Conv<T>::bm(r.w0, r.w1, z0, z1);
+      else Conv<T>::bm(r.w2, r.w3, z0, z1);
+      c.u[e] = (kk & 1) ? z1 : z0;
+    }
+    ss = fma(c.u[e], c.u[e], ss);
+  }
+  const T rn = T(1) / sqrt(group_sum<32>(ss));
+#pragma unroll
+  for (int e = 0; e < E; ++e) c.u[e] *= rn;
+  const P4 b = key.block((uint32_t)c.t, 0, (uint32_t)D);
+  const P4 b1 = key.block((uint32_t)c.t, 0, (uint32_t)(D + 1));
+  c.logy = slice_threshold<T>(c.lp, Conv<T>::log_u(b.w0, b.w1));
+  c.L = -v.w * Conv<T>::u(b.w2, b.w3);
+  c.R = c.L + v.w;
+  c.J = min((int)floor(T(v.mlim) * Conv<T>::u(b1.w0, b1.w1)), v.mlim - 1);
+  c.K = v.mlim - 1 - c.J;
+  c.s = 0;
+  c.nev = 0;
+  if (c.J > 0) c.k = SL_LEFT;
+  else slice_after_left<T, E>(v, key, c);
+}
+
+template <typename T, int E>
+__device__ __forceinline__ bool slicew_step(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c, int lane,
+                                            int& err) {
+  const T th = c.k == SL_LEFT ? c.L : c.k == SL_RIGHT ? c.R : c.th;
+  T xp[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) xp[e] = fma(th, c.u[e], c.x[e]);
+  T lpp = warp_logp<T, E>(v.tg, xp, lane);
+  if (!(lpp == lpp)) { lpp = neg_inf<T>(); err |= ERR_NONFINITE; }
+  c.nev += 1;
+  const bool inside = lpp > c.logy;
+  if (c.k == SL_LEFT) {
+    if (inside) {
+      c.L -= v.w;
+      if (--c.J > 0) return false;
+    }
+    slice_after_left<T, E>(v, key, c);
+    return false;
+  }
+  if (c.k == SL_RIGHT) {
+    if (inside) {
+      c.R += v.w;
+      if (--c.K > 0) return false;
+    }
+    slice_propose<T, E>(v, key, c);
+    return false;
+  }
+  c.s += 1;
+  if (inside) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) c.x[e] = xp[e];
+    c.lp = lpp;
+    return true;
+  }
+  if (th < T(0)) c.L = th; else c.R = th;
+  if (c.s >= kMaxShrinks) {  // keep x
+    err |= ERR_SHRINK_CAP;
+    return true;
+  }
+  slice_propose<T, E>(v, key, c);
+  return false;
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void slicew_load(const SliceView<T>& v, int64_t c, SliceChain<T, E>& s, int lane) {
+  const int d = v.tg.d;
+#pragma unroll
+  for (int e = 0; e < E; ++e) s.x[e] = e * 32 + lane < d ? v.x[(size_t)c * d + e * 32 + lane] : T(0);
+  s.lp = v.lp[c];
+  s.t = v.t[c];
+  s.k = v.k[c];
+  if (s.k != SL_START && s.k != SL_DONE) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) s.u[e] = e * 32 + lane < d ? v.u[(size_t)c * d + e * 32 + lane] : T(0);
+    s.logy = v.logy[c]; s.L = v.L[c]; s.R = v.R[c]; s.th = v.th[c];
+    s.J = v.J[c]; s.K = v.K[c]; s.s = v.s[c]; s.nev = v.nev[c];
+  }
+}
+
+// every lane writes its coordinates, lane 0 the scalars (after the lanes have read them)
+template <typename T, int E>
+__device__ __forceinline__ void slicew_store(const SliceView<T>& v, int64_t c, const SliceChain<T, E>& s, int lane) {
+  const int d = v.tg.d;
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = e * 32 + lane;
+    if (k < d) {
+      v.x[(size_t)c * d + k] = s.x[e];
+      if (s.k != SL_START && s.k != SL_DONE) v.u[(size_t)c * d + k] = s.u[e];
+    }
+  }
+  if (lane == 0) {
+    v.lp[c] = s.lp;
+    v.t[c] = s.t;
+    v.k[c] = s.k;
+    if (s.k != SL_START && s.k != SL_DONE) {
+      v.logy[c] = s.logy; v.L[c] = s.L; v.R[c] = s.R; v.th[c] = s.th;
+      v.J[c] = s.J; v.K[c] = s.K; v.s[c] = s.s; v.nev[c] = s.nev;
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void slicew_finish(const SliceView<T>& v, int64_t c, SliceChain<T, E>& s, int lane) {
+  warp_chain_emit<T, E>(v, v.tg.d, c, s.t, s.x, lane);
+  if (lane == 0) {
+    v.counts[(size_t)c * v.n + s.t] = s.nev;
+    v.aux[(size_t)c * v.n + s.t] = s.s;
+  }
+  s.t += 1;
+  if (s.t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
+}
+
+// FSM kernel, a chain per warp, every chain advances `budget` evaluations.
+template <typename T, int E>
+__global__ void __launch_bounds__(128) slice_fsm_warp_kernel(SliceView<T> v, int budget) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < v.m; c += nwarps) {
+    SliceChain<T, E> s;
+    slicew_load<T, E>(v, c, s, lane);
+    if (s.t >= v.n) continue;
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    int err = 0, steps = 0;
+    if (s.k == SL_START) slicew_begin<T, E>(v, key, s, lane);
+    for (int b = 0; b < budget; ++b) {
+      ++steps;
+      if (slicew_step<T, E>(v, key, s, lane, err)) {
+        slicew_finish<T, E>(v, c, s, lane);
+        if (s.t == v.n) { s.k = SL_DONE; break; }
+        slicew_begin<T, E>(v, key, s, lane);
+      }
+    }
+    slicew_store<T, E>(v, c, s, lane);
+    if (lane == 0) {
+      v.steps[c] += steps;
+      if (err) atomicOr(v.err, err);
+    }
+  }
+}
+
+// Synchronised kernel, a chain per warp: as slice_sync_kernel.
+template <typename T, int E>
+__global__ void __launch_bounds__(128) slice_sync_warp_kernel(SliceView<T> v, int t_begin, int t_end,
+                                                              GridBarrier bar, unsigned* active_cnt,
+                                                              unsigned long long* iterations) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t c_first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  __shared__ unsigned blk_active;
+  int iter = 0, err = 0;
+  for (int t = t_begin; t < t_end; ++t) {
+    for (int64_t c = c_first; c < v.m; c += nwarps) {
+      SliceChain<T, E> s;
+      slicew_load<T, E>(v, c, s, lane);
+      const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+      slicew_begin<T, E>(v, key, s, lane);
+      slicew_store<T, E>(v, c, s, lane);
+    }
+    for (int phase = SL_LEFT; phase <= SL_PROP; ++phase) {
+      while (true) {
+        if (threadIdx.x == 0) blk_active = 0;
+        __syncthreads();
+        unsigned mine = 0;
+        for (int64_t c = c_first; c < v.m; c += nwarps) {
+          if (v.k[c] != phase) continue;  // masked: not in this loop (yet, or any more)
+          SliceChain<T, E> s;
+          slicew_load<T, E>(v, c, s, lane);
+          const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+          if (slicew_step<T, E>(v, key, s, lane, err)) {
+            slicew_finish<T, E>(v, c, s, lane);
+            s.k = SL_DONE;
+          }
+          slicew_store<T, E>(v, c, s, lane);
+          if (lane == 0) v.steps[c] += 1;
+          if (s.k == phase) mine = 1;
+        }
+        if (mine && lane == 0) atomicAdd(&blk_active, 1u);
+        __syncthreads();
+        const int slot = iter % 3;
+        if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+        if (!grid_sync(bar, v.err)) return;
+        const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+        if (leader) {
+          active_cnt[(iter + 2) % 3] = 0;
+          *iterations += 1;
+        }
+        ++iter;
+        if (total == 0) break;
+      }
+    }
+  }
+  if (err && lane == 0) atomicOr(v.err, err);
+}
+
+template <typename T, int E>
+__global__ void slice_init_warp_kernel(SliceView<T> v) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= v.m) return;
+  T x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) x[e] = e * 32 + lane < v.tg.d ? v.x[(size_t)c * v.tg.d + e * 32 + lane] : T(0);
+  T lp = warp_logp<T, E>(v.tg, x, lane);
+  if (!(lp == lp)) { lp = neg_inf<T>(); if (lane == 0) atomicOr(v.err, ERR_NONFINITE); }
+  if (lane == 0) {
+    v.lp[c] = lp;
+    v.k[c] = SL_START;
+  }
+}
+
+template <typename T, int E>
+static cudaError_t fsm_warp_launch(const SliceView<T>& v, int budget, int threads, cudaStream_t st) {
+  const int64_t blocks = (v.m * 32 + threads - 1) / threads;
+  slice_fsm_warp_kernel<T, E><<<(unsigned)blocks, threads, 0, st>>>(v, budget);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
+static cudaError_t sync_warp_launch(const SliceView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
+                                    unsigned long long* iters, int threads, cudaStream_t st) {
+  auto kern = slice_sync_warp_kernel<T, E>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (v.m * 32 + threads - 1) / threads);
+  if (blocks < 1) blocks = 1;
+  SliceView<T> vv = v;
+  void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+}
+
+template <typename T, int E>
+static cudaError_t init_warp_launch(const SliceView<T>& v, cudaStream_t st) {
+  slice_init_warp_kernel<T, E><<<(unsigned)((v.m * 32 + 127) / 128), 128, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+#define FSMC_SLICE_WARP_DISPATCH(FN, ...)                    \
+  do {                                                       \
+    const int d = v.tg.d;                                    \
+    if (d <= 64) return FN<T, 2>(__VA_ARGS__);               \
+    if (d <= 128) return FN<T, 4>(__VA_ARGS__);              \
+    if (d <= 256) return FN<T, 8>(__VA_ARGS__);              \
+    if (d <= 512) return FN<T, 16>(__VA_ARGS__);             \
+    if (d <= 1024) return FN<T, 32>(__VA_ARGS__);            \
+    return cudaErrorInvalidValue;                            \
+  } while (0)
+
 // ------------------------------------------------------------------------------------------
 template <typename T, int E>
 static cudaError_t fsm_launch(const SliceView<T>& v, int budget, int threads, cudaStream_t st) {
@@ -363,15 +639,18 @@ static cudaError_t init_launch(const SliceView<T>& v, cudaStream_t st) {
 
 template <typename T>
 cudaError_t launch_slice_fsm(const SliceView<T>& v, int budget, int threads, cudaStream_t st) {
+  if (v.lanes == 32) FSMC_SLICE_WARP_DISPATCH(fsm_warp_launch, v, budget, threads, st);
   FSMC_SLICE_DISPATCH(fsm_launch, v, budget, threads, st);
 }
 template <typename T>
 cudaError_t launch_slice_sync(const SliceView<T>& v, int t0, int t1, GridBarrier bar, unsigned* active_cnt,
                               unsigned long long* iters, int threads, cudaStream_t st) {
+  if (v.lanes == 32) FSMC_SLICE_WARP_DISPATCH(sync_warp_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
   FSMC_SLICE_DISPATCH(sync_launch, v, t0, t1, bar, active_cnt, iters, threads, st);
 }
 template <typename T>
 cudaError_t launch_slice_init(const SliceView<T>& v, cudaStream_t st) {
+  if (v.lanes == 32) FSMC_SLICE_WARP_DISPATCH(init_warp_launch, v, st);
   FSMC_SLICE_DISPATCH(init_launch, v, st);
 }
 

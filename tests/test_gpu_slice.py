@@ -110,7 +110,8 @@ def test_argument_checks(eng):
     wide = W.gauss_diag(40)
     tw = eng.target("gauss_diag", 40, wide["params"])
     with pytest.raises(fsmc.FsmcError):
-        eng.job(tw, "slice", 8, 4)
+        eng.job(tw, "slice", 8, 4, tuning={"lanes_per_chain": 1})   # a chain per thread: d <= 32
+    assert eng.job(tw, "slice", 8, 4).tuning()["lanes_per_chain"] == 32
 
 
 @pytest.mark.parametrize("prec,rtol", [("fp64", 1e-12), ("fp32", 2e-5)])
@@ -132,3 +133,52 @@ def test_moments_only_mode_matches_stored_samples(eng, prec, rtol):
     assert np.allclose(sx2, (xs ** 2).sum(1), rtol=rtol, atol=rtol * n)
     for j in jobs:
         j.close()
+
+
+# ---- a chain per warp (d > 32) ------------------------------------------------------------------
+def _wide_cases():
+    g = W.gauss_diag(100)
+    f = W.funnel(50)
+    mg = W.mog(64, rho=0.5, offsets=(-3.0, 3.0))
+    return {
+        "gauss_diag_d100": (g, 0, W.x0_gauss_diag_exact(g, 96)),
+        "funnel_d50": (f, 0, W.x0_funnel_exact(96, d=50)),
+        "mog_d64": (mg, 2, W.x0_mog_exact(mg, 96)),
+    }
+
+
+@pytest.mark.parametrize("mode", ["fsm", "sync"])
+@pytest.mark.parametrize("name", ["gauss_diag_d100", "funnel_d50", "mog_d64"])
+def test_fp64_chain_per_warp_matches_oracle(eng, name, mode):
+    w, n_data, x0 = _wide_cases()[name]
+    m, n = x0.shape[0], 60
+    sl = {"w": 1.0, "m": 30}
+    tg = eng.target(w["kind"], w["d"], w["params"] if w["params"].size else None, n_data=n_data)
+    job = eng.job(tg, "slice", m, n, x0=x0, seed=4, prec="fp64", slice=sl, tuning={"steps_per_launch": 25})
+    assert job.tuning()["lanes_per_chain"] == 32
+    job.run(mode)
+    ref = O.run("slice", w["kind"], w["params"], x0, n, seed=4, n_data=n_data, algo_params=[1.0, 30])
+    counts, props, _ = job.loop_counts()
+    r = compare(job.samples(), counts, ref["samples"], ref["counts"], "fp64")
+    assert r["max_err"] <= 1e-10
+    assert np.array_equal(props, ref["aux"])
+    job.close()
+
+
+def test_fp32_chain_per_warp_fsm_equals_sync(eng):
+    w, n_data, x0 = _wide_cases()["gauss_diag_d100"]
+    m, n = x0.shape[0], 80
+    tg = eng.target(w["kind"], w["d"], w["params"])
+    a = eng.job(tg, "slice", m, n, x0=x0, seed=2, prec="fp32")
+    b = eng.job(tg, "slice", m, n, x0=x0, seed=2, prec="fp32")
+    a.run("fsm")
+    b.run("sync")
+    (ca, pa, _), (cb, pb, _) = a.loop_counts(), b.loop_counts()
+    assert np.array_equal(ca, cb) and np.array_equal(pa, pb) and np.array_equal(a.samples(), b.samples())
+    ref = O.transitions("slice", w["kind"], w["params"],
+                        np.concatenate([x0.astype(np.float32).astype(np.float64)[:, None, :],
+                                        a.samples()[:, :-1, :]], axis=1).reshape(m * n, -1),
+                        np.repeat(np.arange(m), n), np.tile(np.arange(n), m), seed=2, algo_params=[1.0, 100])
+    transitions_agree(a.samples().reshape(m * n, -1), ca.ravel(), ref, "fp32 slice chain per warp d=100")
+    a.close()
+    b.close()
