@@ -326,3 +326,21 @@ def test_synchronised_forms_equal_the_fsm(eng, form, case):
     assert st["error_word"] == 0
     a.close()
     b.close()
+
+
+def test_synchronised_sweep_with_more_chains_than_its_live_masks_cover(eng):
+    # the sweep form keeps a 32-bit mask of live chains per chain group while groups have at most
+    # 32 chains; 120 000 chains at 32 lanes exceed that (about 3 600 resident groups), so the kernel
+    # reads each chain's state id instead -- still the FSM's samples, bit for bit
+    w = W.gauss_conj(16)
+    m, n = 120_000, 12
+    x0 = W.x0_normal(m, 16)
+    tu = {"lanes_per_chain": 32}
+    a = _run(eng, w, m, n, x0, "fp32", "fsm", tuning=tu)
+    b = _run(eng, w, m, n, x0, "fp32", "sync", tuning={**tu, "sync_form": 1})
+    ca, cb = a.loop_counts()[0], b.loop_counts()[0]
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(a.samples(), b.samples())
+    assert b.stats()["sync_iterations"] == int(cb.max(0).sum())
+    a.close()
+    b.close()
