@@ -8,6 +8,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfsmc.so")
 SOURCES = ["engine.cu", "ess.cu", "ess_block.cu", "ess_tc.cu", "dr.cu", "nuts.cu", "slice.cu", "serving.cu",
            "noalloc.cu", "autotune.cu", "stats.cu"]
+# sources compiled as several objects, each with its own -D (disjoint explicit instantiations)
+PARTS = {"ess.cu": [("ess_p%d" % p, ["-DFSMC_ESS_PART=%d" % p]) for p in (1, 2, 3, 4)]}
 # the benchmark's throughput probe: a separate library, not part of libfsmc.so or its C ABI
 PROBE_LIB = os.path.join(HERE, "libfsmc_probe.so")
 PROBE_SOURCES = ["bench_probe.cu"]
@@ -38,17 +40,18 @@ def _build_lib(lib, sources, force, verbose):
     procs, objs = [], []
     hdr_time = _header_time()
     for src in sources:
-        obj = os.path.join(objdir, src.replace(".cu", ".o"))
-        objs.append(obj)
-        # an object newer than its source and every header is up to date
-        if (not force and not verbose and os.path.exists(obj) and
-                os.path.getmtime(obj) > max(hdr_time, os.path.getmtime(os.path.join(CSRC, src)))):
-            continue
-        cmd = [nvcc] + FLAGS + ARCH + ["-I", os.path.join(HERE, "..", "include"), "-c",
-                                       os.path.join(CSRC, src), "-o", obj]
-        if verbose:
-            cmd.append("-Xptxas=-v")
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        for name, defs in PARTS.get(src, [(src.replace(".cu", ""), [])]):
+            obj = os.path.join(objdir, name + ".o")
+            objs.append(obj)
+            # an object newer than its source and every header is up to date
+            if (not force and not verbose and os.path.exists(obj) and
+                    os.path.getmtime(obj) > max(hdr_time, os.path.getmtime(os.path.join(CSRC, src)))):
+                continue
+            cmd = [nvcc] + FLAGS + ARCH + defs + ["-I", os.path.join(HERE, "..", "include"), "-c",
+                                                  os.path.join(CSRC, src), "-o", obj]
+            if verbose:
+                cmd.append("-Xptxas=-v")
+            procs.append((name, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()

@@ -13,9 +13,19 @@
 // (ess_nu_gen) into a per-chain ring of W slots; this is the paper's amortisation of an
 // expensive state-independent computation, moved out of the step altogether.
 #include <algorithm>
+#include <climits>
 #include "ess_common.cuh"
 #include "fsmc_device.cuh"
 #include "fsmc_kernels.h"
+
+// The build compiles this file as four objects, FSMC_ESS_PART = 1 (FSM step, single precision),
+// 2 (FSM step, double precision, and the fused serving launches), 3 (the synchronised program)
+// and 4 (the rest), each instantiating its own launchers, so that they compile in parallel;
+// without the macro one object holds everything.
+#ifndef FSMC_ESS_PART
+#define FSMC_ESS_PART 0
+#endif
+#define FSMC_ESS_HAS(p) (FSMC_ESS_PART == 0 || FSMC_ESS_PART == (p))
 
 namespace fsmc {
 
@@ -41,6 +51,7 @@ __device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx,
   const int r0 = bz * BM;
   const int w = by;
   const int64_t c0 = bx * BN;
+  const bool fold = ess_ring_folded(v);
 
   int active = 0;
   if (tid < BN) {
@@ -143,7 +154,7 @@ __device__ __forceinline__ void ess_nu_gen_tile(const EssView<T>& v, int64_t bx,
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = r0 + ty * 8 + i;
-      if (r < d) dst[r] = acc[i][j];
+      if (r < d) dst[r] = fold && v.tg.vec[r] > T(0) ? -acc[i][j] : acc[i][j];
     }
   }
   __syncthreads();  // the next tile reuses the shared staging
@@ -195,52 +206,91 @@ __device__ __forceinline__ T ess_loglik(const TargetView<T>& tg, const T (&xp)[E
 constexpr float kLn2f = 0.693147180559945309417f;
 constexpr float kLog2ef = 1.44269504088896340736f;
 
+// The factors of group g of this lane's coordinates (n of them, at most eight) and the log2 of
+// their product; q is the product (> 2^126, infinite or NaN: overflowed).
+template <int G, int E, bool FULL>
+__device__ __forceinline__ float ess_gp32_group(const float (&xs)[E], const float (&ns)[E], float cs2, float sn2,
+                                                int g, int lane, int d, float& q) {
+  constexpr int kGrp = 8;
+  const int n = E - g < kGrp ? E - g : kGrp;  // a constant once the callers' loops are unrolled
+  const float2 c2 = make_float2(cs2, cs2), s2 = make_float2(sn2, sn2), one = make_float2(1.f, 1.f);
+  float f[kGrp];
+#pragma unroll
+  for (int e = 0; e + 1 < n; e += 2) {
+    const int k0 = (g + e) * G + lane, k1 = (g + e + 1) * G + lane;
+    const float2 tt = __ffma2_rn(make_float2(xs[g + e], xs[g + e + 1]), c2,
+                                 __fmul2_rn(make_float2(ns[g + e], ns[g + e + 1]), s2));
+    const float2 y = __fadd2_rn(make_float2(ex2_approx(tt.x), ex2_approx(tt.y)), one);
+    f[e] = (FULL || k0 < d) ? y.x : 1.f;
+    f[e + 1] = (FULL || k1 < d) ? y.y : 1.f;
+  }
+  if (n % 2) {
+    const int e = n - 1, k = (g + e) * G + lane;
+    f[e] = (FULL || k < d) ? ex2_approx(fmaf(xs[g + e], cs2, ns[g + e] * sn2)) + 1.f : 1.f;
+  }
+  // product of the group's factors: pairwise in packed form, then the two halves
+  if (n >= 2) {
+    float2 p = make_float2(f[0], f[1]);
+#pragma unroll
+    for (int e = 2; e + 1 < n; e += 2) p = __fmul2_rn(p, make_float2(f[e], f[e + 1]));
+    q = p.x * p.y;
+    if (n % 2) q *= f[n - 1];
+  } else {
+    q = f[0];
+  }
+  return lg2_approx(q);
+}
+
+// The likelihood.  A lane's term a (the sum of its groups' log2 values) is added over the chain
+// group.  While no group of the warp overflowed, every group's log2 is at most 126, so a <=
+// 126 ceil(E / 8); with 32 lanes the terms are then rounded to the fixed-point grid 2^-kFx (kFx
+// = 19 up to eight coordinates per lane: error <= 2^-20 per lane; 32 of them sum below 2^31,
+// exactly, in a 32-bit integer) and added by one warp reduction (redux.sync) instead of a
+// five-level shuffle tree; the sum's rounding to single precision (half an ulp, 2^-18 near 128)
+// stays the larger error, as it is in the tree.  Chain groups of fewer lanes add by the tree.
+// When some group of the warp overflowed (or is NaN) the whole warp takes the branch in which
+// each lane recomputes its overflowed groups in the per-coordinate form and the lanes add by the
+// tree.
 template <int G, int E, bool FULL = false>
 __device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const float (&ns)[E], float cs2, float sn2,
                                                  int lane, int d, unsigned gmask) {
   constexpr int kGrp = 8;
-  const float2 c2 = make_float2(cs2, cs2), s2 = make_float2(sn2, sn2), one = make_float2(1.f, 1.f);
   float acc = 0.f;
+  bool over = false;
 #pragma unroll
   for (int g = 0; g < E; g += kGrp) {
-    const int n = E - g < kGrp ? E - g : kGrp;  // a constant once the loop is unrolled
-    float f[kGrp];
-#pragma unroll
-    for (int e = 0; e + 1 < n; e += 2) {
-      const int k0 = (g + e) * G + lane, k1 = (g + e + 1) * G + lane;
-      const float2 tt = __ffma2_rn(make_float2(xs[g + e], xs[g + e + 1]), c2,
-                                   __fmul2_rn(make_float2(ns[g + e], ns[g + e + 1]), s2));
-      const float2 y = __fadd2_rn(make_float2(ex2_approx(tt.x), ex2_approx(tt.y)), one);
-      f[e] = (FULL || k0 < d) ? y.x : 1.f;
-      f[e + 1] = (FULL || k1 < d) ? y.y : 1.f;
-    }
-    if (n % 2) {
-      const int e = n - 1, k = (g + e) * G + lane;
-      f[e] = (FULL || k < d) ? ex2_approx(fmaf(xs[g + e], cs2, ns[g + e] * sn2)) + 1.f : 1.f;
-    }
-    // product of the group's factors: pairwise in packed form, then the two halves
     float q;
-    if (n >= 2) {
-      float2 p = make_float2(f[0], f[1]);
-#pragma unroll
-      for (int e = 2; e + 1 < n; e += 2) p = __fmul2_rn(p, make_float2(f[e], f[e + 1]));
-      q = p.x * p.y;
-      if (n % 2) q *= f[n - 1];
-    } else {
-      q = f[0];
-    }
-    if (q <= 0x1p126f) {
-      acc += lg2_approx(q);
-    } else {  // overflowed (or NaN): the per-coordinate form, t' recomputed
-      float r = 0.f;
-#pragma unroll
-      for (int e = 0; e < n; ++e)
-        if (FULL || (g + e) * G + lane < d)
-          r += lg2_approx(1.f + ex2_approx(fminf(fmaf(xs[g + e], cs2, ns[g + e] * sn2), 126.f)));
-      acc += r;
-    }
+    acc += ess_gp32_group<G, E, FULL>(xs, ns, cs2, sn2, g, lane, d, q);
+    over |= !(q <= 0x1p126f);
   }
-  return -kLn2f * group_sum<G>(acc, gmask);
+  if (__any_sync(gmask, over)) {
+    acc = 0.f;
+#pragma unroll
+    for (int g = 0; g < E; g += kGrp) {
+      const int n = E - g < kGrp ? E - g : kGrp;
+      float q;
+      float lq = ess_gp32_group<G, E, FULL>(xs, ns, cs2, sn2, g, lane, d, q);
+      if (!(q <= 0x1p126f)) {  // the per-coordinate form, each term finite for finite t'
+        lq = 0.f;
+#pragma unroll
+        for (int e = 0; e < n; ++e)
+          if (FULL || (g + e) * G + lane < d)
+            lq += lg2_approx(1.f + ex2_approx(fminf(fmaf(xs[g + e], cs2, ns[g + e] * sn2), 126.f)));
+      }
+      acc += lq;
+    }
+    return -kLn2f * group_sum<G>(acc, gmask);
+  }
+  if constexpr (G == 32) {
+    constexpr int kGroups = (E + kGrp - 1) / kGrp;
+    constexpr int kFx = kGroups <= 1 ? 19 : kGroups <= 2 ? 18 : kGroups <= 4 ? 17 : 16;
+    const int qa = __float2int_rn(acc * (float)(1 << kFx));
+    int sum;
+    asm volatile("redux.sync.add.s32 %0, %1, 0xffffffff;" : "=r"(sum) : "r"(qa));
+    return (float)sum * (-kLn2f / (float)(1 << kFx));
+  } else {
+    return -kLn2f * group_sum<G>(acc, gmask);
+  }
 }
 
 // sign of coordinate e flipped where bit e of mask is set (exact)
@@ -354,50 +404,53 @@ struct PhiloxLaneCache {
 // converted to the two uniforms the states use: a = u(w0, w1) (the threshold's u at INIT, the
 // shrink's u at SHRINK) and b = u(w2, w3) (the initial angle's u).  A state then moves one float
 // (SHRINK) or two (INIT) by shuffle instead of four words, and converts nothing; the values are
-// the bits Conv<float>::u gives.
+// the bits Conv<float>::u gives.  The window of the current sample is kept as (lim, sh): offset
+// off < lim sits at lane sh + off.  INIT (offset 0) sets it from the narrow layout, refilling
+// that when the sample is not held; the shrinks of a sample ask for offsets 1, 2, ... in turn,
+// and the first offset past the window refills the cache wide (refill).  Groups of fewer than
+// eight lanes compute each block when it is asked for (lim is then unbounded).
 template <int G>
 struct UniformLaneCache {
   static constexpr int kOff = G < 16 ? G : 16;
   static constexpr int kSamp = G >= 8 ? G / kOff : 1;
   float a = 0.f, b = 0.f;
-  int tb = -(1 << 30), ob = 0;
-  bool wide = false;
+  int tb = -(1 << 30);  // first sample of the narrow layout (far below any sample when wide or empty)
+  int lim = G >= 8 ? 0 : INT_MAX, sh = 0;
   __device__ __forceinline__ void fill(const P4& r) {
     a = Conv<float>::u(r.w0, r.w1);
     b = Conv<float>::u(r.w2, r.w3);
   }
-  // the source lane of (sample t, draw D + off), refilling the cache when it is not held
-  __device__ __forceinline__ int locate(const Key& key, int t, int D, int off, int lane) {
-    if (!wide && (unsigned)t - (unsigned)tb < (unsigned)kSamp && off < kOff) return (t - tb) * kOff + off;
-    if (wide && t == tb && (unsigned)(off - ob) < (unsigned)G) return off - ob;
-    if (off < kOff) {
-      tb = t;
-      wide = false;
-      fill(key.block((uint32_t)(t + lane / kOff), 0, (uint32_t)(D + lane % kOff)));
-      return off;
-    }
-    tb = t;
-    ob = off;
-    wide = true;
-    fill(key.block((uint32_t)t, 0, (uint32_t)(D + off + lane)));
-    return 0;
-  }
-  __device__ __forceinline__ float fetch_a(const Key& key, int t, int D, int off, int lane, unsigned gmask) {
+  // INIT of sample t: the uniforms of offset 0; sets the window of t
+  __device__ __forceinline__ float2 init_ab(const Key& key, int t, int D, int lane, unsigned gmask) {
     if constexpr (G >= 8) {
-      const int src = locate(key, t, D, off, lane);
-      return __shfl_sync(gmask, a, src, G);
+      if ((unsigned)(t - tb) >= (unsigned)kSamp) {
+        tb = t;
+        fill(key.block((uint32_t)(t + lane / kOff), 0, (uint32_t)(D + lane % kOff)));
+      }
+      sh = (t - tb) * kOff;
+      lim = kOff;
+      return make_float2(__shfl_sync(gmask, a, sh, G), __shfl_sync(gmask, b, sh, G));
+    } else {
+      const P4 r = key.block((uint32_t)t, 0, (uint32_t)D);
+      return make_float2(Conv<float>::u(r.w0, r.w1), Conv<float>::u(r.w2, r.w3));
+    }
+  }
+  // offsets off .. off + G - 1 of sample t (off >= lim)
+  __device__ __forceinline__ void refill(const Key& key, int t, int D, int off, int lane) {
+    if constexpr (G >= 8) {
+      tb = -(1 << 30);
+      fill(key.block((uint32_t)t, 0, (uint32_t)(D + off + lane)));
+      sh = -off;
+      lim = off + G;
+    }
+  }
+  // the uniform a of offset off < lim of the current sample t
+  __device__ __forceinline__ float shrink_a(const Key& key, int t, int D, int off, int lane, unsigned gmask) {
+    if constexpr (G >= 8) {
+      return __shfl_sync(gmask, a, sh + off, G);
     } else {
       const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + off));
       return Conv<float>::u(r.w0, r.w1);
-    }
-  }
-  __device__ __forceinline__ float2 fetch_ab(const Key& key, int t, int D, int off, int lane, unsigned gmask) {
-    if constexpr (G >= 8) {
-      const int src = locate(key, t, D, off, lane);
-      return make_float2(__shfl_sync(gmask, a, src, G), __shfl_sync(gmask, b, src, G));
-    } else {
-      const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + off));
-      return make_float2(Conv<float>::u(r.w0, r.w1), Conv<float>::u(r.w2, r.w3));
     }
   }
 };
@@ -523,6 +576,11 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
 // directions were generated before this launch, are copied.
 // MOMC (moments-only jobs): the lane's running sums are held in its shared-memory slot mslot
 // ([4][E]) while the chain advances: loaded here, written back at the end.
+// Loop form: every pass evaluates one angle (one FSM state); the state that follows is set up
+// in the branch the decision takes -- after DONE the next sample's INIT (threshold, initial
+// angle, bracket), after a rejection the SHRINK (bracket end, new angle) -- so a state costs
+// one decision branch.  A launch that ends after a rejection leaves the chain in SHRINK with
+// the rejected angle, as the state machine's SHRINK expects it.
 template <int G, int E, bool FULL, bool PF = false, bool MOMC = false>
 __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, int64_t c, int budget, int lane,
                                                      float* pf = nullptr, float* mslot = nullptr) {
@@ -558,63 +616,93 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
   const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
   int slot = t % v.W;  // ring slot of sample t, advanced with t
   int pf_t = -1;  // sample whose direction is in pf (copy issued)
+  // the chain's rows: direction ring (sign-folded, ess_ring_folded), samples, loop counts
+  const float* ring_c = v.nu + (size_t)c * v.W * v.dstride;
+  float* out_c = v.out ? v.out + (size_t)c * v.n * d : nullptr;
+  int* counts_c = v.counts + (size_t)c * v.n;
   auto load_nu = [&]() {
     if constexpr (PF) {
       if (pf_t == t) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
 #pragma unroll
-        for (int e = 0; e < E; ++e) ns[e] = flip_sign(pf[e * G + lane], smask, e);
+        for (int e = 0; e < E; ++e) ns[e] = pf[e * G + lane];
         return;
       }
     }
-    const float* src = v.nu + ((size_t)c * v.W + slot) * v.dstride;
+    const float* src = ring_c + (size_t)slot * v.dstride;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = e * G + lane;
-      if (FULL || k < d) ns[e] = flip_sign(src[k], smask, e);
+      if (FULL || k < d) ns[e] = src[k];
     }
   };
-  if (st == ESS_SHRINK && t < v.n) load_nu();
-  int steps = 0;
-  int err = 0;
   UniformLaneCache<G> pc;
-  for (int b = 0; b < budget && t < v.n; ++b) {
-    if (st == ESS_INIT) {
-      if (t >= hi) break;  // direction not generated yet
-      load_nu();
-      if constexpr (PF) {
-        if (t + 1 < hi && b + 1 < budget) {
-          __syncwarp();  // every lane has read pf
-          const int nslot = slot + 1 == v.W ? 0 : slot + 1;
-          const float* src = v.nu + ((size_t)c * v.W + nslot) * v.dstride;
-          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(pf);
+  int b = 0;     // states evaluated in this launch
+  int lim2 = 0;  // shrink offsets below lim2 need neither a cache refill nor a budget check
+  // INIT of sample t, the (b+1)-th state of this launch
+  auto init = [&]() {
+    load_nu();
+    if constexpr (PF) {
+      if (t + 1 < hi && b + 1 < budget) {
+        __syncwarp();  // every lane has read pf
+        const int nslot = slot + 1 == v.W ? 0 : slot + 1;
+        const float* src = ring_c + (size_t)nslot * v.dstride;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(pf);
 #pragma unroll
-          for (int j = 0; j < E / 4; ++j) {
-            const int q = (j * G + lane) * 4;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 4u * (uint32_t)q), "l"(src + q)
-                         : "memory");
-          }
-          asm volatile("cp.async.commit_group;" ::: "memory");
-          pf_t = t + 1;
+        for (int j = 0; j < E / 4; ++j) {
+          const int q = (j * G + lane) * 4;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 4u * (uint32_t)q), "l"(src + q)
+                       : "memory");
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        pf_t = t + 1;
       }
-      const float2 u = pc.fetch_ab(key, t, D, 0, lane, gmask);
-      logy = ess_threshold<float>(ell, Conv<float>::log_of(u.x));
-      th = float(kTwoPi) * u.y;
-      thmin = th - float(kTwoPi);
-      thmax = th;
-      s = 0;
-    } else {
-      if (th < 0.f) thmin = th; else thmax = th;
-      th = thmin + (thmax - thmin) * pc.fetch_a(key, t, D, 1 + s, lane, gmask);
-      ++s;
     }
+    const float2 u = pc.init_ab(key, t, D, lane, gmask);
+    logy = ess_threshold<float>(ell, Conv<float>::log_of(u.x));
+    th = float(kTwoPi) * u.y;
+    thmin = th - float(kTwoPi);
+    thmax = th;
+    s = 0;
+    lim2 = min(pc.lim, budget - b);
+  };
+  // SHRINK at offset off = 1 + s < lim2: the bracket end moves to the rejected angle th and a new
+  // angle is drawn inside
+  auto shrink = [&](int off) {
+    if (th < 0.f) thmin = th; else thmax = th;
+    th = thmin + (thmax - thmin) * pc.shrink_a(key, t, D, off, lane, gmask);
+    ++s;
+  };
+  // Before the shrink at offset off >= lim2: the launch's budget is spent (returns false) or the
+  // cache window ends (refilled).  b and off grow together through a sample's shrinks, so
+  // b == budget exactly when off reaches budget - b + off, the bound lim2 folds in; one
+  // comparison per SHRINK state then covers both.
+  auto refill = [&](int off) {
+    if (b == budget) return false;
+    pc.refill(key, t, D, off, lane);
+    lim2 = min(pc.lim, budget - b + off);
+    return true;
+  };
+  int err = 0;
+  bool nonfinite = false;
+  bool run = t < v.n && budget > 0;
+  if (run) {
+    if (st == ESS_INIT) {
+      run = t < hi;  // else the direction is not generated yet
+      if (run) init();
+    } else {
+      load_nu();
+      refill(1 + s);
+      shrink(1 + s);
+    }
+  }
+  while (run) {
     float sn, cs;
     ess_sincos<float>(th, sn, cs);
-    float ellp = ess_loglik_gp32<G, E, FULL>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
-    if (!(ellp == ellp)) { ellp = neg_inf<float>(); err |= ERR_NONFINITE; }
-    ++steps;
+    const float ellp = ess_loglik_gp32<G, E, FULL>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
+    nonfinite |= !(ellp == ellp);  // a NaN is never above the threshold: rejected
+    ++b;
     const bool accept = ellp > logy;
     if (accept || s >= kMaxShrinks) {
       if (accept) {
@@ -638,16 +726,34 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
       float x[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) x[e] = flip_sign(xs[e], smask, e);
-      ess_emit<float, G, E, FULL>(v, c, t, lane, x, MOMC ? mslot : nullptr);
-      if (lane == 0) v.counts[(size_t)c * v.n + t] = s;
+      if (out_c) {
+        float* dst = out_c + (size_t)t * d;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int k = e * G + lane;
+          if (FULL || k < d) dst[k] = x[e];
+        }
+      } else {
+        ess_emit<float, G, E, FULL>(v, c, t, lane, x, MOMC ? mslot : nullptr);
+      }
+      if (lane == 0) counts_c[t] = s;
       ++t;
       if (++slot == v.W) slot = 0;
       st = ESS_INIT;
-      if (t == v.n && lane == 0) atomicAdd(v.chains_done, 1);
+      if (t == v.n) {
+        if (lane == 0) atomicAdd(v.chains_done, 1);
+        break;
+      }
+      if (b == budget || t >= hi) break;
+      init();
     } else {
       st = ESS_SHRINK;
+      const int off = 1 + s;
+      if (off >= lim2 && !refill(off)) break;
+      shrink(off);
     }
   }
+  if (nonfinite) err |= ERR_NONFINITE;
   if constexpr (PF) {
     if (pf_t >= 0) asm volatile("cp.async.wait_all;" ::: "memory");  // pf is reused by the next chain
     __syncwarp();
@@ -669,7 +775,7 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
   if (lane == 0) {
     v.ell[c] = ell; v.logy[c] = logy; v.th[c] = th; v.thmin[c] = thmin; v.thmax[c] = thmax;
     v.t[c] = t; v.k[c] = st; v.s[c] = s;
-    v.steps[c] += steps;
+    v.steps[c] += b;
     if (v.own_window) {
       v.gen_lo[c] = hi;
       v.gen_hi[c] = min(t + v.W, v.n);
@@ -763,7 +869,7 @@ __global__ void __launch_bounds__(256) ess_fsm_multi_kernel(const EssView<T>* vi
   const int k = find_job(off, njobs, item);
   const EssView<T> v = views[k];
   if constexpr (kEssGpFast<T, E>) {
-    if (v.tg.kind == TGT_GP_LOGIT) {
+    if (ess_ring_folded(v)) {
       ess_advance_chain<T, G, E, 1>(v, item - off[k], budget, lane);
       return;
     }
@@ -804,7 +910,7 @@ __device__ __forceinline__ bool ess_sync_visit(const EssView<T>& v, int64_t c, i
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const T* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
   // GP path: the sign-folded coordinates xs = -s x, ns = -s nu, as in the FSM kernel
-  // (ess_advance_chain_gp); otherwise x and nu
+  // (ess_advance_chain_gp; the ring already holds ns, ess_ring_folded); otherwise x and nu
   T xa[E], na[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -813,7 +919,7 @@ __device__ __forceinline__ bool ess_sync_visit(const EssView<T>& v, int64_t c, i
     const T nu = k < d ? src[k] : T(0);
     if constexpr (GP) {
       xa[e] = flip_sign(x, ld.smask, e);
-      na[e] = flip_sign(nu, ld.smask, e);
+      na[e] = nu;
     } else {
       xa[e] = x;
       na[e] = nu;
@@ -1088,13 +1194,13 @@ __global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_cg_iter_k
 }
 
 // After a sample: the next one, while samples remain; its INIT writes list st->phase, cleared here.
-__global__ void ess_cg_next_kernel(EssCgState* st, cudaGraphConditionalHandle outer) {
+static __global__ void ess_cg_next_kernel(EssCgState* st, cudaGraphConditionalHandle outer) {
   st->cnt[st->phase] = 0;
   st->t += 1;
   cudaGraphSetConditional(outer, st->t < st->t_end ? 1u : 0u);
 }
 
-__global__ void ess_cg_begin_kernel(EssCgState* st, int t_begin, int t_end) {
+static __global__ void ess_cg_begin_kernel(EssCgState* st, int t_begin, int t_end) {
   st->t = t_begin;
   st->t_end = t_end;
   st->phase = 0;
@@ -1159,8 +1265,10 @@ cudaError_t launch_moments_from_samples(const T* samples, const int* t, int64_t 
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
 }
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_moments_from_samples<float>(const float*, const int*, int64_t, int, int, float*,
                                                         cudaStream_t);
+#endif
 
 // The sums of x and x^2 ([4][m d] running sums with their compensations) as doubles, [2][m d].
 template <typename T>
@@ -1176,10 +1284,16 @@ cudaError_t launch_moments_to_double(const T* mom, int64_t md, double* out, cuda
   moments_to_double_kernel<T><<<(unsigned)((md + 255) / 256), 256, 0, st>>>(mom, md, out);
   return cudaGetLastError();
 }
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_moments_to_double<float>(const float*, int64_t, double*, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_moments_to_double<double>(const double*, int64_t, double*, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_moments_from_samples<double>(const double*, const int*, int64_t, int, int, double*,
                                                          cudaStream_t);
+#endif
 
 // Refill window of the next pipelined round.  It runs while the FSM kernel of the current
 // round advances t, and may read either the old or the new t: the directions it asks for are
@@ -1200,10 +1314,14 @@ cudaError_t launch_ess_window(const EssView<T>& v, const int* hi_cur, cudaStream
   ess_window_kernel<T><<<(unsigned)((v.m + 255) / 256), 256, 0, st>>>(v, hi_cur);
   return cudaGetLastError();
 }
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_window<float>(const EssView<float>&, const int*, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_window<double>(const EssView<double>&, const int*, cudaStream_t);
+#endif
 
-__global__ void fill_int_kernel(int* p, int64_t n, int value) {
+static __global__ void fill_int_kernel(int* p, int64_t n, int value) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = value;
 }
@@ -1219,23 +1337,33 @@ cudaError_t launch_from_double(const double* src, int64_t n, T* dst, cudaStream_
   from_double_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, n, dst);
   return cudaGetLastError();
 }
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_from_double<float>(const double*, int64_t, float*, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_from_double<double>(const double*, int64_t, double*, cudaStream_t);
+#endif
 
+#if FSMC_ESS_HAS(4)
 cudaError_t launch_fill_int(int* p, int64_t n, int value, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
   fill_int_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, n, value);
   return cudaGetLastError();
 }
+#endif
 
 template <typename T>
 cudaError_t launch_ess_init(const EssView<T>& v, cudaStream_t st) {
   ess_init_kernel<T><<<(unsigned)((v.m + 127) / 128), 128, 0, st>>>(v);
   return cudaGetLastError();
 }
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_init<float>(const EssView<float>&, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_init<double>(const EssView<double>&, cudaStream_t);
+#endif
 
 // ------------------------------------------------------------------------------------------
 // host launchers
@@ -1255,7 +1383,7 @@ static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cuda
     return cudaGetLastError();
   }
   if constexpr (kEssGpFast<T, E>) {
-    if (v.tg.kind == TGT_GP_LOGIT) {
+    if (ess_ring_folded(v)) {
       if (v.tg.d == E * G) {
         const size_t momb = (size_t)threads * (4 * E + 1) * sizeof(float);
         if (kEssPrefetch<T, G, E, 2> && !v.out && momb <= 48 * 1024)
@@ -1278,7 +1406,7 @@ static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier 
                                int* lists, cudaStream_t st) {
   void* kern = form == 2 ? (void*)ess_sync_list_kernel<T, G, E, false> : (void*)ess_sync_kernel<T, G, E, false>;
   if constexpr (kEssGpFast<T, E>) {
-    if (v.tg.kind == TGT_GP_LOGIT)
+    if (ess_ring_folded(v))
       kern = form == 2 ? (void*)ess_sync_list_kernel<T, G, E, true> : (void*)ess_sync_kernel<T, G, E, true>;
   }
   int per_sm = 0;
@@ -1318,7 +1446,7 @@ static cudaError_t sync_graph_build(const EssView<T>& v, int threads, EssCgState
   void* kinit = (void*)ess_cg_init_kernel<T, G, E, false>;
   void* kiter = (void*)ess_cg_iter_kernel<T, G, E, false>;
   if constexpr (kEssGpFast<T, E>) {
-    if (v.tg.kind == TGT_GP_LOGIT) {
+    if (ess_ring_folded(v)) {
       kinit = (void*)ess_cg_init_kernel<T, G, E, true>;
       kiter = (void*)ess_cg_iter_kernel<T, G, E, true>;
     }
@@ -1437,12 +1565,14 @@ cudaError_t launch_ess_nu_gen_multi(const EssView<T>* views, const int64_t* off,
 }
 
 // shape of the group an ESS job belongs to: jobs with equal (lanes, E) share a fused launch
+#if FSMC_ESS_HAS(4)
 int ess_group_E(int G, int d) {
   if (G == 1) return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32;
   if (G == 8) return d <= 64 ? 8 : d <= 128 ? 16 : 32;
   if (G == 16) return d <= 64 ? 4 : d <= 128 ? 8 : d <= 256 ? 16 : 32;
   return d <= 32 ? 1 : d <= 64 ? 2 : d <= 128 ? 4 : d <= 256 ? 8 : d <= 512 ? 16 : 32;
 }
+#endif
 
 template <typename T>
 cudaError_t launch_ess_sync(const EssView<T>& v, int G, int t0, int t1, GridBarrier bar,
@@ -1458,32 +1588,58 @@ cudaError_t build_ess_sync_graph(const EssView<T>& v, int G, int threads, void* 
   FSMC_ESS_DISPATCH(sync_graph_build, v, threads, cg, lists, iters, out);
 }
 
+#if FSMC_ESS_HAS(3)
 cudaError_t launch_ess_sync_graph(cudaGraphExec_t exec, void* cg_state, int t0, int t1, cudaStream_t st) {
   ess_cg_begin_kernel<<<1, 1, 0, st>>>((EssCgState*)cg_state, t0, t1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaGraphLaunch(exec, st);
 }
+#endif
 
+#if FSMC_ESS_HAS(2)
 template cudaError_t launch_ess_fsm_multi<float>(const EssView<float>&, int, const EssView<float>*,
                                                  const int64_t*, int, int64_t, int, int, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(2)
 template cudaError_t launch_ess_fsm_multi<double>(const EssView<double>&, int, const EssView<double>*,
                                                   const int64_t*, int, int64_t, int, int, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_nu_gen_multi<float>(const EssView<float>*, const int64_t*, int, int64_t,
                                                     cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_nu_gen_multi<double>(const EssView<double>*, const int64_t*, int, int64_t,
                                                      cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_nu_gen<float>(const EssView<float>&, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(4)
 template cudaError_t launch_ess_nu_gen<double>(const EssView<double>&, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(1)
 template cudaError_t launch_ess_fsm<float>(const EssView<float>&, int, int, int, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(2)
 template cudaError_t launch_ess_fsm<double>(const EssView<double>&, int, int, int, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(3)
 template cudaError_t launch_ess_sync<float>(const EssView<float>&, int, int, int, GridBarrier,
                                             unsigned*, unsigned long long*, int, int, int*, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(3)
 template cudaError_t launch_ess_sync<double>(const EssView<double>&, int, int, int, GridBarrier,
                                              unsigned*, unsigned long long*, int, int, int*, cudaStream_t);
+#endif
+#if FSMC_ESS_HAS(3)
 template cudaError_t build_ess_sync_graph<float>(const EssView<float>&, int, int, void*, int*,
                                                  unsigned long long*, cudaGraphExec_t*);
+#endif
+#if FSMC_ESS_HAS(3)
 template cudaError_t build_ess_sync_graph<double>(const EssView<double>&, int, int, void*, int*,
                                                   unsigned long long*, cudaGraphExec_t*);
+#endif
 
 }  // namespace fsmc

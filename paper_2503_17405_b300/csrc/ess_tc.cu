@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 #include <algorithm>
 
+#include "ess_common.cuh"
 #include "fsmc_device.cuh"
 #include "fsmc_kernels.h"
 
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
   const bool mma_warp = warp == TC_PRODUCER_WARPS;
   const bool cols_warp = warp == TC_PRODUCER_WARPS + 1;
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
+  const bool fold = ess_ring_folded(v);
   const int nchunks = lay.kpad / TC_KC;
   const long long total = v.col_base[v.m];
   const long long ntiles = (total + TC_N - 1) / TC_N;
@@ -358,10 +360,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (row < d) {
+          const uint32_t sgn = fold && v.tg.vec[row] > 0.f ? 0x80000000u : 0u;  // ess_ring_folded
 #pragma unroll
           for (int jj = 0; jj < TC_N / 2; ++jj) {
             float* dst = cols->dst[bb][jbeg + jj];
-            if (dst) dst[row] = __uint_as_float(r[jj]);
+            if (dst) dst[row] = __uint_as_float(r[jj] ^ sgn);
           }
         }
       }
