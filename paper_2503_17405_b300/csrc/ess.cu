@@ -270,12 +270,14 @@ __device__ __forceinline__ float ess_loglik_gp32(const float (&xs)[E], const flo
       const int n = E - g < kGrp ? E - g : kGrp;
       float q;
       float lq = ess_gp32_group<G, E, FULL>(xs, ns, cs2, sn2, g, lane, d, q);
-      if (!(q <= 0x1p126f)) {  // the per-coordinate form, each term finite for finite t'
+      if (!(q <= 0x1p126f)) {  // the per-coordinate form, each term finite for finite t' (NaN stays NaN)
         lq = 0.f;
 #pragma unroll
         for (int e = 0; e < n; ++e)
-          if (FULL || (g + e) * G + lane < d)
-            lq += lg2_approx(1.f + ex2_approx(fminf(fmaf(xs[g + e], cs2, ns[g + e] * sn2), 126.f)));
+          if (FULL || (g + e) * G + lane < d) {
+            const float tp = fmaf(xs[g + e], cs2, ns[g + e] * sn2);
+            lq += lg2_approx(1.f + ex2_approx(tp > 126.f ? 126.f : tp));
+          }
       }
       acc += lq;
     }
@@ -685,7 +687,6 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
     return true;
   };
   int err = 0;
-  bool nonfinite = false;
   bool run = t < v.n && budget > 0;
   if (run) {
     if (st == ESS_INIT) {
@@ -701,7 +702,6 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
     float sn, cs;
     ess_sincos<float>(th, sn, cs);
     const float ellp = ess_loglik_gp32<G, E, FULL>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, gmask);
-    nonfinite |= !(ellp == ellp);  // a NaN is never above the threshold: rejected
     ++b;
     const bool accept = ellp > logy;
     if (accept || s >= kMaxShrinks) {
@@ -721,7 +721,9 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
         }
         ell = ellp;
       } else {
-        err |= ERR_SHRINK_CAP;
+        // a NaN likelihood (non-finite coordinates) is never above the threshold: such a
+        // sample ends here, at the shrink cap
+        err |= ellp == ellp ? ERR_SHRINK_CAP : ERR_SHRINK_CAP | ERR_NONFINITE;
       }
       float x[E];
 #pragma unroll
@@ -753,7 +755,6 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
       shrink(off);
     }
   }
-  if (nonfinite) err |= ERR_NONFINITE;
   if constexpr (PF) {
     if (pf_t >= 0) asm volatile("cp.async.wait_all;" ::: "memory");  // pf is reused by the next chain
     __syncwarp();

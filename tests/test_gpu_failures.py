@@ -5,6 +5,8 @@ after each failure the device is shown to still answer by a run that succeeds.
   * a grid-barrier wait of the synchronised kernel runs out -> FSMC_ETIMEOUT, error bit 2;
   * a log density that is NaN everywhere (a NaN label in the logistic-regression data) is
     treated as -inf: every proposal is rejected and error bit 4 is set;
+  * ESS on the GP-logit target from a state with a NaN coordinate: no proposal clears the
+    threshold, every sample ends at the shrink cap (bits 1 and 4) with the state unchanged;
   * a running submitted job is cancelled -> FSMC_ECANCELED, while a job beside it finishes with
     the samples it has when run alone;
   * a job larger than the device's memory, under a budget that admits it -> FSMC_ENOMEM.
@@ -14,7 +16,7 @@ import time
 import numpy as np
 import pytest
 
-from paper_2503_17405_b300 import workloads as W
+from paper_2503_17405_b300 import fsmc, workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -92,6 +94,28 @@ def test_nan_log_density_rejects_every_proposal_and_sets_the_error_bit(eng, algo
             assert np.all(counts == 3)       # every stage tried and rejected
         else:
             assert np.all(counts == 1) and np.all(depth == 1)  # the first leaf diverges
+        job.close()
+
+
+@pytest.mark.parametrize("lanes", [32, 1])
+def test_ess_gp_logit_from_a_nan_state_ends_every_sample_at_the_shrink_cap(eng, lanes):
+    d = 256 if lanes == 32 else 16
+    w = W.gp_logit(d)
+    tg = eng.target("gp_logit", d, w["params"])
+    m, n = 64, 2
+    x0 = W.x0_zeros(m, d)
+    x0[5, 3] = np.nan
+    for mode in ("fsm", "sync"):
+        job = eng.job(tg, "ess", m, n, x0=x0, seed=1, prec="fp32", tuning={"lanes_per_chain": lanes})
+        with pytest.raises(fsmc.FsmcError, match="shrink cap"):   # the run completes, then reports
+            job.run(mode)
+        st = job.stats()
+        assert st["error_word"] & 5 == 5, st["error_word"]
+        assert st["samples_done"] == m * n
+        counts, _, _ = job.loop_counts()
+        assert np.all(counts[5] == 10000)   # the shrink cap
+        assert np.all(np.isnan(job.samples(5, 1)[0, :, 3]))
+        assert np.all(counts[np.arange(m) != 5] < 10000)
         job.close()
 
 
