@@ -35,8 +35,10 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 # ncu --set full of one FSM-step launch of the headline workload's kernel (ESS-GP, d = 256, 32 lanes
 # per chain) on a small case; the summary and its command are in profiles/
-ESS_GP_STEP_NCU = {"chains": 4096, "states": 512, "dram_bytes": 402.5e6 + 354.0e6, "issue_active": 0.731,
-                   "warp_instructions_per_state": 268.5e6 / (4096 * 512),
+ESS_GP_STEP_NCU = {"chains": 4096, "states": 512, "dram_bytes": 402.5e6 + 354.6e6, "issue_active": 0.714,
+                   # whole job (4096 chains x 400 samples): smsp__inst_executed of every FSM-step launch
+                   # over the job's FSM states
+                   "warp_instructions_per_state": 108.35,
                    "source": "profiles/ess_gp_d256_m4096_n400_kernels.md (ncu --set full, 4096 chains x 512 states)"}
 
 
