@@ -41,23 +41,6 @@ __device__ __forceinline__ T la1(T lp_cur, T lp_prop) {
   return lp_prop == neg_inf<T>() ? neg_inf<T>() : fmin(T(0), lp_prop - lp_cur);
 }
 
-template <typename T>
-__device__ __forceinline__ T la2(T pc, T pf, T ps, T q1_cf, T q1_sf) {
-  const T num = ps + q1_sf + l1m(la1(ps, pf));
-  const T den = pc + q1_cf + l1m(la1(pc, pf));
-  if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
-  return fmin(T(0), num - den);
-}
-
-template <typename T>
-__device__ __forceinline__ T la3(T p0, T p1, T p2, T p3, T q1_x_y1, T q2_x_y2, T q1_y3_y2,
-                                 T q2_y3_y1, T q1_y1_y2) {
-  const T num = p3 + q1_y3_y2 + q2_y3_y1 + l1m(la1(p3, p2)) + l1m(la2(p3, p2, p1, q1_y3_y2, q1_y1_y2));
-  const T den = p0 + q1_x_y1 + q2_x_y2 + l1m(la1(p0, p1)) + l1m(la2(p0, p1, p2, q1_x_y1, q1_y1_y2));
-  if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
-  return fmin(T(0), num - den);
-}
-
 template <typename T, int E>
 __device__ __forceinline__ T sqdist(const T (&a)[E], const T (&b)[E], int d) {
   T acc = T(0);
@@ -103,7 +86,7 @@ __device__ __forceinline__ T dr_eval(const DrView<T>& v, const T (&y)[E], int& e
 // stage where they first appear: after stage 1 rejects, l1m(a1(x, y1)); after stage 2 rejects,
 // the stage-2 ratio's l1m(a2(x, y1, y2)), l1m(a1(y1, y2)) and the proposal-density terms between
 // x, y1 and y2.  Stage 3 then evaluates two l1m instead of eight (and stage 2 one instead of
-// two), on the values the full formulas (la2, la3) would recompute.
+// two), on the values the full stage-2 and stage-3 ratios would recompute.
 template <typename T>
 struct DrCache {
   T a1;       // l1m(a1(x, y1))
@@ -114,29 +97,79 @@ struct DrCache {
   T q2xy2;    // lq2(x -> y2)
 };
 
+// Explicitly rounded add and multiply: the ratio terms below are written with them (and fma) so
+// that the per-stage form (dr_ratio, dr_decide: the synchronised kernel, whose iterations are
+// stage-uniform, and the four-state ablation) and the all-stages form of the FSM step
+// (dr_ratio_all, dr_decide_all) round every operation alike whatever the compiler would contract.
+template <typename T>
+__device__ __forceinline__ T add_rn(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fadd_rn(a, b); else return __dadd_rn(a, b);
+}
+template <typename T>
+__device__ __forceinline__ T mul_rn(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fmul_rn(a, b); else return __dmul_rn(a, b);
+}
+template <typename T>
+__device__ __forceinline__ T clip_ratio(T num, T den) {
+  return (num == neg_inf<T>() || den == neg_inf<T>()) ? neg_inf<T>() : fmin(T(0), num - den);
+}
+
 template <typename T, int E>
 __device__ __forceinline__ T dr_ratio(const DrView<T>& v, int k, const T (&x)[E], T lp, const T (&y1)[E], T lp1,
                                       const T (&y2)[E], T lp2, const T (&y)[E], T lpy, const DrCache<T>& cc) {
   const int d = v.tg.d;
   if (k == 0) return la1(lp, lpy);
   const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]);
-  if (k == 1) {  // la2(lp, lp1, lpy, lq1(x -> y1), lq1(y -> y1)) with its l1m(a1(x, y1)) kept
-    const T num = lpy + i1 * sqdist(y, y1, d) + l1m(la1(lpy, lp1));
-    const T den = lp + i1 * sqdist(x, y1, d) + cc.a1;
-    if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
-    return fmin(T(0), num - den);
+  if (k == 1) {  // log alpha_2(x, y1, y) with its l1m(a1(x, y1)) kept
+    const T num = add_rn(add_rn(lpy, mul_rn(i1, sqdist(y, y1, d))), l1m(la1(lpy, lp1)));
+    const T den = add_rn(add_rn(lp, mul_rn(i1, sqdist(x, y1, d))), cc.a1);
+    return clip_ratio(num, den);
   }
-  // la3(lp, lp1, lp2, lpy, ...) with the terms of x, y1, y2 kept
+  // log alpha_3(x, y1, y2, y) with the terms of x, y1, y2 kept
   const T i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
-  const T q1_y3_y2 = i1 * sqdist(y, y2, d);
+  const T q1_y3_y2 = mul_rn(i1, sqdist(y, y2, d));
   const T a1_32 = l1m(la1(lpy, lp2));
-  const T n2 = lp1 + cc.q1y1y2 + cc.a1y1y2;  // la2(lpy, lp2, lp1, q1_y3_y2, q1_y1_y2)
-  const T d2 = lpy + q1_y3_y2 + a1_32;
-  const T a2_321 = (n2 == neg_inf<T>() || d2 == neg_inf<T>()) ? neg_inf<T>() : fmin(T(0), n2 - d2);
-  const T num = lpy + q1_y3_y2 + i2 * sqdist(y, y1, d) + a1_32 + l1m(a2_321);
-  const T den = lp + cc.q1xy1 + cc.q2xy2 + cc.a1 + cc.a2;
-  if (num == neg_inf<T>() || den == neg_inf<T>()) return neg_inf<T>();
-  return fmin(T(0), num - den);
+  const T n2 = add_rn(add_rn(lp1, cc.q1y1y2), cc.a1y1y2);  // log alpha_2(y, y2, y1): numerator
+  const T d2 = add_rn(add_rn(lpy, q1_y3_y2), a1_32);
+  const T num = add_rn(add_rn(add_rn(add_rn(lpy, q1_y3_y2), mul_rn(i2, sqdist(y, y1, d))), a1_32),
+                       l1m(clip_ratio(n2, d2)));
+  const T den = add_rn(add_rn(add_rn(add_rn(lp, cc.q1xy1), cc.q2xy2), cc.a1), cc.a2);
+  return clip_ratio(num, den);
+}
+
+// dr_ratio for every stage in one instruction stream (same bits): a warp's chains sit at
+// different stages, so the terms of stages 2 and 3 are computed by every thread and selected;
+// stage 3 pairs the new proposal with y2 where stage 2 pairs it with y1.
+template <typename T, int E>
+__device__ __forceinline__ T dr_ratio_all(const DrView<T>& v, int k, const T (&x)[E], T lp, const T (&y1)[E],
+                                          T lp1, const T (&y2)[E], T lp2, const T (&y)[E], T lpy,
+                                          const DrCache<T>& cc) {
+  const int d = v.tg.d;
+  const T r1 = la1(lp, lpy);
+  if (v.n_stages < 2) return r1;
+  const bool k2 = k >= 2;
+  const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]);
+  T a[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) a[e] = k2 ? y2[e] : y1[e];
+  const T q1_ya = mul_rn(i1, sqdist(y, a, d));  // stage 2: lq1(y -> y1); stage 3: lq1(y -> y2)
+  const T a1_ya = l1m(la1(lpy, k2 ? lp2 : lp1));
+  T num = add_rn(lpy, q1_ya);
+  T den = add_rn(lp, k2 ? cc.q1xy1 : mul_rn(i1, sqdist(x, y1, d)));
+  if (v.n_stages > 2) {  // stage-uniform for the launch
+    const T i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
+    const T n2 = add_rn(add_rn(lp1, cc.q1y1y2), cc.a1y1y2);
+    const T d2 = add_rn(add_rn(lpy, q1_ya), a1_ya);
+    const T a2_321 = l1m(clip_ratio(n2, d2));
+    const T num3 = add_rn(add_rn(add_rn(num, mul_rn(i2, sqdist(y, y1, d))), a1_ya), a2_321);
+    const T den3 = add_rn(add_rn(add_rn(den, cc.q2xy2), cc.a1), cc.a2);
+    num = k2 ? num3 : add_rn(num, a1_ya);
+    den = k2 ? den3 : add_rn(den, cc.a1);
+  } else {
+    num = add_rn(num, a1_ya);
+    den = add_rn(den, cc.a1);
+  }
+  return k == 0 ? r1 : clip_ratio(num, den);
 }
 
 // Returns true when the sample is finished (accepted, or rejected at the last stage); then x/lp
@@ -162,15 +195,56 @@ __device__ __forceinline__ bool dr_decide(const DrView<T>& v, const Key& key, in
     cc.a1 = l1m(la);
   } else {
     const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]), i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
-    cc.q1xy1 = i1 * sqdist(x, y1, d);
-    cc.q1y1y2 = i1 * sqdist(y, y1, d);
+    cc.q1xy1 = mul_rn(i1, sqdist(x, y1, d));
+    cc.q1y1y2 = mul_rn(i1, sqdist(y, y1, d));
     cc.a2 = l1m(la);
     cc.a1y1y2 = l1m(la1(lp1, lpy));
-    cc.q2xy2 = i2 * sqdist(x, y, d);
+    cc.q2xy2 = mul_rn(i2, sqdist(x, y, d));
 #pragma unroll
     for (int e = 0; e < E; ++e) y2[e] = y[e];
     lp2 = lpy;
   }
+  return false;
+}
+
+// dr_decide for every stage in one instruction stream (same bits): the terms a stage-2 rejection
+// keeps are computed by every rejecting thread and selected, l1m of the ratio is taken once
+// (stage 1 keeps it as a1, stage 2 as a2).
+template <typename T, int E>
+__device__ __forceinline__ bool dr_decide_all(const DrView<T>& v, const Key& key, int t, int k, T la, T (&x)[E],
+                                              T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, const T (&y)[E],
+                                              T lpy, DrCache<T>& cc) {
+  const int D = (v.tg.d + 3) / 4;
+  const P4 r = key.block((uint32_t)t, 0, (uint32_t)(k * (D + 1) + D));
+  if (Conv<T>::log_u(r.w0, r.w1) < la) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = y[e];
+    lp = lpy;
+    return true;
+  }
+  if (k + 1 >= v.n_stages) return true;
+  const int d = v.tg.d;
+  const bool k1 = k == 1;
+  const T l1m_la = l1m(la);
+  if (v.n_stages > 2) {  // stage-uniform for the launch: a stage-2 rejection is possible
+    const T i1 = T(-0.5) / (v.sig[0] * v.sig[0]), i2 = T(-0.5) / (v.sig[1] * v.sig[1]);
+    const T q1xy1 = mul_rn(i1, sqdist(x, y1, d));
+    const T q1y1y2 = mul_rn(i1, sqdist(y, y1, d));
+    const T a1y1y2 = l1m(la1(lp1, lpy));
+    const T q2xy2 = mul_rn(i2, sqdist(x, y, d));
+    if (k1) {
+      cc.q1xy1 = q1xy1; cc.q1y1y2 = q1y1y2; cc.a1y1y2 = a1y1y2; cc.q2xy2 = q2xy2;
+    }
+  }
+  cc.a1 = k1 ? cc.a1 : l1m_la;
+  cc.a2 = k1 ? l1m_la : cc.a2;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    y1[e] = k1 ? y1[e] : y[e];
+    y2[e] = k1 ? y[e] : y2[e];
+  }
+  lp1 = k1 ? lp1 : lpy;
+  lp2 = k1 ? lpy : lp2;
   return false;
 }
 
@@ -226,15 +300,22 @@ __device__ __forceinline__ bool sdr_step(const DrView<T>& v, const Key& key, int
 }
 
 // One PROPOSE step of stage k for one chain (all four parts); the symmetric sampler's try k.
-template <typename T, int E>
+// ALL: the stage-dependent parts in one instruction stream (the FSM step, whose warps hold chains
+// at every stage); otherwise per stage (the synchronised kernel, stage-uniform).  Same bits.
+template <typename T, int E, bool ALL = false>
 __device__ __forceinline__ bool dr_step(const DrView<T>& v, const Key& key, int t, int k, T (&x)[E],
                                         T& lp, T (&y1)[E], T& lp1, T (&y2)[E], T& lp2, DrCache<T>& cc, int& err) {
   if (v.symmetric) return sdr_step<T, E>(v, key, t, k, x, lp, y1, lp1, err);
   T y[E];
   dr_draw<T, E>(v, key, t, k, x, y);
   const T lpy = dr_eval<T, E>(v, y, err);
-  const T la = dr_ratio<T, E>(v, k, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
-  return dr_decide<T, E>(v, key, t, k, la, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
+  if constexpr (ALL) {
+    const T la = dr_ratio_all<T, E>(v, k, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
+    return dr_decide_all<T, E>(v, key, t, k, la, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
+  } else {
+    const T la = dr_ratio<T, E>(v, k, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
+    return dr_decide<T, E>(v, key, t, k, la, x, lp, y1, lp1, y2, lp2, y, lpy, cc);
+  }
 }
 
 // The kept terms live in lpy[4 + i][m] between launches (and between synchronised iterations).
@@ -315,7 +396,7 @@ __global__ void __launch_bounds__(256) dr_fsm_kernel(DrView<T> v, int budget) {
     for (int b = 0; b < budget && t < v.n; ++b) {
       ++steps;
       if constexpr (CONDENSED) {
-        if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, err)) {
+        if (dr_step<T, E, true>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, err)) {
           dr_emit<T, E>(v, c, t, x, ms);
           v.counts[(size_t)c * v.n + t] = k + 1;
           ++t;
