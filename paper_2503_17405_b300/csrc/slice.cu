@@ -166,6 +166,50 @@ __device__ __forceinline__ bool slice_step(const SliceView<T>& v, const Key& key
   return false;
 }
 
+// The FSM kernel's form of slice_step (same samples): the state decisions as one instruction
+// stream with one place that draws the next shrink proposal's Philox block; in the per-state form
+// a warp whose chains sit in different states draws it at up to three places.
+template <typename T, int E>
+__device__ __forceinline__ bool slice_step_fsm(const SliceView<T>& v, const Key& key, SliceChain<T, E>& c, int& err) {
+  const T th = c.k == SL_LEFT ? c.L : c.k == SL_RIGHT ? c.R : c.th;
+  T xp[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) xp[e] = fma(th, c.u[e], c.x[e]);
+  T lpp = full_logp<T, E>(v.tg, xp);
+  if (!(lpp == lpp)) { lpp = neg_inf<T>(); err |= ERR_NONFINITE; }
+  c.nev += 1;
+  const bool inside = lpp > c.logy;
+  bool prop = false, fin = false;
+  if (c.k != SL_PROP) {  // stepping out: the left end while J lasts, then the right end while K lasts
+    const bool left = c.k == SL_LEFT;
+    if (inside) {
+      if (left) { c.L -= v.w; --c.J; } else { c.R += v.w; --c.K; }
+    }
+    if (!(inside && (left ? c.J : c.K) > 0)) {
+      if (left && c.K > 0) c.k = SL_RIGHT;
+      else prop = true;
+    }
+  } else {
+    c.s += 1;
+    if (inside) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) c.x[e] = xp[e];
+      c.lp = lpp;
+      fin = true;
+    } else {
+      if (th < T(0)) c.L = th; else c.R = th;
+      if (c.s >= kMaxShrinks) {  // keep x
+        err |= ERR_SHRINK_CAP;
+        fin = true;
+      } else {
+        prop = true;
+      }
+    }
+  }
+  if (prop) slice_propose<T, E>(v, key, c);
+  return fin;
+}
+
 template <typename T, int E>
 __device__ __forceinline__ void slice_load(const SliceView<T>& v, int64_t c, SliceChain<T, E>& s) {
   const int d = v.tg.d;
@@ -232,7 +276,7 @@ __global__ void __launch_bounds__(256) slice_fsm_kernel(SliceView<T> v, int budg
     for (int b = 0; b < budget; ++b) {
       ++steps;
       if (pf.q < D + 2 && s.t + 1 < v.n) slice_draw_block<T, E>(key, s.t + 1, D, pf);
-      if (slice_step<T, E>(v, key, s, err)) {
+      if (slice_step_fsm<T, E>(v, key, s, err)) {
         slice_finish<T, E>(v, c, s, ms);
         if (s.t == v.n) { s.k = SL_DONE; break; }
         slice_begin<T, E>(v, key, s, pf);
