@@ -130,7 +130,9 @@ typedef struct fsmc_tuning {
                             0 = auto                                                      */
   int steps_per_launch;  /* FSM states each chain advances per launch                    */
   int ring_slots;        /* ESS: pre-generated ellipse directions kept per chain         */
-  int threads_per_block; /* 32..256, multiple of 32                                      */
+  int threads_per_block; /* 32..256, multiple of 32; GP_REG: the CTA of one chain, 32, 64
+                            or 128 (0 auto: more warps when chains are too few to fill
+                            the SMs)                                                     */
   int profile_kernels;   /* 1: time every launch with CUDA events (see fsmc_stats)        */
   int generator;         /* ESS directions nu = L z: 0 auto, 1 CUDA cores, 2 tensor cores
                             (tcgen05; FP32 jobs with d <= 256)                            */

@@ -354,7 +354,8 @@ static void default_tuning(fsmc_job* j) {
     tu.ring_slots = 0;
     tu.generator = 0;
     tu.pipelined = 2;
-    tu.threads_per_block = 32;  // a warp per chain
+    // a CTA of 1, 2 or 4 warps per chain, more when there are too few chains to fill the SMs
+    if (!tu.threads_per_block) tu.threads_per_block = 32 * ess_block_auto_wpc(j->m, j->e->sms);
     if (!tu.steps_per_launch) tu.steps_per_launch = 8;
   } else if (j->algo == FSMC_ESS) {
     if (!tu.lanes_per_chain) {
@@ -564,6 +565,7 @@ EssBlockView<T> ess_block_view(const fsmc_job* j) {
   v.spill_stride = j->spill_stride;
   v.max_ctas = j->spill_stride ? j->spill_ctas : INT64_MAX;
   v.rows_smem = j->rows_smem;
+  v.wpc = j->tun.threads_per_block / 32;  // set by default_tuning when the caller left it open
   return v;
 }
 
@@ -736,8 +738,12 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
   if (j->dev) return fsmc_fail(FSMC_ESTATE, "tuning must be set before the first run");
   fsmc_tuning t = *tu;
   if (ess_block(j) && ((t.lanes_per_chain && t.lanes_per_chain != 32) || t.generator || t.ring_slots ||
-                       t.step_form == 2 || (t.threads_per_block && t.threads_per_block != 32)))
-    return fsmc_fail(FSMC_EINVAL, "GP_REG jobs run a warp per chain; only steps_per_launch is tunable");
+                       t.step_form == 2 ||
+                       (t.threads_per_block && t.threads_per_block != 32 && t.threads_per_block != 64 &&
+                        t.threads_per_block != 128)))
+    return fsmc_fail(FSMC_EINVAL,
+                     "GP_REG jobs run a CTA of 1, 2 or 4 warps per chain; only steps_per_launch and "
+                     "threads_per_block (32, 64, 128) are tunable");
   if (t.lanes_per_chain && t.lanes_per_chain != 1 && t.lanes_per_chain != 8 && t.lanes_per_chain != 16 &&
       t.lanes_per_chain != 32)
     return fsmc_fail(FSMC_EINVAL, "lanes_per_chain must be 1, 8, 16 or 32");

@@ -421,6 +421,7 @@ static int blk_wpc(int64_t m, int sms) {
   const int64_t want = (int64_t)sms * 16;
   return m >= want ? 1 : m * 2 >= want ? 2 : 4;
 }
+int ess_block_auto_wpc(int64_t m, int sms) { return blk_wpc(m, sms); }
 
 template <typename T, int WPC>
 static cudaError_t fsm_launch(const EssBlockView<T>& v, int budget, cudaStream_t st) {
@@ -467,7 +468,7 @@ static cudaError_t init_launch(const EssBlockView<T>& v, cudaStream_t st) {
     int dev = 0, sms = 0;                             \
     cudaGetDevice(&dev);                              \
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev); \
-    switch (blk_wpc(v.m, sms)) {                      \
+    switch (v.wpc ? v.wpc : blk_wpc(v.m, sms)) {      \
       case 1: return FN<T, 1>(__VA_ARGS__);           \
       case 2: return FN<T, 2>(__VA_ARGS__);           \
       default: return FN<T, 4>(__VA_ARGS__);          \

@@ -80,6 +80,7 @@ struct EssBlockView : ChainsView<T> {
   size_t spill_stride;   // its elements per CTA
   int64_t max_ctas;      // CTAs the scratch has room for (launches use at most this many)
   int rows_smem;         // covariance rows kept in shared memory (the rest in the scratch)
+  int wpc = 0;           // warps per chain's CTA: 1, 2 or 4; 0 chooses by chain count
 };
 
 template <typename T>
@@ -153,6 +154,8 @@ template <typename T>
 size_t gpreg_spill_elems(int n);
 template <typename T>
 int gpreg_smem_rows(int n);
+// warps per chain of a GP-regression job of m chains on `sms` SMs when the caller leaves it open
+int ess_block_auto_wpc(int64_t m, int sms);
 template <typename T>
 cudaError_t launch_ess_block_fsm(const EssBlockView<T>& v, int budget, cudaStream_t st);
 template <typename T>
