@@ -128,7 +128,7 @@ typedef struct fsmc_tuning {
                             32 < d <= 256), 16 = two chains per warp (ESS, 32 < d <= 512),
                             32 = chain-per-warp (ESS, NUTS; DR and slice with d > 32),
                             0 = auto                                                      */
-  int steps_per_launch;  /* FSM states each chain advances per launch                    */
+  int steps_per_launch;  /* FSM states each chain advances per launch (at most 2^24)       */
   int ring_slots;        /* ESS: pre-generated ellipse directions kept per chain         */
   int threads_per_block; /* 32..256, multiple of 32; GP_REG: the CTA of one chain, 32, 64
                             or 128 (0 auto: more warps when chains are too few to fill

@@ -765,6 +765,9 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
     return fsmc_fail(FSMC_EINVAL, "threads_per_block must be a multiple of 32 in [32, 256]");
   if (t.steps_per_launch < 0 || t.ring_slots < 0 || t.ring_slots > 4096)
     return fsmc_fail(FSMC_EINVAL, "negative steps / ring slots");
+  // a launch's state budget plus a sample's shrink offsets stays far inside int
+  if (t.steps_per_launch > (1 << 24))
+    return fsmc_fail(FSMC_EINVAL, "steps_per_launch must be at most 2^24");
   if (t.generator < 0 || t.generator > 2) return fsmc_fail(FSMC_EINVAL, "generator must be 0, 1 or 2");
   if (t.pipelined < 0 || t.pipelined > 2) return fsmc_fail(FSMC_EINVAL, "pipelined must be 0, 1 or 2");
   if (t.step_form < 0 || t.step_form > 2) return fsmc_fail(FSMC_EINVAL, "step_form must be 0, 1 or 2");
