@@ -244,10 +244,11 @@ __device__ __forceinline__ float ess_gp32_group(const float (&xs)[E], const floa
 // The likelihood.  A lane's term a (the sum of its groups' log2 values) is added over the chain
 // group.  While no group of the warp overflowed, every group's log2 is at most 126, so a <=
 // 126 ceil(E / 8); with 32 lanes the terms are then rounded to the fixed-point grid 2^-kFx (kFx
-// = 19 up to eight coordinates per lane: error <= 2^-20 per lane; 32 of them sum below 2^31,
-// exactly, in a 32-bit integer) and added by one warp reduction (redux.sync) instead of a
-// five-level shuffle tree; the sum's rounding to single precision (half an ulp, 2^-18 near 128)
-// stays the larger error, as it is in the tree.  Chain groups of fewer lanes add by the tree.
+// = 19 up to eight coordinates per lane: error <= 2^-20 per lane, about 2^-18 root-mean-square
+// over 32 lanes; 32 of them sum below 2^31, exactly, in a 32-bit integer) and added by one warp
+// reduction (redux.sync) instead of a five-level shuffle tree.  The tree's five roundings and the
+// sum's own rounding to single precision (half an ulp: 2^-18 to 2^-17 for sums of 64 to 256) are
+// errors of the same order.  Chain groups of fewer lanes add by the tree.
 // When some group of the warp overflowed (or is NaN) the whole warp takes the branch in which
 // each lane recomputes its overflowed groups in the per-coordinate form and the lanes add by the
 // tree.
