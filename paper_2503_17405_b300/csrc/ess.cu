@@ -568,6 +568,24 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
   }
 }
 
+// Moments-only single-precision GP-logit jobs keep each lane's running sums in a shared-memory slot
+// of kEssMomSlot(E) floats, [4][E] (sum, compensation, sum of squares, compensation): an even
+// stride, so that coordinate pairs move as 8-byte words (two wavefronts per warp access, the
+// minimum for 8-byte words).
+template <int E>
+constexpr int kEssMomSlot = 4 * E + 2;
+
+// The compensated (Kahan) update of kahan_add for a coordinate pair, in packed single-precision
+// instructions: x - c and (t - s) - y are taken as fma(c, -1, x) and fma(y, -1, t - s) (exact
+// negations), each one correctly rounded operation.
+__device__ __forceinline__ void kahan_add2(float2& sum, float2& comp, float2 x) {
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  const float2 y = __ffma2_rn(comp, neg1, x);
+  const float2 t = __fadd2_rn(sum, y);
+  comp = __ffma2_rn(y, neg1, __ffma2_rn(sum, neg1, t));
+  sum = t;
+}
+
 // Single-precision GP-logit: the lanes hold only the sign-folded coordinates xs = -s x and
 // ns = -s nu (exact; bit e of smask marks the coordinates whose sign is flipped), so the
 // likelihood is one multiply-add per coordinate (ess_loglik_gp32), the accepted state is
@@ -736,6 +754,17 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
           const int k = e * G + lane;
           if (FULL || k < d) dst[k] = x[e];
         }
+      } else if constexpr (MOMC && E % 2 == 0) {
+        // the pair (e, e + 1) of each of the four sums as one 8-byte word of the slot
+#pragma unroll
+        for (int e = 0; e < E; e += 2) {
+          const float2 xv = make_float2(x[e], x[e + 1]);
+          float2* sp = reinterpret_cast<float2*>(mslot + e);
+          float2 s1 = sp[0], c1 = sp[E / 2], s2 = sp[E], c2 = sp[3 * E / 2];
+          kahan_add2(s1, c1, xv);
+          kahan_add2(s2, c2, __fmul2_rn(xv, xv));
+          sp[0] = s1; sp[E / 2] = c1; sp[E] = s2; sp[3 * E / 2] = c2;
+        }
       } else {
         ess_emit<float, G, E, FULL>(v, c, t, lane, x, MOMC ? mslot : nullptr);
       }
@@ -812,7 +841,7 @@ template <typename T, int G, int E, int MODE>
 constexpr bool kEssPrefetch = sizeof(T) == 4 && MODE == 2 && G == 32 && E % 4 == 0;
 
 // MOMC (with the prefetch form, moments-only jobs): each thread's running sums in a dynamic
-// shared-memory slot of 4 E + 1 floats (odd stride: a warp's slots start in 32 banks).
+// shared-memory slot of kEssMomSlot<E> floats.
 template <typename T, int G, int E, int MODE, bool MOMC = false>
 __global__ void __launch_bounds__(256, (ess_min_blocks<T, G, E, MODE>()))
 ess_fsm_kernel(EssView<T> v, int budget) {
@@ -824,7 +853,7 @@ ess_fsm_kernel(EssView<T> v, int budget) {
     float* pf = pf_rows[threadIdx.x / 32];
     if constexpr (MOMC) {
       extern __shared__ __align__(16) float ess_mom_smem[];
-      float* mslot = ess_mom_smem + (size_t)threadIdx.x * (4 * E + 1);
+      float* mslot = ess_mom_smem + (size_t)threadIdx.x * kEssMomSlot<E>;
       for (int64_t c = group; c < v.m; c += ngroups)
         ess_advance_chain_gp<G, E, true, true, true>(v, c, budget, lane, pf, mslot);
     } else {
@@ -1387,7 +1416,7 @@ static cudaError_t fsm_launch(const EssView<T>& v, int budget, int threads, cuda
   if constexpr (kEssGpFast<T, E>) {
     if (ess_ring_folded(v)) {
       if (v.tg.d == E * G) {
-        const size_t momb = (size_t)threads * (4 * E + 1) * sizeof(float);
+        const size_t momb = (size_t)threads * kEssMomSlot<E> * sizeof(float);
         if (kEssPrefetch<T, G, E, 2> && !v.out && momb <= 48 * 1024)
           ess_fsm_kernel<T, G, E, 2, true><<<(unsigned)blocks, threads, momb, st>>>(v, budget);
         else
