@@ -568,12 +568,16 @@ __device__ __forceinline__ void ess_advance_chain_generic(const EssView<T>& v, i
   }
 }
 
-// Moments-only single-precision GP-logit jobs keep each lane's running sums in a shared-memory slot
-// of kEssMomSlot(E) floats, [4][E] (sum, compensation, sum of squares, compensation): an even
-// stride, so that coordinate pairs move as 8-byte words (two wavefronts per warp access, the
-// minimum for 8-byte words).
+// Moments-only single-precision GP-logit jobs sum each lane's samples in blocks of up to
+// kEssMomBlock: the plain partial sums of x and x^2 over the current block sit in a shared-memory
+// slot of kEssMomSlot(E) floats, [2][E], and are folded into the compensated sums in device memory
+// (v.mom: sum, compensation, sum of squares, compensation) when the block is full and when the
+// chain leaves the launch.  A partial of 16 terms has relative error ~1e-6, well inside what the
+// compensated sum keeps.  An even stride, so that coordinate pairs move as 8-byte words (two
+// wavefronts per warp access, the minimum for 8-byte words).
 template <int E>
-constexpr int kEssMomSlot = 4 * E + 2;
+constexpr int kEssMomSlot = 2 * E + 2;
+constexpr int kEssMomBlock = 16;
 
 // The compensated (Kahan) update of kahan_add for a coordinate pair, in packed single-precision
 // instructions: x - c and (t - s) - y are taken as fma(c, -1, x) and fma(y, -1, t - s) (exact
@@ -595,8 +599,9 @@ __device__ __forceinline__ void kahan_add2(float2& sum, float2& comp, float2 x) 
 // group's shared-memory row `pf` (cp.async, 16 bytes per copy, L2 only) when sample t starts,
 // so that its ring row is on chip when t + 1 starts.  Only samples below gen_hi, whose
 // directions were generated before this launch, are copied.
-// MOMC (moments-only jobs): the lane's running sums are held in its shared-memory slot mslot
-// ([4][E]) while the chain advances: loaded here, written back at the end.
+// MOMC (moments-only jobs): the lane's partial sums over the current block of samples are held
+// in its shared-memory slot mslot (kEssMomSlot) and folded into the compensated sums in device
+// memory every kEssMomBlock samples and when the chain leaves the launch.
 // Loop form: every pass evaluates one angle (one FSM state); the state that follows is set up
 // in the branch the decision takes -- after DONE the next sample's INIT (threshold, initial
 // angle, bracket), after a rejection the SHRINK (bracket end, new angle) -- so a state costs
@@ -607,14 +612,33 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
                                                      float* pf = nullptr, float* mslot = nullptr) {
   static_assert(!PF || (G == 32 && FULL && E % 4 == 0), "prefetch needs full 32-lane rows");
   const int d = FULL ? E * G : v.tg.d;
+  int mom_pending = 0;  // samples in the current block of partial sums (MOMC)
+  // the block's partial sums into the compensated sums in device memory, the partials cleared
+  auto mom_flush = [&]() {
+    if constexpr (MOMC && E % 2 == 0) {
+      float* m0 = v.mom + (size_t)c * d + lane;
+#pragma unroll
+      for (int e = 0; e < E; e += 2) {
+        float2* sp = reinterpret_cast<float2*>(mslot + e);
+        const size_t k0 = (size_t)e * G, k1 = k0 + G;
+        float2 s1 = make_float2(m0[k0], m0[k1]);
+        float2 c1 = make_float2(m0[v.mom_stride + k0], m0[v.mom_stride + k1]);
+        float2 s2 = make_float2(m0[2 * v.mom_stride + k0], m0[2 * v.mom_stride + k1]);
+        float2 c2 = make_float2(m0[3 * v.mom_stride + k0], m0[3 * v.mom_stride + k1]);
+        kahan_add2(s1, c1, sp[0]);
+        kahan_add2(s2, c2, sp[E / 2]);
+        m0[k0] = s1.x; m0[k1] = s1.y;
+        m0[v.mom_stride + k0] = c1.x; m0[v.mom_stride + k1] = c1.y;
+        m0[2 * v.mom_stride + k0] = s2.x; m0[2 * v.mom_stride + k1] = s2.y;
+        m0[3 * v.mom_stride + k0] = c2.x; m0[3 * v.mom_stride + k1] = c2.y;
+        sp[0] = make_float2(0.f, 0.f);
+        sp[E / 2] = make_float2(0.f, 0.f);
+      }
+    }
+  };
   if constexpr (MOMC) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int k = e * G + lane;
-        if (FULL || k < d) mslot[q * E + e] = v.mom[q * v.mom_stride + (size_t)c * d + k];
-      }
+    for (int e = 0; e < 2 * E; ++e) mslot[e] = 0.f;
   }
   const int D = (d + 3) / 4;  // Philox blocks of z (four normals each)
   const unsigned gmask = group_mask<G>();
@@ -755,15 +779,18 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
           if (FULL || k < d) dst[k] = x[e];
         }
       } else if constexpr (MOMC && E % 2 == 0) {
-        // the pair (e, e + 1) of each of the four sums as one 8-byte word of the slot
+        // the pair (e, e + 1) of each sum as one 8-byte word of the slot: into the block's
+        // partial sums, which join the compensated sums every kEssMomBlock samples
 #pragma unroll
         for (int e = 0; e < E; e += 2) {
           const float2 xv = make_float2(x[e], x[e + 1]);
           float2* sp = reinterpret_cast<float2*>(mslot + e);
-          float2 s1 = sp[0], c1 = sp[E / 2], s2 = sp[E], c2 = sp[3 * E / 2];
-          kahan_add2(s1, c1, xv);
-          kahan_add2(s2, c2, __fmul2_rn(xv, xv));
-          sp[0] = s1; sp[E / 2] = c1; sp[E] = s2; sp[3 * E / 2] = c2;
+          sp[0] = __fadd2_rn(sp[0], xv);
+          sp[E / 2] = __ffma2_rn(xv, xv, sp[E / 2]);
+        }
+        if (++mom_pending == kEssMomBlock) {
+          mom_flush();
+          mom_pending = 0;
         }
       } else {
         ess_emit<float, G, E, FULL>(v, c, t, lane, x, MOMC ? mslot : nullptr);
@@ -790,13 +817,7 @@ __device__ __forceinline__ void ess_advance_chain_gp(const EssView<float>& v, in
     __syncwarp();
   }
   if constexpr (MOMC) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int k = e * G + lane;
-        if (FULL || k < d) v.mom[q * v.mom_stride + (size_t)c * d + k] = mslot[q * E + e];
-      }
+    if (mom_pending) mom_flush();
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
