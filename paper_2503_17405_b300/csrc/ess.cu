@@ -1107,7 +1107,7 @@ __global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_sync_kern
       const int slot = iter % 3;
       if (threadIdx.x == 0 && blk_active) *(volatile unsigned*)&active_cnt[slot] = 1u;
       if (!grid_sync(bar, v.err)) return;
-      const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+      const unsigned total = read_after_grid_sync(&active_cnt[slot]);
       if (leader) {
         active_cnt[(iter + 2) % 3] = 0;  // last read one iteration ago, next written in two
         if (!first) *iterations += 1;    // one loop-body iteration of the batched while
@@ -1146,7 +1146,7 @@ __global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_sync_list
     }
     while (true) {
       if (!grid_sync(bar, v.err)) return;
-      const unsigned n_act = *(volatile unsigned*)&cnt[it % 3];
+      const unsigned n_act = read_after_grid_sync(&cnt[it % 3]);
       const int* in = lists + (size_t)(it & 1) * v.m;
       if (leader) cnt[(it + 2) % 3] = 0;
       ++it;

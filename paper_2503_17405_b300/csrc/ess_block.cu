@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(32 * WPC) ess_block_sync_kernel(EssBlockView<T
       const int slot = iter % 3;
       if (threadIdx.x == 0 && mine) atomicAdd(&active_cnt[slot], mine);
       if (!grid_sync(bar, v.err)) return;
-      const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+      const unsigned total = read_after_grid_sync(&active_cnt[slot]);
       if (leader) {
         active_cnt[(iter + 2) % 3] = 0;
         *iterations += 1;

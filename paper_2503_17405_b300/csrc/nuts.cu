@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(256) nuts_sync_kernel(NutsView<T> v, int t_beg
     const int slot = iter % 3;
     if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
     if (!grid_sync<kBarFlag>(bar, v.err)) return false;
-    total = *(volatile unsigned*)&active_cnt[slot];
+    total = read_after_grid_sync(&active_cnt[slot]);
     if (leader) active_cnt[(iter + 2) % 3] = 0;
     ++iter;
     return true;

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) slice_sync_kernel(SliceView<T> v, int t_b
         const int slot = iter % 3;
         if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
         if (!grid_sync(bar, v.err)) return;
-        const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+        const unsigned total = read_after_grid_sync(&active_cnt[slot]);
         if (leader) {
           active_cnt[(iter + 2) % 3] = 0;
           *iterations += 1;
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(128) slice_sync_warp_kernel(SliceView<T> v, in
         const int slot = iter % 3;
         if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
         if (!grid_sync(bar, v.err)) return;
-        const unsigned total = *(volatile unsigned*)&active_cnt[slot];
+        const unsigned total = read_after_grid_sync(&active_cnt[slot]);
         if (leader) {
           active_cnt[(iter + 2) % 3] = 0;
           *iterations += 1;
