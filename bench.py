@@ -334,11 +334,14 @@ def run_ours(args, rank, world):
     value = job_throughput(world, args.steps, m, n, total_ms)
 
     # synchronised program (Alg. 6) on the same workload, fewer steps: it is the slow baseline.
-    # ESS runs each of its three forms (sweep, compacted list, conditional graph) on a job of its
-    # own and the fastest is the baseline; the others run their one (sweep) form.
+    # ESS runs each of its forms (sweep, compacted list, conditional graph, and for single-precision
+    # GP-logit jobs the resident sweep) on a job of its own and the fastest is the baseline; the
+    # others run their one (sweep) form.
     sync = None
     if not args.no_sync:
         forms = [1, 2, 3] if cfg["algo"] == "ess" and w["kind"] != "gp_reg" else [0]
+        if cfg["algo"] == "ess" and w["kind"] == "gp_logit" and cfg["prec"] == "fp32" and w["d"] in (32, 64, 128, 256):
+            forms.append(4)  # the resident sweep
         per_form = {}
         for f in forms:
             if f:
@@ -364,7 +367,7 @@ def run_ours(args, rank, world):
                 sms.append(ms)
             ms = sum(sms) / len(sms)
             iters = sst["sync_iterations"]
-            per_form[{0: "sweep", 1: "sweep", 2: "list", 3: "graph"}[f]] = {
+            per_form[{0: "sweep", 1: "sweep", 2: "list", 3: "graph", 4: "resident"}[f]] = {
                 "value": m * n / (ms / 1e3), "ms_per_step": ms, "sync_iterations": iters,
                 "sync_kernel_ms": sst["kernel_ms"][2], "refill_ms": sst["kernel_ms"][0],
                 # the synchronised kernels' time per loop step (the loop-body iterations plus the

@@ -159,8 +159,13 @@ typedef struct fsmc_tuning {
                             iteration; 2 list: the chains still in the loop kept in a compacted
                             list shared by the whole grid, a grid barrier per iteration; 3 graph:
                             the list iterations as kernel launches in a CUDA graph whose while
-                            loops (conditional nodes) test their conditions on the device.
-                            DR, slice and NUTS jobs run the sweep form                         */
+                            loops (conditional nodes) test their conditions on the device; 4
+                            resident: the sweep with every chain's state and current direction
+                            kept on chip (registers, shared memory) for the whole launch --
+                            single-precision GP-logit jobs, 32 lanes per chain, d of 32, 64, 128
+                            or 256 (EINVAL otherwise), at most 8 chains per warp of the grid (the
+                            run fails with ECUDA beyond).  DR, slice and NUTS jobs run the sweep
+                            form                                                               */
 } fsmc_tuning;
 
 /* Run statistics (Sec. 4): loop-body counts N_ij and what each mode spent. */

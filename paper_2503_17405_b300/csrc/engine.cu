@@ -358,6 +358,7 @@ static void default_tuning(fsmc_job* j) {
     if (!tu.threads_per_block) tu.threads_per_block = 32 * ess_block_auto_wpc(j->m, j->e->sms);
     if (!tu.steps_per_launch) tu.steps_per_launch = 8;
   } else if (j->algo == FSMC_ESS) {
+    if (!tu.lanes_per_chain && tu.sync_form == 4) tu.lanes_per_chain = 32;  // the resident form's layout
     if (!tu.lanes_per_chain) {
       // chain-per-warp when one chain's likelihood is wide (d >= 64) or when there are too
       // few chains to fill the machine one per thread
@@ -777,7 +778,14 @@ extern "C" fsmc_status fsmc_job_set_tuning(fsmc_job* j, const fsmc_tuning* tu) {
     return fsmc_fail(FSMC_EINVAL, "the tensor-core generator needs an FP32 ESS job with d <= 256");
   if (t.barrier_spin_limit < 0 || t.barrier_test_missing < 0 || t.barrier_test_missing > 1)
     return fsmc_fail(FSMC_EINVAL, "barrier_spin_limit must be >= 0 and barrier_test_missing 0 or 1");
-  if (t.sync_form < 0 || t.sync_form > 3) return fsmc_fail(FSMC_EINVAL, "sync_form must be 0, 1, 2 or 3");
+  if (t.sync_form < 0 || t.sync_form > 4) return fsmc_fail(FSMC_EINVAL, "sync_form must be 0, 1, 2, 3 or 4");
+  if (t.sync_form == 4 &&
+      !(j->algo == FSMC_ESS && !ess_block(j) && j->prec == FSMC_FP32 && j->tg->kind == FSMC_TGT_GP_LOGIT &&
+        (j->d == 32 || j->d == 64 || j->d == 128 || j->d == 256) &&
+        (t.lanes_per_chain == 0 || t.lanes_per_chain == 32) && t.step_form != 2))
+    return fsmc_fail(FSMC_EINVAL,
+                     "sync_form 4 (resident) needs a single-precision GP-logit ESS job, 32 lanes per chain, "
+                     "d of 32, 64, 128 or 256");
   if (t.sync_form == 3 && t.barrier_test_missing)
     return fsmc_fail(FSMC_EINVAL, "the graph form of the synchronised program has no grid barrier");
   j->tun = t;

@@ -1120,6 +1120,175 @@ __global__ void __launch_bounds__(256, (ess_sync_min_blocks<T>())) ess_sync_kern
   if (err && lane == 0) atomicOr(v.err, err);
 }
 
+// One visit of a resident chain: INIT (first) or SHRINK, the proposal's likelihood, DONE -- the
+// arithmetic of ess_sync_visit on the shared-memory copies.  sl: the chain's slot (ns, the
+// uniforms, the scalars).  Returns true while sample t is still open.
+template <int E>
+__device__ __forceinline__ bool ess_res_visit(const EssView<float>& v, int64_t c, int t, bool first, float (&xs)[E],
+                                              float* sl, uint32_t smask, int lane, int D, int& err) {
+  constexpr int G = 32, d = 32 * E;
+  float* ua = sl + 32 * E;
+  float* sc = ua + 32;
+  const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+  float ns[E];
+  float logy, th, thmin, thmax;
+  int s;
+  if (first) {  // INIT: the sample's direction from its ring row, its uniforms, the bracket
+    const float* src = v.nu + ((size_t)c * v.W + (t % v.W)) * v.dstride;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      ns[e] = src[e * G + lane];
+      sl[e * G + lane] = ns[e];
+    }
+    const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + lane));
+    const float a = Conv<float>::u(r.w0, r.w1);
+    ua[lane] = a;
+    const float a0 = __shfl_sync(0xffffffffu, a, 0);
+    const float b0 = __shfl_sync(0xffffffffu, Conv<float>::u(r.w2, r.w3), 0);
+    logy = ess_threshold<float>(sc[4], Conv<float>::log_of(a0));
+    th = float(kTwoPi) * b0;
+    thmin = th - float(kTwoPi);
+    thmax = th;
+    s = 0;
+  } else {      // SHRINK
+#pragma unroll
+    for (int e = 0; e < E; ++e) ns[e] = sl[e * G + lane];
+    logy = sc[0]; th = sc[1]; thmin = sc[2]; thmax = sc[3]; s = __float_as_int(sc[5]);
+    if (th < 0.f) thmin = th; else thmax = th;
+    const int off = 1 + s;
+    float u;
+    if (off < 32) {
+      u = ua[off];
+    } else {
+      const P4 r = key.block((uint32_t)t, 0, (uint32_t)(D + off));
+      u = Conv<float>::u(r.w0, r.w1);
+    }
+    th = thmin + (thmax - thmin) * u;
+    ++s;
+  }
+  float sn, cs;
+  ess_sincos<float>(th, sn, cs);
+  float ellp = ess_loglik_gp32<G, E, true>(xs, ns, cs * kLog2ef, sn * kLog2ef, lane, d, 0xffffffffu);
+  if (!(ellp == ellp)) { ellp = neg_inf<float>(); err |= ERR_NONFINITE; }
+  const bool accept = ellp > logy;
+  __syncwarp();  // every lane has read the slot's scalars
+  if (accept || s >= kMaxShrinks) {  // DONE
+    float x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float xn = accept ? fmaf(xs[e], cs, ns[e] * sn) : xs[e];
+      xs[e] = xn;
+      x[e] = flip_sign(xn, smask, e);
+    }
+    if (!accept) err |= ERR_SHRINK_CAP;
+    ess_emit<float, G, E, true>(v, c, t, lane, x);
+    if (lane == 0) {
+      if (accept) sc[4] = ellp;
+      v.counts[(size_t)c * v.n + t] = s;
+      if (t + 1 == v.n) atomicAdd(v.chains_done, 1);
+    }
+    return false;
+  }
+  if (lane == 0) {
+    sc[0] = logy; sc[1] = th; sc[2] = thmin; sc[3] = thmax; sc[5] = __int_as_float(s);
+  }
+  return true;
+}
+
+// Resident form of the sweep (single-precision GP-logit, 32-lane groups, full rows, d = 32 E):
+// each group keeps its chains on chip for the whole launch -- the sign-folded state xs of every
+// chain in registers (xs[slot][E]), the current sample's sign-folded direction ns, the sample's
+// Philox uniforms (lane l: draw D + l, the uniform a; lane 0 also b) and the bracket in shared
+// memory -- so a loop-body visit reads no device memory; the direction of sample t is read from
+// its ring row once, at its INIT.  Same visits in the same order as the sweep (same samples, loop
+// counts and iteration counts); the state goes back to device memory when the launch ends.
+// Slots: chain group + j ngroups for j < kEssResSlots; a launch needs m <= kEssResSlots ngroups.
+constexpr int kEssResSlots = 8;
+constexpr int kEssResScalars = 8;  // per slot: logy, th, thmin, thmax, ell, s, pad, visits
+
+template <int E>
+__host__ __device__ constexpr size_t ess_res_slot_floats() { return (size_t)32 * E + 32 + kEssResScalars; }
+
+template <int E>
+__global__ void __launch_bounds__(256, 2) ess_sync_resident_kernel(EssView<float> v, int t_begin, int t_end,
+                                                                   GridBarrier bar, unsigned* active_cnt,
+                                                                   unsigned long long* iterations) {
+  constexpr int G = 32, d = 32 * E;
+  extern __shared__ __align__(16) float res_smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const int D = (d + 3) / 4;
+  float* wbase = res_smem + (size_t)warp * kEssResSlots * ess_res_slot_floats<E>();
+  __shared__ unsigned blk_active;
+  int iter = 0, err = 0;
+  uint32_t smask = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (v.tg.vec[e * G + lane] > 0.f) smask |= 1u << e;
+  float xs[kEssResSlots][E];
+#pragma unroll
+  for (int j = 0; j < kEssResSlots; ++j) {
+    const int64_t c = group + (int64_t)j * ngroups;
+    float* sl = wbase + (size_t)j * ess_res_slot_floats<E>();
+    if (lane == 0) sl[32 * E + 32 + 7] = __int_as_float(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) xs[j][e] = c < v.m ? flip_sign(v.x[(size_t)c * d + e * G + lane], smask, e) : 0.f;
+    if (lane == 0 && c < v.m) sl[32 * E + 32 + 4] = v.ell[c];
+  }
+  __syncwarp();
+  for (int t = t_begin; t < t_end; ++t) {
+    bool first = true;
+    unsigned live = 0;
+    while (true) {
+      if (threadIdx.x == 0) blk_active = 0;
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kEssResSlots; ++j) {
+        const int64_t c = group + (int64_t)j * ngroups;
+        if (c < v.m && (first || ((live >> j) & 1u))) {
+          float* sl = wbase + (size_t)j * ess_res_slot_floats<E>();
+          if (lane == 0) sl[32 * E + 39] = __int_as_float(__float_as_int(sl[32 * E + 39]) + 1);
+          if (ess_res_visit<E>(v, c, t, first, xs[j], sl, smask, lane, D, err)) live |= 1u << j;
+          else live &= ~(1u << j);
+        }
+      }
+      if (live && lane == 0) atomicAdd(&blk_active, 1u);
+      __syncthreads();
+      const int slot = iter % 3;
+      if (threadIdx.x == 0 && blk_active) *(volatile unsigned*)&active_cnt[slot] = 1u;
+      if (!grid_sync(bar, v.err)) return;
+      const unsigned total = read_after_grid_sync(&active_cnt[slot]);
+      if (leader) {
+        active_cnt[(iter + 2) % 3] = 0;
+        if (!first) *iterations += 1;
+      }
+      ++iter;
+      first = false;
+      if (total == 0) break;
+    }
+  }
+  // every chain finished samples t_begin .. t_end - 1: its state back to device memory
+#pragma unroll
+  for (int j = 0; j < kEssResSlots; ++j) {
+    const int64_t c = group + (int64_t)j * ngroups;
+    if (c < v.m) {
+      const float* sl = wbase + (size_t)j * ess_res_slot_floats<E>();
+#pragma unroll
+      for (int e = 0; e < E; ++e) v.x[(size_t)c * d + e * G + lane] = flip_sign(xs[j][e], smask, e);
+      if (lane == 0) {
+        v.ell[c] = sl[32 * E + 32 + 4];
+        v.t[c] = t_end;
+        v.k[c] = ESS_INIT;
+        v.steps[c] += (long long)__float_as_int(sl[32 * E + 39]);
+      }
+    }
+  }
+  if (err && lane == 0) atomicOr(v.err, err);
+}
+
 // List form.  Iteration `it` (counted over the whole launch) appends the chains that stay in the
 // loop to list it % 2 with counter it % 3; after the barrier every group reads that counter and
 // takes list entries i = group, group + ngroups, ...  The leader clears counter (it + 2) % 3,
@@ -1456,6 +1625,29 @@ template <typename T, int G, int E>
 static cudaError_t sync_launch(const EssView<T>& v, int t0, int t1, GridBarrier bar,
                                unsigned* active_cnt, unsigned long long* iters, int threads, int form,
                                int* lists, cudaStream_t st) {
+  if (form == 4) {  // resident sweep: single-precision GP-logit, 32 lanes, d = 32 E, E <= 8
+    if constexpr (sizeof(T) == 4 && G == 32 && E <= 8) {
+      if (!ess_ring_folded(v) || v.tg.d != 32 * E) return cudaErrorInvalidValue;
+      auto kern = ess_sync_resident_kernel<E>;
+      const size_t smem = (size_t)8 * kEssResSlots * ess_res_slot_floats<E>() * sizeof(float);
+      cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+      if (e != cudaSuccess) return e;
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int64_t need = (v.m + 8 * kEssResSlots - 1) / (8 * kEssResSlots);  // blocks for m chains
+      if (per_sm < 1 || need > (int64_t)per_sm * sms) return cudaErrorInvalidValue;
+      const int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (v.m + 7) / 8);
+      EssView<float> vv = v;
+      void* args[] = {(void*)&vv, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active_cnt, (void*)&iters};
+      return cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)blocks), dim3(256), args, smem, st);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   void* kern = form == 2 ? (void*)ess_sync_list_kernel<T, G, E, false> : (void*)ess_sync_kernel<T, G, E, false>;
   if constexpr (kEssGpFast<T, E>) {
     if (ess_ring_folded(v))

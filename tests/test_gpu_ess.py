@@ -328,6 +328,39 @@ def test_synchronised_forms_equal_the_fsm(eng, form, case):
     b.close()
 
 
+@pytest.mark.parametrize("d,m,n", [(256, 300, 64), (256, 16384, 12), (64, 1000, 40)])
+def test_resident_synchronised_form_equals_the_fsm(eng, d, m, n):
+    # the resident sweep (sync_form 4: every chain's state and current direction on chip for the
+    # launch) runs the sweep's visits: the FSM's samples and loop counts bit for bit, max_j N_ij
+    # iterations per sample; 16384 chains fill seven of the eight slots of every warp of the grid
+    w = W.gp_logit(d)
+    x0 = W.x0_normal(m, d, scale=0.1)
+    tu = {"lanes_per_chain": 32}
+    a = _run(eng, w, m, n, x0, "fp32", "fsm", tuning=tu)
+    b = _run(eng, w, m, n, x0, "fp32", "sync", tuning={**tu, "sync_form": 4})
+    ca, _, _ = a.loop_counts()
+    cb, _, _ = b.loop_counts()
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(a.samples(), b.samples())
+    st = b.stats()
+    assert st["sync_iterations"] == int(cb.max(0).sum())
+    assert st["error_word"] == 0
+    a.close()
+    b.close()
+
+
+def test_resident_synchronised_form_refuses_other_jobs(eng):
+    from paper_2503_17405_b300 import fsmc
+    w = W.gauss_conj(16)
+    tg = eng.target("gauss_conj", 16, w["params"])
+    with pytest.raises(fsmc.FsmcError, match="sync_form 4"):
+        eng.job(tg, "ess", 64, 10, x0=W.x0_normal(64, 16), prec="fp64", tuning={"sync_form": 4})
+    g = W.gp_logit(256)
+    tg2 = eng.target("gp_logit", 256, g["params"])
+    with pytest.raises(fsmc.FsmcError, match="sync_form 4"):
+        eng.job(tg2, "ess", 64, 10, x0=W.x0_normal(64, 256), prec="fp64", tuning={"sync_form": 4})
+
+
 def test_synchronised_sweep_with_more_chains_than_its_live_masks_cover(eng):
     # the sweep form keeps a 32-bit mask of live chains per chain group while groups have at most
     # 32 chains; 120 000 chains at 32 lanes exceed that (about 3 600 resident groups), so the kernel
