@@ -460,6 +460,64 @@ __global__ void __launch_bounds__(256) dr_sync_kernel(DrView<T> v, int t_begin, 
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   __shared__ unsigned blk_active;
   int iter = 0, err = 0;
+  if (stride >= v.m) {
+    // At most one chain per thread (the grid is sized to cover the job when it fits): the chain's
+    // state stays in the thread's registers for the whole launch -- loaded once, stored once --
+    // instead of a load and a store around every stage; same steps in the same order.
+    const int64_t c = c_first;
+    const bool has = c < v.m;
+    T x[E], y1[E], y2[E];
+    T lp = T(0), lp1 = T(0), lp2 = T(0);
+    DrCache<T> cc{};
+    if (has) {
+      dr_load<T, E>(v, c, x, y1, y2);
+      lp = v.lp[c]; lp1 = v.lpy[c]; lp2 = v.lpy[v.m + c];
+      cc = dr_cache_load<T>(v, c);
+    }
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    long long steps = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      int kc = 0;  // next stage of this chain's sample t
+      for (int k = 0; k < v.n_stages; ++k) {
+        if (threadIdx.x == 0) blk_active = 0;
+        __syncthreads();
+        unsigned mine = 0;
+        if (has && kc == k) {
+          ++steps;
+          if (dr_step<T, E>(v, key, t, k, x, lp, y1, lp1, y2, lp2, cc, err)) {
+            dr_emit<T, E>(v, c, t, x);
+            v.counts[(size_t)c * v.n + t] = k + 1;
+            kc = v.n_stages;
+            if (t + 1 == v.n) atomicAdd(v.chains_done, 1);
+          } else {
+            kc = k + 1;
+            mine = 1;
+          }
+        }
+        if (mine) atomicAdd(&blk_active, 1u);
+        __syncthreads();
+        const int slot = iter % 3;
+        if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+        if (!grid_sync(bar, v.err)) return;
+        const unsigned total = read_after_grid_sync(&active_cnt[slot]);
+        if (leader) {
+          active_cnt[(iter + 2) % 3] = 0;
+          *iterations += 1;
+        }
+        ++iter;
+        if (total == 0) break;
+      }
+    }
+    if (has) {
+      dr_store<T, E>(v, c, x, y1, y2, 0);
+      v.lp[c] = lp;
+      v.t[c] = t_end;
+      v.k[c] = 0;
+      v.steps[c] += steps;
+    }
+    if (err) atomicOr(v.err, err);
+    return;
+  }
   for (int t = t_begin; t < t_end; ++t) {
     for (int k = 0; k < v.n_stages; ++k) {
       if (threadIdx.x == 0) blk_active = 0;
