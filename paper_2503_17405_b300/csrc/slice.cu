@@ -301,6 +301,57 @@ __global__ void __launch_bounds__(256) slice_sync_kernel(SliceView<T> v, int t_b
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   __shared__ unsigned blk_active;
   int iter = 0, err = 0;
+  if (stride >= v.m) {
+    // At most one chain per thread (the grid covers the job when it fits): the chain's state
+    // stays in the thread's registers for the whole launch instead of a device-memory load and
+    // store around every loop iteration; same steps in the same order.
+    const int64_t c = c_first;
+    const bool has = c < v.m;
+    SliceChain<T, E> s;
+    if (has) slice_load<T, E>(v, c, s);
+    const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+    long long steps = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      if (has) {
+        SlicePrefetch<T, E> pf;
+        pf.q = 0;
+        slice_begin<T, E>(v, key, s, pf);
+      }
+      for (int phase = SL_LEFT; phase <= SL_PROP; ++phase) {
+        while (true) {
+          if (threadIdx.x == 0) blk_active = 0;
+          __syncthreads();
+          unsigned mine = 0;
+          if (has && s.k == phase) {
+            ++steps;
+            if (slice_step<T, E>(v, key, s, err)) {
+              slice_finish<T, E>(v, c, s);
+              s.k = SL_DONE;
+            }
+            if (s.k == phase) mine = 1;
+          }
+          if (mine) atomicAdd(&blk_active, 1u);
+          __syncthreads();
+          const int slot = iter % 3;
+          if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+          if (!grid_sync(bar, v.err)) return;
+          const unsigned total = read_after_grid_sync(&active_cnt[slot]);
+          if (leader) {
+            active_cnt[(iter + 2) % 3] = 0;
+            *iterations += 1;
+          }
+          ++iter;
+          if (total == 0) break;
+        }
+      }
+    }
+    if (has) {
+      slice_store<T, E>(v, c, s);
+      v.steps[c] += steps;
+    }
+    if (err) atomicOr(v.err, err);
+    return;
+  }
   for (int t = t_begin; t < t_end; ++t) {
     for (int64_t c = c_first; c < v.m; c += stride) {
       SliceChain<T, E> s;
