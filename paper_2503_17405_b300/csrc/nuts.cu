@@ -980,6 +980,114 @@ __global__ void __launch_bounds__(256) nuts_sync_kernel(NutsView<T> v, int t_beg
   }
 }
 
+// Synchronised kernel for logistic regression with the batched gradient: the program of
+// nuts_sync_kernel (the same states, iterations and grid barriers), but in each leapfrog iteration
+// the C warps of a block compute the gradients of their chains together (block_logreg_grad, as
+// the FSM's batched kernel does), slot by slot: slot j is chain warp + j nwarps of every warp.
+// A chain's gradient does not depend on which chains share its block, so the samples equal the
+// FSM's bit for bit.
+template <typename T, int E, int C>
+__global__ void __launch_bounds__(32 * C) nuts_sync_batched_kernel(NutsView<T> v, int t_begin, int t_end,
+                                                                   GridBarrier bar, unsigned* active_cnt,
+                                                                   unsigned long long* iterations) {
+  extern __shared__ __align__(16) unsigned char nbs_smem[];
+  const GradSmem<T, C> sm = grad_smem<T, C>(reinterpret_cast<T*>(nbs_smem));
+  __shared__ unsigned blk_active;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = v.tg.d;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t slots = (v.m + nwarps - 1) / nwarps;  // chains per warp, the same for every warp
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  int iter = 0;
+  auto count_state = [&](int want, unsigned& total) -> bool {
+    if (threadIdx.x == 0) blk_active = 0;
+    __syncthreads();
+    unsigned mine = 0;
+    for (int64_t c = warp0; c < v.m; c += nwarps)
+      if (v.iv[I_ST * v.m + c] == want) ++mine;
+    if (lane == 0 && mine) atomicAdd(&blk_active, mine);
+    __syncthreads();
+    const int slot = iter % 3;
+    if (threadIdx.x == 0 && blk_active) atomicAdd(&active_cnt[slot], blk_active);
+    if (!grid_sync<kBarFlag>(bar, v.err)) return false;
+    total = read_after_grid_sync(&active_cnt[slot]);
+    if (leader) active_cnt[(iter + 2) % 3] = 0;
+    ++iter;
+    return true;
+  };
+  for (int t = t_begin; t < t_end; ++t) {
+    for (int64_t c = warp0; c < v.m; c += nwarps) {
+      Chain<T, E> s;
+      chain_load<T, E>(v, c, lane, s);
+      const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+      nuts_init<T, E>(v, key, lane, s);
+      nuts_double<T, E>(key, s);
+      chain_store<T, E>(v, c, lane, s);
+    }
+    while (true) {  // outer loop: doublings
+      while (true) {  // inner loop: leapfrog steps of the current subtrees
+        for (int64_t j = 0; j < slots; ++j) {
+          const int64_t c = warp0 + j * nwarps;
+          const bool act = c < v.m && v.iv[I_ST * v.m + c] == N_INTEGRATE;
+          if (!__syncthreads_or(act)) continue;  // no chain of the block integrates in this slot
+          Chain<T, E> s;
+          Leaf<T, E> lf;
+          if (act) {
+            chain_load<T, E>(v, c, lane, s);
+            nuts_lf_pre<T, E>(v, s, lf);
+          }
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int k = lane + 32 * e;
+            if (k < d) sm.th[k * C + warp] = act ? lf.xe[e] : T(0);
+          }
+          __syncthreads();
+          block_logreg_grad<T, C>(v.tg, sm);
+          if (act) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int k = lane + 32 * e;
+              lf.ge[e] = k < d ? sm.G[k * C + warp] : T(0);
+            }
+            const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+            Sub<T, E> sb;
+            const int r = nuts_lf_post<T, E>(v, key, c, lane, s, lf, sm.lp[warp], sb);
+            if (r == 1) { sub_store<T, E>(v, c, lane, sb); s.st = N_CHECK; }
+            if (r == 2) s.st = N_DONE;
+            chain_store<T, E>(v, c, lane, s);
+            if (lane == 0) v.steps[c] += 1;
+          }
+        }
+        unsigned building = 0;
+        if (!count_state(N_INTEGRATE, building)) return;
+        if (leader) *iterations += 1;
+        if (building == 0) break;
+      }
+      for (int64_t c = warp0; c < v.m; c += nwarps) {
+        if (v.iv[I_ST * v.m + c] != N_CHECK) continue;
+        Chain<T, E> s;
+        chain_load<T, E>(v, c, lane, s);
+        const Key key{(uint32_t)(v.chain0 + c), v.seed_lo, v.seed_hi};
+        Sub<T, E> sb;
+        sub_load<T, E>(v, c, lane, sb);
+        if (nuts_check<T, E>(v, key, s, sb)) nuts_double<T, E>(key, s);
+        else s.st = N_DONE;
+        chain_store<T, E>(v, c, lane, s);
+      }
+      unsigned doubling = 0;
+      if (!count_state(N_INTEGRATE, doubling)) return;
+      if (doubling == 0) break;
+    }
+    for (int64_t c = warp0; c < v.m; c += nwarps) {
+      Chain<T, E> s;
+      chain_load<T, E>(v, c, lane, s);
+      nuts_done<T, E>(v, c, lane, s);
+      chain_store<T, E>(v, c, lane, s);
+    }
+  }
+}
+
 template <typename T, int E>
 __global__ void __launch_bounds__(256) nuts_init_kernel(NutsView<T> v) {
   __shared__ T wsm_all[kWarpsMax][kWsm];
@@ -1097,6 +1205,20 @@ template <typename T, int E>
 static cudaError_t nuts_sync_launch(fsmc_job* j, int t0, int t1, GridBarrier bar, unsigned* active,
                                     unsigned long long* iters, cudaStream_t st) {
   NutsView<T> v = nuts_view<T>(j);
+  if (j->tg->kind == FSMC_TGT_LOGREG && j->tun.lanes_per_chain == 32) {  // the batched gradient
+    constexpr int C = kBatchChains;
+    auto kern = nuts_sync_batched_kernel<T, E, C>;
+    const size_t smem = grad_smem_bytes<T, C>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * C, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = std::min<int64_t>((int64_t)per_sm * j->e->sms, (j->m + C - 1) / C);
+    if (blocks < 1) blocks = 1;
+    void* args[] = {(void*)&v, (void*)&t0, (void*)&t1, (void*)&bar, (void*)&active, (void*)&iters};
+    return cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(32 * C), args, smem, st);
+  }
   auto kern = nuts_sync_kernel<T, E>;
   const int threads = j->tun.threads_per_block;
   int per_sm = 0;
