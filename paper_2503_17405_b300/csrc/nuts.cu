@@ -47,6 +47,7 @@ struct NutsView : ChainsView<T> {
   T* sub;   // [3][m][d]: completed subtree rho, prop x, prop grad (synchronised mode)
   T* subs;  // [2][m]: its prop log-density and log-weight
   int* aux; // [m][n] tree depth
+  int* sched;  // [2]: group rotation and block ticket of the batched FSM launch
 };
 
 template <typename T>
@@ -851,11 +852,38 @@ __device__ __forceinline__ void nuts_batched_block(const NutsView<T>& v, int64_t
   }
 }
 
+// The grid is at most the blocks that can be resident at once (P).  With G <= P chain groups
+// each block runs one group for `budget` states.  With G > P groups a launch of one group per
+// block would run in ceil(G / P) waves, the last one partly empty (4096 chains, 512 groups, 296
+// resident blocks: 1.73 waves' work in two waves' time), so each block runs several groups one
+// after another, and the block times are balanced instead: with G = a P + r, blocks below r take
+// a + 1 groups of `budget` states, the others a groups of budget + ceil(budget / a) states.  The
+// groups' order is rotated by sched[0], which the last block of a launch to finish advances by
+// the number of groups given the longer budget, so that every group takes it in turn.  Which
+// states run in which launch does not change any chain's samples.
 template <typename T, int E, int C>
 __global__ void __launch_bounds__(32 * C) nuts_fsm_batched_kernel(NutsView<T> v, int budget) {
   extern __shared__ __align__(16) unsigned char nb_smem[];
   const GradSmem<T, C> sm = grad_smem<T, C>(reinterpret_cast<T*>(nb_smem));
-  nuts_batched_block<T, E, C>(v, blockIdx.x, budget, sm);
+  const int64_t G = (v.m + C - 1) / C, P = gridDim.x, b = blockIdx.x;
+  if (G <= P) {
+    nuts_batched_block<T, E, C>(v, b, budget, sm);
+    return;
+  }
+  const int64_t a = G / P, r = G % P;
+  const int64_t first = b < r ? b * (a + 1) : r * (a + 1) + (b - r) * a;
+  const int64_t cnt = b < r ? a + 1 : a;
+  const int gb = b < r ? budget : budget + (int)((budget + a - 1) / a);
+  const int64_t rot = *(volatile int*)&v.sched[0];
+  for (int64_t k = 0; k < cnt; ++k) nuts_batched_block<T, E, C>(v, (first + k + rot) % G, gb, sm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&v.sched[1], 1) == (int)P - 1) {
+      v.sched[1] = 0;
+      v.sched[0] = (int)((rot + (P - r) * a) % G);
+    }
+  }
 }
 
 // Fused launch over several logistic-regression NUTS jobs (serving): job k owns blocks
@@ -1140,6 +1168,7 @@ static NutsView<T> nuts_view(const fsmc_job* j) {
   v.stks = (T*)(b + take(m * kLevels * 2 * es));
   v.sub = (T*)(b + take(3 * m * d * es));
   v.subs = (T*)(b + take(2 * m * es));
+  v.sched = (int*)(b + take(64));
   v.aux = (int*)(b + j->o_aux);
   return v;
 }
@@ -1161,6 +1190,7 @@ void nuts_layout(fsmc_job* j, size_t& off) {
   take(m * kLevels * 2 * es);
   take(3 * m * d * es);
   take(2 * m * es);
+  take(64);  // batched FSM launch schedule (rotation, ticket)
   j->o_nuts_end = off;
 }
 
@@ -1191,7 +1221,11 @@ static cudaError_t nuts_fsm_launch(fsmc_job* j, cudaStream_t st) {
     const size_t smem = grad_smem_bytes<T, C>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (j->m + C - 1) / C;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * C, smem);
+    if (e != cudaSuccess) return e;
+    // at most the resident blocks; more groups than that are balanced over them
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((j->m + C - 1) / C, (int64_t)per_sm * j->e->sms));
     kern<<<(unsigned)blocks, 32 * C, smem, st>>>(v, j->tun.steps_per_launch);
     return cudaGetLastError();
   }
