@@ -386,7 +386,10 @@ static void default_tuning(fsmc_job* j) {
     // long launches: fewer kernel tails (funnel, 65536 chains: DR 48.8 -> 48.0 ms, slice 47.4 ->
     // 45.9 ms per job from 256 to 1024 states per launch)
     if (!tu.steps_per_launch) tu.steps_per_launch = 1024;
-    if (!tu.threads_per_block) tu.threads_per_block = 128;
+    // chain per thread: 256-thread blocks (funnel, 65536 chains, ms per job for 32 / 64 / 128 /
+    // 256 threads: DR 45.8 / 45.9 / 45.9 / 44.4, slice 43.9 / 44.1 / 44.0 / 43.6); chain per
+    // warp: 128 (the warp kernels' bound)
+    if (!tu.threads_per_block) tu.threads_per_block = tu.lanes_per_chain == 1 ? 256 : 128;
   } else {
     if (!tu.lanes_per_chain) tu.lanes_per_chain = 32;
     // leapfrog steps per launch: enough that a launch's tail (its slowest warp) and the launch

@@ -151,6 +151,41 @@ __device__ __forceinline__ void group_sum_n(T (&v)[N], unsigned mask = 0xfffffff
 }
 
 
+// ---- balanced FSM launch over a resident grid ------------------------------------------------
+// An FSM launch runs every unit (a chain, or a group of chains that share a block) for `budget`
+// states.  With one unit per worker (warp or block) and more units than workers that can be
+// resident (P), a latency-bound launch takes ceil(G / P) waves of time for G / P waves of work
+// (NUTS on logistic regression, 4096 chains in 512 blocks of eight, 296 resident: 1.73 waves
+// in two).  Instead the grid is P resident workers and each runs its share of the units one
+// after another, with the workers' times balanced: for G = a P + r, workers below r take a + 1
+// units of `budget` states, the others a units of budget + ceil(budget / a) states.  The order of the units is rotated by rot (sched[0]), which
+// the last block of each launch advances by the units that took the longer budget, so that
+// every unit takes it in turn.  Which states run in which launch changes no chain's samples.
+struct BalancedRun {
+  int64_t first, count;  // units first .. first + count - 1 (before rotation)
+  int budget;            // states per unit
+};
+__device__ __forceinline__ BalancedRun balanced_run(int64_t G, int64_t P, int64_t w, int budget) {
+  if (G <= P) return BalancedRun{w, w < G ? 1 : 0, budget};
+  const int64_t a = G / P, r = G % P;
+  if (w < r) return BalancedRun{w * (a + 1), a + 1, budget};
+  return BalancedRun{r * (a + 1) + (w - r) * a, a, budget + (int)((budget + a - 1) / a)};
+}
+// After the block's last unit (every thread of the block calls it): the block's arrival on
+// sched[1]; the last of the grid's blocks advances the rotation sched[0].  The next launch on the
+// stream reads the new value.
+__device__ __forceinline__ void balanced_done(int* sched, int64_t G, int64_t P, int rot) {
+  __syncthreads();
+  if (threadIdx.x == 0 && G > P) {
+    __threadfence();
+    if (atomicAdd(&sched[1], 1) == (int)gridDim.x - 1) {
+      const int64_t a = G / P, r = G % P;
+      sched[1] = 0;
+      sched[0] = (int)((rot + (P - r) * a) % G);
+    }
+  }
+}
+
 // ---- bounded grid barrier (cooperative launches only) ----------------------------------------
 // Counting barrier in two forms; both count arrivals in count[0] (zeroed by the host before
 // every launch, kGridBarrierBytes), so that with n = blocks (+ missing) the arrival that sees

@@ -585,6 +585,9 @@ __device__ __forceinline__ void nuts_advance_chain(const NutsView<T>& v, int64_t
   if (lane == 0) v.steps[c] += steps;
 }
 
+// A chain per warp.  (A resident grid with balanced warp times, as the batched kernel has, was
+// measured slower here: 240 against 236 ms per 4096-chain mixture job; the chains' states vary
+// in cost, and the hardware's block scheduler already evens out the blocks' times.)
 template <typename T, int E>
 __global__ void __launch_bounds__(256) nuts_fsm_kernel(NutsView<T> v, int budget) {
   __shared__ T wsm_all[kWarpsMax][kWsm];
@@ -852,38 +855,17 @@ __device__ __forceinline__ void nuts_batched_block(const NutsView<T>& v, int64_t
   }
 }
 
-// The grid is at most the blocks that can be resident at once (P).  With G <= P chain groups
-// each block runs one group for `budget` states.  With G > P groups a launch of one group per
-// block would run in ceil(G / P) waves, the last one partly empty (4096 chains, 512 groups, 296
-// resident blocks: 1.73 waves' work in two waves' time), so each block runs several groups one
-// after another, and the block times are balanced instead: with G = a P + r, blocks below r take
-// a + 1 groups of `budget` states, the others a groups of budget + ceil(budget / a) states.  The
-// groups' order is rotated by sched[0], which the last block of a launch to finish advances by
-// the number of groups given the longer budget, so that every group takes it in turn.  Which
-// states run in which launch does not change any chain's samples.
+// The grid is at most the blocks that can be resident at once; with more chain groups than
+// blocks each block runs several groups in turn, the block times balanced (balanced_run).
 template <typename T, int E, int C>
 __global__ void __launch_bounds__(32 * C) nuts_fsm_batched_kernel(NutsView<T> v, int budget) {
   extern __shared__ __align__(16) unsigned char nb_smem[];
   const GradSmem<T, C> sm = grad_smem<T, C>(reinterpret_cast<T*>(nb_smem));
-  const int64_t G = (v.m + C - 1) / C, P = gridDim.x, b = blockIdx.x;
-  if (G <= P) {
-    nuts_batched_block<T, E, C>(v, b, budget, sm);
-    return;
-  }
-  const int64_t a = G / P, r = G % P;
-  const int64_t first = b < r ? b * (a + 1) : r * (a + 1) + (b - r) * a;
-  const int64_t cnt = b < r ? a + 1 : a;
-  const int gb = b < r ? budget : budget + (int)((budget + a - 1) / a);
-  const int64_t rot = *(volatile int*)&v.sched[0];
-  for (int64_t k = 0; k < cnt; ++k) nuts_batched_block<T, E, C>(v, (first + k + rot) % G, gb, sm);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&v.sched[1], 1) == (int)P - 1) {
-      v.sched[1] = 0;
-      v.sched[0] = (int)((rot + (P - r) * a) % G);
-    }
-  }
+  const int64_t G = (v.m + C - 1) / C, P = gridDim.x;
+  const int rot = G > P ? *(volatile int*)&v.sched[0] : 0;
+  const BalancedRun q = balanced_run(G, P, blockIdx.x, budget);
+  for (int64_t k = 0; k < q.count; ++k) nuts_batched_block<T, E, C>(v, (q.first + k + rot) % G, q.budget, sm);
+  balanced_done(v.sched, G, P, rot);
 }
 
 // Fused launch over several logistic-regression NUTS jobs (serving): job k owns blocks
