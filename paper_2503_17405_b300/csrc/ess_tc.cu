@@ -335,13 +335,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
     constexpr int kPasses = 64 / (2 * kGroupWarps);  // core-matrix pairs per warp per chunk
     // accumulators of local tile i -> the chains' direction rings
     // (warp w: row tile (w >> 2) & 1, tensor-memory lane quadrant w & 3, column half w >> 3)
+    // this thread's epilogue row (the same for every tile) and the sign folded into it
+    // (ess_ring_folded), read once
+    const int ep_row = ((warp >> 2) & 1) * 128 + (warp & 3) * 32 + lane;
+    const uint32_t sgn = fold && ep_row < d && v.tg.vec[ep_row] > 0.f ? 0x80000000u : 0u;
     auto epilogue = [&](long long i) {
       const int bb = (int)(i & 1);
       if (!warp_wait(&bars->acc_full[bb], (unsigned)((i >> 1) & 1), fail)) { *fail = 1; return; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int rt = (warp >> 2) & 1;
       if (rt == 0 || lay.K1) {
-        const int row = rt * 128 + (warp & 3) * 32 + lane;
+        const int row = ep_row;
         const int jbeg = (warp >> 3) * (TC_N / 2);
         // both 16-column loads in flight before the single wait
         uint32_t r[TC_N / 2];
@@ -360,7 +364,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ess_nu_gen_tc_kernel(EssView<fl
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (row < d) {
-          const uint32_t sgn = fold && v.tg.vec[row] > 0.f ? 0x80000000u : 0u;  // ess_ring_folded
 #pragma unroll
           for (int jj = 0; jj < TC_N / 2; ++jj) {
             float* dst = cols->dst[bb][jbeg + jj];
