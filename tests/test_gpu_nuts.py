@@ -120,6 +120,47 @@ def test_sync_and_fsm_identical_fp32(eng):
     b.close()
 
 
+def test_balanced_grid_with_more_groups_than_resident_blocks(eng):
+    """5000 chains are 625 groups of eight, more than the blocks that can be resident (two per
+    SM), so each block of the batched FSM launch runs several groups with balanced budgets and
+    the assignment rotates from launch to launch.  Which launch runs a state must not change any
+    chain: the samples equal the synchronised program's bit for bit, and a run stopped after a
+    few launches and resumed from a snapshot in a fresh job equals the uninterrupted run."""
+    w = W.logreg(1000, 25)
+    nuts = {"eps": 0.05, "max_depth": 10, "max_dH": 1000.0}
+    m, n = 5000, 12
+    x0 = W.x0_logreg(w, m)
+    tg = eng.target("logreg", 25, w["params"], n_data=1000)
+    tu = {"steps_per_launch": 16}
+
+    def job():
+        return eng.job(tg, "nuts", m, n, x0=x0, seed=1, prec="fp32", nuts=nuts, tuning=tu)
+
+    a = job()
+    a.run("fsm")
+    ca, da, sa = a.loop_counts()
+    assert (sa > 16 * 4).all()  # every chain ran over several launches
+    b = job()
+    b.run("sync")
+    cb, db, _ = b.loop_counts()
+    assert np.array_equal(ca, cb) and np.array_equal(da, db)
+    assert np.array_equal(a.samples(), b.samples())
+    b.close()
+    part = job()
+    part.run("fsm", max_fsm_steps=48)
+    assert not part.progress()[1]
+    blob = part.snapshot()
+    part.close()
+    fresh = job()
+    fresh.restore(blob)
+    fresh.run("fsm")
+    cf, df, sf = fresh.loop_counts()
+    assert np.array_equal(ca, cf) and np.array_equal(da, df) and np.array_equal(sa, sf)
+    assert np.array_equal(a.samples(), fresh.samples())
+    fresh.close()
+    a.close()
+
+
 @pytest.fixture(scope="module")
 def full_nuts_job(eng):
     """4096 chains x 1000 draws of NUTS on logistic regression (1000 x 25), FP32."""
