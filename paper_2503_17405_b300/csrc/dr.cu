@@ -578,7 +578,7 @@ __global__ void dr_init_kernel(DrView<T> v) {
   v.lp[c] = lp;
 }
 
-// ---- a chain per warp (32 < d <= 1024; the benchmark spec's layout for wider log-densities) -------------
+// ---- a chain per warp (32 < d <= 1024: the layout for log-densities too wide for one thread) -------
 // Lane l holds coordinates k = e 32 + l (e < E) of x, y1, y2 and the proposal; every sum over
 // coordinates (the log density's, the proposal densities' squared distances) is a warp sum, and
 // the chain's scalars (log pi values, the kept ratio terms, the stage) are the same in every lane.
