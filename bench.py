@@ -158,17 +158,34 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = None
+        self.skip = 0
+
+    def _lines(self):
+        with open(self.path) as f:
+            return sum(1 for _ in f)
 
     def start(self):
+        """Starts nvidia-smi (a sample every 50 ms) and returns once it has written its first
+        sample, so that the timed region that follows is sampled; samples written before the
+        region starts are left out (mark)."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while self._lines() == 0 and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self):
+        """The timed region starts: later samples only."""
+        if self.proc is not None:
+            self.skip = self._lines()
 
     def stop(self):
         if self.proc is None:
@@ -184,6 +201,8 @@ class ClockSampler:
             if len(parts) >= 9:
                 rows.append(parts)
         os.unlink(self.path)
+        # the samples of the timed region (all of them if it was shorter than one interval)
+        rows = rows[self.skip:] or rows[-1:]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -311,10 +330,11 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         one("fsm")
     clocks = ClockSampler(dev)
+    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark()
     fsm_ms, stats = [], []
     for _ in range(args.steps):
         ms, st = one("fsm")
